@@ -1,0 +1,334 @@
+"""Pins of the FP64 CPU oracle against facts fixed outside the oracle itself.
+
+Each test names the paper passage or the mathematical fact it pins.  None of
+them compares the oracle with a retyping of its own formulas: the references
+are the paper's printed table, the second-quantised definition of H built
+from Jordan-Wigner matrices (numpy/scipy Kronecker products), closed forms,
+library routines (numpy eigh, scipy expm) and invariants.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.sparse as sp
+
+import oracle
+from oracle import adapt as oadapt
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small_system(n, na, nb, seed, h2_scale=1.0):
+    h1, h2, ec = synth.integrals(n, seed)
+    return oracle.System(h1, h2 * h2_scale, ec, n, na, nb)
+
+
+# --------------------------------------------------------------------------
+# Table 1 (paper, "tab:hilbert_ci_sizes"): sizes of Omega_CI and Omega_CIk
+# --------------------------------------------------------------------------
+def _table1():
+    rows = []
+    with open(os.path.join(GOLD, "table1_sizes.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, ne, q, ci, cik = line.split()
+            rows.append((name, int(ne), int(q), int(ci), int(cik)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _table1(), ids=lambda r: r[0])
+def test_table1_space_sizes(row):
+    name, ne, q, ci, cik = row
+    n = q // 2
+    assert oracle.binom(2 * n, ne) == ci
+    s = oracle.System(np.zeros((n, n)), np.zeros((n,) * 4), 0.0, n, ne // 2,
+                      ne // 2)
+    assert s.n_det == cik
+    assert s.n_astr * s.n_bstr == cik
+
+
+def test_enumeration_is_bijective_colex():
+    """Determinant index = position among all strings in increasing numeric
+    (colexicographic) order; brute force over all 2^n masks."""
+    n, na, nb = 7, 4, 3
+    s = small_system(n, na, nb, 1)
+    dets = s.dets()
+    assert len(set(dets.tolist())) == s.n_det
+    alphas = [m for m in range(1 << n) if bin(m).count("1") == na]
+    betas = [m for m in range(1 << n) if bin(m).count("1") == nb]
+    expect = [a | (b << n) for a in alphas for b in betas]
+    assert dets.tolist() == expect
+    for i in range(0, s.n_det, 7):
+        assert s.index(int(dets[i])) == i
+
+
+# --------------------------------------------------------------------------
+# Jordan-Wigner matrices built by Kronecker products (independent of the
+# oracle's bit-level sign rule).  Qubit j = spin orbital j (blocked order);
+# basis index = sum_j n_j 2^j, so qubit 0 is the rightmost Kronecker factor.
+# --------------------------------------------------------------------------
+_SM = sp.csr_matrix(np.array([[0.0, 1.0], [0.0, 0.0]]))   # |0><1|: destroys
+_Z = sp.csr_matrix(np.diag([1.0, -1.0]))
+_I = sp.identity(2, format="csr")
+
+
+def jw_annihilators(M):
+    ops = []
+    for j in range(M):
+        factors = [_I] * (M - 1 - j) + [_SM] + [_Z] * j
+        m = factors[0]
+        for f in factors[1:]:
+            m = sp.kron(m, f, format="csr")
+        ops.append(m)
+    return ops
+
+
+def jw_hamiltonian(h1, h2, e_core, n):
+    M = 2 * n
+    a = jw_annihilators(M)
+    ad = [x.T.tocsr() for x in a]
+    dim = 1 << M
+    H = sp.identity(dim, format="csr") * e_core
+    spin = lambda P: P // n
+    orb = lambda P: P % n
+    for P in range(M):
+        for Q in range(M):
+            if spin(P) == spin(Q) and h1[orb(P), orb(Q)] != 0:
+                H = H + h1[orb(P), orb(Q)] * (ad[P] @ a[Q])
+    for P, Q, R, S in itertools.product(range(M), repeat=4):
+        if spin(P) != spin(Q) or spin(R) != spin(S):
+            continue
+        c = h2[orb(P), orb(Q), orb(R), orb(S)]
+        if c != 0:
+            H = H + 0.5 * c * (ad[P] @ ad[R] @ a[S] @ a[Q])
+    return H.tocsr(), a
+
+
+def test_operator_definition_matches_jordan_wigner():
+    """orc_apply_ops on every basis state of 6 modes == JW Kronecker matrices."""
+    M = 6
+    a = jw_annihilators(M)
+    for mode in range(M):
+        for dag in (0, 1):
+            mat = (a[mode].T if dag else a[mode]).toarray()
+            for d in range(1 << M):
+                res = oracle.apply_operator_string([2 * mode + dag], d)
+                col = mat[:, d]
+                if res is None:
+                    assert np.all(col == 0)
+                else:
+                    out, sg = res
+                    assert col[out] == sg
+                    assert np.count_nonzero(col) == 1
+
+
+@pytest.mark.parametrize("n,na,nb", [(3, 2, 1), (4, 2, 2), (5, 3, 2)])
+def test_slater_condon_equals_jordan_wigner_hamiltonian(n, na, nb):
+    """Dense Slater-Condon H on Omega_CIk == the JW-mapped second-quantised H
+    restricted to Omega_CIk, and the full JW H has no matrix elements that
+    leave the sector (number and S_z conservation)."""
+    h1, h2, _ = synth.integrals(n, 7 + n)
+    e_core = 0.37
+    s = oracle.System(h1, h2, e_core, n, na, nb)
+    Hjw, _ = jw_hamiltonian(h1, h2, e_core, n)
+    dets = s.dets().astype(np.int64)
+    Hd = Hjw.toarray()
+    sub = Hd[np.ix_(dets, dets)]
+    assert np.allclose(sub, s.dense_h(), atol=1e-12, rtol=0)
+    # no leakage: rows outside the sector receive nothing from sector columns
+    mask = np.zeros(Hd.shape[0], dtype=bool)
+    mask[dets] = True
+    assert np.abs(Hd[np.ix_(~mask, dets)]).max() < 1e-14
+    # Hermiticity of the definition
+    assert np.abs(Hd - Hd.T).max() < 1e-12
+
+
+@pytest.mark.parametrize("n,na,nb", [(4, 2, 2), (5, 2, 3), (6, 3, 3)])
+def test_sigma_equals_term_by_term_definition(n, na, nb):
+    s = small_system(n, na, nb, 11 + n)
+    psi = synth.random_state(s.n_det, 5)
+    assert np.allclose(s.sigma(psi), s.sigma_definition(psi), atol=1e-12,
+                       rtol=0)
+
+
+def test_sigma_hermitian_and_sampled_rows():
+    s = small_system(8, 4, 4, 1005)
+    x = synth.random_state(s.n_det, 1)
+    y = synth.random_state(s.n_det, 2)
+    sx, sy = s.sigma(x), s.sigma(y)
+    assert abs(y @ sx - x @ sy) < 1e-12
+    rows = np.arange(0, s.n_det, 97)
+    assert np.array_equal(s.sigma_rows(x, rows), sx[rows])
+
+
+def test_one_electron_closed_form():
+    """One alpha electron: H on Omega_CIk is h1 + e_core exactly."""
+    n = 5
+    h1, h2, _ = synth.integrals(n, 3)
+    s = oracle.System(h1, h2, 0.25, n, 1, 0)
+    assert np.allclose(s.dense_h(), h1 + 0.25 * np.eye(n), atol=1e-14)
+
+
+def test_noninteracting_fci_closed_form():
+    """h2 = 0: the ground energy is the sum of the lowest n_alpha and n_beta
+    eigenvalues of h1 (one Slater determinant of h1 eigenorbitals)."""
+    n, na, nb = 6, 3, 2
+    h1, h2, _ = synth.integrals(n, 17)
+    s = oracle.System(h1, 0 * h2, 0.0, n, na, nb)
+    w = np.linalg.eigvalsh(h1)
+    assert abs(s.fci_energy() - (w[:na].sum() + w[:nb].sum())) < 1e-12
+
+
+def test_two_orbital_two_electron_closed_form():
+    """Two orbitals, one alpha + one beta electron, integrals chosen with only
+    (00|00), (11|11), (00|11), (01|01) nonzero and h1 diagonal: the S_z = 0
+    block is the textbook 4x4 minimal-basis H2 matrix."""
+    n = 2
+    h1 = np.diag([-1.2, -0.4])
+    h2 = np.zeros((2, 2, 2, 2))
+    J00, J11, J01, K = 0.6, 0.5, 0.55, 0.15
+    h2[0, 0, 0, 0] = J00
+    h2[1, 1, 1, 1] = J11
+    h2[0, 0, 1, 1] = h2[1, 1, 0, 0] = J01
+    for idx in [(0, 1, 0, 1), (1, 0, 1, 0), (0, 1, 1, 0), (1, 0, 0, 1)]:
+        h2[idx] = K
+    s = oracle.System(h1, h2, 0.0, 2, 1, 1)
+    H = s.dense_h()
+    # basis (a, b) in index order: (0,0), (0,1), (1,0), (1,1) of orbitals
+    e00 = 2 * h1[0, 0] + J00
+    e11 = 2 * h1[1, 1] + J11
+    e01 = h1[0, 0] + h1[1, 1] + J01
+    assert np.isclose(H[0, 0], e00) and np.isclose(H[3, 3], e11)
+    assert np.isclose(H[1, 1], e01) and np.isclose(H[2, 2], e01)
+    # open-shell pair coupled by exchange, closed shells by K (|K| each)
+    assert np.isclose(abs(H[1, 2]), K) and np.isclose(abs(H[0, 3]), K)
+    assert np.isclose(H[0, 1], 0) and np.isclose(H[0, 2], 0)
+    ev = np.linalg.eigvalsh(H)
+    assert np.isclose(ev[0], s.fci_energy())
+
+
+def test_variational_bound():
+    s = small_system(6, 3, 3, 1001)
+    e0 = s.fci_energy()
+    for seed in range(5):
+        psi = synth.random_state(s.n_det, seed)
+        assert s.energy(psi) >= e0 - 1e-12
+
+
+# --------------------------------------------------------------------------
+# pool, exp(theta A) and gradients
+# --------------------------------------------------------------------------
+def _pool_count(o, v):
+    c2 = lambda x: x * (x - 1) // 2
+    return (o * v + c2(o) * c2(v) + 2 * c2(o) * c2(v) + o * v
+            + 2 * o * c2(v) + 2 * c2(o) * v)
+
+
+@pytest.mark.parametrize("n", [4, 6, 8])
+def test_pool_size_closed_shell(n):
+    s = small_system(n, n // 2, n // 2, 1)
+    assert len(s.pool()) == _pool_count(n // 2, n - n // 2)
+
+
+def _dense_generator_jw(op, n, dets, a):
+    ad = [x.T.tocsr() for x in a]
+    A = None
+    for q in range(op[0]):
+        t = op[1 + 5 * q: 6 + 5 * q]
+        if t[0] == 1:
+            C = ad[t[1]] @ a[t[4]]
+        else:
+            C = ad[t[1]] @ ad[t[2]] @ a[t[3]] @ a[t[4]]
+        term = C - C.T
+        A = term if A is None else A + term
+    return A.toarray()[np.ix_(dets, dets)]
+
+
+def test_generator_and_exponential_against_jw_and_expm():
+    """A_k built by the oracle == JW Kronecker A_k on Omega_CIk; the closed
+    form exp(theta A) == scipy expm; constituents commute; norm preserved."""
+    n, na, nb = 4, 2, 2
+    s = small_system(n, na, nb, 23)
+    pool = s.pool()
+    a = jw_annihilators(2 * n)
+    dets = s.dets().astype(np.int64)
+    psi = synth.random_state(s.n_det, 9)
+    eye = np.eye(s.n_det)
+    for op in pool:
+        Ajw = _dense_generator_jw(op, n, dets, a)
+        Aor = np.stack([s.apply_generator(op, eye[:, j])
+                        for j in range(s.n_det)], axis=1)
+        assert np.allclose(Aor, Ajw, atol=1e-15)
+        assert np.allclose(Ajw, -Ajw.T)
+        for theta in (0.3, -1.1):
+            ref = scipy.linalg.expm(theta * Ajw) @ psi
+            got = s.apply_excitation(op, theta, psi)
+            assert np.allclose(got, ref, atol=1e-13)
+            assert abs(np.linalg.norm(got) - 1.0) < 1e-14
+        if op[0] == 2:
+            parts = []
+            for q in range(2):
+                one = op.copy()
+                one[0] = 1
+                one[1:6] = op[1 + 5 * q: 6 + 5 * q]
+                parts.append(_dense_generator_jw(one, n, dets, a))
+            comm = parts[0] @ parts[1] - parts[1] @ parts[0]
+            assert np.abs(comm).max() < 1e-14
+
+
+def test_pool_constituents_valid_on_hf():
+    s = small_system(6, 3, 3, 1001)
+    hf = s.hf_state()
+    for op in s.pool():
+        v = s.apply_generator(op, hf)
+        assert np.linalg.norm(v) > 0.5   # each op excites HF
+
+
+@pytest.mark.parametrize("n,na,nb,step", [(6, 3, 3, 1), (8, 4, 4, 37)])
+def test_gradient_matches_central_differences(n, na, nb, step):
+    """g_k = dE/dtheta at 0 checked by (E(+h) - E(-h)) / 2h, h = 1e-4."""
+    s = small_system(n, na, nb, 1001 if n == 6 else 1005)
+    pool = s.pool()
+    # a correlated state: a few excitations away from HF
+    psi = s.hf_state()
+    for k, t in [(0, 0.2), (len(pool) - 1, -0.3), (len(pool) // 2, 0.15)]:
+        psi = s.apply_excitation(pool[k], t, psi)
+    sigma = s.sigma(psi)
+    g = s.gradients(pool, psi, sigma)
+    h = 1e-4
+    for k in range(0, len(pool), step):
+        ep = s.energy(s.apply_excitation(pool[k], h, psi))
+        em = s.energy(s.apply_excitation(pool[k], -h, psi))
+        assert abs((ep - em) / (2 * h) - g[k]) < 1e-7
+
+
+# --------------------------------------------------------------------------
+# ADAPT-VQE loop
+# --------------------------------------------------------------------------
+def test_adapt_monotone_and_above_fci():
+    """Energies decrease monotonically and stay above E_FCI (variational)."""
+    s = small_system(6, 3, 3, 1001)
+    pool = s.pool()
+    rec = oadapt.run(s, pool, max_iter=8)
+    e = np.array(rec["energy"])
+    efci = s.fci_energy()
+    assert np.all(np.diff(e) <= 1e-12)
+    assert np.all(e >= efci - 1e-12)
+    assert e[-1] < s.energy(s.hf_state())
+
+
+def test_adapt_singles_reach_noninteracting_ground_state():
+    """h2 = 0: singles-only ADAPT reaches E_FCI (Thouless: the ground state is
+    an orbital rotation of HF)."""
+    n, na, nb = 4, 2, 2
+    h1, h2, _ = synth.integrals(n, 41)
+    s = oracle.System(h1, 0 * h2, 0.0, n, na, nb)
+    pool = s.pool()
+    singles = [k for k, op in enumerate(pool)
+               if all(op[1 + 5 * q] == 1 for q in range(op[0]))]
+    rec = oadapt.run(s, pool, max_iter=30, eps_grad=1e-9, pool_subset=singles)
+    assert abs(rec["energy"][-1] - s.fci_energy()) < 1e-9
