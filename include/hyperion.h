@@ -1,0 +1,208 @@
+/*
+ * hyperion.h -- C ABI of the GB300 state-vector ADAPT-VQE hot path.
+ *
+ * The operations follow the statement of the problem in arXiv 2604.01176
+ * ("High Performance Quantum Emulation for Chemistry Applications with
+ * Hyperion"):
+ *   - the variational energy E(theta) = <psi|H|psi> of a real molecular
+ *     Hamiltonian (Method section, Eq. "ev");
+ *   - H mapped to qubits by Jordan-Wigner and applied to a state held only on
+ *     the particle- and S_z-conserving determinant space Omega_CIk
+ *     (Sparse State-Vector Emulation section, Table 1);
+ *   - the three sparse operations the paper's library provides: H times a
+ *     state, inner products, and the application of an exponentiated
+ *     fermionic operator (same section);
+ *   - the ADAPT-VQE pool-gradient screen (Numerical performance subsection).
+ *
+ * Conventions shared by every call
+ *   - Spin orbitals are in blocked order: qubit p is orbital p alpha for
+ *     p < n_orb, qubit n_orb + p is orbital p beta.  A determinant is a
+ *     2*n_orb-bit occupation mask (uint64, alpha block in the low bits).
+ *   - An alpha (beta) string is an n_orb-bit mask; its rank is the
+ *     colexicographic combinadic rank sum_i C(pos_i, i+1) over its set bits
+ *     pos_0 < pos_1 < ...  The determinant index is
+ *     I = rank(alpha) * N_beta + rank(beta); a state vector is a dense array
+ *     of N_det = N_alpha * N_beta amplitudes in that order.
+ *   - Precision: HY_F64 computes in double; HY_F32 keeps amplitudes and the
+ *     bulk arithmetic in float with float accumulation.  Energies, norms,
+ *     dot products and gradients are always accumulated and returned in
+ *     double.
+ *   - Ownership: the caller owns every state vector and output buffer passed
+ *     in (device pointers unless stated "host") and the CUDA stream (passed
+ *     as void*, NULL = legacy default stream).  The library owns the tables
+ *     inside hy_ham / hy_pool and a per-handle workspace it allocates with
+ *     cudaMalloc on first use (so make the first call of each kind before
+ *     capturing a CUDA graph).  All launches are stream-ordered; no call
+ *     synchronises the host except where stated.
+ *   - Errors: every call returns hy_status; hy_last_error() gives a message
+ *     for the calling thread's most recent failure.  Sizes and arguments are
+ *     validated on the host before any launch; no call traps on the device.
+ *   - Limits: 1 <= n_orb <= 16 (32 qubits), 0 <= n_alpha, n_beta <= n_orb.
+ *   - Threading: calls on one handle must not overlap in time on different
+ *     streams (they share the handle's workspace).
+ */
+#ifndef HYPERION_H
+#define HYPERION_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HY_OK = 0,
+    HY_ERR_ARG = 1,          /* invalid argument, size or shape            */
+    HY_ERR_CUDA = 2,         /* a CUDA runtime call failed                 */
+    HY_ERR_OOM = 3,          /* device or host allocation failed          */
+    HY_ERR_TIMEOUT = 4,      /* a bounded device wait ran out              */
+    HY_ERR_UNSUPPORTED = 5   /* input outside what the library implements */
+} hy_status;
+
+typedef enum { HY_F64 = 0, HY_F32 = 1 } hy_dtype;
+
+typedef enum { HY_POOL_SPIN_ADAPTED_SD = 0 } hy_pool_kind;
+
+typedef struct hy_ham hy_ham;
+typedef struct hy_pool hy_pool;
+
+/* Message describing the calling thread's most recent error ("" if none). */
+const char *hy_last_error(void);
+
+/* Library version string. */
+const char *hy_version(void);
+
+/* ---------------------------------------------------------------------- */
+/* Hamiltonian                                                              */
+/* ---------------------------------------------------------------------- */
+
+/* Build H from integrals (Sparse State-Vector Emulation section: fermionic
+ * operators mapped to qubits and summed; Methods: the Hamiltonian is real).
+ *   h1     host, n_orb*n_orb row-major one-electron integrals h_pq (symmetric)
+ *   h2     host, n_orb^4 two-electron integrals in chemists' notation,
+ *          (pq|rs) at ((p*n+q)*n+r)*n+s, with (pq|rs) = (qp|sr) = (rs|pq)
+ *   e_core constant energy added to the diagonal
+ *   prune_tol  Pauli terms with |coefficient| <= prune_tol are dropped
+ *          (the paper builds its Hamiltonian with a 1e-14 threshold)
+ * H = e_core + sum h_pq a+_ps a_qs + 1/2 sum (pq|rs) a+_ps a+_rt a_st a_qs.
+ * The build maps every term by Jordan-Wigner into a table of Pauli strings
+ * grouped by X-mask, derives the kernel tables from that table, and uploads
+ * them to the current CUDA device.  Returns HY_ERR_ARG for bad sizes or
+ * integrals that are not symmetric to 1e-12, HY_ERR_OOM on allocation
+ * failure.  *out receives an owned handle (free with hy_ham_destroy). */
+hy_status hy_build_hamiltonian(const double *h1, const double *h2,
+                               double e_core, int n_orb, int n_alpha,
+                               int n_beta, double prune_tol, hy_ham **out);
+
+/* Host-only build of the Jordan-Wigner Pauli table of H (no CUDA device is
+ * touched; same integrals, conventions and pruning as hy_build_hamiltonian).
+ * Terms are returned as in hy_ham_pauli_table.  Call with capacity 0 (or any
+ * output NULL) to obtain *n_terms and *n_groups only; otherwise x, z and
+ * coeff need room for capacity >= *n_terms entries and group_offsets for
+ * capacity + 1.  Returns HY_ERR_ARG for bad sizes or non-symmetric
+ * integrals, HY_ERR_ARG also when capacity is too small (sizes still set). */
+hy_status hy_pauli_table_build(const double *h1, const double *h2,
+                               double e_core, int n_orb, double prune_tol,
+                               int64_t capacity, uint64_t *x, uint64_t *z,
+                               double *coeff, int64_t *group_offsets,
+                               int64_t *n_terms, int64_t *n_groups);
+
+/* Release a handle and its device memory (NULL is accepted). */
+hy_status hy_ham_destroy(hy_ham *h);
+
+/* Sizes: determinants, alpha / beta strings, X-mask groups, Pauli terms.
+ * Any output pointer may be NULL. */
+hy_status hy_ham_info(const hy_ham *h, int64_t *n_det, int64_t *n_alpha_str,
+                      int64_t *n_beta_str, int64_t *n_groups,
+                      int64_t *n_terms);
+
+/* Copy the Pauli table (host outputs, caller-allocated).  Term t is
+ * coeff[t] * P(x[t], z[t]) where P is the Hermitian Pauli string with X on
+ * bits of x & ~z, Z on z & ~x and Y on x & z (bit j = qubit j).  Terms are
+ * sorted by (x, z); group g holds terms group_offsets[g] .. [g+1]-1 and all
+ * share x.  Arrays hold n_terms (x, z, coeff) and n_groups + 1 entries. */
+hy_status hy_ham_pauli_table(const hy_ham *h, uint64_t *x, uint64_t *z,
+                             double *coeff, int64_t *group_offsets);
+
+/* ---------------------------------------------------------------------- */
+/* Determinant indexing (bit-exact)                                         */
+/* ---------------------------------------------------------------------- */
+
+/* idx[i] = index of determinant dets[i], or -1 if it is not in Omega_CIk.
+ * dets, idx: device arrays of m entries. */
+hy_status hy_rank(const hy_ham *h, const uint64_t *dets, int64_t *idx,
+                  int64_t m, void *stream);
+
+/* dets[i] = determinant of index idx[i] (0 when idx is out of range).
+ * idx, dets: device arrays of m entries. */
+hy_status hy_unrank(const hy_ham *h, const int64_t *idx, uint64_t *dets,
+                    int64_t m, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Sweeps                                                                   */
+/* ---------------------------------------------------------------------- */
+
+/* sigma = H psi on Omega_CIk (the paper's sparse H times sparse state).
+ * psi, sigma: device arrays of n_det elements of the given dtype; they must
+ * not alias.  The first call per dtype allocates the handle's workspace. */
+hy_status hy_apply_h(const hy_ham *h, const void *psi, void *sigma,
+                     hy_dtype dt, void *stream);
+
+/* *e_out (device, one double) = <psi|sigma> accumulated in double; if
+ * sigma_or_null is NULL, sigma = H psi is computed first into the
+ * workspace.  psi is not normalised by this call. */
+hy_status hy_energy(const hy_ham *h, const void *psi, const void *sigma_or_null,
+                    hy_dtype dt, double *e_out, void *stream);
+
+/* *out (device, one double) = <x|y> accumulated in double (deterministic:
+ * fixed grid and fixed summation order for a given device). */
+hy_status hy_dot(const hy_ham *h, const void *x, const void *y, hy_dtype dt,
+                 double *out, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Operator pool, gradients and exp(theta A)                                */
+/* ---------------------------------------------------------------------- */
+
+/* Spin-adapted singles and doubles relative to the Hartree-Fock determinant
+ * (lowest n_alpha / n_beta orbitals occupied).  Order: singles (i<a), then
+ * same-spin doubles (i<j, a<b), then opposite-spin doubles (i<=j, a<=b,
+ * couplings); an operator whose constituents would share a spin orbital is
+ * split into one pool entry per constituent, so every generator
+ * A_k = sum_c (C_c - C_c^dagger) is a sum of commuting terms on disjoint
+ * spin orbitals.  *out receives an owned pool (free with hy_pool_destroy). */
+hy_status hy_pool_create(const hy_ham *h, hy_pool_kind kind, hy_pool **out);
+hy_status hy_pool_destroy(hy_pool *p);
+hy_status hy_pool_size(const hy_pool *p, int64_t *k);
+
+/* Host output desc[11]: [n_constituents, then per constituent (rank, c0, c1,
+ * a1, a0)]; rank 1 is a+_{c0} a_{a0}, rank 2 is a+_{c0} a+_{c1} a_{a1}
+ * a_{a0}; modes are spin orbitals in blocked order. */
+hy_status hy_pool_describe(const hy_pool *p, int64_t k, int32_t *desc);
+
+/* g_out[i] (device doubles) = 2 <sigma | A_{op_i} psi> for op_i =
+ * ops_or_null[i] (device int32 list of n_ops pool indices), or for every
+ * pool operator in order when ops_or_null is NULL (n_ops is then ignored
+ * and the pool size is used).  With sigma = H psi this is dE/dtheta of
+ * exp(theta A) psi at theta = 0 (the ADAPT-VQE screen).  Pool indices are
+ * assumed valid (the caller checks them). */
+hy_status hy_pool_gradients(const hy_ham *h, const hy_pool *p, const void *psi,
+                            const void *sigma, const int32_t *ops_or_null,
+                            int64_t n_ops, double *g_out, hy_dtype dt,
+                            void *stream);
+
+/* psi <- exp(theta A_k) psi in place: for each constituent C (sign s on the
+ * pair d -> C d) and each connected pair, psi(d) <- cos psi(d) - s sin
+ * psi(Cd), psi(Cd) <- cos psi(Cd) + s sin psi(d).  With renormalize != 0
+ * psi is then divided by its double-precision norm (HY_F32 drift control). */
+hy_status hy_apply_excitation(const hy_ham *h, const hy_pool *p, int64_t k,
+                              double theta, void *psi, hy_dtype dt,
+                              int renormalize, void *stream);
+
+/* Scale psi by 1 / sqrt(<psi|psi>) (norm accumulated in double). */
+hy_status hy_normalize(const hy_ham *h, void *psi, hy_dtype dt, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYPERION_H */

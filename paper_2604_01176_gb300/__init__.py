@@ -1,0 +1,260 @@
+"""GB300-native hot path of exact state-vector ADAPT-VQE emulation.
+
+Thin Python layer over the C ABI in include/hyperion.h (libhyperion.so,
+sm_103a CUDA kernels).  PyTorch provides device memory and streams; every
+step of H psi, the energy and norm reductions, the pool-gradient screen and
+exp(theta A) runs in the library's kernels.  The library fails loudly when it
+is not built or no CUDA device is present: there is no CPU fallback.
+
+Paper: arXiv 2604.01176, Sparse State-Vector Emulation section (H applied
+to a state on the particle- and S_z-conserving determinant space, inner
+products, exponentiated fermionic operators) and the ADAPT-VQE description
+of its Numerical performance subsection.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import HY_F32, HY_F64, HyError, check
+
+__all__ = ["Hamiltonian", "Pool", "HyError", "dtype_code", "stream_ptr"]
+
+
+def dtype_code(t: torch.dtype) -> int:
+    if t == torch.float64:
+        return HY_F64
+    if t == torch.float32:
+        return HY_F32
+    raise TypeError(f"unsupported dtype {t}: use float64 or float32")
+
+
+def stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError("tensors must live on a CUDA device")
+        if not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+
+
+class Hamiltonian:
+    """H built from integrals (chemists' notation) on Omega_CIk."""
+
+    def __init__(self, h1, h2, e_core, n_orb, n_alpha, n_beta, prune_tol=1e-14):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        lib = _abi.load()
+        self.n_orb, self.n_alpha, self.n_beta = int(n_orb), int(n_alpha), int(n_beta)
+        h1 = np.ascontiguousarray(h1, dtype=np.float64)
+        h2 = np.ascontiguousarray(h2, dtype=np.float64)
+        if h1.shape != (n_orb, n_orb) or h2.shape != (n_orb,) * 4:
+            raise ValueError("h1 must be (n, n) and h2 (n, n, n, n)")
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        handle = ctypes.c_void_p()
+        check(lib.hy_build_hamiltonian(
+            h1.ctypes.data_as(ctypes.c_void_p), h2.ctypes.data_as(ctypes.c_void_p),
+            float(e_core), self.n_orb, self.n_alpha, self.n_beta, float(prune_tol),
+            ctypes.byref(handle)))
+        self._h = handle
+        vals = [ctypes.c_int64() for _ in range(5)]
+        check(lib.hy_ham_info(self._h, *[ctypes.byref(v) for v in vals]))
+        (self.n_det, self.n_alpha_str, self.n_beta_str, self.n_groups,
+         self.n_terms) = [v.value for v in vals]
+        self._scalar = torch.zeros(4, dtype=torch.float64, device=self.device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _abi.load().hy_ham_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- tables --------------------------------------------------------------
+    def pauli_table(self):
+        x = np.empty(self.n_terms, dtype=np.uint64)
+        z = np.empty(self.n_terms, dtype=np.uint64)
+        c = np.empty(self.n_terms, dtype=np.float64)
+        off = np.empty(self.n_groups + 1, dtype=np.int64)
+        check(_abi.load().hy_ham_pauli_table(
+            self._h, x.ctypes.data_as(ctypes.c_void_p), z.ctypes.data_as(ctypes.c_void_p),
+            c.ctypes.data_as(ctypes.c_void_p), off.ctypes.data_as(ctypes.c_void_p)))
+        return x, z, c, off
+
+    # -- indexing ------------------------------------------------------------
+    def rank(self, dets: torch.Tensor, stream=None) -> torch.Tensor:
+        _require_cuda(dets)
+        if dets.dtype not in (torch.int64, torch.uint64):
+            raise TypeError("dets must be 64-bit integers")
+        idx = torch.empty(dets.numel(), dtype=torch.int64, device=dets.device)
+        check(_abi.load().hy_rank(self._h, _ptr(dets), _ptr(idx), dets.numel(),
+                                  stream_ptr(stream)))
+        return idx
+
+    def unrank(self, idx: torch.Tensor, stream=None) -> torch.Tensor:
+        _require_cuda(idx)
+        out = torch.empty(idx.numel(), dtype=torch.int64, device=idx.device)
+        check(_abi.load().hy_unrank(self._h, _ptr(idx), _ptr(out), idx.numel(),
+                                    stream_ptr(stream)))
+        return out
+
+    def connections_per_det(self) -> float:
+        """Nonzero matrix elements of H per determinant row (diagonal, alpha
+        and beta singles and doubles, alpha-beta doubles): the number of
+        multiply-adds one H psi needs per output amplitude."""
+        from math import comb
+        n, a, b = self.n_orb, self.n_alpha, self.n_beta
+        sa, sb = a * (n - a), b * (n - b)
+        da = comb(a, 2) * comb(n - a, 2)
+        db = comb(b, 2) * comb(n - b, 2)
+        return float(1 + sa + sb + da + db + sa * sb)
+
+    def hf_index(self) -> int:
+        # HF = lowest orbitals occupied: rank 0 in both spins
+        return 0
+
+    def hf_state(self, dtype=torch.float64) -> torch.Tensor:
+        v = torch.zeros(self.n_det, dtype=dtype, device=self.device)
+        v[self.hf_index()] = 1.0
+        return v
+
+    # -- sweeps --------------------------------------------------------------
+    def _check_state(self, *ts):
+        _require_cuda(*ts)
+        for t in ts:
+            if t is not None and t.numel() != self.n_det:
+                raise ValueError(f"state must have n_det = {self.n_det} elements")
+
+    def apply_h(self, psi: torch.Tensor, out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+        self._check_state(psi, out)
+        if out is None:
+            out = torch.empty_like(psi)
+        check(_abi.load().hy_apply_h(self._h, _ptr(psi), _ptr(out),
+                                     dtype_code(psi.dtype), stream_ptr(stream)))
+        return out
+
+    def energy(self, psi: torch.Tensor, sigma: torch.Tensor | None = None,
+               out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """<psi|H|psi> (or <psi|sigma>) as a 0-d float64 device tensor."""
+        self._check_state(psi, sigma)
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device=psi.device)
+        check(_abi.load().hy_energy(
+            self._h, _ptr(psi), _ptr(sigma) if sigma is not None else None,
+            dtype_code(psi.dtype), _ptr(out), stream_ptr(stream)))
+        return out
+
+    def dot(self, x: torch.Tensor, y: torch.Tensor, out=None, stream=None):
+        self._check_state(x, y)
+        if x.dtype != y.dtype:
+            raise TypeError("x and y must share a dtype")
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device=x.device)
+        check(_abi.load().hy_dot(self._h, _ptr(x), _ptr(y), dtype_code(x.dtype),
+                                 _ptr(out), stream_ptr(stream)))
+        return out
+
+    def normalize(self, psi: torch.Tensor, stream=None) -> torch.Tensor:
+        self._check_state(psi)
+        check(_abi.load().hy_normalize(self._h, _ptr(psi), dtype_code(psi.dtype),
+                                       stream_ptr(stream)))
+        return psi
+
+
+class Pool:
+    """Spin-adapted singles+doubles pool relative to the HF determinant."""
+
+    def __init__(self, ham: Hamiltonian):
+        lib = _abi.load()
+        self.ham = ham
+        handle = ctypes.c_void_p()
+        check(lib.hy_pool_create(ham.handle, _abi.HY_POOL_SPIN_ADAPTED_SD,
+                                 ctypes.byref(handle)))
+        self._p = handle
+        k = ctypes.c_int64()
+        check(lib.hy_pool_size(self._p, ctypes.byref(k)))
+        self.size = k.value
+
+    def close(self):
+        if getattr(self, "_p", None):
+            _abi.load().hy_pool_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return self.size
+
+    @property
+    def handle(self):
+        return self._p
+
+    def n_kernels(self, k: int) -> int:
+        """Kernel launches of one apply_excitation(k) (one per constituent)."""
+        if not hasattr(self, "_nc"):
+            self._nc = [int(d[0]) for d in self.descriptors()]
+        return self._nc[k]
+
+    def describe(self, k: int) -> np.ndarray:
+        d = np.zeros(11, dtype=np.int32)
+        check(_abi.load().hy_pool_describe(self._p, int(k),
+                                           d.ctypes.data_as(ctypes.c_void_p)))
+        return d
+
+    def descriptors(self) -> np.ndarray:
+        return np.stack([self.describe(k) for k in range(self.size)]) if self.size \
+            else np.zeros((0, 11), dtype=np.int32)
+
+    def gradients(self, psi: torch.Tensor, sigma: torch.Tensor,
+                  ops: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+        """g_i = 2 <sigma|A_{ops[i]} psi> (all ops when ops is None)."""
+        self.ham._check_state(psi, sigma)
+        if psi.dtype != sigma.dtype:
+            raise TypeError("psi and sigma must share a dtype")
+        n = self.size if ops is None else ops.numel()
+        if ops is not None:
+            _require_cuda(ops)
+            if ops.dtype != torch.int32:
+                raise TypeError("ops must be int32")
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=psi.device)
+        check(_abi.load().hy_pool_gradients(
+            self.ham.handle, self._p, _ptr(psi), _ptr(sigma),
+            _ptr(ops) if ops is not None else None, n, _ptr(out),
+            dtype_code(psi.dtype), stream_ptr(stream)))
+        return out
+
+    def apply_excitation(self, k: int, theta: float, psi: torch.Tensor,
+                         renormalize: bool = False, stream=None) -> torch.Tensor:
+        self.ham._check_state(psi)
+        check(_abi.load().hy_apply_excitation(
+            self.ham.handle, self._p, int(k), float(theta), _ptr(psi),
+            dtype_code(psi.dtype), 1 if renormalize else 0, stream_ptr(stream)))
+        return psi

@@ -1,0 +1,86 @@
+"""ctypes binding of include/hyperion.h (argument marshalling only).
+
+Every numerical step runs in the CUDA library ``libhyperion.so``; this module
+declares the C signatures and raises if the library is missing.  There is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhyperion.so")
+
+HY_OK, HY_ERR_ARG, HY_ERR_CUDA, HY_ERR_OOM, HY_ERR_TIMEOUT, HY_ERR_UNSUPPORTED = range(6)
+HY_F64, HY_F32 = 0, 1
+HY_POOL_SPIN_ADAPTED_SD = 0
+
+_STATUS = {HY_ERR_ARG: "HY_ERR_ARG", HY_ERR_CUDA: "HY_ERR_CUDA",
+           HY_ERR_OOM: "HY_ERR_OOM", HY_ERR_TIMEOUT: "HY_ERR_TIMEOUT",
+           HY_ERR_UNSUPPORTED: "HY_ERR_UNSUPPORTED"}
+
+
+class HyError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int
+I64 = ctypes.c_int64
+D = ctypes.c_double
+PP = ctypes.POINTER(ctypes.c_void_p)
+PI64 = ctypes.POINTER(ctypes.c_int64)
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "hy_last_error": (ctypes.c_char_p, []),
+    "hy_version": (ctypes.c_char_p, []),
+    "hy_build_hamiltonian": (I32, [P, P, D, I32, I32, I32, D, PP]),
+    "hy_ham_destroy": (I32, [P]),
+    "hy_ham_info": (I32, [P, PI64, PI64, PI64, PI64, PI64]),
+    "hy_ham_pauli_table": (I32, [P, P, P, P, P]),
+    "hy_pauli_table_build": (I32, [P, P, D, I32, D, I64, P, P, P, P, PI64, PI64]),
+    "hy_rank": (I32, [P, P, P, I64, P]),
+    "hy_unrank": (I32, [P, P, P, I64, P]),
+    "hy_apply_h": (I32, [P, P, P, I32, P]),
+    "hy_energy": (I32, [P, P, P, I32, P, P]),
+    "hy_dot": (I32, [P, P, P, I32, P, P]),
+    "hy_normalize": (I32, [P, P, I32, P]),
+    "hy_pool_create": (I32, [P, I32, PP]),
+    "hy_pool_destroy": (I32, [P]),
+    "hy_pool_size": (I32, [P, PI64]),
+    "hy_pool_describe": (I32, [P, I64, P]),
+    "hy_pool_gradients": (I32, [P, P, P, P, P, I64, P, I32, P]),
+    "hy_apply_excitation": (I32, [P, P, I64, D, P, I32, I32, P]),
+}
+
+
+def load():
+    """Load libhyperion.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"{LIB_PATH} is missing: build it with "
+            "paper_2604_01176_gb300.build.build() (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != HY_OK:
+        msg = load().hy_last_error()
+        raise HyError(status, msg.decode() if msg else "")

@@ -1,0 +1,115 @@
+// hy_internal.h -- host-side data structures shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "hyperion.h"
+
+namespace hy {
+
+constexpr int kMaxOrb = 16;
+
+// Binomial coefficients C(n, k) for 0 <= n, k <= 32.
+uint32_t binom(int n, int k);
+
+// Colexicographic combinadic rank of an occupation string:
+// rank = sum_i C(pos_i, i + 1) over set bits pos_0 < pos_1 < ...
+uint32_t string_rank(uint32_t mask);
+// Inverse of string_rank for strings of k electrons.
+uint32_t string_unrank(uint32_t rank, int k);
+
+// Packed single-excitation entry: partner string rank in bits 0..15, the
+// orbital p created on the output string in bits 16..19, the orbital q
+// annihilated (present in the partner) in bits 20..23, bit 31 set when the
+// Jordan-Wigner sign is negative.
+inline uint32_t pack_ex(uint32_t partner, int p, int q, int neg)
+{
+    return partner | (uint32_t(p) << 16) | (uint32_t(q) << 20) |
+           (uint32_t(neg ? 1u : 0u) << 31);
+}
+
+// All strings of k electrons in n orbitals, in rank order, and for each
+// output string K every single excitation K = a+_p a_q J (p in K, q not in
+// K): partner J, orbitals (p, q) and sign (-1)^popcount(K & between(p, q)).
+struct StringSpace {
+    int n = 0, k = 0;
+    int64_t N = 0;
+    int nex = 0;                    // k * (n - k) entries per string
+    std::vector<uint32_t> str;      // rank -> mask
+    std::vector<uint32_t> ex;       // [N][nex] packed entries
+};
+void build_string_space(int n, int k, StringSpace &s);
+
+// Jordan-Wigner Pauli table grouped by X-mask.  Coefficients are kept in the
+// X^x Z^z basis (real for a real Hamiltonian): H = sum_t cxz[t] X^x Z^z,
+// with X^x Z^z |d> = (-1)^popcount(d & z) |d ^ x>.
+struct PauliTable {
+    int n_qubits = 0;
+    std::vector<uint64_t> x, z;
+    std::vector<double> cxz;
+    std::vector<int64_t> group_off;             // n_groups + 1
+    std::unordered_map<uint64_t, int64_t> group_of_x;
+    // <bra|H|ket> = f_x(ket) with x = bra ^ ket.
+    double element(uint64_t bra, uint64_t ket) const;
+};
+
+// Build the table from integrals; returns false with a message on failure.
+bool build_pauli_table(const double *h1, const double *h2, double e_core,
+                       int n, double prune_tol, PauliTable &t,
+                       std::string &err);
+// Check that every group has the structure of a two-body number- and
+// spin-conserving Hamiltonian (what the kernel tables rely on).
+bool check_two_body_structure(const PauliTable &t, int n, std::string &err);
+
+// Kernel tables folded from the Pauli table.
+//   sigma(a', b') = sum_J Ma[a'][J] psi[J][b'] + sum_J Mb[b'][J] psi[a'][J]
+//     + sum_{(p,q) in X(a'), (r,s) in X(b')} sa sb V[p][q][r][s] psi[a'^pq][b'^rs]
+// where X(s) holds the single excitations (p in s created, q annihilated)
+// and the diagonal pairs (p, p) for occupied p.
+struct CsrHost {
+    int64_t rows = 0;
+    std::vector<int32_t> ptr, col;
+    std::vector<double> val;
+};
+struct KernelTables {
+    CsrHost Ma, Mb;
+    std::vector<double> V;   // n^4, index ((p*n+q)*n+r)*n+s
+    double E0 = 0.0;         // <vacuum|H|vacuum>
+};
+void fold_tables(const PauliTable &t, int n, const StringSpace &A,
+                 const StringSpace &B, KernelTables &kt);
+
+// ---------------------------------------------------------------------------
+// Operator pool.
+// ---------------------------------------------------------------------------
+struct PoolOpHost {
+    int32_t desc[11];   // [nc, (rank, c0, c1, a1, a0) x 2]
+};
+void build_pool_spin_adapted(int n, int na, int nb, std::vector<PoolOpHost> &ops);
+
+// A constituent split into its alpha part and beta part: C = eps * Ca * Cb.
+// Each part is a pattern id into the per-spin pattern lists, or -1 for the
+// identity.
+struct PatternKey {
+    int nops;
+    int ops[4];          // 2 * orbital + dagger, in product order
+    bool operator==(const PatternKey &o) const;
+};
+struct PatternKeyHash {
+    size_t operator()(const PatternKey &k) const;
+};
+struct PatternLists {
+    // entries: bits 0..14 string S in the pattern's domain, bits 15..29
+    // image S' = C S, bit 31 set for a negative sign.
+    std::vector<uint32_t> entry;
+    std::vector<int64_t> off;   // per pattern
+    std::vector<int64_t> cnt;
+    std::unordered_map<PatternKey, int, PatternKeyHash> id;
+    int get(const PatternKey &k, const StringSpace &s);
+};
+
+}  // namespace hy

@@ -1,0 +1,230 @@
+// hy_sigma.cu -- sigma = H psi on Omega_CIk (paper: the sparse Hamiltonian
+// times sparse state-vector product of the Sparse State-Vector Emulation
+// section), computed matrix-free from the kernel tables folded out of the
+// Jordan-Wigner X-mask groups:
+//
+//   sigma[a'][b'] = sum_J Ma[a'][J] psi[J][b']                 (alpha part)
+//                 + sum_J Mb[b'][J] psi[a'][J]                 (beta part)
+//                 + sum_{(p,q) in X(a')} sum_{(r,s) in X(b')}
+//                       sa * sb * V[p][q][r][s] * psi[a'^pq][b'^rs]
+//
+// psi is row-major [N_alpha][N_beta].  The alpha part is a sparse-times-dense
+// product whose rows of psi are read contiguously; the beta part is the same
+// product on the transposed state; the alpha-beta coupling stages one
+// partner row of psi in shared memory per alpha excitation of the output
+// row and gathers the beta partners from it.
+#include "hy_kernels.cuh"
+
+namespace hy {
+namespace k {
+
+// ---------------------------------------------------------------------------
+// Y = M X (or Y += M X) with M in CSR over strings and X, Y row-major
+// [rows][ncols].  Grid: x = output row (so all rows of one column tile run
+// together and the tile of X stays in L2), y = column tile.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_spmm(const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+       const T *__restrict__ val, const T *__restrict__ X, T *__restrict__ Y,
+       int64_t ncols, int accumulate)
+{
+    const int64_t r = blockIdx.x;
+    const int64_t c = int64_t(blockIdx.y) * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    const int beg = ptr[r], end = ptr[r + 1];
+    T s0 = T(0), s1 = T(0);
+    int kk = beg;
+    for (; kk + 1 < end; kk += 2) {
+        s0 += val[kk] * X[int64_t(col[kk]) * ncols + c];
+        s1 += val[kk + 1] * X[int64_t(col[kk + 1]) * ncols + c];
+    }
+    if (kk < end) s0 += val[kk] * X[int64_t(col[kk]) * ncols + c];
+    const T s = s0 + s1;
+    T *y = Y + r * ncols + c;
+    if (accumulate) *y += s; else *y = s;
+}
+
+template <typename T>
+cudaError_t spmm(const int32_t *ptr, const int32_t *col, const T *val,
+                 int64_t rows, const T *X, T *Y, int64_t ncols, bool accumulate,
+                 cudaStream_t st)
+{
+    if (rows == 0 || ncols == 0) return cudaSuccess;
+    dim3 grid(unsigned(rows), unsigned((ncols + 255) / 256));
+    k_spmm<T><<<grid, 256, 0, st>>>(ptr, col, val, X, Y, ncols, accumulate ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// out[c][r] = in[r][c]   and   sigma[r][c] += tau[c][r]
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_transpose(const T *__restrict__ in, T *__restrict__ out, int64_t R, int64_t C)
+{
+    __shared__ T tile[32][33];
+    const int64_t c0 = int64_t(blockIdx.x) * 32, r0 = int64_t(blockIdx.y) * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int j = ty; j < 32; j += 8) {
+        int64_t r = r0 + j, c = c0 + tx;
+        if (r < R && c < C) tile[j][tx] = in[r * C + c];
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        int64_t c = c0 + j, r = r0 + tx;
+        if (r < R && c < C) out[c * R + r] = tile[tx][j];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_add_transposed(const T *__restrict__ tau, T *__restrict__ sigma, int64_t R,
+                 int64_t C)
+{
+    __shared__ T tile[32][33];
+    const int64_t r0 = int64_t(blockIdx.x) * 32, c0 = int64_t(blockIdx.y) * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int j = ty; j < 32; j += 8) {         // tau is [C][R]
+        int64_t c = c0 + j, r = r0 + tx;
+        if (r < R && c < C) tile[j][tx] = tau[c * R + r];
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        int64_t r = r0 + j, c = c0 + tx;
+        if (r < R && c < C) sigma[r * C + c] += tile[tx][j];
+    }
+}
+
+template <typename T>
+cudaError_t transpose(const T *in, T *out, int64_t R, int64_t C, cudaStream_t st)
+{
+    if (R == 0 || C == 0) return cudaSuccess;
+    dim3 grid(unsigned((C + 31) / 32), unsigned((R + 31) / 32)), block(32, 8);
+    k_transpose<T><<<grid, block, 0, st>>>(in, out, R, C);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t add_transposed(const T *tau, T *sigma, int64_t R, int64_t C,
+                           cudaStream_t st)
+{
+    if (R == 0 || C == 0) return cudaSuccess;
+    dim3 grid(unsigned((R + 31) / 32), unsigned((C + 31) / 32)), block(32, 8);
+    k_add_transposed<T><<<grid, block, 0, st>>>(tau, sigma, R, C);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// alpha-beta coupling.  One CTA per output alpha row a' (grid-stride).  For
+// each partner entry e of a' -- the diagonal (partner a' itself, coefficient
+// sum_{p in a'} V[p][p][.][.]) and each single excitation (p, q) (partner
+// a'^pq, coefficient sa V[p][q][.][.]) -- the partner row of psi is staged
+// in shared memory, the n*n coefficient slice likewise, and every output
+// column b' accumulates its diagonal beta term plus its nexb beta
+// excitations gathered from the staged row.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_coupling(CouplingArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t Nb = a.Nb;
+    T *row = reinterpret_cast<T *>(smem_raw);
+    T *acc = row + Nb;
+    T *C = acc + Nb;
+    const int n = a.n, nn = n * n;
+    for (int64_t ar = blockIdx.x; ar < a.Na; ar += gridDim.x) {
+        for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) acc[b] = T(0);
+        const uint32_t amask = a.astr[ar];
+        for (int e = -1; e < a.nexa; ++e) {
+            __syncthreads();
+            int64_t Ja;
+            if (e < 0) {
+                Ja = ar;
+                for (int rs = threadIdx.x; rs < nn; rs += blockDim.x) {
+                    T s = T(0);
+                    for (uint32_t m = amask; m; m &= m - 1) {
+                        int p = __ffs(m) - 1;
+                        s += a.V[size_t(p * n + p) * nn + rs];
+                    }
+                    C[rs] = s;
+                }
+            } else {
+                const uint32_t u = a.aex[ar * a.nexa + e];
+                Ja = u & 0xFFFFu;
+                const int p = (u >> 16) & 15, q = (u >> 20) & 15;
+                const bool neg = (u >> 31) != 0;
+                for (int rs = threadIdx.x; rs < nn; rs += blockDim.x) {
+                    T v = a.V[size_t(p * n + q) * nn + rs];
+                    C[rs] = neg ? -v : v;
+                }
+            }
+            const T *src = a.psi + Ja * Nb;
+            for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) row[b] = src[b];
+            __syncthreads();
+            for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) {
+                T d = T(0);
+                for (uint32_t m = a.bstr[b]; m; m &= m - 1) {
+                    int r = __ffs(m) - 1;
+                    d += C[r * n + r];
+                }
+                T s = d * row[b];
+                const uint32_t *bx = a.bexT + b;
+                for (int f = 0; f < a.nexb; ++f) {
+                    const uint32_t u = bx[size_t(f) * Nb];
+                    const int r = (u >> 16) & 15, t = (u >> 20) & 15;
+                    T cv = C[r * n + t];
+                    if (u >> 31) cv = -cv;
+                    s += cv * row[u & 0xFFFFu];
+                }
+                acc[b] += s;
+            }
+        }
+        __syncthreads();
+        T *dst = a.sigma + ar * Nb;
+        for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) dst[b] += acc[b];
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t coupling(const CouplingArgs<T> &a, int num_sms, cudaStream_t st)
+{
+    if (a.Na == 0 || a.Nb == 0) return cudaSuccess;
+    const size_t smem = (2 * size_t(a.Nb) + size_t(a.n) * a.n) * sizeof(T);
+    cudaError_t err = cudaFuncSetAttribute(
+        k_coupling<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coupling<T>,
+                                                        512, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int64_t grid = int64_t(num_sms) * per_sm;
+    if (grid > a.Na) grid = a.Na;
+    k_coupling<T><<<unsigned(grid), 512, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t spmm<double>(const int32_t *, const int32_t *, const double *,
+                                  int64_t, const double *, double *, int64_t, bool,
+                                  cudaStream_t);
+template cudaError_t spmm<float>(const int32_t *, const int32_t *, const float *,
+                                 int64_t, const float *, float *, int64_t, bool,
+                                 cudaStream_t);
+template cudaError_t transpose<double>(const double *, double *, int64_t, int64_t,
+                                       cudaStream_t);
+template cudaError_t transpose<float>(const float *, float *, int64_t, int64_t,
+                                      cudaStream_t);
+template cudaError_t add_transposed<double>(const double *, double *, int64_t,
+                                            int64_t, cudaStream_t);
+template cudaError_t add_transposed<float>(const float *, float *, int64_t,
+                                           int64_t, cudaStream_t);
+template cudaError_t coupling<double>(const CouplingArgs<double> &, int,
+                                      cudaStream_t);
+template cudaError_t coupling<float>(const CouplingArgs<float> &, int,
+                                     cudaStream_t);
+
+}  // namespace k
+}  // namespace hy
