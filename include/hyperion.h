@@ -201,6 +201,92 @@ hy_status hy_apply_excitation(const hy_ham *h, const hy_pool *p, int64_t k,
 /* Scale psi by 1 / sqrt(<psi|psi>) (norm accumulated in double). */
 hy_status hy_normalize(const hy_ham *h, void *psi, hy_dtype dt, void *stream);
 
+/* ---------------------------------------------------------------------- */
+/* ADAPT-VQE driver                                                         */
+/* ---------------------------------------------------------------------- */
+
+/* The ADAPT-VQE loop of the paper's Numerical performance subsection: start
+ * from the Hartree-Fock determinant; each iteration screens the pool by
+ * |g_k| = |dE/dtheta_k|, appends the operator with the largest |g_k| with
+ * theta = 0 (ties go to the lowest index within 1e-12 max|g|), then
+ * re-optimises every theta (here: BFGS with backtracking line search and
+ * analytic adjoint gradients, warm-started from the previous parameters).
+ * Each energy evaluation is E(theta) = <psi0|U(theta)^T H U(theta)|psi0>
+ * (Method section); the state preparation applies the ansatz's exp(theta A)
+ * in order (cost T_0 per operator of the paper's C-tilde metric) and the
+ * measurement is one H psi plus one inner product (cost T_1).
+ *
+ * bulk = HY_F64: everything in double ("plain FP64").
+ * bulk = HY_F32: state, H psi and gradients in float with float accumulation
+ *   inside H psi; energies, norms and gradients reduced in double; psi is
+ *   renormalised (norm in double) after every exp(theta A); after the float
+ *   optimisation at most refine_steps BFGS steps run in double, and the
+ *   recorded energy is always a double-precision evaluation. */
+typedef struct {
+    hy_dtype bulk;        /* HY_F64 or HY_F32                                  */
+    int max_iter;         /* capacity of the ansatz (iterations)               */
+    double eps_grad;      /* converged when ||g||_2 over the screen < eps_grad */
+    double gtol;          /* optimiser: stop when max |dE/dtheta| < gtol       */
+    double gtol_bulk;     /* HY_F32 only: float-phase tolerance                */
+    int max_evals;        /* optimiser: cap on evaluations per iteration       */
+    int refine_steps;     /* HY_F32 only: double-precision BFGS steps (>= 0)   */
+    int screen_top_m;     /* 0: full screen; M > 0: screen only the M operators
+                             a ranker proposes (hy_adapt_set_ranker)           */
+    int judge;            /* with screen_top_m > 0: also run the full screen
+                             and report the true argmax and its rank           */
+} hy_adapt_config;
+
+/* One ADAPT iteration (all times in seconds, host wall clock). */
+typedef struct {
+    int32_t iter;          /* 0-based iteration index                         */
+    int32_t converged;     /* 1: ||g|| < eps_grad, nothing appended            */
+    int64_t selected;      /* pool index appended (-1 if converged)           */
+    double max_grad;       /* |g| of the selected operator                    */
+    double grad_norm;      /* ||g||_2 over the screened operators             */
+    double energy;         /* double-precision energy after optimisation      */
+    double energy_bulk;    /* bulk-precision energy at the bulk optimum        */
+    double energy_bulk_err;/* |energy_bulk - double energy at the same theta| */
+    int32_t n_evals;       /* energy+gradient evaluations (all precisions)    */
+    int32_t n_evals_f64;   /* of which in double precision                    */
+    int64_t true_argmax;   /* judge: argmax of the full screen (-1 if none)   */
+    int64_t true_rank;     /* judge: rank of true_argmax among the proposals
+                              (0 = proposed first; -1 = not proposed)          */
+    double t_screen, t_optimise, t_total;
+} hy_adapt_record;
+
+typedef struct hy_adapt hy_adapt;
+typedef struct hy_ranker hy_ranker;
+
+/* Create a driver for (h, p); allocates its state buffers on the device.
+ * cfg == NULL takes the defaults: HY_F64, max_iter 64, eps_grad 1e-5,
+ * gtol 1e-9, gtol_bulk 1e-5, max_evals 200, refine_steps 4, full screen. */
+hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p,
+                          const hy_adapt_config *cfg, hy_adapt **out);
+hy_status hy_adapt_destroy(hy_adapt *a);
+
+/* Run one iteration on `stream` (the host waits for its results).  *rec
+ * (host) receives the record.  Returns HY_ERR_ARG when the ansatz is full. */
+hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream);
+
+/* Copy the ansatz (host arrays with room for cap entries); *len gets its
+ * length.  Pass cap = 0 to query the length. */
+hy_status hy_adapt_ansatz(const hy_adapt *a, int64_t *ops, double *thetas,
+                          int64_t cap, int64_t *len);
+
+/* Replace the ansatz (checkpoint / resume: the state is rebuilt from HF). */
+hy_status hy_adapt_set_ansatz(hy_adapt *a, const int64_t *ops,
+                              const double *thetas, int64_t len);
+
+/* Energy and adjoint gradient of the current ansatz at `thetas` (host, len
+ * = ansatz length) in `dt`; *e and grad (host, len doubles) are outputs. */
+hy_status hy_adapt_evaluate(hy_adapt *a, const double *thetas, hy_dtype dt,
+                            double *e, double *grad, void *stream);
+
+/* Copy the driver's current state (after the last evaluation) into psi
+ * (device, n_det elements of dt). */
+hy_status hy_adapt_state(const hy_adapt *a, void *psi, hy_dtype dt,
+                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

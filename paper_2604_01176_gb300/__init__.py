@@ -21,7 +21,7 @@ import torch
 from . import _abi
 from ._abi import HY_F32, HY_F64, HyError, check
 
-__all__ = ["Hamiltonian", "Pool", "HyError", "dtype_code", "stream_ptr"]
+__all__ = ["Hamiltonian", "Pool", "Adapt", "HyError", "dtype_code", "stream_ptr"]
 
 
 def dtype_code(t: torch.dtype) -> int:
@@ -258,3 +258,92 @@ class Pool:
             self.ham.handle, self._p, int(k), float(theta), _ptr(psi),
             dtype_code(psi.dtype), 1 if renormalize else 0, stream_ptr(stream)))
         return psi
+
+
+class Adapt:
+    """ADAPT-VQE driver (hy_adapt_*): screen, select, append, re-optimise.
+
+    precision "f64" is plain double precision; "mixed" keeps the bulk of
+    the sweeps in float (state renormalised in double after every
+    exp(theta A)) and refines the parameters and the energy in double."""
+
+    def __init__(self, ham: Hamiltonian, pool: Pool, precision="f64", max_iter=64,
+                 eps_grad=1e-5, gtol=1e-9, gtol_bulk=1e-5, max_evals=200,
+                 refine_steps=4, screen_top_m=0, judge=False):
+        lib = _abi.load()
+        self.ham, self.pool = ham, pool
+        if precision not in ("f64", "mixed"):
+            raise ValueError("precision must be 'f64' or 'mixed'")
+        cfg = _abi.AdaptConfig(HY_F64 if precision == "f64" else HY_F32, int(max_iter),
+                               float(eps_grad), float(gtol), float(gtol_bulk),
+                               int(max_evals), int(refine_steps), int(screen_top_m),
+                               1 if judge else 0)
+        handle = ctypes.c_void_p()
+        check(lib.hy_adapt_create(ham.handle, pool.handle, ctypes.byref(cfg),
+                                  ctypes.byref(handle)))
+        self._a = handle
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "_a", None):
+            _abi.load().hy_adapt_destroy(self._a)
+            self._a = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._a
+
+    def step(self, stream=None) -> dict:
+        rec = _abi.AdaptRecord()
+        check(_abi.load().hy_adapt_step(self._a, ctypes.byref(rec), stream_ptr(stream)))
+        return rec.as_dict()
+
+    def run(self, iters: int, stream=None) -> list:
+        out = []
+        for _ in range(iters):
+            r = self.step(stream)
+            out.append(r)
+            if r["converged"]:
+                break
+        return out
+
+    def ansatz(self):
+        lib = _abi.load()
+        n = ctypes.c_int64()
+        check(lib.hy_adapt_ansatz(self._a, None, None, 0, ctypes.byref(n)))
+        ops = np.zeros(n.value, dtype=np.int64)
+        th = np.zeros(n.value)
+        if n.value:
+            check(lib.hy_adapt_ansatz(self._a, ops.ctypes.data_as(ctypes.c_void_p),
+                                      th.ctypes.data_as(ctypes.c_void_p), n.value,
+                                      ctypes.byref(n)))
+        return ops, th
+
+    def set_ansatz(self, ops, thetas):
+        ops = np.ascontiguousarray(ops, dtype=np.int64)
+        th = np.ascontiguousarray(thetas, dtype=np.float64)
+        check(_abi.load().hy_adapt_set_ansatz(self._a, ops.ctypes.data_as(ctypes.c_void_p),
+                                              th.ctypes.data_as(ctypes.c_void_p), len(ops)))
+
+    def evaluate(self, thetas, dtype=torch.float64, stream=None):
+        """(E, dE/dtheta) of the current ansatz at `thetas` (adjoint sweep)."""
+        th = np.ascontiguousarray(thetas, dtype=np.float64)
+        e = ctypes.c_double()
+        g = np.zeros(len(th))
+        check(_abi.load().hy_adapt_evaluate(self._a, th.ctypes.data_as(ctypes.c_void_p),
+                                            dtype_code(dtype), ctypes.byref(e),
+                                            g.ctypes.data_as(ctypes.c_void_p),
+                                            stream_ptr(stream)))
+        return e.value, g
+
+    def state(self, dtype=torch.float64, stream=None) -> torch.Tensor:
+        out = torch.empty(self.ham.n_det, dtype=dtype, device=self.ham.device)
+        check(_abi.load().hy_adapt_state(self._a, _ptr(out), dtype_code(dtype),
+                                         stream_ptr(stream)))
+        return out

@@ -29,6 +29,30 @@ class HyError(RuntimeError):
 
 _lib = None
 
+
+class AdaptConfig(ctypes.Structure):
+    """Mirror of hy_adapt_config."""
+    _fields_ = [("bulk", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("eps_grad", ctypes.c_double), ("gtol", ctypes.c_double),
+                ("gtol_bulk", ctypes.c_double), ("max_evals", ctypes.c_int),
+                ("refine_steps", ctypes.c_int), ("screen_top_m", ctypes.c_int),
+                ("judge", ctypes.c_int)]
+
+
+class AdaptRecord(ctypes.Structure):
+    """Mirror of hy_adapt_record."""
+    _fields_ = [("iter", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("selected", ctypes.c_int64), ("max_grad", ctypes.c_double),
+                ("grad_norm", ctypes.c_double), ("energy", ctypes.c_double),
+                ("energy_bulk", ctypes.c_double), ("energy_bulk_err", ctypes.c_double),
+                ("n_evals", ctypes.c_int32), ("n_evals_f64", ctypes.c_int32),
+                ("true_argmax", ctypes.c_int64), ("true_rank", ctypes.c_int64),
+                ("t_screen", ctypes.c_double), ("t_optimise", ctypes.c_double),
+                ("t_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
 P = ctypes.c_void_p
 I32 = ctypes.c_int
 I64 = ctypes.c_int64
@@ -57,6 +81,13 @@ SIGNATURES = {
     "hy_pool_describe": (I32, [P, I64, P]),
     "hy_pool_gradients": (I32, [P, P, P, P, P, I64, P, I32, P]),
     "hy_apply_excitation": (I32, [P, P, I64, D, P, I32, I32, P]),
+    "hy_adapt_create": (I32, [P, P, P, PP]),
+    "hy_adapt_destroy": (I32, [P]),
+    "hy_adapt_step": (I32, [P, P, P]),
+    "hy_adapt_ansatz": (I32, [P, P, P, I64, PI64]),
+    "hy_adapt_set_ansatz": (I32, [P, P, P, I64]),
+    "hy_adapt_evaluate": (I32, [P, P, I32, P, P, P]),
+    "hy_adapt_state": (I32, [P, P, I32, P]),
 }
 
 

@@ -1,0 +1,462 @@
+// hy_adapt.cpp -- the ADAPT-VQE driver (include/hyperion.h, "ADAPT-VQE
+// driver").  Host code only: it is a client of the library's own C ABI
+// (hy_apply_excitation, hy_apply_h, hy_energy, hy_pool_gradients), so every
+// sweep over the state runs in the CUDA kernels; this file holds the loop,
+// the BFGS optimiser and the bookkeeping.
+//
+// Paper: ADAPT-VQE as described in the Numerical performance subsection
+// (screen the pool by energy gradient, append the largest, re-optimise all
+// parameters), with the energy of Eq. "ev" prepared from the Hartree-Fock
+// state by the ansatz's exponentiated fermionic operators.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "hyperion.h"
+#include "hy_internal.h"
+
+namespace {
+
+double now_s()
+{
+    using clk = std::chrono::steady_clock;
+    return std::chrono::duration<double>(clk::now().time_since_epoch()).count();
+}
+
+size_t esize(hy_dtype dt) { return dt == HY_F64 ? 8 : 4; }
+
+}  // namespace
+
+struct hy_adapt {
+    const hy_ham *h = nullptr;
+    const hy_pool *p = nullptr;
+    const hy_ranker *ranker = nullptr;
+    hy_adapt_config cfg{};
+    int64_t N = 0, K = 0;
+    // device state: [dtype][psi, sigma, phi, lam]
+    void *buf[2][4] = {{nullptr, nullptr, nullptr, nullptr},
+                       {nullptr, nullptr, nullptr, nullptr}};
+    double *d_g = nullptr;        // screen gradients [K]
+    double *d_ga = nullptr;       // ansatz gradients [max_iter]
+    double *d_e = nullptr;        // scalar
+    int32_t *d_ops = nullptr;     // ansatz ops [max_iter]
+    int32_t *d_prop = nullptr;    // proposals [K]
+    std::vector<int64_t> ops;
+    std::vector<double> theta;
+    std::vector<double> hinv;     // inverse-Hessian estimate (len x len)
+    bool hinv_fresh = true;       // hinv is the identity (not yet scaled)
+    // which (dtype, theta) the psi/sigma buffers currently hold
+    int valid_dt = -1;
+    std::vector<double> valid_theta;
+    int evals = 0, evals64 = 0;
+    int iter = 0;
+};
+
+namespace {
+
+hy_status set_err(hy_status s, const char *msg);
+
+#define HY_TRY(x)                       \
+    do {                                \
+        hy_status s_ = (x);             \
+        if (s_ != HY_OK) return s_;     \
+    } while (0)
+
+hy_status cu(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return HY_OK;
+    return set_err(e == cudaErrorMemoryAllocation ? HY_ERR_OOM : HY_ERR_CUDA, what);
+}
+
+int di(hy_dtype dt) { return dt == HY_F64 ? 0 : 1; }
+
+// psi <- HF determinant (index 0: lowest orbitals of both spins occupied)
+hy_status set_hf(hy_adapt *a, void *psi, hy_dtype dt, cudaStream_t st)
+{
+    static const double one64 = 1.0;
+    static const float one32 = 1.0f;
+    HY_TRY(cu(cudaMemsetAsync(psi, 0, size_t(a->N) * esize(dt), st), "memset"));
+    const void *src = dt == HY_F64 ? static_cast<const void *>(&one64)
+                                   : static_cast<const void *>(&one32);
+    return cu(cudaMemcpyAsync(psi, src, esize(dt), cudaMemcpyHostToDevice, st),
+              "set HF amplitude");
+}
+
+// psi = U(theta) |HF>, sigma = H psi, returns E = <psi|sigma>
+hy_status energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
+                 cudaStream_t st, double *e)
+{
+    void *psi = a->buf[di(dt)][0], *sigma = a->buf[di(dt)][1];
+    HY_TRY(set_hf(a, psi, dt, st));
+    const int renorm = dt == HY_F32 ? 1 : 0;
+    for (size_t l = 0; l < a->ops.size(); ++l)
+        HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], th[l], psi, dt, renorm, st));
+    HY_TRY(hy_apply_h(a->h, psi, sigma, dt, st));
+    HY_TRY(hy_energy(a->h, psi, sigma, dt, a->d_e, st));
+    HY_TRY(cu(cudaMemcpyAsync(e, a->d_e, sizeof(double), cudaMemcpyDeviceToHost, st),
+              "energy readback"));
+    HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+    ++a->evals;
+    if (dt == HY_F64) ++a->evals64;
+    a->valid_dt = dt;
+    a->valid_theta = th;
+    return HY_OK;
+}
+
+// adjoint gradient at the point of the last energy() call in dt
+hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
+                   cudaStream_t st, std::vector<double> &g)
+{
+    const size_t j = a->ops.size(), es = esize(dt);
+    g.assign(j, 0.0);
+    if (j == 0) return HY_OK;
+    void *psi = a->buf[di(dt)][0], *sigma = a->buf[di(dt)][1];
+    void *phi = a->buf[di(dt)][2], *lam = a->buf[di(dt)][3];
+    HY_TRY(cu(cudaMemcpyAsync(phi, psi, size_t(a->N) * es, cudaMemcpyDeviceToDevice, st), "copy"));
+    HY_TRY(cu(cudaMemcpyAsync(lam, sigma, size_t(a->N) * es, cudaMemcpyDeviceToDevice, st), "copy"));
+    for (size_t l = j; l-- > 0;) {
+        HY_TRY(hy_pool_gradients(a->h, a->p, phi, lam, a->d_ops + l, 1, a->d_ga + l, dt, st));
+        if (l == 0) break;
+        HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], -th[l], phi, dt, 0, st));
+        HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], -th[l], lam, dt, 0, st));
+    }
+    HY_TRY(cu(cudaMemcpyAsync(g.data(), a->d_ga, j * sizeof(double), cudaMemcpyDeviceToHost, st),
+              "gradient readback"));
+    return cu(cudaStreamSynchronize(st), "sync");
+}
+
+hy_status upload_ops(hy_adapt *a, cudaStream_t st)
+{
+    std::vector<int32_t> o(a->ops.begin(), a->ops.end());
+    if (o.empty()) return HY_OK;
+    HY_TRY(cu(cudaMemcpyAsync(a->d_ops, o.data(), o.size() * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, st), "upload ops"));
+    return cu(cudaStreamSynchronize(st), "sync");
+}
+
+double dotv(const std::vector<double> &x, const std::vector<double> &y)
+{
+    double s = 0.0;
+    for (size_t i = 0; i < x.size(); ++i) s += x[i] * y[i];
+    return s;
+}
+
+double maxabs(const std::vector<double> &x)
+{
+    double m = 0.0;
+    for (double v : x) m = std::max(m, std::fabs(v));
+    return m;
+}
+
+// BFGS with backtracking (Armijo) line search on E(theta) in dt, starting
+// from a->theta and a->hinv; updates both.  *e_out = final energy.
+hy_status bfgs(hy_adapt *a, hy_dtype dt, double gtol, int max_steps, cudaStream_t st,
+               double *e_out)
+{
+    const size_t j = a->ops.size();
+    std::vector<double> x = a->theta, g, gn, pdir(j), xn(j), s(j), y(j), Hy(j);
+    double e = 0.0;
+    HY_TRY(energy(a, x, dt, st, &e));
+    HY_TRY(gradient(a, x, dt, st, g));
+    std::vector<double> &H = a->hinv;
+    const int ev_start = a->evals;
+    for (int it = 0; it < max_steps; ++it) {
+        if (maxabs(g) < gtol || a->evals - ev_start >= a->cfg.max_evals) break;
+        for (size_t r = 0; r < j; ++r) {
+            double v = 0.0;
+            for (size_t c = 0; c < j; ++c) v -= H[r * j + c] * g[c];
+            pdir[r] = v;
+        }
+        double slope = dotv(g, pdir);
+        if (!(slope < 0.0)) {   // not a descent direction: restart from I
+            std::fill(H.begin(), H.end(), 0.0);
+            for (size_t r = 0; r < j; ++r) H[r * j + r] = 1.0;
+            for (size_t r = 0; r < j; ++r) pdir[r] = -g[r];
+            slope = -dotv(g, g);
+            a->hinv_fresh = true;
+        }
+        double alpha = 1.0, en = 0.0;
+        bool ok = false;
+        for (int ls = 0; ls < 40; ++ls) {
+            for (size_t r = 0; r < j; ++r) xn[r] = x[r] + alpha * pdir[r];
+            HY_TRY(energy(a, xn, dt, st, &en));
+            if (en <= e + 1e-4 * alpha * slope) {
+                ok = true;
+                break;
+            }
+            alpha *= 0.5;
+        }
+        if (!ok) {
+            // no decrease representable in this precision: keep x
+            HY_TRY(energy(a, x, dt, st, &e));
+            break;
+        }
+        HY_TRY(gradient(a, xn, dt, st, gn));
+        for (size_t r = 0; r < j; ++r) {
+            s[r] = xn[r] - x[r];
+            y[r] = gn[r] - g[r];
+        }
+        const double sy = dotv(s, y);
+        if (sy > 1e-300) {
+            if (a->hinv_fresh) {   // scale an identity start (Nocedal & Wright 6.20)
+                const double sc = sy / dotv(y, y);
+                for (size_t r = 0; r < j; ++r) H[r * j + r] = sc;
+                a->hinv_fresh = false;
+            }
+            for (size_t r = 0; r < j; ++r) {
+                double v = 0.0;
+                for (size_t c = 0; c < j; ++c) v += H[r * j + c] * y[c];
+                Hy[r] = v;
+            }
+            const double yHy = dotv(y, Hy), rho = 1.0 / sy;
+            for (size_t r = 0; r < j; ++r)
+                for (size_t c = 0; c < j; ++c)
+                    H[r * j + c] += (1.0 + rho * yHy) * rho * s[r] * s[c] -
+                                    rho * (Hy[r] * s[c] + s[r] * Hy[c]);
+        }
+        x = xn;
+        e = en;
+        g = gn;
+    }
+    a->theta = x;
+    *e_out = e;
+    return HY_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// error plumbing shared with the rest of the library (hy_api.cu)
+// ---------------------------------------------------------------------------
+namespace hy {
+void set_last_error(const std::string &msg);
+}
+
+namespace {
+hy_status set_err(hy_status s, const char *msg)
+{
+    hy::set_last_error(msg);
+    return s;
+}
+}  // namespace
+
+extern "C" {
+
+hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_config *cfg,
+                          hy_adapt **out)
+{
+    if (!out) return set_err(HY_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!h || !p) return set_err(HY_ERR_ARG, "handle is NULL");
+    hy_adapt_config c;
+    if (cfg) {
+        c = *cfg;
+    } else {
+        c.bulk = HY_F64;
+        c.max_iter = 64;
+        c.eps_grad = 1e-5;
+        c.gtol = 1e-9;
+        c.gtol_bulk = 1e-5;
+        c.max_evals = 200;
+        c.refine_steps = 4;
+        c.screen_top_m = 0;
+        c.judge = 0;
+    }
+    if ((c.bulk != HY_F64 && c.bulk != HY_F32) || c.max_iter < 1 || c.max_iter > (1 << 20) ||
+        !(c.eps_grad >= 0) || !(c.gtol > 0) || !(c.gtol_bulk > 0) || c.max_evals < 1 ||
+        c.refine_steps < 0 || c.screen_top_m < 0)
+        return set_err(HY_ERR_ARG, "invalid hy_adapt_config");
+    hy_adapt *a = new (std::nothrow) hy_adapt;
+    if (!a) return set_err(HY_ERR_OOM, "host allocation failed");
+    a->h = h;
+    a->p = p;
+    a->cfg = c;
+    hy_status s = hy_ham_info(h, &a->N, nullptr, nullptr, nullptr, nullptr);
+    if (s == HY_OK) s = hy_pool_size(p, &a->K);
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (s != HY_OK) return;
+        s = cu(cudaMalloc(ptr, bytes ? bytes : 8), "cudaMalloc (driver)");
+    };
+    for (int b = 0; b < 4; ++b) alloc(&a->buf[0][b], size_t(a->N) * 8);
+    if (c.bulk == HY_F32)
+        for (int b = 0; b < 4; ++b) alloc(&a->buf[1][b], size_t(a->N) * 4);
+    alloc(reinterpret_cast<void **>(&a->d_g), size_t(a->K) * 8);
+    alloc(reinterpret_cast<void **>(&a->d_ga), size_t(c.max_iter) * 8);
+    alloc(reinterpret_cast<void **>(&a->d_e), 8);
+    alloc(reinterpret_cast<void **>(&a->d_ops), size_t(c.max_iter) * 4);
+    alloc(reinterpret_cast<void **>(&a->d_prop), size_t(a->K) * 4);
+    if (s != HY_OK) {
+        hy_adapt_destroy(a);
+        return s;
+    }
+    *out = a;
+    return HY_OK;
+}
+
+hy_status hy_adapt_destroy(hy_adapt *a)
+{
+    if (!a) return HY_OK;
+    for (auto &row : a->buf)
+        for (void *&b : row)
+            if (b) cudaFree(b);
+    cudaFree(a->d_g);
+    cudaFree(a->d_ga);
+    cudaFree(a->d_e);
+    cudaFree(a->d_ops);
+    cudaFree(a->d_prop);
+    delete a;
+    return HY_OK;
+}
+
+hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
+{
+    if (!a || !rec) return set_err(HY_ERR_ARG, "NULL argument");
+    if (int64_t(a->ops.size()) >= a->cfg.max_iter)
+        return set_err(HY_ERR_ARG, "ansatz is full (max_iter)");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::memset(rec, 0, sizeof(*rec));
+    rec->iter = a->iter;
+    rec->selected = -1;
+    rec->true_argmax = -1;
+    rec->true_rank = -1;
+    const double t0 = now_s();
+    const int ev0 = a->evals, ev640 = a->evals64;
+    const hy_dtype bulk = a->cfg.bulk;
+    // 1. state and sigma at the current parameters in the bulk precision
+    if (a->valid_dt != bulk || a->valid_theta != a->theta) {
+        double e;
+        HY_TRY(energy(a, a->theta, bulk, st, &e));
+    }
+    void *psi = a->buf[di(bulk)][0], *sigma = a->buf[di(bulk)][1];
+    // 2. screen
+    if (a->cfg.screen_top_m > 0)
+        return set_err(HY_ERR_UNSUPPORTED, "ranked screen needs a ranker");
+    HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, nullptr, a->K, a->d_g, bulk, st));
+    std::vector<double> g(a->K);
+    HY_TRY(cu(cudaMemcpyAsync(g.data(), a->d_g, a->K * sizeof(double), cudaMemcpyDeviceToHost, st),
+              "screen readback"));
+    HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+    const double t1 = now_s();
+    double gmax = 0.0, gn2 = 0.0;
+    for (double v : g) {
+        gmax = std::max(gmax, std::fabs(v));
+        gn2 += v * v;
+    }
+    rec->grad_norm = std::sqrt(gn2);
+    int64_t sel = -1;
+    for (int64_t k = 0; k < a->K; ++k)
+        if (std::fabs(g[k]) >= gmax - 1e-12 * gmax) {
+            sel = k;
+            break;
+        }
+    rec->t_screen = t1 - t0;
+    if (a->K == 0 || rec->grad_norm < a->cfg.eps_grad) {
+        rec->converged = 1;
+        rec->energy = rec->energy_bulk = 0.0;
+        rec->t_total = now_s() - t0;
+        return HY_OK;
+    }
+    rec->selected = sel;
+    rec->max_grad = std::fabs(g[sel]);
+    // 3. append and re-optimise
+    const size_t j = a->ops.size();
+    a->ops.push_back(sel);
+    a->theta.push_back(0.0);
+    // warm start: previous inverse Hessian, unit curvature guess for the
+    // new parameter
+    std::vector<double> H((j + 1) * (j + 1), 0.0);
+    for (size_t r = 0; r < j; ++r)
+        for (size_t c = 0; c < j; ++c) H[r * (j + 1) + c] = a->hinv[r * j + c];
+    H[j * (j + 1) + j] = 1.0;
+    a->hinv = H;
+    if (j == 0) a->hinv_fresh = true;
+    HY_TRY(upload_ops(a, st));
+    double e = 0.0;
+    if (bulk == HY_F64) {
+        HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.max_evals, st, &e));
+        rec->energy = rec->energy_bulk = e;
+        rec->energy_bulk_err = 0.0;
+    } else {
+        double e32 = 0.0, e64 = 0.0;
+        HY_TRY(bfgs(a, HY_F32, a->cfg.gtol_bulk, a->cfg.max_evals, st, &e32));
+        rec->energy_bulk = e32;
+        HY_TRY(energy(a, a->theta, HY_F64, st, &e64));
+        rec->energy_bulk_err = std::fabs(e32 - e64);
+        if (a->cfg.refine_steps > 0)
+            HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.refine_steps, st, &e64));
+        rec->energy = e64;
+    }
+    rec->n_evals = a->evals - ev0;
+    rec->n_evals_f64 = a->evals64 - ev640;
+    rec->t_optimise = now_s() - t1;
+    rec->t_total = now_s() - t0;
+    ++a->iter;
+    return HY_OK;
+}
+
+hy_status hy_adapt_ansatz(const hy_adapt *a, int64_t *ops, double *thetas, int64_t cap,
+                          int64_t *len)
+{
+    if (!a || !len) return set_err(HY_ERR_ARG, "NULL argument");
+    *len = int64_t(a->ops.size());
+    if (cap <= 0) return HY_OK;
+    if (!ops || !thetas || cap < *len) return set_err(HY_ERR_ARG, "output too small");
+    for (size_t l = 0; l < a->ops.size(); ++l) {
+        ops[l] = a->ops[l];
+        thetas[l] = a->theta[l];
+    }
+    return HY_OK;
+}
+
+hy_status hy_adapt_set_ansatz(hy_adapt *a, const int64_t *ops, const double *thetas,
+                              int64_t len)
+{
+    if (!a || len < 0 || (len > 0 && (!ops || !thetas)))
+        return set_err(HY_ERR_ARG, "bad arguments");
+    if (len > a->cfg.max_iter) return set_err(HY_ERR_ARG, "ansatz longer than max_iter");
+    for (int64_t l = 0; l < len; ++l)
+        if (ops[l] < 0 || ops[l] >= a->K || !std::isfinite(thetas[l]))
+            return set_err(HY_ERR_ARG, "invalid operator index or parameter");
+    a->ops.assign(ops, ops + len);
+    a->theta.assign(thetas, thetas + len);
+    a->hinv.assign(size_t(len) * len, 0.0);
+    for (int64_t l = 0; l < len; ++l) a->hinv[l * len + l] = 1.0;
+    a->hinv_fresh = true;
+    a->valid_dt = -1;
+    a->iter = int(len);
+    cudaStream_t st = nullptr;
+    return upload_ops(a, st);
+}
+
+hy_status hy_adapt_evaluate(hy_adapt *a, const double *thetas, hy_dtype dt, double *e,
+                            double *grad, void *stream)
+{
+    if (!a || !e || (!thetas && !a->ops.empty())) return set_err(HY_ERR_ARG, "NULL argument");
+    if (dt != HY_F64 && !(dt == HY_F32 && a->cfg.bulk == HY_F32))
+        return set_err(HY_ERR_ARG, "dtype not allocated by this driver");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<double> th(thetas, thetas + a->ops.size()), g;
+    HY_TRY(upload_ops(a, st));
+    HY_TRY(energy(a, th, dt, st, e));
+    if (grad) {
+        HY_TRY(gradient(a, th, dt, st, g));
+        std::copy(g.begin(), g.end(), grad);
+    }
+    return HY_OK;
+}
+
+hy_status hy_adapt_state(const hy_adapt *a, void *psi, hy_dtype dt, void *stream)
+{
+    if (!a || !psi) return set_err(HY_ERR_ARG, "NULL argument");
+    if (a->valid_dt != dt) return set_err(HY_ERR_ARG, "no state of this dtype evaluated yet");
+    return cu(cudaMemcpyAsync(psi, a->buf[di(dt)][0], size_t(a->N) * esize(dt),
+                              cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)),
+              "state copy");
+}
+
+}  // extern "C"

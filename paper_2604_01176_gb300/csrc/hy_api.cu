@@ -64,6 +64,10 @@ struct DevCsr {
 
 }  // namespace
 
+namespace hy {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace hy
+
 struct hy_ham {
     int n = 0, na = 0, nb = 0;
     int64_t Na = 0, Nb = 0, N = 0;

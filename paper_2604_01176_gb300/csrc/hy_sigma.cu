@@ -123,17 +123,54 @@ cudaError_t add_transposed(const T *tau, T *sigma, int64_t R, int64_t C,
 // in shared memory, the n*n coefficient slice likewise, and every output
 // column b' accumulates its diagonal beta term plus its nexb beta
 // excitations gathered from the staged row.
+//
+// Shared-memory staging is done in 32-bit planes: a double is kept as two
+// separate arrays of low and high words, so each random gather is two
+// 4-byte loads (one bank each) instead of one 8-byte load spanning two
+// banks, which conflicts about twice as often.
 // ---------------------------------------------------------------------------
+template <typename T>
+struct Planes;
+
+template <>
+struct Planes<float> {
+    static constexpr int kWords = 1;
+    __device__ static void put(uint32_t *base, int64_t stride, int64_t i, float v)
+    {
+        base[i] = __float_as_uint(v);
+    }
+    __device__ static float get(const uint32_t *base, int64_t stride, int64_t i)
+    {
+        return __uint_as_float(base[i]);
+    }
+};
+
+template <>
+struct Planes<double> {
+    static constexpr int kWords = 2;
+    __device__ static void put(uint32_t *base, int64_t stride, int64_t i, double v)
+    {
+        base[i] = uint32_t(__double2loint(v));
+        base[stride + i] = uint32_t(__double2hiint(v));
+    }
+    __device__ static double get(const uint32_t *base, int64_t stride, int64_t i)
+    {
+        return __hiloint2double(int(base[stride + i]), int(base[i]));
+    }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(512)
 k_coupling(CouplingArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    using PL = Planes<T>;
     const int64_t Nb = a.Nb;
-    T *row = reinterpret_cast<T *>(smem_raw);
-    T *acc = row + Nb;
-    T *C = acc + Nb;
     const int n = a.n, nn = n * n;
+    T *acc = reinterpret_cast<T *>(smem_raw);                 // [Nb]
+    uint32_t *row = reinterpret_cast<uint32_t *>(acc + Nb);    // planes [Nb]
+    uint32_t *C = row + PL::kWords * Nb;                       // planes [nn]
+    T *Cdiag = reinterpret_cast<T *>(C + PL::kWords * nn + (PL::kWords * nn) % 2);  // [n]
     for (int64_t ar = blockIdx.x; ar < a.Na; ar += gridDim.x) {
         for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) acc[b] = T(0);
         const uint32_t amask = a.astr[ar];
@@ -143,12 +180,13 @@ k_coupling(CouplingArgs<T> a)
             if (e < 0) {
                 Ja = ar;
                 for (int rs = threadIdx.x; rs < nn; rs += blockDim.x) {
-                    T s = T(0);
+                    T v = T(0);
                     for (uint32_t m = amask; m; m &= m - 1) {
                         int p = __ffs(m) - 1;
-                        s += a.V[size_t(p * n + p) * nn + rs];
+                        v += a.V[size_t(p * n + p) * nn + rs];
                     }
-                    C[rs] = s;
+                    PL::put(C, nn, rs, v);
+                    if (rs / n == rs % n) Cdiag[rs / n] = v;
                 }
             } else {
                 const uint32_t u = a.aex[ar * a.nexa + e];
@@ -157,26 +195,25 @@ k_coupling(CouplingArgs<T> a)
                 const bool neg = (u >> 31) != 0;
                 for (int rs = threadIdx.x; rs < nn; rs += blockDim.x) {
                     T v = a.V[size_t(p * n + q) * nn + rs];
-                    C[rs] = neg ? -v : v;
+                    v = neg ? -v : v;
+                    PL::put(C, nn, rs, v);
+                    if (rs / n == rs % n) Cdiag[rs / n] = v;
                 }
             }
             const T *src = a.psi + Ja * Nb;
-            for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) row[b] = src[b];
+            for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) PL::put(row, Nb, b, src[b]);
             __syncthreads();
             for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) {
                 T d = T(0);
-                for (uint32_t m = a.bstr[b]; m; m &= m - 1) {
-                    int r = __ffs(m) - 1;
-                    d += C[r * n + r];
-                }
-                T s = d * row[b];
+                for (uint32_t m = a.bstr[b]; m; m &= m - 1) d += Cdiag[__ffs(m) - 1];
+                T s = d * PL::get(row, Nb, b);
                 const uint32_t *bx = a.bexT + b;
                 for (int f = 0; f < a.nexb; ++f) {
                     const uint32_t u = bx[size_t(f) * Nb];
-                    const int r = (u >> 16) & 15, t = (u >> 20) & 15;
-                    T cv = C[r * n + t];
-                    if (u >> 31) cv = -cv;
-                    s += cv * row[u & 0xFFFFu];
+                    const int rt = ((u >> 16) & 15) * n + ((u >> 20) & 15);
+                    T cv = PL::get(C, nn, rt);
+                    cv = (u >> 31) ? -cv : cv;
+                    s += cv * PL::get(row, Nb, u & 0xFFFFu);
                 }
                 acc[b] += s;
             }
@@ -192,7 +229,11 @@ template <typename T>
 cudaError_t coupling(const CouplingArgs<T> &a, int num_sms, cudaStream_t st)
 {
     if (a.Na == 0 || a.Nb == 0) return cudaSuccess;
-    const size_t smem = (2 * size_t(a.Nb) + size_t(a.n) * a.n) * sizeof(T);
+    // acc [Nb] T, row planes [Nb] T, coefficient planes [n*n] T (+ pad),
+    // diagonal coefficients [n] T
+    const size_t nn = size_t(a.n) * a.n;
+    const size_t smem = 2 * size_t(a.Nb) * sizeof(T) + (nn + 1) * sizeof(T) +
+                        size_t(a.n) * sizeof(T);
     cudaError_t err = cudaFuncSetAttribute(
         k_coupling<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (err != cudaSuccess) return err;
