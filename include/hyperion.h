@@ -65,6 +65,8 @@ typedef enum { HY_POOL_SPIN_ADAPTED_SD = 0 } hy_pool_kind;
 
 typedef struct hy_ham hy_ham;
 typedef struct hy_pool hy_pool;
+typedef struct hy_ranker hy_ranker;
+typedef struct hy_adapt hy_adapt;
 
 /* Message describing the calling thread's most recent error ("" if none). */
 const char *hy_last_error(void);
@@ -202,6 +204,127 @@ hy_status hy_apply_excitation(const hy_ham *h, const hy_pool *p, int64_t k,
 hy_status hy_normalize(const hy_ham *h, void *psi, hy_dtype dt, void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Batches of molecules                                                     */
+/* ---------------------------------------------------------------------- */
+
+/* A batch runs sigma = H psi (and the energies <psi|sigma>) for many
+ * molecules of uneven size in one persistent launch: CTAs are split into
+ * groups of tile.gsize threads; each group takes the next (molecule, alpha
+ * row) task from a device work-list (largest molecules first) and computes
+ * that output row completely, then writes its <psi|sigma> partial, which a
+ * second small kernel sums per molecule in row order.  Intended for
+ * molecules of up to 12 orbitals (their tables stay in L2); larger ones are
+ * correct but slow.  States are packed: molecule m's amplitudes start at
+ * element offsets[m] of one buffer (offsets are multiples of 32). */
+typedef struct hy_batch hy_batch;
+
+typedef struct {
+    int gsize;        /* threads per group (32, 64, ..., 1024)             */
+    int groups;       /* groups per CTA (gsize * groups <= 1024, <= 15)    */
+    int ctas_per_sm;  /* 0: as many as occupancy allows                    */
+} hy_batch_tile;
+
+/* hams: host array of `count` handles, which must outlive the batch. */
+hy_status hy_batch_create(const hy_ham *const *hams, int count, hy_batch **out);
+hy_status hy_batch_destroy(hy_batch *b);
+/* *total: packed state length; *n_tasks: rows of all molecules. */
+hy_status hy_batch_info(const hy_batch *b, int64_t *total, int64_t *n_tasks);
+/* offsets: host, count + 1 entries (the last one = total). */
+hy_status hy_batch_offsets(const hy_batch *b, int64_t *offsets);
+hy_status hy_batch_set_tile(hy_batch *b, const hy_batch_tile *tile);
+hy_status hy_batch_get_tile(const hy_batch *b, hy_batch_tile *tile);
+
+/* sigma = H psi for every molecule (packed device buffers of dt); if
+ * energies is not NULL, energies[m] (device doubles) = <psi_m|sigma_m>.
+ * Launches: one memset of the task counter, the persistent kernel, and the
+ * energy kernel.  No host synchronisation (capturable). */
+hy_status hy_batch_apply_h(hy_batch *b, const void *psi, void *sigma,
+                           hy_dtype dt, double *energies, void *stream);
+
+/* Same as hy_batch_apply_h, through a CUDA graph the batch captures on the
+ * first call for these (psi, sigma, dt, energies, tile) and replays after. */
+hy_status hy_batch_graph_launch(hy_batch *b, const void *psi, void *sigma,
+                                hy_dtype dt, double *energies, void *stream);
+
+/* Autotuner: times every tile shape (gsize in 32..512, groups in 1..8,
+ * within the shared-memory and barrier limits) on these buffers with CUDA
+ * events (2 warm-up + 3 timed launches each), keeps the fastest as the
+ * batch's tile and returns it with its mean time in *ms (host). */
+hy_status hy_batch_tune(hy_batch *b, const void *psi, void *sigma, hy_dtype dt,
+                        hy_batch_tile *best, double *ms, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Learned pool ranker                                                      */
+/* ---------------------------------------------------------------------- */
+
+/* Occupation numbers <psi|n_P|psi> / <psi|psi> of the 2*n_orb spin orbitals
+ * (blocked order) into occ (device floats).  One pass over psi; the sums
+ * run in a fixed order.  (Used by the ranker features.) */
+hy_status hy_occupations(const hy_ham *h, const void *psi, hy_dtype dt,
+                         float *occ, void *stream);
+
+/* The ranker is an addition with no counterpart in the paper's method: a
+ * small MLP that predicts, per pool operator, t_k = log10(|g_k| / max|g| +
+ * 1e-12) from 16 features, so that only its top-M operators are screened
+ * exactly.  Features of operator k (first constituent; modes in blocked
+ * order): [0..3] kind flags (single, same-spin double, opposite-spin
+ * double, extra constituents); [4..7] annihilated and created spatial
+ * orbitals / n_orb (-0.1 where absent); [8] log10 |integral| (h_ca for
+ * singles, (c0 a0|c1 a1) minus exchange for same spin); [9] diagonal
+ * one-electron gap; [10] product of occupations n_a0 n_a1 (1-n_c0)(1-n_c1)
+ * of psi, the weight of determinants the operator acts on under a
+ * mean-field estimate; [11] n_a0 + n_a1 - n_c0 - n_c1; [12..15] the caller's
+ * extra[k][0..3] (the driver passes the stale log10 |g_k| / max, its age,
+ * the operator's count in the ansatz and its summed |theta|), or 0.
+ * feat: device, K x 16 floats; extra: device K x 4 floats or NULL. */
+hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
+                             hy_dtype dt, const float *extra, float *feat,
+                             void *stream);
+
+/* MLP 16 -> hidden -> hidden -> hidden -> 1 (ReLU), FP32, He-uniform init
+ * from `seed` (SplitMix64).  The ranker owns its device parameters, Adam
+ * moments and training set. */
+hy_status hy_ranker_create(int hidden, uint64_t seed, hy_ranker **out);
+hy_status hy_ranker_destroy(hy_ranker *r);
+hy_status hy_ranker_info(const hy_ranker *r, int64_t *n_params,
+                         int64_t *n_samples, int *n_features, int *fitted);
+/* Parameters as one host float array of n_params entries (checkpoints). */
+hy_status hy_ranker_get_params(const hy_ranker *r, float *host);
+hy_status hy_ranker_set_params(hy_ranker *r, const float *host);
+
+/* score[i] (device) = MLP(feat[i]) for m rows (device K x 16). */
+hy_status hy_ranker_predict(hy_ranker *r, const float *feat, int64_t m,
+                            float *score, void *stream);
+
+/* Append m training pairs: features (device m x 16) and the exact
+ * gradients g (device doubles) of one screen; the targets are normalised
+ * by that screen's max |g|. */
+hy_status hy_ranker_add_samples(hy_ranker *r, const float *feat,
+                                const double *g, int64_t m, void *stream);
+
+/* Adam (lr, beta 0.9 / 0.999) on the mean squared error over all samples,
+ * `epochs` passes in shuffled minibatches of `batch` rows (shuffle seeded).
+ * *loss (host, optional) = mean squared error of the last epoch. */
+hy_status hy_ranker_fit(hy_ranker *r, int epochs, int batch, float lr,
+                        uint64_t seed, float *loss, void *stream);
+
+/* idx[0..k-1] (device int32) = indices of the k largest of m <= 8192 scores
+ * (device floats), descending, ties to the lower index. */
+hy_status hy_ranker_topk(const float *score, int64_t m, int64_t k,
+                         int32_t *idx, void *stream);
+
+/* Attach a ranker to a driver created with screen_top_m = M > 0.  The first
+ * warm_iters iterations run the full screen and feed the ranker (features,
+ * exact |g|) pairs; it is then fitted (`epochs` passes) and from then on
+ * proposes the top M operators, which are screened exactly.  The full
+ * screen stays the fallback (run whenever the proposals' ||g|| would stop
+ * the loop) and, with cfg.judge, the judge: every ranked iteration also
+ * runs it, records the rank of the true argmax, adds its pairs, and refits
+ * every refit_every ranked iterations (0: never). */
+hy_status hy_adapt_set_ranker(hy_adapt *a, hy_ranker *r, int warm_iters,
+                              int epochs, int refit_every);
+
+/* ---------------------------------------------------------------------- */
 /* ADAPT-VQE driver                                                         */
 /* ---------------------------------------------------------------------- */
 
@@ -251,11 +374,10 @@ typedef struct {
     int64_t true_argmax;   /* judge: argmax of the full screen (-1 if none)   */
     int64_t true_rank;     /* judge: rank of true_argmax among the proposals
                               (0 = proposed first; -1 = not proposed)          */
-    double t_screen, t_optimise, t_total;
+    double t_screen, t_optimise, t_total;   /* judge time excluded            */
+    double t_judge;        /* judge: time of the extra full screen and refit  */
 } hy_adapt_record;
 
-typedef struct hy_adapt hy_adapt;
-typedef struct hy_ranker hy_ranker;
 
 /* Create a driver for (h, p); allocates its state buffers on the device.
  * cfg == NULL takes the defaults: HY_F64, max_iter 64, eps_grad 1e-5,

@@ -21,7 +21,10 @@ import torch
 from . import _abi
 from ._abi import HY_F32, HY_F64, HyError, check
 
-__all__ = ["Hamiltonian", "Pool", "Adapt", "HyError", "dtype_code", "stream_ptr"]
+__all__ = ["Hamiltonian", "Pool", "Adapt", "Ranker", "Batch", "HyError", "dtype_code",
+           "stream_ptr", "occupations", "ranker_features", "topk"]
+
+N_FEATURES = 16
 
 
 def dtype_code(t: torch.dtype) -> int:
@@ -342,8 +345,191 @@ class Adapt:
                                             stream_ptr(stream)))
         return e.value, g
 
+    def set_ranker(self, ranker: "Ranker", warm_iters=3, epochs=30, refit_every=0):
+        check(_abi.load().hy_adapt_set_ranker(self._a, ranker.handle, int(warm_iters),
+                                              int(epochs), int(refit_every)))
+        self._ranker = ranker   # keep it alive as long as the driver
+
     def state(self, dtype=torch.float64, stream=None) -> torch.Tensor:
         out = torch.empty(self.ham.n_det, dtype=dtype, device=self.ham.device)
         check(_abi.load().hy_adapt_state(self._a, _ptr(out), dtype_code(dtype),
                                          stream_ptr(stream)))
         return out
+
+
+def occupations(ham: Hamiltonian, psi: torch.Tensor, stream=None) -> torch.Tensor:
+    """<psi|n_P|psi>/<psi|psi> for the 2n spin orbitals (blocked order)."""
+    ham._check_state(psi)
+    out = torch.empty(2 * ham.n_orb, dtype=torch.float32, device=psi.device)
+    check(_abi.load().hy_occupations(ham.handle, _ptr(psi), dtype_code(psi.dtype),
+                                     _ptr(out), stream_ptr(stream)))
+    return out
+
+
+def ranker_features(ham: Hamiltonian, pool: Pool, psi: torch.Tensor,
+                    extra: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Per-operator ranker features, (K, 16) float32 on the device."""
+    ham._check_state(psi)
+    out = torch.empty((len(pool), N_FEATURES), dtype=torch.float32, device=psi.device)
+    if extra is not None:
+        _require_cuda(extra)
+        if extra.dtype != torch.float32 or extra.shape != (len(pool), 4):
+            raise ValueError("extra must be float32 of shape (K, 4)")
+    check(_abi.load().hy_ranker_features(
+        ham.handle, pool.handle, _ptr(psi), dtype_code(psi.dtype),
+        _ptr(extra) if extra is not None else None, _ptr(out), stream_ptr(stream)))
+    return out
+
+
+def topk(scores: torch.Tensor, k: int, stream=None) -> torch.Tensor:
+    """Indices of the k largest scores (descending, ties to the lower index)."""
+    _require_cuda(scores)
+    if scores.dtype != torch.float32:
+        raise TypeError("scores must be float32")
+    out = torch.empty(int(k), dtype=torch.int32, device=scores.device)
+    check(_abi.load().hy_ranker_topk(_ptr(scores), scores.numel(), int(k), _ptr(out),
+                                     stream_ptr(stream)))
+    return out
+
+
+class Ranker:
+    """Learned pool ranker: MLP 16 -> H -> H -> H -> 1 (ReLU, FP32)."""
+
+    def __init__(self, hidden=256, seed=7):
+        handle = ctypes.c_void_p()
+        check(_abi.load().hy_ranker_create(int(hidden), int(seed), ctypes.byref(handle)))
+        self._r = handle
+        self.hidden = int(hidden)
+
+    def close(self):
+        if getattr(self, "_r", None):
+            _abi.load().hy_ranker_destroy(self._r)
+            self._r = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._r
+
+    def info(self) -> dict:
+        npar, nsam = ctypes.c_int64(), ctypes.c_int64()
+        nf, fit = ctypes.c_int(), ctypes.c_int()
+        check(_abi.load().hy_ranker_info(self._r, ctypes.byref(npar), ctypes.byref(nsam),
+                                         ctypes.byref(nf), ctypes.byref(fit)))
+        return {"n_params": npar.value, "n_samples": nsam.value,
+                "n_features": nf.value, "fitted": bool(fit.value)}
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.info()["n_params"], dtype=np.float32)
+        check(_abi.load().hy_ranker_get_params(self._r, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_params(self, w: np.ndarray):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        if w.size != self.info()["n_params"]:
+            raise ValueError("parameter count mismatch")
+        check(_abi.load().hy_ranker_set_params(self._r, w.ctypes.data_as(ctypes.c_void_p)))
+
+    def predict(self, feat: torch.Tensor, stream=None) -> torch.Tensor:
+        _require_cuda(feat)
+        out = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
+        check(_abi.load().hy_ranker_predict(self._r, _ptr(feat), feat.shape[0], _ptr(out),
+                                            stream_ptr(stream)))
+        return out
+
+    def add_samples(self, feat: torch.Tensor, g: torch.Tensor, stream=None):
+        _require_cuda(feat, g)
+        if g.dtype != torch.float64 or feat.dtype != torch.float32:
+            raise TypeError("feat must be float32 and g float64")
+        check(_abi.load().hy_ranker_add_samples(self._r, _ptr(feat), _ptr(g), g.numel(),
+                                                stream_ptr(stream)))
+
+    def fit(self, epochs=30, batch=256, lr=1e-3, seed=1234, stream=None) -> float:
+        loss = ctypes.c_float()
+        check(_abi.load().hy_ranker_fit(self._r, int(epochs), int(batch), float(lr),
+                                        int(seed), ctypes.byref(loss), stream_ptr(stream)))
+        return loss.value
+
+
+class Batch:
+    """Many molecules in one persistent launch (hy_batch_*).  States are
+    packed into one buffer; `offsets[m]` is molecule m's first amplitude."""
+
+    def __init__(self, hams):
+        self.hams = list(hams)
+        arr = (ctypes.c_void_p * len(self.hams))(*[h.handle for h in self.hams])
+        handle = ctypes.c_void_p()
+        check(_abi.load().hy_batch_create(arr, len(self.hams), ctypes.byref(handle)))
+        self._b = handle
+        tot, nt = ctypes.c_int64(), ctypes.c_int64()
+        check(_abi.load().hy_batch_info(self._b, ctypes.byref(tot), ctypes.byref(nt)))
+        self.total, self.n_tasks = tot.value, nt.value
+        off = np.zeros(len(self.hams) + 1, dtype=np.int64)
+        check(_abi.load().hy_batch_offsets(self._b, off.ctypes.data_as(ctypes.c_void_p)))
+        self.offsets = off
+        self.device = self.hams[0].device
+
+    def close(self):
+        if getattr(self, "_b", None):
+            _abi.load().hy_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self, dtype=torch.float64) -> torch.Tensor:
+        return torch.zeros(self.total, dtype=dtype, device=self.device)
+
+    def pack(self, states, dtype=torch.float64) -> torch.Tensor:
+        out = self.empty(dtype)
+        for m, s in enumerate(states):
+            out[self.offsets[m]:self.offsets[m] + self.hams[m].n_det] = s
+        return out
+
+    def unpack(self, packed: torch.Tensor):
+        return [packed[self.offsets[m]:self.offsets[m] + h.n_det]
+                for m, h in enumerate(self.hams)]
+
+    def _check(self, psi, sigma, energies):
+        _require_cuda(psi, sigma, energies)
+        if psi.numel() != self.total or sigma.numel() != self.total or psi.dtype != sigma.dtype:
+            raise ValueError("packed psi / sigma must have `total` elements of one dtype")
+        if energies is not None and (energies.dtype != torch.float64
+                                     or energies.numel() != len(self.hams)):
+            raise ValueError("energies must be float64 with one entry per molecule")
+
+    def apply_h(self, psi, sigma=None, energies=None, graph=False, stream=None):
+        if sigma is None:
+            sigma = torch.empty_like(psi)
+        self._check(psi, sigma, energies)
+        fn = _abi.load().hy_batch_graph_launch if graph else _abi.load().hy_batch_apply_h
+        check(fn(self._b, _ptr(psi), _ptr(sigma), dtype_code(psi.dtype),
+                 _ptr(energies) if energies is not None else None, stream_ptr(stream)))
+        return sigma
+
+    @property
+    def tile(self) -> dict:
+        t = _abi.BatchTile()
+        check(_abi.load().hy_batch_get_tile(self._b, ctypes.byref(t)))
+        return {"gsize": t.gsize, "groups": t.groups, "ctas_per_sm": t.ctas_per_sm}
+
+    def set_tile(self, gsize, groups, ctas_per_sm=0):
+        t = _abi.BatchTile(int(gsize), int(groups), int(ctas_per_sm))
+        check(_abi.load().hy_batch_set_tile(self._b, ctypes.byref(t)))
+
+    def tune(self, psi, sigma, stream=None):
+        """Autotune the tile shape on these buffers; returns (tile, ms)."""
+        self._check(psi, sigma, None)
+        t = _abi.BatchTile()
+        ms = ctypes.c_double()
+        check(_abi.load().hy_batch_tune(self._b, _ptr(psi), _ptr(sigma), dtype_code(psi.dtype),
+                                        ctypes.byref(t), ctypes.byref(ms), stream_ptr(stream)))
+        return {"gsize": t.gsize, "groups": t.groups, "ctas_per_sm": t.ctas_per_sm}, ms.value

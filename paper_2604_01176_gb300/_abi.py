@@ -30,6 +30,12 @@ class HyError(RuntimeError):
 _lib = None
 
 
+class BatchTile(ctypes.Structure):
+    """Mirror of hy_batch_tile."""
+    _fields_ = [("gsize", ctypes.c_int), ("groups", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int)]
+
+
 class AdaptConfig(ctypes.Structure):
     """Mirror of hy_adapt_config."""
     _fields_ = [("bulk", ctypes.c_int), ("max_iter", ctypes.c_int),
@@ -48,7 +54,7 @@ class AdaptRecord(ctypes.Structure):
                 ("n_evals", ctypes.c_int32), ("n_evals_f64", ctypes.c_int32),
                 ("true_argmax", ctypes.c_int64), ("true_rank", ctypes.c_int64),
                 ("t_screen", ctypes.c_double), ("t_optimise", ctypes.c_double),
-                ("t_total", ctypes.c_double)]
+                ("t_total", ctypes.c_double), ("t_judge", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -81,6 +87,27 @@ SIGNATURES = {
     "hy_pool_describe": (I32, [P, I64, P]),
     "hy_pool_gradients": (I32, [P, P, P, P, P, I64, P, I32, P]),
     "hy_apply_excitation": (I32, [P, P, I64, D, P, I32, I32, P]),
+    "hy_batch_create": (I32, [P, I32, PP]),
+    "hy_batch_destroy": (I32, [P]),
+    "hy_batch_info": (I32, [P, PI64, PI64]),
+    "hy_batch_offsets": (I32, [P, P]),
+    "hy_batch_set_tile": (I32, [P, P]),
+    "hy_batch_get_tile": (I32, [P, P]),
+    "hy_batch_apply_h": (I32, [P, P, P, I32, P, P]),
+    "hy_batch_graph_launch": (I32, [P, P, P, I32, P, P]),
+    "hy_batch_tune": (I32, [P, P, P, I32, P, P, P]),
+    "hy_occupations": (I32, [P, P, I32, P, P]),
+    "hy_ranker_features": (I32, [P, P, P, I32, P, P, P]),
+    "hy_ranker_create": (I32, [I32, ctypes.c_uint64, PP]),
+    "hy_ranker_destroy": (I32, [P]),
+    "hy_ranker_info": (I32, [P, PI64, PI64, P, P]),
+    "hy_ranker_get_params": (I32, [P, P]),
+    "hy_ranker_set_params": (I32, [P, P]),
+    "hy_ranker_predict": (I32, [P, P, I64, P, P]),
+    "hy_ranker_add_samples": (I32, [P, P, P, I64, P]),
+    "hy_ranker_fit": (I32, [P, I32, I32, ctypes.c_float, ctypes.c_uint64, P, P]),
+    "hy_ranker_topk": (I32, [P, I64, I64, P, P]),
+    "hy_adapt_set_ranker": (I32, [P, P, I32, I32, I32]),
     "hy_adapt_create": (I32, [P, P, P, PP]),
     "hy_adapt_destroy": (I32, [P]),
     "hy_adapt_step": (I32, [P, P, P]),

@@ -35,7 +35,13 @@ size_t esize(hy_dtype dt) { return dt == HY_F64 ? 8 : 4; }
 struct hy_adapt {
     const hy_ham *h = nullptr;
     const hy_pool *p = nullptr;
-    const hy_ranker *ranker = nullptr;
+    hy_ranker *ranker = nullptr;
+    int warm_iters = 0, epochs = 0, refit_every = 0, ranked_iters = 0;
+    float *d_feat = nullptr, *d_extra = nullptr, *d_score = nullptr;
+    double *d_gp = nullptr;       // proposals' exact gradients [M]
+    std::vector<double> last_g;   // |g_k| when last screened (-1: never)
+    std::vector<int> age;         // iterations since last screened
+    std::vector<float> count, thsum;
     hy_adapt_config cfg{};
     int64_t N = 0, K = 0;
     // device state: [dtype][psi, sigma, phi, lam]
@@ -153,10 +159,43 @@ double maxabs(const std::vector<double> &x)
     return m;
 }
 
+// remember the exact |g_k| of the operators just screened; age the rest
+void note_screen(hy_adapt *a, const std::vector<int64_t> &ids, const std::vector<double> &gv)
+{
+    for (auto &x : a->age) ++x;
+    for (size_t i = 0; i < ids.size(); ++i) {
+        a->last_g[ids[i]] = std::fabs(gv[i]);
+        a->age[ids[i]] = 0;
+    }
+}
+
+// per-operator extra ranker features from the driver's bookkeeping
+hy_status upload_extra(hy_adapt *a, cudaStream_t st)
+{
+    double mx = 0.0;
+    for (double v : a->last_g) mx = std::max(mx, v);
+    std::vector<float> ex(size_t(a->K) * 4);
+    for (int64_t k = 0; k < a->K; ++k) {
+        const double lg = a->last_g[k];
+        ex[4 * k + 0] = lg < 0.0 ? -12.0f : float(std::log10(lg / (mx > 0 ? mx : 1.0) + 1e-12));
+        ex[4 * k + 1] = float(std::min(a->age[k], 50)) / 10.0f;
+        ex[4 * k + 2] = a->count[k];
+        ex[4 * k + 3] = a->thsum[k];
+    }
+    for (size_t l = 0; l < a->ops.size(); ++l) ex[4 * a->ops[l] + 3] = 0.0f;
+    for (size_t l = 0; l < a->ops.size(); ++l) ex[4 * a->ops[l] + 3] += float(std::fabs(a->theta[l]));
+    HY_TRY(cu(cudaMemcpyAsync(a->d_extra, ex.data(), ex.size() * 4, cudaMemcpyHostToDevice, st),
+              "upload extra features"));
+    return cu(cudaStreamSynchronize(st), "sync");
+}
+
 // BFGS with backtracking (Armijo) line search on E(theta) in dt, starting
-// from a->theta and a->hinv; updates both.  *e_out = final energy.
+// from a->theta and a->hinv; updates both.  *e_out = final energy.  With
+// stall > 0 the run also stops after an accepted step whose decrease is
+// below stall * |E| (the rounding floor of a float evaluation, where further
+// steps only follow noise).
 hy_status bfgs(hy_adapt *a, hy_dtype dt, double gtol, int max_steps, cudaStream_t st,
-               double *e_out)
+               double *e_out, double stall = 0.0)
 {
     const size_t j = a->ops.size();
     std::vector<double> x = a->theta, g, gn, pdir(j), xn(j), s(j), y(j), Hy(j);
@@ -219,9 +258,11 @@ hy_status bfgs(hy_adapt *a, hy_dtype dt, double gtol, int max_steps, cudaStream_
                     H[r * j + c] += (1.0 + rho * yHy) * rho * s[r] * s[c] -
                                     rho * (Hy[r] * s[c] + s[r] * Hy[c]);
         }
+        const bool stalled = stall > 0.0 && (e - en) < stall * std::fabs(e);
         x = xn;
         e = en;
         g = gn;
+        if (stalled) break;
     }
     a->theta = x;
     *e_out = e;
@@ -290,6 +331,16 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
     alloc(reinterpret_cast<void **>(&a->d_e), 8);
     alloc(reinterpret_cast<void **>(&a->d_ops), size_t(c.max_iter) * 4);
     alloc(reinterpret_cast<void **>(&a->d_prop), size_t(a->K) * 4);
+    if (c.screen_top_m > 0) {
+        alloc(reinterpret_cast<void **>(&a->d_feat), size_t(a->K) * 16 * 4);
+        alloc(reinterpret_cast<void **>(&a->d_extra), size_t(a->K) * 4 * 4);
+        alloc(reinterpret_cast<void **>(&a->d_score), size_t(a->K) * 4);
+        alloc(reinterpret_cast<void **>(&a->d_gp), size_t(a->K) * 8);
+    }
+    a->last_g.assign(a->K, -1.0);
+    a->age.assign(a->K, 0);
+    a->count.assign(a->K, 0.0f);
+    a->thsum.assign(a->K, 0.0f);
     if (s != HY_OK) {
         hy_adapt_destroy(a);
         return s;
@@ -309,6 +360,10 @@ hy_status hy_adapt_destroy(hy_adapt *a)
     cudaFree(a->d_e);
     cudaFree(a->d_ops);
     cudaFree(a->d_prop);
+    cudaFree(a->d_feat);
+    cudaFree(a->d_extra);
+    cudaFree(a->d_score);
+    cudaFree(a->d_gp);
     delete a;
     return HY_OK;
 }
@@ -333,36 +388,100 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         HY_TRY(energy(a, a->theta, bulk, st, &e));
     }
     void *psi = a->buf[di(bulk)][0], *sigma = a->buf[di(bulk)][1];
-    // 2. screen
-    if (a->cfg.screen_top_m > 0)
-        return set_err(HY_ERR_UNSUPPORTED, "ranked screen needs a ranker");
-    HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, nullptr, a->K, a->d_g, bulk, st));
-    std::vector<double> g(a->K);
-    HY_TRY(cu(cudaMemcpyAsync(g.data(), a->d_g, a->K * sizeof(double), cudaMemcpyDeviceToHost, st),
-              "screen readback"));
-    HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
-    const double t1 = now_s();
-    double gmax = 0.0, gn2 = 0.0;
-    for (double v : g) {
-        gmax = std::max(gmax, std::fabs(v));
-        gn2 += v * v;
-    }
-    rec->grad_norm = std::sqrt(gn2);
+    // 2. screen: full, or the ranker's top-M proposals screened exactly
+    const bool ranked = a->cfg.screen_top_m > 0;
+    if (ranked && !a->ranker) return set_err(HY_ERR_UNSUPPORTED, "ranked screen needs a ranker");
+    const bool use_ranker = ranked && a->iter >= a->warm_iters;
+    std::vector<double> g;
+    std::vector<int64_t> cand;   // screened operators, in proposal order
     int64_t sel = -1;
-    for (int64_t k = 0; k < a->K; ++k)
-        if (std::fabs(g[k]) >= gmax - 1e-12 * gmax) {
-            sel = k;
-            break;
+    double gmax = 0.0, gn2 = 0.0;
+    auto full_screen = [&]() -> hy_status {
+        HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, nullptr, a->K, a->d_g, bulk, st));
+        g.assign(a->K, 0.0);
+        HY_TRY(cu(cudaMemcpyAsync(g.data(), a->d_g, a->K * sizeof(double),
+                                  cudaMemcpyDeviceToHost, st), "screen readback"));
+        return cu(cudaStreamSynchronize(st), "sync");
+    };
+    auto pick = [&](const std::vector<int64_t> &ids, const std::vector<double> &gv) {
+        gmax = 0.0;
+        gn2 = 0.0;
+        for (double v : gv) {
+            gmax = std::max(gmax, std::fabs(v));
+            gn2 += v * v;
         }
+        sel = -1;
+        for (size_t i = 0; i < gv.size(); ++i)
+            if (std::fabs(gv[i]) >= gmax - 1e-12 * gmax && (sel < 0 || ids[i] < sel)) sel = ids[i];
+    };
+    std::vector<int64_t> all(a->K);
+    for (int64_t k = 0; k < a->K; ++k) all[k] = k;
+    double t_judge = 0.0;
+    if (ranked) HY_TRY(upload_extra(a, st));
+    if (!use_ranker) {
+        HY_TRY(full_screen());
+        pick(all, g);
+        if (ranked) {
+            HY_TRY(hy_ranker_features(a->h, a->p, psi, bulk, a->d_extra, a->d_feat, st));
+            HY_TRY(hy_ranker_add_samples(a->ranker, a->d_feat, a->d_g, a->K, st));
+            if (a->iter + 1 == a->warm_iters)
+                HY_TRY(hy_ranker_fit(a->ranker, a->epochs, 256, 1e-3f, 1234 + a->iter, nullptr, st));
+        }
+        note_screen(a, all, g);
+    } else {
+        const int64_t M = std::min<int64_t>(a->cfg.screen_top_m, a->K);
+        HY_TRY(hy_ranker_features(a->h, a->p, psi, bulk, a->d_extra, a->d_feat, st));
+        HY_TRY(hy_ranker_predict(a->ranker, a->d_feat, a->K, a->d_score, st));
+        HY_TRY(hy_ranker_topk(a->d_score, a->K, M, a->d_prop, st));
+        HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, a->d_prop, M, a->d_gp, bulk, st));
+        std::vector<int32_t> prop(M);
+        std::vector<double> gp(M);
+        HY_TRY(cu(cudaMemcpyAsync(prop.data(), a->d_prop, M * 4, cudaMemcpyDeviceToHost, st),
+                  "proposals readback"));
+        HY_TRY(cu(cudaMemcpyAsync(gp.data(), a->d_gp, M * 8, cudaMemcpyDeviceToHost, st),
+                  "proposals readback"));
+        HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+        cand.assign(prop.begin(), prop.end());
+        pick(cand, gp);
+        note_screen(a, cand, gp);
+        if (std::sqrt(gn2) < a->cfg.eps_grad) {
+            // fallback: never stop on the proposals alone
+            HY_TRY(full_screen());
+            pick(all, g);
+            note_screen(a, all, g);
+        } else if (a->cfg.judge) {
+            const double tj = now_s();
+            std::vector<double> gsave(gp);
+            HY_TRY(full_screen());
+            double tmax = 0.0;
+            int64_t targ = -1;
+            for (int64_t k = 0; k < a->K; ++k)
+                if (std::fabs(g[k]) > tmax + 1e-12 * tmax) {
+                    tmax = std::fabs(g[k]);
+                    targ = k;
+                }
+            rec->true_argmax = targ;
+            for (size_t i = 0; i < cand.size(); ++i)
+                if (cand[i] == targ) rec->true_rank = int64_t(i);
+            HY_TRY(hy_ranker_add_samples(a->ranker, a->d_feat, a->d_g, a->K, st));
+            ++a->ranked_iters;
+            if (a->refit_every > 0 && a->ranked_iters % a->refit_every == 0)
+                HY_TRY(hy_ranker_fit(a->ranker, a->epochs, 256, 1e-3f, 4321 + a->iter, nullptr, st));
+            t_judge = now_s() - tj;
+        }
+    }
+    const double t1 = now_s() - t_judge;
+    rec->grad_norm = std::sqrt(gn2);
     rec->t_screen = t1 - t0;
+    rec->t_judge = t_judge;
     if (a->K == 0 || rec->grad_norm < a->cfg.eps_grad) {
         rec->converged = 1;
         rec->energy = rec->energy_bulk = 0.0;
-        rec->t_total = now_s() - t0;
+        rec->t_total = now_s() - t0 - t_judge;
         return HY_OK;
     }
     rec->selected = sel;
-    rec->max_grad = std::fabs(g[sel]);
+    rec->max_grad = gmax;
     // 3. append and re-optimise
     const size_t j = a->ops.size();
     a->ops.push_back(sel);
@@ -383,7 +502,9 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         rec->energy_bulk_err = 0.0;
     } else {
         double e32 = 0.0, e64 = 0.0;
-        HY_TRY(bfgs(a, HY_F32, a->cfg.gtol_bulk, a->cfg.max_evals, st, &e32));
+        // float phase; 2^-22 |E| is a few float roundings of the energy
+        HY_TRY(bfgs(a, HY_F32, a->cfg.gtol_bulk, a->cfg.max_evals, st, &e32,
+                    std::ldexp(1.0, -22)));
         rec->energy_bulk = e32;
         HY_TRY(energy(a, a->theta, HY_F64, st, &e64));
         rec->energy_bulk_err = std::fabs(e32 - e64);
@@ -393,9 +514,25 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     }
     rec->n_evals = a->evals - ev0;
     rec->n_evals_f64 = a->evals64 - ev640;
-    rec->t_optimise = now_s() - t1;
-    rec->t_total = now_s() - t0;
+    rec->t_optimise = now_s() - t_judge - t1;
+    rec->t_total = now_s() - t0 - t_judge;
+    a->count[sel] += 1.0f;
     ++a->iter;
+    return HY_OK;
+}
+
+hy_status hy_adapt_set_ranker(hy_adapt *a, hy_ranker *r, int warm_iters, int epochs,
+                              int refit_every)
+{
+    if (!a || !r) return set_err(HY_ERR_ARG, "NULL argument");
+    if (a->cfg.screen_top_m <= 0)
+        return set_err(HY_ERR_ARG, "driver was created without screen_top_m");
+    if (warm_iters < 1 || epochs < 1 || refit_every < 0)
+        return set_err(HY_ERR_ARG, "warm_iters and epochs must be >= 1, refit_every >= 0");
+    a->ranker = r;
+    a->warm_iters = warm_iters;
+    a->epochs = epochs;
+    a->refit_every = refit_every;
     return HY_OK;
 }
 

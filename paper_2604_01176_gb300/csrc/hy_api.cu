@@ -4,7 +4,9 @@
 // hy_sweeps.cu; this file only marshals.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -83,6 +85,10 @@ struct hy_ham {
     DevCsr<float> Ma32, Mb32;
     double *d_V64 = nullptr;
     float *d_V32 = nullptr;
+    double *d_h1 = nullptr, *d_eri = nullptr;   // integrals (ranker features)
+    double *d_occ_partial = nullptr;            // [occ_blocks][33]
+    float *d_occ = nullptr;                     // [2n]
+    int occ_blocks = 0;
     // workspace (grown on demand; growth synchronises the device)
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -100,6 +106,29 @@ struct hy_pool {
     hy::k::ConsDev *d_cons = nullptr;
     uint32_t *d_aent = nullptr, *d_bent = nullptr;
     int64_t *d_aoff = nullptr, *d_acnt = nullptr, *d_boff = nullptr, *d_bcnt = nullptr;
+    int32_t *d_desc = nullptr;   // [K][11] operator descriptors (ranker features)
+};
+
+struct hy_batch {
+    std::vector<const hy_ham *> hams;
+    std::vector<int64_t> offsets;   // count + 1
+    std::vector<int> order;         // molecules by decreasing row cost
+    int64_t total = 0, n_tasks = 0;
+    int nb_max = 0, nn_max = 0, num_sms = 0;
+    hy_batch_tile tile{64, 4, 0};
+    hy::k::BatchMol<double> *d_mols64 = nullptr;
+    hy::k::BatchMol<float> *d_mols32 = nullptr;
+    int2 *d_tasks = nullptr;
+    int *d_counter = nullptr;
+    double *d_row_energy = nullptr;
+    int64_t *d_base = nullptr, *d_rows = nullptr;
+    // captured graph and what it was captured for
+    cudaGraphExec_t gexec = nullptr;
+    const void *g_psi = nullptr;
+    void *g_sigma = nullptr;
+    double *g_energies = nullptr;
+    int g_dt = -1;
+    hy_batch_tile g_tile{0, 0, 0};
 };
 
 namespace {
@@ -421,6 +450,15 @@ hy_status hy_build_hamiltonian(const double *h1, const double *h2, double e_core
     up(ar.upload(&h->d_binom, binom.data(), binom.size()), "upload binomials");
     up(ar.upload(&h->d_V64, h->kt.V.data(), h->kt.V.size()), "upload V");
     up(ar.upload(&h->d_V32, V32.data(), V32.size()), "upload V32");
+    up(ar.upload(&h->d_h1, h1, size_t(n_orb) * n_orb), "upload h1");
+    up(ar.upload(&h->d_eri, h2, size_t(n_orb) * n_orb * n_orb * n_orb), "upload h2");
+    h->occ_blocks = 2 * h->num_sms;
+    {
+        std::vector<double> zp(size_t(h->occ_blocks) * 33, 0.0);
+        std::vector<float> zo(size_t(2 * n_orb), 0.0f);
+        up(ar.upload(&h->d_occ_partial, zp.data(), zp.size()), "occupation partials");
+        up(ar.upload(&h->d_occ, zo.data(), zo.size()), "occupations");
+    }
     if (s == HY_OK) s = upload_csr<double>(ar, h->kt.Ma, h->Ma64);
     if (s == HY_OK) s = upload_csr<double>(ar, h->kt.Mb, h->Mb64);
     if (s == HY_OK) s = upload_csr<float>(ar, h->kt.Ma, h->Ma32);
@@ -623,6 +661,12 @@ hy_status hy_pool_create(const hy_ham *h, hy_pool_kind kind, hy_pool **out)
     up(ar.upload(&p->d_acnt, p->pa.cnt.data(), p->pa.cnt.size()), "upload counts");
     up(ar.upload(&p->d_boff, p->pb.off.data(), p->pb.off.size()), "upload offsets");
     up(ar.upload(&p->d_bcnt, p->pb.cnt.data(), p->pb.cnt.size()), "upload counts");
+    {
+        std::vector<int32_t> desc;
+        desc.reserve(p->ops.size() * 11);
+        for (const auto &op : p->ops) desc.insert(desc.end(), op.desc, op.desc + 11);
+        up(ar.upload(&p->d_desc, desc.data(), desc.size()), "upload descriptors");
+    }
     if (s != HY_OK) {
         std::string msg = g_err;
         hy_pool_destroy(p);
@@ -695,6 +739,340 @@ hy_status hy_apply_excitation(const hy_ham *hc, const hy_pool *p, int64_t k,
             s = normalize_t<float>(h, static_cast<float *>(psi), as_stream(stream));
     }
     return s;
+}
+
+hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi, hy_dtype dt,
+                             const float *extra, float *feat, void *stream)
+{
+    if (!h || !p || !psi || !feat || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
+    if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
+    cudaStream_t st = as_stream(stream);
+    if (dt == HY_F64)
+        HY_CUDA(hy::k::occupations<double>(static_cast<const double *>(psi), h->Na, h->Nb,
+                                           h->d_astr, h->d_bstr, h->n, h->d_occ_partial,
+                                           h->occ_blocks, h->d_occ, st), "occupations");
+    else
+        HY_CUDA(hy::k::occupations<float>(static_cast<const float *>(psi), h->Na, h->Nb,
+                                          h->d_astr, h->d_bstr, h->n, h->d_occ_partial,
+                                          h->occ_blocks, h->d_occ, st), "occupations");
+    HY_CUDA(hy::k::features(p->d_desc, int64_t(p->ops.size()), h->n, h->d_h1, h->d_eri,
+                            h->d_occ, extra, feat, st), "features");
+    return HY_OK;
+}
+
+hy_status hy_occupations(const hy_ham *h, const void *psi, hy_dtype dt, float *occ,
+                         void *stream)
+{
+    if (!h || !psi || !occ || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
+    cudaStream_t st = as_stream(stream);
+    if (dt == HY_F64)
+        HY_CUDA(hy::k::occupations<double>(static_cast<const double *>(psi), h->Na, h->Nb,
+                                           h->d_astr, h->d_bstr, h->n, h->d_occ_partial,
+                                           h->occ_blocks, occ, st), "occupations");
+    else
+        HY_CUDA(hy::k::occupations<float>(static_cast<const float *>(psi), h->Na, h->Nb,
+                                          h->d_astr, h->d_bstr, h->n, h->d_occ_partial,
+                                          h->occ_blocks, occ, st), "occupations");
+    return HY_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+hy::k::BatchArgs<T> batch_args(const hy_batch *b, const void *psi, void *sigma, double *row_e)
+{
+    hy::k::BatchArgs<T> a;
+    a.psi = static_cast<const T *>(psi);
+    a.sigma = static_cast<T *>(sigma);
+    if constexpr (sizeof(T) == 8) a.mols = b->d_mols64; else a.mols = b->d_mols32;
+    a.tasks = b->d_tasks;
+    a.n_tasks = int(b->n_tasks);
+    a.counter = b->d_counter;
+    a.row_energy = row_e;
+    a.gsize = b->tile.gsize;
+    a.threads = b->tile.gsize * b->tile.groups;
+    a.nb_max = b->nb_max;
+    a.nn_max = b->nn_max;
+    a.group_smem = hy::k::batch_group_smem<T>(b->nb_max, b->nn_max, b->tile.gsize);
+    return a;
+}
+
+bool tile_ok(const hy_batch *b, const hy_batch_tile &t, size_t elem)
+{
+    if (t.gsize < 32 || t.gsize > 1024 || (t.gsize & (t.gsize - 1))) return false;
+    if (t.groups < 1 || t.groups > 15 || t.gsize * t.groups > 1024) return false;
+    if (t.ctas_per_sm < 0) return false;
+    const size_t g = elem == 8 ? hy::k::batch_group_smem<double>(b->nb_max, b->nn_max, t.gsize)
+                               : hy::k::batch_group_smem<float>(b->nb_max, b->nn_max, t.gsize);
+    return g * t.groups <= 227 * 1024;
+}
+
+template <typename T>
+hy_status batch_apply_t(hy_batch *b, const void *psi, void *sigma, double *energies,
+                        cudaStream_t st)
+{
+    if (!tile_ok(b, b->tile, sizeof(T))) return fail(HY_ERR_ARG, "tile shape does not fit");
+    hy::k::BatchArgs<T> a = batch_args<T>(b, psi, sigma, energies ? b->d_row_energy : nullptr);
+    int per_sm = 0;
+    HY_CUDA(hy::k::batch_occupancy<T>(a, &per_sm), "batch occupancy");
+    if (per_sm < 1) return fail(HY_ERR_ARG, "tile shape does not fit an SM");
+    if (b->tile.ctas_per_sm > 0 && b->tile.ctas_per_sm < per_sm) per_sm = b->tile.ctas_per_sm;
+    int64_t grid = int64_t(b->num_sms) * per_sm;
+    const int64_t need = (b->n_tasks + b->tile.groups - 1) / b->tile.groups;
+    if (grid > need) grid = need > 0 ? need : 1;
+    HY_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st), "reset task counter");
+    HY_CUDA(hy::k::batch_rows<T>(a, int(grid), st), "batch rows");
+    if (energies)
+        HY_CUDA(hy::k::batch_energy(b->d_row_energy, b->d_base, b->d_rows, int(b->hams.size()),
+                                    energies, st), "batch energies");
+    return HY_OK;
+}
+
+hy_status batch_apply(hy_batch *b, const void *psi, void *sigma, hy_dtype dt, double *energies,
+                      cudaStream_t st)
+{
+    if (dt == HY_F64) return batch_apply_t<double>(b, psi, sigma, energies, st);
+    return batch_apply_t<float>(b, psi, sigma, energies, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+hy_status hy_batch_create(const hy_ham *const *hams, int count, hy_batch **out)
+{
+    if (!out) return fail(HY_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!hams || count < 1) return fail(HY_ERR_ARG, "empty batch");
+    for (int i = 0; i < count; ++i)
+        if (!hams[i]) return fail(HY_ERR_ARG, "NULL Hamiltonian in batch");
+    hy_batch *b = new (std::nothrow) hy_batch;
+    if (!b) return fail(HY_ERR_OOM, "host allocation failed");
+    b->hams.assign(hams, hams + count);
+    b->num_sms = hams[0]->num_sms;
+    std::vector<double> cost(count);
+    for (int i = 0; i < count; ++i) {
+        const hy_ham *h = hams[i];
+        const double rowc = double(h->Nb) *
+            (double(h->kt.Ma.ptr.back()) / double(h->Na) + double(h->kt.Mb.ptr.back()) / double(h->Nb) +
+             double(h->A.nex + 1) * double(h->B.nex + 1));
+        cost[i] = rowc;
+        b->order.push_back(i);
+        b->nb_max = std::max<int>(b->nb_max, int(h->Nb));
+        b->nn_max = std::max(b->nn_max, h->n * h->n);
+    }
+    std::stable_sort(b->order.begin(), b->order.end(),
+                     [&](int x, int y) { return cost[x] > cost[y]; });
+    b->offsets.assign(count + 1, 0);
+    int64_t off = 0;
+    for (int i = 0; i < count; ++i) {
+        b->offsets[i] = off;
+        off += (hams[i]->N + 31) / 32 * 32;
+    }
+    b->offsets[count] = off;
+    b->total = off;
+    std::vector<hy::k::BatchMol<double>> m64(count);
+    std::vector<hy::k::BatchMol<float>> m32(count);
+    std::vector<int64_t> base(count), rows(count);
+    int64_t tb = 0;
+    for (int i = 0; i < count; ++i) {
+        const hy_ham *h = hams[i];
+        auto fill = [&](auto &m, const auto &Ma, const auto &Mb, const auto *V) {
+            m.offset = b->offsets[i];
+            m.Na = h->Na;
+            m.Nb = h->Nb;
+            m.task_base = tb;
+            m.n = h->n;
+            m.nexa = h->A.nex;
+            m.nexb = h->B.nex;
+            m.pad = 0;
+            m.Ma_ptr = Ma.ptr; m.Ma_col = Ma.col; m.Ma_val = Ma.val;
+            m.Mb_ptr = Mb.ptr; m.Mb_col = Mb.col; m.Mb_val = Mb.val;
+            m.V = V;
+            m.aex = h->d_aex; m.bexT = h->d_bexT; m.astr = h->d_astr; m.bstr = h->d_bstr;
+        };
+        fill(m64[i], h->Ma64, h->Mb64, h->d_V64);
+        fill(m32[i], h->Ma32, h->Mb32, h->d_V32);
+        base[i] = tb;
+        rows[i] = h->Na;
+        tb += h->Na;
+    }
+    std::vector<int2> tasks;
+    for (int i : b->order)
+        for (int64_t r = 0; r < hams[i]->Na; ++r) tasks.push_back(make_int2(i, int(r)));
+    b->n_tasks = int64_t(tasks.size());
+    hy_status s = HY_OK;
+    auto up = [&](cudaError_t err, const char *what) {
+        if (s == HY_OK && err != cudaSuccess) s = cuda_fail(err, what);
+    };
+    auto put = [&](auto **dst, const auto *src, size_t cnt, const char *what) {
+        if (s != HY_OK) return;
+        up(cudaMalloc(reinterpret_cast<void **>(dst), cnt * sizeof(**dst)), what);
+        if (s == HY_OK && src)
+            up(cudaMemcpy(*dst, src, cnt * sizeof(**dst), cudaMemcpyHostToDevice), what);
+    };
+    put(&b->d_mols64, m64.data(), m64.size(), "batch tables");
+    put(&b->d_mols32, m32.data(), m32.size(), "batch tables");
+    put(&b->d_tasks, tasks.data(), tasks.size(), "batch tasks");
+    put(&b->d_counter, static_cast<const int *>(nullptr), 1, "batch counter");
+    put(&b->d_row_energy, static_cast<const double *>(nullptr), size_t(tb), "batch partials");
+    put(&b->d_base, base.data(), base.size(), "batch tables");
+    put(&b->d_rows, rows.data(), rows.size(), "batch tables");
+    if (s != HY_OK) {
+        std::string msg = g_err;
+        hy_batch_destroy(b);
+        g_err = msg;
+        return s;
+    }
+    *out = b;
+    return HY_OK;
+}
+
+hy_status hy_batch_destroy(hy_batch *b)
+{
+    if (!b) return HY_OK;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    cudaFree(b->d_mols64);
+    cudaFree(b->d_mols32);
+    cudaFree(b->d_tasks);
+    cudaFree(b->d_counter);
+    cudaFree(b->d_row_energy);
+    cudaFree(b->d_base);
+    cudaFree(b->d_rows);
+    delete b;
+    return HY_OK;
+}
+
+hy_status hy_batch_info(const hy_batch *b, int64_t *total, int64_t *n_tasks)
+{
+    if (!b) return fail(HY_ERR_ARG, "batch is NULL");
+    if (total) *total = b->total;
+    if (n_tasks) *n_tasks = b->n_tasks;
+    return HY_OK;
+}
+
+hy_status hy_batch_offsets(const hy_batch *b, int64_t *offsets)
+{
+    if (!b || !offsets) return fail(HY_ERR_ARG, "NULL argument");
+    std::memcpy(offsets, b->offsets.data(), b->offsets.size() * sizeof(int64_t));
+    return HY_OK;
+}
+
+hy_status hy_batch_set_tile(hy_batch *b, const hy_batch_tile *tile)
+{
+    if (!b || !tile) return fail(HY_ERR_ARG, "NULL argument");
+    if (!tile_ok(b, *tile, 8) && !tile_ok(b, *tile, 4)) return fail(HY_ERR_ARG, "invalid tile shape");
+    b->tile = *tile;
+    return HY_OK;
+}
+
+hy_status hy_batch_get_tile(const hy_batch *b, hy_batch_tile *tile)
+{
+    if (!b || !tile) return fail(HY_ERR_ARG, "NULL argument");
+    *tile = b->tile;
+    return HY_OK;
+}
+
+hy_status hy_batch_apply_h(hy_batch *b, const void *psi, void *sigma, hy_dtype dt,
+                           double *energies, void *stream)
+{
+    if (!b || !psi || !sigma || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
+    if (psi == sigma) return fail(HY_ERR_ARG, "psi and sigma must not alias");
+    return batch_apply(b, psi, sigma, dt, energies, as_stream(stream));
+}
+
+hy_status hy_batch_graph_launch(hy_batch *b, const void *psi, void *sigma, hy_dtype dt,
+                                double *energies, void *stream)
+{
+    if (!b || !psi || !sigma || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
+    if (psi == sigma) return fail(HY_ERR_ARG, "psi and sigma must not alias");
+    cudaStream_t st = as_stream(stream);
+    const bool same = b->gexec && b->g_psi == psi && b->g_sigma == sigma &&
+                      b->g_energies == energies && b->g_dt == int(dt) &&
+                      b->g_tile.gsize == b->tile.gsize && b->g_tile.groups == b->tile.groups &&
+                      b->g_tile.ctas_per_sm == b->tile.ctas_per_sm;
+    if (!same) {
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        cudaStream_t cap = nullptr;
+        HY_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        hy_status s = HY_OK;
+        if (e == cudaSuccess) {
+            s = batch_apply(b, psi, sigma, dt, energies, cap);
+            cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+            if (s == HY_OK && e2 != cudaSuccess) s = cuda_fail(e2, "end capture");
+        } else {
+            s = cuda_fail(e, "begin capture");
+        }
+        cudaStreamDestroy(cap);
+        if (s != HY_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        e = cudaGraphInstantiate(&b->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->gexec = nullptr;
+            return cuda_fail(e, "graph instantiate");
+        }
+        b->g_psi = psi;
+        b->g_sigma = sigma;
+        b->g_energies = energies;
+        b->g_dt = int(dt);
+        b->g_tile = b->tile;
+    }
+    HY_CUDA(cudaGraphLaunch(b->gexec, st), "graph launch");
+    return HY_OK;
+}
+
+hy_status hy_batch_tune(hy_batch *b, const void *psi, void *sigma, hy_dtype dt,
+                        hy_batch_tile *best, double *ms, void *stream)
+{
+    if (!b || !psi || !sigma || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
+    cudaStream_t st = as_stream(stream);
+    const size_t elem = dt == HY_F64 ? 8 : 4;
+    cudaEvent_t e0, e1;
+    HY_CUDA(cudaEventCreate(&e0), "event");
+    HY_CUDA(cudaEventCreate(&e1), "event");
+    const hy_batch_tile saved = b->tile;
+    hy_batch_tile win = saved;
+    double win_ms = 1e300;
+    hy_status s = HY_OK;
+    for (int gsize = 32; gsize <= 512 && s == HY_OK; gsize *= 2)
+        for (int groups = 1; groups <= 8 && s == HY_OK; groups *= 2) {
+            hy_batch_tile t{gsize, groups, 0};
+            if (!tile_ok(b, t, elem)) continue;
+            b->tile = t;
+            for (int w = 0; w < 2 && s == HY_OK; ++w) s = batch_apply(b, psi, sigma, dt, nullptr, st);
+            if (s != HY_OK) break;
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && s == HY_OK; ++r) s = batch_apply(b, psi, sigma, dt, nullptr, st);
+            cudaEventRecord(e1, st);
+            cudaError_t ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) {
+                s = cuda_fail(ce, "tuning");
+                break;
+            }
+            float t_ms = 0.0f;
+            cudaEventElapsedTime(&t_ms, e0, e1);
+            if (t_ms / 3.0 < win_ms) {
+                win_ms = t_ms / 3.0;
+                win = t;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tile = s == HY_OK ? win : saved;
+    if (s != HY_OK) return s;
+    if (best) *best = win;
+    if (ms) *ms = win_ms;
+    return HY_OK;
 }
 
 }  // extern "C"

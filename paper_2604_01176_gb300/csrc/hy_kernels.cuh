@@ -69,6 +69,49 @@ cudaError_t excite(T *psi, const uint32_t *ae, int64_t nrows, const uint32_t *be
                    int64_t ncols, int64_t Nb, double c, double s_eps,
                    cudaStream_t st);
 
+// learned ranker (hy_ranker.cu)
+constexpr int kRankerFeatures = 16;
+constexpr int kTopKMax = 8192;
+template <typename T>
+cudaError_t occupations(const T *psi, int64_t Na, int64_t Nb, const uint32_t *astr,
+                        const uint32_t *bstr, int n, double *partial, int G, float *out,
+                        cudaStream_t st);
+cudaError_t features(const int32_t *desc, int64_t K, int n, const double *h1,
+                     const double *eri, const float *occ, const float *extra, float *feat,
+                     cudaStream_t st);
+
+// batched rows over many molecules (hy_batch.cu)
+template <typename T>
+struct BatchMol {
+    int64_t offset;          // first amplitude of this molecule in the packed state
+    int64_t Na, Nb, task_base;
+    int n, nexa, nexb, pad;
+    const int32_t *Ma_ptr, *Ma_col, *Mb_ptr, *Mb_col;
+    const T *Ma_val, *Mb_val, *V;
+    const uint32_t *aex, *bexT, *astr, *bstr;
+};
+template <typename T>
+struct BatchArgs {
+    const T *psi;
+    T *sigma;
+    const BatchMol<T> *mols;
+    const int2 *tasks;       // (molecule, alpha row)
+    int n_tasks;
+    int *counter;            // zeroed before each launch
+    double *row_energy;      // per-row <psi|sigma> partials or nullptr
+    int gsize, threads;      // group size and CTA size (tile shape)
+    int nb_max, nn_max;
+    size_t group_smem;
+};
+template <typename T>
+size_t batch_group_smem(int nb_max, int nn_max, int gsize);
+template <typename T>
+cudaError_t batch_rows(const BatchArgs<T> &a, int grid, cudaStream_t st);
+template <typename T>
+cudaError_t batch_occupancy(const BatchArgs<T> &a, int *per_sm);
+cudaError_t batch_energy(const double *row_energy, const int64_t *base, const int64_t *rows,
+                         int count, double *energies, cudaStream_t st);
+
 cudaError_t rank(const uint64_t *dets, int64_t *idx, int64_t m, int n, int na,
                  int nb, int64_t Nb, const uint32_t *binom33, cudaStream_t st);
 cudaError_t unrank(const int64_t *idx, uint64_t *dets, int64_t m, int n, int na,
