@@ -342,9 +342,13 @@ hy_status hy_adapt_set_ranker(hy_adapt *a, hy_ranker *r, int warm_iters,
  * bulk = HY_F64: everything in double ("plain FP64").
  * bulk = HY_F32: state, H psi and gradients in float with float accumulation
  *   inside H psi; energies, norms and gradients reduced in double; psi is
- *   renormalised (norm in double) after every exp(theta A); after the float
- *   optimisation at most refine_steps BFGS steps run in double, and the
- *   recorded energy is always a double-precision evaluation. */
+ *   renormalised (norm in double) after every exp(theta A).  The float
+ *   optimisation stops at gtol_bulk or at the float rounding floor; every
+ *   refine_every-th iteration (and in hy_adapt_refine) it is followed by
+ *   at most refine_steps BFGS steps in double, and that iteration's
+ *   recorded energy is a double-precision evaluation with the float
+ *   energy's error beside it.  Other iterations record the float-bulk
+ *   energy (reduced in double) and energy_bulk_err = -1. */
 typedef struct {
     hy_dtype bulk;        /* HY_F64 or HY_F32                                  */
     int max_iter;         /* capacity of the ansatz (iterations)               */
@@ -353,6 +357,9 @@ typedef struct {
     double gtol_bulk;     /* HY_F32 only: float-phase tolerance                */
     int max_evals;        /* optimiser: cap on evaluations per iteration       */
     int refine_steps;     /* HY_F32 only: double-precision BFGS steps (>= 0)   */
+    int refine_every;     /* HY_F32 only: refine in double after every k-th
+                             iteration (1: every iteration; 0: only when
+                             hy_adapt_refine is called)                        */
     int screen_top_m;     /* 0: full screen; M > 0: screen only the M operators
                              a ranker proposes (hy_adapt_set_ranker)           */
     int judge;            /* with screen_top_m > 0: also run the full screen
@@ -366,9 +373,11 @@ typedef struct {
     int64_t selected;      /* pool index appended (-1 if converged)           */
     double max_grad;       /* |g| of the selected operator                    */
     double grad_norm;      /* ||g||_2 over the screened operators             */
-    double energy;         /* double-precision energy after optimisation      */
+    double energy;         /* energy after optimisation (double precision when
+                              refined, else the float-bulk energy)           */
     double energy_bulk;    /* bulk-precision energy at the bulk optimum        */
-    double energy_bulk_err;/* |energy_bulk - double energy at the same theta| */
+    double energy_bulk_err;/* |energy_bulk - double energy at the same theta|,
+                              -1 when this iteration was not refined          */
     int32_t n_evals;       /* energy+gradient evaluations (all precisions)    */
     int32_t n_evals_f64;   /* of which in double precision                    */
     int64_t true_argmax;   /* judge: argmax of the full screen (-1 if none)   */
@@ -381,7 +390,8 @@ typedef struct {
 
 /* Create a driver for (h, p); allocates its state buffers on the device.
  * cfg == NULL takes the defaults: HY_F64, max_iter 64, eps_grad 1e-5,
- * gtol 1e-9, gtol_bulk 1e-5, max_evals 200, refine_steps 4, full screen. */
+ * gtol 1e-9, gtol_bulk 1e-5, max_evals 200, refine_steps 4, refine_every 1,
+ * full screen. */
 hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p,
                           const hy_adapt_config *cfg, hy_adapt **out);
 hy_status hy_adapt_destroy(hy_adapt *a);
@@ -389,6 +399,12 @@ hy_status hy_adapt_destroy(hy_adapt *a);
 /* Run one iteration on `stream` (the host waits for its results).  *rec
  * (host) receives the record.  Returns HY_ERR_ARG when the ansatz is full. */
 hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream);
+
+/* HY_F32 drivers: refine the current ansatz in double precision (at most
+ * `steps` BFGS steps from the current parameters) and return the double
+ * energy in *e (host); the parameters are updated.  The run's final energy
+ * in the mixed mode comes from this call. */
+hy_status hy_adapt_refine(hy_adapt *a, int steps, double *e, void *stream);
 
 /* Copy the ansatz (host arrays with room for cap entries); *len gets its
  * length.  Pass cap = 0 to query the length. */

@@ -272,15 +272,15 @@ class Adapt:
 
     def __init__(self, ham: Hamiltonian, pool: Pool, precision="f64", max_iter=64,
                  eps_grad=1e-5, gtol=1e-9, gtol_bulk=1e-5, max_evals=200,
-                 refine_steps=4, screen_top_m=0, judge=False):
+                 refine_steps=4, refine_every=1, screen_top_m=0, judge=False):
         lib = _abi.load()
         self.ham, self.pool = ham, pool
         if precision not in ("f64", "mixed"):
             raise ValueError("precision must be 'f64' or 'mixed'")
         cfg = _abi.AdaptConfig(HY_F64 if precision == "f64" else HY_F32, int(max_iter),
                                float(eps_grad), float(gtol), float(gtol_bulk),
-                               int(max_evals), int(refine_steps), int(screen_top_m),
-                               1 if judge else 0)
+                               int(max_evals), int(refine_steps), int(refine_every),
+                               int(screen_top_m), 1 if judge else 0)
         handle = ctypes.c_void_p()
         check(lib.hy_adapt_create(ham.handle, pool.handle, ctypes.byref(cfg),
                                   ctypes.byref(handle)))
@@ -315,6 +315,13 @@ class Adapt:
             if r["converged"]:
                 break
         return out
+
+    def refine(self, steps=4, stream=None) -> float:
+        """Refine the current ansatz in double precision; the double energy."""
+        e = ctypes.c_double()
+        check(_abi.load().hy_adapt_refine(self._a, int(steps), ctypes.byref(e),
+                                          stream_ptr(stream)))
+        return e.value
 
     def ansatz(self):
         lib = _abi.load()

@@ -41,7 +41,8 @@ class AdaptConfig(ctypes.Structure):
     _fields_ = [("bulk", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("eps_grad", ctypes.c_double), ("gtol", ctypes.c_double),
                 ("gtol_bulk", ctypes.c_double), ("max_evals", ctypes.c_int),
-                ("refine_steps", ctypes.c_int), ("screen_top_m", ctypes.c_int),
+                ("refine_steps", ctypes.c_int), ("refine_every", ctypes.c_int),
+                ("screen_top_m", ctypes.c_int),
                 ("judge", ctypes.c_int)]
 
 
@@ -112,6 +113,7 @@ SIGNATURES = {
     "hy_adapt_destroy": (I32, [P]),
     "hy_adapt_step": (I32, [P, P, P]),
     "hy_adapt_ansatz": (I32, [P, P, P, I64, PI64]),
+    "hy_adapt_refine": (I32, [P, I32, P, P]),
     "hy_adapt_set_ansatz": (I32, [P, P, P, I64]),
     "hy_adapt_evaluate": (I32, [P, P, I32, P, P, P]),
     "hy_adapt_state": (I32, [P, P, I32, P]),

@@ -305,12 +305,13 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
         c.gtol_bulk = 1e-5;
         c.max_evals = 200;
         c.refine_steps = 4;
+        c.refine_every = 1;
         c.screen_top_m = 0;
         c.judge = 0;
     }
     if ((c.bulk != HY_F64 && c.bulk != HY_F32) || c.max_iter < 1 || c.max_iter > (1 << 20) ||
         !(c.eps_grad >= 0) || !(c.gtol > 0) || !(c.gtol_bulk > 0) || c.max_evals < 1 ||
-        c.refine_steps < 0 || c.screen_top_m < 0)
+        c.refine_steps < 0 || c.refine_every < 0 || c.screen_top_m < 0)
         return set_err(HY_ERR_ARG, "invalid hy_adapt_config");
     hy_adapt *a = new (std::nothrow) hy_adapt;
     if (!a) return set_err(HY_ERR_OOM, "host allocation failed");
@@ -506,11 +507,15 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         HY_TRY(bfgs(a, HY_F32, a->cfg.gtol_bulk, a->cfg.max_evals, st, &e32,
                     std::ldexp(1.0, -22)));
         rec->energy_bulk = e32;
-        HY_TRY(energy(a, a->theta, HY_F64, st, &e64));
-        rec->energy_bulk_err = std::fabs(e32 - e64);
-        if (a->cfg.refine_steps > 0)
-            HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.refine_steps, st, &e64));
-        rec->energy = e64;
+        rec->energy = e32;
+        rec->energy_bulk_err = -1.0;
+        if (a->cfg.refine_every > 0 && (a->iter + 1) % a->cfg.refine_every == 0) {
+            HY_TRY(energy(a, a->theta, HY_F64, st, &e64));
+            rec->energy_bulk_err = std::fabs(e32 - e64);
+            if (a->cfg.refine_steps > 0)
+                HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.refine_steps, st, &e64));
+            rec->energy = e64;
+        }
     }
     rec->n_evals = a->evals - ev0;
     rec->n_evals_f64 = a->evals64 - ev640;
@@ -533,6 +538,20 @@ hy_status hy_adapt_set_ranker(hy_adapt *a, hy_ranker *r, int warm_iters, int epo
     a->warm_iters = warm_iters;
     a->epochs = epochs;
     a->refit_every = refit_every;
+    return HY_OK;
+}
+
+hy_status hy_adapt_refine(hy_adapt *a, int steps, double *e, void *stream)
+{
+    if (!a || !e || steps < 0) return set_err(HY_ERR_ARG, "bad arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    HY_TRY(upload_ops(a, st));
+    double e64 = 0.0;
+    if (steps > 0)
+        HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, steps, st, &e64));
+    else
+        HY_TRY(energy(a, a->theta, HY_F64, st, &e64));
+    *e = e64;
     return HY_OK;
 }
 

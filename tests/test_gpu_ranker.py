@@ -156,7 +156,7 @@ def test_ranker_learns_a_ranking():
     rng = np.random.default_rng(4)
     F, m = 16, 4000
     X = rng.normal(size=(m, F)).astype(np.float32)
-    g = 10 ** (1.5 * X[:, 0] - X[:, 3] + 0.5 * X[:, 10])
+    g = 10 ** (1.5 * X[:, 0] - X[:, 3] + 0.5 * X[:, 10]).astype(np.float64)
     r = hy.Ranker(hidden=64, seed=3)
     Xd = torch.from_numpy(X).cuda()
     r.add_samples(Xd, torch.from_numpy(g).cuda())
