@@ -192,6 +192,32 @@ hy_status hy_pool_gradients(const hy_ham *h, const hy_pool *p, const void *psi,
                             int64_t n_ops, double *g_out, hy_dtype dt,
                             void *stream);
 
+/* Allocation-free variant of hy_pool_gradients (the paper has no
+ * counterpart: this is a deployment convenience).  For callers that cannot
+ * let a library allocate device memory -- e.g. a serving process whose
+ * device memory is fully reserved by another allocator, or a loop that must
+ * never pay cudaFree's implicit device-wide synchronisation -- this call
+ * computes exactly what hy_pool_gradients computes (same kernels, same
+ * arguments, same results) but keeps its partial sums in a fixed
+ * file-scope device array of 2^18 doubles (2 MiB), resident on every
+ * device that loads the library until the process exits, instead of the
+ * handle's workspace.  It calls no cudaMalloc or cudaFree.
+ *   - Limit: the call needs n_ops * max(1, ceil(4 * SMs / n_ops)) partial
+ *     sums, so n_ops may be at most 262,144; larger requests return
+ *     HY_ERR_ARG before any launch, with the limit in hy_last_error().
+ *   - The first call on each device resolves the array's device address
+ *     (cudaGetSymbolAddress) once; make that first call before any stream
+ *     capture.
+ *   - Every call on a device shares the one array: calls whose launches may
+ *     overlap on the GPU (different streams, or threads without ordering)
+ *     race and give wrong results; serialise them.  Each call overwrites
+ *     every partial it later reads, so nothing needs clearing between
+ *     calls. */
+hy_status hy_pool_gradients_noalloc(const hy_ham *h, const hy_pool *p,
+                                    const void *psi, const void *sigma,
+                                    const int32_t *ops_or_null, int64_t n_ops,
+                                    double *g_out, hy_dtype dt, void *stream);
+
 /* psi <- exp(theta A_k) psi in place: for each constituent C (sign s on the
  * pair d -> C d) and each connected pair, psi(d) <- cos psi(d) - s sin
  * psi(Cd), psi(Cd) <- cos psi(Cd) + s sin psi(d).  With renormalize != 0

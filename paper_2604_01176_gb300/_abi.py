@@ -88,6 +88,7 @@ SIGNATURES = {
     "hy_pool_describe": (I32, [P, I64, P]),
     "hy_pool_gradients": (I32, [P, P, P, P, P, I64, P, I32, P]),
     "hy_apply_excitation": (I32, [P, P, I64, D, P, I32, I32, P]),
+    "hy_pool_gradients_noalloc": (I32, [P, P, P, P, P, I64, P, I32, P]),
     "hy_batch_create": (I32, [P, I32, PP]),
     "hy_batch_destroy": (I32, [P]),
     "hy_batch_info": (I32, [P, PI64, PI64]),

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -717,6 +718,106 @@ hy_status hy_pool_gradients(const hy_ham *hc, const hy_pool *p, const void *psi,
     return grad_t<float>(h, p, static_cast<const float *>(psi),
                          static_cast<const float *>(sigma), ops_or_null, n_ops, g_out,
                          as_stream(stream));
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free gradient screen.  Some callers cannot let a library call
+// cudaMalloc / cudaFree: a serving loop whose device memory is entirely
+// reserved by another allocator, or one that must never hit the implicit
+// device-wide synchronisation of cudaFree or the latency of a first-use
+// allocation.  hy_pool_gradients_noalloc gives them the screen with its
+// per-(operator, row-chunk) partial sums in a fixed, file-scope device array
+// instead of the handle's cudaMalloc'd workspace.  The array is
+// kNoAllocPartials doubles (2 MiB) and stays resident on every device that
+// loads the library until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocPartials = int64_t(1) << 18;
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_partials on the current device (the host-side
+// name is only a stand-in, not a device address).  Resolved once per device.
+hy_status noalloc_scratch(double **out)
+{
+    int dev = 0;
+    HY_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(HY_ERR_UNSUPPORTED, "device ordinal beyond the no-alloc table");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+        if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_ptr[dev] = static_cast<double *>(ptr);
+    }
+    *out = g_noalloc_ptr[dev];
+    return HY_OK;
+}
+
+template <typename T>
+hy_status grad_noalloc_t(hy_ham *h, const hy_pool *p, const T *psi, const T *sigma,
+                         const int32_t *ops, int64_t n_ops, double *g, double *scratch,
+                         cudaStream_t st)
+{
+    hy::k::GradArgs<T> a;
+    a.psi = psi;
+    a.sigma = sigma;
+    a.ops = ops;
+    a.n_ops = n_ops;
+    a.opd = p->d_op;
+    a.cons = p->d_cons;
+    a.aent = p->d_aent;
+    a.aoff = p->d_aoff;
+    a.acnt = p->d_acnt;
+    a.bent = p->d_bent;
+    a.boff = p->d_boff;
+    a.bcnt = p->d_bcnt;
+    a.Na = h->Na;
+    a.Nb = h->Nb;
+    a.CH = grad_chunks(h, n_ops);
+    a.partials = scratch;
+    a.g = g;
+    HY_CUDA(hy::k::grad<T>(a, st), "pool gradients (no-alloc)");
+    return HY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hy_status hy_pool_gradients_noalloc(const hy_ham *hc, const hy_pool *p, const void *psi,
+                                    const void *sigma, const int32_t *ops_or_null,
+                                    int64_t n_ops, double *g_out, hy_dtype dt, void *stream)
+{
+    hy_ham *h = const_cast<hy_ham *>(hc);
+    if (!h || !p || !psi || !sigma || !g_out || !valid_dtype(dt))
+        return fail(HY_ERR_ARG, "bad arguments");
+    if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
+    if (!ops_or_null) n_ops = int64_t(p->ops.size());
+    if (n_ops < 0) return fail(HY_ERR_ARG, "n_ops out of range");
+    // every launch uses n_ops * chunks <= n_ops + 4 * SMs partial sums
+    const int64_t need = n_ops * int64_t(grad_chunks(h, n_ops));
+    if (need > kNoAllocPartials)
+        return fail(HY_ERR_ARG, "n_ops = " + std::to_string(n_ops) +
+                                    " needs more partial sums than the no-alloc scratch holds (" +
+                                    std::to_string(kNoAllocPartials) + "); use hy_pool_gradients");
+    double *scratch = nullptr;
+    hy_status s = noalloc_scratch(&scratch);
+    if (s != HY_OK) return s;
+    if (dt == HY_F64)
+        return grad_noalloc_t<double>(h, p, static_cast<const double *>(psi),
+                                      static_cast<const double *>(sigma), ops_or_null, n_ops,
+                                      g_out, scratch, as_stream(stream));
+    return grad_noalloc_t<float>(h, p, static_cast<const float *>(psi),
+                                 static_cast<const float *>(sigma), ops_or_null, n_ops, g_out,
+                                 scratch, as_stream(stream));
 }
 
 hy_status hy_apply_excitation(const hy_ham *hc, const hy_pool *p, int64_t k,
