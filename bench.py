@@ -2,19 +2,27 @@
 """Benchmark of the state-vector ADAPT-VQE hot path on one GB300 (or N
 independent replicas under torchrun).
 
-One step = one ADAPT iteration sweep at 32 qubits (16 orbitals, 8 alpha + 8
-beta electrons, 165,636,900 determinants, seeded synthetic integrals):
-  1. state preparation psi = prod_i exp(theta_i A_{k_i}) |HF> over the current
-     ansatz (10 operators),
-  2. sigma = H psi,
-  3. E = <psi|sigma>,
-  4. the full pool-gradient screen g_k = 2 <sigma|A_k psi> (2,928 operators),
-  5. selection argmax |g_k| on the host (device -> host copy of g and E).
-`value` is the number of such iterations per second over all ranks with the
-state resident in HBM.  `e2e` repeats the step through the same C-ABI calls
-starting from a host (pinned) reference state copied in every step.
+Workload: 32 qubits -- 16 orbitals, 8 alpha + 8 beta electrons, 165,636,900
+determinants, seeded synthetic integrals shaped like the H16 STO-3G chain,
+the spin-adapted singles+doubles pool (3,376 operators).
 
-Every step runs only in the library's kernels (libhyperion.so); the FP64 CPU
+One step = one ADAPT-VQE iteration of the mixed-precision driver with the
+learned ranker: screen (ranker features -> MLP -> top-32 proposals screened
+exactly in float), select, append, re-optimise every parameter with BFGS
+(each evaluation: state preparation by exp(theta A) with double-precision
+renormalisation, H psi, energy and adjoint gradient, bulk in float,
+reductions in double).  The first `warmup` iterations run the full screen
+and train the ranker; the next `steps` are timed.  `value` = timed ADAPT
+iterations per second over all ranks.
+
+Also reported: H|psi> time, algorithmic GB/s and HBM fraction in FP64 and
+FP32; one plain FP64 full-screen iteration timed from the same ansatz
+("plain vs mixed+ranker"); the double-precision refinement of the final
+energy and its gap to the float bulk; the ranker's rank of the true argmax
+at the final state.  `e2e` repeats the step through the public API with the
+ansatz restored from host memory every step (a stateless-serving step).
+
+Every sweep runs in the library's kernels (libhyperion.so); the FP64 CPU
 oracle is timed on a bounded sample for `cpu_baseline` and for the
 `--impl reference` arm.
 """
@@ -39,17 +47,17 @@ import synth  # noqa: E402
 
 METRIC = ("H|psi> GB/s (% of ~8 TB/s) and ADAPT iters/s at 32 qubits, "
           "plain vs mixed+ranker")
-ANSATZ_LEN = 10
+TOP_M = 32
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="h16_32q")
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 iteration")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of oracle work per CPU sample")
@@ -60,15 +68,12 @@ def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
-            d = json.load(f)
-        return d, "measured"
+            return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# ---------------------------------------------------------------------------
-# clocks sampled during the timed region
-# ---------------------------------------------------------------------------
 class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -111,10 +116,12 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # oracle timing on the host cores (bounded samples of the same workload)
 # ---------------------------------------------------------------------------
-def oracle_step_estimate(n, na, nb, seed, budget_s, ansatz_len, state=None):
-    """Seconds the FP64 CPU oracle would take for one full step, extrapolated
-    from a bounded sample: sigma on sampled rows, the gradient of a few pool
-    operators, and one exp(theta A).  Returns (seconds, threads, sample)."""
+def oracle_iteration_estimate(n, na, nb, seed, budget_s, ansatz_len, n_evals, state=None):
+    """Seconds the FP64 CPU oracle would take for one plain ADAPT iteration
+    with `n_evals` energy+gradient evaluations at ansatz length `ansatz_len`,
+    extrapolated from a bounded sample: sigma on sampled rows, the gradient
+    of a few pool operators (each O(N_det)), and one exp(theta A).
+    Returns (seconds, threads, sample description)."""
     import oracle
     h1, h2, ec = synth.integrals(n, seed)
     ref = oracle.System(h1, h2, ec, n, na, nb)
@@ -122,7 +129,6 @@ def oracle_step_estimate(n, na, nb, seed, budget_s, ansatz_len, state=None):
     if state is None:
         state = synth.random_state(ref.n_det, 99)
     rng = np.random.default_rng(1)
-    # sigma rows: calibrate on a small batch, then fill ~half the budget
     rows = rng.integers(0, ref.n_det, 64 * threads)
     t0 = time.perf_counter()
     ref.sigma_rows(state, rows, threads)
@@ -133,28 +139,55 @@ def oracle_step_estimate(n, na, nb, seed, budget_s, ansatz_len, state=None):
     ref.sigma_rows(state, rows, threads)
     t_rows = time.perf_counter() - t0
     t_sigma = t_rows * ref.n_det / m
-    # gradients: a few operators, one per thread (each O(N_det))
     pool = ref.pool()
     nops = max(1, min(threads, 4))
-    sig_stub = state  # arithmetic cost does not depend on the values
     t0 = time.perf_counter()
-    ref.gradients(pool[:nops], state, sig_stub, nops)
+    ref.gradients(pool[:nops], state, state, nops)
     t_g = time.perf_counter() - t0
-    t_screen = t_g * len(pool) / nops
-    # one exp(theta A) (single thread, O(N_det))
+    t_op = t_g / nops            # one operator's gradient, one thread
     t0 = time.perf_counter()
     ref.apply_excitation(pool[len(pool) - 1], 0.1, state)
     t_x = time.perf_counter() - t0
-    total = t_sigma + t_sigma / 10 + t_screen + ansatz_len * t_x
-    sample = (f"sigma on {m} sampled rows ({t_rows:.1f} s), gradients of {nops} ops "
-              f"({t_g:.1f} s), one exp(theta A) ({t_x:.1f} s); extrapolated to "
-              f"{ref.n_det} rows, {len(pool)} ops, {ansatz_len} exps")
+    # screen (all operators, parallel over threads) + per evaluation: prepare
+    # (j exps), sigma, energy, adjoint gradient (2j exps + j generator dots)
+    t_screen = t_op * len(pool) / threads
+    t_eval = t_sigma + ansatz_len * t_x + 2 * ansatz_len * t_x + ansatz_len * t_op
+    total = t_screen + n_evals * t_eval
+    sample = (f"sigma on {m} sampled rows ({t_rows:.1f} s, {threads} threads), gradients of "
+              f"{nops} ops ({t_g:.1f} s), one exp(theta A) ({t_x:.1f} s); extrapolated to one "
+              f"plain ADAPT iteration: full screen of {len(pool)} ops + {n_evals} evaluations "
+              f"at ansatz length {ansatz_len} over {ref.n_det} determinants")
     return total, threads, sample
 
 
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+def time_sweeps(ham, pool, dt, reps=3):
+    """Mean device time (ms) of H psi and of the full screen in dtype dt."""
+    import torch
+    g = torch.Generator(device=ham.device)
+    g.manual_seed(5)
+    psi = torch.randn(ham.n_det, dtype=dt, device=ham.device, generator=g)
+    psi /= psi.norm()
+    sig = torch.empty_like(psi)
+    gr = torch.empty(len(pool), dtype=torch.float64, device=ham.device)
+    st = torch.cuda.current_stream()
+    ham.apply_h(psi, out=sig)
+    pool.gradients(psi, sig, out=gr)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record(st)
+    for _ in range(reps):
+        ham.apply_h(psi, out=sig)
+    e[1].record(st)
+    for _ in range(reps):
+        pool.gradients(psi, sig, out=gr)
+    e[2].record(st)
+    torch.cuda.synchronize()
+    return e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2604_01176_gb300 as hy
@@ -169,45 +202,19 @@ def run_ours(args, rank, world):
     ham = hy.Hamiltonian(h1, h2, ec, n, na, nb)
     pool = hy.Pool(ham)
     t_build = time.perf_counter() - tb
-    dt = torch.float64 if args.precision == "f64" else torch.float32
-    s_elem = 8 if dt == torch.float64 else 4
     N, K = ham.n_det, len(pool)
-    rng = np.random.default_rng(seed + 17 * rank)
-    ansatz = [(int(k), float(t)) for k, t in zip(rng.integers(0, K, ANSATZ_LEN),
-                                                 rng.normal(0, 0.1, ANSATZ_LEN))]
-    hf = ham.hf_state(dt)
-    psi = torch.empty_like(hf)
-    sigma = torch.empty_like(hf)
-    g = torch.empty(K, dtype=torch.float64, device=dev)
-    e = torch.empty((), dtype=torch.float64, device=dev)
-    g_host = torch.empty(K, dtype=torch.float64).pin_memory()
-    e_host = torch.empty((), dtype=torch.float64).pin_memory()
-    hf_host = hf.cpu().pin_memory()
+    W, S = args.warmup, args.steps
+    out = dict(N=N, K=K, n=n, na=na, nb=nb, seed=seed, t_build=t_build,
+               conn=ham.connections_per_det())
+    out["hpsi_ms_f64"], out["screen_ms_f64"] = time_sweeps(ham, pool, torch.float64)
+    out["hpsi_ms_f32"], out["screen_ms_f32"] = time_sweeps(ham, pool, torch.float32)
+
+    # mixed precision + learned ranker
+    cap = W + 2 * S + 4
+    ranker = hy.Ranker(hidden=256, seed=7 + rank)
+    ad = hy.Adapt(ham, pool, "mixed", max_iter=cap, screen_top_m=TOP_M, refine_every=0)
+    ad.set_ranker(ranker, warm_iters=W, epochs=30)
     stream = torch.cuda.current_stream()
-    ev_h = []
-
-    def step(timed=False, from_host=False):
-        if from_host:
-            psi.copy_(hf_host, non_blocking=True)
-        else:
-            psi.copy_(hf)
-        for k, t in ansatz:
-            pool.apply_excitation(k, t, psi)
-        if timed:
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-        ham.apply_h(psi, out=sigma)
-        if timed:
-            b.record(stream)
-            ev_h.append((a, b))
-        ham.energy(psi, sigma, out=e)
-        pool.gradients(psi, sigma, out=g)
-        g_host.copy_(g, non_blocking=True)
-        e_host.copy_(e, non_blocking=True)
-        stream.synchronize()
-        return int(np.argmax(np.abs(g_host.numpy()))), float(e_host.item())
-
-    launches_per_step = sum(pool.n_kernels(k) for k, _ in ansatz) + 5 + 2 + 2
 
     def barrier():
         torch.cuda.synchronize()
@@ -215,38 +222,68 @@ def run_ours(args, rank, world):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        step()
+    warm = [ad.step() for _ in range(W)]
     clocks = Clocks(dev.index)
     barrier()
     clocks.start()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
+    l0 = hy.launch_count()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    for _ in range(args.steps):
-        sel, energy = step(timed=True)
+    timed = [ad.step() for _ in range(S)]
     t1.record(stream)
     barrier()
+    launches = hy.launch_count() - l0
     ms = t0.elapsed_time(t1)
-    hpsi_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_h)
-    # end to end: host reference state in, gradients and energy out
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    # end to end: each step restores the ansatz from host memory, runs the
+    # iteration through the public API and reads the ansatz back
+    io0 = ad.io_bytes()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        step(from_host=True)
+    for _ in range(S):
+        ops, th = ad.ansatz()
+        ad.set_ansatz(ops, th)
+        ad.step()
+        ad.ansatz()
     e1.record(stream)
     barrier()
     clk = clocks.stop()
+    io1 = ad.io_bytes()
     ms_e2e = e0.elapsed_time(e1)
+    ops, th = ad.ansatz()
+    # ranker quality at the final state: rank of the true argmax
+    e_bulk, _ = ad.evaluate(th, torch.float32)
+    psi32 = ad.state(torch.float32)
+    sig32 = ham.apply_h(psi32)
+    gfull = pool.gradients(psi32, sig32)
+    feat = hy.ranker_features(ham, pool, psi32)
+    prop = hy.topk(ranker.predict(feat), TOP_M).cpu().numpy()
+    true_k = int(torch.argmax(gfull.abs()).item())
+    true_rank = int(np.nonzero(prop == true_k)[0][0]) if true_k in prop else -1
+    del psi32, sig32
+    # final energy in double precision (refinement) and its float gap
+    e_final = ad.refine(steps=4)
+    out.update(ms=ms, ms_e2e=ms_e2e, launches=launches, clocks=clk,
+               io=((io1[0] - io0[0]) / S, (io1[1] - io0[1]) / S),
+               timed=timed, warm=warm, e_final=e_final, e_bulk=e_bulk,
+               true_rank=true_rank, ansatz_len=len(ops))
+    # plain FP64 full-screen iteration from the same (refined) ansatz
+    if not args.no_plain:
+        ops, th = ad.ansatz()
+        del ad
+        plain = hy.Adapt(ham, pool, "f64", max_iter=len(ops) + 2)
+        plain.set_ansatz(ops, th)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        p0.record(stream)
+        prec = plain.step()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        out.update(plain_ms=p0.elapsed_time(p1), plain_rec=prec)
     if world > 1:
-        t = torch.tensor([ms, ms_e2e, hpsi_ms], dtype=torch.float64, device=dev)
+        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, ms_e2e, hpsi_ms = t.tolist()
-    return dict(ham=ham, N=N, K=K, n=n, ms=ms, ms_e2e=ms_e2e, hpsi_ms=hpsi_ms,
-                s_elem=s_elem, sel=sel, energy=energy, clocks=clk, t_build=t_build,
-                launches=launches_per_step * args.steps, seed=seed, na=na, nb=nb)
+        out["ms"], out["ms_e2e"] = t.tolist()
+    return out
 
 
 def main():
@@ -265,63 +302,77 @@ def main():
             torch.distributed.destroy_process_group()
         return
     peaks, peak_kind = load_peaks()
-    N, s = r["N"], r["s_elem"]
-    steps = args.steps
-    value = world * steps / (r["ms"] / 1e3)
-    e2e = world * steps / (r["ms_e2e"] / 1e3)
-    hpsi_bytes = 2.0 * N * s
-    hpsi_gbs = hpsi_bytes / (r["hpsi_ms"] / 1e3) / 1e9
-    # H psi contributions (FMAs) per determinant, see DESIGN: alpha and beta
-    # same-spin rows plus the alpha-beta coupling
-    conn = r["ham"].connections_per_det()
-    flops = 2.0 * conn * N
-    if s == 8:
-        fp_peak = 152 * 2 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    else:
-        fp_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    achieved = flops / (r["hpsi_ms"] / 1e3) / 1e12
+    N, S = r["N"], args.steps
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    fp64_peak = 152 * 2 * 2 * mhz * 1e6 / 1e12
+    flops = 2.0 * r["conn"] * N
+
+    def hp(ms, s):
+        gbs = 2.0 * N * s / (ms / 1e3) / 1e9
+        return {"ms": round(ms, 3), "gbs": round(gbs, 3),
+                "hbm_frac": round(gbs / peaks["hbm_gbs"], 6),
+                "tflops": round(flops / (ms / 1e3) / 1e12, 4)}
+
+    timed = r["timed"]
     out = {
         "metric": METRIC,
-        "value": round(value, 6),
+        "value": round(world * S / (r["ms"] / 1e3), 6),
         "unit": "ADAPT iters/s",
         "n_gpus": world,
-        "steps": steps,
+        "steps": S,
         "warmup": args.warmup,
-        "ms_per_step": round(r["ms"] / steps, 3),
+        "ms_per_step": round(r["ms"] / S, 3),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if s == 8 else "f32",
+        "dtype": "f32 bulk + f64 reductions",
         "data": "synthetic (seeded integrals shaped like the H16 STO-3G chain; no PySCF)",
         "config": {"workload": f"{args.workload}: {r['n']} orbitals, {r['na']}a+{r['nb']}b, "
                                f"{N} determinants, seed {r['seed']}",
-                   "precision": args.precision, "ansatz_ops": ANSATZ_LEN,
+                   "mode": "mixed precision + learned ranker (top-32 screened exactly)",
                    "pool_ops": r["K"], "replicas": world,
-                   "l2": "inputs larger than L2 (state vector 1.3 GB FP64)",
-                   "step": "prepare(10 exp) + H|psi> + E + full screen + host argmax"},
-        "hpsi": {"ms": round(r["hpsi_ms"], 3), "gbs": round(hpsi_gbs, 3),
-                 "hbm_frac": round(hpsi_gbs / peaks["hbm_gbs"], 6),
-                 "algorithmic_bytes": hpsi_bytes, "connections_per_det": conn},
-        "roofline": {"bound": "alu", "achieved": round(achieved, 4),
-                     "peak": round(fp_peak, 3), "unit": "TFLOP/s",
-                     "frac": round(achieved / fp_peak, 4), "traffic": None,
-                     "kernel": "hy_apply_h (all its launches)",
-                     "peak_kind": ("derived FP64 FMA rate: 152 SMs x 2 FMA/clk x "
-                                   if s == 8 else
-                                   "derived FP32 FMA rate: 152 SMs x 128 FMA/clk x ")
-                                  + f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} clock)"},
-        "e2e": {"value": round(e2e, 6), "unit": "ADAPT iters/s",
-                "h2d_bytes_per_step": N * s, "d2h_bytes_per_step": (r["K"] + 1) * 8},
-        "gpu_launches": r["launches"],
+                   "ansatz_len_timed": [rec["iter"] + 1 for rec in timed],
+                   "l2": "inputs larger than L2 (state vector 0.66 GB FP32 / 1.33 GB FP64)",
+                   "step": "one ADAPT iteration: ranked screen + select + BFGS re-optimisation"},
+        "hpsi": {"f64": hp(r["hpsi_ms_f64"], 8), "f32": hp(r["hpsi_ms_f32"], 4),
+                 "algorithmic_bytes": "2 * N_det * sizeof(amplitude)",
+                 "connections_per_det": r["conn"]},
+        "screen_ms": {"f64": round(r["screen_ms_f64"], 3), "f32": round(r["screen_ms_f32"], 3)},
+        "roofline": {"bound": "alu", "achieved": round(flops / (r["hpsi_ms_f32"] / 1e3) / 1e12, 4),
+                     "peak": round(fp32_peak, 3), "unit": "TFLOP/s",
+                     "frac": round(flops / (r["hpsi_ms_f32"] / 1e3) / 1e12 / fp32_peak, 4),
+                     "traffic": None, "kernel": "hy_apply_h FP32 (k_coupling dominant)",
+                     "peak_kind": f"derived FP32 FMA rate: 152 SMs x 128 FMA/clk x {mhz} MHz",
+                     "f64": {"achieved": round(flops / (r["hpsi_ms_f64"] / 1e3) / 1e12, 4),
+                             "peak": round(fp64_peak, 3),
+                             "frac": round(flops / (r["hpsi_ms_f64"] / 1e3) / 1e12 / fp64_peak, 4),
+                             "peak_kind": f"derived FP64 rate: 152 SMs x 2 FMA/clk x {mhz} MHz"}},
+        "mixed": {"n_evals": [rec["n_evals"] for rec in timed],
+                  "energy_bulk": [rec["energy"] for rec in timed],
+                  "t_screen_s": [round(rec["t_screen"], 4) for rec in timed],
+                  "final_energy_f64": r["e_final"],
+                  "final_bulk_minus_f64": r["e_bulk"] - r["e_final"],
+                  "ranker_true_argmax_rank": r["true_rank"]},
+        "e2e": {"value": round(world * S / (r["ms_e2e"] / 1e3), 6), "unit": "ADAPT iters/s",
+                "h2d_bytes_per_step": int(r["io"][0]), "d2h_bytes_per_step": int(r["io"][1])},
+        "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
-        "energy": r["energy"],
         "build_s": round(r["t_build"], 2),
     }
+    if "plain_ms" in r:
+        pr = r["plain_rec"]
+        out["plain"] = {"iters_per_s": round(1e3 / r["plain_ms"], 6), "ms": round(r["plain_ms"], 1),
+                        "n_evals": pr["n_evals"], "ansatz_len": pr["iter"] + 1,
+                        "energy": pr["energy"],
+                        "speedup_mixed_ranker": round(r["plain_ms"] / (r["ms"] / S), 3)}
     if not args.no_cpu_baseline and world == 1:
-        n, na, nb = r["n"], r["na"], r["nb"]
+        n_evals = r["plain_rec"]["n_evals"] if "plain_rec" in r else 10
+        jlen = r["ansatz_len"]
+        n, na, nb, seed = r["n"], r["na"], r["nb"], r["seed"]
         del r
-        tot, thr, sample = oracle_step_estimate(n, na, nb, synth.workload(args.workload)[3],
-                                                args.cpu_budget, ANSATZ_LEN)
+        tot, thr, sample = oracle_iteration_estimate(n, na, nb, seed, args.cpu_budget, jlen,
+                                                     n_evals)
         out["cpu_baseline"] = {"value": 1.0 / tot, "unit": "ADAPT iters/s", "cores": thr,
                                "kind": "oracle", "sample": sample}
     print(json.dumps(out), flush=True)
@@ -332,20 +383,22 @@ def main():
 
 def run_reference(args, rank, world):
     """The oracle as it stands, timed on the host cores: every step is a
-    bounded sample of the same workload extrapolated to a full step."""
+    bounded sample of the same workload extrapolated to one plain ADAPT
+    iteration (10 evaluations at ansatz length warmup + steps)."""
     if rank != 0:
         return
-    n, na, nb, seed = synth.workload(args.workload)
     import oracle
+    n, na, nb, seed = synth.workload(args.workload)
     h1, h2, ec = synth.integrals(n, seed)
     n_det = oracle.System(h1, h2, ec, n, na, nb).n_det
     state = synth.random_state(n_det, 99)
     per = max(2.0, min(args.cpu_budget, 150.0 / max(1, args.steps + args.warmup)))
+    jlen = args.warmup + args.steps
     for _ in range(args.warmup):
-        oracle_step_estimate(n, na, nb, seed, per, ANSATZ_LEN, state)
+        oracle_iteration_estimate(n, na, nb, seed, per, jlen, 10, state)
     tots = []
     for _ in range(args.steps):
-        tot, thr, sample = oracle_step_estimate(n, na, nb, seed, per, ANSATZ_LEN, state)
+        tot, thr, sample = oracle_iteration_estimate(n, na, nb, seed, per, jlen, 10, state)
         tots.append(tot)
     t = sum(tots)
     v = args.steps / t
@@ -355,7 +408,7 @@ def run_reference(args, rank, world):
            "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": f"{args.workload}: {n} orbitals, {na}a+{nb}b, "
                                   f"{n_det} determinants, seed {seed}",
-                      "precision": "f64", "ansatz_ops": ANSATZ_LEN},
+                      "mode": "FP64 CPU oracle, plain full screen"},
            "cpu_baseline": {"value": v, "unit": "ADAPT iters/s", "cores": thr,
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "ADAPT iters/s", "h2d_bytes_per_step": 0,

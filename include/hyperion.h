@@ -74,6 +74,10 @@ const char *hy_last_error(void);
 /* Library version string. */
 const char *hy_version(void);
 
+/* Number of kernels this library has launched in this process (including
+ * the kernels of each CUDA-graph replay it issues). */
+int64_t hy_launch_count(void);
+
 /* ---------------------------------------------------------------------- */
 /* Hamiltonian                                                              */
 /* ---------------------------------------------------------------------- */
@@ -445,6 +449,11 @@ hy_status hy_adapt_set_ansatz(hy_adapt *a, const int64_t *ops,
  * = ansatz length) in `dt`; *e and grad (host, len doubles) are outputs. */
 hy_status hy_adapt_evaluate(hy_adapt *a, const double *thetas, hy_dtype dt,
                             double *e, double *grad, void *stream);
+
+/* Bytes the driver has copied host -> device (*h2d) and device -> host
+ * (*d2h) since it was created: operator lists, extra ranker features, HF
+ * amplitudes, energy / gradient / screen readbacks.  Either may be NULL. */
+hy_status hy_adapt_io_bytes(const hy_adapt *a, int64_t *h2d, int64_t *d2h);
 
 /* Copy the driver's current state (after the last evaluation) into psi
  * (device, n_det elements of dt). */

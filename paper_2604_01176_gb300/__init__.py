@@ -27,6 +27,11 @@ __all__ = ["Hamiltonian", "Pool", "Adapt", "Ranker", "Batch", "HyError", "dtype_
 N_FEATURES = 16
 
 
+def launch_count() -> int:
+    """Kernels the library has launched so far in this process."""
+    return int(_abi.load().hy_launch_count())
+
+
 def dtype_code(t: torch.dtype) -> int:
     if t == torch.float64:
         return HY_F64
@@ -315,6 +320,12 @@ class Adapt:
             if r["converged"]:
                 break
         return out
+
+    def io_bytes(self):
+        """(host->device, device->host) bytes the driver has copied so far."""
+        h, d = ctypes.c_int64(), ctypes.c_int64()
+        check(_abi.load().hy_adapt_io_bytes(self._a, ctypes.byref(h), ctypes.byref(d)))
+        return h.value, d.value
 
     def refine(self, steps=4, stream=None) -> float:
         """Refine the current ansatz in double precision; the double energy."""

@@ -71,6 +71,7 @@ PI64 = ctypes.POINTER(ctypes.c_int64)
 SIGNATURES = {
     "hy_last_error": (ctypes.c_char_p, []),
     "hy_version": (ctypes.c_char_p, []),
+    "hy_launch_count": (I64, []),
     "hy_build_hamiltonian": (I32, [P, P, D, I32, I32, I32, D, PP]),
     "hy_ham_destroy": (I32, [P]),
     "hy_ham_info": (I32, [P, PI64, PI64, PI64, PI64, PI64]),
@@ -115,6 +116,7 @@ SIGNATURES = {
     "hy_adapt_step": (I32, [P, P, P]),
     "hy_adapt_ansatz": (I32, [P, P, P, I64, PI64]),
     "hy_adapt_refine": (I32, [P, I32, P, P]),
+    "hy_adapt_io_bytes": (I32, [P, PI64, PI64]),
     "hy_adapt_set_ansatz": (I32, [P, P, P, I64]),
     "hy_adapt_evaluate": (I32, [P, P, I32, P, P, P]),
     "hy_adapt_state": (I32, [P, P, I32, P]),

@@ -61,6 +61,7 @@ struct hy_adapt {
     std::vector<double> valid_theta;
     int evals = 0, evals64 = 0;
     int iter = 0;
+    int64_t h2d = 0, d2h = 0;     // bytes copied host <-> device so far
 };
 
 namespace {
@@ -81,6 +82,15 @@ hy_status cu(cudaError_t e, const char *what)
 
 int di(hy_dtype dt) { return dt == HY_F64 ? 0 : 1; }
 
+// host <-> device copy on the driver's stream, counted in a->h2d / a->d2h
+hy_status xfer(hy_adapt *a, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind,
+               cudaStream_t st, const char *what)
+{
+    if (kind == cudaMemcpyHostToDevice) a->h2d += int64_t(bytes);
+    if (kind == cudaMemcpyDeviceToHost) a->d2h += int64_t(bytes);
+    return cu(cudaMemcpyAsync(dst, src, bytes, kind, st), what);
+}
+
 // psi <- HF determinant (index 0: lowest orbitals of both spins occupied)
 hy_status set_hf(hy_adapt *a, void *psi, hy_dtype dt, cudaStream_t st)
 {
@@ -89,8 +99,7 @@ hy_status set_hf(hy_adapt *a, void *psi, hy_dtype dt, cudaStream_t st)
     HY_TRY(cu(cudaMemsetAsync(psi, 0, size_t(a->N) * esize(dt), st), "memset"));
     const void *src = dt == HY_F64 ? static_cast<const void *>(&one64)
                                    : static_cast<const void *>(&one32);
-    return cu(cudaMemcpyAsync(psi, src, esize(dt), cudaMemcpyHostToDevice, st),
-              "set HF amplitude");
+    return xfer(a, psi, src, esize(dt), cudaMemcpyHostToDevice, st, "set HF amplitude");
 }
 
 // psi = U(theta) |HF>, sigma = H psi, returns E = <psi|sigma>
@@ -104,8 +113,7 @@ hy_status energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
         HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], th[l], psi, dt, renorm, st));
     HY_TRY(hy_apply_h(a->h, psi, sigma, dt, st));
     HY_TRY(hy_energy(a->h, psi, sigma, dt, a->d_e, st));
-    HY_TRY(cu(cudaMemcpyAsync(e, a->d_e, sizeof(double), cudaMemcpyDeviceToHost, st),
-              "energy readback"));
+    HY_TRY(xfer(a, e, a->d_e, sizeof(double), cudaMemcpyDeviceToHost, st, "energy readback"));
     HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
     ++a->evals;
     if (dt == HY_F64) ++a->evals64;
@@ -131,8 +139,8 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
         HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], -th[l], phi, dt, 0, st));
         HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], -th[l], lam, dt, 0, st));
     }
-    HY_TRY(cu(cudaMemcpyAsync(g.data(), a->d_ga, j * sizeof(double), cudaMemcpyDeviceToHost, st),
-              "gradient readback"));
+    HY_TRY(xfer(a, g.data(), a->d_ga, j * sizeof(double), cudaMemcpyDeviceToHost, st,
+                "gradient readback"));
     return cu(cudaStreamSynchronize(st), "sync");
 }
 
@@ -140,8 +148,8 @@ hy_status upload_ops(hy_adapt *a, cudaStream_t st)
 {
     std::vector<int32_t> o(a->ops.begin(), a->ops.end());
     if (o.empty()) return HY_OK;
-    HY_TRY(cu(cudaMemcpyAsync(a->d_ops, o.data(), o.size() * sizeof(int32_t),
-                              cudaMemcpyHostToDevice, st), "upload ops"));
+    HY_TRY(xfer(a, a->d_ops, o.data(), o.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st,
+                "upload ops"));
     return cu(cudaStreamSynchronize(st), "sync");
 }
 
@@ -184,8 +192,8 @@ hy_status upload_extra(hy_adapt *a, cudaStream_t st)
     }
     for (size_t l = 0; l < a->ops.size(); ++l) ex[4 * a->ops[l] + 3] = 0.0f;
     for (size_t l = 0; l < a->ops.size(); ++l) ex[4 * a->ops[l] + 3] += float(std::fabs(a->theta[l]));
-    HY_TRY(cu(cudaMemcpyAsync(a->d_extra, ex.data(), ex.size() * 4, cudaMemcpyHostToDevice, st),
-              "upload extra features"));
+    HY_TRY(xfer(a, a->d_extra, ex.data(), ex.size() * 4, cudaMemcpyHostToDevice, st,
+                "upload extra features"));
     return cu(cudaStreamSynchronize(st), "sync");
 }
 
@@ -400,8 +408,8 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     auto full_screen = [&]() -> hy_status {
         HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, nullptr, a->K, a->d_g, bulk, st));
         g.assign(a->K, 0.0);
-        HY_TRY(cu(cudaMemcpyAsync(g.data(), a->d_g, a->K * sizeof(double),
-                                  cudaMemcpyDeviceToHost, st), "screen readback"));
+        HY_TRY(xfer(a, g.data(), a->d_g, a->K * sizeof(double), cudaMemcpyDeviceToHost, st,
+                    "screen readback"));
         return cu(cudaStreamSynchronize(st), "sync");
     };
     auto pick = [&](const std::vector<int64_t> &ids, const std::vector<double> &gv) {
@@ -437,10 +445,10 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, a->d_prop, M, a->d_gp, bulk, st));
         std::vector<int32_t> prop(M);
         std::vector<double> gp(M);
-        HY_TRY(cu(cudaMemcpyAsync(prop.data(), a->d_prop, M * 4, cudaMemcpyDeviceToHost, st),
-                  "proposals readback"));
-        HY_TRY(cu(cudaMemcpyAsync(gp.data(), a->d_gp, M * 8, cudaMemcpyDeviceToHost, st),
-                  "proposals readback"));
+        HY_TRY(xfer(a, prop.data(), a->d_prop, M * 4, cudaMemcpyDeviceToHost, st,
+                    "proposals readback"));
+        HY_TRY(xfer(a, gp.data(), a->d_gp, M * 8, cudaMemcpyDeviceToHost, st,
+                    "proposals readback"));
         HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
         cand.assign(prop.begin(), prop.end());
         pick(cand, gp);
@@ -603,6 +611,14 @@ hy_status hy_adapt_evaluate(hy_adapt *a, const double *thetas, hy_dtype dt, doub
         HY_TRY(gradient(a, th, dt, st, g));
         std::copy(g.begin(), g.end(), grad);
     }
+    return HY_OK;
+}
+
+hy_status hy_adapt_io_bytes(const hy_adapt *a, int64_t *h2d, int64_t *d2h)
+{
+    if (!a) return set_err(HY_ERR_ARG, "NULL argument");
+    if (h2d) *h2d = a->h2d;
+    if (d2h) *d2h = a->d2h;
     return HY_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -67,8 +68,11 @@ struct DevCsr {
 
 }  // namespace
 
+std::atomic<long long> g_launches{0};
+
 namespace hy {
 void set_last_error(const std::string &msg) { g_err = msg; }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace hy
 
 struct hy_ham {
@@ -386,6 +390,8 @@ extern "C" {
 const char *hy_last_error(void) { return g_err.c_str(); }
 
 const char *hy_version(void) { return "hyperion-gb300 0.1 (sm_103a)"; }
+
+int64_t hy_launch_count(void) { return int64_t(g_launches.load(std::memory_order_relaxed)); }
 
 hy_status hy_build_hamiltonian(const double *h1, const double *h2, double e_core,
                                int n_orb, int n_alpha, int n_beta,
@@ -1129,6 +1135,8 @@ hy_status hy_batch_graph_launch(hy_batch *b, const void *psi, void *sigma, hy_dt
         b->g_tile = b->tile;
     }
     HY_CUDA(cudaGraphLaunch(b->gexec, st), "graph launch");
+    hy::count_launch();                       // the persistent rows kernel
+    if (energies) hy::count_launch();         // the per-molecule energy sums
     return HY_OK;
 }
 

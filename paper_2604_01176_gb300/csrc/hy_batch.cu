@@ -193,7 +193,7 @@ cudaError_t batch_rows(const BatchArgs<T> &a, int grid, cudaStream_t st)
     cudaError_t e = cudaFuncSetAttribute(k_batch_rows<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    k_batch_rows<T><<<grid, a.threads, smem, st>>>(a);
+    k_batch_rows<T><<<grid, a.threads, smem, st>>>(a); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -211,7 +211,7 @@ cudaError_t batch_occupancy(const BatchArgs<T> &a, int *per_sm)
 cudaError_t batch_energy(const double *row_energy, const int64_t *base, const int64_t *rows,
                          int count, double *energies, cudaStream_t st)
 {
-    k_batch_energy<<<(count + 63) / 64, 64, 0, st>>>(row_energy, base, rows, count, energies);
+    k_batch_energy<<<(count + 63) / 64, 64, 0, st>>>(row_energy, base, rows, count, energies); hy::count_launch();
     return cudaGetLastError();
 }
 

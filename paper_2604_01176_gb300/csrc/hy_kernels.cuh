@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 namespace hy {
+// counts every kernel launch the library makes (hy_launch_count)
+void count_launch();
 namespace k {
 
 // Pool metadata on the device.  A constituent C = eps * Ca * Cb with Ca / Cb
@@ -15,6 +17,10 @@ struct ConsDev {
 struct OpDev {
     int32_t nc, c0, c1, pad;
 };
+
+// columns of the output row each coupling thread keeps in registers
+// (1024 threads x 13 columns covers N_beta = 12,870 at 16 orbitals)
+constexpr int kCouplingMaxCpt = 13;
 
 template <typename T>
 struct CouplingArgs {

@@ -87,8 +87,8 @@ cudaError_t occupations(const T *psi, int64_t Na, int64_t Nb, const uint32_t *as
                         const uint32_t *bstr, int n, double *partial, int G, float *out,
                         cudaStream_t st)
 {
-    k_occ_partial<T><<<G, 256, 0, st>>>(psi, Na, Nb, astr, bstr, n, partial);
-    k_occ_final<<<1, 64, 0, st>>>(partial, G, n, out);
+    k_occ_partial<T><<<G, 256, 0, st>>>(psi, Na, Nb, astr, bstr, n, partial); hy::count_launch();
+    k_occ_final<<<1, 64, 0, st>>>(partial, G, n, out); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -149,7 +149,7 @@ cudaError_t features(const int32_t *desc, int64_t K, int n, const double *h1,
 {
     if (K == 0) return cudaSuccess;
     k_features<<<unsigned((K + 127) / 128), 128, 0, st>>>(desc, K, n, h1, eri, occ, extra,
-                                                          feat);
+                                                          feat); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -205,7 +205,7 @@ cudaError_t gemm(const float *A, const float *B, float *C, int M, int N, int Kd,
 {
     if (M == 0 || N == 0) return cudaSuccess;
     dim3 grid((N + 15) / 16, (M + 15) / 16);
-    k_gemm<TA, TB><<<grid, 256, 0, st>>>(A, B, C, M, N, Kd, lda, ldb, ldc, bias, relu ? 1 : 0);
+    k_gemm<TA, TB><<<grid, 256, 0, st>>>(A, B, C, M, N, Kd, lda, ldb, ldc, bias, relu ? 1 : 0); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -544,7 +544,7 @@ hy_status hy_ranker_add_samples(hy_ranker *r, const float *feat, const double *g
     }
     RTRY(rcu(cudaMemcpyAsync(r->X + size_t(r->n_samples) * r->F, feat, size_t(m) * r->F * 4,
                              cudaMemcpyDeviceToDevice, st), "append features"));
-    hy::k::k_targets<<<1, 1024, 0, st>>>(g, m, r->Y + r->n_samples);
+    hy::k::k_targets<<<1, 1024, 0, st>>>(g, m, r->Y + r->n_samples); hy::count_launch();
     RTRY(rcu(cudaGetLastError(), "targets"));
     r->n_samples += m;
     return HY_OK;
@@ -577,25 +577,25 @@ hy_status hy_ranker_fit(hy_ranker *r, int epochs, int batch, float lr, uint64_t 
             RTRY(rcu(cudaMemcpyAsync(r->idx, perm.data() + o, size_t(mb) * 4,
                                      cudaMemcpyHostToDevice, st), "upload batch"));
             const unsigned gx = unsigned((int64_t(mb) * F + 255) / 256);
-            K::k_gather_rows<<<gx, 256, 0, st>>>(r->X, r->idx, mb, F, r->xb);
-            K::k_gather_rows<<<unsigned((mb + 255) / 256), 256, 0, st>>>(r->Y, r->idx, mb, 1, r->yb);
+            K::k_gather_rows<<<gx, 256, 0, st>>>(r->X, r->idx, mb, F, r->xb); hy::count_launch();
+            K::k_gather_rows<<<unsigned((mb + 255) / 256), 256, 0, st>>>(r->Y, r->idx, mb, 1, r->yb); hy::count_launch();
             RTRY(forward(r, r->xb, mb, st));
-            K::k_mse<<<unsigned((mb + 255) / 256), 256, 0, st>>>(r->out, r->yb, mb, r->dout, r->sq);
+            K::k_mse<<<unsigned((mb + 255) / 256), 256, 0, st>>>(r->out, r->yb, mb, r->dout, r->sq); hy::count_launch();
             // layer 3 (H -> 1): dW3 = dout^T z2, db3 = sum dout, d2 = dout W3
             RTRY(rcu(K::gemm<true, false>(r->dout, r->z[2], r->gw + r->woff[3], 1, H, mb, 1, H, H,
                                           nullptr, false, st), "mlp backward"));
-            K::k_colsum<<<1, 32, 0, st>>>(r->dout, mb, 1, r->gw + r->boff[3]);
+            K::k_colsum<<<1, 32, 0, st>>>(r->dout, mb, 1, r->gw + r->boff[3]); hy::count_launch();
             RTRY(rcu(K::gemm<false, false>(r->dout, r->w + r->woff[3], r->d[2], mb, H, 1, 1, H, H,
                                            nullptr, false, st), "mlp backward"));
             for (int l = 2; l >= 0; --l) {
                 const int64_t cnt = int64_t(mb) * H;
-                K::k_relu_bwd<<<unsigned((cnt + 255) / 256), 256, 0, st>>>(r->d[l], r->z[l], cnt);
+                K::k_relu_bwd<<<unsigned((cnt + 255) / 256), 256, 0, st>>>(r->d[l], r->z[l], cnt); hy::count_launch();
                 const float *xin = l == 0 ? r->xb : r->z[l - 1];
                 const int fin = l == 0 ? F : H;
                 RTRY(rcu(K::gemm<true, false>(r->d[l], xin, r->gw + r->woff[l], H, fin, mb, H, fin,
                                               fin, nullptr, false, st), "mlp backward"));
                 K::k_colsum<<<unsigned((H + 127) / 128), 128, 0, st>>>(r->d[l], mb, H,
-                                                                       r->gw + r->boff[l]);
+                                                                       r->gw + r->boff[l]); hy::count_launch();
                 if (l > 0)
                     RTRY(rcu(K::gemm<false, false>(r->d[l], r->w + r->woff[l], r->d[l - 1], mb, H,
                                                    H, H, H, H, nullptr, false, st),
@@ -604,7 +604,7 @@ hy_status hy_ranker_fit(hy_ranker *r, int epochs, int batch, float lr, uint64_t 
             ++r->step;
             const float b1t = std::pow(0.9f, float(r->step)), b2t = std::pow(0.999f, float(r->step));
             K::k_adam<<<unsigned((r->nparam + 255) / 256), 256, 0, st>>>(
-                r->w, r->gw, r->m1, r->m2, int64_t(r->nparam), lr, b1t, b2t);
+                r->w, r->gw, r->m1, r->m2, int64_t(r->nparam), lr, b1t, b2t); hy::count_launch();
             RTRY(rcu(cudaGetLastError(), "mlp step"));
             if (ep == epochs - 1) {
                 RTRY(rcu(cudaMemcpyAsync(sq.data(), r->sq, size_t(mb) * 4, cudaMemcpyDeviceToHost,
@@ -632,7 +632,7 @@ hy_status hy_ranker_topk(const float *score, int64_t m, int64_t k, int32_t *idx,
     cudaError_t e = cudaFuncSetAttribute(hy::k::k_topk, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem));
     if (e != cudaSuccess) return rcu(e, "top-k attribute");
-    hy::k::k_topk<<<1, 1024, smem, static_cast<cudaStream_t>(stream)>>>(score, int(m), int(k), idx);
+    hy::k::k_topk<<<1, 1024, smem, static_cast<cudaStream_t>(stream)>>>(score, int(m), int(k), idx); hy::count_launch();
     return rcu(cudaGetLastError(), "top-k");
 }
 

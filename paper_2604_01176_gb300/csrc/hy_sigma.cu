@@ -52,7 +52,7 @@ cudaError_t spmm(const int32_t *ptr, const int32_t *col, const T *val,
 {
     if (rows == 0 || ncols == 0) return cudaSuccess;
     dim3 grid(unsigned(rows), unsigned((ncols + 255) / 256));
-    k_spmm<T><<<grid, 256, 0, st>>>(ptr, col, val, X, Y, ncols, accumulate ? 1 : 0);
+    k_spmm<T><<<grid, 256, 0, st>>>(ptr, col, val, X, Y, ncols, accumulate ? 1 : 0); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -101,7 +101,7 @@ cudaError_t transpose(const T *in, T *out, int64_t R, int64_t C, cudaStream_t st
 {
     if (R == 0 || C == 0) return cudaSuccess;
     dim3 grid(unsigned((C + 31) / 32), unsigned((R + 31) / 32)), block(32, 8);
-    k_transpose<T><<<grid, block, 0, st>>>(in, out, R, C);
+    k_transpose<T><<<grid, block, 0, st>>>(in, out, R, C); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -111,7 +111,7 @@ cudaError_t add_transposed(const T *tau, T *sigma, int64_t R, int64_t C,
 {
     if (R == 0 || C == 0) return cudaSuccess;
     dim3 grid(unsigned((R + 31) / 32), unsigned((C + 31) / 32)), block(32, 8);
-    k_add_transposed<T><<<grid, block, 0, st>>>(tau, sigma, R, C);
+    k_add_transposed<T><<<grid, block, 0, st>>>(tau, sigma, R, C); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -159,30 +159,66 @@ struct Planes<double> {
     }
 };
 
+// Sign of a staged coefficient flipped by the excitation's sign bit (bit
+// 31 of the packed entry) with an integer XOR on the high word, so no
+// floating-point instruction is spent on it.
 template <typename T>
-__global__ void __launch_bounds__(512)
-k_coupling(CouplingArgs<T> a)
+__device__ __forceinline__ T coef_signed(const uint32_t *C, int nn, int rt, uint32_t sbit);
+template <>
+__device__ __forceinline__ float coef_signed<float>(const uint32_t *C, int, int rt, uint32_t sbit)
+{
+    return __uint_as_float(C[rt] ^ sbit);
+}
+template <>
+__device__ __forceinline__ double coef_signed<double>(const uint32_t *C, int nn, int rt,
+                                                      uint32_t sbit)
+{
+    return __hiloint2double(int(C[nn + rt] ^ sbit), int(C[rt]));
+}
+
+// Shared memory of the coupling kernel: row planes [W*Nb] | coefficient
+// planes [W*n*n] | Cdiag [16] T | diagonal half-mask tables TL, TH [256] T.
+// TL[m] (TH[m]) = sum of Cdiag[r] over the set bits r of m (of m shifted by
+// 8), so the diagonal beta term of a column is TL[b & 255] + TH[b >> 8].
+template <typename T>
+size_t coupling_smem(int64_t Nb, int n)
+{
+    constexpr int W = sizeof(T) / 4;
+    size_t words = size_t(W) * Nb + size_t(W) * n * n;
+    words = (words + 3) / 4 * 4;
+    return words * 4 + (16 + 512) * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024, 1)
+k_coupling(CouplingArgs<T> a, int cpt)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using PL = Planes<T>;
+    constexpr int W = sizeof(T) / 4;
     const int64_t Nb = a.Nb;
     const int n = a.n, nn = n * n;
-    T *acc = reinterpret_cast<T *>(smem_raw);                 // [Nb]
-    uint32_t *row = reinterpret_cast<uint32_t *>(acc + Nb);    // planes [Nb]
-    uint32_t *C = row + PL::kWords * Nb;                       // planes [nn]
-    T *Cdiag = reinterpret_cast<T *>(C + PL::kWords * nn + (PL::kWords * nn) % 2);  // [n]
+    uint32_t *row = reinterpret_cast<uint32_t *>(smem_raw);     // planes [Nb]
+    uint32_t *C = row + W * Nb;                                 // planes [nn]
+    size_t words = size_t(W) * Nb + size_t(W) * nn;
+    words = (words + 3) / 4 * 4;
+    T *Cdiag = reinterpret_cast<T *>(smem_raw + words * 4);     // [16]
+    T *TL = Cdiag + 16, *TH = TL + 256;                         // [256] each
+    const int tid = threadIdx.x, nt = blockDim.x;
     for (int64_t ar = blockIdx.x; ar < a.Na; ar += gridDim.x) {
-        for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) acc[b] = T(0);
+        T acc[kCouplingMaxCpt];
+#pragma unroll
+        for (int j = 0; j < kCouplingMaxCpt; ++j) acc[j] = T(0);
         const uint32_t amask = a.astr[ar];
         for (int e = -1; e < a.nexa; ++e) {
             __syncthreads();
             int64_t Ja;
             if (e < 0) {
                 Ja = ar;
-                for (int rs = threadIdx.x; rs < nn; rs += blockDim.x) {
+                for (int rs = tid; rs < nn; rs += nt) {
                     T v = T(0);
                     for (uint32_t m = amask; m; m &= m - 1) {
-                        int p = __ffs(m) - 1;
+                        const int p = __ffs(m) - 1;
                         v += a.V[size_t(p * n + p) * nn + rs];
                     }
                     PL::put(C, nn, rs, v);
@@ -193,35 +229,50 @@ k_coupling(CouplingArgs<T> a)
                 Ja = u & 0xFFFFu;
                 const int p = (u >> 16) & 15, q = (u >> 20) & 15;
                 const bool neg = (u >> 31) != 0;
-                for (int rs = threadIdx.x; rs < nn; rs += blockDim.x) {
+                for (int rs = tid; rs < nn; rs += nt) {
                     T v = a.V[size_t(p * n + q) * nn + rs];
                     v = neg ? -v : v;
                     PL::put(C, nn, rs, v);
                     if (rs / n == rs % n) Cdiag[rs / n] = v;
                 }
             }
+            for (int i = tid; i < 16 - n; i += nt) Cdiag[n + i] = T(0);
             const T *src = a.psi + Ja * Nb;
-            for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) PL::put(row, Nb, b, src[b]);
+            for (int64_t b = tid; b < Nb; b += nt) PL::put(row, Nb, b, src[b]);
             __syncthreads();
-            for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) {
-                T d = T(0);
-                for (uint32_t m = a.bstr[b]; m; m &= m - 1) d += Cdiag[__ffs(m) - 1];
-                T s = d * PL::get(row, Nb, b);
-                const uint32_t *bx = a.bexT + b;
-                for (int f = 0; f < a.nexb; ++f) {
-                    const uint32_t u = bx[size_t(f) * Nb];
-                    const int rt = ((u >> 16) & 15) * n + ((u >> 20) & 15);
-                    T cv = PL::get(C, nn, rt);
-                    cv = (u >> 31) ? -cv : cv;
-                    s += cv * PL::get(row, Nb, u & 0xFFFFu);
+            for (int i = tid; i < 512; i += nt) {
+                const int m = i & 255, base = i < 256 ? 0 : 8;
+                T v = T(0);
+                for (int r = 0; r < 8; ++r)
+                    if ((m >> r) & 1) v += Cdiag[base + r];
+                (i < 256 ? TL : TH)[m] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < kCouplingMaxCpt; ++j) {
+                const int64_t b = tid + int64_t(j) * nt;
+                if (j < cpt && b < Nb) {
+                    const uint32_t m = a.bstr[b];
+                    const T d = TL[m & 255u] + TH[m >> 8];
+                    T s = d * PL::get(row, Nb, b) + acc[j];
+                    const uint32_t *bx = a.bexT + b;
+#pragma unroll 4
+                    for (int f = 0; f < a.nexb; ++f) {
+                        const uint32_t u = bx[size_t(f) * Nb];
+                        const int rt = ((u >> 16) & 15) * n + ((u >> 20) & 15);
+                        const T cv = coef_signed<T>(C, nn, rt, u & 0x80000000u);
+                        s += cv * PL::get(row, Nb, u & 0xFFFFu);
+                    }
+                    acc[j] = s;
                 }
-                acc[b] += s;
             }
         }
-        __syncthreads();
         T *dst = a.sigma + ar * Nb;
-        for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) dst[b] += acc[b];
-        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kCouplingMaxCpt; ++j) {
+            const int64_t b = tid + int64_t(j) * nt;
+            if (j < cpt && b < Nb) dst[b] += acc[j];
+        }
     }
 }
 
@@ -229,22 +280,20 @@ template <typename T>
 cudaError_t coupling(const CouplingArgs<T> &a, int num_sms, cudaStream_t st)
 {
     if (a.Na == 0 || a.Nb == 0) return cudaSuccess;
-    // acc [Nb] T, row planes [Nb] T, coefficient planes [n*n] T (+ pad),
-    // diagonal coefficients [n] T
-    const size_t nn = size_t(a.n) * a.n;
-    const size_t smem = 2 * size_t(a.Nb) * sizeof(T) + (nn + 1) * sizeof(T) +
-                        size_t(a.n) * sizeof(T);
+    int threads = int(a.Nb < 1024 ? (a.Nb + 31) / 32 * 32 : 1024);
+    const int cpt = int((a.Nb + threads - 1) / threads);
+    if (cpt > kCouplingMaxCpt) return cudaErrorInvalidValue;
+    const size_t smem = coupling_smem<T>(a.Nb, a.n);
     cudaError_t err = cudaFuncSetAttribute(
         k_coupling<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (err != cudaSuccess) return err;
     int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coupling<T>,
-                                                        512, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coupling<T>, threads, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = int64_t(num_sms) * per_sm;
     if (grid > a.Na) grid = a.Na;
-    k_coupling<T><<<unsigned(grid), 512, smem, st>>>(a);
+    k_coupling<T><<<unsigned(grid), threads, smem, st>>>(a, cpt); hy::count_launch();
     return cudaGetLastError();
 }
 

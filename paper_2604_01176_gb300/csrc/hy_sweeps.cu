@@ -59,8 +59,8 @@ template <typename T>
 cudaError_t dot(const T *x, const T *y, int64_t N, double *partials, int G,
                 double *out, cudaStream_t st)
 {
-    k_dot_partial<T><<<G, 256, 0, st>>>(x, y, N, partials);
-    k_sum_partials<<<1, 256, 0, st>>>(partials, G, out);
+    k_dot_partial<T><<<G, 256, 0, st>>>(x, y, N, partials); hy::count_launch();
+    k_sum_partials<<<1, 256, 0, st>>>(partials, G, out); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -80,7 +80,7 @@ cudaError_t scale_rsqrt(T *x, int64_t N, const double *norm2, cudaStream_t st)
     int64_t blocks = (N + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    k_scale_rsqrt<T><<<unsigned(blocks), 256, 0, st>>>(x, N, norm2);
+    k_scale_rsqrt<T><<<unsigned(blocks), 256, 0, st>>>(x, N, norm2); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -155,9 +155,9 @@ cudaError_t grad(const GradArgs<T> &a, cudaStream_t st)
 {
     if (a.n_ops == 0) return cudaSuccess;
     dim3 grid(unsigned(a.n_ops), unsigned(a.CH));
-    k_grad_partial<T><<<grid, 256, 0, st>>>(a);
+    k_grad_partial<T><<<grid, 256, 0, st>>>(a); hy::count_launch();
     k_grad_final<<<unsigned((a.n_ops + 255) / 256), 256, 0, st>>>(a.partials, a.CH,
-                                                                 a.n_ops, a.g);
+                                                                 a.n_ops, a.g); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -202,7 +202,7 @@ cudaError_t excite(T *psi, const uint32_t *ae, int64_t nrows, const uint32_t *be
 {
     if (nrows == 0 || ncols == 0) return cudaSuccess;
     dim3 grid(unsigned((ncols + 255) / 256), unsigned(nrows));
-    k_excite<T><<<grid, 256, 0, st>>>(psi, ae, be, ncols, Nb, T(c), T(s_eps));
+    k_excite<T><<<grid, 256, 0, st>>>(psi, ae, be, ncols, Nb, T(c), T(s_eps)); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -278,7 +278,7 @@ cudaError_t rank(const uint64_t *dets, int64_t *idx, int64_t m, int n, int na,
 {
     if (m == 0) return cudaSuccess;
     k_rank<<<unsigned((m + 255) / 256), 256, 0, st>>>(dets, idx, m, n, na, nb, Nb,
-                                                     binom33);
+                                                     binom33); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -288,7 +288,7 @@ cudaError_t unrank(const int64_t *idx, uint64_t *dets, int64_t m, int n, int na,
 {
     if (m == 0) return cudaSuccess;
     k_unrank<<<unsigned((m + 255) / 256), 256, 0, st>>>(idx, dets, m, n, na, nb, Na,
-                                                       Nb, binom33);
+                                                       Nb, binom33); hy::count_launch();
     return cudaGetLastError();
 }
 
