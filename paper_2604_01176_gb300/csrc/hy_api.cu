@@ -85,6 +85,7 @@ struct hy_ham {
     DevArena arena;
     uint32_t *d_astr = nullptr, *d_bstr = nullptr;
     uint32_t *d_aex = nullptr, *d_bexT = nullptr;
+    uint8_t *d_ainv = nullptr;   // inverse alpha excitation positions
     uint32_t *d_binom = nullptr;
     DevCsr<double> Ma64, Mb64;
     DevCsr<float> Ma32, Mb32;
@@ -244,8 +245,19 @@ template <typename T>
 hy_status apply_h_t(hy_ham *h, const T *psi, T *sigma, cudaStream_t st)
 {
     const WsLayout L = ws_layout(h, n_partials_needed(h, 0), sizeof(T));
-    hy_status s = ensure_ws(h, L.total);
-    if (s != HY_OK) return s;
+    // float: room for the dense coupling's intermediate T after the state
+    // buffers, sized before any launch; without it the direct kernel runs
+    const int64_t Nbp = (h->Nb + 63) / 64 * 64;
+    const size_t tbytes = sizeof(T) == sizeof(float)
+        ? size_t(h->Na) * size_t(h->A.nex + 1) * size_t(Nbp) * sizeof(float) : 0;
+    bool dense = false;
+    if (tbytes && ensure_ws(h, L.total + tbytes) == HY_OK) {
+        dense = true;
+    } else {
+        cudaGetLastError();   // clear a failed allocation
+        hy_status s = ensure_ws(h, L.total);
+        if (s != HY_OK) return s;
+    }
     char *ws = static_cast<char *>(h->ws);
     T *psiT = reinterpret_cast<T *>(ws + L.buf1);
     T *tau = reinterpret_cast<T *>(ws + L.buf2);
@@ -264,6 +276,28 @@ hy_status apply_h_t(hy_ham *h, const T *psi, T *sigma, cudaStream_t st)
     HY_CUDA(hy::k::spmm<T>(Mb->ptr, Mb->col, Mb->val, h->Nb, psiT, tau, h->Na,
                            false, st), "beta part");
     HY_CUDA(hy::k::add_transposed<T>(tau, sigma, h->Na, h->Nb, st), "beta add");
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (dense) {
+            hy::k::CplDenseArgs d;
+            d.psi = psi;
+            d.sigma = sigma;
+            d.T = reinterpret_cast<float *>(static_cast<char *>(h->ws) + L.total);
+            d.aex = h->d_aex;
+            d.inv = h->d_ainv;
+            d.bexT = h->d_bexT;
+            d.astr = h->d_astr;
+            d.bstr = h->d_bstr;
+            d.V = h->d_V32;
+            d.n = h->n;
+            d.nexa = h->A.nex;
+            d.nexb = h->B.nex;
+            d.Na = h->Na;
+            d.Nb = h->Nb;
+            d.Nbp = Nbp;
+            HY_CUDA(hy::k::coupling_dense(d, h->num_sms, st), "alpha-beta coupling (dense)");
+            return HY_OK;
+        }
+    }
     hy::k::CouplingArgs<T> a;
     a.psi = psi;
     a.sigma = sigma;
@@ -453,6 +487,7 @@ hy_status hy_build_hamiltonian(const double *h1, const double *h2, double e_core
     up(ar.upload(&h->d_astr, h->A.str.data(), h->A.str.size()), "upload alpha strings");
     up(ar.upload(&h->d_bstr, h->B.str.data(), h->B.str.size()), "upload beta strings");
     up(ar.upload(&h->d_aex, h->A.ex.data(), h->A.ex.size()), "upload alpha excitations");
+    up(ar.upload(&h->d_ainv, h->A.inv.data(), h->A.inv.size()), "upload inverse excitations");
     up(ar.upload(&h->d_bexT, bexT.data(), bexT.size()), "upload beta excitations");
     up(ar.upload(&h->d_binom, binom.data(), binom.size()), "upload binomials");
     up(ar.upload(&h->d_V64, h->kt.V.data(), h->kt.V.size()), "upload V");

@@ -98,6 +98,19 @@ void build_string_space(int n, int k, StringSpace &s)
             }
         }
     }
+    // inverse positions: the partner J of (r, e) lists r at the entry whose
+    // orbitals are swapped (J lacks p and holds q)
+    s.inv.assign(size_t(s.N) * s.nex, 0);
+    for (int64_t r = 0; r < s.N; ++r)
+        for (int e = 0; e < s.nex; ++e) {
+            const uint32_t u = s.ex[size_t(r) * s.nex + e];
+            const uint32_t J = u & 0xFFFFu;
+            for (int f = 0; f < s.nex; ++f)
+                if ((s.ex[size_t(J) * s.nex + f] & 0xFFFFu) == uint32_t(r)) {
+                    s.inv[size_t(r) * s.nex + e] = uint8_t(f);
+                    break;
+                }
+        }
 }
 
 // ---------------------------------------------------------------------------

@@ -41,6 +41,9 @@ struct StringSpace {
     int nex = 0;                    // k * (n - k) entries per string
     std::vector<uint32_t> str;      // rank -> mask
     std::vector<uint32_t> ex;       // [N][nex] packed entries
+    // inv[r][e]: position of string r in the entry list of its partner
+    // ex[r][e] (the same excitation seen from the partner's side)
+    std::vector<uint8_t> inv;       // [N][nex]
 };
 void build_string_space(int n, int k, StringSpace &s);
 

@@ -52,6 +52,22 @@ struct GradArgs {
     double *g;              // [n_ops]
 };
 
+// float alpha-beta coupling through the dense intermediate T (hy_sigma.cu)
+struct CplDenseArgs {
+    const float *psi;
+    float *sigma;
+    float *T;               // [Na][nexa+1][Nbp]
+    const uint32_t *aex;    // [Na][nexa]
+    const uint8_t *inv;     // [Na][nexa] position of the row in its partner's list
+    const uint32_t *bexT;   // [nexb][Nb]
+    const uint32_t *astr, *bstr;
+    const float *V;         // n^4
+    int n, nexa, nexb;
+    int64_t Na, Nb, Nbp;    // Nbp: row stride of T (multiple of 64)
+};
+size_t cpl_dense_smem(int64_t Nb, int n);
+cudaError_t coupling_dense(const CplDenseArgs &a, int num_sms, cudaStream_t st);
+
 template <typename T>
 cudaError_t spmm(const int32_t *ptr, const int32_t *col, const T *val,
                  int64_t rows, const T *X, T *Y, int64_t ncols, bool accumulate,

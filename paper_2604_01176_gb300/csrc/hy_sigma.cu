@@ -23,26 +23,55 @@ namespace k {
 // [rows][ncols].  Grid: x = output row (so all rows of one column tile run
 // together and the tile of X stays in L2), y = column tile.
 // ---------------------------------------------------------------------------
+template <typename T, int VEC>
+struct VecOf;
+template <> struct VecOf<float, 1> { using type = float; };
+template <> struct VecOf<float, 2> { using type = float2; };
+template <> struct VecOf<double, 1> { using type = double; };
+template <> struct VecOf<double, 2> { using type = double2; };
+
 template <typename T>
+__device__ __forceinline__ void vfma(T &acc, T w, T x) { acc += w * x; }
+__device__ __forceinline__ void vfma(float2 &acc, float w, float2 x)
+{
+    acc.x += w * x.x;
+    acc.y += w * x.y;
+}
+__device__ __forceinline__ void vfma(double2 &acc, double w, double2 x)
+{
+    acc.x += w * x.x;
+    acc.y += w * x.y;
+}
+template <typename V> __device__ __forceinline__ V vzero() { return V{}; }
+
+// Each thread owns VEC consecutive columns (one vector load per partner row
+// and nonzero), so the broadcast loads of the CSR value and column index
+// are shared by VEC multiply-adds.
+template <typename T, int VEC>
 __global__ void __launch_bounds__(256)
 k_spmm(const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
        const T *__restrict__ val, const T *__restrict__ X, T *__restrict__ Y,
        int64_t ncols, int accumulate)
 {
+    using V = typename VecOf<T, VEC>::type;
     const int64_t r = blockIdx.x;
-    const int64_t c = int64_t(blockIdx.y) * blockDim.x + threadIdx.x;
+    const int64_t c = (int64_t(blockIdx.y) * blockDim.x + threadIdx.x) * VEC;
     if (c >= ncols) return;
     const int beg = ptr[r], end = ptr[r + 1];
-    T s0 = T(0), s1 = T(0);
+    V s0 = vzero<V>(), s1 = vzero<V>();
     int kk = beg;
     for (; kk + 1 < end; kk += 2) {
-        s0 += val[kk] * X[int64_t(col[kk]) * ncols + c];
-        s1 += val[kk + 1] * X[int64_t(col[kk + 1]) * ncols + c];
+        vfma(s0, val[kk], *reinterpret_cast<const V *>(X + int64_t(col[kk]) * ncols + c));
+        vfma(s1, val[kk + 1], *reinterpret_cast<const V *>(X + int64_t(col[kk + 1]) * ncols + c));
     }
-    if (kk < end) s0 += val[kk] * X[int64_t(col[kk]) * ncols + c];
-    const T s = s0 + s1;
+    if (kk < end) vfma(s0, val[kk], *reinterpret_cast<const V *>(X + int64_t(col[kk]) * ncols + c));
+    const T *a0 = reinterpret_cast<const T *>(&s0), *a1 = reinterpret_cast<const T *>(&s1);
     T *y = Y + r * ncols + c;
-    if (accumulate) *y += s; else *y = s;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+        const T sv = a0[v] + a1[v];
+        if (accumulate) y[v] += sv; else y[v] = sv;
+    }
 }
 
 template <typename T>
@@ -51,8 +80,17 @@ cudaError_t spmm(const int32_t *ptr, const int32_t *col, const T *val,
                  cudaStream_t st)
 {
     if (rows == 0 || ncols == 0) return cudaSuccess;
-    dim3 grid(unsigned(rows), unsigned((ncols + 255) / 256));
-    k_spmm<T><<<grid, 256, 0, st>>>(ptr, col, val, X, Y, ncols, accumulate ? 1 : 0); hy::count_launch();
+    // two columns per thread when every row starts on a vector boundary
+    const bool v2 = (ncols % 2 == 0) &&
+                    (reinterpret_cast<uintptr_t>(X) % (2 * sizeof(T)) == 0) &&
+                    (reinterpret_cast<uintptr_t>(Y) % (2 * sizeof(T)) == 0);
+    if (v2) {
+        dim3 grid(unsigned(rows), unsigned((ncols / 2 + 255) / 256));
+        k_spmm<T, 2><<<grid, 256, 0, st>>>(ptr, col, val, X, Y, ncols, accumulate ? 1 : 0); hy::count_launch();
+    } else {
+        dim3 grid(unsigned(rows), unsigned((ncols + 255) / 256));
+        k_spmm<T, 1><<<grid, 256, 0, st>>>(ptr, col, val, X, Y, ncols, accumulate ? 1 : 0); hy::count_launch();
+    }
     return cudaGetLastError();
 }
 
@@ -294,6 +332,159 @@ cudaError_t coupling(const CouplingArgs<T> &a, int num_sms, cudaStream_t st)
     int64_t grid = int64_t(num_sms) * per_sm;
     if (grid > a.Na) grid = a.Na;
     k_coupling<T><<<unsigned(grid), threads, smem, st>>>(a, cpt); hy::count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// alpha-beta coupling in float as two dense phases.
+//
+// Phase A, per alpha string J (one CTA, grid-stride):
+//   T[J][m][b'] = sum_t W_J[t][m] G_J[t][b']
+// with t = r*n + s running over every beta excitation type (s = r: the
+// diagonal pair), G_J[t][b'] = sign * psi[J][b' with r -> s] where that
+// excitation exists for b' (else 0), and W_J[t][m] the coupling coefficient
+// of output alpha row a_m = the m-th single-excitation partner of J
+// (V[q][p][t] with J's entry (p, q), times its sign), or for m = nexa the
+// diagonal coefficient sum_{p in J} V[p][p][t].  This is a dense product of
+// a (nexa+1) x n^2 by an n^2 x N_beta matrix, tiled 80 x 64 with 5 x 4
+// outputs per thread; each gathered amplitude is reused by all 65 output
+// rows and each coefficient by every column.
+//
+// Phase B, per output alpha row a' (one CTA, grid-stride):
+//   sigma[a'][b'] += T[a'][nexa][b'] + sum_e T[J_e][inv_e][b']
+// where inv_e is the position of a' in the partner list of J_e; 65 coalesced
+// row reads per output row, no atomics, fixed summation order.
+// ---------------------------------------------------------------------------
+constexpr int kDM = 80, kDN = 64;
+
+__global__ void __launch_bounds__(256, 1)
+k_cpl_gemm(CplDenseArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t Nb = a.Nb;
+    const int n = a.n, nn = n * n, nexa = a.nexa, nexb = a.nexb;
+    const int slots = nexa + 1;
+    float *row = reinterpret_cast<float *>(smem_raw);
+    float *W = row + (Nb + 3) / 4 * 4;                  // [nn][kDM]
+    float *G = W + size_t(nn) * kDM;                    // [nn][kDN], 16-byte aligned
+    const int tid = threadIdx.x, mg = tid >> 4, ng = tid & 15;
+    for (int64_t J = blockIdx.x; J < a.Na; J += gridDim.x) {
+        __syncthreads();
+        const float *src = a.psi + J * Nb;
+        for (int64_t b = tid; b < Nb; b += blockDim.x) row[b] = src[b];
+        const uint32_t jm = a.astr[J];
+        for (int idx = tid; idx < nn * kDM; idx += blockDim.x) {
+            const int t = idx / kDM, m = idx % kDM;
+            float v = 0.0f;
+            if (m < nexa) {
+                const uint32_t u = a.aex[J * nexa + m];
+                const int pj = (u >> 16) & 15, qj = (u >> 20) & 15;
+                v = a.V[size_t(qj * n + pj) * nn + t];
+                if (u >> 31) v = -v;
+            } else if (m == nexa) {
+                for (uint32_t mm = jm; mm; mm &= mm - 1) {
+                    const int p = __ffs(mm) - 1;
+                    v += a.V[size_t(p * n + p) * nn + t];
+                }
+            }
+            W[idx] = v;
+        }
+        for (int64_t b0 = 0; b0 < Nb; b0 += kDN) {
+            __syncthreads();          // W / row ready; previous tile's G consumed
+            for (int idx = tid; idx < nn * kDN; idx += blockDim.x) G[idx] = 0.0f;
+            __syncthreads();
+            for (int idx = tid; idx < kDN * (nexb + n); idx += blockDim.x) {
+                const int nl = idx % kDN, f = idx / kDN;
+                const int64_t b = b0 + nl;
+                if (b >= Nb) continue;
+                if (f < nexb) {
+                    const uint32_t u = a.bexT[size_t(f) * Nb + b];
+                    const int r = (u >> 16) & 15, sv = (u >> 20) & 15;
+                    const float v = row[u & 0xFFFFu];
+                    G[(r * n + sv) * kDN + nl] = (u >> 31) ? -v : v;
+                } else {
+                    const int r = f - nexb;
+                    if ((a.bstr[b] >> r) & 1u) G[(r * n + r) * kDN + nl] = row[b];
+                }
+            }
+            __syncthreads();
+            float acc[5][4];
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+            const float *wp = W + mg * 5;
+            const float *gp = G + ng * 4;
+#pragma unroll 4
+            for (int t = 0; t < nn; ++t) {
+                const float4 g = *reinterpret_cast<const float4 *>(gp + t * kDN);
+                const float *wt = wp + t * kDM;
+#pragma unroll
+                for (int i = 0; i < 5; ++i) {
+                    const float w = wt[i];
+                    acc[i][0] += w * g.x;
+                    acc[i][1] += w * g.y;
+                    acc[i][2] += w * g.z;
+                    acc[i][3] += w * g.w;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                const int m = mg * 5 + i;
+                if (m >= slots) continue;
+                const int64_t b = b0 + ng * 4;
+                float *dst = a.T + (J * slots + m) * a.Nbp + b;
+                if (b + 3 < a.Nbp)
+                    *reinterpret_cast<float4 *>(dst) =
+                        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_cpl_gather(CplDenseArgs a)
+{
+    const int64_t Nb = a.Nb;
+    const int nexa = a.nexa, slots = nexa + 1;
+    for (int64_t ar = blockIdx.x; ar < a.Na; ar += gridDim.x) {
+        for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) {
+            float s = a.T[(ar * slots + nexa) * a.Nbp + b];
+            for (int e = 0; e < nexa; ++e) {
+                const int64_t J = a.aex[ar * nexa + e] & 0xFFFFu;
+                const int m = a.inv[ar * nexa + e];
+                s += a.T[(J * slots + m) * a.Nbp + b];
+            }
+            a.sigma[ar * Nb + b] += s;
+        }
+    }
+}
+
+size_t cpl_dense_smem(int64_t Nb, int n)
+{
+    return (size_t((Nb + 3) / 4 * 4) + size_t(n) * n * (kDM + kDN)) * sizeof(float);
+}
+
+cudaError_t coupling_dense(const CplDenseArgs &a, int num_sms, cudaStream_t st)
+{
+    if (a.Na == 0 || a.Nb == 0) return cudaSuccess;
+    if (a.nexa + 1 > kDM) return cudaErrorInvalidValue;
+    const size_t smem = cpl_dense_smem(a.Nb, a.n);
+    cudaError_t err = cudaFuncSetAttribute(k_cpl_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           int(smem));
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpl_gemm, 256, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int64_t grid = int64_t(num_sms) * per_sm;
+    if (grid > a.Na) grid = a.Na;
+    k_cpl_gemm<<<unsigned(grid), 256, smem, st>>>(a); hy::count_launch();
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    int64_t g2 = int64_t(num_sms) * 8;
+    if (g2 > a.Na) g2 = a.Na;
+    k_cpl_gather<<<unsigned(g2), 256, 0, st>>>(a); hy::count_launch();
     return cudaGetLastError();
 }
 
