@@ -346,13 +346,15 @@ hy_status hy_ranker_topk(const float *score, int64_t m, int64_t k,
 /* Attach a ranker to a driver created with screen_top_m = M > 0.  The first
  * warm_iters iterations run the full screen and feed the ranker (features,
  * exact |g|) pairs; it is then fitted (`epochs` passes) and from then on
- * proposes the top M operators, which are screened exactly.  The full
- * screen stays the fallback (run whenever the proposals' ||g|| would stop
- * the loop) and, with cfg.judge, the judge: every ranked iteration also
- * runs it, records the rank of the true argmax, adds its pairs, and refits
- * every refit_every ranked iterations (0: never). */
+ * proposes the top M operators, which are screened exactly.  Every
+ * refresh_every-th ranked iteration (0: never) selects from the full screen
+ * instead, adds its pairs and refits the ranker (epochs / 4 passes, warm
+ * start), which bounds the age of the stale-gradient features.  The full
+ * screen is also the fallback, run whenever the proposals' ||g|| would stop
+ * the loop, and, with cfg.judge, the judge: every ranked iteration also runs
+ * it, records the rank of the true argmax and adds its pairs. */
 hy_status hy_adapt_set_ranker(hy_adapt *a, hy_ranker *r, int warm_iters,
-                              int epochs, int refit_every);
+                              int epochs, int refresh_every);
 
 /* ---------------------------------------------------------------------- */
 /* ADAPT-VQE driver                                                         */

@@ -363,9 +363,9 @@ class Adapt:
                                             stream_ptr(stream)))
         return e.value, g
 
-    def set_ranker(self, ranker: "Ranker", warm_iters=3, epochs=30, refit_every=0):
+    def set_ranker(self, ranker: "Ranker", warm_iters=3, epochs=30, refresh_every=0):
         check(_abi.load().hy_adapt_set_ranker(self._a, ranker.handle, int(warm_iters),
-                                              int(epochs), int(refit_every)))
+                                              int(epochs), int(refresh_every)))
         self._ranker = ranker   # keep it alive as long as the driver
 
     def state(self, dtype=torch.float64, stream=None) -> torch.Tensor:

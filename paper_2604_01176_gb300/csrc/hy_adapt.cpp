@@ -36,7 +36,7 @@ struct hy_adapt {
     const hy_ham *h = nullptr;
     const hy_pool *p = nullptr;
     hy_ranker *ranker = nullptr;
-    int warm_iters = 0, epochs = 0, refit_every = 0, ranked_iters = 0;
+    int warm_iters = 0, epochs = 0, refresh_every = 0;
     float *d_feat = nullptr, *d_extra = nullptr, *d_score = nullptr;
     double *d_gp = nullptr;       // proposals' exact gradients [M]
     std::vector<double> last_g;   // |g_k| when last screened (-1: never)
@@ -400,7 +400,12 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     // 2. screen: full, or the ranker's top-M proposals screened exactly
     const bool ranked = a->cfg.screen_top_m > 0;
     if (ranked && !a->ranker) return set_err(HY_ERR_UNSUPPORTED, "ranked screen needs a ranker");
-    const bool use_ranker = ranked && a->iter >= a->warm_iters;
+    // warm-up and refresh iterations select from the full screen and feed
+    // (and refit) the ranker; the others screen only its proposals
+    const int post = a->iter - a->warm_iters;   // ranked iteration index
+    const bool refresh = ranked && post >= 0 && a->refresh_every > 0 &&
+                         (post + 1) % a->refresh_every == 0;
+    const bool use_ranker = ranked && post >= 0 && !refresh;
     std::vector<double> g;
     std::vector<int64_t> cand;   // screened operators, in proposal order
     int64_t sel = -1;
@@ -435,6 +440,9 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
             HY_TRY(hy_ranker_add_samples(a->ranker, a->d_feat, a->d_g, a->K, st));
             if (a->iter + 1 == a->warm_iters)
                 HY_TRY(hy_ranker_fit(a->ranker, a->epochs, 256, 1e-3f, 1234 + a->iter, nullptr, st));
+            else if (refresh)   // warm-started refit on the grown training set
+                HY_TRY(hy_ranker_fit(a->ranker, std::max(1, a->epochs / 4), 256, 1e-3f,
+                                     1234 + a->iter, nullptr, st));
         }
         note_screen(a, all, g);
     } else {
@@ -460,7 +468,6 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
             note_screen(a, all, g);
         } else if (a->cfg.judge) {
             const double tj = now_s();
-            std::vector<double> gsave(gp);
             HY_TRY(full_screen());
             double tmax = 0.0;
             int64_t targ = -1;
@@ -473,9 +480,6 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
             for (size_t i = 0; i < cand.size(); ++i)
                 if (cand[i] == targ) rec->true_rank = int64_t(i);
             HY_TRY(hy_ranker_add_samples(a->ranker, a->d_feat, a->d_g, a->K, st));
-            ++a->ranked_iters;
-            if (a->refit_every > 0 && a->ranked_iters % a->refit_every == 0)
-                HY_TRY(hy_ranker_fit(a->ranker, a->epochs, 256, 1e-3f, 4321 + a->iter, nullptr, st));
             t_judge = now_s() - tj;
         }
     }
@@ -535,17 +539,17 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
 }
 
 hy_status hy_adapt_set_ranker(hy_adapt *a, hy_ranker *r, int warm_iters, int epochs,
-                              int refit_every)
+                              int refresh_every)
 {
     if (!a || !r) return set_err(HY_ERR_ARG, "NULL argument");
     if (a->cfg.screen_top_m <= 0)
         return set_err(HY_ERR_ARG, "driver was created without screen_top_m");
-    if (warm_iters < 1 || epochs < 1 || refit_every < 0)
-        return set_err(HY_ERR_ARG, "warm_iters and epochs must be >= 1, refit_every >= 0");
+    if (warm_iters < 1 || epochs < 1 || refresh_every < 0)
+        return set_err(HY_ERR_ARG, "warm_iters and epochs must be >= 1, refresh_every >= 0");
     a->ranker = r;
     a->warm_iters = warm_iters;
     a->epochs = epochs;
-    a->refit_every = refit_every;
+    a->refresh_every = refresh_every;
     return HY_OK;
 }
 

@@ -176,11 +176,15 @@ def test_ranked_driver_mechanics_and_judge():
     plain = hy.Adapt(ham, pool, "f64", max_iter=iters).run(iters)
     r = hy.Ranker(hidden=64, seed=9)
     ad = hy.Adapt(ham, pool, "f64", max_iter=iters, screen_top_m=M, judge=True)
-    ad.set_ranker(r, warm_iters=3, epochs=40, refit_every=1)
+    ad.set_ranker(r, warm_iters=3, epochs=40, refresh_every=2)
     recs = ad.run(iters)
     assert r.info()["fitted"] and r.info()["n_samples"] >= 3 * len(pool)
     for i, rec in enumerate(recs):
-        if i < 3:      # warm-up iterations run the full screen
+        refresh = i >= 3 and (i - 3 + 1) % 2 == 0
+        if i < 3 or refresh:   # warm-up and refresh iterations: full screen
+            if refresh:
+                assert rec["true_argmax"] == -1
+                continue
             assert rec["selected"] == plain[i]["selected"]
             assert abs(rec["energy"] - plain[i]["energy"]) < 1e-9
             assert rec["true_argmax"] == -1
