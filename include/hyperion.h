@@ -295,7 +295,7 @@ hy_status hy_occupations(const hy_ham *h, const void *psi, hy_dtype dt,
 
 /* The ranker is an addition with no counterpart in the paper's method: a
  * small MLP that predicts, per pool operator, t_k = log10(|g_k| / max|g| +
- * 1e-12) from 16 features, so that only its top-M operators are screened
+ * 1e-6) from 16 features, so that only its top-M operators are screened
  * exactly.  Features of operator k (first constituent; modes in blocked
  * order): [0..3] kind flags (single, same-spin double, opposite-spin
  * double, extra constituents); [4..7] annihilated and created spatial
@@ -437,6 +437,10 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream);
  * energy in *e (host); the parameters are updated.  The run's final energy
  * in the mixed mode comes from this call. */
 hy_status hy_adapt_refine(hy_adapt *a, int steps, double *e, void *stream);
+
+/* Turn the judge (the extra full screen of every ranked iteration, see
+ * hy_adapt_set_ranker) on or off for the following iterations. */
+hy_status hy_adapt_set_judge(hy_adapt *a, int judge);
 
 /* Copy the ansatz (host arrays with room for cap entries); *len gets its
  * length.  Pass cap = 0 to query the length. */

@@ -321,6 +321,10 @@ class Adapt:
                 break
         return out
 
+    def set_judge(self, on: bool):
+        """Run the full screen as judge on the following ranked iterations."""
+        check(_abi.load().hy_adapt_set_judge(self._a, 1 if on else 0))
+
     def io_bytes(self):
         """(host->device, device->host) bytes the driver has copied so far."""
         h, d = ctypes.c_int64(), ctypes.c_int64()

@@ -117,6 +117,7 @@ SIGNATURES = {
     "hy_adapt_ansatz": (I32, [P, P, P, I64, PI64]),
     "hy_adapt_refine": (I32, [P, I32, P, P]),
     "hy_adapt_io_bytes": (I32, [P, PI64, PI64]),
+    "hy_adapt_set_judge": (I32, [P, I32]),
     "hy_adapt_set_ansatz": (I32, [P, P, P, I64]),
     "hy_adapt_evaluate": (I32, [P, P, I32, P, P, P]),
     "hy_adapt_state": (I32, [P, P, I32, P]),

@@ -197,6 +197,12 @@ hy_status upload_extra(hy_adapt *a, cudaStream_t st)
     return cu(cudaStreamSynchronize(st), "sync");
 }
 
+// Relative energy decrease below which an accepted double-precision step is
+// rounding noise: the Armijo test cannot reject such steps once its
+// threshold e + c * alpha * slope rounds to e, and following them only
+// spends evaluations.
+const double kStall64 = std::ldexp(1.0, -50);
+
 // BFGS with backtracking (Armijo) line search on E(theta) in dt, starting
 // from a->theta and a->hinv; updates both.  *e_out = final energy.  With
 // stall > 0 the run also stops after an accepted step whose decrease is
@@ -510,7 +516,7 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     HY_TRY(upload_ops(a, st));
     double e = 0.0;
     if (bulk == HY_F64) {
-        HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.max_evals, st, &e));
+        HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.max_evals, st, &e, kStall64));
         rec->energy = rec->energy_bulk = e;
         rec->energy_bulk_err = 0.0;
     } else {
@@ -525,7 +531,7 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
             HY_TRY(energy(a, a->theta, HY_F64, st, &e64));
             rec->energy_bulk_err = std::fabs(e32 - e64);
             if (a->cfg.refine_steps > 0)
-                HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.refine_steps, st, &e64));
+                HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.refine_steps, st, &e64, kStall64));
             rec->energy = e64;
         }
     }
@@ -535,6 +541,13 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     rec->t_total = now_s() - t0 - t_judge;
     a->count[sel] += 1.0f;
     ++a->iter;
+    return HY_OK;
+}
+
+hy_status hy_adapt_set_judge(hy_adapt *a, int judge)
+{
+    if (!a) return set_err(HY_ERR_ARG, "NULL argument");
+    a->cfg.judge = judge ? 1 : 0;
     return HY_OK;
 }
 
@@ -560,7 +573,7 @@ hy_status hy_adapt_refine(hy_adapt *a, int steps, double *e, void *stream)
     HY_TRY(upload_ops(a, st));
     double e64 = 0.0;
     if (steps > 0)
-        HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, steps, st, &e64));
+        HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, steps, st, &e64, kStall64));
     else
         HY_TRY(energy(a, a->theta, HY_F64, st, &e64));
     *e = e64;

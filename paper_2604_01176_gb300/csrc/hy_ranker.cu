@@ -263,7 +263,8 @@ __global__ void k_gather_rows(const float *__restrict__ X, const int32_t *__rest
     out[t] = X[size_t(idx[r]) * F + c];
 }
 
-// target t_k = log10(|g_k| / max |g| + 1e-12), max over the m entries; one CTA
+// target t_k = log10(|g_k| / max |g| + 1e-6), max over the m entries; one CTA
+// (the floor keeps the fit on the operators that can compete for the top)
 __global__ void __launch_bounds__(1024)
 k_targets(const double *__restrict__ g, int64_t m, float *__restrict__ t)
 {
@@ -278,7 +279,7 @@ k_targets(const double *__restrict__ g, int64_t m, float *__restrict__ t)
     }
     const double M = red[0] > 0.0 ? red[0] : 1.0;
     for (int64_t i = threadIdx.x; i < m; i += blockDim.x)
-        t[i] = float(log10(fabs(g[i]) / M + 1e-12));
+        t[i] = float(log10(fabs(g[i]) / M + 1e-6));
 }
 
 // top-k of m <= kTopKMax scores (descending; ties to the lower index) by a

@@ -346,35 +346,39 @@ cudaError_t coupling(const CouplingArgs<T> &a, int num_sms, cudaStream_t st)
 // of output alpha row a_m = the m-th single-excitation partner of J
 // (V[q][p][t] with J's entry (p, q), times its sign), or for m = nexa the
 // diagonal coefficient sum_{p in J} V[p][p][t].  This is a dense product of
-// a (nexa+1) x n^2 by an n^2 x N_beta matrix, tiled 80 x 64 with 5 x 4
+// a (nexa+1) x n^2 by an n^2 x N_beta matrix, tiled 72 x 128 with 8 x 4
 // outputs per thread; each gathered amplitude is reused by all 65 output
-// rows and each coefficient by every column.
+// rows and each coefficient by every column.  Type rows that are zero for
+// every column of a tile (no string of the tile holds r, or every string
+// holds s) are skipped: the active set is taken from the OR / AND of the
+// tile's beta strings.
 //
 // Phase B, per output alpha row a' (one CTA, grid-stride):
 //   sigma[a'][b'] += T[a'][nexa][b'] + sum_e T[J_e][inv_e][b']
 // where inv_e is the position of a' in the partner list of J_e; 65 coalesced
 // row reads per output row, no atomics, fixed summation order.
 // ---------------------------------------------------------------------------
-constexpr int kDM = 80, kDN = 64;
+constexpr int kGM = 72, kGN = 128, kGThreads = 288;
 
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kGThreads, 1)
 k_cpl_gemm(CplDenseArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t Nb = a.Nb;
     const int n = a.n, nn = n * n, nexa = a.nexa, nexb = a.nexb;
     const int slots = nexa + 1;
-    float *row = reinterpret_cast<float *>(smem_raw);
-    float *W = row + (Nb + 3) / 4 * 4;                  // [nn][kDM]
-    float *G = W + size_t(nn) * kDM;                    // [nn][kDN], 16-byte aligned
-    const int tid = threadIdx.x, mg = tid >> 4, ng = tid & 15;
+    float *W = reinterpret_cast<float *>(smem_raw);             // [nn][kGM]
+    float *G = W + size_t(nn) * kGM;                            // [active][kGN]
+    int16_t *act = reinterpret_cast<int16_t *>(G + size_t(nn) * kGN);   // [nn]
+    int16_t *pos = act + 256;                                   // [nn] type -> row of G
+    int *misc = reinterpret_cast<int *>(pos + 256);             // or, and, n_active, warp counts[9]
+    const int tid = threadIdx.x, mg = tid >> 5, ng = tid & 31;
     for (int64_t J = blockIdx.x; J < a.Na; J += gridDim.x) {
         __syncthreads();
         const float *src = a.psi + J * Nb;
-        for (int64_t b = tid; b < Nb; b += blockDim.x) row[b] = src[b];
         const uint32_t jm = a.astr[J];
-        for (int idx = tid; idx < nn * kDM; idx += blockDim.x) {
-            const int t = idx / kDM, m = idx % kDM;
+        for (int idx = tid; idx < nn * kGM; idx += blockDim.x) {
+            const int t = idx / kGM, m = idx % kGM;
             float v = 0.0f;
             if (m < nexa) {
                 const uint32_t u = a.aex[J * nexa + m];
@@ -389,53 +393,98 @@ k_cpl_gemm(CplDenseArgs a)
             }
             W[idx] = v;
         }
-        for (int64_t b0 = 0; b0 < Nb; b0 += kDN) {
-            __syncthreads();          // W / row ready; previous tile's G consumed
-            for (int idx = tid; idx < nn * kDN; idx += blockDim.x) G[idx] = 0.0f;
+        for (int64_t b0 = 0; b0 < Nb; b0 += kGN) {
+            __syncthreads();   // W ready; previous tile's G and lists consumed
+            if (tid == 0) {
+                misc[0] = 0;
+                misc[1] = int(0xFFFFFFFFu >> (32 - n));
+            }
             __syncthreads();
-            for (int idx = tid; idx < kDN * (nexb + n); idx += blockDim.x) {
-                const int nl = idx % kDN, f = idx / kDN;
+            if (tid < kGN && b0 + tid < Nb) {
+                const int m = int(a.bstr[b0 + tid]);
+                atomicOr(&misc[0], m);
+                atomicAnd(&misc[1], m);
+            }
+            __syncthreads();
+            // active superset: (r, r) with r in OR; (r, s) with r in OR, s not in AND
+            const uint32_t om = uint32_t(misc[0]), am = uint32_t(misc[1]);
+            int flag = 0, t = tid;
+            if (t < nn) {
+                const int r = t / n, s2 = t % n;
+                flag = ((om >> r) & 1u) && (r == s2 || !((am >> s2) & 1u));
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, flag);
+            if ((tid & 31) == 0) misc[3 + mg] = __popc(bal);
+            __syncthreads();
+            if (t < nn) {
+                int base = 0;
+                for (int w = 0; w < mg; ++w) base += misc[3 + w];
+                const int p = base + __popc(bal & ((1u << (tid & 31)) - 1u));
+                pos[t] = flag ? int16_t(p) : int16_t(-1);
+                if (flag) act[p] = int16_t(t);
+                if (tid == nn - 1) misc[2] = p + flag;
+            }
+            __syncthreads();
+            const int na = misc[2];
+            for (int idx = tid; idx < na * kGN; idx += blockDim.x) G[idx] = 0.0f;
+            __syncthreads();
+            for (int idx = tid; idx < kGN * (nexb + n); idx += blockDim.x) {
+                const int nl = idx % kGN, f = idx / kGN;
                 const int64_t b = b0 + nl;
                 if (b >= Nb) continue;
                 if (f < nexb) {
                     const uint32_t u = a.bexT[size_t(f) * Nb + b];
                     const int r = (u >> 16) & 15, sv = (u >> 20) & 15;
-                    const float v = row[u & 0xFFFFu];
-                    G[(r * n + sv) * kDN + nl] = (u >> 31) ? -v : v;
+                    const float v = __ldg(src + (u & 0xFFFFu));
+                    G[pos[r * n + sv] * kGN + nl] = (u >> 31) ? -v : v;
                 } else {
                     const int r = f - nexb;
-                    if ((a.bstr[b] >> r) & 1u) G[(r * n + r) * kDN + nl] = row[b];
+                    if ((a.bstr[b] >> r) & 1u) G[pos[r * n + r] * kGN + nl] = __ldg(src + b);
                 }
             }
             __syncthreads();
-            float acc[5][4];
+            float acc[8][4];
 #pragma unroll
-            for (int i = 0; i < 5; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-            const float *wp = W + mg * 5;
+            const float *wp = W + mg * 8;
             const float *gp = G + ng * 4;
-#pragma unroll 4
-            for (int t = 0; t < nn; ++t) {
-                const float4 g = *reinterpret_cast<const float4 *>(gp + t * kDN);
-                const float *wt = wp + t * kDM;
-#pragma unroll
-                for (int i = 0; i < 5; ++i) {
-                    const float w = wt[i];
-                    acc[i][0] += w * g.x;
-                    acc[i][1] += w * g.y;
-                    acc[i][2] += w * g.z;
-                    acc[i][3] += w * g.w;
-                }
+            // operands of the next active type are loaded while the current
+            // one is multiplied (register double buffering)
+            float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), w1 = w0, g = w0;
+            if (na > 0) {
+                const int tt = act[0];
+                w0 = *reinterpret_cast<const float4 *>(wp + tt * kGM);
+                w1 = *reinterpret_cast<const float4 *>(wp + tt * kGM + 4);
+                g = *reinterpret_cast<const float4 *>(gp);
             }
+            for (int ai = 0; ai < na; ++ai) {
+                float4 nw0 = w0, nw1 = w1, ngv = g;
+                if (ai + 1 < na) {
+                    const int tn = act[ai + 1];
+                    nw0 = *reinterpret_cast<const float4 *>(wp + tn * kGM);
+                    nw1 = *reinterpret_cast<const float4 *>(wp + tn * kGM + 4);
+                    ngv = *reinterpret_cast<const float4 *>(gp + (ai + 1) * kGN);
+                }
+                const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                const int m = mg * 5 + i;
-                if (m >= slots) continue;
-                const int64_t b = b0 + ng * 4;
-                float *dst = a.T + (J * slots + m) * a.Nbp + b;
-                if (b + 3 < a.Nbp)
-                    *reinterpret_cast<float4 *>(dst) =
+                for (int i = 0; i < 8; ++i) {
+                    acc[i][0] += w[i] * g.x;
+                    acc[i][1] += w[i] * g.y;
+                    acc[i][2] += w[i] * g.z;
+                    acc[i][3] += w[i] * g.w;
+                }
+                w0 = nw0;
+                w1 = nw1;
+                g = ngv;
+            }
+            const int64_t b = b0 + ng * 4;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int m = mg * 8 + i;
+                if (m < slots && b + 3 < a.Nbp)
+                    *reinterpret_cast<float4 *>(a.T + (J * slots + m) * a.Nbp + b) =
                         make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
             }
         }
@@ -462,24 +511,27 @@ k_cpl_gather(CplDenseArgs a)
 
 size_t cpl_dense_smem(int64_t Nb, int n)
 {
-    return (size_t((Nb + 3) / 4 * 4) + size_t(n) * n * (kDM + kDN)) * sizeof(float);
+    (void)Nb;
+    // W [n^2][72] + G [n^2][128] floats, type lists 2 x 256 int16, 16 ints
+    return size_t(n) * n * (kGM + kGN) * sizeof(float) + 2 * 256 * sizeof(int16_t) +
+           16 * sizeof(int);
 }
 
 cudaError_t coupling_dense(const CplDenseArgs &a, int num_sms, cudaStream_t st)
 {
     if (a.Na == 0 || a.Nb == 0) return cudaSuccess;
-    if (a.nexa + 1 > kDM) return cudaErrorInvalidValue;
+    if (a.nexa + 1 > kGM) return cudaErrorInvalidValue;
     const size_t smem = cpl_dense_smem(a.Nb, a.n);
     cudaError_t err = cudaFuncSetAttribute(k_cpl_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            int(smem));
     if (err != cudaSuccess) return err;
     int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpl_gemm, 256, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpl_gemm, kGThreads, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = int64_t(num_sms) * per_sm;
     if (grid > a.Na) grid = a.Na;
-    k_cpl_gemm<<<unsigned(grid), 256, smem, st>>>(a); hy::count_launch();
+    k_cpl_gemm<<<unsigned(grid), kGThreads, smem, st>>>(a); hy::count_launch();
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     int64_t g2 = int64_t(num_sms) * 8;

@@ -133,8 +133,8 @@ def test_mlp_forward_and_first_adam_step():
     layers = [(torch.from_numpy(W.copy()), torch.from_numpy(b.copy())) for W, b in unpack(w0, F, H)]
     ref_pred = torch_forward(layers, torch.from_numpy(X)).numpy()
     assert np.abs(pred - ref_pred).max() < 1e-4 * max(1.0, np.abs(ref_pred).max())
-    # targets as defined: log10(|g| / max|g| + 1e-12)
-    t = np.log10(np.abs(g) / np.abs(g).max() + 1e-12).astype(np.float32)
+    # targets as defined: log10(|g| / max|g| + 1e-6)
+    t = np.log10(np.abs(g) / np.abs(g).max() + 1e-6).astype(np.float32)
     r.add_samples(torch.from_numpy(X).cuda(), torch.from_numpy(g).cuda())
     r.fit(epochs=1, batch=m, lr=1e-3, seed=5)
     w1 = r.params()
