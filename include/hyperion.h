@@ -293,6 +293,15 @@ hy_status hy_batch_tune(hy_batch *b, const void *psi, void *sigma, hy_dtype dt,
 hy_status hy_occupations(const hy_ham *h, const void *psi, hy_dtype dt,
                          float *occ, void *stream);
 
+/* Weights of the state on the determinants an excitation touches:
+ * D[(i*n+a)*n*n + j*n+b] (device, n^4 floats) = sum over determinants with
+ * i occupied and a empty in the alpha string and j occupied and b empty in
+ * the beta string of |psi|^2, where i == a (j == b) drops the alpha (beta)
+ * condition; D[0] = <psi|psi>.  Two passes: per alpha string the beta
+ * pair weights, then their contraction over alpha strings. */
+hy_status hy_touched_weights(const hy_ham *h, const void *psi, hy_dtype dt,
+                             float *D, void *stream);
+
 /* The ranker is an addition with no counterpart in the paper's method: a
  * small MLP that predicts, per pool operator, t_k = log10(|g_k| / max|g| +
  * 1e-6) from 16 features, so that only its top-M operators are screened
@@ -301,15 +310,21 @@ hy_status hy_occupations(const hy_ham *h, const void *psi, hy_dtype dt,
  * double, extra constituents); [4..7] annihilated and created spatial
  * orbitals / n_orb (-0.1 where absent); [8] log10 |integral| (h_ca for
  * singles, (c0 a0|c1 a1) minus exchange for same spin); [9] diagonal
- * one-electron gap; [10] product of occupations n_a0 n_a1 (1-n_c0)(1-n_c1)
- * of psi, the weight of determinants the operator acts on under a
- * mean-field estimate; [11] n_a0 + n_a1 - n_c0 - n_c1; [12..15] the caller's
- * extra[k][0..3] (the driver passes the stale log10 |g_k| / max, its age,
- * the operator's count in the ansatz and its summed |theta|), or 0.
- * feat: device, K x 16 floats; extra: device K x 4 floats or NULL. */
+ * one-electron gap; [10], [11] with sigma given: log10 of the
+ * Cauchy-Schwarz bound 2 sum_c (|sigma_img| |psi_dom| + |sigma_dom|
+ * |psi_img|) / (|sigma| |psi|) over the operator's constituents c, and
+ * log10 of the state weight on the touched determinants sum_c (|psi_dom|^2
+ * + |psi_img|^2) / |psi|^2 (exact for singles and opposite-spin doubles,
+ * geometric mean of the two pair weights for same-spin doubles) -- without
+ * sigma: the mean-field occupation product n_a0 n_a1 (1-n_c0)(1-n_c1) and
+ * n_a0 + n_a1 - n_c0 - n_c1; [12..15] the caller's extra[k][0..3] (the
+ * driver passes the stale log10 |g_k| / max, its age, the operator's count
+ * in the ansatz and its summed |theta|), or 0.
+ * feat: device, K x 16 floats; extra: device K x 4 floats or NULL;
+ * sigma_or_null: H psi in dt, or NULL. */
 hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
-                             hy_dtype dt, const float *extra, float *feat,
-                             void *stream);
+                             const void *sigma_or_null, hy_dtype dt,
+                             const float *extra, float *feat, void *stream);
 
 /* MLP 16 -> hidden -> hidden -> hidden -> 1 (ReLU), FP32, He-uniform init
  * from `seed` (SplitMix64).  The ranker owns its device parameters, Adam

@@ -22,7 +22,7 @@ from . import _abi
 from ._abi import HY_F32, HY_F64, HyError, check
 
 __all__ = ["Hamiltonian", "Pool", "Adapt", "Ranker", "Batch", "HyError", "dtype_code",
-           "stream_ptr", "occupations", "ranker_features", "topk"]
+           "stream_ptr", "occupations", "ranker_features", "touched_weights", "topk"]
 
 N_FEATURES = 16
 
@@ -389,18 +389,34 @@ def occupations(ham: Hamiltonian, psi: torch.Tensor, stream=None) -> torch.Tenso
 
 
 def ranker_features(ham: Hamiltonian, pool: Pool, psi: torch.Tensor,
-                    extra: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+                    extra: torch.Tensor | None = None, sigma: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
     """Per-operator ranker features, (K, 16) float32 on the device."""
-    ham._check_state(psi)
+    ham._check_state(psi, sigma)
     out = torch.empty((len(pool), N_FEATURES), dtype=torch.float32, device=psi.device)
     if extra is not None:
         _require_cuda(extra)
         if extra.dtype != torch.float32 or extra.shape != (len(pool), 4):
             raise ValueError("extra must be float32 of shape (K, 4)")
+    if sigma is not None and sigma.dtype != psi.dtype:
+        raise TypeError("psi and sigma must share a dtype")
     check(_abi.load().hy_ranker_features(
-        ham.handle, pool.handle, _ptr(psi), dtype_code(psi.dtype),
-        _ptr(extra) if extra is not None else None, _ptr(out), stream_ptr(stream)))
+        ham.handle, pool.handle, _ptr(psi), _ptr(sigma) if sigma is not None else None,
+        dtype_code(psi.dtype), _ptr(extra) if extra is not None else None, _ptr(out),
+        stream_ptr(stream)))
     return out
+
+
+def touched_weights(ham: Hamiltonian, psi: torch.Tensor, stream=None) -> torch.Tensor:
+    """D[(i,a), (j,b)]: weight of |psi|^2 on determinants with i in / a out of
+    the alpha string and j in / b out of the beta string (i == a or j == b:
+    no condition), shape (n*n, n*n)."""
+    ham._check_state(psi)
+    n = ham.n_orb
+    out = torch.empty(n ** 4, dtype=torch.float32, device=psi.device)
+    check(_abi.load().hy_touched_weights(ham.handle, _ptr(psi), dtype_code(psi.dtype),
+                                         _ptr(out), stream_ptr(stream)))
+    return out.view(n * n, n * n)
 
 
 def topk(scores: torch.Tensor, k: int, stream=None) -> torch.Tensor:

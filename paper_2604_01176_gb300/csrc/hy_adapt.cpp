@@ -442,7 +442,7 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         HY_TRY(full_screen());
         pick(all, g);
         if (ranked) {
-            HY_TRY(hy_ranker_features(a->h, a->p, psi, bulk, a->d_extra, a->d_feat, st));
+            HY_TRY(hy_ranker_features(a->h, a->p, psi, sigma, bulk, a->d_extra, a->d_feat, st));
             HY_TRY(hy_ranker_add_samples(a->ranker, a->d_feat, a->d_g, a->K, st));
             if (a->iter + 1 == a->warm_iters)
                 HY_TRY(hy_ranker_fit(a->ranker, a->epochs, 256, 1e-3f, 1234 + a->iter, nullptr, st));
@@ -453,7 +453,7 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         note_screen(a, all, g);
     } else {
         const int64_t M = std::min<int64_t>(a->cfg.screen_top_m, a->K);
-        HY_TRY(hy_ranker_features(a->h, a->p, psi, bulk, a->d_extra, a->d_feat, st));
+        HY_TRY(hy_ranker_features(a->h, a->p, psi, sigma, bulk, a->d_extra, a->d_feat, st));
         HY_TRY(hy_ranker_predict(a->ranker, a->d_feat, a->K, a->d_score, st));
         HY_TRY(hy_ranker_topk(a->d_score, a->K, M, a->d_prop, st));
         HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, a->d_prop, M, a->d_gp, bulk, st));

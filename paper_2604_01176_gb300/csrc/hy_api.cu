@@ -94,6 +94,9 @@ struct hy_ham {
     double *d_h1 = nullptr, *d_eri = nullptr;   // integrals (ranker features)
     double *d_occ_partial = nullptr;            // [occ_blocks][33]
     float *d_occ = nullptr;                     // [2n]
+    float *d_pairB = nullptr;                   // [2][Na][n^2] touched-weight partials
+    float *d_pairRs = nullptr;                  // [2][Na]
+    float *d_pairD = nullptr;                   // [2][n^4] touched weights (psi, sigma)
     int occ_blocks = 0;
     // workspace (grown on demand; growth synchronises the device)
     void *ws = nullptr;
@@ -500,6 +503,12 @@ hy_status hy_build_hamiltonian(const double *h1, const double *h2, double e_core
         std::vector<float> zo(size_t(2 * n_orb), 0.0f);
         up(ar.upload(&h->d_occ_partial, zp.data(), zp.size()), "occupation partials");
         up(ar.upload(&h->d_occ, zo.data(), zo.size()), "occupations");
+        const size_t nn = size_t(n_orb) * n_orb;
+        std::vector<float> zb(2 * size_t(h->Na) * nn, 0.0f), zr(2 * size_t(h->Na), 0.0f),
+            zd(2 * nn * nn, 0.0f);
+        up(ar.upload(&h->d_pairB, zb.data(), zb.size()), "touched-weight partials");
+        up(ar.upload(&h->d_pairRs, zr.data(), zr.size()), "touched-weight partials");
+        up(ar.upload(&h->d_pairD, zd.data(), zd.size()), "touched weights");
     }
     if (s == HY_OK) s = upload_csr<double>(ar, h->kt.Ma, h->Ma64);
     if (s == HY_OK) s = upload_csr<double>(ar, h->kt.Mb, h->Mb64);
@@ -883,12 +892,27 @@ hy_status hy_apply_excitation(const hy_ham *hc, const hy_pool *p, int64_t k,
     return s;
 }
 
-hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi, hy_dtype dt,
-                             const float *extra, float *feat, void *stream)
+hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
+                             const void *sigma_or_null, hy_dtype dt, const float *extra,
+                             float *feat, void *stream)
 {
     if (!h || !p || !psi || !feat || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
     if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
     cudaStream_t st = as_stream(stream);
+    const size_t nn = size_t(h->n) * h->n;
+    const void *vecs[2] = {psi, sigma_or_null};
+    for (int v = 0; v < 2 && vecs[v]; ++v) {
+        float *B = h->d_pairB + size_t(v) * h->Na * nn, *rs = h->d_pairRs + size_t(v) * h->Na;
+        float *D = h->d_pairD + size_t(v) * nn * nn;
+        if (dt == HY_F64)
+            HY_CUDA(hy::k::touched_weights<double>(static_cast<const double *>(vecs[v]), h->Na,
+                                                   h->Nb, h->d_astr, h->d_bstr, h->n, B, rs, D,
+                                                   h->num_sms, st), "touched weights");
+        else
+            HY_CUDA(hy::k::touched_weights<float>(static_cast<const float *>(vecs[v]), h->Na,
+                                                  h->Nb, h->d_astr, h->d_bstr, h->n, B, rs, D,
+                                                  h->num_sms, st), "touched weights");
+    }
     if (dt == HY_F64)
         HY_CUDA(hy::k::occupations<double>(static_cast<const double *>(psi), h->Na, h->Nb,
                                            h->d_astr, h->d_bstr, h->n, h->d_occ_partial,
@@ -897,8 +921,26 @@ hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
         HY_CUDA(hy::k::occupations<float>(static_cast<const float *>(psi), h->Na, h->Nb,
                                           h->d_astr, h->d_bstr, h->n, h->d_occ_partial,
                                           h->occ_blocks, h->d_occ, st), "occupations");
+    const float *Dp = sigma_or_null ? h->d_pairD : nullptr;
+    const float *Ds = sigma_or_null ? h->d_pairD + nn * nn : nullptr;
     HY_CUDA(hy::k::features(p->d_desc, int64_t(p->ops.size()), h->n, h->d_h1, h->d_eri,
-                            h->d_occ, extra, feat, st), "features");
+                            h->d_occ, extra, Dp, Ds, feat, st), "features");
+    return HY_OK;
+}
+
+hy_status hy_touched_weights(const hy_ham *h, const void *psi, hy_dtype dt, float *D,
+                             void *stream)
+{
+    if (!h || !psi || !D || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
+    cudaStream_t st = as_stream(stream);
+    if (dt == HY_F64)
+        HY_CUDA(hy::k::touched_weights<double>(static_cast<const double *>(psi), h->Na, h->Nb,
+                                               h->d_astr, h->d_bstr, h->n, h->d_pairB,
+                                               h->d_pairRs, D, h->num_sms, st), "touched weights");
+    else
+        HY_CUDA(hy::k::touched_weights<float>(static_cast<const float *>(psi), h->Na, h->Nb,
+                                              h->d_astr, h->d_bstr, h->n, h->d_pairB,
+                                              h->d_pairRs, D, h->num_sms, st), "touched weights");
     return HY_OK;
 }
 

@@ -99,8 +99,12 @@ cudaError_t occupations(const T *psi, int64_t Na, int64_t Nb, const uint32_t *as
                         const uint32_t *bstr, int n, double *partial, int G, float *out,
                         cudaStream_t st);
 cudaError_t features(const int32_t *desc, int64_t K, int n, const double *h1,
-                     const double *eri, const float *occ, const float *extra, float *feat,
-                     cudaStream_t st);
+                     const double *eri, const float *occ, const float *extra, const float *Dpsi,
+                     const float *Dsig, float *feat, cudaStream_t st);
+template <typename T>
+cudaError_t touched_weights(const T *psi, int64_t Na, int64_t Nb, const uint32_t *astr,
+                            const uint32_t *bstr, int n, float *Bw, float *rs, float *D,
+                            int num_sms, cudaStream_t st);
 
 // batched rows over many molecules (hy_batch.cu)
 template <typename T>

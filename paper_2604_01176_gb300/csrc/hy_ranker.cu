@@ -93,12 +93,120 @@ cudaError_t occupations(const T *psi, int64_t Na, int64_t Nb, const uint32_t *as
 }
 
 // ---------------------------------------------------------------------------
+// Weights of the state on the determinants an operator touches.
+//   Bw[a][j*n+b] = sum_beta w(a, beta) [j in beta][b in beta],  w = psi^2
+//   (or sigma^2), rs[a] = sum_beta w(a, beta)
+// then
+//   D[(i,a)][(j,b)] = sum_alpha [i in alpha][a not in alpha] *
+//                     sum_beta w [j in beta][b not in beta]
+// with i == a (j == b) meaning "no condition on the alpha (beta) string".
+// The inner beta sum for j != b is Bw[.][j*n+j] - Bw[.][j*n+b].
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_pair_weights(const T *__restrict__ psi, int64_t Na, int64_t Nb,
+               const uint32_t *__restrict__ bstr, int n, float *__restrict__ Bw,
+               float *__restrict__ rs)
+{
+    extern __shared__ float wsh[];     // [Nb]
+    __shared__ float red[256];
+    const int nn = n * n, t = threadIdx.x;
+    const int j = t < nn ? t / n : 0, b = t < nn ? t % n : 0;
+    for (int64_t a = blockIdx.x; a < Na; a += gridDim.x) {
+        __syncthreads();
+        float part = 0.0f;
+        for (int64_t c = t; c < Nb; c += blockDim.x) {
+            const float v = float(psi[a * Nb + c]);
+            wsh[c] = v * v;
+            part += v * v;
+        }
+        red[t] = part;
+        __syncthreads();
+        for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+            if (t < st) red[t] += red[t + st];
+            __syncthreads();
+        }
+        if (t == 0) rs[a] = red[0];
+        if (t < nn) {
+            float acc = 0.0f;
+            const uint32_t sel = (1u << j) | (1u << b);
+            for (int64_t c = 0; c < Nb; ++c)
+                if ((__ldg(bstr + c) & sel) == sel) acc += wsh[c];
+            Bw[a * nn + t] = acc;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_pair_contract(const float *__restrict__ Bw, const float *__restrict__ rs,
+                const uint32_t *__restrict__ astr, int64_t Na, int n, float *__restrict__ D)
+{
+    const int nn = n * n;
+    const int64_t id = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (id >= int64_t(nn) * nn) return;
+    const int ia = int(id / nn), jb = int(id % nn);
+    const int i = ia / n, aa = ia % n, j = jb / n, b = jb % n;
+    double acc = 0.0;
+    for (int64_t al = 0; al < Na; ++al) {
+        const uint32_t m = astr[al];
+        if (i != aa && !(((m >> i) & 1u) && !((m >> aa) & 1u))) continue;
+        acc += (j == b) ? rs[al] : (Bw[al * nn + j * n + j] - Bw[al * nn + j * n + b]);
+    }
+    D[id] = float(acc);
+}
+
+template <typename T>
+cudaError_t touched_weights(const T *psi, int64_t Na, int64_t Nb, const uint32_t *astr,
+                            const uint32_t *bstr, int n, float *Bw, float *rs, float *D,
+                            int num_sms, cudaStream_t st)
+{
+    const size_t smem = size_t(Nb) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_pair_weights<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    int64_t g = int64_t(num_sms) * 2;
+    if (g > Na) g = Na;
+    k_pair_weights<T><<<unsigned(g), 256, smem, st>>>(psi, Na, Nb, bstr, n, Bw, rs); hy::count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t tot = int64_t(n) * n * n * n;
+    k_pair_contract<<<unsigned((tot + 255) / 256), 256, 0, st>>>(Bw, rs, astr, Na, n, D); hy::count_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t touched_weights<double>(const double *, int64_t, int64_t, const uint32_t *,
+                                             const uint32_t *, int, float *, float *, float *,
+                                             int, cudaStream_t);
+template cudaError_t touched_weights<float>(const float *, int64_t, int64_t, const uint32_t *,
+                                            const uint32_t *, int, float *, float *, float *,
+                                            int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
 // per-operator features (kRankerFeatures floats per operator)
 // ---------------------------------------------------------------------------
+// weight of one constituent's domain (x annihilated present, y created
+// absent) from the touched-weight tensor D; nap / nbp alpha / beta pairs
+__device__ float touched(const float *D, int n, int nap, const int *ax, const int *ay, int nbp,
+                         const int *bx, const int *by)
+{
+    const int nn = n * n;
+    if (nap <= 1 && nbp <= 1) {
+        const int ia = nap ? ax[0] * n + ay[0] : 0, jb = nbp ? bx[0] * n + by[0] : 0;
+        return fmaxf(D[ia * nn + jb], 0.0f);
+    }
+    if (nap == 2 && nbp == 0)
+        return sqrtf(fmaxf(D[(ax[0] * n + ay[0]) * nn], 0.0f) *
+                     fmaxf(D[(ax[1] * n + ay[1]) * nn], 0.0f));
+    if (nbp == 2 && nap == 0)
+        return sqrtf(fmaxf(D[bx[0] * n + by[0]], 0.0f) * fmaxf(D[bx[1] * n + by[1]], 0.0f));
+    return 0.0f;
+}
+
 __global__ void __launch_bounds__(128)
 k_features(const int32_t *__restrict__ desc, int64_t K, int n, const double *__restrict__ h1,
            const double *__restrict__ eri, const float *__restrict__ occ,
-           const float *__restrict__ extra, float *__restrict__ feat)
+           const float *__restrict__ extra, const float *__restrict__ Dpsi,
+           const float *__restrict__ Dsig, float *__restrict__ feat)
 {
     const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (k >= K) return;
@@ -137,6 +245,32 @@ k_features(const int32_t *__restrict__ desc, int64_t K, int n, const double *__r
     const float na1 = single ? 1.0f : occ[a1], nc1 = single ? 0.0f : occ[c1];
     f[10] = na0 * na1 * (1.0f - nc0) * (1.0f - nc1);
     f[11] = na0 + na1 - nc0 - nc1;
+    if (Dpsi && Dsig) {
+        // Cauchy-Schwarz bound on |g_k| over its constituents' pairs:
+        // 2 (|sigma_img| |psi_dom| + |sigma_dom| |psi_img|), relative to
+        // |sigma| |psi|, and the state weight on the touched determinants
+        float bound = 0.0f, wsum = 0.0f;
+        for (int c = 0; c < nc; ++c) {
+            const int32_t *q = d + 1 + 5 * c;
+            const int modes_c[2] = {q[1], q[2]}, modes_a[2] = {q[4], q[3]};
+            const int nm = q[0];
+            int ax[2], ay[2], bx[2], by[2], nap = 0, nbp = 0;
+            for (int u = 0; u < nm; ++u) {
+                const int x = modes_a[u], y = modes_c[u];
+                if (x < n) { ax[nap] = x; ay[nap] = y; ++nap; }
+                else { bx[nbp] = x - n; by[nbp] = y - n; ++nbp; }
+            }
+            const float dp = touched(Dpsi, n, nap, ax, ay, nbp, bx, by);
+            const float ip = touched(Dpsi, n, nap, ay, ax, nbp, by, bx);
+            const float ds = touched(Dsig, n, nap, ax, ay, nbp, bx, by);
+            const float is = touched(Dsig, n, nap, ay, ax, nbp, by, bx);
+            bound += 2.0f * (sqrtf(dp * is) + sqrtf(ip * ds));
+            wsum += dp + ip;
+        }
+        const float np2 = fmaxf(Dpsi[0], 1e-30f), ns2 = fmaxf(Dsig[0], 1e-30f);
+        f[10] = log10f(bound / sqrtf(np2 * ns2) + 1e-12f);
+        f[11] = log10f(wsum / np2 + 1e-12f);
+    }
     if (extra)
         for (int i = 0; i < 4; ++i) f[12 + i] = extra[4 * k + i];
     float *o = feat + kRankerFeatures * k;
@@ -144,12 +278,12 @@ k_features(const int32_t *__restrict__ desc, int64_t K, int n, const double *__r
 }
 
 cudaError_t features(const int32_t *desc, int64_t K, int n, const double *h1,
-                     const double *eri, const float *occ, const float *extra, float *feat,
-                     cudaStream_t st)
+                     const double *eri, const float *occ, const float *extra, const float *Dpsi,
+                     const float *Dsig, float *feat, cudaStream_t st)
 {
     if (K == 0) return cudaSuccess;
-    k_features<<<unsigned((K + 127) / 128), 128, 0, st>>>(desc, K, n, h1, eri, occ, extra,
-                                                          feat); hy::count_launch();
+    k_features<<<unsigned((K + 127) / 128), 128, 0, st>>>(desc, K, n, h1, eri, occ, extra, Dpsi,
+                                                          Dsig, feat); hy::count_launch();
     return cudaGetLastError();
 }
 

@@ -102,6 +102,46 @@ def test_features_match_definition():
     assert np.all(f0[:, 12:] == 0)
 
 
+def test_touched_weights_brute_force():
+    import paper_2604_01176_gb300 as hy
+    ref, ham, pool, _, _ = make(6, 3, 2, 21)
+    psi = synth.random_state(ref.n_det, 4, normalise=False)
+    n = 6
+    D = hy.touched_weights(ham, torch.from_numpy(psi).cuda()).cpu().numpy()
+    dets = ref.dets()
+    w = psi ** 2
+    al = np.array([int(d) & ((1 << n) - 1) for d in dets])
+    be = np.array([int(d) >> n for d in dets])
+    exp = np.zeros((n * n, n * n))
+    for i in range(n):
+        for a in range(n):
+            ca = np.ones(len(dets), bool) if i == a else ((al >> i) & 1 == 1) & ((al >> a) & 1 == 0)
+            for j in range(n):
+                for b in range(n):
+                    cb = np.ones(len(dets), bool) if j == b else ((be >> j) & 1 == 1) & ((be >> b) & 1 == 0)
+                    exp[i * n + a, j * n + b] = w[ca & cb].sum()
+    assert abs(D[0, 0] - w.sum()) < 1e-5 * w.sum()
+    assert np.abs(D - exp).max() < 1e-5 * w.sum()
+
+
+def test_gradient_bound_feature_is_an_upper_bound():
+    """Feature 10 with sigma given is log10 of an upper bound on |g_k| / (|sigma||psi|)."""
+    import paper_2604_01176_gb300 as hy
+    ref, ham, pool, _, _ = make(8, 4, 4, 1005)
+    opd = ref.pool()
+    psi = ref.hf_state()
+    for k, t in [(0, 0.4), (len(opd) - 1, -0.7), (100, 0.2), (40, 0.3)]:
+        psi = ref.apply_excitation(opd[k], t, psi)
+    sig = ref.sigma(psi)
+    g = ref.gradients(opd, psi, sig)
+    P, S = torch.from_numpy(psi).cuda(), torch.from_numpy(sig).cuda()
+    f = hy.ranker_features(ham, pool, P, sigma=S).cpu().numpy().astype(np.float64)
+    bound = (10.0 ** f[:, 10] - 1e-12) * np.linalg.norm(psi) * np.linalg.norm(sig)
+    assert np.all(np.abs(g) <= bound * (1 + 1e-4) + 1e-9)
+    top = int(np.argmax(np.abs(g)))
+    assert f[top, 10] > np.median(f[:, 10])
+
+
 def unpack(w, F, H):
     out, o = [], 0
     for fin, fout in [(F, H), (H, H), (H, H), (H, 1)]:
