@@ -70,7 +70,70 @@ def parse():
                     help="plain FP64 ADAPT vs mixed+ranker ADAPT with the full screen as judge: "
                          "per-iteration rank of the true argmax and energy gap")
     ap.add_argument("--iters", type=int, default=12, help="iterations of --ranker-eval")
+    ap.add_argument("--batch", action="store_true",
+                    help="64 molecules of 8-12 orbitals: H psi + energies of all in one persistent "
+                         "graph-captured launch (autotuned tile) vs one launch sequence per molecule")
     return ap.parse_args()
+
+
+def batch_bench(args, count=64, reps=5):
+    """Batched sweeps over the uneven 64-molecule workload."""
+    import torch
+    import paper_2604_01176_gb300 as hy
+    from paper_2604_01176_gb300 import build as hybuild
+    hybuild.build()
+    hams = []
+    for n, na, nb, seed in synth.batch_molecules(count):
+        h1, h2, ec = synth.integrals(n, seed)
+        hams.append(hy.Hamiltonian(h1, h2, ec, n, na, nb))
+    b = hy.Batch(hams)
+    total = sum(h.n_det for h in hams)
+    out = {"batch": f"{count} molecules, n = 8..12 at half filling, seeds 2000+i",
+           "determinants": total, "tasks": b.n_tasks}
+    st = torch.cuda.current_stream()
+    for d, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(3)
+        states = [torch.randn(h.n_det, dtype=dt, device="cuda", generator=gen) for h in hams]
+        states = [x / x.norm() for x in states]
+        psi = b.pack(states, dt)
+        sig = torch.zeros_like(psi)
+        en = torch.empty(count, dtype=torch.float64, device="cuda")
+        tile, tune_ms = b.tune(psi, sig)
+        b.apply_h(psi, sig, en, graph=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        l0 = hy.launch_count()
+        ev[0].record(st)
+        for _ in range(reps):
+            b.apply_h(psi, sig, en, graph=True)
+        ev[1].record(st)
+        l1 = hy.launch_count()
+        sigs = [torch.empty_like(x) for x in states]
+        eo = [torch.empty((), dtype=torch.float64, device="cuda") for _ in hams]
+        for h, x, y, e in zip(hams, states, sigs, eo):     # warm the per-molecule path
+            h.apply_h(x, out=y)
+            h.energy(x, y, out=e)
+        torch.cuda.synchronize()
+        l2 = hy.launch_count()
+        ev[2].record(st)
+        for _ in range(reps):
+            for h, x, y, e in zip(hams, states, sigs, eo):
+                h.apply_h(x, out=y)
+                h.energy(x, y, out=e)
+        ev[3].record(st)
+        torch.cuda.synchronize()
+        l3 = hy.launch_count()
+        t_b = ev[0].elapsed_time(ev[1]) / reps
+        t_l = ev[2].elapsed_time(ev[3]) / reps
+        err = max(abs(float(en[m].item()) - float(eo[m].item())) for m in range(count))
+        out[d] = {"tile": tile, "tune_ms": round(tune_ms, 3),
+                  "batched_ms": round(t_b, 3), "looped_ms": round(t_l, 3),
+                  "speedup": round(t_l / t_b, 2),
+                  "batched_launches": (l1 - l0) // reps, "looped_launches": (l3 - l2) // reps,
+                  "molecules_per_s": round(count / (t_b / 1e3), 1),
+                  "max_energy_diff_vs_looped": err}
+    print(json.dumps(out), flush=True)
 
 
 def ranker_eval(args):
@@ -371,6 +434,8 @@ def main():
         return sweeps_only(args)
     if args.ranker_eval:
         return ranker_eval(args)
+    if args.batch:
+        return batch_bench(args)
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
