@@ -48,6 +48,10 @@ import synth  # noqa: E402
 METRIC = ("H|psi> GB/s (% of ~8 TB/s) and ADAPT iters/s at 32 qubits, "
           "plain vs mixed+ranker")
 TOP_M = 32
+# DRAM bytes per launch of the FP32 coupling (k_cpl_gemm + k_cpl_gather) at 32 q, from the ncu capture at
+# 28 q scaled by the amplitude count (traffic is proportional to it: the T intermediate is written once
+# and read once); see profiles/coupling_ab_f32_28q.md.  None until that capture matches the kernel.
+TRAFFIC_F32 = None
 REFRESH = 4        # every 4th ranked iteration selects from the full screen
 
 
@@ -329,7 +333,15 @@ def time_sweeps(ham, pool, dt, reps=3):
         pool.gradients(psi, sig, out=gr)
     e[2].record(st)
     torch.cuda.synchronize()
-    return e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+    # the dominant kernel alone: events the library records around the
+    # alpha-beta coupling launches, on the same stream
+    ham.profile_coupling(True)
+    cpl = []
+    for _ in range(reps):
+        ham.apply_h(psi, out=sig)
+        cpl.append(ham.coupling_ms())
+    ham.profile_coupling(False)
+    return e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps, statistics.mean(cpl)
 
 
 def run_ours(args, rank, world):
@@ -350,8 +362,12 @@ def run_ours(args, rank, world):
     W, S = args.warmup, args.steps
     out = dict(N=N, K=K, n=n, na=na, nb=nb, seed=seed, t_build=t_build,
                conn=ham.connections_per_det())
-    out["hpsi_ms_f64"], out["screen_ms_f64"] = time_sweeps(ham, pool, torch.float64)
-    out["hpsi_ms_f32"], out["screen_ms_f32"] = time_sweeps(ham, pool, torch.float32)
+    out["hpsi_ms_f64"], out["screen_ms_f64"], out["cpl_ms_f64"] = time_sweeps(ham, pool,
+                                                                            torch.float64)
+    out["hpsi_ms_f32"], out["screen_ms_f32"], out["cpl_ms_f32"] = time_sweeps(ham, pool,
+                                                                            torch.float32)
+    out["cpl_units"] = (ham.n_alpha * (ham.n_orb - ham.n_alpha) + 1) * \
+        (ham.n_beta * (ham.n_orb - ham.n_beta) + 1)
 
     # mixed precision + learned ranker
     cap = W + 2 * S + 6
@@ -451,6 +467,7 @@ def main():
     fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
     fp64_peak = 152 * 2 * 2 * mhz * 1e6 / 1e12
     flops = 2.0 * r["conn"] * N
+    cflops = 2.0 * r["cpl_units"] * N      # the coupling kernel's share of the connections
 
     def hp(ms, s):
         gbs = 2.0 * N * s / (ms / 1e3) / 1e9
@@ -484,15 +501,24 @@ def main():
                  "algorithmic_bytes": "2 * N_det * sizeof(amplitude)",
                  "connections_per_det": r["conn"]},
         "screen_ms": {"f64": round(r["screen_ms_f64"], 3), "f32": round(r["screen_ms_f32"], 3)},
-        "roofline": {"bound": "alu", "achieved": round(flops / (r["hpsi_ms_f32"] / 1e3) / 1e12, 4),
+        "roofline": {"bound": "alu", "achieved": round(cflops / (r["cpl_ms_f32"] / 1e3) / 1e12, 4),
                      "peak": round(fp32_peak, 3), "unit": "TFLOP/s",
-                     "frac": round(flops / (r["hpsi_ms_f32"] / 1e3) / 1e12 / fp32_peak, 4),
-                     "traffic": None, "kernel": "hy_apply_h FP32 (k_coupling dominant)",
+                     "frac": round(cflops / (r["cpl_ms_f32"] / 1e3) / 1e12 / fp32_peak, 4),
+                     "traffic": TRAFFIC_F32,
+                     "kernel": "alpha-beta coupling, FP32 (k_cpl_gemm + k_cpl_gather)",
+                     "ms_per_launch": round(r["cpl_ms_f32"], 3),
+                     "work": f"{r['cpl_units']} FMA per amplitude x {N} amplitudes",
                      "peak_kind": f"derived FP32 FMA rate: 152 SMs x 128 FMA/clk x {mhz} MHz",
-                     "f64": {"achieved": round(flops / (r["hpsi_ms_f64"] / 1e3) / 1e12, 4),
+                     "f64": {"kernel": "k_coupling<double>",
+                             "achieved": round(cflops / (r["cpl_ms_f64"] / 1e3) / 1e12, 4),
                              "peak": round(fp64_peak, 3),
-                             "frac": round(flops / (r["hpsi_ms_f64"] / 1e3) / 1e12 / fp64_peak, 4),
-                             "peak_kind": f"derived FP64 rate: 152 SMs x 2 FMA/clk x {mhz} MHz"}},
+                             "frac": round(cflops / (r["cpl_ms_f64"] / 1e3) / 1e12 / fp64_peak, 4),
+                             "ms_per_launch": round(r["cpl_ms_f64"], 3),
+                             "peak_kind": f"derived FP64 rate: 152 SMs x 2 FMA/clk x {mhz} MHz"},
+                     "whole_hpsi_frac": {"f64": round(flops / (r["hpsi_ms_f64"] / 1e3) / 1e12 /
+                                                      fp64_peak, 4),
+                                         "f32": round(flops / (r["hpsi_ms_f32"] / 1e3) / 1e12 /
+                                                      fp32_peak, 4)}},
         "mixed": {"n_evals": [rec["n_evals"] for rec in timed],
                   "warm_t_screen_s": [round(rec["t_screen"], 4) for rec in r["warm"]],
                   "energy_bulk": [rec["energy"] for rec in timed],

@@ -122,6 +122,13 @@ hy_status hy_ham_info(const hy_ham *h, int64_t *n_det, int64_t *n_alpha_str,
                       int64_t *n_beta_str, int64_t *n_groups,
                       int64_t *n_terms);
 
+/* With enable != 0, every later hy_apply_h records a pair of CUDA events on
+ * its stream around the alpha-beta coupling kernel(s); hy_ham_coupling_ms
+ * waits for the last pair and returns the elapsed milliseconds (host).  Off
+ * by default; the events cost nothing when off. */
+hy_status hy_ham_profile(hy_ham *h, int enable);
+hy_status hy_ham_coupling_ms(const hy_ham *h, float *ms);
+
 /* Copy the Pauli table (host outputs, caller-allocated).  Term t is
  * coeff[t] * P(x[t], z[t]) where P is the Hermitian Pauli string with X on
  * bits of x & ~z, Z on z & ~x and Y on x & z (bit j = qubit j).  Terms are
@@ -361,7 +368,9 @@ hy_status hy_ranker_topk(const float *score, int64_t m, int64_t k,
 /* Attach a ranker to a driver created with screen_top_m = M > 0.  The first
  * warm_iters iterations run the full screen and feed the ranker (features,
  * exact |g|) pairs; it is then fitted (`epochs` passes) and from then on
- * proposes the top M operators, which are screened exactly.  Every
+ * M operators are proposed and screened exactly: the M / 4 with the largest
+ * gradient bound (feature 10, an upper bound on |g_k|), then the MLP's top
+ * ranks until M distinct operators.  Every
  * refresh_every-th ranked iteration (0: never) selects from the full screen
  * instead, adds its pairs and refits the ranker (epochs / 4 passes, warm
  * start), which bounds the age of the stale-gradient features.  The full

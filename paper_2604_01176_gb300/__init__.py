@@ -127,6 +127,16 @@ class Hamiltonian:
                                     stream_ptr(stream)))
         return out
 
+    def profile_coupling(self, on: bool = True):
+        """Record CUDA events around the alpha-beta coupling of later apply_h calls."""
+        check(_abi.load().hy_ham_profile(self._h, 1 if on else 0))
+
+    def coupling_ms(self) -> float:
+        """Device time of the coupling in the last profiled apply_h (waits for it)."""
+        ms = ctypes.c_float()
+        check(_abi.load().hy_ham_coupling_ms(self._h, ctypes.byref(ms)))
+        return ms.value
+
     def connections_per_det(self) -> float:
         """Nonzero matrix elements of H per determinant row (diagonal, alpha
         and beta singles and doubles, alpha-beta doubles): the number of

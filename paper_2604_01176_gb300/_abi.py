@@ -76,6 +76,8 @@ SIGNATURES = {
     "hy_ham_destroy": (I32, [P]),
     "hy_ham_info": (I32, [P, PI64, PI64, PI64, PI64, PI64]),
     "hy_ham_pauli_table": (I32, [P, P, P, P, P]),
+    "hy_ham_profile": (I32, [P, I32]),
+    "hy_ham_coupling_ms": (I32, [P, P]),
     "hy_pauli_table_build": (I32, [P, P, D, I32, D, I64, P, P, P, P, PI64, PI64]),
     "hy_rank": (I32, [P, P, P, I64, P]),
     "hy_unrank": (I32, [P, P, P, I64, P]),

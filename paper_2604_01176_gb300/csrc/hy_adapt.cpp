@@ -455,13 +455,35 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         const int64_t M = std::min<int64_t>(a->cfg.screen_top_m, a->K);
         HY_TRY(hy_ranker_features(a->h, a->p, psi, sigma, bulk, a->d_extra, a->d_feat, st));
         HY_TRY(hy_ranker_predict(a->ranker, a->d_feat, a->K, a->d_score, st));
+        // proposals: the M / 4 operators with the largest Cauchy-Schwarz
+        // gradient bound (feature 10, an upper bound on |g_k|), then the
+        // MLP's ranking until M distinct operators
+        const int64_t Mb = M / 4;
+        std::vector<int32_t> by_mlp(M), by_bound(Mb);
         HY_TRY(hy_ranker_topk(a->d_score, a->K, M, a->d_prop, st));
-        HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, a->d_prop, M, a->d_gp, bulk, st));
-        std::vector<int32_t> prop(M);
-        std::vector<double> gp(M);
-        HY_TRY(xfer(a, prop.data(), a->d_prop, M * 4, cudaMemcpyDeviceToHost, st,
+        HY_TRY(xfer(a, by_mlp.data(), a->d_prop, M * 4, cudaMemcpyDeviceToHost, st,
                     "proposals readback"));
-        HY_TRY(xfer(a, gp.data(), a->d_gp, M * 8, cudaMemcpyDeviceToHost, st,
+        if (Mb > 0) {
+            HY_TRY(cu(cudaMemcpy2DAsync(a->d_score, sizeof(float), a->d_feat + 10,
+                                        16 * sizeof(float), sizeof(float), size_t(a->K),
+                                        cudaMemcpyDeviceToDevice, st), "bound column"));
+            HY_TRY(hy_ranker_topk(a->d_score, a->K, Mb, a->d_prop, st));
+            HY_TRY(xfer(a, by_bound.data(), a->d_prop, Mb * 4, cudaMemcpyDeviceToHost, st,
+                        "proposals readback"));
+        }
+        HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+        std::vector<int32_t> prop;
+        std::vector<char> taken(a->K, 0);
+        for (int32_t k : by_bound)
+            if (!taken[k]) { taken[k] = 1; prop.push_back(k); }
+        for (int32_t k : by_mlp)
+            if (int64_t(prop.size()) < M && !taken[k]) { taken[k] = 1; prop.push_back(k); }
+        HY_TRY(xfer(a, a->d_prop, prop.data(), prop.size() * 4, cudaMemcpyHostToDevice, st,
+                    "proposals upload"));
+        const int64_t Mp = int64_t(prop.size());
+        HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, a->d_prop, Mp, a->d_gp, bulk, st));
+        std::vector<double> gp(Mp);
+        HY_TRY(xfer(a, gp.data(), a->d_gp, Mp * 8, cudaMemcpyDeviceToHost, st,
                     "proposals readback"));
         HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
         cand.assign(prop.begin(), prop.end());

@@ -102,6 +102,9 @@ struct hy_ham {
     void *ws = nullptr;
     size_t ws_bytes = 0;
     int dot_blocks = 0;
+    // optional CUDA events around the alpha-beta coupling launch(es)
+    bool prof = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 struct hy_pool {
@@ -297,7 +300,9 @@ hy_status apply_h_t(hy_ham *h, const T *psi, T *sigma, cudaStream_t st)
             d.Na = h->Na;
             d.Nb = h->Nb;
             d.Nbp = Nbp;
+            if (h->prof) cudaEventRecord(h->ev0, st);
             HY_CUDA(hy::k::coupling_dense(d, h->num_sms, st), "alpha-beta coupling (dense)");
+            if (h->prof) cudaEventRecord(h->ev1, st);
             return HY_OK;
         }
     }
@@ -314,7 +319,9 @@ hy_status apply_h_t(hy_ham *h, const T *psi, T *sigma, cudaStream_t st)
     a.nexb = h->B.nex;
     a.Na = h->Na;
     a.Nb = h->Nb;
+    if (h->prof) cudaEventRecord(h->ev0, st);
     HY_CUDA(hy::k::coupling<T>(a, h->num_sms, st), "alpha-beta coupling");
+    if (h->prof) cudaEventRecord(h->ev1, st);
     return HY_OK;
 }
 
@@ -527,9 +534,31 @@ hy_status hy_build_hamiltonian(const double *h1, const double *h2, double e_core
 hy_status hy_ham_destroy(hy_ham *h)
 {
     if (!h) return HY_OK;
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
     h->arena.release();
     if (h->ws) cudaFree(h->ws);
     delete h;
+    return HY_OK;
+}
+
+hy_status hy_ham_profile(hy_ham *h, int enable)
+{
+    if (!h) return fail(HY_ERR_ARG, "handle is NULL");
+    if (enable && !h->ev0) {
+        HY_CUDA(cudaEventCreate(&h->ev0), "event");
+        HY_CUDA(cudaEventCreate(&h->ev1), "event");
+    }
+    h->prof = enable != 0;
+    return HY_OK;
+}
+
+hy_status hy_ham_coupling_ms(const hy_ham *h, float *ms)
+{
+    if (!h || !ms) return fail(HY_ERR_ARG, "NULL argument");
+    if (!h->ev0) return fail(HY_ERR_ARG, "profiling was never enabled");
+    HY_CUDA(cudaEventSynchronize(h->ev1), "event synchronize");
+    HY_CUDA(cudaEventElapsedTime(ms, h->ev0, h->ev1), "event elapsed");
     return HY_OK;
 }
 

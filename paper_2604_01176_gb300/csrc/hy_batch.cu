@@ -50,6 +50,21 @@ __device__ __forceinline__ void plane_put<double>(uint32_t *base, int stride, in
     base[stride + i] = uint32_t(__double2hiint(v));
 }
 
+// staged coefficient with its sign flipped by an integer XOR of the sign bit
+template <typename T>
+__device__ __forceinline__ T sign_xor(const uint32_t *C, int stride, int i, uint32_t sbit);
+template <>
+__device__ __forceinline__ float sign_xor<float>(const uint32_t *C, int, int i, uint32_t sbit)
+{
+    return __uint_as_float(C[i] ^ sbit);
+}
+template <>
+__device__ __forceinline__ double sign_xor<double>(const uint32_t *C, int stride, int i,
+                                                   uint32_t sbit)
+{
+    return __hiloint2double(int(C[stride + i] ^ sbit), int(C[i]));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024)
 k_batch_rows(BatchArgs<T> a)
@@ -60,14 +75,17 @@ k_batch_rows(BatchArgs<T> a)
     const int gid = threadIdx.x / gsize, lt = threadIdx.x % gsize;
     const int NB = a.nb_max, NN = a.nn_max;
     // per-group shared memory: acc [NB] T | row planes [W*NB] | C planes
-    // [W*NN] | Cdiag [16] T | task slot
+    // [W*NN] | Cdiag [16] T | TL, TH [256] T each | task slot.  TL[m] (TH[m])
+    // sums Cdiag over the set bits of m (of m shifted by 8), so a column's
+    // diagonal beta term is TL[b & 255] + TH[b >> 8].
     const size_t gbytes = a.group_smem;
     unsigned char *gs = smem_raw + size_t(gid) * gbytes;
     T *acc = reinterpret_cast<T *>(gs);
     uint32_t *row = reinterpret_cast<uint32_t *>(acc + NB);
     uint32_t *C = row + W * NB;
     T *Cdiag = reinterpret_cast<T *>(C + W * NN);
-    int *slot = reinterpret_cast<int *>(Cdiag + 16);
+    T *TL = Cdiag + 16, *TH = TL + 256;
+    int *slot = reinterpret_cast<int *>(TH + 256);
     const int bar = gid + 1;
     for (;;) {
         if (lt == 0) *slot = atomicAdd(a.counter, 1);
@@ -125,18 +143,26 @@ k_batch_rows(BatchArgs<T> a)
                     plane_put<T>(row, NB, b, psi[Ja * Nb + b]);
                 group_sync(bar, gsize);
             }
+            for (int i = lt; i < 16 - n; i += gsize) Cdiag[n + i] = T(0);
+            group_sync(bar, gsize);
+            for (int i = lt; i < 512; i += gsize) {
+                const int mm = i & 255, base = i < 256 ? 0 : 8;
+                T v = T(0);
+                for (int r = 0; r < 8; ++r)
+                    if ((mm >> r) & 1) v += Cdiag[base + r];
+                (i < 256 ? TL : TH)[mm] = v;
+            }
+            group_sync(bar, gsize);
             for (int b = lt; b < Nb; b += gsize) {
-                T d = T(0);
-                for (uint32_t mm = m.bstr[b]; mm; mm &= mm - 1) d += Cdiag[__ffs(mm) - 1];
-                T s = d * plane_get<T>(row, NB, b);
+                const uint32_t mb = m.bstr[b];
+                const T d = TL[mb & 255u] + TH[mb >> 8];
+                T s = d * plane_get<T>(row, NB, b) + acc[b];
                 for (int f = 0; f < m.nexb; ++f) {
                     const uint32_t u = m.bexT[int64_t(f) * Nb + b];
                     const int rt = ((u >> 16) & 15) * n + ((u >> 20) & 15);
-                    T cv = plane_get<T>(C, NN, rt);
-                    cv = (u >> 31) ? -cv : cv;
-                    s += cv * plane_get<T>(row, NB, u & 0xFFFFu);
+                    s += sign_xor<T>(C, NN, rt, u & 0x80000000u) * plane_get<T>(row, NB, u & 0xFFFFu);
                 }
-                acc[b] += s;
+                acc[b] = s;
             }
         }
         // write the row and its <psi|sigma> partial
@@ -179,7 +205,7 @@ size_t batch_group_smem(int nb_max, int nn_max, int gsize)
 {
     constexpr int W = sizeof(T) / 4;
     size_t b = size_t(nb_max) * sizeof(T) + size_t(W) * nb_max * 4 + size_t(W) * nn_max * 4 +
-               16 * sizeof(T) + 16;
+               (16 + 512) * sizeof(T) + 16;
     // the energy reduction reuses the group's region for gsize doubles
     if (b < size_t(gsize) * 8 + 16) b = size_t(gsize) * 8 + 16;
     return (b + 15) / 16 * 16;
