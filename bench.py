@@ -74,6 +74,8 @@ def parse():
                     help="plain FP64 ADAPT vs mixed+ranker ADAPT with the full screen as judge: "
                          "per-iteration rank of the true argmax and energy gap")
     ap.add_argument("--iters", type=int, default=12, help="iterations of --ranker-eval")
+    ap.add_argument("--judge-only", action="store_true",
+                    help="--ranker-eval without the plain run (ranks of the true argmax only)")
     ap.add_argument("--batch", action="store_true",
                     help="64 molecules of 8-12 orbitals: H psi + energies of all in one persistent "
                          "graph-captured launch (autotuned tile) vs one launch sequence per molecule")
@@ -153,19 +155,22 @@ def ranker_eval(args):
     ham = hy.Hamiltonian(h1, h2, ec, n, na, nb)
     pool = hy.Pool(ham)
     it = args.iters
-    plain = hy.Adapt(ham, pool, "f64", max_iter=it).run(it)
+    plain = None if args.judge_only else hy.Adapt(ham, pool, "f64", max_iter=it).run(it)
     ranker = hy.Ranker(hidden=256, seed=7)
     ad = hy.Adapt(ham, pool, "mixed", max_iter=it, screen_top_m=TOP_M, judge=True,
-                  refine_every=1)
+                  refine_every=0 if args.judge_only else 1)
     ad.set_ranker(ranker, warm_iters=args.warmup, epochs=30, refresh_every=REFRESH)
     ranked = ad.run(it)
     rows = []
-    for p, r in zip(plain, ranked):
-        rows.append({"iter": p["iter"], "e_plain": p["energy"], "e_ranked": r["energy"],
-                     "gap": r["energy"] - p["energy"], "true_rank": r["true_rank"],
-                     "same_op": p["selected"] == r["selected"],
-                     "t_screen_plain": round(p["t_screen"], 5),
-                     "t_screen_ranked": round(r["t_screen"], 5)})
+    for i, r in enumerate(ranked):
+        row = {"iter": r["iter"], "e_ranked": r["energy"], "true_rank": r["true_rank"],
+               "t_screen_ranked": round(r["t_screen"], 5), "t_total": round(r["t_total"], 3)}
+        if plain is not None:
+            p = plain[i]
+            row.update({"e_plain": p["energy"], "gap": r["energy"] - p["energy"],
+                        "same_op": p["selected"] == r["selected"],
+                        "t_screen_plain": round(p["t_screen"], 5)})
+        rows.append(row)
     print(json.dumps({"ranker_eval": args.workload, "top_m": TOP_M, "warm": args.warmup,
                       "refresh_every": REFRESH, "pool_ops": len(pool), "rows": rows}), flush=True)
 
@@ -422,6 +427,34 @@ def run_ours(args, rank, world):
                io=((io1[0] - io0[0]) / S, (io1[1] - io0[1]) / S),
                timed=timed, warm=warm, e_final=e_final, e_bulk=e_bulk,
                true_rank=true_rank, ansatz_len=len(ad.ansatz()[0]))
+    # the same iterations with the sparse-state path (automatic while psi
+    # has at most N/64 nonzero amplitudes): a fresh mixed + ranker driver,
+    # warmed and timed like the dense one, and one plain FP64 iteration
+    sp = hy.Adapt(ham, pool, "mixed", max_iter=cap, screen_top_m=TOP_M, refine_every=0,
+                  sparse=True)
+    sp_ranker = hy.Ranker(hidden=256, seed=7 + rank)
+    sp.set_ranker(sp_ranker, warm_iters=W, epochs=30, refresh_every=REFRESH)
+    [sp.step() for _ in range(W)]
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s0.record(stream)
+    sp_timed = [sp.step() for _ in range(S)]
+    s1.record(stream)
+    torch.cuda.synchronize()
+    out["sparse_ms"] = s0.elapsed_time(s1)
+    out["sparse_evals"] = [rec["n_evals"] for rec in sp_timed]
+    sops, sth = sp.ansatz()
+    del sp
+    sp_plain = hy.Adapt(ham, pool, "f64", max_iter=len(sops) + 2, sparse=True)
+    sp_plain.set_ansatz(sops, sth)
+    torch.cuda.synchronize()
+    s0.record(stream)
+    sprec = sp_plain.step()
+    s1.record(stream)
+    torch.cuda.synchronize()
+    out["sparse_plain_ms"] = s0.elapsed_time(s1)
+    out["sparse_plain_rec"] = sprec
+    del sp_plain
     # plain FP64 full-screen iteration from the same (refined) ansatz
     if not args.no_plain:
         ops, th = ad.ansatz()
@@ -532,6 +565,13 @@ def main():
         "clocks": r["clocks"],
         "build_s": round(r["t_build"], 2),
     }
+    out["sparse_state_path"] = {
+        "mixed_ranker_iters_per_s": round(S / (r["sparse_ms"] / 1e3), 4),
+        "mixed_ranker_n_evals": r["sparse_evals"],
+        "plain_f64_iters_per_s": round(1e3 / r["sparse_plain_ms"], 4),
+        "plain_f64_n_evals": r["sparse_plain_rec"]["n_evals"],
+        "note": "same iterations with hy_apply_h_sparse / hy_pool_gradients_sparse while "
+                "psi has <= N/64 nonzero amplitudes"}
     if "plain_ms" in r:
         pr = r["plain_rec"]
         out["plain"] = {"iters_per_s": round(1e3 / r["plain_ms"], 6), "ms": round(r["plain_ms"], 1),

@@ -172,6 +172,33 @@ hy_status hy_energy(const hy_ham *h, const void *psi, const void *sigma_or_null,
 hy_status hy_dot(const hy_ham *h, const void *x, const void *y, hy_dtype dt,
                  double *out, void *stream);
 
+/* Sparse states (paper: the state vector is stored sparse and H is applied
+ * as a sparse matrix to a sparse vector).  psi stays a dense array over
+ * Omega_CIk; these calls take the list of its nonzero amplitudes. */
+
+/* list[0..min(count,cap)-1] (device int64) = indices of the nonzero entries
+ * of psi, in no particular order; *count (device int64) = their number, even
+ * when it exceeds cap (then only cap are listed). */
+hy_status hy_support(const hy_ham *h, const void *psi, hy_dtype dt, int64_t *list,
+                     int64_t cap, int64_t *count, void *stream);
+
+/* sigma = H psi for a psi that is zero outside list[0..m-1] (device): sigma
+ * is zeroed and every listed amplitude is scattered to all determinants H
+ * connects it to (atomic adds; the summation order is not fixed, so results
+ * agree with hy_apply_h to rounding).  Cost ~ m x (connections per row). */
+hy_status hy_apply_h_sparse(const hy_ham *h, const void *psi, void *sigma,
+                            hy_dtype dt, const int64_t *list, int64_t m,
+                            void *stream);
+
+/* hy_pool_gradients for a psi that is zero outside list[0..m-1]: only the
+ * pairs of each operator with an endpoint in the list are visited (sigma
+ * must be the full H psi). */
+hy_status hy_pool_gradients_sparse(const hy_ham *h, const hy_pool *p,
+                                   const void *psi, const void *sigma,
+                                   const int64_t *list, int64_t m,
+                                   const int32_t *ops_or_null, int64_t n_ops,
+                                   double *g_out, hy_dtype dt, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Operator pool, gradients and exp(theta A)                                */
 /* ---------------------------------------------------------------------- */
@@ -420,6 +447,10 @@ typedef struct {
                              a ranker proposes (hy_adapt_set_ranker)           */
     int judge;            /* with screen_top_m > 0: also run the full screen
                              and report the true argmax and its rank           */
+    int sparse;           /* 1: while psi has at most N_det / 64 nonzero
+                             amplitudes, apply H and screen through the sparse
+                             path (hy_apply_h_sparse, hy_pool_gradients_sparse);
+                             0: always the dense sweeps                        */
 } hy_adapt_config;
 
 /* One ADAPT iteration (all times in seconds, host wall clock). */
@@ -447,7 +478,7 @@ typedef struct {
 /* Create a driver for (h, p); allocates its state buffers on the device.
  * cfg == NULL takes the defaults: HY_F64, max_iter 64, eps_grad 1e-5,
  * gtol 1e-9, gtol_bulk 1e-5, max_evals 200, refine_steps 4, refine_every 1,
- * full screen. */
+ * full screen, dense sweeps. */
 hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p,
                           const hy_adapt_config *cfg, hy_adapt **out);
 hy_status hy_adapt_destroy(hy_adapt *a);

@@ -43,7 +43,7 @@ class AdaptConfig(ctypes.Structure):
                 ("gtol_bulk", ctypes.c_double), ("max_evals", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("refine_every", ctypes.c_int),
                 ("screen_top_m", ctypes.c_int),
-                ("judge", ctypes.c_int)]
+                ("judge", ctypes.c_int), ("sparse", ctypes.c_int)]
 
 
 class AdaptRecord(ctypes.Structure):
@@ -82,6 +82,9 @@ SIGNATURES = {
     "hy_rank": (I32, [P, P, P, I64, P]),
     "hy_unrank": (I32, [P, P, P, I64, P]),
     "hy_apply_h": (I32, [P, P, P, I32, P]),
+    "hy_support": (I32, [P, P, I32, P, I64, P, P]),
+    "hy_apply_h_sparse": (I32, [P, P, P, I32, P, I64, P]),
+    "hy_pool_gradients_sparse": (I32, [P, P, P, P, P, I64, P, I64, P, I32, P]),
     "hy_energy": (I32, [P, P, P, I32, P, P]),
     "hy_dot": (I32, [P, P, P, I32, P, P]),
     "hy_normalize": (I32, [P, P, I32, P]),

@@ -62,6 +62,9 @@ struct hy_adapt {
     int evals = 0, evals64 = 0;
     int iter = 0;
     int64_t h2d = 0, d2h = 0;     // bytes copied host <-> device so far
+    // sparse path: nonzero list of the last evaluated state (-1: dense)
+    int64_t *d_list = nullptr, *d_count = nullptr;
+    int64_t sparse_cap = 0, sparse_m = -1;
 };
 
 namespace {
@@ -111,7 +114,19 @@ hy_status energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     const int renorm = dt == HY_F32 ? 1 : 0;
     for (size_t l = 0; l < a->ops.size(); ++l)
         HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], th[l], psi, dt, renorm, st));
-    HY_TRY(hy_apply_h(a->h, psi, sigma, dt, st));
+    a->sparse_m = -1;
+    if (a->cfg.sparse) {
+        int64_t cnt = 0;
+        HY_TRY(hy_support(a->h, psi, dt, a->d_list, a->sparse_cap, a->d_count, st));
+        HY_TRY(xfer(a, &cnt, a->d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, st,
+                    "support count"));
+        HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+        if (cnt <= a->sparse_cap) a->sparse_m = cnt;
+    }
+    if (a->sparse_m >= 0)
+        HY_TRY(hy_apply_h_sparse(a->h, psi, sigma, dt, a->d_list, a->sparse_m, st));
+    else
+        HY_TRY(hy_apply_h(a->h, psi, sigma, dt, st));
     HY_TRY(hy_energy(a->h, psi, sigma, dt, a->d_e, st));
     HY_TRY(xfer(a, e, a->d_e, sizeof(double), cudaMemcpyDeviceToHost, st, "energy readback"));
     HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
@@ -322,6 +337,7 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
         c.refine_every = 1;
         c.screen_top_m = 0;
         c.judge = 0;
+        c.sparse = 0;
     }
     if ((c.bulk != HY_F64 && c.bulk != HY_F32) || c.max_iter < 1 || c.max_iter > (1 << 20) ||
         !(c.eps_grad >= 0) || !(c.gtol > 0) || !(c.gtol_bulk > 0) || c.max_evals < 1 ||
@@ -352,6 +368,11 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
         alloc(reinterpret_cast<void **>(&a->d_score), size_t(a->K) * 4);
         alloc(reinterpret_cast<void **>(&a->d_gp), size_t(a->K) * 8);
     }
+    if (c.sparse) {
+        a->sparse_cap = std::max<int64_t>(1, a->N / 64);
+        alloc(reinterpret_cast<void **>(&a->d_list), size_t(a->sparse_cap) * 8);
+        alloc(reinterpret_cast<void **>(&a->d_count), 8);
+    }
     a->last_g.assign(a->K, -1.0);
     a->age.assign(a->K, 0);
     a->count.assign(a->K, 0.0f);
@@ -379,6 +400,8 @@ hy_status hy_adapt_destroy(hy_adapt *a)
     cudaFree(a->d_extra);
     cudaFree(a->d_score);
     cudaFree(a->d_gp);
+    cudaFree(a->d_list);
+    cudaFree(a->d_count);
     delete a;
     return HY_OK;
 }
@@ -417,7 +440,11 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     int64_t sel = -1;
     double gmax = 0.0, gn2 = 0.0;
     auto full_screen = [&]() -> hy_status {
-        HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, nullptr, a->K, a->d_g, bulk, st));
+        if (a->sparse_m >= 0)
+            HY_TRY(hy_pool_gradients_sparse(a->h, a->p, psi, sigma, a->d_list, a->sparse_m,
+                                            nullptr, a->K, a->d_g, bulk, st));
+        else
+            HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, nullptr, a->K, a->d_g, bulk, st));
         g.assign(a->K, 0.0);
         HY_TRY(xfer(a, g.data(), a->d_g, a->K * sizeof(double), cudaMemcpyDeviceToHost, st,
                     "screen readback"));
@@ -481,7 +508,11 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         HY_TRY(xfer(a, a->d_prop, prop.data(), prop.size() * 4, cudaMemcpyHostToDevice, st,
                     "proposals upload"));
         const int64_t Mp = int64_t(prop.size());
-        HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, a->d_prop, Mp, a->d_gp, bulk, st));
+        if (a->sparse_m >= 0)
+            HY_TRY(hy_pool_gradients_sparse(a->h, a->p, psi, sigma, a->d_list, a->sparse_m,
+                                            a->d_prop, Mp, a->d_gp, bulk, st));
+        else
+            HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, a->d_prop, Mp, a->d_gp, bulk, st));
         std::vector<double> gp(Mp);
         HY_TRY(xfer(a, gp.data(), a->d_gp, Mp * 8, cudaMemcpyDeviceToHost, st,
                     "proposals readback"));

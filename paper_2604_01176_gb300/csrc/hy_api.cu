@@ -921,6 +921,95 @@ hy_status hy_apply_excitation(const hy_ham *hc, const hy_pool *p, int64_t k,
     return s;
 }
 
+hy_status hy_support(const hy_ham *h, const void *psi, hy_dtype dt, int64_t *list, int64_t cap,
+                     int64_t *count, void *stream)
+{
+    if (!h || !psi || !count || !valid_dtype(dt) || cap < 0 || (cap > 0 && !list))
+        return fail(HY_ERR_ARG, "bad arguments");
+    auto *cnt = reinterpret_cast<unsigned long long *>(count);
+    if (dt == HY_F64)
+        HY_CUDA(hy::k::support<double>(static_cast<const double *>(psi), h->N, list, cap, cnt,
+                                       h->num_sms, as_stream(stream)), "support");
+    else
+        HY_CUDA(hy::k::support<float>(static_cast<const float *>(psi), h->N, list, cap, cnt,
+                                      h->num_sms, as_stream(stream)), "support");
+    return HY_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+hy::k::SparseArgs<T> sparse_args(const hy_ham *h, const void *psi, void *sigma,
+                                 const int64_t *list, int64_t m)
+{
+    hy::k::SparseArgs<T> a;
+    a.psi = static_cast<const T *>(psi);
+    a.sigma = static_cast<T *>(sigma);
+    a.list = list;
+    a.m = m;
+    const DevCsr<T> *Ma, *Mb;
+    if constexpr (sizeof(T) == 8) {
+        Ma = &h->Ma64; Mb = &h->Mb64; a.V = h->d_V64;
+    } else {
+        Ma = &h->Ma32; Mb = &h->Mb32; a.V = h->d_V32;
+    }
+    a.Ma_ptr = Ma->ptr; a.Ma_col = Ma->col; a.Ma_val = Ma->val;
+    a.Mb_ptr = Mb->ptr; a.Mb_col = Mb->col; a.Mb_val = Mb->val;
+    a.aex = h->d_aex; a.bexT = h->d_bexT; a.astr = h->d_astr; a.bstr = h->d_bstr;
+    a.n = h->n; a.nexa = h->A.nex; a.nexb = h->B.nex; a.Na = h->Na; a.Nb = h->Nb;
+    return a;
+}
+}  // namespace
+
+extern "C" {
+
+hy_status hy_apply_h_sparse(const hy_ham *h, const void *psi, void *sigma, hy_dtype dt,
+                            const int64_t *list, int64_t m, void *stream)
+{
+    if (!h || !psi || !sigma || !valid_dtype(dt) || m < 0 || (m > 0 && !list))
+        return fail(HY_ERR_ARG, "bad arguments");
+    if (psi == sigma) return fail(HY_ERR_ARG, "psi and sigma must not alias");
+    if (dt == HY_F64)
+        HY_CUDA(hy::k::hpsi_scatter<double>(sparse_args<double>(h, psi, sigma, list, m), h->num_sms,
+                                            as_stream(stream)), "sparse H psi");
+    else
+        HY_CUDA(hy::k::hpsi_scatter<float>(sparse_args<float>(h, psi, sigma, list, m), h->num_sms,
+                                           as_stream(stream)), "sparse H psi");
+    return HY_OK;
+}
+
+hy_status hy_pool_gradients_sparse(const hy_ham *h, const hy_pool *p, const void *psi,
+                                   const void *sigma, const int64_t *list, int64_t m,
+                                   const int32_t *ops_or_null, int64_t n_ops, double *g_out,
+                                   hy_dtype dt, void *stream)
+{
+    if (!h || !p || !psi || !sigma || !g_out || !valid_dtype(dt) || m < 0 || (m > 0 && !list))
+        return fail(HY_ERR_ARG, "bad arguments");
+    if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
+    if (!ops_or_null) n_ops = int64_t(p->ops.size());
+    if (n_ops < 0) return fail(HY_ERR_ARG, "n_ops out of range");
+    auto fill = [&](auto &a) {
+        a.list = list; a.m = m; a.desc = p->d_desc; a.ops = ops_or_null; a.n_ops = n_ops;
+        a.astr = h->d_astr; a.bstr = h->d_bstr; a.binom33 = h->d_binom; a.n = h->n;
+        a.Nb = h->Nb; a.g = g_out;
+    };
+    if (dt == HY_F64) {
+        hy::k::SparseGradArgs<double> a;
+        a.psi = static_cast<const double *>(psi);
+        a.sigma = static_cast<const double *>(sigma);
+        fill(a);
+        HY_CUDA(hy::k::grad_sparse<double>(a, h->num_sms, as_stream(stream)), "sparse screen");
+    } else {
+        hy::k::SparseGradArgs<float> a;
+        a.psi = static_cast<const float *>(psi);
+        a.sigma = static_cast<const float *>(sigma);
+        fill(a);
+        HY_CUDA(hy::k::grad_sparse<float>(a, h->num_sms, as_stream(stream)), "sparse screen");
+    }
+    return HY_OK;
+}
+
 hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
                              const void *sigma_or_null, hy_dtype dt, const float *extra,
                              float *feat, void *stream)

@@ -106,6 +106,40 @@ cudaError_t touched_weights(const T *psi, int64_t Na, int64_t Nb, const uint32_t
                             const uint32_t *bstr, int n, float *Bw, float *rs, float *D,
                             int num_sms, cudaStream_t st);
 
+// sparse-state path (hy_sparse.cu)
+template <typename T>
+struct SparseArgs {
+    const T *psi;
+    T *sigma;
+    const int64_t *list;     // nonzero amplitudes of psi
+    int64_t m;
+    const int32_t *Ma_ptr, *Ma_col, *Mb_ptr, *Mb_col;
+    const T *Ma_val, *Mb_val, *V;
+    const uint32_t *aex, *bexT, *astr, *bstr;
+    int n, nexa, nexb;
+    int64_t Na, Nb;
+};
+template <typename T>
+struct SparseGradArgs {
+    const T *psi, *sigma;
+    const int64_t *list;
+    int64_t m;
+    const int32_t *desc;     // [K][11] operator descriptors
+    const int32_t *ops;      // operator list or nullptr (all)
+    int64_t n_ops;
+    const uint32_t *astr, *bstr, *binom33;
+    int n;
+    int64_t Nb;
+    double *g;
+};
+template <typename T>
+cudaError_t support(const T *psi, int64_t N, int64_t *list, int64_t cap,
+                    unsigned long long *count, int num_sms, cudaStream_t st);
+template <typename T>
+cudaError_t hpsi_scatter(const SparseArgs<T> &a, int num_sms, cudaStream_t st);
+template <typename T>
+cudaError_t grad_sparse(const SparseGradArgs<T> &a, int num_sms, cudaStream_t st);
+
 // batched rows over many molecules (hy_batch.cu)
 template <typename T>
 struct BatchMol {

@@ -428,18 +428,40 @@ k_cpl_gemm(CplDenseArgs a)
             const int na = misc[2];
             for (int idx = tid; idx < na * kGN; idx += blockDim.x) G[idx] = 0.0f;
             __syncthreads();
-            for (int idx = tid; idx < kGN * (nexb + n); idx += blockDim.x) {
-                const int nl = idx % kGN, f = idx / kGN;
-                const int64_t b = b0 + nl;
-                if (b >= Nb) continue;
-                if (f < nexb) {
-                    const uint32_t u = a.bexT[size_t(f) * Nb + b];
-                    const int r = (u >> 16) & 15, sv = (u >> 20) & 15;
-                    const float v = __ldg(src + (u & 0xFFFFu));
-                    G[pos[r * n + sv] * kGN + nl] = (u >> 31) ? -v : v;
-                } else {
-                    const int r = f - nexb;
-                    if ((a.bstr[b] >> r) & 1u) G[pos[r * n + r] * kGN + nl] = __ldg(src + b);
+            // single-excitation entries: four per thread in flight (entry
+            // loads first, then the amplitude loads), so the L2 latency of
+            // the two dependent loads overlaps across entries
+            constexpr int kU = 4;
+            const int nsing = kGN * nexb;
+            for (int base = tid; base < nsing; base += kU * blockDim.x) {
+                uint32_t u[kU];
+                bool ok[kU];
+#pragma unroll
+                for (int q = 0; q < kU; ++q) {
+                    const int idx = base + q * blockDim.x;
+                    const int nl = idx % kGN, f = idx / kGN;
+                    ok[q] = idx < nsing && b0 + nl < Nb;
+                    u[q] = ok[q] ? __ldg(a.bexT + size_t(f) * Nb + b0 + nl) : 0u;
+                }
+                float v[kU];
+#pragma unroll
+                for (int q = 0; q < kU; ++q) v[q] = ok[q] ? __ldg(src + (u[q] & 0xFFFFu)) : 0.0f;
+#pragma unroll
+                for (int q = 0; q < kU; ++q) {
+                    if (!ok[q]) continue;
+                    const int nl = (base + q * blockDim.x) % kGN;
+                    const int r = (u[q] >> 16) & 15, sv = (u[q] >> 20) & 15;
+                    G[pos[r * n + sv] * kGN + nl] = (u[q] >> 31) ? -v[q] : v[q];
+                }
+            }
+            // diagonal types: one thread per column writes psi[J][b'] into the
+            // (r, r) row of every occupied r
+            if (tid < kGN && b0 + tid < Nb) {
+                const int64_t b = b0 + tid;
+                const float v = __ldg(src + b);
+                for (uint32_t mm = __ldg(a.bstr + b); mm; mm &= mm - 1) {
+                    const int r = __ffs(mm) - 1;
+                    G[pos[r * n + r] * kGN + tid] = v;
                 }
             }
             __syncthreads();
