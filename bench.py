@@ -7,13 +7,15 @@ determinants, seeded synthetic integrals shaped like the H16 STO-3G chain,
 the spin-adapted singles+doubles pool (3,376 operators).
 
 One step = one ADAPT-VQE iteration of the mixed-precision driver with the
-learned ranker: screen (ranker features -> MLP -> top-32 proposals screened
-exactly in float), select, append, re-optimise every parameter with BFGS
-(each evaluation: state preparation by exp(theta A) with double-precision
-renormalisation, H psi, energy and adjoint gradient, bulk in float,
-reductions in double).  The first `warmup` iterations run the full screen
-and train the ranker; the next `steps` are timed.  `value` = timed ADAPT
-iterations per second over all ranks.
+learned ranker: screen, select, append, re-optimise every parameter with
+BFGS (each evaluation: state preparation by exp(theta A) with
+double-precision renormalisation, H psi, energy and adjoint gradient, bulk
+in float, reductions in double).  While psi has few nonzero amplitudes (the
+paper's sparse regime) H psi and the screen run on the sparse-state path
+and the screen is exact; later the ranker's top-32 proposals are screened.
+The first `warmup` iterations run the full screen and train the ranker; the
+next `steps` are timed.  `value` = timed ADAPT iterations per second over all
+ranks.  The same run with the dense sweeps only is reported beside it.
 
 Also reported: H|psi> time, algorithmic GB/s and HBM fraction in FP64 and
 FP32; one plain FP64 full-screen iteration timed from the same ansatz
@@ -74,6 +76,9 @@ def parse():
                     help="plain FP64 ADAPT vs mixed+ranker ADAPT with the full screen as judge: "
                          "per-iteration rank of the true argmax and energy gap")
     ap.add_argument("--iters", type=int, default=12, help="iterations of --ranker-eval")
+    ap.add_argument("--adapt-only", action="store_true",
+                    help="profiling mode: only the headline ADAPT leg (no sweeps, plain, dense, "
+                         "CPU), printing its iterations/s")
     ap.add_argument("--judge-only", action="store_true",
                     help="--ranker-eval without the plain run (ranks of the true argmax only)")
     ap.add_argument("--batch", action="store_true",
@@ -349,6 +354,76 @@ def time_sweeps(ham, pool, dt, reps=3):
     return e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps, statistics.mean(cpl)
 
 
+def adapt_leg(ham, pool, hy, torch, args, rank, world, sparse, clocks=None):
+    """Mixed precision + ranker ADAPT: W warm-up iterations (full screens that
+    train the ranker), S timed iterations, then S end-to-end iterations that
+    restore the ansatz from host memory, two judged iterations, the double
+    refinement of the final energy, and one plain FP64 full-screen iteration
+    from the same ansatz (unless --no-plain)."""
+    W, S = args.warmup, args.steps
+    stream = torch.cuda.current_stream()
+    cap = W + 2 * S + 6
+    ranker = hy.Ranker(hidden=256, seed=7 + rank)
+    ad = hy.Adapt(ham, pool, "mixed", max_iter=cap, screen_top_m=TOP_M, refine_every=0,
+                  sparse=sparse)
+    ad.set_ranker(ranker, warm_iters=W, epochs=30, refresh_every=REFRESH)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    warm = [ad.step() for _ in range(W)]
+    barrier()
+    if clocks:
+        clocks.start()
+    l0 = hy.launch_count()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    timed = [ad.step() for _ in range(S)]
+    t1.record(stream)
+    barrier()
+    launches = hy.launch_count() - l0
+    ms = t0.elapsed_time(t1)
+    io0 = ad.io_bytes()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(S):
+        ops, th = ad.ansatz()
+        ad.set_ansatz(ops, th)
+        ad.step()
+        ad.ansatz()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop() if clocks else None
+    io1 = ad.io_bytes()
+    ms_e2e = e0.elapsed_time(e1)
+    ad.set_judge(True)
+    judged = [ad.step() for _ in range(2)]
+    ad.set_judge(False)
+    e_bulk = judged[-1]["energy"]
+    e_final = ad.refine(steps=4)
+    ops, th = ad.ansatz()
+    res = dict(ms=ms, ms_e2e=ms_e2e, launches=launches, clocks=clk, timed=timed, warm=warm,
+               io=((io1[0] - io0[0]) / S, (io1[1] - io0[1]) / S), e_final=e_final,
+               e_bulk=e_bulk, true_rank=[j["true_rank"] for j in judged], ansatz_len=len(ops))
+    del ad
+    if not args.no_plain:
+        plain = hy.Adapt(ham, pool, "f64", max_iter=len(ops) + 2, sparse=sparse)
+        plain.set_ansatz(ops, th)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        p0.record(stream)
+        prec = plain.step()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        res.update(plain_ms=p0.elapsed_time(p1), plain_rec=prec)
+    if world > 1:
+        res["ms"], res["ms_e2e"] = max_over_ranks([ms, ms_e2e], torch.device("cuda"))
+    return res
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2604_01176_gb300 as hy
@@ -363,113 +438,38 @@ def run_ours(args, rank, world):
     ham = hy.Hamiltonian(h1, h2, ec, n, na, nb)
     pool = hy.Pool(ham)
     t_build = time.perf_counter() - tb
-    N, K = ham.n_det, len(pool)
-    W, S = args.warmup, args.steps
-    out = dict(N=N, K=K, n=n, na=na, nb=nb, seed=seed, t_build=t_build,
+    out = dict(N=ham.n_det, K=len(pool), n=n, na=na, nb=nb, seed=seed, t_build=t_build,
                conn=ham.connections_per_det())
+    if args.adapt_only:
+        args.no_plain = True
+        out["head"] = adapt_leg(ham, pool, hy, torch, args, rank, world, True)
+        return out
     out["hpsi_ms_f64"], out["screen_ms_f64"], out["cpl_ms_f64"] = time_sweeps(ham, pool,
                                                                             torch.float64)
     out["hpsi_ms_f32"], out["screen_ms_f32"], out["cpl_ms_f32"] = time_sweeps(ham, pool,
                                                                             torch.float32)
     out["cpl_units"] = (ham.n_alpha * (ham.n_orb - ham.n_alpha) + 1) * \
         (ham.n_beta * (ham.n_orb - ham.n_beta) + 1)
+    # headline: the sparse-state path (automatic while psi is sparse)
+    out["head"] = adapt_leg(ham, pool, hy, torch, args, rank, world, True, Clocks(dev.index))
+    # the same with the dense sweeps only (tracks the dense kernels)
+    out["dense"] = adapt_leg(ham, pool, hy, torch, args, rank, world, False)
+    return out
 
-    # mixed precision + learned ranker
-    cap = W + 2 * S + 6
-    ranker = hy.Ranker(hidden=256, seed=7 + rank)
-    ad = hy.Adapt(ham, pool, "mixed", max_iter=cap, screen_top_m=TOP_M, refine_every=0)
-    ad.set_ranker(ranker, warm_iters=W, epochs=30, refresh_every=REFRESH)
-    stream = torch.cuda.current_stream()
 
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-            torch.cuda.synchronize()
-
-    warm = [ad.step() for _ in range(W)]
-    clocks = Clocks(dev.index)
-    barrier()
-    clocks.start()
-    l0 = hy.launch_count()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    timed = [ad.step() for _ in range(S)]
-    t1.record(stream)
-    barrier()
-    launches = hy.launch_count() - l0
-    ms = t0.elapsed_time(t1)
-    # end to end: each step restores the ansatz from host memory, runs the
-    # iteration through the public API and reads the ansatz back
-    io0 = ad.io_bytes()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(S):
-        ops, th = ad.ansatz()
-        ad.set_ansatz(ops, th)
-        ad.step()
-        ad.ansatz()
-    e1.record(stream)
-    barrier()
-    clk = clocks.stop()
-    io1 = ad.io_bytes()
-    ms_e2e = e0.elapsed_time(e1)
-    # ranker quality: two more iterations with the full screen as judge
-    # (untimed): the rank of the true argmax among the proposals
-    ad.set_judge(True)
-    judged = [ad.step() for _ in range(2)]
-    ad.set_judge(False)
-    e_bulk = judged[-1]["energy"]
-    true_rank = [j["true_rank"] for j in judged]
-    # final energy in double precision (refinement) and its float gap
-    e_final = ad.refine(steps=4)
-    out.update(ms=ms, ms_e2e=ms_e2e, launches=launches, clocks=clk,
-               io=((io1[0] - io0[0]) / S, (io1[1] - io0[1]) / S),
-               timed=timed, warm=warm, e_final=e_final, e_bulk=e_bulk,
-               true_rank=true_rank, ansatz_len=len(ad.ansatz()[0]))
-    # the same iterations with the sparse-state path (automatic while psi
-    # has at most N/64 nonzero amplitudes): a fresh mixed + ranker driver,
-    # warmed and timed like the dense one, and one plain FP64 iteration
-    sp = hy.Adapt(ham, pool, "mixed", max_iter=cap, screen_top_m=TOP_M, refine_every=0,
-                  sparse=True)
-    sp_ranker = hy.Ranker(hidden=256, seed=7 + rank)
-    sp.set_ranker(sp_ranker, warm_iters=W, epochs=30, refresh_every=REFRESH)
-    [sp.step() for _ in range(W)]
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    s0.record(stream)
-    sp_timed = [sp.step() for _ in range(S)]
-    s1.record(stream)
-    torch.cuda.synchronize()
-    out["sparse_ms"] = s0.elapsed_time(s1)
-    out["sparse_evals"] = [rec["n_evals"] for rec in sp_timed]
-    sops, sth = sp.ansatz()
-    del sp
-    sp_plain = hy.Adapt(ham, pool, "f64", max_iter=len(sops) + 2, sparse=True)
-    sp_plain.set_ansatz(sops, sth)
-    torch.cuda.synchronize()
-    s0.record(stream)
-    sprec = sp_plain.step()
-    s1.record(stream)
-    torch.cuda.synchronize()
-    out["sparse_plain_ms"] = s0.elapsed_time(s1)
-    out["sparse_plain_rec"] = sprec
-    del sp_plain
-    # plain FP64 full-screen iteration from the same (refined) ansatz
-    if not args.no_plain:
-        ops, th = ad.ansatz()
-        del ad
-        plain = hy.Adapt(ham, pool, "f64", max_iter=len(ops) + 2)
-        plain.set_ansatz(ops, th)
-        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        p0.record(stream)
-        prec = plain.step()
-        p1.record(stream)
-        torch.cuda.synchronize()
-        out.update(plain_ms=p0.elapsed_time(p1), plain_rec=prec)
-    if world > 1:
-        out["ms"], out["ms_e2e"] = max_over_ranks([ms, ms_e2e], dev)
+def leg_summary(leg, S):
+    out = {"iters_per_s": round(S / (leg["ms"] / 1e3), 5),
+           "n_evals": [rec["n_evals"] for rec in leg["timed"]],
+           "t_screen_s": [round(rec["t_screen"], 4) for rec in leg["timed"]],
+           "energy_bulk": [rec["energy"] for rec in leg["timed"]],
+           "final_energy_f64": leg["e_final"],
+           "final_bulk_minus_f64": leg["e_bulk"] - leg["e_final"],
+           "ranker_true_argmax_rank_judged": leg["true_rank"]}
+    if "plain_ms" in leg:
+        out["plain_f64_full_screen"] = {
+            "iters_per_s": round(1e3 / leg["plain_ms"], 5), "ms": round(leg["plain_ms"], 1),
+            "n_evals": leg["plain_rec"]["n_evals"], "ansatz_len": leg["plain_rec"]["iter"] + 1}
+        out["speedup_vs_plain"] = round(leg["plain_ms"] / (leg["ms"] / S), 3)
     return out
 
 
@@ -508,15 +508,21 @@ def main():
                 "hbm_frac": round(gbs / peaks["hbm_gbs"], 6),
                 "tflops": round(flops / (ms / 1e3) / 1e12, 4)}
 
-    timed = r["timed"]
+    if args.adapt_only:
+        print(json.dumps({"adapt_only": args.workload,
+                          "iters_per_s": round(S / (r["head"]["ms"] / 1e3), 5),
+                          "n_evals": [rec["n_evals"] for rec in r["head"]["timed"]],
+                          "launches": r["head"]["launches"]}), flush=True)
+        return
+    head, dense = r["head"], r["dense"]
     out = {
         "metric": METRIC,
-        "value": round(job_throughput(world, S, r["ms"]), 6),
+        "value": round(job_throughput(world, S, head["ms"]), 6),
         "unit": "ADAPT iters/s",
         "n_gpus": world,
         "steps": S,
         "warmup": args.warmup,
-        "ms_per_step": round(r["ms"] / S, 3),
+        "ms_per_step": round(head["ms"] / S, 3),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -524,21 +530,24 @@ def main():
         "data": "synthetic (seeded integrals shaped like the H16 STO-3G chain; no PySCF)",
         "config": {"workload": f"{args.workload}: {r['n']} orbitals, {r['na']}a+{r['nb']}b, "
                                f"{N} determinants, seed {r['seed']}",
-                   "mode": "mixed precision + learned ranker (top-32 screened exactly, "
-                           "full-screen refresh every 4th ranked iteration)",
+                   "mode": ("mixed precision + learned ranker (top-32 screened exactly, full-screen "
+                            "refresh every 4th ranked iteration); sparse-state path while psi has "
+                            "<= N/64 nonzeros, exact sparse screen while pool x nonzeros <= 5e9"),
                    "pool_ops": r["K"], "replicas": world,
-                   "ansatz_len_timed": [rec["iter"] + 1 for rec in timed],
+                   "ansatz_len_timed": [rec["iter"] + 1 for rec in head["timed"]],
                    "l2": "inputs larger than L2 (state vector 0.66 GB FP32 / 1.33 GB FP64)",
-                   "step": "one ADAPT iteration: ranked screen + select + BFGS re-optimisation"},
+                   "step": "one ADAPT iteration: screen + select + BFGS re-optimisation"},
+        "mixed_ranker": leg_summary(head, S),
+        "dense_path": leg_summary(dense, S),
         "hpsi": {"f64": hp(r["hpsi_ms_f64"], 8), "f32": hp(r["hpsi_ms_f32"], 4),
                  "algorithmic_bytes": "2 * N_det * sizeof(amplitude)",
-                 "connections_per_det": r["conn"]},
+                 "connections_per_det": r["conn"], "state": "dense seeded random state"},
         "screen_ms": {"f64": round(r["screen_ms_f64"], 3), "f32": round(r["screen_ms_f32"], 3)},
         "roofline": {"bound": "alu", "achieved": round(cflops / (r["cpl_ms_f32"] / 1e3) / 1e12, 4),
                      "peak": round(fp32_peak, 3), "unit": "TFLOP/s",
                      "frac": round(cflops / (r["cpl_ms_f32"] / 1e3) / 1e12 / fp32_peak, 4),
                      "traffic": TRAFFIC_F32,
-                     "kernel": "alpha-beta coupling, FP32 (k_cpl_gemm + k_cpl_gather)",
+                     "kernel": "alpha-beta coupling of dense H|psi>, FP32 (k_cpl_gemm + k_cpl_gather)",
                      "ms_per_launch": round(r["cpl_ms_f32"], 3),
                      "work": f"{r['cpl_units']} FMA per amplitude x {N} amplitudes",
                      "peak_kind": f"derived FP32 FMA rate: 152 SMs x 128 FMA/clk x {mhz} MHz",
@@ -552,37 +561,18 @@ def main():
                                                       fp64_peak, 4),
                                          "f32": round(flops / (r["hpsi_ms_f32"] / 1e3) / 1e12 /
                                                       fp32_peak, 4)}},
-        "mixed": {"n_evals": [rec["n_evals"] for rec in timed],
-                  "warm_t_screen_s": [round(rec["t_screen"], 4) for rec in r["warm"]],
-                  "energy_bulk": [rec["energy"] for rec in timed],
-                  "t_screen_s": [round(rec["t_screen"], 4) for rec in timed],
-                  "final_energy_f64": r["e_final"],
-                  "final_bulk_minus_f64": r["e_bulk"] - r["e_final"],
-                  "ranker_true_argmax_rank_judged": r["true_rank"]},
-        "e2e": {"value": round(job_throughput(world, S, r["ms_e2e"]), 6), "unit": "ADAPT iters/s",
-                "h2d_bytes_per_step": int(r["io"][0]), "d2h_bytes_per_step": int(r["io"][1])},
-        "gpu_launches": int(r["launches"]),
-        "clocks": r["clocks"],
+        "e2e": {"value": round(job_throughput(world, S, head["ms_e2e"]), 6),
+                "unit": "ADAPT iters/s",
+                "h2d_bytes_per_step": int(head["io"][0]), "d2h_bytes_per_step": int(head["io"][1])},
+        "gpu_launches": int(head["launches"]),
+        "clocks": head["clocks"],
         "build_s": round(r["t_build"], 2),
     }
-    out["sparse_state_path"] = {
-        "mixed_ranker_iters_per_s": round(S / (r["sparse_ms"] / 1e3), 4),
-        "mixed_ranker_n_evals": r["sparse_evals"],
-        "plain_f64_iters_per_s": round(1e3 / r["sparse_plain_ms"], 4),
-        "plain_f64_n_evals": r["sparse_plain_rec"]["n_evals"],
-        "note": "same iterations with hy_apply_h_sparse / hy_pool_gradients_sparse while "
-                "psi has <= N/64 nonzero amplitudes"}
-    if "plain_ms" in r:
-        pr = r["plain_rec"]
-        out["plain"] = {"iters_per_s": round(1e3 / r["plain_ms"], 6), "ms": round(r["plain_ms"], 1),
-                        "n_evals": pr["n_evals"], "ansatz_len": pr["iter"] + 1,
-                        "energy": pr["energy"],
-                        "speedup_mixed_ranker": round(r["plain_ms"] / (r["ms"] / S), 3)}
     if not args.no_cpu_baseline and world == 1:
-        n_evals = r["plain_rec"]["n_evals"] if "plain_rec" in r else 10
-        jlen = r["ansatz_len"]
+        n_evals = dense["plain_rec"]["n_evals"] if "plain_rec" in dense else 10
+        jlen = head["ansatz_len"]
         n, na, nb, seed = r["n"], r["na"], r["nb"], r["seed"]
-        del r
+        del r, head, dense
         tot, thr, sample = oracle_iteration_estimate(n, na, nb, seed, args.cpu_budget, jlen,
                                                      n_evals)
         out["cpu_baseline"] = {"value": 1.0 / tot, "unit": "ADAPT iters/s", "cores": thr,

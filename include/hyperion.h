@@ -352,8 +352,9 @@ hy_status hy_touched_weights(const hy_ham *h, const void *psi, hy_dtype dt,
  * geometric mean of the two pair weights for same-spin doubles) -- without
  * sigma: the mean-field occupation product n_a0 n_a1 (1-n_c0)(1-n_c1) and
  * n_a0 + n_a1 - n_c0 - n_c1; [12..15] the caller's extra[k][0..3] (the
- * driver passes the stale log10 |g_k| / max, its age, the operator's count
- * in the ansatz and its summed |theta|), or 0.
+ * driver passes log10 of the operator's last exact |g_k| relative to the
+ * largest |g| of the most recent screen, its age in iterations / 10, the
+ * operator's count in the ansatz and its summed |theta|), or 0.
  * feat: device, K x 16 floats; extra: device K x 4 floats or NULL;
  * sigma_or_null: H psi in dt, or NULL. */
 hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
@@ -449,7 +450,10 @@ typedef struct {
                              and report the true argmax and its rank           */
     int sparse;           /* 1: while psi has at most N_det / 64 nonzero
                              amplitudes, apply H and screen through the sparse
-                             path (hy_apply_h_sparse, hy_pool_gradients_sparse);
+                             path (hy_apply_h_sparse, hy_pool_gradients_sparse),
+                             and while (pool size) x (nonzeros) <= 5e9 screen
+                             the whole pool exactly even when a ranker is
+                             attached (its pairs still train the ranker);
                              0: always the dense sweeps                        */
 } hy_adapt_config;
 

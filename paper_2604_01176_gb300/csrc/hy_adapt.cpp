@@ -42,6 +42,7 @@ struct hy_adapt {
     std::vector<double> last_g;   // |g_k| when last screened (-1: never)
     std::vector<int> age;         // iterations since last screened
     std::vector<float> count, thsum;
+    double last_max = 0.0;        // largest |g| of the most recent screen
     hy_adapt_config cfg{};
     int64_t N = 0, K = 0;
     // device state: [dtype][psi, sigma, phi, lam]
@@ -186,17 +187,21 @@ double maxabs(const std::vector<double> &x)
 void note_screen(hy_adapt *a, const std::vector<int64_t> &ids, const std::vector<double> &gv)
 {
     for (auto &x : a->age) ++x;
+    double mx = 0.0;
     for (size_t i = 0; i < ids.size(); ++i) {
         a->last_g[ids[i]] = std::fabs(gv[i]);
         a->age[ids[i]] = 0;
+        mx = std::max(mx, std::fabs(gv[i]));
     }
+    a->last_max = mx;
 }
 
 // per-operator extra ranker features from the driver's bookkeeping
 hy_status upload_extra(hy_adapt *a, cudaStream_t st)
 {
-    double mx = 0.0;
-    for (double v : a->last_g) mx = std::max(mx, v);
+    // stale |g| relative to the most recent screen's largest |g| (not the
+    // largest ever seen, which early iterations dominate)
+    const double mx = a->last_max;
     std::vector<float> ex(size_t(a->K) * 4);
     for (int64_t k = 0; k < a->K; ++k) {
         const double lg = a->last_g[k];
@@ -217,6 +222,11 @@ hy_status upload_extra(hy_adapt *a, cudaStream_t st)
 // threshold e + c * alpha * slope rounds to e, and following them only
 // spends evaluations.
 const double kStall64 = std::ldexp(1.0, -50);
+
+// (pool size) x (nonzero amplitudes) below which the exact sparse screen
+// replaces the ranker's proposals (~10 ms on a GB300, the cost of the
+// ranker's feature pass at 32 qubits)
+const double kExactScreenWork = 5e9;
 
 // BFGS with backtracking (Armijo) line search on E(theta) in dt, starting
 // from a->theta and a->hinv; updates both.  *e_out = final energy.  With
@@ -434,7 +444,12 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     const int post = a->iter - a->warm_iters;   // ranked iteration index
     const bool refresh = ranked && post >= 0 && a->refresh_every > 0 &&
                          (post + 1) % a->refresh_every == 0;
-    const bool use_ranker = ranked && post >= 0 && !refresh;
+    // in the sparse regime an exact screen over the support costs about as
+    // much as the ranker's features: screen exactly (and keep feeding the
+    // ranker) while K x nonzeros stays below kExactScreenWork
+    const bool cheap_exact = a->sparse_m >= 0 &&
+                             double(a->sparse_m) * double(a->K) <= kExactScreenWork;
+    const bool use_ranker = ranked && post >= 0 && !refresh && !cheap_exact;
     std::vector<double> g;
     std::vector<int64_t> cand;   // screened operators, in proposal order
     int64_t sel = -1;
