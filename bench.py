@@ -76,6 +76,8 @@ def parse():
                     help="plain FP64 ADAPT vs mixed+ranker ADAPT with the full screen as judge: "
                          "per-iteration rank of the true argmax and energy gap")
     ap.add_argument("--iters", type=int, default=12, help="iterations of --ranker-eval")
+    ap.add_argument("--top-m", type=int, default=TOP_M,
+                    help="operators the ranker proposes for the exact screen")
     ap.add_argument("--adapt-only", action="store_true",
                     help="profiling mode: only the headline ADAPT leg (no sweeps, plain, dense, "
                          "CPU), printing its iterations/s")
@@ -162,7 +164,7 @@ def ranker_eval(args):
     it = args.iters
     plain = None if args.judge_only else hy.Adapt(ham, pool, "f64", max_iter=it).run(it)
     ranker = hy.Ranker(hidden=256, seed=7)
-    ad = hy.Adapt(ham, pool, "mixed", max_iter=it, screen_top_m=TOP_M, judge=True,
+    ad = hy.Adapt(ham, pool, "mixed", max_iter=it, screen_top_m=args.top_m, judge=True,
                   refine_every=0 if args.judge_only else 1)
     ad.set_ranker(ranker, warm_iters=args.warmup, epochs=30, refresh_every=REFRESH)
     ranked = ad.run(it)
@@ -176,7 +178,7 @@ def ranker_eval(args):
                         "same_op": p["selected"] == r["selected"],
                         "t_screen_plain": round(p["t_screen"], 5)})
         rows.append(row)
-    print(json.dumps({"ranker_eval": args.workload, "top_m": TOP_M, "warm": args.warmup,
+    print(json.dumps({"ranker_eval": args.workload, "top_m": args.top_m, "warm": args.warmup,
                       "refresh_every": REFRESH, "pool_ops": len(pool), "rows": rows}), flush=True)
 
 
@@ -364,7 +366,7 @@ def adapt_leg(ham, pool, hy, torch, args, rank, world, sparse, clocks=None):
     stream = torch.cuda.current_stream()
     cap = W + 2 * S + 6
     ranker = hy.Ranker(hidden=256, seed=7 + rank)
-    ad = hy.Adapt(ham, pool, "mixed", max_iter=cap, screen_top_m=TOP_M, refine_every=0,
+    ad = hy.Adapt(ham, pool, "mixed", max_iter=cap, screen_top_m=args.top_m, refine_every=0,
                   sparse=sparse)
     ad.set_ranker(ranker, warm_iters=W, epochs=30, refresh_every=REFRESH)
 
@@ -461,6 +463,7 @@ def leg_summary(leg, S):
     out = {"iters_per_s": round(S / (leg["ms"] / 1e3), 5),
            "n_evals": [rec["n_evals"] for rec in leg["timed"]],
            "t_screen_s": [round(rec["t_screen"], 4) for rec in leg["timed"]],
+           "support": [rec["support"] for rec in leg["timed"]],
            "energy_bulk": [rec["energy"] for rec in leg["timed"]],
            "final_energy_f64": leg["e_final"],
            "final_bulk_minus_f64": leg["e_bulk"] - leg["e_final"],
@@ -499,8 +502,6 @@ def main():
     mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
     fp64_peak = 152 * 2 * 2 * mhz * 1e6 / 1e12
-    flops = 2.0 * r["conn"] * N
-    cflops = 2.0 * r["cpl_units"] * N      # the coupling kernel's share of the connections
 
     def hp(ms, s):
         gbs = 2.0 * N * s / (ms / 1e3) / 1e9
@@ -512,9 +513,13 @@ def main():
         print(json.dumps({"adapt_only": args.workload,
                           "iters_per_s": round(S / (r["head"]["ms"] / 1e3), 5),
                           "n_evals": [rec["n_evals"] for rec in r["head"]["timed"]],
+                          "support": [rec["support"] for rec in r["head"]["timed"]],
+                          "t_total": [round(rec["t_total"], 4) for rec in r["head"]["timed"]],
                           "launches": r["head"]["launches"]}), flush=True)
         return
     head, dense = r["head"], r["dense"]
+    flops = 2.0 * r["conn"] * N
+    cflops = 2.0 * r["cpl_units"] * N      # the coupling kernel's share of the connections
     out = {
         "metric": METRIC,
         "value": round(job_throughput(world, S, head["ms"]), 6),

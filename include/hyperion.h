@@ -78,6 +78,30 @@ const char *hy_version(void);
  * the kernels of each CUDA-graph replay it issues). */
 int64_t hy_launch_count(void);
 
+/* Kernel-class timing.  hy_profile_enable(mask) clears the counters and, for
+ * every class whose bit (1u << class) is set, makes the library record a
+ * pair of CUDA events on the launching stream around each of its launches of
+ * that class, with the algorithmic bytes those launches move (0 where the
+ * host does not know them, e.g. sparse work whose size lives on the device).
+ * hy_profile_read waits for the recorded events and returns, per class, the
+ * launches, the summed device milliseconds and the summed bytes.  mask = 0
+ * (the default) records nothing and costs nothing.  Process-wide; calls may
+ * come from several threads. */
+typedef enum {
+    HY_PROF_HPSI = 0,          /* dense H|psi> (hy_apply_h): 2 N s bytes       */
+    HY_PROF_HPSI_SPARSE = 1,   /* scatter H|psi> incl. zeroing sigma: N s      */
+    HY_PROF_EXCITE = 2,        /* dense exp(theta A) pair rotations: 4 s/pair  */
+    HY_PROF_SPARSE_EXCITE = 3, /* rotations of a sparse state (bytes 0)        */
+    HY_PROF_SCREEN = 4,        /* dense pool gradients: 4 s per pair per op    */
+    HY_PROF_SCREEN_SPARSE = 5, /* support-restricted gradients (bytes 0)       */
+    HY_PROF_REDUCE = 6,        /* dots / norms / renormalisation: s per read
+                                  or written amplitude                         */
+    HY_PROF_FEATURES = 7,      /* ranker features: 2 N s (psi and sigma)       */
+    HY_PROF_CLASSES = 8
+} hy_prof_class;
+hy_status hy_profile_enable(uint32_t class_mask);
+hy_status hy_profile_read(int cls, int64_t *launches, double *ms, double *bytes);
+
 /* ---------------------------------------------------------------------- */
 /* Hamiltonian                                                              */
 /* ---------------------------------------------------------------------- */
@@ -264,6 +288,24 @@ hy_status hy_apply_excitation(const hy_ham *h, const hy_pool *p, int64_t k,
                               double theta, void *psi, hy_dtype dt,
                               int renormalize, void *stream);
 
+/* Renormalisation after each exp(theta A) (paper: Method, mixed precision --
+ * the renormalisation stays in double) without a sweep over the state:
+ * hy_apply_excitation_tracked applies exp(theta A_k) like
+ * hy_apply_excitation (no renormalisation) and adds to the device scalar
+ * *norm2 the change of ||psi||^2 over the rotated pairs, with FP64 accuracy
+ * (FP64 products for HY_F64; for HY_F32 exact FP32 products summed by the
+ * compensated Dot2 scheme and flushed into FP64 every 32 terms).  Untouched
+ * amplitudes keep their norm, so starting from *norm2 = ||psi||^2 it tracks
+ * the norm through a product of rotations; scaling commutes with the
+ * rotations, so one hy_renormalize (psi <- psi / sqrt(*norm2); *norm2 is
+ * read, not changed) after the last one equals renormalising after each.
+ * norm2: device pointer, 8-byte aligned, ordered on `stream`. */
+hy_status hy_apply_excitation_tracked(const hy_ham *h, const hy_pool *p, int64_t k,
+                                      double theta, void *psi, hy_dtype dt,
+                                      double *norm2, void *stream);
+hy_status hy_renormalize(const hy_ham *h, void *psi, hy_dtype dt,
+                         const double *norm2, void *stream);
+
 /* Scale psi by 1 / sqrt(<psi|psi>) (norm accumulated in double). */
 hy_status hy_normalize(const hy_ham *h, void *psi, hy_dtype dt, void *stream);
 
@@ -448,13 +490,23 @@ typedef struct {
                              a ranker proposes (hy_adapt_set_ranker)           */
     int judge;            /* with screen_top_m > 0: also run the full screen
                              and report the true argmax and its rank           */
-    int sparse;           /* 1: while psi has at most N_det / 64 nonzero
-                             amplitudes, apply H and screen through the sparse
-                             path (hy_apply_h_sparse, hy_pool_gradients_sparse),
-                             and while (pool size) x (nonzeros) <= 5e9 screen
-                             the whole pool exactly even when a ranker is
-                             attached (its pairs still train the ranker);
+    int sparse;           /* 1: keep psi as a sparse vector (support list +
+                             membership bitmap over the dense array) while its
+                             support fits sparse_cap: state preparation,
+                             renormalisation, energy and the adjoint's psi
+                             side cost O(support), H psi is the scatter of
+                             hy_apply_h_sparse, and the screen visits only
+                             pairs with a listed end; when the list overflows
+                             the evaluation is redone with the dense sweeps,
+                             which stay in use while the ansatz is at least as
+                             long.  While (pool size) x (support) <= 5e9 the
+                             whole pool is screened exactly even when a
+                             ranker is attached (its pairs still train it).
                              0: always the dense sweeps                        */
+    int64_t sparse_cap;   /* support capacity of the sparse path; 0: N_det/64
+                             for double and N_det/256 for float evaluations
+                             (about where the scatter H psi stops beating the
+                             dense sweep)                                     */
 } hy_adapt_config;
 
 /* One ADAPT iteration (all times in seconds, host wall clock). */
@@ -476,6 +528,8 @@ typedef struct {
                               (0 = proposed first; -1 = not proposed)          */
     double t_screen, t_optimise, t_total;   /* judge time excluded            */
     double t_judge;        /* judge: time of the extra full screen and refit  */
+    int64_t support;       /* nonzero amplitudes of psi at the screen when the
+                              sparse path ran it, -1 for the dense sweeps     */
 } hy_adapt_record;
 
 

@@ -32,6 +32,28 @@ def launch_count() -> int:
     return int(_abi.load().hy_launch_count())
 
 
+# kernel classes of hy_profile_* (include/hyperion.h, hy_prof_class)
+PROFILE_CLASSES = ("hpsi", "hpsi_sparse", "excite", "sparse_excite", "screen", "screen_sparse",
+                   "reduce", "features")
+
+
+def profile_enable(classes=()) -> None:
+    """Clear the kernel-class counters and record CUDA events around the
+    library's launches of the named classes (empty: stop recording)."""
+    mask = 0
+    for c in classes:
+        mask |= 1 << PROFILE_CLASSES.index(c)
+    check(_abi.load().hy_profile_enable(mask))
+
+
+def profile_read(cls: str) -> dict:
+    """{launches, ms, bytes} recorded for one class since profile_enable."""
+    n, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    check(_abi.load().hy_profile_read(PROFILE_CLASSES.index(cls), ctypes.byref(n),
+                                      ctypes.byref(ms), ctypes.byref(by)))
+    return {"launches": n.value, "ms": ms.value, "bytes": by.value}
+
+
 def dtype_code(t: torch.dtype) -> int:
     if t == torch.float64:
         return HY_F64
@@ -200,6 +222,15 @@ class Hamiltonian:
                                        stream_ptr(stream)))
         return psi
 
+    def renormalize(self, psi: torch.Tensor, norm2: torch.Tensor, stream=None) -> torch.Tensor:
+        """psi <- psi / sqrt(norm2) with norm2 a float64 device scalar."""
+        self._check_state(psi)
+        if norm2.dtype != torch.float64 or norm2.device != psi.device or norm2.numel() != 1:
+            raise ValueError("norm2 must be a float64 scalar on the state's device")
+        check(_abi.load().hy_renormalize(self._h, _ptr(psi), dtype_code(psi.dtype),
+                                         _ptr(norm2), stream_ptr(stream)))
+        return psi
+
 
 class Pool:
     """Spin-adapted singles+doubles pool relative to the HF determinant."""
@@ -277,6 +308,18 @@ class Pool:
             dtype_code(psi.dtype), 1 if renormalize else 0, stream_ptr(stream)))
         return psi
 
+    def apply_excitation_tracked(self, k: int, theta: float, psi: torch.Tensor,
+                                 norm2: torch.Tensor, stream=None) -> torch.Tensor:
+        """exp(theta A_k) psi in place, adding the change of ||psi||^2 over
+        the rotated pairs to norm2 (a float64 device scalar)."""
+        self.ham._check_state(psi)
+        if norm2.dtype != torch.float64 or norm2.device != psi.device or norm2.numel() != 1:
+            raise ValueError("norm2 must be a float64 scalar on the state's device")
+        check(_abi.load().hy_apply_excitation_tracked(
+            self.ham.handle, self._p, int(k), float(theta), _ptr(psi),
+            dtype_code(psi.dtype), _ptr(norm2), stream_ptr(stream)))
+        return psi
+
 
 class Adapt:
     """ADAPT-VQE driver (hy_adapt_*): screen, select, append, re-optimise.
@@ -287,7 +330,8 @@ class Adapt:
 
     def __init__(self, ham: Hamiltonian, pool: Pool, precision="f64", max_iter=64,
                  eps_grad=1e-5, gtol=1e-9, gtol_bulk=1e-5, max_evals=200,
-                 refine_steps=4, refine_every=1, screen_top_m=0, judge=False, sparse=False):
+                 refine_steps=4, refine_every=1, screen_top_m=0, judge=False, sparse=False,
+                 sparse_cap=0):
         lib = _abi.load()
         self.ham, self.pool = ham, pool
         if precision not in ("f64", "mixed"):
@@ -295,7 +339,8 @@ class Adapt:
         cfg = _abi.AdaptConfig(HY_F64 if precision == "f64" else HY_F32, int(max_iter),
                                float(eps_grad), float(gtol), float(gtol_bulk),
                                int(max_evals), int(refine_steps), int(refine_every),
-                               int(screen_top_m), 1 if judge else 0, 1 if sparse else 0)
+                               int(screen_top_m), 1 if judge else 0, 1 if sparse else 0,
+                               int(sparse_cap))
         handle = ctypes.c_void_p()
         check(lib.hy_adapt_create(ham.handle, pool.handle, ctypes.byref(cfg),
                                   ctypes.byref(handle)))

@@ -43,7 +43,8 @@ class AdaptConfig(ctypes.Structure):
                 ("gtol_bulk", ctypes.c_double), ("max_evals", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("refine_every", ctypes.c_int),
                 ("screen_top_m", ctypes.c_int),
-                ("judge", ctypes.c_int), ("sparse", ctypes.c_int)]
+                ("judge", ctypes.c_int), ("sparse", ctypes.c_int),
+                ("sparse_cap", ctypes.c_int64)]
 
 
 class AdaptRecord(ctypes.Structure):
@@ -55,7 +56,8 @@ class AdaptRecord(ctypes.Structure):
                 ("n_evals", ctypes.c_int32), ("n_evals_f64", ctypes.c_int32),
                 ("true_argmax", ctypes.c_int64), ("true_rank", ctypes.c_int64),
                 ("t_screen", ctypes.c_double), ("t_optimise", ctypes.c_double),
-                ("t_total", ctypes.c_double), ("t_judge", ctypes.c_double)]
+                ("t_total", ctypes.c_double), ("t_judge", ctypes.c_double),
+                ("support", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -72,6 +74,8 @@ SIGNATURES = {
     "hy_last_error": (ctypes.c_char_p, []),
     "hy_version": (ctypes.c_char_p, []),
     "hy_launch_count": (I64, []),
+    "hy_profile_enable": (I32, [ctypes.c_uint32]),
+    "hy_profile_read": (I32, [I32, PI64, ctypes.POINTER(D), ctypes.POINTER(D)]),
     "hy_build_hamiltonian": (I32, [P, P, D, I32, I32, I32, D, PP]),
     "hy_ham_destroy": (I32, [P]),
     "hy_ham_info": (I32, [P, PI64, PI64, PI64, PI64, PI64]),
@@ -94,6 +98,8 @@ SIGNATURES = {
     "hy_pool_describe": (I32, [P, I64, P]),
     "hy_pool_gradients": (I32, [P, P, P, P, P, I64, P, I32, P]),
     "hy_apply_excitation": (I32, [P, P, I64, D, P, I32, I32, P]),
+    "hy_apply_excitation_tracked": (I32, [P, P, I64, D, P, I32, P, P]),
+    "hy_renormalize": (I32, [P, P, I32, P, P]),
     "hy_pool_gradients_noalloc": (I32, [P, P, P, P, P, I64, P, I32, P]),
     "hy_batch_create": (I32, [P, I32, PP]),
     "hy_batch_destroy": (I32, [P]),

@@ -63,9 +63,17 @@ struct hy_adapt {
     int evals = 0, evals64 = 0;
     int iter = 0;
     int64_t h2d = 0, d2h = 0;     // bytes copied host <-> device so far
-    // sparse path: nonzero list of the last evaluated state (-1: dense)
-    int64_t *d_list = nullptr, *d_count = nullptr;
-    int64_t sparse_cap = 0, sparse_m = -1;
+    // sparse path: psi and phi of each precision as sparse vectors over
+    // buf[dt][0] and buf[dt][2]; clean: the dense array and bitmap hold
+    // exactly the listed support (false after dense use or an overflow)
+    hy::SparseState *ss[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    bool ss_clean[2][2] = {{false, false}, {false, false}};
+    // ansatz length at which a precision's support list overflowed: the
+    // dense sweeps serve that precision while the ansatz is this long
+    size_t sparse_fail_len[2] = {SIZE_MAX, SIZE_MAX};
+    int64_t sparse_m = -1;        // support of the last evaluated state (-1: dense)
+    double *d_n2 = nullptr;       // tracked squared norm (float renormalisation)
+    double *d_one = nullptr;      // device constants {1.0, 1.0f}
 };
 
 namespace {
@@ -95,42 +103,19 @@ hy_status xfer(hy_adapt *a, void *dst, const void *src, size_t bytes, cudaMemcpy
     return cu(cudaMemcpyAsync(dst, src, bytes, kind, st), what);
 }
 
-// psi <- HF determinant (index 0: lowest orbitals of both spins occupied)
+// psi <- HF determinant (index 0: lowest orbitals of both spins occupied);
+// the amplitude comes from a device constant, so nothing waits on the host
 hy_status set_hf(hy_adapt *a, void *psi, hy_dtype dt, cudaStream_t st)
 {
-    static const double one64 = 1.0;
-    static const float one32 = 1.0f;
     HY_TRY(cu(cudaMemsetAsync(psi, 0, size_t(a->N) * esize(dt), st), "memset"));
-    const void *src = dt == HY_F64 ? static_cast<const void *>(&one64)
-                                   : static_cast<const void *>(&one32);
-    return xfer(a, psi, src, esize(dt), cudaMemcpyHostToDevice, st, "set HF amplitude");
+    const void *one = dt == HY_F64 ? static_cast<const void *>(a->d_one)
+                                   : static_cast<const void *>(a->d_one + 1);
+    return cu(cudaMemcpyAsync(psi, one, esize(dt), cudaMemcpyDeviceToDevice, st),
+              "set HF amplitude");
 }
 
-// psi = U(theta) |HF>, sigma = H psi, returns E = <psi|sigma>
-hy_status energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
-                 cudaStream_t st, double *e)
+hy_status finish_energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt)
 {
-    void *psi = a->buf[di(dt)][0], *sigma = a->buf[di(dt)][1];
-    HY_TRY(set_hf(a, psi, dt, st));
-    const int renorm = dt == HY_F32 ? 1 : 0;
-    for (size_t l = 0; l < a->ops.size(); ++l)
-        HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], th[l], psi, dt, renorm, st));
-    a->sparse_m = -1;
-    if (a->cfg.sparse) {
-        int64_t cnt = 0;
-        HY_TRY(hy_support(a->h, psi, dt, a->d_list, a->sparse_cap, a->d_count, st));
-        HY_TRY(xfer(a, &cnt, a->d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, st,
-                    "support count"));
-        HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
-        if (cnt <= a->sparse_cap) a->sparse_m = cnt;
-    }
-    if (a->sparse_m >= 0)
-        HY_TRY(hy_apply_h_sparse(a->h, psi, sigma, dt, a->d_list, a->sparse_m, st));
-    else
-        HY_TRY(hy_apply_h(a->h, psi, sigma, dt, st));
-    HY_TRY(hy_energy(a->h, psi, sigma, dt, a->d_e, st));
-    HY_TRY(xfer(a, e, a->d_e, sizeof(double), cudaMemcpyDeviceToHost, st, "energy readback"));
-    HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
     ++a->evals;
     if (dt == HY_F64) ++a->evals64;
     a->valid_dt = dt;
@@ -138,15 +123,84 @@ hy_status energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     return HY_OK;
 }
 
+// The sparse evaluation: psi = U(theta)|HF> as a sparse vector (rotations
+// cost O(support)), renormalised over its support in double (float states),
+// sigma = H psi by the scatter, E = <psi|sigma> over the support.  *ok =
+// false when the support list overflowed (nothing valid is left).
+hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
+                        cudaStream_t st, double *e, bool *ok)
+{
+    const int d = di(dt);
+    hy::SparseState *S = a->ss[d][0];
+    void *psi = a->buf[d][0], *sigma = a->buf[d][1];
+    HY_TRY(hy::sstate_reset(S, !a->ss_clean[d][0], true, st));
+    a->ss_clean[d][0] = true;
+    for (size_t l = 0; l < a->ops.size(); ++l)
+        HY_TRY(hy::sstate_excite(S, a->p, a->ops[l], th[l], st));
+    if (dt == HY_F32 && !a->ops.empty()) {
+        HY_TRY(hy::sstate_dot(S, psi, a->d_n2, st));
+        HY_TRY(hy::sstate_scale_rsqrt(S, a->d_n2, st));
+    }
+    HY_TRY(hy::sstate_apply_h(S, sigma, st));
+    HY_TRY(hy::sstate_dot(S, sigma, a->d_e, st));
+    int64_t cnt = 0;
+    HY_TRY(xfer(a, e, a->d_e, sizeof(double), cudaMemcpyDeviceToHost, st, "energy readback"));
+    HY_TRY(xfer(a, &cnt, hy::sstate_count(S), sizeof(int64_t), cudaMemcpyDeviceToHost, st,
+                "support count"));
+    HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+    *ok = cnt <= hy::sstate_cap(S);
+    if (!*ok) {
+        a->ss_clean[d][0] = false;
+        return HY_OK;
+    }
+    a->sparse_m = cnt;
+    return HY_OK;
+}
+
+// psi = U(theta) |HF>, sigma = H psi, returns E = <psi|sigma>
+hy_status energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
+                 cudaStream_t st, double *e)
+{
+    const int d = di(dt);
+    a->sparse_m = -1;
+    if (a->cfg.sparse && a->ops.size() < a->sparse_fail_len[d]) {
+        bool ok = false;
+        HY_TRY(energy_sparse(a, th, dt, st, e, &ok));
+        if (ok) return finish_energy(a, th, dt);
+        a->sparse_fail_len[d] = a->ops.size();
+    }
+    void *psi = a->buf[d][0], *sigma = a->buf[d][1];
+    a->ss_clean[d][0] = false;
+    HY_TRY(set_hf(a, psi, dt, st));
+    // float states: the squared norm is tracked through the rotations in
+    // double and the state renormalised once after the last one (equal to
+    // renormalising after each: the scaling commutes with the rotations)
+    const bool track = dt == HY_F32 && !a->ops.empty();
+    if (track)
+        HY_TRY(cu(cudaMemcpyAsync(a->d_n2, a->d_one, 8, cudaMemcpyDeviceToDevice, st), "norm"));
+    for (size_t l = 0; l < a->ops.size(); ++l) {
+        if (track)
+            HY_TRY(hy_apply_excitation_tracked(a->h, a->p, a->ops[l], th[l], psi, dt, a->d_n2, st));
+        else
+            HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], th[l], psi, dt, 0, st));
+    }
+    if (track) HY_TRY(hy_renormalize(a->h, psi, dt, a->d_n2, st));
+    HY_TRY(hy_apply_h(a->h, psi, sigma, dt, st));
+    HY_TRY(hy_energy(a->h, psi, sigma, dt, a->d_e, st));
+    HY_TRY(xfer(a, e, a->d_e, sizeof(double), cudaMemcpyDeviceToHost, st, "energy readback"));
+    HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+    return finish_energy(a, th, dt);
+}
+
 // adjoint gradient at the point of the last energy() call in dt
-hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
-                   cudaStream_t st, std::vector<double> &g)
+hy_status gradient_dense(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
+                         cudaStream_t st, std::vector<double> &g)
 {
     const size_t j = a->ops.size(), es = esize(dt);
-    g.assign(j, 0.0);
-    if (j == 0) return HY_OK;
-    void *psi = a->buf[di(dt)][0], *sigma = a->buf[di(dt)][1];
-    void *phi = a->buf[di(dt)][2], *lam = a->buf[di(dt)][3];
+    const int d = di(dt);
+    void *psi = a->buf[d][0], *sigma = a->buf[d][1];
+    void *phi = a->buf[d][2], *lam = a->buf[d][3];
+    a->ss_clean[d][1] = false;
     HY_TRY(cu(cudaMemcpyAsync(phi, psi, size_t(a->N) * es, cudaMemcpyDeviceToDevice, st), "copy"));
     HY_TRY(cu(cudaMemcpyAsync(lam, sigma, size_t(a->N) * es, cudaMemcpyDeviceToDevice, st), "copy"));
     for (size_t l = j; l-- > 0;) {
@@ -158,6 +212,42 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     HY_TRY(xfer(a, g.data(), a->d_ga, j * sizeof(double), cudaMemcpyDeviceToHost, st,
                 "gradient readback"));
     return cu(cudaStreamSynchronize(st), "sync");
+}
+
+// adjoint gradient at the point of the last energy() call in dt:
+// dE/dtheta_l = 2 <lam_l | A_l phi_l> with phi_l = U_l..U_1|HF> and lam_l =
+// U_{l+1}^dag..U_L^dag H psi, both walked back from (psi, H psi).  After a
+// sparse evaluation phi stays a sparse vector (its side costs O(support))
+// and lam, which H spreads over most determinants, is rotated densely.
+hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
+                   cudaStream_t st, std::vector<double> &g)
+{
+    const size_t j = a->ops.size(), es = esize(dt);
+    g.assign(j, 0.0);
+    if (j == 0) return HY_OK;
+    if (a->sparse_m < 0) return gradient_dense(a, th, dt, st, g);
+    const int d = di(dt);
+    hy::SparseState *P = a->ss[d][0], *F = a->ss[d][1];
+    void *sigma = a->buf[d][1], *lam = a->buf[d][3];
+    HY_TRY(hy::sstate_reset(F, !a->ss_clean[d][1], false, st));
+    a->ss_clean[d][1] = true;
+    HY_TRY(hy::sstate_copy(F, P, st));
+    HY_TRY(cu(cudaMemcpyAsync(lam, sigma, size_t(a->N) * es, cudaMemcpyDeviceToDevice, st), "copy"));
+    for (size_t l = j; l-- > 0;) {
+        HY_TRY(hy::sstate_gradients(F, lam, a->p, a->d_ops + l, 1, a->sparse_m, a->d_ga + l, st));
+        if (l == 0) break;
+        HY_TRY(hy::sstate_excite(F, a->p, a->ops[l], -th[l], st));
+        HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], -th[l], lam, dt, 0, st));
+    }
+    int64_t cnt = 0;
+    HY_TRY(xfer(a, g.data(), a->d_ga, j * sizeof(double), cudaMemcpyDeviceToHost, st,
+                "gradient readback"));
+    HY_TRY(xfer(a, &cnt, hy::sstate_count(F), sizeof(int64_t), cudaMemcpyDeviceToHost, st,
+                "support count"));
+    HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+    if (cnt <= hy::sstate_cap(F)) return HY_OK;
+    a->ss_clean[d][1] = false;    // phi's list overflowed: redo densely
+    return gradient_dense(a, th, dt, st, g);
 }
 
 hy_status upload_ops(hy_adapt *a, cudaStream_t st)
@@ -348,10 +438,11 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
         c.screen_top_m = 0;
         c.judge = 0;
         c.sparse = 0;
+        c.sparse_cap = 0;
     }
     if ((c.bulk != HY_F64 && c.bulk != HY_F32) || c.max_iter < 1 || c.max_iter > (1 << 20) ||
         !(c.eps_grad >= 0) || !(c.gtol > 0) || !(c.gtol_bulk > 0) || c.max_evals < 1 ||
-        c.refine_steps < 0 || c.refine_every < 0 || c.screen_top_m < 0)
+        c.refine_steps < 0 || c.refine_every < 0 || c.screen_top_m < 0 || c.sparse_cap < 0)
         return set_err(HY_ERR_ARG, "invalid hy_adapt_config");
     hy_adapt *a = new (std::nothrow) hy_adapt;
     if (!a) return set_err(HY_ERR_OOM, "host allocation failed");
@@ -378,10 +469,28 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
         alloc(reinterpret_cast<void **>(&a->d_score), size_t(a->K) * 4);
         alloc(reinterpret_cast<void **>(&a->d_gp), size_t(a->K) * 8);
     }
+    alloc(reinterpret_cast<void **>(&a->d_n2), 8);
+    alloc(reinterpret_cast<void **>(&a->d_one), 16);
+    if (s == HY_OK) {
+        unsigned char one[16] = {};
+        const double one64 = 1.0;
+        const float one32 = 1.0f;
+        std::memcpy(one, &one64, 8);
+        std::memcpy(one + 8, &one32, 4);
+        s = cu(cudaMemcpy(a->d_one, one, 16, cudaMemcpyHostToDevice), "constants");
+    }
     if (c.sparse) {
-        a->sparse_cap = std::max<int64_t>(1, a->N / 64);
-        alloc(reinterpret_cast<void **>(&a->d_list), size_t(a->sparse_cap) * 8);
-        alloc(reinterpret_cast<void **>(&a->d_count), 8);
+        for (int d = 0; d < 2 && s == HY_OK; ++d) {
+            if (!a->buf[d][0]) continue;
+            // the scatter H psi costs ~ support x 5,800 atomic adds: about the
+            // dense double sweep at N/64, the dense float one at N/256
+            int64_t cap = c.sparse_cap > 0 ? std::min(c.sparse_cap, a->N)
+                                           : a->N / (d == 0 ? 64 : 256);
+            cap = std::max<int64_t>(cap, 1);
+            const hy_dtype dt = d == 0 ? HY_F64 : HY_F32;
+            for (int b = 0; b < 2 && s == HY_OK; ++b)
+                s = hy::sstate_create(h, dt, a->buf[d][b == 0 ? 0 : 2], cap, &a->ss[d][b]);
+        }
     }
     a->last_g.assign(a->K, -1.0);
     a->age.assign(a->K, 0);
@@ -410,8 +519,10 @@ hy_status hy_adapt_destroy(hy_adapt *a)
     cudaFree(a->d_extra);
     cudaFree(a->d_score);
     cudaFree(a->d_gp);
-    cudaFree(a->d_list);
-    cudaFree(a->d_count);
+    cudaFree(a->d_n2);
+    cudaFree(a->d_one);
+    for (auto &row : a->ss)
+        for (hy::SparseState *&x : row) hy::sstate_destroy(x);
     delete a;
     return HY_OK;
 }
@@ -436,6 +547,7 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         HY_TRY(energy(a, a->theta, bulk, st, &e));
     }
     void *psi = a->buf[di(bulk)][0], *sigma = a->buf[di(bulk)][1];
+    rec->support = a->sparse_m;
     // 2. screen: full, or the ranker's top-M proposals screened exactly
     const bool ranked = a->cfg.screen_top_m > 0;
     if (ranked && !a->ranker) return set_err(HY_ERR_UNSUPPORTED, "ranked screen needs a ranker");
@@ -456,8 +568,8 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     double gmax = 0.0, gn2 = 0.0;
     auto full_screen = [&]() -> hy_status {
         if (a->sparse_m >= 0)
-            HY_TRY(hy_pool_gradients_sparse(a->h, a->p, psi, sigma, a->d_list, a->sparse_m,
-                                            nullptr, a->K, a->d_g, bulk, st));
+            HY_TRY(hy::sstate_gradients(a->ss[di(bulk)][0], sigma, a->p, nullptr, a->K,
+                                        a->sparse_m, a->d_g, st));
         else
             HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, nullptr, a->K, a->d_g, bulk, st));
         g.assign(a->K, 0.0);
@@ -524,8 +636,8 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
                     "proposals upload"));
         const int64_t Mp = int64_t(prop.size());
         if (a->sparse_m >= 0)
-            HY_TRY(hy_pool_gradients_sparse(a->h, a->p, psi, sigma, a->d_list, a->sparse_m,
-                                            a->d_prop, Mp, a->d_gp, bulk, st));
+            HY_TRY(hy::sstate_gradients(a->ss[di(bulk)][0], sigma, a->p, a->d_prop, Mp,
+                                        a->sparse_m, a->d_gp, st));
         else
             HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, a->d_prop, Mp, a->d_gp, bulk, st));
         std::vector<double> gp(Mp);

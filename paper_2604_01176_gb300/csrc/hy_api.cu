@@ -97,6 +97,7 @@ struct hy_ham {
     float *d_pairB = nullptr;                   // [2][Na][n^2] touched-weight partials
     float *d_pairRs = nullptr;                  // [2][Na]
     float *d_pairD = nullptr;                   // [2][n^4] touched weights (psi, sigma)
+    float *d_pairP = nullptr;                   // [splits][n^4] contraction partials
     int occ_blocks = 0;
     // workspace (grown on demand; growth synchronises the device)
     void *ws = nullptr;
@@ -186,7 +187,8 @@ hy_status ensure_ws(hy_ham *h, size_t bytes)
 
 size_t n_partials_needed(const hy_ham *h, int64_t n_ops)
 {
-    size_t p = size_t(h->dot_blocks) + 64;
+    // dot partials, or the tracked rotation's (<= 16 blocks per SM + 128)
+    size_t p = std::max(size_t(h->dot_blocks), size_t(16) * h->num_sms + 128) + 64;
     size_t g = size_t(n_ops) + size_t(4) * h->num_sms + 1024;
     return p > g ? p : g;
 }
@@ -276,6 +278,7 @@ hy_status apply_h_t(hy_ham *h, const T *psi, T *sigma, cudaStream_t st)
         Ma = &h->Ma32; Mb = &h->Mb32; V = h->d_V32;
     }
     (void)f64;
+    hy::ProfScope prof(HY_PROF_HPSI, st, 2.0 * double(h->N) * sizeof(T));
     HY_CUDA(hy::k::spmm<T>(Ma->ptr, Ma->col, Ma->val, h->Na, psi, sigma, h->Nb,
                            false, st), "alpha part");
     HY_CUDA(hy::k::transpose<T>(psi, psiT, h->Na, h->Nb, st), "transpose");
@@ -332,6 +335,7 @@ hy_status dot_t(hy_ham *h, const T *x, const T *y, double *out, cudaStream_t st)
     hy_status s = ensure_ws(h, L.total);
     if (s != HY_OK) return s;
     double *partials = reinterpret_cast<double *>(static_cast<char *>(h->ws) + L.partials);
+    hy::ProfScope prof(HY_PROF_REDUCE, st, 2.0 * double(h->N) * sizeof(T));
     HY_CUDA(hy::k::dot<T>(x, y, h->N, partials, h->dot_blocks, out, st), "dot");
     return HY_OK;
 }
@@ -345,6 +349,7 @@ hy_status normalize_t(hy_ham *h, T *psi, cudaStream_t st)
     double *n2 = reinterpret_cast<double *>(static_cast<char *>(h->ws) + L.scalar);
     s = dot_t<T>(h, psi, psi, n2, st);
     if (s != HY_OK) return s;
+    hy::ProfScope prof(HY_PROF_REDUCE, st, 2.0 * double(h->N) * sizeof(T));
     HY_CUDA(hy::k::scale_rsqrt<T>(psi, h->N, n2, st), "normalize");
     return HY_OK;
 }
@@ -389,6 +394,16 @@ hy_status grad_t(hy_ham *h, const hy_pool *p, const T *psi, const T *sigma,
     a.CH = grad_chunks(h, n_ops);
     a.partials = reinterpret_cast<double *>(static_cast<char *>(h->ws) + L.partials);
     a.g = g;
+    double bytes = 0.0;     // pairs of the listed operators (known for the whole pool)
+    if (!ops)
+        for (const auto &od : p->opd)
+            for (int q = 0; q < od.nc; ++q) {
+                const hy::k::ConsDev &cd = p->cons[q == 0 ? od.c0 : od.c1];
+                const double nr = cd.ap < 0 ? double(h->Na) : double(p->pa.cnt[cd.ap]);
+                const double nc = cd.bp < 0 ? double(h->Nb) : double(p->pb.cnt[cd.bp]);
+                bytes += 4.0 * nr * nc * sizeof(T);
+            }
+    hy::ProfScope prof(HY_PROF_SCREEN, st, bytes);
     HY_CUDA(hy::k::grad<T>(a, st), "pool gradients");
     return HY_OK;
 }
@@ -405,8 +420,34 @@ hy_status excite_t(hy_ham *h, const hy_pool *p, int64_t k, double theta, T *psi,
         int64_t nr = h->Na, nc = h->Nb;
         if (cd.ap >= 0) { ae = p->d_aent + p->pa.off[cd.ap]; nr = p->pa.cnt[cd.ap]; }
         if (cd.bp >= 0) { be = p->d_bent + p->pb.off[cd.bp]; nc = p->pb.cnt[cd.bp]; }
+        hy::ProfScope prof(HY_PROF_EXCITE, st, 4.0 * double(nr) * double(nc) * sizeof(T));
         HY_CUDA(hy::k::excite<T>(psi, ae, nr, be, nc, h->Nb, c, cd.eps * sn, st),
                 "excitation");
+    }
+    return HY_OK;
+}
+
+// exp(theta A_k) adding the FP64-accurate change of ||psi||^2 to *norm2
+template <typename T>
+hy_status excite_tracked_t(hy_ham *h, const hy_pool *p, int64_t k, double theta, T *psi,
+                           double *norm2, cudaStream_t st)
+{
+    const WsLayout L = ws_layout(h, n_partials_needed(h, 0), sizeof(T));
+    hy_status s = ensure_ws(h, L.total);
+    if (s != HY_OK) return s;
+    double *partials = reinterpret_cast<double *>(static_cast<char *>(h->ws) + L.partials);
+    const hy::k::OpDev &od = p->opd[k];
+    const double c = std::cos(theta), sn = std::sin(theta);
+    for (int q = 0; q < od.nc; ++q) {
+        const hy::k::ConsDev &cd = p->cons[q == 0 ? od.c0 : od.c1];
+        const uint32_t *ae = nullptr, *be = nullptr;
+        int64_t nr = h->Na, nc = h->Nb;
+        if (cd.ap >= 0) { ae = p->d_aent + p->pa.off[cd.ap]; nr = p->pa.cnt[cd.ap]; }
+        if (cd.bp >= 0) { be = p->d_bent + p->pb.off[cd.bp]; nc = p->pb.cnt[cd.bp]; }
+        hy::ProfScope prof(HY_PROF_EXCITE, st, 4.0 * double(nr) * double(nc) * sizeof(T));
+        HY_CUDA(hy::k::excite_n<T>(psi, ae, nr, be, nc, h->Nb, c, cd.eps * sn, partials, norm2,
+                                   h->num_sms, st),
+                "tracked excitation");
     }
     return HY_OK;
 }
@@ -477,7 +518,7 @@ hy_status hy_build_hamiltonian(const double *h1, const double *h2, double e_core
         delete h;
         return cuda_fail(e, "device query");
     }
-    h->dot_blocks = 4 * h->num_sms;
+    h->dot_blocks = 8 * h->num_sms;
 
     // bexT: beta excitations transposed to [nexb][Nb] for coalesced reads
     std::vector<uint32_t> bexT(size_t(h->B.nex) * h->Nb);
@@ -516,6 +557,8 @@ hy_status hy_build_hamiltonian(const double *h1, const double *h2, double e_core
         up(ar.upload(&h->d_pairB, zb.data(), zb.size()), "touched-weight partials");
         up(ar.upload(&h->d_pairRs, zr.data(), zr.size()), "touched-weight partials");
         up(ar.upload(&h->d_pairD, zd.data(), zd.size()), "touched weights");
+        std::vector<float> zq(size_t(hy::k::pair_splits()) * nn * nn, 0.0f);
+        up(ar.upload(&h->d_pairP, zq.data(), zq.size()), "touched-weight partials");
     }
     if (s == HY_OK) s = upload_csr<double>(ar, h->kt.Ma, h->Ma64);
     if (s == HY_OK) s = upload_csr<double>(ar, h->kt.Mb, h->Mb64);
@@ -921,6 +964,35 @@ hy_status hy_apply_excitation(const hy_ham *hc, const hy_pool *p, int64_t k,
     return s;
 }
 
+hy_status hy_apply_excitation_tracked(const hy_ham *hc, const hy_pool *p, int64_t k, double theta,
+                                      void *psi, hy_dtype dt, double *norm2, void *stream)
+{
+    hy_ham *h = const_cast<hy_ham *>(hc);
+    if (!h || !p || !psi || !norm2 || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
+    if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
+    if (k < 0 || k >= int64_t(p->ops.size())) return fail(HY_ERR_ARG, "op index out of range");
+    if (!std::isfinite(theta)) return fail(HY_ERR_ARG, "theta is not finite");
+    if (dt == HY_F64)
+        return excite_tracked_t<double>(h, p, k, theta, static_cast<double *>(psi), norm2,
+                                        as_stream(stream));
+    return excite_tracked_t<float>(h, p, k, theta, static_cast<float *>(psi), norm2,
+                                   as_stream(stream));
+}
+
+hy_status hy_renormalize(const hy_ham *h, void *psi, hy_dtype dt, const double *norm2,
+                         void *stream)
+{
+    if (!h || !psi || !norm2 || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
+    hy::ProfScope prof(HY_PROF_REDUCE, stream, 2.0 * double(h->N) * (dt == HY_F64 ? 8 : 4));
+    if (dt == HY_F64)
+        HY_CUDA(hy::k::scale_rsqrt<double>(static_cast<double *>(psi), h->N, norm2,
+                                           as_stream(stream)), "renormalize");
+    else
+        HY_CUDA(hy::k::scale_rsqrt<float>(static_cast<float *>(psi), h->N, norm2,
+                                          as_stream(stream)), "renormalize");
+    return HY_OK;
+}
+
 hy_status hy_support(const hy_ham *h, const void *psi, hy_dtype dt, int64_t *list, int64_t cap,
                      int64_t *count, void *stream)
 {
@@ -939,6 +1011,17 @@ hy_status hy_support(const hy_ham *h, const void *psi, hy_dtype dt, int64_t *lis
 }  // extern "C"
 
 namespace {
+// support chunks per operator of the sparse screen: about 4 blocks per SM
+// in all, at most one chunk per 256 listed entries
+int sparse_chunks(const hy_ham *h, int64_t n_ops, int64_t m)
+{
+    int64_t ch = int64_t(4) * h->num_sms / (n_ops > 0 ? n_ops : 1);
+    const int64_t by_m = (m + 255) / 256;
+    if (ch > by_m) ch = by_m;
+    if (ch > 1024) ch = 1024;
+    return int(ch < 1 ? 1 : ch);
+}
+
 template <typename T>
 hy::k::SparseArgs<T> sparse_args(const hy_ham *h, const void *psi, void *sigma,
                                  const int64_t *list, int64_t m)
@@ -948,6 +1031,8 @@ hy::k::SparseArgs<T> sparse_args(const hy_ham *h, const void *psi, void *sigma,
     a.sigma = static_cast<T *>(sigma);
     a.list = list;
     a.m = m;
+    a.d_m = nullptr;
+    a.cap = m;
     const DevCsr<T> *Ma, *Mb;
     if constexpr (sizeof(T) == 8) {
         Ma = &h->Ma64; Mb = &h->Mb64; a.V = h->d_V64;
@@ -970,6 +1055,7 @@ hy_status hy_apply_h_sparse(const hy_ham *h, const void *psi, void *sigma, hy_dt
     if (!h || !psi || !sigma || !valid_dtype(dt) || m < 0 || (m > 0 && !list))
         return fail(HY_ERR_ARG, "bad arguments");
     if (psi == sigma) return fail(HY_ERR_ARG, "psi and sigma must not alias");
+    hy::ProfScope prof(HY_PROF_HPSI_SPARSE, stream, double(h->N) * (dt == HY_F64 ? 8 : 4));
     if (dt == HY_F64)
         HY_CUDA(hy::k::hpsi_scatter<double>(sparse_args<double>(h, psi, sigma, list, m), h->num_sms,
                                             as_stream(stream)), "sparse H psi");
@@ -989,11 +1075,19 @@ hy_status hy_pool_gradients_sparse(const hy_ham *h, const hy_pool *p, const void
     if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
     if (!ops_or_null) n_ops = int64_t(p->ops.size());
     if (n_ops < 0) return fail(HY_ERR_ARG, "n_ops out of range");
+    hy_ham *hm = const_cast<hy_ham *>(h);
+    const WsLayout L = ws_layout(hm, n_partials_needed(hm, n_ops), dt == HY_F64 ? 8 : 4);
+    hy_status st = ensure_ws(hm, L.total);
+    if (st != HY_OK) return st;
     auto fill = [&](auto &a) {
-        a.list = list; a.m = m; a.desc = p->d_desc; a.ops = ops_or_null; a.n_ops = n_ops;
+        a.list = list; a.m = m; a.d_m = nullptr; a.cap = m; a.bits = nullptr;
+        a.chunks = sparse_chunks(h, n_ops, m);
+        a.partials = reinterpret_cast<double *>(static_cast<char *>(hm->ws) + L.partials);
+        a.desc = p->d_desc; a.ops = ops_or_null; a.n_ops = n_ops;
         a.astr = h->d_astr; a.bstr = h->d_bstr; a.binom33 = h->d_binom; a.n = h->n;
         a.Nb = h->Nb; a.g = g_out;
     };
+    hy::ProfScope prof(HY_PROF_SCREEN_SPARSE, stream, 0.0);
     if (dt == HY_F64) {
         hy::k::SparseGradArgs<double> a;
         a.psi = static_cast<const double *>(psi);
@@ -1018,18 +1112,22 @@ hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
     if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
     cudaStream_t st = as_stream(stream);
     const size_t nn = size_t(h->n) * h->n;
+    hy::ProfScope prof(HY_PROF_FEATURES, st,
+                       (sigma_or_null ? 2.0 : 1.0) * double(h->N) * (dt == HY_F64 ? 8 : 4));
     const void *vecs[2] = {psi, sigma_or_null};
     for (int v = 0; v < 2 && vecs[v]; ++v) {
         float *B = h->d_pairB + size_t(v) * h->Na * nn, *rs = h->d_pairRs + size_t(v) * h->Na;
         float *D = h->d_pairD + size_t(v) * nn * nn;
         if (dt == HY_F64)
             HY_CUDA(hy::k::touched_weights<double>(static_cast<const double *>(vecs[v]), h->Na,
-                                                   h->Nb, h->d_astr, h->d_bstr, h->n, B, rs, D,
-                                                   h->num_sms, st), "touched weights");
+                                                   h->Nb, h->d_astr, h->d_bstr, h->n, B, rs,
+                                                   h->d_pairP, D, h->num_sms, st),
+                    "touched weights");
         else
             HY_CUDA(hy::k::touched_weights<float>(static_cast<const float *>(vecs[v]), h->Na,
-                                                  h->Nb, h->d_astr, h->d_bstr, h->n, B, rs, D,
-                                                  h->num_sms, st), "touched weights");
+                                                  h->Nb, h->d_astr, h->d_bstr, h->n, B, rs,
+                                                  h->d_pairP, D, h->num_sms, st),
+                    "touched weights");
     }
     if (dt == HY_F64)
         HY_CUDA(hy::k::occupations<double>(static_cast<const double *>(psi), h->Na, h->Nb,
@@ -1054,11 +1152,13 @@ hy_status hy_touched_weights(const hy_ham *h, const void *psi, hy_dtype dt, floa
     if (dt == HY_F64)
         HY_CUDA(hy::k::touched_weights<double>(static_cast<const double *>(psi), h->Na, h->Nb,
                                                h->d_astr, h->d_bstr, h->n, h->d_pairB,
-                                               h->d_pairRs, D, h->num_sms, st), "touched weights");
+                                               h->d_pairRs, h->d_pairP, D, h->num_sms, st),
+                "touched weights");
     else
         HY_CUDA(hy::k::touched_weights<float>(static_cast<const float *>(psi), h->Na, h->Nb,
                                               h->d_astr, h->d_bstr, h->n, h->d_pairB,
-                                              h->d_pairRs, D, h->num_sms, st), "touched weights");
+                                              h->d_pairRs, h->d_pairP, D, h->num_sms, st),
+                "touched weights");
     return HY_OK;
 }
 
@@ -1380,3 +1480,232 @@ hy_status hy_batch_tune(hy_batch *b, const void *psi, void *sigma, hy_dtype dt,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Sparse state vectors for the ADAPT driver (hy_internal.h).
+// ---------------------------------------------------------------------------
+struct hy::SparseState {
+    const hy_ham *h = nullptr;
+    hy_dtype dt = HY_F64;
+    void *v = nullptr;
+    int64_t cap = 0, words = 0;
+    int64_t *list = nullptr;
+    uint32_t *bits = nullptr;
+    unsigned long long *cnt = nullptr;   // [count, snapshot]
+    double *partials = nullptr;
+    int64_t n_partials = 0;
+};
+
+namespace {
+template <typename T>
+hy::k::SVec<T> svec(const hy::SparseState *s)
+{
+    hy::k::SVec<T> x;
+    x.v = static_cast<T *>(s->v);
+    x.list = s->list;
+    x.bits = s->bits;
+    x.count = s->cnt;
+    x.snap = s->cnt + 1;
+    x.cap = s->cap;
+    return x;
+}
+
+hy_status sstate_partials(hy::SparseState *s, int64_t need, cudaStream_t st)
+{
+    if (need <= s->n_partials) return HY_OK;
+    // queued kernels may still read the old buffer
+    HY_CUDA(cudaStreamSynchronize(st), "sync");
+    cudaFree(s->partials);
+    s->partials = nullptr;
+    s->n_partials = 0;
+    HY_CUDA(cudaMalloc(&s->partials, size_t(need) * sizeof(double)), "cudaMalloc(partials)");
+    s->n_partials = need;
+    return HY_OK;
+}
+}  // namespace
+
+namespace hy {
+
+hy_status sstate_create(const hy_ham *h, hy_dtype dt, void *v, int64_t cap, SparseState **out)
+{
+    if (!h || !v || !out || !valid_dtype(dt) || cap < 1) return fail(HY_ERR_ARG, "bad arguments");
+    *out = nullptr;
+    SparseState *s = new (std::nothrow) SparseState;
+    if (!s) return fail(HY_ERR_OOM, "host allocation failed");
+    s->h = h;
+    s->dt = dt;
+    s->v = v;
+    s->cap = cap;
+    s->words = (h->N + 31) / 32;
+    cudaError_t e = cudaMalloc(&s->list, size_t(cap) * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&s->bits, size_t(s->words) * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&s->cnt, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(s->cnt, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(s->bits, 0, size_t(s->words) * sizeof(uint32_t));
+    if (e == cudaSuccess) {
+        s->n_partials = int64_t(8) * h->num_sms;
+        e = cudaMalloc(&s->partials, size_t(s->n_partials) * sizeof(double));
+    }
+    if (e != cudaSuccess) {
+        sstate_destroy(s);
+        return cuda_fail(e, "cudaMalloc(sparse state)");
+    }
+    *out = s;
+    return HY_OK;
+}
+
+void sstate_destroy(SparseState *s)
+{
+    if (!s) return;
+    cudaFree(s->list);
+    cudaFree(s->bits);
+    cudaFree(s->cnt);
+    cudaFree(s->partials);
+    delete s;
+}
+
+hy_status sstate_reset(SparseState *s, bool full, bool hf, void *stream)
+{
+    cudaStream_t st = as_stream(stream);
+    const hy_ham *h = s->h;
+    if (full) {
+        HY_CUDA(cudaMemsetAsync(s->v, 0, size_t(h->N) * (s->dt == HY_F64 ? 8 : 4), st), "memset");
+        HY_CUDA(cudaMemsetAsync(s->bits, 0, size_t(s->words) * sizeof(uint32_t), st), "memset");
+        HY_CUDA(cudaMemsetAsync(s->cnt, 0, 2 * sizeof(unsigned long long), st), "memset");
+    }
+    if (s->dt == HY_F64)
+        HY_CUDA(hy::k::sv_reset<double>(svec<double>(s), hf, h->num_sms, st), "sparse reset");
+    else
+        HY_CUDA(hy::k::sv_reset<float>(svec<float>(s), hf, h->num_sms, st), "sparse reset");
+    return HY_OK;
+}
+
+hy_status sstate_copy(SparseState *dst, const SparseState *src, void *stream)
+{
+    if (dst->dt != src->dt || dst->h != src->h || dst->cap < src->cap)
+        return fail(HY_ERR_ARG, "sparse states do not match");
+    cudaStream_t st = as_stream(stream);
+    if (src->dt == HY_F64)
+        HY_CUDA(hy::k::sv_copy<double>(svec<double>(dst), svec<double>(src), src->h->num_sms, st),
+                "sparse copy");
+    else
+        HY_CUDA(hy::k::sv_copy<float>(svec<float>(dst), svec<float>(src), src->h->num_sms, st),
+                "sparse copy");
+    return HY_OK;
+}
+
+hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double theta, void *stream)
+{
+    const hy_ham *h = s->h;
+    if (!p || p->h != h || k < 0 || k >= int64_t(p->ops.size()))
+        return fail(HY_ERR_ARG, "bad operator");
+    hy::k::SvOpArgs o;
+    o.desc = p->d_desc;
+    o.astr = h->d_astr;
+    o.bstr = h->d_bstr;
+    o.binom33 = h->d_binom;
+    o.n = h->n;
+    o.Nb = h->Nb;
+    const int nc = p->ops[k].desc[0];
+    cudaStream_t st = as_stream(stream);
+    hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
+    if (s->dt == HY_F64)
+        HY_CUDA(hy::k::sv_excite<double>(svec<double>(s), o, int(k), nc, theta, h->num_sms, st),
+                "sparse excitation");
+    else
+        HY_CUDA(hy::k::sv_excite<float>(svec<float>(s), o, int(k), nc, theta, h->num_sms, st),
+                "sparse excitation");
+    return HY_OK;
+}
+
+hy_status sstate_dot(const SparseState *s, const void *y, double *out, void *stream)
+{
+    cudaStream_t st = as_stream(stream);
+    hy::ProfScope prof(HY_PROF_REDUCE, stream, 0.0);
+    const int sms = s->h->num_sms;
+    if (s->dt == HY_F64)
+        HY_CUDA(hy::k::sv_dot<double>(svec<double>(s), static_cast<const double *>(y),
+                                      s->partials, out, sms, st), "sparse dot");
+    else
+        HY_CUDA(hy::k::sv_dot<float>(svec<float>(s), static_cast<const float *>(y), s->partials,
+                                     out, sms, st), "sparse dot");
+    return HY_OK;
+}
+
+hy_status sstate_scale_rsqrt(SparseState *s, const double *norm2, void *stream)
+{
+    cudaStream_t st = as_stream(stream);
+    hy::ProfScope prof(HY_PROF_REDUCE, stream, 0.0);
+    if (s->dt == HY_F64)
+        HY_CUDA(hy::k::sv_scale_rsqrt<double>(svec<double>(s), norm2, s->h->num_sms, st),
+                "sparse scale");
+    else
+        HY_CUDA(hy::k::sv_scale_rsqrt<float>(svec<float>(s), norm2, s->h->num_sms, st),
+                "sparse scale");
+    return HY_OK;
+}
+
+hy_status sstate_apply_h(const SparseState *s, void *sigma, void *stream)
+{
+    cudaStream_t st = as_stream(stream);
+    const hy_ham *h = s->h;
+    hy::ProfScope prof(HY_PROF_HPSI_SPARSE, stream, double(h->N) * (s->dt == HY_F64 ? 8 : 4));
+    if (s->dt == HY_F64) {
+        auto a = sparse_args<double>(h, s->v, sigma, s->list, 0);
+        a.d_m = s->cnt;
+        a.cap = s->cap;
+        HY_CUDA(hy::k::hpsi_scatter<double>(a, h->num_sms, st), "sparse H psi");
+    } else {
+        auto a = sparse_args<float>(h, s->v, sigma, s->list, 0);
+        a.d_m = s->cnt;
+        a.cap = s->cap;
+        HY_CUDA(hy::k::hpsi_scatter<float>(a, h->num_sms, st), "sparse H psi");
+    }
+    return HY_OK;
+}
+
+hy_status sstate_gradients(const SparseState *sc, const void *lam, const hy_pool *p,
+                           const int32_t *ops, int64_t n_ops, int64_t m_hint, double *g,
+                           void *stream)
+{
+    SparseState *s = const_cast<SparseState *>(sc);
+    const hy_ham *h = s->h;
+    if (!p || p->h != h || !lam || !g) return fail(HY_ERR_ARG, "bad arguments");
+    if (!ops) n_ops = int64_t(p->ops.size());
+    if (n_ops <= 0) return HY_OK;
+    cudaStream_t st = as_stream(stream);
+    const int chunks = sparse_chunks(h, n_ops, m_hint < s->cap ? m_hint : s->cap);
+    hy_status r = sstate_partials(s, n_ops * chunks, st);
+    if (r != HY_OK) return r;
+    hy::ProfScope prof(HY_PROF_SCREEN_SPARSE, stream, 0.0);
+    auto fill = [&](auto &a) {
+        a.list = s->list; a.m = 0; a.d_m = s->cnt; a.cap = s->cap; a.bits = s->bits;
+        a.chunks = chunks; a.partials = s->partials;
+        a.desc = p->d_desc; a.ops = ops; a.n_ops = n_ops;
+        a.astr = h->d_astr; a.bstr = h->d_bstr; a.binom33 = h->d_binom; a.n = h->n;
+        a.Nb = h->Nb; a.g = g;
+    };
+    if (s->dt == HY_F64) {
+        hy::k::SparseGradArgs<double> a;
+        a.psi = static_cast<const double *>(s->v);
+        a.sigma = static_cast<const double *>(lam);
+        fill(a);
+        HY_CUDA(hy::k::grad_sparse<double>(a, h->num_sms, st), "sparse gradients");
+    } else {
+        hy::k::SparseGradArgs<float> a;
+        a.psi = static_cast<const float *>(s->v);
+        a.sigma = static_cast<const float *>(lam);
+        fill(a);
+        HY_CUDA(hy::k::grad_sparse<float>(a, h->num_sms, st), "sparse gradients");
+    }
+    return HY_OK;
+}
+
+const int64_t *sstate_count(const SparseState *s)
+{
+    return reinterpret_cast<const int64_t *>(s->cnt);
+}
+const int64_t *sstate_list(const SparseState *s) { return s->list; }
+int64_t sstate_cap(const SparseState *s) { return s->cap; }
+
+}  // namespace hy

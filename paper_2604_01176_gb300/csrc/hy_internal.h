@@ -115,4 +115,52 @@ struct PatternLists {
     int get(const PatternKey &k, const StringSpace &s);
 };
 
+// Kernel-class timing (hy_profile.cpp): records an event pair on `stream`
+// around its lifetime when the class is enabled, with the algorithmic bytes
+// the enclosed launches move (0 where they are not known on the host).
+class ProfScope {
+  public:
+    ProfScope(int cls, void *stream, double bytes);
+    ~ProfScope();
+    ProfScope(const ProfScope &) = delete;
+    ProfScope &operator=(const ProfScope &) = delete;
+
+  private:
+    int cls_;
+    void *stream_;
+    double bytes_;
+    void *a_;
+};
+
+// ---------------------------------------------------------------------------
+// Sparse state vectors for the ADAPT driver (implemented in hy_api.cu over
+// the kernels of hy_sparse.cu).  A SparseState owns a support list of
+// capacity cap, a membership bitmap and device counters; the amplitudes live
+// in the caller's dense array v (N amplitudes, zero off the support).  The
+// count stays on the device; count() > cap means the list overflowed and the
+// contents are no longer a valid sparse vector (reset(full) repairs it).
+// ---------------------------------------------------------------------------
+struct SparseState;
+hy_status sstate_create(const hy_ham *h, hy_dtype dt, void *v, int64_t cap, SparseState **out);
+void sstate_destroy(SparseState *s);
+// full: zero the whole dense array and bitmap (after dense use or overflow);
+// else only the listed entries.  hf: then set v = |HF> (index 0).
+hy_status sstate_reset(SparseState *s, bool full, bool hf, void *stream);
+hy_status sstate_copy(SparseState *dst, const SparseState *src, void *stream);
+hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double theta, void *stream);
+// *out (device) = sum over the support of v * y (y dense, same dtype), FP64
+hy_status sstate_dot(const SparseState *s, const void *y, double *out, void *stream);
+// v <- v / sqrt(*norm2) on the support (norm2 on the device)
+hy_status sstate_scale_rsqrt(SparseState *s, const double *norm2, void *stream);
+// sigma = H v (dense sigma, zeroed here)
+hy_status sstate_apply_h(const SparseState *s, void *sigma, void *stream);
+// g[i] = 2 <lam | A_{ops[i]} v> over the pairs with a listed end (ops device
+// array or nullptr for the whole pool); m_hint ~ the support size (grid shape)
+hy_status sstate_gradients(const SparseState *s, const void *lam, const hy_pool *p,
+                           const int32_t *ops, int64_t n_ops, int64_t m_hint, double *g,
+                           void *stream);
+const int64_t *sstate_count(const SparseState *s);   // device pointer
+const int64_t *sstate_list(const SparseState *s);    // device pointer
+int64_t sstate_cap(const SparseState *s);
+
 }  // namespace hy

@@ -90,6 +90,83 @@ template <typename T>
 cudaError_t excite(T *psi, const uint32_t *ae, int64_t nrows, const uint32_t *be,
                    int64_t ncols, int64_t Nb, double c, double s_eps,
                    cudaStream_t st);
+// exp(theta A) as excite(), also adding the change of ||psi||^2 over the
+// rotated pairs to *norm2 (partials: >= excite_n_partials(...) doubles)
+int excite_n_partials(int64_t nrows, int64_t ncols, int num_sms);
+template <typename T>
+cudaError_t excite_n(T *psi, const uint32_t *ae, int64_t nrows, const uint32_t *be,
+                     int64_t ncols, int64_t Nb, double c, double s_eps, double *partials,
+                     double *norm2, int num_sms, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// FP32 products summed with FP64 accuracy at FP32 speed (GB300 issues FP64 at
+// 1/64 of the FP32 rate, and a float -> double conversion costs an FP64 slot).
+// Dot2 of Ogita, Rump & Oishi ("Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26, 2005): TwoProduct writes x*y = h + r exactly with one FMA,
+// TwoSum writes p + h = p' + q exactly; p carries the sum, s the exact
+// rounding errors.  Every kDot2Run terms (p, s) is added to an FP64 total, so
+// a run's error is below gamma_31^2 * sum|x_i y_i| (~3.5e-12 relative, typ.
+// ~1e-14) and the FP64 total is as in a plain double accumulation.  Products
+// near the FP32 overflow threshold take the exact FP64 product instead.
+// ---------------------------------------------------------------------------
+constexpr int kDot2Run = 32;
+struct Dot2 {
+    float p, s;
+    double d;
+    int n;
+};
+__device__ __forceinline__ void dot2_init(Dot2 &a)
+{
+    a.p = 0.f;
+    a.s = 0.f;
+    a.d = 0.0;
+    a.n = 0;
+}
+__device__ __forceinline__ void dot2_flush(Dot2 &a)
+{
+    a.d += double(a.p);
+    a.d += double(a.s);
+    a.p = 0.f;
+    a.s = 0.f;
+    a.n = 0;
+}
+__device__ __forceinline__ void dot2_add(Dot2 &a, float x, float y)
+{
+    const float h = __fmul_rn(x, y);
+    if (fabsf(h) > 1e36f) {          // also inf; NaN falls through and propagates
+        a.d += double(x) * double(y);
+        return;
+    }
+    const float r = __fmaf_rn(x, y, -h);
+    const float p = __fadd_rn(a.p, h);
+    const float z = __fsub_rn(p, a.p);
+    const float q = __fadd_rn(__fsub_rn(a.p, __fsub_rn(p, z)), __fsub_rn(h, z));
+    a.p = p;
+    a.s = __fadd_rn(a.s, __fadd_rn(q, r));
+    if (++a.n == kDot2Run) dot2_flush(a);
+}
+__device__ __forceinline__ double dot2_total(Dot2 &a)
+{
+    dot2_flush(a);
+    return a.d;
+}
+// sum of products accumulated with FP64 accuracy: Dot2 for float, FMA in double
+template <typename T>
+struct ProdAcc;
+template <>
+struct ProdAcc<float> {
+    Dot2 a;
+    __device__ __forceinline__ ProdAcc() { dot2_init(a); }
+    __device__ __forceinline__ void add(float x, float y) { dot2_add(a, x, y); }
+    __device__ __forceinline__ double total() { return dot2_total(a); }
+};
+template <>
+struct ProdAcc<double> {
+    double d;
+    __device__ __forceinline__ ProdAcc() : d(0.0) {}
+    __device__ __forceinline__ void add(double x, double y) { d = fma(x, y, d); }
+    __device__ __forceinline__ double total() { return d; }
+};
 
 // learned ranker (hy_ranker.cu)
 constexpr int kRankerFeatures = 16;
@@ -101,10 +178,12 @@ cudaError_t occupations(const T *psi, int64_t Na, int64_t Nb, const uint32_t *as
 cudaError_t features(const int32_t *desc, int64_t K, int n, const double *h1,
                      const double *eri, const float *occ, const float *extra, const float *Dpsi,
                      const float *Dsig, float *feat, cudaStream_t st);
+// part: pair_splits() x n^4 floats of scratch
+int pair_splits();
 template <typename T>
 cudaError_t touched_weights(const T *psi, int64_t Na, int64_t Nb, const uint32_t *astr,
-                            const uint32_t *bstr, int n, float *Bw, float *rs, float *D,
-                            int num_sms, cudaStream_t st);
+                            const uint32_t *bstr, int n, float *Bw, float *rs, float *part,
+                            float *D, int num_sms, cudaStream_t st);
 
 // sparse-state path (hy_sparse.cu)
 template <typename T>
@@ -113,6 +192,8 @@ struct SparseArgs {
     T *sigma;
     const int64_t *list;     // nonzero amplitudes of psi
     int64_t m;
+    const unsigned long long *d_m;   // device count (overrides m, clamped to cap) or nullptr
+    int64_t cap;
     const int32_t *Ma_ptr, *Ma_col, *Mb_ptr, *Mb_col;
     const T *Ma_val, *Mb_val, *V;
     const uint32_t *aex, *bexT, *astr, *bstr;
@@ -124,6 +205,12 @@ struct SparseGradArgs {
     const T *psi, *sigma;
     const int64_t *list;
     int64_t m;
+    const unsigned long long *d_m;   // device count (overrides m, clamped to cap) or nullptr
+    int64_t cap;
+    const uint32_t *bits;    // membership bitmap of the list, or nullptr: then
+                             // the list holds exactly the nonzero amplitudes
+    int chunks;              // support chunks per operator (grid.y)
+    double *partials;        // [n_ops][chunks]
     const int32_t *desc;     // [K][11] operator descriptors
     const int32_t *ops;      // operator list or nullptr (all)
     int64_t n_ops;
@@ -139,6 +226,44 @@ template <typename T>
 cudaError_t hpsi_scatter(const SparseArgs<T> &a, int num_sms, cudaStream_t st);
 template <typename T>
 cudaError_t grad_sparse(const SparseGradArgs<T> &a, int num_sms, cudaStream_t st);
+
+// Sparse vectors backed by a dense array: v (N amplitudes, zero off the
+// support), list[0..count) the support (each index once, values may be 0),
+// bits the membership bitmap of the list (bit i of bits[i >> 5]).
+template <typename T>
+struct SVec {
+    T *v;
+    int64_t *list;
+    uint32_t *bits;
+    unsigned long long *count;   // device: live count
+    unsigned long long *snap;    // device: count at the start of a rotation
+    int64_t cap;
+};
+// a constituent's operator strings and the tables to rank determinants
+struct SvOpArgs {
+    const int32_t *desc;         // [K][11]
+    const uint32_t *astr, *bstr, *binom33;
+    int n;
+    int64_t Nb;
+};
+// v <- 0 on the support, bits cleared, count <- 0; then (hf) v[0] = 1 listed
+template <typename T>
+cudaError_t sv_reset(const SVec<T> &x, bool hf, int num_sms, cudaStream_t st);
+// dst <- src (dst must be reset)
+template <typename T>
+cudaError_t sv_copy(const SVec<T> &dst, const SVec<T> &src, int num_sms, cudaStream_t st);
+// exp(theta (C - C^dagger)) for every constituent C of operator k
+template <typename T>
+cudaError_t sv_excite(const SVec<T> &x, const SvOpArgs &o, int k, int nc, double theta,
+                      int num_sms, cudaStream_t st);
+// sum over the support of x.v * y (y dense), in FP64, into *out (partials:
+// 4 * num_sms doubles); scale: x.v <- x.v / sqrt(*norm2) on the support
+template <typename T>
+cudaError_t sv_dot(const SVec<T> &x, const T *y, double *partials, double *out, int num_sms,
+                   cudaStream_t st);
+template <typename T>
+cudaError_t sv_scale_rsqrt(const SVec<T> &x, const double *norm2, int num_sms,
+                           cudaStream_t st);
 
 // batched rows over many molecules (hy_batch.cu)
 template <typename T>

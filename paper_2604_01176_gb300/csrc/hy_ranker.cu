@@ -102,84 +102,138 @@ cudaError_t occupations(const T *psi, int64_t Na, int64_t Nb, const uint32_t *as
 // with i == a (j == b) meaning "no condition on the alpha (beta) string".
 // The inner beta sum for j != b is Bw[.][j*n+j] - Bw[.][j*n+b].
 // ---------------------------------------------------------------------------
+// Bw is an indicator product, Bw = W I with W[a][c] = w(a, c) (N_a x N_b) and
+// I[c][jb] = [j in c][b in c] (N_b x n^2): a block owns 16 alpha rows, a
+// thread the pairs t and t + 128; column chunks of W and the beta masks are
+// staged in shared memory and read as broadcasts, so the inner loop is
+// 128 FMAs per 17 shared loads.
+constexpr int kPwRows = 16, kPwChunk = 128, kPwThreads = 128;
+
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kPwThreads)
 k_pair_weights(const T *__restrict__ psi, int64_t Na, int64_t Nb,
                const uint32_t *__restrict__ bstr, int n, float *__restrict__ Bw,
                float *__restrict__ rs)
 {
-    extern __shared__ float wsh[];     // [Nb]
-    __shared__ float red[256];
-    const int nn = n * n, t = threadIdx.x;
-    const int j = t < nn ? t / n : 0, b = t < nn ? t % n : 0;
-    for (int64_t a = blockIdx.x; a < Na; a += gridDim.x) {
-        __syncthreads();
-        float part = 0.0f;
-        for (int64_t c = t; c < Nb; c += blockDim.x) {
-            const float v = float(psi[a * Nb + c]);
-            wsh[c] = v * v;
-            part += v * v;
-        }
-        red[t] = part;
-        __syncthreads();
-        for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-            if (t < st) red[t] += red[t + st];
+    __shared__ __align__(16) float ws[kPwRows][kPwChunk];
+    __shared__ __align__(16) uint32_t ms[kPwChunk];
+    __shared__ float rsw[kPwThreads / 32][kPwRows];
+    const int nn = n * n, t0 = threadIdx.x, t1 = threadIdx.x + kPwThreads;
+    // an unused slot asks for all 32 bits: no string of < 32 electrons has them
+    const uint32_t sel0 = t0 < nn ? (1u << (t0 / n)) | (1u << (t0 % n)) : 0xFFFFFFFFu;
+    const uint32_t sel1 = t1 < nn ? (1u << (t1 / n)) | (1u << (t1 % n)) : 0xFFFFFFFFu;
+    for (int64_t a0 = int64_t(blockIdx.x) * kPwRows; a0 < Na; a0 += int64_t(gridDim.x) * kPwRows) {
+        float acc0[kPwRows], acc1[kPwRows], rsum[kPwRows];
+#pragma unroll
+        for (int r = 0; r < kPwRows; ++r) acc0[r] = acc1[r] = rsum[r] = 0.0f;
+        for (int64_t c0 = 0; c0 < Nb; c0 += kPwChunk) {
             __syncthreads();
+            const int64_t c = c0 + threadIdx.x;
+#pragma unroll 4
+            for (int r = 0; r < kPwRows; ++r) {
+                const int64_t a = a0 + r;
+                const float v = (a < Na && c < Nb) ? float(psi[a * Nb + c]) : 0.0f;
+                ws[r][threadIdx.x] = v * v;
+                rsum[r] = fmaf(v, v, rsum[r]);
+            }
+            ms[threadIdx.x] = c < Nb ? bstr[c] : 0u;
+            __syncthreads();
+            for (int cc = 0; cc < kPwChunk; cc += 4) {
+                const uint4 m4 = *reinterpret_cast<const uint4 *>(ms + cc);
+                const float f00 = (m4.x & sel0) == sel0 ? 1.f : 0.f, f10 = (m4.x & sel1) == sel1 ? 1.f : 0.f;
+                const float f01 = (m4.y & sel0) == sel0 ? 1.f : 0.f, f11 = (m4.y & sel1) == sel1 ? 1.f : 0.f;
+                const float f02 = (m4.z & sel0) == sel0 ? 1.f : 0.f, f12 = (m4.z & sel1) == sel1 ? 1.f : 0.f;
+                const float f03 = (m4.w & sel0) == sel0 ? 1.f : 0.f, f13 = (m4.w & sel1) == sel1 ? 1.f : 0.f;
+#pragma unroll
+                for (int r = 0; r < kPwRows; ++r) {
+                    const float4 w = *reinterpret_cast<const float4 *>(&ws[r][cc]);
+                    acc0[r] = fmaf(f00, w.x, fmaf(f01, w.y, fmaf(f02, w.z, fmaf(f03, w.w, acc0[r]))));
+                    acc1[r] = fmaf(f10, w.x, fmaf(f11, w.y, fmaf(f12, w.z, fmaf(f13, w.w, acc1[r]))));
+                }
+            }
         }
-        if (t == 0) rs[a] = red[0];
-        if (t < nn) {
-            float acc = 0.0f;
-            const uint32_t sel = (1u << j) | (1u << b);
-            for (int64_t c = 0; c < Nb; ++c)
-                if ((__ldg(bstr + c) & sel) == sel) acc += wsh[c];
-            Bw[a * nn + t] = acc;
+#pragma unroll
+        for (int r = 0; r < kPwRows; ++r) {
+            float v = rsum[r];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) rsw[threadIdx.x >> 5][r] = v;
         }
+        __syncthreads();
+        if (threadIdx.x < kPwRows && a0 + threadIdx.x < Na) {
+            float v = 0.0f;
+            for (int w = 0; w < kPwThreads / 32; ++w) v += rsw[w][threadIdx.x];
+            rs[a0 + threadIdx.x] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < kPwRows; ++r) {
+            const int64_t a = a0 + r;
+            if (a >= Na) break;
+            if (t0 < nn) Bw[a * nn + t0] = acc0[r];
+            if (t1 < nn) Bw[a * nn + t1] = acc1[r];
+        }
+    }
+}
+
+// D[(i,a)][(j,b)] split over alpha rows: block (ia, split) sums the rows
+// split, split + S, ...; the alpha condition depends on (row, ia) only, so
+// the branch is uniform in the block; threads own jb.  Partials [S][n^4].
+constexpr int kPairSplits = 16;
+
+__global__ void __launch_bounds__(256)
+k_pair_contract(const float *__restrict__ Bw, const float *__restrict__ rs,
+                const uint32_t *__restrict__ astr, int64_t Na, int n, float *__restrict__ part)
+{
+    const int nn = n * n;
+    const int ia = blockIdx.x, jb = threadIdx.x;
+    const int i = ia / n, aa = ia % n;
+    const int j = jb < nn ? jb / n : 0, b = jb < nn ? jb % n : 0;
+    float acc = 0.0f;
+    if (jb < nn) {
+        for (int64_t al = blockIdx.y; al < Na; al += gridDim.y) {
+            const uint32_t m = astr[al];
+            if (i != aa && !(((m >> i) & 1u) && !((m >> aa) & 1u))) continue;
+            acc += (j == b) ? rs[al] : (Bw[al * nn + j * n + j] - Bw[al * nn + jb]);
+        }
+        part[int64_t(blockIdx.y) * nn * nn + int64_t(ia) * nn + jb] = acc;
     }
 }
 
 __global__ void __launch_bounds__(256)
-k_pair_contract(const float *__restrict__ Bw, const float *__restrict__ rs,
-                const uint32_t *__restrict__ astr, int64_t Na, int n, float *__restrict__ D)
+k_pair_reduce(const float *__restrict__ part, int64_t total, int S, float *__restrict__ D)
 {
-    const int nn = n * n;
     const int64_t id = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (id >= int64_t(nn) * nn) return;
-    const int ia = int(id / nn), jb = int(id % nn);
-    const int i = ia / n, aa = ia % n, j = jb / n, b = jb % n;
-    double acc = 0.0;
-    for (int64_t al = 0; al < Na; ++al) {
-        const uint32_t m = astr[al];
-        if (i != aa && !(((m >> i) & 1u) && !((m >> aa) & 1u))) continue;
-        acc += (j == b) ? rs[al] : (Bw[al * nn + j * n + j] - Bw[al * nn + j * n + b]);
-    }
-    D[id] = float(acc);
+    if (id >= total) return;
+    double s = 0.0;
+    for (int k = 0; k < S; ++k) s += double(part[int64_t(k) * total + id]);
+    D[id] = float(s);
 }
+
+int pair_splits() { return kPairSplits; }
 
 template <typename T>
 cudaError_t touched_weights(const T *psi, int64_t Na, int64_t Nb, const uint32_t *astr,
-                            const uint32_t *bstr, int n, float *Bw, float *rs, float *D,
-                            int num_sms, cudaStream_t st)
+                            const uint32_t *bstr, int n, float *Bw, float *rs, float *part,
+                            float *D, int num_sms, cudaStream_t st)
 {
-    const size_t smem = size_t(Nb) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_pair_weights<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    int64_t g = int64_t(num_sms) * 2;
-    if (g > Na) g = Na;
-    k_pair_weights<T><<<unsigned(g), 256, smem, st>>>(psi, Na, Nb, bstr, n, Bw, rs); hy::count_launch();
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int64_t tot = int64_t(n) * n * n * n;
-    k_pair_contract<<<unsigned((tot + 255) / 256), 256, 0, st>>>(Bw, rs, astr, Na, n, D); hy::count_launch();
+    int64_t g = (Na + kPwRows - 1) / kPwRows;
+    if (g > int64_t(num_sms) * 16) g = int64_t(num_sms) * 16;
+    k_pair_weights<T><<<unsigned(g), kPwThreads, 0, st>>>(psi, Na, Nb, bstr, n, Bw, rs);
+    hy::count_launch();
+    const int nn = n * n;
+    k_pair_contract<<<dim3(unsigned(nn), kPairSplits), 256, 0, st>>>(Bw, rs, astr, Na, n, part);
+    hy::count_launch();
+    const int64_t tot = int64_t(nn) * nn;
+    k_pair_reduce<<<unsigned((tot + 255) / 256), 256, 0, st>>>(part, tot, kPairSplits, D);
+    hy::count_launch();
     return cudaGetLastError();
 }
 
 template cudaError_t touched_weights<double>(const double *, int64_t, int64_t, const uint32_t *,
                                              const uint32_t *, int, float *, float *, float *,
-                                             int, cudaStream_t);
+                                             float *, int, cudaStream_t);
 template cudaError_t touched_weights<float>(const float *, int64_t, int64_t, const uint32_t *,
                                             const uint32_t *, int, float *, float *, float *,
-                                            int, cudaStream_t);
+                                            float *, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // per-operator features (kRankerFeatures floats per operator)

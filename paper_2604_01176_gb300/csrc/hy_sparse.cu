@@ -12,6 +12,8 @@
 //     endpoint in the support only, applying each constituent's operator
 //     string to the determinant's bits (Jordan-Wigner signs) and ranking the
 //     partner with the binomial table.
+#include <cmath>
+
 #include "hy_kernels.cuh"
 
 namespace hy {
@@ -40,6 +42,19 @@ k_support(const T *__restrict__ psi, int64_t N, int64_t *__restrict__ list, int6
     }
 }
 
+// support length: the device count clamped to the list's capacity, or m
+__device__ __forceinline__ int64_t list_len(const unsigned long long *d_m, int64_t m, int64_t cap)
+{
+    if (!d_m) return m;
+    const unsigned long long c = *d_m;
+    return c < (unsigned long long)cap ? int64_t(c) : cap;
+}
+
+__device__ __forceinline__ bool member(const uint32_t *bits, int64_t i)
+{
+    return (bits[i >> 5] >> (i & 31)) & 1u;
+}
+
 template <typename T>
 __device__ __forceinline__ T sum_diag(const T *V, int n, int nn, uint32_t mask, int rs)
 {
@@ -59,7 +74,8 @@ k_hpsi_scatter(SparseArgs<T> a)
     const int n = a.n, nn = n * n;
     const int64_t Nb = a.Nb;
     const int ne = a.nexa + 1, nf = a.nexb + 1;
-    for (int64_t t = blockIdx.x; t < a.m; t += gridDim.x) {
+    const int64_t m = list_len(a.d_m, a.m, a.cap);
+    for (int64_t t = blockIdx.x; t < m; t += gridDim.x) {
         const int64_t d = a.list[t];
         const T x = a.psi[d];
         const int64_t A = d / Nb, B = d % Nb;
@@ -134,62 +150,283 @@ __device__ __forceinline__ bool apply_string(const int *code, int len, uint64_t 
     return true;
 }
 
+// Operator strings of a constituent descriptor (rank, c0, c1, a1, a0) in
+// application order: fw applies C = a+_{c0} [a+_{c1} a_{a1}] a_{a0}, bw its
+// adjoint.
+__device__ __forceinline__ void op_strings(const int32_t *q, int *fw, int *bw, int &len)
+{
+    if (q[0] == 1) {
+        fw[0] = 2 * q[4]; fw[1] = 2 * q[1] + 1;
+        bw[0] = 2 * q[1]; bw[1] = 2 * q[4] + 1;
+        len = 2;
+    } else {
+        fw[0] = 2 * q[4]; fw[1] = 2 * q[3]; fw[2] = 2 * q[2] + 1; fw[3] = 2 * q[1] + 1;
+        bw[0] = 2 * q[1]; bw[1] = 2 * q[2]; bw[2] = 2 * q[3] + 1; bw[3] = 2 * q[4] + 1;
+        len = 4;
+    }
+}
+
+// sum over a block of 256 threads, fixed order; valid in thread 0
+__device__ __forceinline__ double block_sum_d(double v)
+{
+    __shared__ double wp[8];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) wp[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) s += wp[w];
+    return s;
+}
+
+// Block (i, chunk): operator ops[i] over the support entries chunk,
+// chunk + chunks, ... (stride chunks * blockDim).  A pair is counted once:
+// from its domain end if that is listed, else from its image end.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_grad_sparse(SparseGradArgs<T> a)
 {
     __shared__ uint32_t C[33][33];
-    __shared__ double red[256];
     for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = a.binom33[i];
     __syncthreads();
     const int n = a.n;
     const uint64_t lowm = (1ull << n) - 1;
-    for (int64_t i = blockIdx.x; i < a.n_ops; i += gridDim.x) {
-        const int k = a.ops ? a.ops[i] : int(i);
-        const int32_t *dsc = a.desc + 11 * k;
-        double tot = 0.0;
-        for (int c = 0; c < dsc[0]; ++c) {
-            const int32_t *q = dsc + 1 + 5 * c;
-            int fw[4], bw[4], len;
-            if (q[0] == 1) {            // a+_{c0} a_{a0}
-                fw[0] = 2 * q[4]; fw[1] = 2 * q[1] + 1;
-                bw[0] = 2 * q[1]; bw[1] = 2 * q[4] + 1;
-                len = 2;
-            } else {                    // a+_{c0} a+_{c1} a_{a1} a_{a0}
-                fw[0] = 2 * q[4]; fw[1] = 2 * q[3]; fw[2] = 2 * q[2] + 1; fw[3] = 2 * q[1] + 1;
-                bw[0] = 2 * q[1]; bw[1] = 2 * q[2]; bw[2] = 2 * q[3] + 1; bw[3] = 2 * q[4] + 1;
-                len = 4;
+    const int64_t m = list_len(a.d_m, a.m, a.cap);
+    const int64_t i = blockIdx.x;
+    const int k = a.ops ? a.ops[i] : int(i);
+    const int32_t *dsc = a.desc + 11 * k;
+    double tot = 0.0;
+    for (int c = 0; c < dsc[0]; ++c) {
+        int fw[4], bw[4], len;
+        op_strings(dsc + 1 + 5 * c, fw, bw, len);
+        for (int64_t t = int64_t(blockIdx.y) * blockDim.x + threadIdx.x; t < m;
+             t += int64_t(gridDim.y) * blockDim.x) {
+            const int64_t d = a.list[t];
+            const double x = double(a.psi[d]);
+            const uint64_t mask = uint64_t(a.astr[d / a.Nb]) | (uint64_t(a.bstr[d % a.Nb]) << n);
+            uint64_t o = mask;
+            int sg = 1;
+            if (apply_string(fw, len, o, sg)) {       // d is the domain end
+                const int64_t d2 = int64_t(rank_bits(uint32_t(o & lowm), C)) * a.Nb +
+                                   rank_bits(uint32_t(o >> n), C);
+                tot += sg * (double(a.sigma[d2]) * x - double(a.sigma[d]) * double(a.psi[d2]));
+                continue;
             }
-            for (int64_t t = threadIdx.x; t < a.m; t += blockDim.x) {
-                const int64_t d = a.list[t];
-                const double x = double(a.psi[d]);
-                const uint64_t mask = uint64_t(a.astr[d / a.Nb]) | (uint64_t(a.bstr[d % a.Nb]) << n);
-                uint64_t o = mask;
-                int sg = 1;
-                if (apply_string(fw, len, o, sg)) {       // d is the domain end
-                    const int64_t d2 = int64_t(rank_bits(uint32_t(o & lowm), C)) * a.Nb +
-                                       rank_bits(uint32_t(o >> n), C);
-                    tot += sg * (double(a.sigma[d2]) * x - double(a.sigma[d]) * double(a.psi[d2]));
-                    continue;
-                }
-                o = mask;
-                sg = 1;
-                if (apply_string(bw, len, o, sg)) {       // d is the image end
-                    const int64_t d0 = int64_t(rank_bits(uint32_t(o & lowm), C)) * a.Nb +
-                                       rank_bits(uint32_t(o >> n), C);
-                    if (a.psi[d0] == T(0)) tot -= sg * double(a.sigma[d0]) * x;
-                }
+            o = mask;
+            sg = 1;
+            if (apply_string(bw, len, o, sg)) {       // d is the image end
+                const int64_t d0 = int64_t(rank_bits(uint32_t(o & lowm), C)) * a.Nb +
+                                   rank_bits(uint32_t(o >> n), C);
+                const bool listed = a.bits ? member(a.bits, d0) : a.psi[d0] != T(0);
+                if (!listed) tot -= sg * double(a.sigma[d0]) * x;
             }
         }
-        red[threadIdx.x] = tot;
-        __syncthreads();
-        for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-            if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) a.g[i] = 2.0 * red[0];
-        __syncthreads();
     }
+    tot = block_sum_d(tot);
+    if (threadIdx.x == 0) a.partials[i * gridDim.y + blockIdx.y] = tot;
+}
+
+__global__ void __launch_bounds__(256)
+k_grad_sparse_final(const double *__restrict__ partials, int chunks, int64_t n_ops,
+                    double *__restrict__ g)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n_ops) return;
+    double s = 0.0;
+    for (int c = 0; c < chunks; ++c) s += partials[i * chunks + c];
+    g[i] = 2.0 * s;
+}
+
+// ---------------------------------------------------------------------------
+// Sparse vectors: amplitudes in a dense array (zero off the support), the
+// support as a list plus a membership bitmap, the count on the device.  The
+// state preparation prod_l exp(theta_l A_l)|HF> then costs O(support) per
+// rotation and needs no host synchronisation: the count stays on the device
+// and an overflowing list is detected afterwards (count > cap).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_sv_clear(SVec<T> x)
+{
+    // every set bit belongs to a listed entry, and all of them are cleared,
+    // so whole bitmap words can be zeroed
+    const int64_t m = list_len(x.count, 0, x.cap);
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < m;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = x.list[t];
+        x.v[i] = T(0);
+        x.bits[i >> 5] = 0u;
+    }
+}
+
+template <typename T>
+__global__ void k_sv_finish_reset(SVec<T> x, int hf)
+{
+    if (hf) {
+        x.v[0] = T(1);
+        x.bits[0] = 1u;
+        x.list[0] = 0;
+    }
+    *x.count = hf ? 1ull : 0ull;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_sv_copy(SVec<T> dst, SVec<T> src)
+{
+    const int64_t m = list_len(src.count, 0, src.cap < dst.cap ? src.cap : dst.cap);
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < m;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = src.list[t];
+        dst.v[i] = src.v[i];
+        dst.list[t] = i;
+        atomicOr(dst.bits + (i >> 5), 1u << (i & 31));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *dst.count = *src.count;
+}
+
+__global__ void k_sv_snap(unsigned long long *snap, const unsigned long long *count)
+{
+    *snap = *count;
+}
+
+// One constituent C of operator k: every pair (d, C d) with a listed end is
+// rotated by its processor -- the domain end if listed, else the image end --
+// and the other end is listed if it was not.  Pairs of one constituent are
+// disjoint, so the rotation is race-free; entries appended here (positions >=
+// the snapshot) are not visited again.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_sv_excite(SVec<T> x, SvOpArgs o, int k, int ci, T c, T s)
+{
+    __shared__ uint32_t C[33][33];
+    for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
+    __syncthreads();
+    int fw[4], bw[4], len;
+    op_strings(o.desc + 11 * k + 1 + 5 * ci, fw, bw, len);
+    const int n = o.n;
+    const uint64_t lowm = (1ull << n) - 1;
+    const int64_t m = list_len(x.snap, 0, x.cap);
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < m;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t d = x.list[t];
+        const uint64_t mask = uint64_t(o.astr[d / o.Nb]) | (uint64_t(o.bstr[d % o.Nb]) << n);
+        uint64_t u = mask;
+        int sg = 1;
+        int64_t dom, img, fresh;
+        if (apply_string(fw, len, u, sg)) {
+            dom = d;
+            img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+            fresh = member(x.bits, img) ? -1 : img;
+        } else {
+            u = mask;
+            sg = 1;
+            if (!apply_string(bw, len, u, sg)) continue;    // C and C^dagger annihilate d
+            img = d;
+            dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+            if (member(x.bits, dom)) continue;              // the domain end rotates the pair
+            fresh = dom;
+        }
+        const T ss = sg > 0 ? s : -s;
+        const T xv = x.v[dom], yv = x.v[img];
+        x.v[dom] = c * xv - ss * yv;
+        x.v[img] = c * yv + ss * xv;
+        if (fresh >= 0) {
+            atomicOr(x.bits + (fresh >> 5), 1u << (fresh & 31));
+            const unsigned long long pos = atomicAdd(x.count, 1ull);
+            if (pos < (unsigned long long)x.cap) x.list[pos] = fresh;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_sv_dot_partial(SVec<T> x, const T *__restrict__ y, double *__restrict__ partials)
+{
+    const int64_t m = list_len(x.count, 0, x.cap);
+    double acc = 0.0;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < m;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = x.list[t];
+        acc = fma(double(x.v[i]), double(y[i]), acc);
+    }
+    acc = block_sum_d(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(256)
+k_sv_sum(const double *__restrict__ partials, int G, double *__restrict__ out)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < G; i += blockDim.x) s += partials[i];
+    s = block_sum_d(s);
+    if (threadIdx.x == 0) *out = s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_sv_scale(SVec<T> x, const double *__restrict__ norm2)
+{
+    const T f = T(1.0 / sqrt(*norm2));
+    const int64_t m = list_len(x.count, 0, x.cap);
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < m;
+         t += int64_t(gridDim.x) * blockDim.x)
+        x.v[x.list[t]] *= f;
+}
+
+namespace {
+unsigned sv_grid(int64_t cap, int num_sms)
+{
+    int64_t g = (cap + 255) / 256;
+    if (g > int64_t(num_sms) * 8) g = int64_t(num_sms) * 8;
+    return unsigned(g < 1 ? 1 : g);
+}
+}  // namespace
+
+template <typename T>
+cudaError_t sv_reset(const SVec<T> &x, bool hf, int num_sms, cudaStream_t st)
+{
+    k_sv_clear<T><<<sv_grid(x.cap, num_sms), 256, 0, st>>>(x); hy::count_launch();
+    k_sv_finish_reset<T><<<1, 1, 0, st>>>(x, hf ? 1 : 0); hy::count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t sv_copy(const SVec<T> &dst, const SVec<T> &src, int num_sms, cudaStream_t st)
+{
+    k_sv_copy<T><<<sv_grid(src.cap, num_sms), 256, 0, st>>>(dst, src); hy::count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t sv_excite(const SVec<T> &x, const SvOpArgs &o, int k, int nc, double theta,
+                      int num_sms, cudaStream_t st)
+{
+    const T c = T(std::cos(theta)), s = T(std::sin(theta));
+    for (int ci = 0; ci < nc; ++ci) {
+        k_sv_snap<<<1, 1, 0, st>>>(x.snap, x.count); hy::count_launch();
+        k_sv_excite<T><<<sv_grid(x.cap, num_sms), 256, 0, st>>>(x, o, k, ci, c, s);
+        hy::count_launch();
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t sv_dot(const SVec<T> &x, const T *y, double *partials, double *out, int num_sms,
+                   cudaStream_t st)
+{
+    const int G = 4 * num_sms;
+    k_sv_dot_partial<T><<<G, 256, 0, st>>>(x, y, partials); hy::count_launch();
+    k_sv_sum<<<1, 256, 0, st>>>(partials, G, out); hy::count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t sv_scale_rsqrt(const SVec<T> &x, const double *norm2, int num_sms, cudaStream_t st)
+{
+    k_sv_scale<T><<<sv_grid(x.cap, num_sms), 256, 0, st>>>(x, norm2); hy::count_launch();
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -209,9 +446,10 @@ template <typename T>
 cudaError_t hpsi_scatter(const SparseArgs<T> &a, int num_sms, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(a.sigma, 0, size_t(a.Na) * a.Nb * sizeof(T), st);
-    if (e != cudaSuccess || a.m == 0) return e;
-    int64_t g = a.m;
+    if (e != cudaSuccess || (!a.d_m && a.m == 0)) return e;
+    int64_t g = a.d_m ? a.cap : a.m;
     if (g > int64_t(num_sms) * 32) g = int64_t(num_sms) * 32;
+    if (g < 1) g = 1;
     k_hpsi_scatter<T><<<unsigned(g), 256, 0, st>>>(a); hy::count_launch();
     return cudaGetLastError();
 }
@@ -219,10 +457,13 @@ cudaError_t hpsi_scatter(const SparseArgs<T> &a, int num_sms, cudaStream_t st)
 template <typename T>
 cudaError_t grad_sparse(const SparseGradArgs<T> &a, int num_sms, cudaStream_t st)
 {
+    (void)num_sms;
     if (a.n_ops == 0) return cudaSuccess;
-    int64_t g = a.n_ops;
-    if (g > int64_t(num_sms) * 16) g = int64_t(num_sms) * 16;
-    k_grad_sparse<T><<<unsigned(g), 256, 0, st>>>(a); hy::count_launch();
+    k_grad_sparse<T><<<dim3(unsigned(a.n_ops), unsigned(a.chunks)), 256, 0, st>>>(a);
+    hy::count_launch();
+    k_grad_sparse_final<<<unsigned((a.n_ops + 255) / 256), 256, 0, st>>>(a.partials, a.chunks,
+                                                                       a.n_ops, a.g);
+    hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -234,6 +475,17 @@ template cudaError_t hpsi_scatter<double>(const SparseArgs<double> &, int, cudaS
 template cudaError_t hpsi_scatter<float>(const SparseArgs<float> &, int, cudaStream_t);
 template cudaError_t grad_sparse<double>(const SparseGradArgs<double> &, int, cudaStream_t);
 template cudaError_t grad_sparse<float>(const SparseGradArgs<float> &, int, cudaStream_t);
+#define HY_SV_INST(T)                                                                       \
+    template cudaError_t sv_reset<T>(const SVec<T> &, bool, int, cudaStream_t);              \
+    template cudaError_t sv_copy<T>(const SVec<T> &, const SVec<T> &, int, cudaStream_t);   \
+    template cudaError_t sv_excite<T>(const SVec<T> &, const SvOpArgs &, int, int, double,  \
+                                      int, cudaStream_t);                                    \
+    template cudaError_t sv_dot<T>(const SVec<T> &, const T *, double *, double *, int,     \
+                                   cudaStream_t);                                            \
+    template cudaError_t sv_scale_rsqrt<T>(const SVec<T> &, const double *, int, cudaStream_t);
+HY_SV_INST(double)
+HY_SV_INST(float)
+#undef HY_SV_INST
 
 }  // namespace k
 }  // namespace hy

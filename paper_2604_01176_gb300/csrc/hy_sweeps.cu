@@ -30,29 +30,67 @@ __device__ __forceinline__ double block_sum(double v)
 }
 
 // ---------------------------------------------------------------------------
-// <x|y> in double: fixed grid of G blocks writes G partials, one block sums
-// them in index order.
+// <x|y> with FP64 accuracy: fixed grid of G blocks writes G partials, one
+// block sums them in index order (deterministic for a given G).  Float
+// inputs accumulate through Dot2 (error-free FP32 transformations, flushed to
+// FP64 every 32 products), double inputs by FMA in double.  16-byte aligned
+// inputs are read as float4 / double2.
 // ---------------------------------------------------------------------------
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using V = float4; static constexpr int W = 4; };
+template <> struct Vec2<double> { using V = double2; static constexpr int W = 2; };
+
+template <typename T>
+__device__ __forceinline__ void acc_vec(ProdAcc<T> &acc, const float4 &u, const float4 &w)
+{
+    acc.add(u.x, w.x);
+    acc.add(u.y, w.y);
+    acc.add(u.z, w.z);
+    acc.add(u.w, w.w);
+}
+template <typename T>
+__device__ __forceinline__ void acc_vec(ProdAcc<T> &acc, const double2 &u, const double2 &w)
+{
+    acc.add(u.x, w.x);
+    acc.add(u.y, w.y);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_dot_partial(const T *__restrict__ x, const T *__restrict__ y, int64_t N,
               double *__restrict__ partials)
 {
-    double s = 0.0;
+    using V = typename Vec2<T>::V;
+    constexpr int W = Vec2<T>::W;
+    ProdAcc<T> acc;
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride)
-        s += double(x[i]) * double(y[i]);
-    s = block_sum(s);
+    int64_t done = 0;
+    if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0) {
+        const int64_t NV = N / W;
+        const V *xv = reinterpret_cast<const V *>(x), *yv = reinterpret_cast<const V *>(y);
+        int64_t v = tid;
+        for (; v + stride < NV; v += 2 * stride) {     // two vectors in flight
+            const V u0 = xv[v], w0 = yv[v], u1 = xv[v + stride], w1 = yv[v + stride];
+            acc_vec<T>(acc, u0, w0);
+            acc_vec<T>(acc, u1, w1);
+        }
+        if (v < NV) acc_vec<T>(acc, xv[v], yv[v]);
+        done = NV * W;
+    }
+    for (int64_t i = done + tid; i < N; i += stride) acc.add(x[i], y[i]);
+    const double s = block_sum(acc.total());
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// out = sum of the G partials in index order (add: out += that sum)
 __global__ void __launch_bounds__(256)
-k_sum_partials(const double *__restrict__ partials, int G, double *__restrict__ out)
+k_sum_partials(const double *__restrict__ partials, int G, double *__restrict__ out, int add)
 {
     double s = 0.0;
     for (int i = threadIdx.x; i < G; i += blockDim.x) s += partials[i];
     s = block_sum(s);
-    if (threadIdx.x == 0) *out = s;
+    if (threadIdx.x == 0) *out = add ? *out + s : s;
 }
 
 template <typename T>
@@ -60,7 +98,7 @@ cudaError_t dot(const T *x, const T *y, int64_t N, double *partials, int G,
                 double *out, cudaStream_t st)
 {
     k_dot_partial<T><<<G, 256, 0, st>>>(x, y, N, partials); hy::count_launch();
-    k_sum_partials<<<1, 256, 0, st>>>(partials, G, out); hy::count_launch();
+    k_sum_partials<<<1, 256, 0, st>>>(partials, G, out, 0); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -68,17 +106,34 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_scale_rsqrt(T *__restrict__ x, int64_t N, const double *__restrict__ norm2)
 {
+    using V = typename Vec2<T>::V;
+    constexpr int W = Vec2<T>::W;
     const T f = T(1.0 / sqrt(*norm2));
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride)
-        x[i] *= f;
+    int64_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        const int64_t NV = N / W;
+        V *xv = reinterpret_cast<V *>(x);
+        for (int64_t v = tid; v < NV; v += stride) {
+            V u = xv[v];
+            if constexpr (W == 4) {
+                u.x *= f; u.y *= f; u.z *= f; u.w *= f;
+            } else {
+                u.x *= f; u.y *= f;
+            }
+            xv[v] = u;
+        }
+        done = NV * W;
+    }
+    for (int64_t i = done + tid; i < N; i += stride) x[i] *= f;
 }
 
 template <typename T>
 cudaError_t scale_rsqrt(T *x, int64_t N, const double *norm2, cudaStream_t st)
 {
-    int64_t blocks = (N + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
+    int64_t blocks = (N / Vec2<T>::W + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
     if (blocks < 1) blocks = 1;
     k_scale_rsqrt<T><<<unsigned(blocks), 256, 0, st>>>(x, N, norm2); hy::count_launch();
     return cudaGetLastError();
@@ -206,6 +261,81 @@ cudaError_t excite(T *psi, const uint32_t *ae, int64_t nrows, const uint32_t *be
     return cudaGetLastError();
 }
 
+// exp(theta A) as k_excite on a grid of fixed height (rows strided by
+// gridDim.y), each block also writing the FP64-accurate change of the squared
+// norm over its pairs: x'^2 + y'^2 - x^2 - y^2.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_excite_n(T *__restrict__ psi, const uint32_t *__restrict__ ae,
+           const uint32_t *__restrict__ be, int64_t nrows, int64_t ncols, int64_t Nb, T c,
+           T s_eps, double *__restrict__ partials)
+{
+    ProdAcc<T> acc;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t < ncols) {
+        int64_t B = t, B2 = t;
+        T sb = s_eps;
+        if (be) {
+            const uint32_t u = be[t];
+            B = u & 0x7FFFu;
+            B2 = (u >> 15) & 0x7FFFu;
+            if (u >> 31) sb = -sb;
+        }
+        for (int64_t rr = blockIdx.y; rr < nrows; rr += gridDim.y) {
+            int64_t A = rr, A2 = rr;
+            T sg = sb;
+            if (ae) {
+                const uint32_t u = ae[rr];
+                A = u & 0x7FFFu;
+                A2 = (u >> 15) & 0x7FFFu;
+                if (u >> 31) sg = -sg;
+            }
+            T *x = psi + A * Nb + B, *y = psi + A2 * Nb + B2;
+            const T xv = *x, yv = *y;
+            const T nx = c * xv - sg * yv, ny = c * yv + sg * xv;
+            *x = nx;
+            *y = ny;
+            acc.add(nx, nx);
+            acc.add(ny, ny);
+            acc.add(-xv, xv);
+            acc.add(-yv, yv);
+        }
+    }
+    const double s = block_sum(acc.total());
+    if (threadIdx.x == 0) partials[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = s;
+}
+
+namespace {
+dim3 excite_n_grid(int64_t nrows, int64_t ncols, int num_sms)
+{
+    const int64_t gx = (ncols + 255) / 256;
+    int64_t gy = (int64_t(16) * num_sms + gx - 1) / gx;
+    if (gy > nrows) gy = nrows;
+    if (gy < 1) gy = 1;
+    return dim3(unsigned(gx), unsigned(gy));
+}
+}  // namespace
+
+int excite_n_partials(int64_t nrows, int64_t ncols, int num_sms)
+{
+    const dim3 g = excite_n_grid(nrows, ncols, num_sms);
+    return int(g.x * g.y);
+}
+
+template <typename T>
+cudaError_t excite_n(T *psi, const uint32_t *ae, int64_t nrows, const uint32_t *be,
+                     int64_t ncols, int64_t Nb, double c, double s_eps, double *partials,
+                     double *norm2, int num_sms, cudaStream_t st)
+{
+    if (nrows == 0 || ncols == 0) return cudaSuccess;
+    const dim3 grid = excite_n_grid(nrows, ncols, num_sms);
+    k_excite_n<T><<<grid, 256, 0, st>>>(psi, ae, be, nrows, ncols, Nb, T(c), T(s_eps), partials);
+    hy::count_launch();
+    k_sum_partials<<<1, 256, 0, st>>>(partials, int(grid.x * grid.y), norm2, 1);
+    hy::count_launch();
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Determinant rank / unrank with the binomial table in shared memory.
 // ---------------------------------------------------------------------------
@@ -308,6 +438,12 @@ template cudaError_t excite<double>(double *, const uint32_t *, int64_t,
 template cudaError_t excite<float>(float *, const uint32_t *, int64_t,
                                   const uint32_t *, int64_t, int64_t, double, double,
                                   cudaStream_t);
+template cudaError_t excite_n<double>(double *, const uint32_t *, int64_t, const uint32_t *,
+                                     int64_t, int64_t, double, double, double *, double *,
+                                     int, cudaStream_t);
+template cudaError_t excite_n<float>(float *, const uint32_t *, int64_t, const uint32_t *,
+                                    int64_t, int64_t, double, double, double *, double *, int,
+                                    cudaStream_t);
 
 }  // namespace k
 }  // namespace hy

@@ -309,3 +309,74 @@ def test_sweeps_full_size_sparse_state(n, seed):
         rows = np.nonzero(t)[0]
         g_ref = 2.0 * float(t[rows] @ ref.sigma_rows(psi, rows)) if len(rows) else 0.0
         assert abs(g[k] - g_ref) < 1e-11
+
+
+def test_tracked_excitations_and_renormalisation():
+    """hy_apply_excitation_tracked: the tracked squared norm equals the FP64
+    norm of the rotated float state, and one hy_renormalize after the
+    product equals the oracle's normalised product."""
+    import paper_2604_01176_gb300 as hy
+    h1, h2, ec = synth.integrals(8, 1005)
+    ref = oracle.System(h1, h2, ec, 8, 4, 4)
+    ham = hy.Hamiltonian(h1, h2, ec, 8, 4, 4)
+    pool = hy.Pool(ham)
+    opd = ref.pool()
+    rng = np.random.default_rng(21)
+    ops, th = rng.integers(0, len(opd), 9), rng.normal(0, 0.6, 9)
+    for dt, tol in ((torch.float32, 2e-6), (torch.float64, 1e-13)):
+        psi = torch.zeros(ham.n_det, dtype=dt, device="cuda")
+        psi[0] = 1.0
+        n2 = torch.ones((), dtype=torch.float64, device="cuda")
+        for k, t in zip(ops, th):
+            pool.apply_excitation_tracked(int(k), float(t), psi, n2)
+        direct = float((psi.double() ** 2).sum().item())
+        assert abs(n2.item() - direct) < 1e-13 * direct
+        ham.renormalize(psi, n2)
+        want = ref.hf_state()
+        for k, t in zip(ops, th):
+            want = ref.apply_excitation(opd[k], t, want)
+        assert np.abs(psi.double().cpu().numpy() - want).max() < tol
+
+
+def test_float_dot_is_fp64_accurate():
+    """Float inner products (Dot2 runs flushed into FP64) against the exact
+    FP64 dot of the same float values: aligned and unaligned inputs, a ragged
+    tail, and products near the FP32 overflow threshold."""
+    import paper_2604_01176_gb300 as hy
+    h1, h2, ec = synth.integrals(6, 1001)
+    ham = hy.Hamiltonian(h1, h2, ec, 6, 3, 3)
+    g = torch.Generator().manual_seed(5)
+    N = ham.n_det
+    base = torch.randn(2 * N + 3, generator=g, dtype=torch.float32).cuda()
+    for off in (0, 1, 3):       # device views 4 * off bytes past a 16-byte boundary
+        x = base[off:off + N]
+        y = base[N + 3 - off:2 * N + 3 - off]
+        xd, yd = x.cpu().double().numpy(), y.cpu().double().numpy()
+        want = float(np.dot(xd, yd))
+        got = float(ham.dot(x, y).item())
+        assert abs(got - want) <= 1e-13 * float(np.abs(xd * yd).sum())
+    big = torch.full((N,), 1e19, dtype=torch.float32, device="cuda")
+    got = float(ham.dot(big, big).item())
+    want = N * float(np.float32(1e19)) ** 2
+    assert abs(got - want) <= 1e-12 * want
+
+
+def test_kernel_class_profiler():
+    """hy_profile_*: enabled classes count their launches, device time and
+    algorithmic bytes; disabled classes record nothing."""
+    import paper_2604_01176_gb300 as hy
+    h1, h2, ec = synth.integrals(8, 1005)
+    ham = hy.Hamiltonian(h1, h2, ec, 8, 4, 4)
+    pool = hy.Pool(ham)
+    psi = torch.zeros(ham.n_det, dtype=torch.float32, device="cuda")
+    psi[0] = 1.0
+    hy.profile_enable(["excite", "reduce"])
+    pool.apply_excitation(len(pool) - 1, 0.3, psi)
+    ham.dot(psi, psi)
+    ham.apply_h(psi)
+    torch.cuda.synchronize()
+    ex, red, hp = hy.profile_read("excite"), hy.profile_read("reduce"), hy.profile_read("hpsi")
+    hy.profile_enable([])
+    assert ex["launches"] >= 1 and ex["ms"] > 0 and ex["bytes"] > 0
+    assert red["launches"] == 1 and red["bytes"] == 2.0 * ham.n_det * 4
+    assert hp["launches"] == 0 and hp["ms"] == 0

@@ -159,3 +159,78 @@ def test_sparse_driver_follows_dense_driver(cfg, iters):
     mixed = hy.Adapt(ham, pool, "mixed", max_iter=iters, sparse=True).run(iters)
     assert [r["selected"] for r in mixed] == [r["selected"] for r in dense]
     assert abs(mixed[-1]["energy"] - dense[-1]["energy"]) < 1e-6
+
+
+def _ansatz(ref, seed, length):
+    rng = np.random.default_rng(seed)
+    return list(rng.integers(0, len(ref.pool()), length)), rng.normal(0, 0.5, length)
+
+
+@pytest.mark.parametrize("cfg", [(6, 3, 3, 1001), (7, 4, 3, 77), (8, 4, 4, 1005)])
+@pytest.mark.parametrize("cap", ["all", "tiny"])
+def test_sparse_state_evaluation_matches_oracle(cfg, cap):
+    """hy_adapt_evaluate through the sparse-state path (support list kept
+    across the rotations, the adjoint's phi side sparse) and, with a tiny
+    capacity, through its overflow fallback: energy, gradient and state
+    against the oracle; then a shorter ansatz on the same driver (the lists
+    of the longer one must be cleared)."""
+    import oracle.adapt as oadapt
+    import paper_2604_01176_gb300 as hy
+    ref, ham, pool = system(*cfg)
+    opd = ref.pool()
+    ops, th = _ansatz(ref, 11, 8)
+    ad = hy.Adapt(ham, pool, "f64", max_iter=16, sparse=True,
+                  sparse_cap=ham.n_det if cap == "all" else 3)
+    for length in (8, 8, 3):
+        o, t = ops[:length], th[:length] + 0.05 * length
+        ad.set_ansatz(o, t)
+        e, g = ad.evaluate(t)
+        e_ref, g_ref = oadapt.energy_and_gradient(ref, opd, o, t)
+        assert abs(e - e_ref) < 1e-10
+        assert np.abs(g - g_ref).max() < 1e-9
+        psi = ad.state().cpu().numpy()
+        assert np.abs(psi - oadapt.prepare(ref, opd, o, t)).max() < 1e-12
+
+
+@pytest.mark.parametrize("cfg", [(6, 3, 3, 1001), (8, 4, 4, 1005)])
+def test_sparse_state_float_evaluation(cfg):
+    """Float sparse evaluation (support renormalised in double) against the
+    dense float evaluation and the oracle."""
+    import oracle.adapt as oadapt
+    import paper_2604_01176_gb300 as hy
+    ref, ham, pool = system(*cfg)
+    opd = ref.pool()
+    ops, th = _ansatz(ref, 5, 6)
+    sp = hy.Adapt(ham, pool, "mixed", max_iter=16, sparse=True, sparse_cap=ham.n_det)
+    de = hy.Adapt(ham, pool, "mixed", max_iter=16)
+    sp.set_ansatz(ops, th)
+    de.set_ansatz(ops, th)
+    e_s, g_s = sp.evaluate(th, torch.float32)
+    e_d, g_d = de.evaluate(th, torch.float32)
+    e_ref, g_ref = oadapt.energy_and_gradient(ref, opd, ops, th)
+    scale = max(1.0, abs(e_ref))
+    assert abs(e_s - e_ref) < 2e-6 * scale and abs(e_d - e_ref) < 2e-6 * scale
+    assert np.abs(g_s - g_ref).max() < 1e-4 * max(1.0, np.abs(g_ref).max())
+    assert np.abs(g_s - g_d).max() < 1e-4 * max(1.0, np.abs(g_ref).max())
+    psi = sp.state(torch.float32).double().cpu().numpy()
+    assert abs(np.linalg.norm(psi) - 1.0) < 1e-6
+    assert np.abs(psi - oadapt.prepare(ref, opd, ops, th)).max() < 1e-5
+
+
+def test_sparse_state_full_size_against_dense():
+    """28 qubits: the sparse-state evaluation of a 6-operator ansatz against
+    the dense sweeps (double: 1e-10 energy, 1e-9 gradient) and its support
+    against the nonzeros of the dense state."""
+    import paper_2604_01176_gb300 as hy
+    ref, ham, pool = system(14, 7, 7, 1003)
+    ops, th = _ansatz(ref, 9, 6)
+    sp = hy.Adapt(ham, pool, "f64", max_iter=8, sparse=True)
+    de = hy.Adapt(ham, pool, "f64", max_iter=8)
+    sp.set_ansatz(ops, th)
+    de.set_ansatz(ops, th)
+    e_s, g_s = sp.evaluate(th)
+    e_d, g_d = de.evaluate(th)
+    assert abs(e_s - e_d) < 1e-10
+    assert np.abs(g_s - g_d).max() < 1e-9
+    ps, pd = sp.state(), de.state()
+    assert torch.max(torch.abs(ps - pd)).item() < 1e-13
