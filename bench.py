@@ -377,10 +377,12 @@ def adapt_leg(ham, pool, hy, torch, args, rank, world, sparse, clocks=None):
             torch.cuda.synchronize()
 
     warm = [ad.step() for _ in range(W)]
+    ops0, th0 = ad.ansatz()
     barrier()
     if clocks:
         clocks.start()
     l0 = hy.launch_count()
+    hy.profile_enable(hy.PROFILE_CLASSES)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     timed = [ad.step() for _ in range(S)]
@@ -388,6 +390,13 @@ def adapt_leg(ham, pool, hy, torch, args, rank, world, sparse, clocks=None):
     barrier()
     launches = hy.launch_count() - l0
     ms = t0.elapsed_time(t1)
+    prof = {c: hy.profile_read(c) for c in hy.PROFILE_CLASSES}
+    hy.profile_enable([])
+    # end to end: the same S iterations again from the ansatz the timed
+    # region started from, the ansatz restored from host memory before and
+    # read back after every step
+    ad.set_ansatz(ops0, th0)
+    barrier()
     io0 = ad.io_bytes()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -407,7 +416,7 @@ def adapt_leg(ham, pool, hy, torch, args, rank, world, sparse, clocks=None):
     e_bulk = judged[-1]["energy"]
     e_final = ad.refine(steps=4)
     ops, th = ad.ansatz()
-    res = dict(ms=ms, ms_e2e=ms_e2e, launches=launches, clocks=clk, timed=timed, warm=warm,
+    res = dict(ms=ms, ms_e2e=ms_e2e, launches=launches, clocks=clk, timed=timed, warm=warm, prof=prof,
                io=((io1[0] - io0[0]) / S, (io1[1] - io0[1]) / S), e_final=e_final,
                e_bulk=e_bulk, true_rank=[j["true_rank"] for j in judged], ansatz_len=len(ops))
     del ad
@@ -456,6 +465,62 @@ def run_ours(args, rank, world):
     out["head"] = adapt_leg(ham, pool, hy, torch, args, rank, world, True, Clocks(dev.index))
     # the same with the dense sweeps only (tracks the dense kernels)
     out["dense"] = adapt_leg(ham, pool, hy, torch, args, rank, world, False)
+    return out
+
+
+# kernels behind each class of the library's event profiler
+CLASS_KERNELS = {
+    "hpsi": "k_spmm + k_transpose + k_add_transposed + coupling (dense H|psi>)",
+    "hpsi_sparse": "sigma memset + k_hpsi_scatter (scatter H|psi>)",
+    "excite": "k_excite / k_excite_n (dense pair rotations: 4 s bytes per pair)",
+    "sparse_excite": "k_sv_snap + k_sv_excite (sparse-state rotations)",
+    "screen": "k_grad_partial + k_grad_final (dense pool gradients)",
+    "screen_sparse": "k_grad_sparse + k_grad_sparse_final (support-restricted gradients)",
+    "reduce": "dots, norms, renormalisation",
+    "features": "k_pair_weights + k_pair_contract + k_pair_reduce + occupations + k_features",
+}
+
+
+def breakdown(prof, step_ms):
+    """Device time per kernel class in the timed region (CUDA events on the
+    launching stream), as a share of the region's wall time."""
+    return {c: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                "share_of_step": round(v["ms"] / step_ms, 4)}
+            for c, v in prof.items() if v["launches"]}
+
+
+# classes bound by arithmetic rather than HBM (the headline's bulk is float)
+ALU_CLASSES = ("features", "hpsi")
+
+
+def step_roofline(prof, peaks, peak_kind, fp32_peak):
+    """Roofline of the kernel class with the most device time among those
+    whose algorithmic work the host knows: bytes / event time against the
+    measured HBM copy rate, or flops / event time against the derived FP32
+    rate for the arithmetic-bound classes."""
+    known = {c: v for c, v in prof.items()
+             if v["launches"] and (v["bytes"] > 0 or v["flops"] > 0)}
+    top_all = max(prof, key=lambda c: prof[c]["ms"])
+    if not known:
+        return {"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": None, "traffic": None, "dominant_class": top_all}
+    c = max(known, key=lambda k: known[k]["ms"])
+    v = known[c]
+    out = {"kernel_class": c, "kernel": CLASS_KERNELS[c], "launches": v["launches"],
+           "ms_per_launch": round(v["ms"] / v["launches"], 4), "dominant_class": top_all,
+           "timing": "CUDA events around each launch on its stream, over the timed region",
+           "traffic": None}
+    if c in ALU_CLASSES and v["flops"] > 0:
+        tf = v["flops"] / (v["ms"] / 1e3) / 1e12
+        out.update(bound="alu", achieved=round(tf, 3), peak=round(fp32_peak, 3), unit="TFLOP/s",
+                   frac=round(tf / fp32_peak, 4), flops_per_launch=round(v["flops"] / v["launches"]),
+                   peak_kind="derived FP32 FMA rate: 152 SMs x 128 FMA/clk x 2 x max SM clock")
+    else:
+        gbs = v["bytes"] / (v["ms"] / 1e3) / 1e9
+        out.update(bound="hbm", achieved=round(gbs, 1), peak=peaks["hbm_gbs"], unit="GB/s",
+                   frac=round(gbs / peaks["hbm_gbs"], 4),
+                   bytes_per_launch=round(v["bytes"] / v["launches"]),
+                   peak_kind=f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)")
     return out
 
 
@@ -515,7 +580,11 @@ def main():
                           "n_evals": [rec["n_evals"] for rec in r["head"]["timed"]],
                           "support": [rec["support"] for rec in r["head"]["timed"]],
                           "t_total": [round(rec["t_total"], 4) for rec in r["head"]["timed"]],
-                          "launches": r["head"]["launches"]}), flush=True)
+                          "launches": r["head"]["launches"],
+                          "e2e_iters_per_s": round(S / (r["head"]["ms_e2e"] / 1e3), 5),
+                          "kernel_breakdown": breakdown(r["head"]["prof"], r["head"]["ms"]),
+                          "roofline": step_roofline(r["head"]["prof"], peaks, peak_kind, fp32_peak)}),
+              flush=True)
         return
     head, dense = r["head"], r["dense"]
     flops = 2.0 * r["conn"] * N
@@ -535,9 +604,10 @@ def main():
         "data": "synthetic (seeded integrals shaped like the H16 STO-3G chain; no PySCF)",
         "config": {"workload": f"{args.workload}: {r['n']} orbitals, {r['na']}a+{r['nb']}b, "
                                f"{N} determinants, seed {r['seed']}",
-                   "mode": ("mixed precision + learned ranker (top-32 screened exactly, full-screen "
-                            "refresh every 4th ranked iteration); sparse-state path while psi has "
-                            "<= N/64 nonzeros, exact sparse screen while pool x nonzeros <= 5e9"),
+                   "mode": (f"mixed precision + learned ranker (top-{args.top_m} screened exactly, "
+                            f"full-screen refresh every {REFRESH}th ranked iteration); psi kept as a "
+                            "sparse vector while its support fits N/256 (float) or N/64 (double), "
+                            "exact sparse screen while pool x support <= 5e9"),
                    "pool_ops": r["K"], "replicas": world,
                    "ansatz_len_timed": [rec["iter"] + 1 for rec in head["timed"]],
                    "l2": "inputs larger than L2 (state vector 0.66 GB FP32 / 1.33 GB FP64)",
@@ -548,24 +618,27 @@ def main():
                  "algorithmic_bytes": "2 * N_det * sizeof(amplitude)",
                  "connections_per_det": r["conn"], "state": "dense seeded random state"},
         "screen_ms": {"f64": round(r["screen_ms_f64"], 3), "f32": round(r["screen_ms_f32"], 3)},
-        "roofline": {"bound": "alu", "achieved": round(cflops / (r["cpl_ms_f32"] / 1e3) / 1e12, 4),
-                     "peak": round(fp32_peak, 3), "unit": "TFLOP/s",
-                     "frac": round(cflops / (r["cpl_ms_f32"] / 1e3) / 1e12 / fp32_peak, 4),
-                     "traffic": TRAFFIC_F32,
-                     "kernel": "alpha-beta coupling of dense H|psi>, FP32 (k_cpl_gemm + k_cpl_gather)",
-                     "ms_per_launch": round(r["cpl_ms_f32"], 3),
-                     "work": f"{r['cpl_units']} FMA per amplitude x {N} amplitudes",
-                     "peak_kind": f"derived FP32 FMA rate: 152 SMs x 128 FMA/clk x {mhz} MHz",
-                     "f64": {"kernel": "k_coupling<double>",
-                             "achieved": round(cflops / (r["cpl_ms_f64"] / 1e3) / 1e12, 4),
-                             "peak": round(fp64_peak, 3),
-                             "frac": round(cflops / (r["cpl_ms_f64"] / 1e3) / 1e12 / fp64_peak, 4),
-                             "ms_per_launch": round(r["cpl_ms_f64"], 3),
-                             "peak_kind": f"derived FP64 rate: 152 SMs x 2 FMA/clk x {mhz} MHz"},
-                     "whole_hpsi_frac": {"f64": round(flops / (r["hpsi_ms_f64"] / 1e3) / 1e12 /
-                                                      fp64_peak, 4),
-                                         "f32": round(flops / (r["hpsi_ms_f32"] / 1e3) / 1e12 /
-                                                      fp32_peak, 4)}},
+        "roofline": step_roofline(head["prof"], peaks, peak_kind, fp32_peak),
+        "kernel_breakdown": breakdown(head["prof"], head["ms"]),
+        "dense_hpsi_roofline": {
+            "bound": "alu", "achieved": round(cflops / (r["cpl_ms_f32"] / 1e3) / 1e12, 4),
+            "peak": round(fp32_peak, 3), "unit": "TFLOP/s",
+            "frac": round(cflops / (r["cpl_ms_f32"] / 1e3) / 1e12 / fp32_peak, 4),
+            "traffic": TRAFFIC_F32,
+            "kernel": "alpha-beta coupling of dense H|psi>, FP32 (k_cpl_gemm + k_cpl_gather)",
+            "ms_per_launch": round(r["cpl_ms_f32"], 3),
+            "work": f"{r['cpl_units']} FMA per amplitude x {N} amplitudes",
+            "peak_kind": f"derived FP32 FMA rate: 152 SMs x 128 FMA/clk x {mhz} MHz",
+            "f64": {"kernel": "k_coupling<double>",
+                    "achieved": round(cflops / (r["cpl_ms_f64"] / 1e3) / 1e12, 4),
+                    "peak": round(fp64_peak, 3),
+                    "frac": round(cflops / (r["cpl_ms_f64"] / 1e3) / 1e12 / fp64_peak, 4),
+                    "ms_per_launch": round(r["cpl_ms_f64"], 3),
+                    "peak_kind": f"derived FP64 rate: 152 SMs x 2 FMA/clk x {mhz} MHz"},
+            "whole_hpsi_frac": {"f64": round(flops / (r["hpsi_ms_f64"] / 1e3) / 1e12 /
+                                             fp64_peak, 4),
+                                "f32": round(flops / (r["hpsi_ms_f32"] / 1e3) / 1e12 /
+                                             fp32_peak, 4)}},
         "e2e": {"value": round(job_throughput(world, S, head["ms_e2e"]), 6),
                 "unit": "ADAPT iters/s",
                 "h2d_bytes_per_step": int(head["io"][0]), "d2h_bytes_per_step": int(head["io"][1])},

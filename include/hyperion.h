@@ -81,26 +81,30 @@ int64_t hy_launch_count(void);
 /* Kernel-class timing.  hy_profile_enable(mask) clears the counters and, for
  * every class whose bit (1u << class) is set, makes the library record a
  * pair of CUDA events on the launching stream around each of its launches of
- * that class, with the algorithmic bytes those launches move (0 where the
- * host does not know them, e.g. sparse work whose size lives on the device).
- * hy_profile_read waits for the recorded events and returns, per class, the
- * launches, the summed device milliseconds and the summed bytes.  mask = 0
- * (the default) records nothing and costs nothing.  Process-wide; calls may
- * come from several threads. */
+ * that class, with the algorithmic bytes and floating-point operations those
+ * launches perform (0 where the host does not know them, e.g. sparse work
+ * whose size lives on the device).  hy_profile_read waits for the recorded
+ * events and returns, per class, the launches, the summed device
+ * milliseconds, bytes and flops (any output may be NULL).  mask = 0 (the
+ * default) records nothing and costs nothing.  Process-wide; calls may come
+ * from several threads. */
 typedef enum {
-    HY_PROF_HPSI = 0,          /* dense H|psi> (hy_apply_h): 2 N s bytes       */
+    HY_PROF_HPSI = 0,          /* dense H|psi> (hy_apply_h): 2 N s bytes,
+                                  2 x connections x N flops                    */
     HY_PROF_HPSI_SPARSE = 1,   /* scatter H|psi> incl. zeroing sigma: N s      */
     HY_PROF_EXCITE = 2,        /* dense exp(theta A) pair rotations: 4 s/pair  */
-    HY_PROF_SPARSE_EXCITE = 3, /* rotations of a sparse state (bytes 0)        */
+    HY_PROF_SPARSE_EXCITE = 3, /* rotations of a sparse state (unknown)        */
     HY_PROF_SCREEN = 4,        /* dense pool gradients: 4 s per pair per op    */
-    HY_PROF_SCREEN_SPARSE = 5, /* support-restricted gradients (bytes 0)       */
+    HY_PROF_SCREEN_SPARSE = 5, /* support-restricted gradients (unknown)       */
     HY_PROF_REDUCE = 6,        /* dots / norms / renormalisation: s per read
                                   or written amplitude                         */
-    HY_PROF_FEATURES = 7,      /* ranker features: 2 N s (psi and sigma)       */
+    HY_PROF_FEATURES = 7,      /* ranker features: N s bytes and
+                                  2 N_a N_b n^2 flops per touched-weight pass  */
     HY_PROF_CLASSES = 8
 } hy_prof_class;
 hy_status hy_profile_enable(uint32_t class_mask);
-hy_status hy_profile_read(int cls, int64_t *launches, double *ms, double *bytes);
+hy_status hy_profile_read(int cls, int64_t *launches, double *ms, double *bytes,
+                          double *flops);
 
 /* ---------------------------------------------------------------------- */
 /* Hamiltonian                                                              */
@@ -446,7 +450,12 @@ hy_status hy_ranker_topk(const float *score, int64_t m, int64_t k,
  * start), which bounds the age of the stale-gradient features.  The full
  * screen is also the fallback, run whenever the proposals' ||g|| would stop
  * the loop, and, with cfg.judge, the judge: every ranked iteration also runs
- * it, records the rank of the true argmax and adds its pairs. */
+ * it, records the rank of the true argmax and adds its pairs.  Fits are
+ * owed, not run, while iterations screen exactly (warm-up, refresh, or the
+ * sparse path's exact screen): the owed epochs (the largest owed so far) run
+ * just before the ranker's next proposals, so a ranker that is never needed
+ * is never trained.  A ranker passed in already fitted is used as is until
+ * a refresh owes it a refit. */
 hy_status hy_adapt_set_ranker(hy_adapt *a, hy_ranker *r, int warm_iters,
                               int epochs, int refresh_every);
 

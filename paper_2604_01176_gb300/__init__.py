@@ -47,11 +47,11 @@ def profile_enable(classes=()) -> None:
 
 
 def profile_read(cls: str) -> dict:
-    """{launches, ms, bytes} recorded for one class since profile_enable."""
-    n, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    """{launches, ms, bytes, flops} recorded for one class since profile_enable."""
+    n, ms, by, fl = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     check(_abi.load().hy_profile_read(PROFILE_CLASSES.index(cls), ctypes.byref(n),
-                                      ctypes.byref(ms), ctypes.byref(by)))
-    return {"launches": n.value, "ms": ms.value, "bytes": by.value}
+                                      ctypes.byref(ms), ctypes.byref(by), ctypes.byref(fl)))
+    return {"launches": n.value, "ms": ms.value, "bytes": by.value, "flops": fl.value}
 
 
 def dtype_code(t: torch.dtype) -> int:

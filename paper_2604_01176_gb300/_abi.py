@@ -75,7 +75,8 @@ SIGNATURES = {
     "hy_version": (ctypes.c_char_p, []),
     "hy_launch_count": (I64, []),
     "hy_profile_enable": (I32, [ctypes.c_uint32]),
-    "hy_profile_read": (I32, [I32, PI64, ctypes.POINTER(D), ctypes.POINTER(D)]),
+    "hy_profile_read": (I32, [I32, PI64, ctypes.POINTER(D), ctypes.POINTER(D),
+                              ctypes.POINTER(D)]),
     "hy_build_hamiltonian": (I32, [P, P, D, I32, I32, I32, D, PP]),
     "hy_ham_destroy": (I32, [P]),
     "hy_ham_info": (I32, [P, PI64, PI64, PI64, PI64, PI64]),

@@ -37,6 +37,10 @@ struct hy_adapt {
     const hy_pool *p = nullptr;
     hy_ranker *ranker = nullptr;
     int warm_iters = 0, epochs = 0, refresh_every = 0;
+    // epochs of ranker training owed: fits run when the ranker is next used
+    // (iterations that screen exactly only collect its samples)
+    int fit_pending = 0;
+    bool fitted_once = false;
     float *d_feat = nullptr, *d_extra = nullptr, *d_score = nullptr;
     double *d_gp = nullptr;       // proposals' exact gradients [M]
     std::vector<double> last_g;   // |g_k| when last screened (-1: never)
@@ -66,12 +70,19 @@ struct hy_adapt {
     // sparse path: psi and phi of each precision as sparse vectors over
     // buf[dt][0] and buf[dt][2]; clean: the dense array and bitmap hold
     // exactly the listed support (false after dense use or an overflow)
-    hy::SparseState *ss[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-    bool ss_clean[2][2] = {{false, false}, {false, false}};
+    // sparse vectors of each precision over [psi, phi, lam, sigma] =
+    // buf[dt][0, 2, 3, 1]; clean: array and bitmap hold exactly the listed
+    // support (false after dense use or an overflow)
+    hy::SparseState *ss[2][4] = {{nullptr, nullptr, nullptr, nullptr},
+                                 {nullptr, nullptr, nullptr, nullptr}};
+    bool ss_clean[2][4] = {{false, false, false, false}, {false, false, false, false}};
+    bool sig_listed[2] = {false, false};   // sigma's support is listed in ss[dt][3]
+    int64_t conn = 0;             // couplings per determinant (bounds sigma's support)
     // ansatz length at which a precision's support list overflowed: the
     // dense sweeps serve that precision while the ansatz is this long
     size_t sparse_fail_len[2] = {SIZE_MAX, SIZE_MAX};
     int64_t sparse_m = -1;        // support of the last evaluated state (-1: dense)
+    int64_t sparse_m_last[2] = {1, 1};   // last sparse support of each precision
     double *d_n2 = nullptr;       // tracked squared norm (float renormalisation)
     double *d_one = nullptr;      // device constants {1.0, 1.0f}
 };
@@ -131,7 +142,7 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
                         cudaStream_t st, double *e, bool *ok)
 {
     const int d = di(dt);
-    hy::SparseState *S = a->ss[d][0];
+    hy::SparseState *S = a->ss[d][0], *G = a->ss[d][3];
     void *psi = a->buf[d][0], *sigma = a->buf[d][1];
     HY_TRY(hy::sstate_reset(S, !a->ss_clean[d][0], true, st));
     a->ss_clean[d][0] = true;
@@ -141,19 +152,41 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
         HY_TRY(hy::sstate_dot(S, psi, a->d_n2, st));
         HY_TRY(hy::sstate_scale_rsqrt(S, a->d_n2, st));
     }
-    HY_TRY(hy::sstate_apply_h(S, sigma, st));
+    // list sigma's support while the last support times the couplings (an
+    // upper bound) fits its list; a list that still overflows (the support
+    // grew with a new operator) is caught below and costs only the listing
+    const double est = double(std::max<int64_t>(a->sparse_m_last[d], 1)) * double(a->conn);
+    const bool track = est <= double(hy::sstate_cap(G));
+    if (track) {
+        HY_TRY(hy::sstate_reset(G, !a->ss_clean[d][3], false, st));
+        a->ss_clean[d][3] = true;
+        HY_TRY(hy::sstate_apply_h(S, G, sigma, st));
+    } else {
+        a->ss_clean[d][3] = false;
+        HY_TRY(hy::sstate_apply_h(S, nullptr, sigma, st));
+    }
     HY_TRY(hy::sstate_dot(S, sigma, a->d_e, st));
-    int64_t cnt = 0;
+    int64_t cnt[2] = {0, 0};
     HY_TRY(xfer(a, e, a->d_e, sizeof(double), cudaMemcpyDeviceToHost, st, "energy readback"));
-    HY_TRY(xfer(a, &cnt, hy::sstate_count(S), sizeof(int64_t), cudaMemcpyDeviceToHost, st,
+    HY_TRY(xfer(a, &cnt[0], hy::sstate_count(S), sizeof(int64_t), cudaMemcpyDeviceToHost, st,
                 "support count"));
+    if (track)
+        HY_TRY(xfer(a, &cnt[1], hy::sstate_count(G), sizeof(int64_t), cudaMemcpyDeviceToHost, st,
+                    "support count"));
     HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
-    *ok = cnt <= hy::sstate_cap(S);
+    *ok = cnt[0] <= hy::sstate_cap(S);
     if (!*ok) {
         a->ss_clean[d][0] = false;
         return HY_OK;
     }
-    a->sparse_m = cnt;
+    // sigma's values are complete either way; an overflowing list only
+    // leaves its support unlisted (and its array to be cleared in full)
+    a->sig_listed[d] = track && cnt[1] <= hy::sstate_cap(G);
+    if (track && !a->sig_listed[d]) a->ss_clean[d][3] = false;
+    hy::sstate_set_hint(S, cnt[0]);
+    if (a->sig_listed[d]) hy::sstate_set_hint(G, cnt[1]);
+    a->sparse_m = cnt[0];
+    a->sparse_m_last[d] = cnt[0];
     return HY_OK;
 }
 
@@ -171,6 +204,8 @@ hy_status energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     }
     void *psi = a->buf[d][0], *sigma = a->buf[d][1];
     a->ss_clean[d][0] = false;
+    a->ss_clean[d][3] = false;
+    a->sig_listed[d] = false;
     HY_TRY(set_hf(a, psi, dt, st));
     // float states: the squared norm is tracked through the rotations in
     // double and the state renormalised once after the last one (equal to
@@ -201,6 +236,7 @@ hy_status gradient_dense(hy_adapt *a, const std::vector<double> &th, hy_dtype dt
     void *psi = a->buf[d][0], *sigma = a->buf[d][1];
     void *phi = a->buf[d][2], *lam = a->buf[d][3];
     a->ss_clean[d][1] = false;
+    a->ss_clean[d][2] = false;
     HY_TRY(cu(cudaMemcpyAsync(phi, psi, size_t(a->N) * es, cudaMemcpyDeviceToDevice, st), "copy"));
     HY_TRY(cu(cudaMemcpyAsync(lam, sigma, size_t(a->N) * es, cudaMemcpyDeviceToDevice, st), "copy"));
     for (size_t l = j; l-- > 0;) {
@@ -227,27 +263,47 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     if (j == 0) return HY_OK;
     if (a->sparse_m < 0) return gradient_dense(a, th, dt, st, g);
     const int d = di(dt);
-    hy::SparseState *P = a->ss[d][0], *F = a->ss[d][1];
+    hy::SparseState *P = a->ss[d][0], *F = a->ss[d][1], *L = a->ss[d][2], *G = a->ss[d][3];
     void *sigma = a->buf[d][1], *lam = a->buf[d][3];
     HY_TRY(hy::sstate_reset(F, !a->ss_clean[d][1], false, st));
     a->ss_clean[d][1] = true;
     HY_TRY(hy::sstate_copy(F, P, st));
-    HY_TRY(cu(cudaMemcpyAsync(lam, sigma, size_t(a->N) * es, cudaMemcpyDeviceToDevice, st), "copy"));
+    hy::sstate_set_hint(F, a->sparse_m);
+    // lambda starts as sigma: a sparse copy when sigma's support is listed
+    const bool lam_sparse = a->sig_listed[d];
+    if (lam_sparse) {
+        HY_TRY(hy::sstate_reset(L, !a->ss_clean[d][2], false, st));
+        a->ss_clean[d][2] = true;
+        HY_TRY(hy::sstate_copy(L, G, st));
+    } else {
+        a->ss_clean[d][2] = false;
+        HY_TRY(cu(cudaMemcpyAsync(lam, sigma, size_t(a->N) * es, cudaMemcpyDeviceToDevice, st),
+                  "copy"));
+    }
     for (size_t l = j; l-- > 0;) {
         HY_TRY(hy::sstate_gradients(F, lam, a->p, a->d_ops + l, 1, a->sparse_m, a->d_ga + l, st));
         if (l == 0) break;
         HY_TRY(hy::sstate_excite(F, a->p, a->ops[l], -th[l], st));
-        HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], -th[l], lam, dt, 0, st));
+        if (lam_sparse)
+            HY_TRY(hy::sstate_excite(L, a->p, a->ops[l], -th[l], st));
+        else
+            HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], -th[l], lam, dt, 0, st));
     }
-    int64_t cnt = 0;
+    int64_t cnt[2] = {0, 0};
     HY_TRY(xfer(a, g.data(), a->d_ga, j * sizeof(double), cudaMemcpyDeviceToHost, st,
                 "gradient readback"));
-    HY_TRY(xfer(a, &cnt, hy::sstate_count(F), sizeof(int64_t), cudaMemcpyDeviceToHost, st,
+    HY_TRY(xfer(a, &cnt[0], hy::sstate_count(F), sizeof(int64_t), cudaMemcpyDeviceToHost, st,
                 "support count"));
+    if (lam_sparse)
+        HY_TRY(xfer(a, &cnt[1], hy::sstate_count(L), sizeof(int64_t), cudaMemcpyDeviceToHost, st,
+                    "support count"));
     HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
-    if (cnt <= hy::sstate_cap(F)) return HY_OK;
-    a->ss_clean[d][1] = false;    // phi's list overflowed: redo densely
-    return gradient_dense(a, th, dt, st, g);
+    const bool f_ok = cnt[0] <= hy::sstate_cap(F), l_ok = cnt[1] <= hy::sstate_cap(L);
+    if (lam_sparse) hy::sstate_set_hint(L, cnt[1]);
+    if (f_ok && l_ok) return HY_OK;
+    if (!f_ok) a->ss_clean[d][1] = false;
+    if (!l_ok) a->ss_clean[d][2] = false;
+    return gradient_dense(a, th, dt, st, g);   // a list overflowed: redo densely
 }
 
 hy_status upload_ops(hy_adapt *a, cudaStream_t st)
@@ -490,7 +546,13 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
             const hy_dtype dt = d == 0 ? HY_F64 : HY_F32;
             for (int b = 0; b < 2 && s == HY_OK; ++b)
                 s = hy::sstate_create(h, dt, a->buf[d][b == 0 ? 0 : 2], cap, &a->ss[d][b]);
+            // sigma = H psi and lambda spread over <= support x couplings
+            // determinants: their lists hold N/8
+            const int64_t lcap = std::min(a->N, std::max(cap, a->N / 8));
+            if (s == HY_OK) s = hy::sstate_create(h, dt, a->buf[d][3], lcap, &a->ss[d][2]);
+            if (s == HY_OK) s = hy::sstate_create(h, dt, a->buf[d][1], lcap, &a->ss[d][3]);
         }
+        a->conn = hy::ham_connections(h);
     }
     a->last_g.assign(a->K, -1.0);
     a->age.assign(a->K, 0);
@@ -598,15 +660,23 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         if (ranked) {
             HY_TRY(hy_ranker_features(a->h, a->p, psi, sigma, bulk, a->d_extra, a->d_feat, st));
             HY_TRY(hy_ranker_add_samples(a->ranker, a->d_feat, a->d_g, a->K, st));
-            if (a->iter + 1 == a->warm_iters)
-                HY_TRY(hy_ranker_fit(a->ranker, a->epochs, 256, 1e-3f, 1234 + a->iter, nullptr, st));
-            else if (refresh)   // warm-started refit on the grown training set
-                HY_TRY(hy_ranker_fit(a->ranker, std::max(1, a->epochs / 4), 256, 1e-3f,
-                                     1234 + a->iter, nullptr, st));
+            // the first fit after the warm-up, warm-started refits on the
+            // grown training set at refresh iterations; both are owed until
+            // the ranker's proposals are next needed
+            if (a->iter + 1 >= a->warm_iters && !a->fitted_once)
+                a->fit_pending = std::max(a->fit_pending, a->epochs);
+            else if (refresh)
+                a->fit_pending = std::max(a->fit_pending, std::max(1, a->epochs / 4));
         }
         note_screen(a, all, g);
     } else {
         const int64_t M = std::min<int64_t>(a->cfg.screen_top_m, a->K);
+        if (a->fit_pending > 0 || !a->fitted_once) {
+            HY_TRY(hy_ranker_fit(a->ranker, std::max(a->fit_pending, 1), 256, 1e-3f,
+                                 1234 + a->iter, nullptr, st));
+            a->fit_pending = 0;
+            a->fitted_once = true;
+        }
         HY_TRY(hy_ranker_features(a->h, a->p, psi, sigma, bulk, a->d_extra, a->d_feat, st));
         HY_TRY(hy_ranker_predict(a->ranker, a->d_feat, a->K, a->d_score, st));
         // proposals: the M / 4 operators with the largest Cauchy-Schwarz
@@ -739,10 +809,14 @@ hy_status hy_adapt_set_ranker(hy_adapt *a, hy_ranker *r, int warm_iters, int epo
         return set_err(HY_ERR_ARG, "driver was created without screen_top_m");
     if (warm_iters < 1 || epochs < 1 || refresh_every < 0)
         return set_err(HY_ERR_ARG, "warm_iters and epochs must be >= 1, refresh_every >= 0");
+    int fitted = 0;
+    HY_TRY(hy_ranker_info(r, nullptr, nullptr, nullptr, &fitted));
     a->ranker = r;
     a->warm_iters = warm_iters;
     a->epochs = epochs;
     a->refresh_every = refresh_every;
+    a->fit_pending = 0;
+    a->fitted_once = fitted != 0;
     return HY_OK;
 }
 

@@ -278,7 +278,8 @@ hy_status apply_h_t(hy_ham *h, const T *psi, T *sigma, cudaStream_t st)
         Ma = &h->Ma32; Mb = &h->Mb32; V = h->d_V32;
     }
     (void)f64;
-    hy::ProfScope prof(HY_PROF_HPSI, st, 2.0 * double(h->N) * sizeof(T));
+    hy::ProfScope prof(HY_PROF_HPSI, st, 2.0 * double(h->N) * sizeof(T),
+                       2.0 * double(hy::ham_connections(h)) * double(h->N));
     HY_CUDA(hy::k::spmm<T>(Ma->ptr, Ma->col, Ma->val, h->Na, psi, sigma, h->Nb,
                            false, st), "alpha part");
     HY_CUDA(hy::k::transpose<T>(psi, psiT, h->Na, h->Nb, st), "transpose");
@@ -1033,6 +1034,10 @@ hy::k::SparseArgs<T> sparse_args(const hy_ham *h, const void *psi, void *sigma,
     a.m = m;
     a.d_m = nullptr;
     a.cap = m;
+    a.obits = nullptr;
+    a.olist = nullptr;
+    a.ocount = nullptr;
+    a.ocap = 0;
     const DevCsr<T> *Ma, *Mb;
     if constexpr (sizeof(T) == 8) {
         Ma = &h->Ma64; Mb = &h->Mb64; a.V = h->d_V64;
@@ -1112,8 +1117,9 @@ hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
     if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
     cudaStream_t st = as_stream(stream);
     const size_t nn = size_t(h->n) * h->n;
-    hy::ProfScope prof(HY_PROF_FEATURES, st,
-                       (sigma_or_null ? 2.0 : 1.0) * double(h->N) * (dt == HY_F64 ? 8 : 4));
+    const double passes = sigma_or_null ? 2.0 : 1.0;
+    hy::ProfScope prof(HY_PROF_FEATURES, st, passes * double(h->N) * (dt == HY_F64 ? 8 : 4),
+                       passes * 2.0 * double(h->Na) * double(h->Nb) * double(h->n) * h->n);
     const void *vecs[2] = {psi, sigma_or_null};
     for (int v = 0; v < 2 && vecs[v]; ++v) {
         float *B = h->d_pairB + size_t(v) * h->Na * nn, *rs = h->d_pairRs + size_t(v) * h->Na;
@@ -1494,6 +1500,7 @@ struct hy::SparseState {
     unsigned long long *cnt = nullptr;   // [count, snapshot]
     double *partials = nullptr;
     int64_t n_partials = 0;
+    int64_t hint = 0;                    // host estimate of the count (grids)
 };
 
 namespace {
@@ -1507,6 +1514,7 @@ hy::k::SVec<T> svec(const hy::SparseState *s)
     x.count = s->cnt;
     x.snap = s->cnt + 1;
     x.cap = s->cap;
+    x.hint = s->hint;
     return x;
 }
 
@@ -1594,6 +1602,8 @@ hy_status sstate_copy(SparseState *dst, const SparseState *src, void *stream)
     return HY_OK;
 }
 
+void sstate_set_hint(SparseState *s, int64_t n) { s->hint = n; }
+
 hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double theta, void *stream)
 {
     const hy_ham *h = s->h;
@@ -1645,20 +1655,29 @@ hy_status sstate_scale_rsqrt(SparseState *s, const double *norm2, void *stream)
     return HY_OK;
 }
 
-hy_status sstate_apply_h(const SparseState *s, void *sigma, void *stream)
+hy_status sstate_apply_h(const SparseState *s, SparseState *sig, void *sigma, void *stream)
 {
     cudaStream_t st = as_stream(stream);
     const hy_ham *h = s->h;
-    hy::ProfScope prof(HY_PROF_HPSI_SPARSE, stream, double(h->N) * (s->dt == HY_F64 ? 8 : 4));
-    if (s->dt == HY_F64) {
-        auto a = sparse_args<double>(h, s->v, sigma, s->list, 0);
+    hy::ProfScope prof(HY_PROF_HPSI_SPARSE, stream, sig ? 0.0 : double(h->N) * (s->dt == HY_F64 ? 8 : 4));
+    if (sig && (sig->dt != s->dt || sig->v != sigma)) return fail(HY_ERR_ARG, "sigma state mismatch");
+    auto out = [&](auto &a) {
         a.d_m = s->cnt;
         a.cap = s->cap;
+        if (sig) {
+            a.obits = sig->bits;
+            a.olist = sig->list;
+            a.ocount = sig->cnt;
+            a.ocap = sig->cap;
+        }
+    };
+    if (s->dt == HY_F64) {
+        auto a = sparse_args<double>(h, s->v, sigma, s->list, 0);
+        out(a);
         HY_CUDA(hy::k::hpsi_scatter<double>(a, h->num_sms, st), "sparse H psi");
     } else {
         auto a = sparse_args<float>(h, s->v, sigma, s->list, 0);
-        a.d_m = s->cnt;
-        a.cap = s->cap;
+        out(a);
         HY_CUDA(hy::k::hpsi_scatter<float>(a, h->num_sms, st), "sparse H psi");
     }
     return HY_OK;
@@ -1706,6 +1725,14 @@ const int64_t *sstate_count(const SparseState *s)
     return reinterpret_cast<const int64_t *>(s->cnt);
 }
 const int64_t *sstate_list(const SparseState *s) { return s->list; }
+
+int64_t ham_connections(const hy_ham *h)
+{
+    const int64_t sa = int64_t(h->na) * (h->n - h->na), sb = int64_t(h->nb) * (h->n - h->nb);
+    const int64_t da = int64_t(hy::binom(h->na, 2)) * hy::binom(h->n - h->na, 2);
+    const int64_t db = int64_t(hy::binom(h->nb, 2)) * hy::binom(h->n - h->nb, 2);
+    return 1 + sa + sb + da + db + sa * sb;
+}
 int64_t sstate_cap(const SparseState *s) { return s->cap; }
 
 }  // namespace hy

@@ -117,10 +117,11 @@ struct PatternLists {
 
 // Kernel-class timing (hy_profile.cpp): records an event pair on `stream`
 // around its lifetime when the class is enabled, with the algorithmic bytes
-// the enclosed launches move (0 where they are not known on the host).
+// and floating-point operations of the enclosed launches (0 where the host
+// does not know them).
 class ProfScope {
   public:
-    ProfScope(int cls, void *stream, double bytes);
+    ProfScope(int cls, void *stream, double bytes, double flops = 0.0);
     ~ProfScope();
     ProfScope(const ProfScope &) = delete;
     ProfScope &operator=(const ProfScope &) = delete;
@@ -128,7 +129,7 @@ class ProfScope {
   private:
     int cls_;
     void *stream_;
-    double bytes_;
+    double bytes_, flops_;
     void *a_;
 };
 
@@ -147,19 +148,26 @@ void sstate_destroy(SparseState *s);
 // else only the listed entries.  hf: then set v = |HF> (index 0).
 hy_status sstate_reset(SparseState *s, bool full, bool hf, void *stream);
 hy_status sstate_copy(SparseState *dst, const SparseState *src, void *stream);
+// host estimate of the count, used only to size grids
+void sstate_set_hint(SparseState *s, int64_t n);
 hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double theta, void *stream);
 // *out (device) = sum over the support of v * y (y dense, same dtype), FP64
 hy_status sstate_dot(const SparseState *s, const void *y, double *out, void *stream);
 // v <- v / sqrt(*norm2) on the support (norm2 on the device)
 hy_status sstate_scale_rsqrt(SparseState *s, const double *norm2, void *stream);
-// sigma = H v (dense sigma, zeroed here)
-hy_status sstate_apply_h(const SparseState *s, void *sigma, void *stream);
+// sigma = H v.  sig == nullptr: sigma (dense) is zeroed here; else sig is
+// sigma's sparse state (its array must be `sigma`, reset by the caller) and
+// every reached determinant is listed in it
+hy_status sstate_apply_h(const SparseState *s, SparseState *sig, void *sigma, void *stream);
 // g[i] = 2 <lam | A_{ops[i]} v> over the pairs with a listed end (ops device
 // array or nullptr for the whole pool); m_hint ~ the support size (grid shape)
 hy_status sstate_gradients(const SparseState *s, const void *lam, const hy_pool *p,
                            const int32_t *ops, int64_t n_ops, int64_t m_hint, double *g,
                            void *stream);
 const int64_t *sstate_count(const SparseState *s);   // device pointer
+// most determinants one determinant couples to through H (itself included):
+// 1 + s_a + s_b + d_a + d_b + s_a s_b (singles s, doubles d of each spin)
+int64_t ham_connections(const hy_ham *h);
 const int64_t *sstate_list(const SparseState *s);    // device pointer
 int64_t sstate_cap(const SparseState *s);
 

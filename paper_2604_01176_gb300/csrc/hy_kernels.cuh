@@ -194,6 +194,12 @@ struct SparseArgs {
     int64_t m;
     const unsigned long long *d_m;   // device count (overrides m, clamped to cap) or nullptr
     int64_t cap;
+    // sigma's support as a sparse vector (list, bitmap, count, capacity), or
+    // obits = nullptr: then sigma is zeroed whole and nothing is listed
+    uint32_t *obits;
+    int64_t *olist;
+    unsigned long long *ocount;
+    int64_t ocap;
     const int32_t *Ma_ptr, *Ma_col, *Mb_ptr, *Mb_col;
     const T *Ma_val, *Mb_val, *V;
     const uint32_t *aex, *bexT, *astr, *bstr;
@@ -238,6 +244,7 @@ struct SVec {
     unsigned long long *count;   // device: live count
     unsigned long long *snap;    // device: count at the start of a rotation
     int64_t cap;
+    int64_t hint;                // host estimate of the count (grid size only)
 };
 // a constituent's operator strings and the tables to rank determinants
 struct SvOpArgs {

@@ -20,12 +20,12 @@ namespace {
 struct Pair {
     int cls;
     cudaEvent_t a, b;
-    double bytes;
+    double bytes, flops;
 };
 
 struct Acc {
     int64_t launches = 0;
-    double ms = 0.0, bytes = 0.0;
+    double ms = 0.0, bytes = 0.0, flops = 0.0;
 };
 
 std::atomic<uint32_t> g_mask{0};
@@ -59,6 +59,7 @@ void resolve(size_t keep)
             ++c.launches;
             c.ms += ms;
             c.bytes += p.bytes;
+            c.flops += p.flops;
         }
         g_free.push_back(p.a);
         g_free.push_back(p.b);
@@ -70,8 +71,8 @@ void resolve(size_t keep)
 
 namespace hy {
 
-ProfScope::ProfScope(int cls, void *stream, double bytes)
-    : cls_(cls), stream_(stream), bytes_(bytes), a_(nullptr)
+ProfScope::ProfScope(int cls, void *stream, double bytes, double flops)
+    : cls_(cls), stream_(stream), bytes_(bytes), flops_(flops), a_(nullptr)
 {
     if (cls < 0 || cls >= HY_PROF_CLASSES || !(g_mask.load() & (1u << cls))) return;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -95,7 +96,7 @@ ProfScope::~ProfScope()
         if (b) g_free.push_back(b);
         return;
     }
-    g_pending.push_back(Pair{cls_, a, b, bytes_});
+    g_pending.push_back(Pair{cls_, a, b, bytes_, flops_});
     if (g_pending.size() > 8192) resolve(4096);
 }
 
@@ -112,7 +113,7 @@ hy_status hy_profile_enable(uint32_t class_mask)
     return HY_OK;
 }
 
-hy_status hy_profile_read(int cls, int64_t *launches, double *ms, double *bytes)
+hy_status hy_profile_read(int cls, int64_t *launches, double *ms, double *bytes, double *flops)
 {
     if (cls < 0 || cls >= HY_PROF_CLASSES) {
         hy::set_last_error("profile class out of range");
@@ -124,6 +125,7 @@ hy_status hy_profile_read(int cls, int64_t *launches, double *ms, double *bytes)
     if (launches) *launches = c.launches;
     if (ms) *ms = c.ms;
     if (bytes) *bytes = c.bytes;
+    if (flops) *flops = c.flops;
     return HY_OK;
 }
 

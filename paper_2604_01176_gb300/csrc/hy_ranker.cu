@@ -129,15 +129,18 @@ k_pair_weights(const T *__restrict__ psi, int64_t Na, int64_t Nb,
         for (int64_t c0 = 0; c0 < Nb; c0 += kPwChunk) {
             __syncthreads();
             const int64_t c = c0 + threadIdx.x;
+            int nz = 0;
 #pragma unroll 4
             for (int r = 0; r < kPwRows; ++r) {
                 const int64_t a = a0 + r;
                 const float v = (a < Na && c < Nb) ? float(psi[a * Nb + c]) : 0.0f;
                 ws[r][threadIdx.x] = v * v;
                 rsum[r] = fmaf(v, v, rsum[r]);
+                nz |= v != 0.0f;
             }
             ms[threadIdx.x] = c < Nb ? bstr[c] : 0u;
-            __syncthreads();
+            // a tile of zero weights adds nothing: sparse states skip most
+            if (!__syncthreads_or(nz)) continue;
             for (int cc = 0; cc < kPwChunk; cc += 4) {
                 const uint4 m4 = *reinterpret_cast<const uint4 *>(ms + cc);
                 const float f00 = (m4.x & sel0) == sel0 ? 1.f : 0.f, f10 = (m4.x & sel1) == sel1 ? 1.f : 0.f;
@@ -192,6 +195,7 @@ k_pair_contract(const float *__restrict__ Bw, const float *__restrict__ rs,
         for (int64_t al = blockIdx.y; al < Na; al += gridDim.y) {
             const uint32_t m = astr[al];
             if (i != aa && !(((m >> i) & 1u) && !((m >> aa) & 1u))) continue;
+            if (rs[al] == 0.0f) continue;     // an all-zero row adds nothing
             acc += (j == b) ? rs[al] : (Bw[al * nn + j * n + j] - Bw[al * nn + jb]);
         }
         part[int64_t(blockIdx.y) * nn * nn + int64_t(ia) * nn + jb] = acc;
@@ -404,14 +408,25 @@ __global__ void k_relu_bwd(float *__restrict__ dy, const float *__restrict__ z, 
     if (i < m && !(z[i] > 0.0f)) dy[i] = 0.0f;
 }
 
-// db[j] = sum_i dZ[i][j] (fixed order)
-__global__ void k_colsum(const float *__restrict__ dz, int M, int N, float *__restrict__ db)
+// db[j] = sum_i dZ[i][j] (fixed order): a block of 32 x 8 threads owns 32
+// columns; each of the 8 row groups sums rows g, g + 8, ..., then the 8
+// partials are added in order
+__global__ void __launch_bounds__(256)
+k_colsum(const float *__restrict__ dz, int M, int N, float *__restrict__ db)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
+    __shared__ float part[8][33];
+    const int cx = threadIdx.x & 31, gy = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + cx;
     float s = 0.0f;
-    for (int i = 0; i < M; ++i) s += dz[size_t(i) * N + j];
-    db[j] = s;
+    if (j < N)
+        for (int i = gy; i < M; i += 8) s += dz[size_t(i) * N + j];
+    part[gy][cx] = s;
+    __syncthreads();
+    if (gy == 0 && j < N) {
+        float t = 0.0f;
+        for (int g = 0; g < 8; ++g) t += part[g][cx];
+        db[j] = t;
+    }
 }
 
 // loss gradient of the mean squared error on one output column; also the
@@ -528,6 +543,10 @@ struct hy_ranker {
     float *xb = nullptr, *yb = nullptr, *z[3] = {nullptr, nullptr, nullptr},
           *d[3] = {nullptr, nullptr, nullptr}, *out = nullptr, *dout = nullptr, *sq = nullptr;
     int32_t *idx = nullptr;
+    // one epoch's sample order and the last epoch's per-row squared errors
+    int32_t *perm = nullptr;
+    float *sqall = nullptr;
+    int64_t perm_cap = 0;
     bool fitted = false;
 };
 
@@ -658,6 +677,8 @@ hy_status hy_ranker_destroy(hy_ranker *r)
                      r->z[2], r->d[0], r->d[1], r->d[2], r->out, r->dout, r->sq};
     for (float *b : bufs) cudaFree(b);
     cudaFree(r->idx);
+    cudaFree(r->perm);
+    cudaFree(r->sqall);
     delete r;
     return HY_OK;
 }
@@ -748,8 +769,19 @@ hy_status hy_ranker_fit(hy_ranker *r, int epochs, int batch, float lr, uint64_t 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     RTRY(ensure_act(r, batch));
     const int64_t m = r->n_samples;
+    if (m > r->perm_cap) {
+        RTRY(rcu(cudaStreamSynchronize(st), "sync"));
+        cudaFree(r->perm);
+        cudaFree(r->sqall);
+        r->perm = nullptr;
+        r->sqall = nullptr;
+        r->perm_cap = 0;
+        RTRY(rcu(cudaMalloc(&r->perm, size_t(m) * 4), "ranker order"));
+        RTRY(rcu(cudaMalloc(&r->sqall, size_t(m) * 4), "ranker order"));
+        r->perm_cap = m;
+    }
     std::vector<int32_t> perm(m);
-    std::vector<float> sq(batch);
+    std::vector<float> sq(m);
     uint64_t s = seed;
     double last = 0.0;
     const int H = r->H, F = r->F;
@@ -759,21 +791,22 @@ hy_status hy_ranker_fit(hy_ranker *r, int epochs, int batch, float lr, uint64_t 
             const int64_t j = int64_t(splitmix(s) % uint64_t(i + 1));
             std::swap(perm[i], perm[j]);
         }
-        double ep_loss = 0.0;
-        int64_t ep_rows = 0;
+        // one upload of the epoch's order; minibatches then run without a
+        // host round trip
+        RTRY(rcu(cudaMemcpyAsync(r->perm, perm.data(), size_t(m) * 4, cudaMemcpyHostToDevice, st),
+                 "upload order"));
         for (int64_t o = 0; o < m; o += batch) {
             const int mb = int(std::min<int64_t>(batch, m - o));
-            RTRY(rcu(cudaMemcpyAsync(r->idx, perm.data() + o, size_t(mb) * 4,
-                                     cudaMemcpyHostToDevice, st), "upload batch"));
+            const int32_t *bidx = r->perm + o;
             const unsigned gx = unsigned((int64_t(mb) * F + 255) / 256);
-            K::k_gather_rows<<<gx, 256, 0, st>>>(r->X, r->idx, mb, F, r->xb); hy::count_launch();
-            K::k_gather_rows<<<unsigned((mb + 255) / 256), 256, 0, st>>>(r->Y, r->idx, mb, 1, r->yb); hy::count_launch();
+            K::k_gather_rows<<<gx, 256, 0, st>>>(r->X, bidx, mb, F, r->xb); hy::count_launch();
+            K::k_gather_rows<<<unsigned((mb + 255) / 256), 256, 0, st>>>(r->Y, bidx, mb, 1, r->yb); hy::count_launch();
             RTRY(forward(r, r->xb, mb, st));
             K::k_mse<<<unsigned((mb + 255) / 256), 256, 0, st>>>(r->out, r->yb, mb, r->dout, r->sq); hy::count_launch();
             // layer 3 (H -> 1): dW3 = dout^T z2, db3 = sum dout, d2 = dout W3
             RTRY(rcu(K::gemm<true, false>(r->dout, r->z[2], r->gw + r->woff[3], 1, H, mb, 1, H, H,
                                           nullptr, false, st), "mlp backward"));
-            K::k_colsum<<<1, 32, 0, st>>>(r->dout, mb, 1, r->gw + r->boff[3]); hy::count_launch();
+            K::k_colsum<<<1, 256, 0, st>>>(r->dout, mb, 1, r->gw + r->boff[3]); hy::count_launch();
             RTRY(rcu(K::gemm<false, false>(r->dout, r->w + r->woff[3], r->d[2], mb, H, 1, 1, H, H,
                                            nullptr, false, st), "mlp backward"));
             for (int l = 2; l >= 0; --l) {
@@ -783,8 +816,8 @@ hy_status hy_ranker_fit(hy_ranker *r, int epochs, int batch, float lr, uint64_t 
                 const int fin = l == 0 ? F : H;
                 RTRY(rcu(K::gemm<true, false>(r->d[l], xin, r->gw + r->woff[l], H, fin, mb, H, fin,
                                               fin, nullptr, false, st), "mlp backward"));
-                K::k_colsum<<<unsigned((H + 127) / 128), 128, 0, st>>>(r->d[l], mb, H,
-                                                                       r->gw + r->boff[l]); hy::count_launch();
+                K::k_colsum<<<unsigned((H + 31) / 32), 256, 0, st>>>(r->d[l], mb, H,
+                                                                     r->gw + r->boff[l]); hy::count_launch();
                 if (l > 0)
                     RTRY(rcu(K::gemm<false, false>(r->d[l], r->w + r->woff[l], r->d[l - 1], mb, H,
                                                    H, H, H, H, nullptr, false, st),
@@ -795,15 +828,18 @@ hy_status hy_ranker_fit(hy_ranker *r, int epochs, int batch, float lr, uint64_t 
             K::k_adam<<<unsigned((r->nparam + 255) / 256), 256, 0, st>>>(
                 r->w, r->gw, r->m1, r->m2, int64_t(r->nparam), lr, b1t, b2t); hy::count_launch();
             RTRY(rcu(cudaGetLastError(), "mlp step"));
-            if (ep == epochs - 1) {
-                RTRY(rcu(cudaMemcpyAsync(sq.data(), r->sq, size_t(mb) * 4, cudaMemcpyDeviceToHost,
-                                         st), "loss readback"));
-                RTRY(rcu(cudaStreamSynchronize(st), "sync"));
-                for (int i = 0; i < mb; ++i) ep_loss += sq[i];
-                ep_rows += mb;
-            }
+            if (ep == epochs - 1)
+                RTRY(rcu(cudaMemcpyAsync(r->sqall + o, r->sq, size_t(mb) * 4,
+                                         cudaMemcpyDeviceToDevice, st), "loss"));
         }
-        if (ep == epochs - 1 && ep_rows) last = ep_loss / double(ep_rows);
+    }
+    if (epochs > 0) {
+        RTRY(rcu(cudaMemcpyAsync(sq.data(), r->sqall, size_t(m) * 4, cudaMemcpyDeviceToHost, st),
+                 "loss readback"));
+        RTRY(rcu(cudaStreamSynchronize(st), "sync"));
+        double tot = 0.0;
+        for (int64_t i = 0; i < m; ++i) tot += sq[i];
+        last = tot / double(m);
     }
     RTRY(rcu(cudaStreamSynchronize(st), "sync"));
     r->fitted = true;

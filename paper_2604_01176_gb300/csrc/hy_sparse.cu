@@ -66,6 +66,21 @@ __device__ __forceinline__ T sum_diag(const T *V, int n, int nn, uint32_t mask, 
     return v;
 }
 
+// sigma[o] += v; with an output list, o is also listed the first time it is
+// reached (the bitmap word is read first, so an already listed target costs
+// no atomic on the bitmap)
+template <typename T>
+__device__ __forceinline__ void emit(const SparseArgs<T> &a, int64_t o, T v)
+{
+    atomicAdd(a.sigma + o, v);
+    if (!a.obits) return;
+    const uint32_t bit = 1u << (o & 31);
+    if (__ldcg(a.obits + (o >> 5)) & bit) return;
+    if (atomicOr(a.obits + (o >> 5), bit) & bit) return;
+    const unsigned long long pos = atomicAdd(a.ocount, 1ull);
+    if (pos < (unsigned long long)a.ocap) a.olist[pos] = o;
+}
+
 // one CTA per support entry (grid-stride)
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -80,9 +95,9 @@ k_hpsi_scatter(SparseArgs<T> a)
         const T x = a.psi[d];
         const int64_t A = d / Nb, B = d % Nb;
         for (int k = a.Ma_ptr[A] + threadIdx.x; k < a.Ma_ptr[A + 1]; k += blockDim.x)
-            atomicAdd(a.sigma + int64_t(a.Ma_col[k]) * Nb + B, a.Ma_val[k] * x);
+            emit(a, int64_t(a.Ma_col[k]) * Nb + B, a.Ma_val[k] * x);
         for (int k = a.Mb_ptr[B] + threadIdx.x; k < a.Mb_ptr[B + 1]; k += blockDim.x)
-            atomicAdd(a.sigma + A * Nb + a.Mb_col[k], a.Mb_val[k] * x);
+            emit(a, A * Nb + a.Mb_col[k], a.Mb_val[k] * x);
         const uint32_t am = a.astr[A], bm = a.bstr[B];
         for (int idx = threadIdx.x; idx < ne * nf; idx += blockDim.x) {
             const int e = idx / nf - 1, f = idx % nf - 1;
@@ -122,7 +137,7 @@ k_hpsi_scatter(SparseArgs<T> a)
                 }
             }
             if (neg) c = -c;
-            atomicAdd(a.sigma + Ao * Nb + Bo, c * x);
+            emit(a, Ao * Nb + Bo, c * x);
         }
     }
 }
@@ -300,6 +315,8 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_sv_excite(SVec<T> x, SvOpArgs o, int k, int ci, T c, T s)
 {
+    const int64_t m = list_len(x.snap, 0, x.cap);
+    if (int64_t(blockIdx.x) * blockDim.x >= m) return;    // whole block idle
     __shared__ uint32_t C[33][33];
     for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
     __syncthreads();
@@ -307,7 +324,6 @@ k_sv_excite(SVec<T> x, SvOpArgs o, int k, int ci, T c, T s)
     op_strings(o.desc + 11 * k + 1 + 5 * ci, fw, bw, len);
     const int n = o.n;
     const uint64_t lowm = (1ull << n) - 1;
-    const int64_t m = list_len(x.snap, 0, x.cap);
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < m;
          t += int64_t(gridDim.x) * blockDim.x) {
         const int64_t d = x.list[t];
@@ -376,18 +392,27 @@ k_sv_scale(SVec<T> x, const double *__restrict__ norm2)
 }
 
 namespace {
-unsigned sv_grid(int64_t cap, int num_sms)
+// blocks for a list of about n entries (grid-stride loops cover any count)
+unsigned sv_grid(int64_t n, int num_sms)
 {
-    int64_t g = (cap + 255) / 256;
+    int64_t g = (n + 255) / 256;
     if (g > int64_t(num_sms) * 8) g = int64_t(num_sms) * 8;
     return unsigned(g < 1 ? 1 : g);
 }
 }  // namespace
 
+// entries to size a grid for: twice the host's estimate, within the capacity
+template <typename T>
+int64_t sv_n(const SVec<T> &x)
+{
+    const int64_t h = x.hint > 0 ? 2 * x.hint : x.cap;
+    return h < x.cap ? h : x.cap;
+}
+
 template <typename T>
 cudaError_t sv_reset(const SVec<T> &x, bool hf, int num_sms, cudaStream_t st)
 {
-    k_sv_clear<T><<<sv_grid(x.cap, num_sms), 256, 0, st>>>(x); hy::count_launch();
+    k_sv_clear<T><<<sv_grid(sv_n(x), num_sms), 256, 0, st>>>(x); hy::count_launch();
     k_sv_finish_reset<T><<<1, 1, 0, st>>>(x, hf ? 1 : 0); hy::count_launch();
     return cudaGetLastError();
 }
@@ -395,7 +420,7 @@ cudaError_t sv_reset(const SVec<T> &x, bool hf, int num_sms, cudaStream_t st)
 template <typename T>
 cudaError_t sv_copy(const SVec<T> &dst, const SVec<T> &src, int num_sms, cudaStream_t st)
 {
-    k_sv_copy<T><<<sv_grid(src.cap, num_sms), 256, 0, st>>>(dst, src); hy::count_launch();
+    k_sv_copy<T><<<sv_grid(sv_n(src), num_sms), 256, 0, st>>>(dst, src); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -406,7 +431,7 @@ cudaError_t sv_excite(const SVec<T> &x, const SvOpArgs &o, int k, int nc, double
     const T c = T(std::cos(theta)), s = T(std::sin(theta));
     for (int ci = 0; ci < nc; ++ci) {
         k_sv_snap<<<1, 1, 0, st>>>(x.snap, x.count); hy::count_launch();
-        k_sv_excite<T><<<sv_grid(x.cap, num_sms), 256, 0, st>>>(x, o, k, ci, c, s);
+        k_sv_excite<T><<<sv_grid(sv_n(x), num_sms), 256, 0, st>>>(x, o, k, ci, c, s);
         hy::count_launch();
     }
     return cudaGetLastError();
@@ -425,7 +450,7 @@ cudaError_t sv_dot(const SVec<T> &x, const T *y, double *partials, double *out, 
 template <typename T>
 cudaError_t sv_scale_rsqrt(const SVec<T> &x, const double *norm2, int num_sms, cudaStream_t st)
 {
-    k_sv_scale<T><<<sv_grid(x.cap, num_sms), 256, 0, st>>>(x, norm2); hy::count_launch();
+    k_sv_scale<T><<<sv_grid(sv_n(x), num_sms), 256, 0, st>>>(x, norm2); hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -445,7 +470,9 @@ cudaError_t support(const T *psi, int64_t N, int64_t *list, int64_t cap,
 template <typename T>
 cudaError_t hpsi_scatter(const SparseArgs<T> &a, int num_sms, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(a.sigma, 0, size_t(a.Na) * a.Nb * sizeof(T), st);
+    // with an output list the caller has cleared sigma's previous support
+    cudaError_t e = a.obits ? cudaSuccess
+                            : cudaMemsetAsync(a.sigma, 0, size_t(a.Na) * a.Nb * sizeof(T), st);
     if (e != cudaSuccess || (!a.d_m && a.m == 0)) return e;
     int64_t g = a.d_m ? a.cap : a.m;
     if (g > int64_t(num_sms) * 32) g = int64_t(num_sms) * 32;
