@@ -77,6 +77,10 @@ struct hy_adapt {
                                  {nullptr, nullptr, nullptr, nullptr}};
     bool ss_clean[2][4] = {{false, false, false, false}, {false, false, false, false}};
     bool sig_listed[2] = {false, false};   // sigma's support is listed in ss[dt][3]
+    int64_t sig_count[2] = {0, 0};         // its size at the last evaluation
+    // growth of lambda's support over the backward rotations, as last seen
+    // (the rotations list partners: each constituent can double it)
+    double lam_growth[2] = {2.0, 2.0};
     int64_t conn = 0;             // couplings per determinant (bounds sigma's support)
     // ansatz length at which a precision's support list overflowed: the
     // dense sweeps serve that precision while the ansatz is this long
@@ -182,6 +186,7 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     // sigma's values are complete either way; an overflowing list only
     // leaves its support unlisted (and its array to be cleared in full)
     a->sig_listed[d] = track && cnt[1] <= hy::sstate_cap(G);
+    a->sig_count[d] = cnt[1];
     if (track && !a->sig_listed[d]) a->ss_clean[d][3] = false;
     hy::sstate_set_hint(S, cnt[0]);
     if (a->sig_listed[d]) hy::sstate_set_hint(G, cnt[1]);
@@ -270,7 +275,9 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     HY_TRY(hy::sstate_copy(F, P, st));
     hy::sstate_set_hint(F, a->sparse_m);
     // lambda starts as sigma: a sparse copy when sigma's support is listed
-    const bool lam_sparse = a->sig_listed[d];
+    // and, grown as last seen, still fits lambda's list
+    const bool lam_sparse = a->sig_listed[d] &&
+        double(a->sig_count[d]) * a->lam_growth[d] <= double(hy::sstate_cap(L));
     if (lam_sparse) {
         HY_TRY(hy::sstate_reset(L, !a->ss_clean[d][2], false, st));
         a->ss_clean[d][2] = true;
@@ -299,7 +306,12 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
                     "support count"));
     HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
     const bool f_ok = cnt[0] <= hy::sstate_cap(F), l_ok = cnt[1] <= hy::sstate_cap(L);
-    if (lam_sparse) hy::sstate_set_hint(L, cnt[1]);
+    if (lam_sparse) {
+        hy::sstate_set_hint(L, cnt[1]);
+        a->lam_growth[d] = l_ok ? std::max(1.0, 1.25 * double(cnt[1]) /
+                                                    double(std::max<int64_t>(a->sig_count[d], 1)))
+                                : 4.0 * a->lam_growth[d];
+    }
     if (f_ok && l_ok) return HY_OK;
     if (!f_ok) a->ss_clean[d][1] = false;
     if (!l_ok) a->ss_clean[d][2] = false;
