@@ -155,6 +155,14 @@ hy_status hy_ham_info(const hy_ham *h, int64_t *n_det, int64_t *n_alpha_str,
  * waits for the last pair and returns the elapsed milliseconds (host).  Off
  * by default; the events cost nothing when off. */
 hy_status hy_ham_profile(hy_ham *h, int enable);
+
+/* Float H|psi>: phase A of the alpha-beta coupling (the dense per-string
+ * product T_J = W_J G_J) on the tensor cores (impl = 0, the default:
+ * tcgen05 TF32 MMAs with split hi/lo operands, FP32 accuracy) or on the FP32
+ * SIMT pipes (impl = 1).  Both feed the same phase B.  A bounded wait of the
+ * tensor-core kernel that runs out is returned as HY_ERR_TIMEOUT by the next
+ * hy_apply_h on this handle. */
+hy_status hy_ham_set_coupling(hy_ham *h, int impl);
 hy_status hy_ham_coupling_ms(const hy_ham *h, float *ms);
 
 /* Copy the Pauli table (host outputs, caller-allocated).  Term t is

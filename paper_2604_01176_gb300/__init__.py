@@ -149,6 +149,11 @@ class Hamiltonian:
                                     stream_ptr(stream)))
         return out
 
+    def set_coupling(self, impl: str) -> None:
+        """Float coupling phase A on the tensor cores ("tensor", default) or
+        the FP32 SIMT pipes ("simt")."""
+        check(_abi.load().hy_ham_set_coupling(self._h, {"tensor": 0, "simt": 1}[impl]))
+
     def profile_coupling(self, on: bool = True):
         """Record CUDA events around the alpha-beta coupling of later apply_h calls."""
         check(_abi.load().hy_ham_profile(self._h, 1 if on else 0))

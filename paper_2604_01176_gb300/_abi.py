@@ -82,6 +82,7 @@ SIGNATURES = {
     "hy_ham_info": (I32, [P, PI64, PI64, PI64, PI64, PI64]),
     "hy_ham_pauli_table": (I32, [P, P, P, P, P]),
     "hy_ham_profile": (I32, [P, I32]),
+    "hy_ham_set_coupling": (I32, [P, I32]),
     "hy_ham_coupling_ms": (I32, [P, P]),
     "hy_pauli_table_build": (I32, [P, P, D, I32, D, I64, P, P, P, P, PI64, PI64]),
     "hy_rank": (I32, [P, P, P, I64, P]),

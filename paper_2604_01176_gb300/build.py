@@ -17,7 +17,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhyperion.so")
 
 SOURCES = ["hy_build.cpp", "hy_api.cu", "hy_sigma.cu", "hy_sweeps.cu",
-           "hy_adapt.cpp", "hy_ranker.cu", "hy_batch.cu", "hy_sparse.cu", "hy_profile.cpp"]
+           "hy_adapt.cpp", "hy_ranker.cu", "hy_batch.cu", "hy_sparse.cu", "hy_profile.cpp",
+           "hy_cpl_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler",
                 "-fPIC,-fopenmp,-O3", "-I", INCLUDE, "-I", CSRC]

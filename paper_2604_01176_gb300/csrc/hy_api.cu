@@ -106,6 +106,10 @@ struct hy_ham {
     // optional CUDA events around the alpha-beta coupling launch(es)
     bool prof = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // float coupling phase A: 0 tensor cores (tcgen05), 1 FP32 SIMT
+    int cpl_impl = 0;
+    int *d_status = nullptr;        // device: a bounded wait of k_cpl_tc ran out
+    int *h_status = nullptr;        // pinned host mirror, copied after each launch
 };
 
 struct hy_pool {
@@ -305,7 +309,20 @@ hy_status apply_h_t(hy_ham *h, const T *psi, T *sigma, cudaStream_t st)
             d.Nb = h->Nb;
             d.Nbp = Nbp;
             if (h->prof) cudaEventRecord(h->ev0, st);
-            HY_CUDA(hy::k::coupling_dense(d, h->num_sms, st), "alpha-beta coupling (dense)");
+            bool done = false;
+            if (h->cpl_impl == 0 && h->d_status) {
+                const cudaError_t e = hy::k::coupling_tc(d, h->d_status, h->num_sms, st);
+                if (e == cudaSuccess) {
+                    HY_CUDA(hy::k::coupling_gather(d, h->num_sms, st), "alpha-beta gather");
+                    HY_CUDA(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int),
+                                            cudaMemcpyDeviceToHost, st), "status copy");
+                    done = true;
+                } else if (e != cudaErrorInvalidValue) {
+                    return cuda_fail(e, "alpha-beta coupling (tensor cores)");
+                }
+            }
+            if (!done)
+                HY_CUDA(hy::k::coupling_dense(d, h->num_sms, st), "alpha-beta coupling (dense)");
             if (h->prof) cudaEventRecord(h->ev1, st);
             return HY_OK;
         }
@@ -520,6 +537,15 @@ hy_status hy_build_hamiltonian(const double *h1, const double *h2, double e_core
         return cuda_fail(e, "device query");
     }
     h->dot_blocks = 8 * h->num_sms;
+    e = cudaMalloc(&h->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_status, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(h->d_status);
+        delete h;
+        return cuda_fail(e, "status flag");
+    }
+    *h->h_status = 0;
 
     // bexT: beta excitations transposed to [nexb][Nb] for coalesced reads
     std::vector<uint32_t> bexT(size_t(h->B.nex) * h->Nb);
@@ -580,9 +606,19 @@ hy_status hy_ham_destroy(hy_ham *h)
     if (!h) return HY_OK;
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    cudaFree(h->d_status);
+    if (h->h_status) cudaFreeHost(h->h_status);
     h->arena.release();
     if (h->ws) cudaFree(h->ws);
     delete h;
+    return HY_OK;
+}
+
+hy_status hy_ham_set_coupling(hy_ham *h, int impl)
+{
+    if (!h) return fail(HY_ERR_ARG, "handle is NULL");
+    if (impl != 0 && impl != 1) return fail(HY_ERR_ARG, "impl must be 0 (tensor cores) or 1 (SIMT)");
+    h->cpl_impl = impl;
     return HY_OK;
 }
 
@@ -674,6 +710,12 @@ hy_status hy_apply_h(const hy_ham *hc, const void *psi, void *sigma, hy_dtype dt
     hy_ham *h = const_cast<hy_ham *>(hc);
     if (!h || !psi || !sigma || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
     if (psi == sigma) return fail(HY_ERR_ARG, "psi and sigma must not alias");
+    if (h->h_status && *h->h_status) {
+        // an earlier tensor-core coupling gave up waiting: report it once
+        *h->h_status = 0;
+        HY_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), as_stream(stream)), "status reset");
+        return fail(HY_ERR_TIMEOUT, "an earlier H psi's tensor-core coupling timed out");
+    }
     if (dt == HY_F64)
         return apply_h_t<double>(h, static_cast<const double *>(psi),
                                  static_cast<double *>(sigma), as_stream(stream));

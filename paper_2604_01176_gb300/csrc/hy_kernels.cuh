@@ -66,7 +66,14 @@ struct CplDenseArgs {
     int64_t Na, Nb, Nbp;    // Nbp: row stride of T (multiple of 64)
 };
 size_t cpl_dense_smem(int64_t Nb, int n);
+// phase A (SIMT) + phase B
 cudaError_t coupling_dense(const CplDenseArgs &a, int num_sms, cudaStream_t st);
+// phase B alone: sigma[a'][b'] += the 65 rows of T that reach a'
+cudaError_t coupling_gather(const CplDenseArgs &a, int num_sms, cudaStream_t st);
+// phase A on the tensor cores (hy_cpl_tc.cu); *status (device) is set to 1
+// if a bounded wait ran out
+size_t cpl_tc_smem(int64_t Nb);
+cudaError_t coupling_tc(const CplDenseArgs &a, int *status, int num_sms, cudaStream_t st);
 
 template <typename T>
 cudaError_t spmm(const int32_t *ptr, const int32_t *col, const T *val,

@@ -556,6 +556,12 @@ cudaError_t coupling_dense(const CplDenseArgs &a, int num_sms, cudaStream_t st)
     k_cpl_gemm<<<unsigned(grid), kGThreads, smem, st>>>(a); hy::count_launch();
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
+    return coupling_gather(a, num_sms, st);
+}
+
+cudaError_t coupling_gather(const CplDenseArgs &a, int num_sms, cudaStream_t st)
+{
+    if (a.Na == 0 || a.Nb == 0) return cudaSuccess;
     int64_t g2 = int64_t(num_sms) * 8;
     if (g2 > a.Na) g2 = a.Na;
     k_cpl_gather<<<unsigned(g2), 256, 0, st>>>(a); hy::count_launch();
