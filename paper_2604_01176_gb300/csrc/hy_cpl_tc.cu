@@ -22,8 +22,9 @@
 // (8-row x 16-byte core matrices; consecutive cores along K 128 bytes apart,
 // along M/N `sbo` bytes apart).  All threads build one stage while the
 // tensor cores multiply the other; the beta excitation entries of the next
-// chunk are loaded while the current one is built.  One thread issues the
-// MMAs (M = 64, N = 128, K = 8) and commits each stage to its mbarrier.
+// chunk are loaded while the current one is built.  A warp of its own issues
+// the MMAs (M = 64, N = 128, K = 8), so its wait for the tensor cores to
+// accept them never stalls a builder, and commits each stage to its mbarrier.
 // Every wait is bounded: on a timeout the kernel records it in *status, waits
 // (bounded) for its own MMAs, frees its tensor memory and returns.
 #include "hy_kernels.cuh"
@@ -33,7 +34,11 @@ namespace k {
 
 namespace {
 
-constexpr int kTcThreads = 256;
+// warps 0-7 build G, warps 8-11 build W chunks, warp 12 issues the MMAs
+constexpr int kTcThreads = 416;
+constexpr int kGThreadsTc = 256;
+constexpr int kAWarps = 4;
+constexpr int kIssueWarp = 12;
 constexpr int kTcN = 128;          // columns per tile (MMA N)
 constexpr int kTcM = 64;           // MMA M (single-excitation slots, zero padded)
 constexpr int kTcKc = 32;          // types per chunk (two values of r)
@@ -169,12 +174,13 @@ k_cpl_tc(CplDenseArgs a, int *status)
         while (ok && waited < issued) {
             if (!wait_bar(b, waited & 1u)) {
                 ok = false;
-                if (tid == 0) atomicExch(status, 1);
+                atomicExch(status, 1);
             }
             ++waited;
         }
     };
-    const int col = tid & (kTcN - 1), half = tid >> 7;        // 2 threads per column
+    const bool gb = tid < kGThreadsTc;                        // a G builder
+    const int col = tid & (kTcN - 1), half = (tid >> 7) & 1;  // 2 G builders per column
 
     for (int64_t J = blockIdx.x; J < a.Na && ok; J += gridDim.x) {
         // W_J in FP32 for the 64 MMA rows, Wd_J for the diagonal slot and
@@ -207,21 +213,26 @@ k_cpl_tc(CplDenseArgs a, int *status)
         __syncthreads();
         for (int64_t b0 = 0; b0 < Nb && ok; b0 += kTcN) {
             const int64_t b = b0 + col;
-            const bool live = b < Nb;
+            const bool live = gb && b < Nb;
             const uint32_t bm = live ? a.bstr[b] : 0u;
             float dsum = 0.0f;
             bool first = true;
-            // beta excitation entries of this thread's r for chunk c (r = 2c +
-            // half created in b': entries f0 .. f0 + free_b - 1), loaded one
-            // chunk ahead
+            // beta excitation entries of this thread's r for chunk c, loaded
+            // one chunk ahead: u[s] is the entry of (r created in b', s empty
+            // in b') -- entry f0 + (empty orbitals below s) of b', since a
+            // string lists its excitations by created orbital, then by empty
+            // orbital, ascending -- or 0 (a packed entry is never 0: p != q)
             uint32_t un[16];
             auto load_entries = [&](int c, uint32_t *u) {
                 const int r = 2 * c + half;
                 const bool has = live && r < n && ((bm >> r) & 1u);
                 const int f0 = has ? __popc(bm & ((1u << r) - 1u)) * free_b : 0;
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    u[q] = (has && q < free_b) ? __ldg(a.bexT + size_t(f0 + q) * Nb + b) : 0u;
+                for (int s = 0; s < 16; ++s) {
+                    const bool emp = has && s < n && !((bm >> s) & 1u);
+                    const int q = s - __popc(bm & ((1u << s) - 1u));
+                    u[s] = emp ? __ldg(a.bexT + size_t(f0 + q) * Nb + b) : 0u;
+                }
             };
             load_entries(0, un);
             for (int c = 0; c < nch && ok; ++c) {
@@ -238,47 +249,56 @@ k_cpl_tc(CplDenseArgs a, int *status)
 #pragma unroll
                 for (int s = 0; s < 16; ++s) g[s] = 0.0f;
                 if (live && r < n && ((bm >> r) & 1u)) {
+                    const float diag = prow[b];           // the diagonal pair (r, r)
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        if (q >= free_b) continue;
-                        const int s = (u[q] >> 20) & 15;
-                        const float v = prow[u[q] & 0xFFFFu];
-                        g[s] = (u[q] >> 31) ? -v : v;
+                    for (int s = 0; s < 16; ++s) {
+                        float v = 0.0f;
+                        if (u[s]) {
+                            const float pv = prow[u[s] & 0xFFFFu];
+                            v = (u[s] >> 31) ? -pv : pv;
+                        } else if (s == r) {
+                            v = diag;
+                        }
+                        g[s] = v;
+                        dsum = fmaf(Wd[r * 16 + s], v, dsum);
                     }
-                    g[r] = prow[b];           // the diagonal pair (r, r)
                 }
                 unsigned char *Ah = stg + st * kStage, *Al = Ah + kABytes;
                 unsigned char *Bh = Al + kABytes, *Bl = Bh + kBBytes;
+                if (gb) {
 #pragma unroll
-                for (int s4 = 0; s4 < 4; ++s4) {
-                    float4 h, l;
-                    split(g[4 * s4 + 0], h.x, l.x);
-                    split(g[4 * s4 + 1], h.y, l.y);
-                    split(g[4 * s4 + 2], h.z, l.z);
-                    split(g[4 * s4 + 3], h.w, l.w);
-                    const uint32_t off = kmaj(col, half * 16 + 4 * s4, kSbo);
-                    *reinterpret_cast<float4 *>(Bh + off) = h;
-                    *reinterpret_cast<float4 *>(Bl + off) = l;
+                    for (int s4 = 0; s4 < 4; ++s4) {
+                        float4 h, l;
+                        split(g[4 * s4 + 0], h.x, l.x);
+                        split(g[4 * s4 + 1], h.y, l.y);
+                        split(g[4 * s4 + 2], h.z, l.z);
+                        split(g[4 * s4 + 3], h.w, l.w);
+                        const uint32_t off = kmaj(col, half * 16 + 4 * s4, kSbo);
+                        *reinterpret_cast<float4 *>(Bh + off) = h;
+                        *reinterpret_cast<float4 *>(Bl + off) = l;
+                    }
+                } else if (warp < kIssueWarp) {
+                    // this chunk's 64 x 32 block of W_J, split: a warp writes
+                    // one whole 8 x 4 core matrix (128 contiguous bytes) per step
+                    const int w4 = warp - kGThreadsTc / 32;
+#pragma unroll
+                    for (int e = 0; e < (kTcM * kTcKc) / (32 * kAWarps); ++e) {
+                        const int core = w4 + e * kAWarps;                 // 0 .. 63
+                        const int m = (core >> 3) * 8 + (lane >> 2);       // 8 cores along K per row group
+                        const int k = (core & 7) * 4 + (lane & 3);
+                        float hi, lo;
+                        split(Wf[m * kWRow + c * kTcKc + k], hi, lo);
+                        const uint32_t off = uint32_t(core) * 128u + uint32_t(lane) * 4u;
+                        *reinterpret_cast<float *>(Ah + off) = hi;
+                        *reinterpret_cast<float *>(Al + off) = lo;
+                    }
                 }
-                // this chunk's 64 x 32 block of W_J, split: a warp writes one
-                // whole 8 x 4 core matrix (128 contiguous bytes) per step
-#pragma unroll
-                for (int e = 0; e < (kTcM * kTcKc) / kTcThreads; ++e) {
-                    const int core = warp + e * (kTcThreads / 32);      // 0 .. 63
-                    const int m = (core >> 3) * 8 + (lane >> 2);        // 8 cores along K per row group
-                    const int k = (core & 7) * 4 + (lane & 3);
-                    float hi, lo;
-                    split(Wf[m * kWRow + c * kTcKc + k], hi, lo);
-                    const uint32_t off = uint32_t(core) * 128u + uint32_t(lane) * 4u;
-                    *reinterpret_cast<float *>(Ah + off) = hi;
-                    *reinterpret_cast<float *>(Al + off) = lo;
-                }
-#pragma unroll
-                for (int s = 0; s < 16; ++s) dsum = fmaf(Wd[r * 16 + s], g[s], dsum);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 ok = __syncthreads_and(ok) != 0;      // block-uniform from here
                 if (!ok) break;
-                if (tid == 0) {
+                // the issuing warp builds nothing: its wait for the tensor
+                // cores to accept the MMAs stays off the builders' path
+                if (warp == kIssueWarp && lane == 0) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t ah = saddr(Ah), al = saddr(Al), bh = saddr(Bh), bl = saddr(Bl);
 #pragma unroll
@@ -294,7 +314,7 @@ k_cpl_tc(CplDenseArgs a, int *status)
                 first = false;
                 if (st == 0) ++issued0; else ++issued1;
             }
-            dpart[half * kTcN + col] = dsum;
+            if (gb) dpart[half * kTcN + col] = dsum;
             drain(&bar[0], waited0, issued0);
             drain(&bar[1], waited1, issued1);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -320,7 +340,7 @@ k_cpl_tc(CplDenseArgs a, int *status)
                                     if (b0 + cb * 32 + i + q < Nb) dst[i + q] = v[i + q];
                     }
                 }
-            } else if (tid - 128 < kTcN) {
+            } else if (tid < 128 + kTcN) {
                 const int cc = tid - 128;
                 if (b0 + cc < Nb)
                     a.T[(J * slots + nexa) * a.Nbp + b0 + cc] = dpart[cc] + dpart[kTcN + cc];
