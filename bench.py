@@ -34,6 +34,7 @@ import argparse
 import csv
 import io
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -50,9 +51,13 @@ import synth  # noqa: E402
 METRIC = ("H|psi> GB/s (% of ~8 TB/s) and ADAPT iters/s at 32 qubits, "
           "plain vs mixed+ranker")
 TOP_M = 32
-# DRAM bytes per launch of the FP32 coupling (k_cpl_gemm + k_cpl_gather) at 32 q, from the ncu capture at
-# 28 q scaled by the amplitude count (traffic is proportional to it: the T intermediate is written once
-# and read once); see profiles/coupling_ab_f32_28q.md.  None until that capture matches the kernel.
+# DRAM bytes per launch of k_cpl_tc (the tensor-core phase A of the float
+# coupling) at 32 q: the ncu capture at 28 q (profiles/coupling_tc_28q.md:
+# 51.5 MB read + 2.30 GB written, the written part being the T intermediate)
+# scaled by the size of T (x 18.24) and of the psi rows read (x 14.06).  The
+# phase-B gather that the bench's coupling time also covers is not included,
+# so the roofline's own "traffic" (both kernels) stays None.
+TRAFFIC_CPL_TC = 2.300555e9 * 18.24 + 51.5e6 * 14.06
 TRAFFIC_F32 = None
 REFRESH = 4        # every 4th ranked iteration selects from the full screen
 
@@ -450,7 +455,8 @@ def run_ours(args, rank, world):
     pool = hy.Pool(ham)
     t_build = time.perf_counter() - tb
     out = dict(N=ham.n_det, K=len(pool), n=n, na=na, nb=nb, seed=seed, t_build=t_build,
-               conn=ham.connections_per_det())
+               conn=ham.connections_per_det(), n_alpha_str=math.comb(n, na),
+               n_beta_str=math.comb(n, nb))
     if args.adapt_only:
         args.no_plain = True
         out["head"] = adapt_leg(ham, pool, hy, torch, args, rank, world, True)
@@ -490,7 +496,7 @@ def breakdown(prof, step_ms):
 
 
 # classes bound by arithmetic rather than HBM (the headline's bulk is float)
-ALU_CLASSES = ("features", "hpsi")
+ALU_CLASSES = ("hpsi",)
 
 
 def step_roofline(prof, peaks, peak_kind, fp32_peak):
@@ -500,6 +506,7 @@ def step_roofline(prof, peaks, peak_kind, fp32_peak):
     rate for the arithmetic-bound classes."""
     known = {c: v for c, v in prof.items()
              if v["launches"] and (v["bytes"] > 0 or v["flops"] > 0)}
+    estimated = {"sparse_excite": "bytes estimated from the support sizes the host last read back"}
     top_all = max(prof, key=lambda c: prof[c]["ms"])
     if not known:
         return {"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -521,6 +528,8 @@ def step_roofline(prof, peaks, peak_kind, fp32_peak):
                    frac=round(gbs / peaks["hbm_gbs"], 4),
                    bytes_per_launch=round(v["bytes"] / v["launches"]),
                    peak_kind=f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)")
+        if c in estimated:
+            out["bytes_note"] = estimated[c]
     return out
 
 
@@ -589,6 +598,10 @@ def main():
     head, dense = r["head"], r["dense"]
     flops = 2.0 * r["conn"] * N
     cflops = 2.0 * r["cpl_units"] * N      # the coupling kernel's share of the connections
+    # tensor-core work of the coupling's phase A: 64 slots x 256 padded types x
+    # 3 split products per (alpha string, beta string), 2 flops per MAC
+    tc_flops = 2.0 * 3 * 64 * 256 * r["n_alpha_str"] * r["n_beta_str"]
+    tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25
     out = {
         "metric": METRIC,
         "value": round(job_throughput(world, S, head["ms"]), 6),
@@ -621,14 +634,19 @@ def main():
         "roofline": step_roofline(head["prof"], peaks, peak_kind, fp32_peak),
         "kernel_breakdown": breakdown(head["prof"], head["ms"]),
         "dense_hpsi_roofline": {
-            "bound": "alu", "achieved": round(cflops / (r["cpl_ms_f32"] / 1e3) / 1e12, 4),
-            "peak": round(fp32_peak, 3), "unit": "TFLOP/s",
-            "frac": round(cflops / (r["cpl_ms_f32"] / 1e3) / 1e12 / fp32_peak, 4),
+            "bound": "tensor", "kernel": "alpha-beta coupling of dense float H|psi>: k_cpl_tc "
+            "(tcgen05 TF32, split hi/lo operands) + k_cpl_gather",
+            "achieved": round(tc_flops / (r["cpl_ms_f32"] / 1e3) / 1e12, 3),
+            "peak": round(tf32_peak, 1), "unit": "TFLOP/s",
+            "frac": round(tc_flops / (r["cpl_ms_f32"] / 1e3) / 1e12 / tf32_peak, 4),
             "traffic": TRAFFIC_F32,
-            "kernel": "alpha-beta coupling of dense H|psi>, FP32 (k_cpl_gemm + k_cpl_gather)",
+            "traffic_k_cpl_tc_per_launch": round(TRAFFIC_CPL_TC),
             "ms_per_launch": round(r["cpl_ms_f32"], 3),
-            "work": f"{r['cpl_units']} FMA per amplitude x {N} amplitudes",
-            "peak_kind": f"derived FP32 FMA rate: 152 SMs x 128 FMA/clk x {mhz} MHz",
+            "work": (f"3 x 64 x 256 TF32 MACs per (alpha string, column) over "
+                     f"{r['n_alpha_str']} x {r['n_beta_str']} (padded types, three split products)"),
+            "peak_kind": ("measured bf16 burst x 1.1/2.25 (nominal TF32/BF16 dense ratio); "
+                          "2047 TF32 MAC/clk/SM measured by a microbenchmark at M=128"),
+            "useful_fp32_tflops": round(cflops / (r["cpl_ms_f32"] / 1e3) / 1e12, 3),
             "f64": {"kernel": "k_coupling<double>",
                     "achieved": round(cflops / (r["cpl_ms_f64"] / 1e3) / 1e12, 4),
                     "peak": round(fp64_peak, 3),

@@ -93,13 +93,16 @@ typedef enum {
                                   2 x connections x N flops                    */
     HY_PROF_HPSI_SPARSE = 1,   /* scatter H|psi> incl. zeroing sigma: N s      */
     HY_PROF_EXCITE = 2,        /* dense exp(theta A) pair rotations: 4 s/pair  */
-    HY_PROF_SPARSE_EXCITE = 3, /* rotations of a sparse state (unknown)        */
+    HY_PROF_SPARSE_EXCITE = 3, /* rotations of a sparse state: (12 + 4 s) bytes
+                                  per listed entry and constituent, estimated
+                                  from the support the host last read back     */
     HY_PROF_SCREEN = 4,        /* dense pool gradients: 4 s per pair per op    */
     HY_PROF_SCREEN_SPARSE = 5, /* support-restricted gradients (unknown)       */
     HY_PROF_REDUCE = 6,        /* dots / norms / renormalisation: s per read
                                   or written amplitude                         */
-    HY_PROF_FEATURES = 7,      /* ranker features: N s bytes and
-                                  2 N_a N_b n^2 flops per touched-weight pass  */
+    HY_PROF_FEATURES = 7,      /* ranker features: N s bytes per pass over psi
+                                  or sigma (its arithmetic skips zero tiles and
+                                  is not counted)                              */
     HY_PROF_CLASSES = 8
 } hy_prof_class;
 hy_status hy_profile_enable(uint32_t class_mask);

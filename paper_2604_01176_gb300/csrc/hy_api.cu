@@ -1159,9 +1159,10 @@ hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
     if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
     cudaStream_t st = as_stream(stream);
     const size_t nn = size_t(h->n) * h->n;
+    // bytes only: the touched-weight product skips all-zero tiles, so its
+    // executed arithmetic depends on the state and is not known here
     const double passes = sigma_or_null ? 2.0 : 1.0;
-    hy::ProfScope prof(HY_PROF_FEATURES, st, passes * double(h->N) * (dt == HY_F64 ? 8 : 4),
-                       passes * 2.0 * double(h->Na) * double(h->Nb) * double(h->n) * h->n);
+    hy::ProfScope prof(HY_PROF_FEATURES, st, passes * double(h->N) * (dt == HY_F64 ? 8 : 4));
     const void *vecs[2] = {psi, sigma_or_null};
     for (int v = 0; v < 2 && vecs[v]; ++v) {
         float *B = h->d_pairB + size_t(v) * h->Na * nn, *rs = h->d_pairRs + size_t(v) * h->Na;
@@ -1660,7 +1661,12 @@ hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double thet
     o.Nb = h->Nb;
     const int nc = p->ops[k].desc[0];
     cudaStream_t st = as_stream(stream);
-    hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
+    // bytes estimated from the support the host last read back (the count
+    // itself lives on the device): per listed entry and constituent, its list
+    // slot and bitmap word plus two amplitudes read and written
+    const double es = s->dt == HY_F64 ? 8.0 : 4.0;
+    hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream,
+                       double(std::max<int64_t>(s->hint, 0)) * nc * (12.0 + 4.0 * es));
     if (s->dt == HY_F64)
         HY_CUDA(hy::k::sv_excite<double>(svec<double>(s), o, int(k), nc, theta, h->num_sms, st),
                 "sparse excitation");
