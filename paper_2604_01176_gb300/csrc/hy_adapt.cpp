@@ -88,6 +88,7 @@ struct hy_adapt {
     int64_t sparse_m = -1;        // support of the last evaluated state (-1: dense)
     int64_t sparse_m_last[2] = {1, 1};   // last sparse support of each precision
     double *d_n2 = nullptr;       // tracked squared norm (float renormalisation)
+    double *h_cs = nullptr, *d_cs = nullptr;   // cos, sin of the ansatz angles (pinned / device)
     double *d_one = nullptr;      // device constants {1.0, 1.0f}
 };
 
@@ -138,6 +139,11 @@ hy_status finish_energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt)
     return HY_OK;
 }
 
+// last support up to which one CTA prepares the sparse state (its 1,024
+// threads then take at most a few dozen entries each per rotation, even
+// after a new operator quadruples the support)
+const int64_t kPrepareSmall = 4096;
+
 // The sparse evaluation: psi = U(theta)|HF> as a sparse vector (rotations
 // cost O(support)), renormalised over its support in double (float states),
 // sigma = H psi by the scatter, E = <psi|sigma> over the support.  *ok =
@@ -148,13 +154,28 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     const int d = di(dt);
     hy::SparseState *S = a->ss[d][0], *G = a->ss[d][3];
     void *psi = a->buf[d][0], *sigma = a->buf[d][1];
-    HY_TRY(hy::sstate_reset(S, !a->ss_clean[d][0], true, st));
-    a->ss_clean[d][0] = true;
-    for (size_t l = 0; l < a->ops.size(); ++l)
-        HY_TRY(hy::sstate_excite(S, a->p, a->ops[l], th[l], st));
-    if (dt == HY_F32 && !a->ops.empty()) {
-        HY_TRY(hy::sstate_dot(S, psi, a->d_n2, st));
-        HY_TRY(hy::sstate_scale_rsqrt(S, a->d_n2, st));
+    const size_t L = a->ops.size();
+    if (a->sparse_m_last[d] <= kPrepareSmall) {
+        // small support: the whole preparation in one launch
+        if (!a->ss_clean[d][0]) HY_TRY(hy::sstate_reset(S, true, false, st));
+        a->ss_clean[d][0] = true;
+        for (size_t l = 0; l < L; ++l) {
+            a->h_cs[2 * l] = std::cos(th[l]);
+            a->h_cs[2 * l + 1] = std::sin(th[l]);
+        }
+        if (L) HY_TRY(xfer(a, a->d_cs, a->h_cs, L * 2 * sizeof(double), cudaMemcpyHostToDevice, st,
+                           "angles"));
+        HY_TRY(hy::sstate_prepare(S, a->p, a->d_ops, a->d_cs, int64_t(L), dt == HY_F32 && L > 0,
+                                  a->d_n2, st));
+    } else {
+        HY_TRY(hy::sstate_reset(S, !a->ss_clean[d][0], true, st));
+        a->ss_clean[d][0] = true;
+        for (size_t l = 0; l < L; ++l)
+            HY_TRY(hy::sstate_excite(S, a->p, a->ops[l], th[l], st));
+        if (dt == HY_F32 && L > 0) {
+            HY_TRY(hy::sstate_dot(S, psi, a->d_n2, st));
+            HY_TRY(hy::sstate_scale_rsqrt(S, a->d_n2, st));
+        }
     }
     // list sigma's support while the last support times the couplings (an
     // upper bound) fits its list; a list that still overflows (the support
@@ -386,6 +407,7 @@ const double kStall64 = std::ldexp(1.0, -50);
 // ranker's feature pass at 32 qubits)
 const double kExactScreenWork = 5e9;
 
+
 // BFGS with backtracking (Armijo) line search on E(theta) in dt, starting
 // from a->theta and a->hinv; updates both.  *e_out = final energy.  With
 // stall > 0 the run also stops after an accepted step whose decrease is
@@ -538,6 +560,8 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
         alloc(reinterpret_cast<void **>(&a->d_gp), size_t(a->K) * 8);
     }
     alloc(reinterpret_cast<void **>(&a->d_n2), 8);
+    alloc(reinterpret_cast<void **>(&a->d_cs), size_t(c.max_iter) * 16);
+    if (s == HY_OK) s = cu(cudaMallocHost(&a->h_cs, size_t(c.max_iter) * 16), "pinned angles");
     alloc(reinterpret_cast<void **>(&a->d_one), 16);
     if (s == HY_OK) {
         unsigned char one[16] = {};
@@ -594,6 +618,8 @@ hy_status hy_adapt_destroy(hy_adapt *a)
     cudaFree(a->d_score);
     cudaFree(a->d_gp);
     cudaFree(a->d_n2);
+    cudaFree(a->d_cs);
+    if (a->h_cs) cudaFreeHost(a->h_cs);
     cudaFree(a->d_one);
     for (auto &row : a->ss)
         for (hy::SparseState *&x : row) hy::sstate_destroy(x);

@@ -1676,6 +1676,30 @@ hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double thet
     return HY_OK;
 }
 
+hy_status sstate_prepare(SparseState *s, const hy_pool *p, const int32_t *ops, const double *cs,
+                         int64_t L, bool renorm, double *norm2, void *stream)
+{
+    const hy_ham *h = s->h;
+    if (!p || p->h != h || (L > 0 && (!ops || !cs)) || L < 0 || L > (1 << 20))
+        return fail(HY_ERR_ARG, "bad arguments");
+    hy::k::SvOpArgs o;
+    o.desc = p->d_desc;
+    o.astr = h->d_astr;
+    o.bstr = h->d_bstr;
+    o.binom33 = h->d_binom;
+    o.n = h->n;
+    o.Nb = h->Nb;
+    cudaStream_t st = as_stream(stream);
+    hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
+    if (s->dt == HY_F64)
+        HY_CUDA(hy::k::sv_prepare<double>(svec<double>(s), o, ops, cs, int(L), renorm, norm2, st),
+                "sparse preparation");
+    else
+        HY_CUDA(hy::k::sv_prepare<float>(svec<float>(s), o, ops, cs, int(L), renorm, norm2, st),
+                "sparse preparation");
+    return HY_OK;
+}
+
 hy_status sstate_dot(const SparseState *s, const void *y, double *out, void *stream)
 {
     cudaStream_t st = as_stream(stream);

@@ -151,6 +151,12 @@ hy_status sstate_copy(SparseState *dst, const SparseState *src, void *stream);
 // host estimate of the count, used only to size grids
 void sstate_set_hint(SparseState *s, int64_t n);
 hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double theta, void *stream);
+// In one CTA: clear the support, |HF>, the rotations of ops[0..L) (device)
+// with cs[2l], cs[2l+1] (device) = cos, sin theta_l, then (renorm) divide by
+// the FP64 norm over the support.  For small supports (one launch instead of
+// two per constituent); the state must be clean.
+hy_status sstate_prepare(SparseState *s, const hy_pool *p, const int32_t *ops, const double *cs,
+                         int64_t L, bool renorm, double *norm2, void *stream);
 // *out (device) = sum over the support of v * y (y dense, same dtype), FP64
 hy_status sstate_dot(const SparseState *s, const void *y, double *out, void *stream);
 // v <- v / sqrt(*norm2) on the support (norm2 on the device)

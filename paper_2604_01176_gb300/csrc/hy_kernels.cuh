@@ -270,6 +270,12 @@ cudaError_t sv_copy(const SVec<T> &dst, const SVec<T> &src, int num_sms, cudaStr
 template <typename T>
 cudaError_t sv_excite(const SVec<T> &x, const SvOpArgs &o, int k, int nc, double theta,
                       int num_sms, cudaStream_t st);
+// one CTA: clear x's support, |HF>, every constituent rotation of ops[0..L)
+// with cs[2l], cs[2l+1] = cos, sin theta_l, then (renorm) divide by the FP64
+// norm over the support (written to *norm2 if not null); for small supports
+template <typename T>
+cudaError_t sv_prepare(const SVec<T> &x, const SvOpArgs &o, const int32_t *ops, const double *cs,
+                       int L, bool renorm, double *norm2, cudaStream_t st);
 // sum over the support of x.v * y (y dense), in FP64, into *out (partials:
 // 4 * num_sms doubles); scale: x.v <- x.v / sqrt(*norm2) on the support
 template <typename T>

@@ -356,6 +356,108 @@ k_sv_excite(SVec<T> x, SvOpArgs o, int k, int ci, T c, T s)
     }
 }
 
+// The whole state preparation of a small support in one CTA: clear the
+// previous support, set |HF>, apply every constituent rotation of the
+// ansatz in order (a block barrier between rotations takes the place of the
+// launch boundary and of the count snapshot), and for float states divide
+// by the FP64 norm over the support.  cs[2l], cs[2l+1] = cos, sin theta_l.
+constexpr int kPrepThreads = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(kPrepThreads)
+k_sv_prepare(SVec<T> x, SvOpArgs o, const int32_t *__restrict__ ops,
+             const double *__restrict__ cs, int L, int renorm, double *__restrict__ norm2)
+{
+    __shared__ uint32_t C[33][33];
+    __shared__ unsigned long long m_sh;
+    __shared__ double red[kPrepThreads / 32];
+    __shared__ double fac;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
+    // clear the previous support (all its bits belong to listed entries)
+    {
+        const int64_t m = list_len(x.count, 0, x.cap);
+        for (int64_t t = tid; t < m; t += blockDim.x) {
+            const int64_t i = x.list[t];
+            x.v[i] = T(0);
+            x.bits[i >> 5] = 0u;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        x.v[0] = T(1);
+        x.bits[0] = 1u;
+        x.list[0] = 0;
+        *x.count = 1ull;
+    }
+    const int n = o.n;
+    const uint64_t lowm = (1ull << n) - 1;
+    for (int l = 0; l < L; ++l) {
+        const int k = ops[l];
+        const int nc = o.desc[11 * k];
+        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
+        for (int ci = 0; ci < nc; ++ci) {
+            __syncthreads();                        // previous rotation complete
+            if (tid == 0) m_sh = *x.count;
+            __syncthreads();
+            const int64_t m = m_sh < (unsigned long long)x.cap ? int64_t(m_sh) : x.cap;
+            int fw[4], bw[4], len;
+            op_strings(o.desc + 11 * k + 1 + 5 * ci, fw, bw, len);
+            for (int64_t t = tid; t < m; t += blockDim.x) {
+                const int64_t d = x.list[t];
+                const uint64_t mask = uint64_t(o.astr[d / o.Nb]) | (uint64_t(o.bstr[d % o.Nb]) << n);
+                uint64_t u = mask;
+                int sg = 1;
+                int64_t dom, img, fresh;
+                if (apply_string(fw, len, u, sg)) {
+                    dom = d;
+                    img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
+                          rank_bits(uint32_t(u >> n), C);
+                    fresh = member(x.bits, img) ? -1 : img;
+                } else {
+                    u = mask;
+                    sg = 1;
+                    if (!apply_string(bw, len, u, sg)) continue;
+                    img = d;
+                    dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
+                          rank_bits(uint32_t(u >> n), C);
+                    if (member(x.bits, dom)) continue;
+                    fresh = dom;
+                }
+                const T ss = sg > 0 ? sn : -sn;
+                const T xv = x.v[dom], yv = x.v[img];
+                x.v[dom] = c * xv - ss * yv;
+                x.v[img] = c * yv + ss * xv;
+                if (fresh >= 0) {
+                    atomicOr(x.bits + (fresh >> 5), 1u << (fresh & 31));
+                    const unsigned long long pos = atomicAdd(x.count, 1ull);
+                    if (pos < (unsigned long long)x.cap) x.list[pos] = fresh;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (!renorm) return;
+    const int64_t m = list_len(x.count, 0, x.cap);
+    double acc = 0.0;
+    for (int64_t t = tid; t < m; t += blockDim.x) {
+        const double v = double(x.v[x.list[t]]);
+        acc = fma(v, v, acc);
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kPrepThreads / 32; ++w) sum += red[w];
+        if (norm2) *norm2 = sum;
+        fac = 1.0 / sqrt(sum);
+    }
+    __syncthreads();
+    const T f = T(fac);
+    for (int64_t t = tid; t < m; t += blockDim.x) x.v[x.list[t]] *= f;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_sv_dot_partial(SVec<T> x, const T *__restrict__ y, double *__restrict__ partials)
@@ -438,6 +540,15 @@ cudaError_t sv_excite(const SVec<T> &x, const SvOpArgs &o, int k, int nc, double
 }
 
 template <typename T>
+cudaError_t sv_prepare(const SVec<T> &x, const SvOpArgs &o, const int32_t *ops, const double *cs,
+                       int L, bool renorm, double *norm2, cudaStream_t st)
+{
+    k_sv_prepare<T><<<1, kPrepThreads, 0, st>>>(x, o, ops, cs, L, renorm ? 1 : 0, norm2);
+    hy::count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t sv_dot(const SVec<T> &x, const T *y, double *partials, double *out, int num_sms,
                    cudaStream_t st)
 {
@@ -507,6 +618,8 @@ template cudaError_t grad_sparse<float>(const SparseGradArgs<float> &, int, cuda
     template cudaError_t sv_copy<T>(const SVec<T> &, const SVec<T> &, int, cudaStream_t);   \
     template cudaError_t sv_excite<T>(const SVec<T> &, const SvOpArgs &, int, int, double,  \
                                       int, cudaStream_t);                                    \
+    template cudaError_t sv_prepare<T>(const SVec<T> &, const SvOpArgs &, const int32_t *,  \
+                                       const double *, int, bool, double *, cudaStream_t);  \
     template cudaError_t sv_dot<T>(const SVec<T> &, const T *, double *, double *, int,     \
                                    cudaStream_t);                                            \
     template cudaError_t sv_scale_rsqrt<T>(const SVec<T> &, const double *, int, cudaStream_t);
