@@ -479,7 +479,7 @@ CLASS_KERNELS = {
     "hpsi": "k_spmm + k_transpose + k_add_transposed + coupling (dense H|psi>)",
     "hpsi_sparse": "sigma memset + k_hpsi_scatter (scatter H|psi>)",
     "excite": "k_excite / k_excite_n (dense pair rotations: 4 s bytes per pair)",
-    "sparse_excite": "k_sv_snap + k_sv_excite (sparse-state rotations)",
+    "sparse_excite": "k_sv_excite, k_sv_prepare (sparse-state rotations)",
     "screen": "k_grad_partial + k_grad_final (dense pool gradients)",
     "screen_sparse": "k_grad_sparse + k_grad_sparse_final (support-restricted gradients)",
     "reduce": "dots, norms, renormalisation",

@@ -1540,7 +1540,7 @@ struct hy::SparseState {
     int64_t cap = 0, words = 0;
     int64_t *list = nullptr;
     uint32_t *bits = nullptr;
-    unsigned long long *cnt = nullptr;   // [count, snapshot]
+    unsigned long long *cnt = nullptr;   // [count, snapshot, finished blocks, pad]
     double *partials = nullptr;
     int64_t n_partials = 0;
     int64_t hint = 0;                    // host estimate of the count (grids)
@@ -1556,6 +1556,7 @@ hy::k::SVec<T> svec(const hy::SparseState *s)
     x.bits = s->bits;
     x.count = s->cnt;
     x.snap = s->cnt + 1;
+    x.done = s->cnt + 2;
     x.cap = s->cap;
     x.hint = s->hint;
     return x;
@@ -1590,8 +1591,8 @@ hy_status sstate_create(const hy_ham *h, hy_dtype dt, void *v, int64_t cap, Spar
     s->words = (h->N + 31) / 32;
     cudaError_t e = cudaMalloc(&s->list, size_t(cap) * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc(&s->bits, size_t(s->words) * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&s->cnt, 2 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(s->cnt, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&s->cnt, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(s->cnt, 0, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(s->bits, 0, size_t(s->words) * sizeof(uint32_t));
     if (e == cudaSuccess) {
         s->n_partials = int64_t(8) * h->num_sms;
@@ -1622,7 +1623,7 @@ hy_status sstate_reset(SparseState *s, bool full, bool hf, void *stream)
     if (full) {
         HY_CUDA(cudaMemsetAsync(s->v, 0, size_t(h->N) * (s->dt == HY_F64 ? 8 : 4), st), "memset");
         HY_CUDA(cudaMemsetAsync(s->bits, 0, size_t(s->words) * sizeof(uint32_t), st), "memset");
-        HY_CUDA(cudaMemsetAsync(s->cnt, 0, 2 * sizeof(unsigned long long), st), "memset");
+        HY_CUDA(cudaMemsetAsync(s->cnt, 0, 4 * sizeof(unsigned long long), st), "memset");
     }
     if (s->dt == HY_F64)
         HY_CUDA(hy::k::sv_reset<double>(svec<double>(s), hf, h->num_sms, st), "sparse reset");

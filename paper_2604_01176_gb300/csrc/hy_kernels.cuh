@@ -250,6 +250,7 @@ struct SVec {
     uint32_t *bits;
     unsigned long long *count;   // device: live count
     unsigned long long *snap;    // device: count at the start of a rotation
+    unsigned long long *done;    // device: blocks of the current rotation finished
     int64_t cap;
     int64_t hint;                // host estimate of the count (grid size only)
 };

@@ -284,6 +284,8 @@ __global__ void k_sv_finish_reset(SVec<T> x, int hf)
         x.list[0] = 0;
     }
     *x.count = hf ? 1ull : 0ull;
+    *x.snap = *x.count;
+    *x.done = 0ull;
 }
 
 template <typename T>
@@ -298,28 +300,18 @@ k_sv_copy(SVec<T> dst, SVec<T> src)
         dst.list[t] = i;
         atomicOr(dst.bits + (i >> 5), 1u << (i & 31));
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *dst.count = *src.count;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *dst.count = *src.count;
+        *dst.snap = *src.count;
+        *dst.done = 0ull;
+    }
 }
 
-__global__ void k_sv_snap(unsigned long long *snap, const unsigned long long *count)
-{
-    *snap = *count;
-}
-
-// One constituent C of operator k: every pair (d, C d) with a listed end is
-// rotated by its processor -- the domain end if listed, else the image end --
-// and the other end is listed if it was not.  Pairs of one constituent are
-// disjoint, so the rotation is race-free; entries appended here (positions >=
-// the snapshot) are not visited again.
+// the rotation loop of k_sv_excite over this block's share of entries < m
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_sv_excite(SVec<T> x, SvOpArgs o, int k, int ci, T c, T s)
+__device__ __forceinline__ void sv_rotate(SVec<T> &x, const SvOpArgs &o, int k, int ci, T c, T s,
+                                          int64_t m, const uint32_t (*C)[33])
 {
-    const int64_t m = list_len(x.snap, 0, x.cap);
-    if (int64_t(blockIdx.x) * blockDim.x >= m) return;    // whole block idle
-    __shared__ uint32_t C[33][33];
-    for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
-    __syncthreads();
     int fw[4], bw[4], len;
     op_strings(o.desc + 11 * k + 1 + 5 * ci, fw, bw, len);
     const int n = o.n;
@@ -355,6 +347,36 @@ k_sv_excite(SVec<T> x, SvOpArgs o, int k, int ci, T c, T s)
         }
     }
 }
+
+// One constituent C of operator k: every pair (d, C d) with a listed end is
+// rotated by its processor -- the domain end if listed, else the image end --
+// and the other end is listed if it was not.  Pairs of one constituent are
+// disjoint, so the rotation is race-free; entries appended here (positions >=
+// the snapshot) are not visited again.  The last block to finish copies the
+// final count into the snapshot for the next rotation.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_sv_excite(SVec<T> x, SvOpArgs o, int k, int ci, T c, T s)
+{
+    const int64_t m = list_len(x.snap, 0, x.cap);
+    const bool idle = int64_t(blockIdx.x) * blockDim.x >= m;     // block-uniform
+    __shared__ uint32_t C[33][33];
+    if (!idle) {
+        for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
+        __syncthreads();
+        sv_rotate(x, o, k, ci, c, s, m, C);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(x.done, 1ull) == gridDim.x - 1) {
+            __threadfence();
+            *x.snap = atomicAdd(x.count, 0ull);
+            *x.done = 0ull;
+        }
+    }
+}
+
 
 // The whole state preparation of a small support in one CTA: clear the
 // previous support, set |HF>, apply every constituent rotation of the
@@ -437,6 +459,10 @@ k_sv_prepare(SVec<T> x, SvOpArgs o, const int32_t *__restrict__ ops,
         }
     }
     __syncthreads();
+    if (tid == 0) {                 // leave the snapshot consistent for later rotations
+        *x.snap = *x.count;
+        *x.done = 0ull;
+    }
     if (!renorm) return;
     const int64_t m = list_len(x.count, 0, x.cap);
     double acc = 0.0;
@@ -532,7 +558,6 @@ cudaError_t sv_excite(const SVec<T> &x, const SvOpArgs &o, int k, int nc, double
 {
     const T c = T(std::cos(theta)), s = T(std::sin(theta));
     for (int ci = 0; ci < nc; ++ci) {
-        k_sv_snap<<<1, 1, 0, st>>>(x.snap, x.count); hy::count_launch();
         k_sv_excite<T><<<sv_grid(sv_n(x), num_sms), 256, 0, st>>>(x, o, k, ci, c, s);
         hy::count_launch();
     }
