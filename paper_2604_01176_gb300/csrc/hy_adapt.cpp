@@ -439,10 +439,14 @@ hy_status bfgs(hy_adapt *a, hy_dtype dt, double gtol, int max_steps, cudaStream_
             a->hinv_fresh = true;
         }
         double alpha = 1.0, en = 0.0;
-        bool ok = false;
+        bool ok = false, tried = false;
         for (int ls = 0; ls < 40; ++ls) {
+            // a step whose predicted decrease is below the precision's
+            // rounding floor cannot be told apart from noise: stop trying
+            if (stall > 0.0 && -alpha * slope < stall * std::fabs(e)) break;
             for (size_t r = 0; r < j; ++r) xn[r] = x[r] + alpha * pdir[r];
             HY_TRY(energy(a, xn, dt, st, &en));
+            tried = true;
             if (en <= e + 1e-4 * alpha * slope) {
                 ok = true;
                 break;
@@ -450,8 +454,9 @@ hy_status bfgs(hy_adapt *a, hy_dtype dt, double gtol, int max_steps, cudaStream_
             alpha *= 0.5;
         }
         if (!ok) {
-            // no decrease representable in this precision: keep x
-            HY_TRY(energy(a, x, dt, st, &e));
+            // no decrease representable in this precision: keep x (the
+            // buffers hold x's state unless a trial point was evaluated)
+            if (tried) HY_TRY(energy(a, x, dt, st, &e));
             break;
         }
         HY_TRY(gradient(a, xn, dt, st, gn));
