@@ -98,6 +98,7 @@ struct hy_ham {
     float *d_pairRs = nullptr;                  // [2][Na]
     float *d_pairD = nullptr;                   // [2][n^4] touched weights (psi, sigma)
     float *d_pairP = nullptr;                   // [splits][n^4] contraction partials
+    int32_t *d_pairRows = nullptr;              // [Na + 1] nonzero alpha rows
     int occ_blocks = 0;
     // workspace (grown on demand; growth synchronises the device)
     void *ws = nullptr;
@@ -586,6 +587,8 @@ hy_status hy_build_hamiltonian(const double *h1, const double *h2, double e_core
         up(ar.upload(&h->d_pairD, zd.data(), zd.size()), "touched weights");
         std::vector<float> zq(size_t(hy::k::pair_splits()) * nn * nn, 0.0f);
         up(ar.upload(&h->d_pairP, zq.data(), zq.size()), "touched-weight partials");
+        std::vector<int32_t> zrow(size_t(h->Na) + 1, 0);
+        up(ar.upload(&h->d_pairRows, zrow.data(), zrow.size()), "touched-weight rows");
     }
     if (s == HY_OK) s = upload_csr<double>(ar, h->kt.Ma, h->Ma64);
     if (s == HY_OK) s = upload_csr<double>(ar, h->kt.Mb, h->Mb64);
@@ -1170,22 +1173,17 @@ hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
         if (dt == HY_F64)
             HY_CUDA(hy::k::touched_weights<double>(static_cast<const double *>(vecs[v]), h->Na,
                                                    h->Nb, h->d_astr, h->d_bstr, h->n, B, rs,
-                                                   h->d_pairP, D, h->num_sms, st),
+                                                   h->d_pairRows, h->d_pairP, D, h->num_sms, st),
                     "touched weights");
         else
             HY_CUDA(hy::k::touched_weights<float>(static_cast<const float *>(vecs[v]), h->Na,
                                                   h->Nb, h->d_astr, h->d_bstr, h->n, B, rs,
-                                                  h->d_pairP, D, h->num_sms, st),
+                                                  h->d_pairRows, h->d_pairP, D, h->num_sms, st),
                     "touched weights");
     }
-    if (dt == HY_F64)
-        HY_CUDA(hy::k::occupations<double>(static_cast<const double *>(psi), h->Na, h->Nb,
-                                           h->d_astr, h->d_bstr, h->n, h->d_occ_partial,
-                                           h->occ_blocks, h->d_occ, st), "occupations");
-    else
-        HY_CUDA(hy::k::occupations<float>(static_cast<const float *>(psi), h->Na, h->Nb,
-                                          h->d_astr, h->d_bstr, h->n, h->d_occ_partial,
-                                          h->occ_blocks, h->d_occ, st), "occupations");
+    // occupations from psi's touched-weight partials: no further pass over psi
+    HY_CUDA(hy::k::occupations_from_weights(h->d_pairB, h->d_pairRs, h->d_astr, h->Na, h->n,
+                                            h->d_occ, st), "occupations");
     const float *Dp = sigma_or_null ? h->d_pairD : nullptr;
     const float *Ds = sigma_or_null ? h->d_pairD + nn * nn : nullptr;
     HY_CUDA(hy::k::features(p->d_desc, int64_t(p->ops.size()), h->n, h->d_h1, h->d_eri,
@@ -1201,12 +1199,14 @@ hy_status hy_touched_weights(const hy_ham *h, const void *psi, hy_dtype dt, floa
     if (dt == HY_F64)
         HY_CUDA(hy::k::touched_weights<double>(static_cast<const double *>(psi), h->Na, h->Nb,
                                                h->d_astr, h->d_bstr, h->n, h->d_pairB,
-                                               h->d_pairRs, h->d_pairP, D, h->num_sms, st),
+                                               h->d_pairRs, h->d_pairRows, h->d_pairP, D,
+                                               h->num_sms, st),
                 "touched weights");
     else
         HY_CUDA(hy::k::touched_weights<float>(static_cast<const float *>(psi), h->Na, h->Nb,
                                               h->d_astr, h->d_bstr, h->n, h->d_pairB,
-                                              h->d_pairRs, h->d_pairP, D, h->num_sms, st),
+                                              h->d_pairRs, h->d_pairRows, h->d_pairP, D,
+                                              h->num_sms, st),
                 "touched weights");
     return HY_OK;
 }

@@ -182,15 +182,18 @@ template <typename T>
 cudaError_t occupations(const T *psi, int64_t Na, int64_t Nb, const uint32_t *astr,
                         const uint32_t *bstr, int n, double *partial, int G, float *out,
                         cudaStream_t st);
+// the same occupations from psi's touched-weight partials (no pass over psi)
+cudaError_t occupations_from_weights(const float *Bw, const float *rs, const uint32_t *astr,
+                                     int64_t Na, int n, float *out, cudaStream_t st);
 cudaError_t features(const int32_t *desc, int64_t K, int n, const double *h1,
                      const double *eri, const float *occ, const float *extra, const float *Dpsi,
                      const float *Dsig, float *feat, cudaStream_t st);
-// part: pair_splits() x n^4 floats of scratch
+// part: pair_splits() x n^4 floats of scratch; rows: Na + 1 ints of scratch
 int pair_splits();
 template <typename T>
 cudaError_t touched_weights(const T *psi, int64_t Na, int64_t Nb, const uint32_t *astr,
-                            const uint32_t *bstr, int n, float *Bw, float *rs, float *part,
-                            float *D, int num_sms, cudaStream_t st);
+                            const uint32_t *bstr, int n, float *Bw, float *rs, int32_t *rows,
+                            float *part, float *D, int num_sms, cudaStream_t st);
 
 // sparse-state path (hy_sparse.cu)
 template <typename T>

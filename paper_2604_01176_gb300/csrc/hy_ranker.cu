@@ -82,6 +82,42 @@ __global__ void k_occ_final(const double *__restrict__ partial, int G, int n,
     else if (i >= 16 && i < 16 + n) out[n + (i - 16)] = float(sums[i] / norm);
 }
 
+// The same occupations from the touched-weight partials of psi (Bw, rs of
+// touched_weights), without another pass over the state: the beta
+// occupation of r is sum_a Bw[a][r*n+r], the alpha occupation of p is
+// sum_{a holding p} rs[a], the norm sum_a rs[a].  One warp per sum, fixed order.
+__global__ void __launch_bounds__(1024)
+k_occ_from_weights(const float *__restrict__ Bw, const float *__restrict__ rs,
+                   const uint32_t *__restrict__ astr, int64_t Na, int n, float *__restrict__ out)
+{
+    __shared__ double sums[33];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nn = n * n;
+    for (int i = warp; i < 33; i += blockDim.x >> 5) {
+        double acc = 0.0;
+        if (i == 32 || (i < 16 && i < n) || (i >= 16 && i - 16 < n))
+            for (int64_t a = lane; a < Na; a += 32) {
+                if (i == 32) acc += double(rs[a]);
+                else if (i < 16) acc += ((astr[a] >> i) & 1u) ? double(rs[a]) : 0.0;
+                else acc += double(Bw[a * nn + (i - 16) * n + (i - 16)]);
+            }
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+        if (lane == 0) sums[i] = acc;
+    }
+    __syncthreads();
+    const int i = threadIdx.x;
+    if (i >= 33) return;
+    const double norm = sums[32] > 0.0 ? sums[32] : 1.0;
+    if (i < n) out[i] = float(sums[i] / norm);
+    else if (i >= 16 && i < 16 + n) out[n + (i - 16)] = float(sums[i] / norm);
+}
+
+cudaError_t occupations_from_weights(const float *Bw, const float *rs, const uint32_t *astr,
+                                     int64_t Na, int n, float *out, cudaStream_t st)
+{
+    k_occ_from_weights<<<1, 1024, 0, st>>>(Bw, rs, astr, Na, n, out); hy::count_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t occupations(const T *psi, int64_t Na, int64_t Nb, const uint32_t *astr,
                         const uint32_t *bstr, int n, double *partial, int G, float *out,
@@ -184,22 +220,58 @@ constexpr int kPairSplits = 16;
 
 __global__ void __launch_bounds__(256)
 k_pair_contract(const float *__restrict__ Bw, const float *__restrict__ rs,
-                const uint32_t *__restrict__ astr, int64_t Na, int n, float *__restrict__ part)
+                const uint32_t *__restrict__ astr, const int32_t *__restrict__ rows,
+                int n, float *__restrict__ part)
 {
     const int nn = n * n;
     const int ia = blockIdx.x, jb = threadIdx.x;
     const int i = ia / n, aa = ia % n;
     const int j = jb < nn ? jb / n : 0, b = jb < nn ? jb % n : 0;
+    const int nrows = rows[0];
     float acc = 0.0f;
     if (jb < nn) {
-        for (int64_t al = blockIdx.y; al < Na; al += gridDim.y) {
+        for (int t = blockIdx.y; t < nrows; t += gridDim.y) {
+            const int64_t al = rows[1 + t];
             const uint32_t m = astr[al];
             if (i != aa && !(((m >> i) & 1u) && !((m >> aa) & 1u))) continue;
-            if (rs[al] == 0.0f) continue;     // an all-zero row adds nothing
             acc += (j == b) ? rs[al] : (Bw[al * nn + j * n + j] - Bw[al * nn + jb]);
         }
         part[int64_t(blockIdx.y) * nn * nn + int64_t(ia) * nn + jb] = acc;
     }
+}
+
+// rows[0] = number of alpha rows with nonzero weight, rows[1..] = those rows
+// in ascending order (one block: per-thread counts, block scan, write), so
+// the contraction skips the all-zero rows of a sparse state
+__global__ void __launch_bounds__(1024)
+k_pair_rows(const float *__restrict__ rs, int64_t Na, int32_t *__restrict__ rows)
+{
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t per = (Na + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = tid * per, hi = lo + per < Na ? lo + per : Na;
+    int cnt = 0;
+    for (int64_t a = lo; a < hi; ++a) cnt += rs[a] != 0.0f;
+    int incl = cnt;                              // inclusive scan within the warp
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < int(blockDim.x >> 5) ? wsum[lane] : 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += u;
+        }
+        wsum[lane] = v;                          // inclusive warp totals
+    }
+    __syncthreads();
+    int pos = incl - cnt + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int64_t a = lo; a < hi; ++a)
+        if (rs[a] != 0.0f) rows[1 + pos++] = int32_t(a);
+    if (tid == blockDim.x - 1) rows[0] = pos;
 }
 
 __global__ void __launch_bounds__(256)
@@ -216,15 +288,16 @@ int pair_splits() { return kPairSplits; }
 
 template <typename T>
 cudaError_t touched_weights(const T *psi, int64_t Na, int64_t Nb, const uint32_t *astr,
-                            const uint32_t *bstr, int n, float *Bw, float *rs, float *part,
-                            float *D, int num_sms, cudaStream_t st)
+                            const uint32_t *bstr, int n, float *Bw, float *rs, int32_t *rows,
+                            float *part, float *D, int num_sms, cudaStream_t st)
 {
     int64_t g = (Na + kPwRows - 1) / kPwRows;
     if (g > int64_t(num_sms) * 16) g = int64_t(num_sms) * 16;
     k_pair_weights<T><<<unsigned(g), kPwThreads, 0, st>>>(psi, Na, Nb, bstr, n, Bw, rs);
     hy::count_launch();
     const int nn = n * n;
-    k_pair_contract<<<dim3(unsigned(nn), kPairSplits), 256, 0, st>>>(Bw, rs, astr, Na, n, part);
+    k_pair_rows<<<1, 1024, 0, st>>>(rs, Na, rows); hy::count_launch();
+    k_pair_contract<<<dim3(unsigned(nn), kPairSplits), 256, 0, st>>>(Bw, rs, astr, rows, n, part);
     hy::count_launch();
     const int64_t tot = int64_t(nn) * nn;
     k_pair_reduce<<<unsigned((tot + 255) / 256), 256, 0, st>>>(part, tot, kPairSplits, D);
@@ -233,11 +306,11 @@ cudaError_t touched_weights(const T *psi, int64_t Na, int64_t Nb, const uint32_t
 }
 
 template cudaError_t touched_weights<double>(const double *, int64_t, int64_t, const uint32_t *,
-                                             const uint32_t *, int, float *, float *, float *,
-                                             float *, int, cudaStream_t);
+                                             const uint32_t *, int, float *, float *, int32_t *,
+                                             float *, float *, int, cudaStream_t);
 template cudaError_t touched_weights<float>(const float *, int64_t, int64_t, const uint32_t *,
-                                            const uint32_t *, int, float *, float *, float *,
-                                            float *, int, cudaStream_t);
+                                            const uint32_t *, int, float *, float *, int32_t *,
+                                            float *, float *, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // per-operator features (kRankerFeatures floats per operator)
