@@ -87,6 +87,8 @@ struct hy_adapt {
     size_t sparse_fail_len[2] = {SIZE_MAX, SIZE_MAX};
     int64_t sparse_m = -1;        // support of the last evaluated state (-1: dense)
     int64_t sparse_m_last[2] = {1, 1};   // last sparse support of each precision
+    bool prep_small = false;             // the last evaluation prepared psi in one CTA
+                                         // (angles on the device for its theta)
     double *d_n2 = nullptr;       // tracked squared norm (float renormalisation)
     double *h_cs = nullptr, *d_cs = nullptr;   // cos, sin of the ansatz angles (pinned / device)
     double *d_one = nullptr;      // device constants {1.0, 1.0f}
@@ -155,7 +157,8 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     hy::SparseState *S = a->ss[d][0], *G = a->ss[d][3];
     void *psi = a->buf[d][0], *sigma = a->buf[d][1];
     const size_t L = a->ops.size();
-    if (a->sparse_m_last[d] <= kPrepareSmall) {
+    a->prep_small = a->sparse_m_last[d] <= kPrepareSmall;
+    if (a->prep_small) {
         // small support: the whole preparation in one launch
         if (!a->ss_clean[d][0]) HY_TRY(hy::sstate_reset(S, true, false, st));
         a->ss_clean[d][0] = true;
@@ -222,6 +225,7 @@ hy_status energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
 {
     const int d = di(dt);
     a->sparse_m = -1;
+    a->prep_small = false;
     if (a->cfg.sparse && a->ops.size() < a->sparse_fail_len[d]) {
         bool ok = false;
         HY_TRY(energy_sparse(a, th, dt, st, e, &ok));
@@ -290,6 +294,26 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     if (a->sparse_m < 0) return gradient_dense(a, th, dt, st, g);
     const int d = di(dt);
     hy::SparseState *P = a->ss[d][0], *F = a->ss[d][1], *L = a->ss[d][2], *G = a->ss[d][3];
+    if (a->prep_small && a->sparse_m <= kPrepareSmall) {
+        // small support: the whole gradient in forward mode in one launch
+        if (!a->ss_clean[d][1]) HY_TRY(hy::sstate_reset(F, true, false, st));
+        if (!a->ss_clean[d][2]) HY_TRY(hy::sstate_reset(L, true, false, st));
+        a->ss_clean[d][1] = a->ss_clean[d][2] = true;
+        HY_TRY(hy::sstate_grad_forward(F, L, a->p, a->d_ops, a->d_cs, int64_t(j), a->buf[d][1],
+                                       dt == HY_F32 ? a->d_n2 : nullptr, a->d_ga, st));
+        int64_t cnt[2] = {0, 0};
+        HY_TRY(xfer(a, g.data(), a->d_ga, j * sizeof(double), cudaMemcpyDeviceToHost, st,
+                    "gradient readback"));
+        HY_TRY(xfer(a, &cnt[0], hy::sstate_count(F), sizeof(int64_t), cudaMemcpyDeviceToHost, st,
+                    "support count"));
+        HY_TRY(xfer(a, &cnt[1], hy::sstate_count(L), sizeof(int64_t), cudaMemcpyDeviceToHost, st,
+                    "support count"));
+        HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+        if (cnt[0] <= hy::sstate_cap(F) && cnt[1] <= hy::sstate_cap(L)) return HY_OK;
+        if (cnt[0] > hy::sstate_cap(F)) a->ss_clean[d][1] = false;
+        if (cnt[1] > hy::sstate_cap(L)) a->ss_clean[d][2] = false;
+        return gradient_dense(a, th, dt, st, g);
+    }
     void *sigma = a->buf[d][1], *lam = a->buf[d][3];
     HY_TRY(hy::sstate_reset(F, !a->ss_clean[d][1], false, st));
     a->ss_clean[d][1] = true;

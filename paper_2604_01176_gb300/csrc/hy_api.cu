@@ -99,6 +99,7 @@ struct hy_ham {
     float *d_pairD = nullptr;                   // [2][n^4] touched weights (psi, sigma)
     float *d_pairP = nullptr;                   // [splits][n^4] contraction partials
     int32_t *d_pairRows = nullptr;              // [Na + 1] nonzero alpha rows
+    double *d_occw = nullptr;                   // [34] occupations-from-weights scratch
     int occ_blocks = 0;
     // workspace (grown on demand; growth synchronises the device)
     void *ws = nullptr;
@@ -589,6 +590,8 @@ hy_status hy_build_hamiltonian(const double *h1, const double *h2, double e_core
         up(ar.upload(&h->d_pairP, zq.data(), zq.size()), "touched-weight partials");
         std::vector<int32_t> zrow(size_t(h->Na) + 1, 0);
         up(ar.upload(&h->d_pairRows, zrow.data(), zrow.size()), "touched-weight rows");
+        std::vector<double> zw(34, 0.0);
+        up(ar.upload(&h->d_occw, zw.data(), zw.size()), "occupation scratch");
     }
     if (s == HY_OK) s = upload_csr<double>(ar, h->kt.Ma, h->Ma64);
     if (s == HY_OK) s = upload_csr<double>(ar, h->kt.Mb, h->Mb64);
@@ -1183,7 +1186,7 @@ hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
     }
     // occupations from psi's touched-weight partials: no further pass over psi
     HY_CUDA(hy::k::occupations_from_weights(h->d_pairB, h->d_pairRs, h->d_astr, h->Na, h->n,
-                                            h->d_occ, st), "occupations");
+                                            h->d_occw, h->d_occ, st), "occupations");
     const float *Dp = sigma_or_null ? h->d_pairD : nullptr;
     const float *Ds = sigma_or_null ? h->d_pairD + nn * nn : nullptr;
     HY_CUDA(hy::k::features(p->d_desc, int64_t(p->ops.size()), h->n, h->d_h1, h->d_eri,
@@ -1698,6 +1701,34 @@ hy_status sstate_prepare(SparseState *s, const hy_pool *p, const int32_t *ops, c
     else
         HY_CUDA(hy::k::sv_prepare<float>(svec<float>(s), o, ops, cs, int(L), renorm, norm2, st),
                 "sparse preparation");
+    return HY_OK;
+}
+
+hy_status sstate_grad_forward(SparseState *f, SparseState *w, const hy_pool *p, const int32_t *ops,
+                              const double *cs, int64_t L, const void *sigma, const double *norm2,
+                              double *g, void *stream)
+{
+    const hy_ham *h = f->h;
+    if (!p || p->h != h || w->h != h || w->dt != f->dt || !sigma || !g || L < 1 ||
+        L > (1 << 20) || !ops || !cs)
+        return fail(HY_ERR_ARG, "bad arguments");
+    hy::k::SvOpArgs o;
+    o.desc = p->d_desc;
+    o.astr = h->d_astr;
+    o.bstr = h->d_bstr;
+    o.binom33 = h->d_binom;
+    o.n = h->n;
+    o.Nb = h->Nb;
+    cudaStream_t st = as_stream(stream);
+    hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
+    if (f->dt == HY_F64)
+        HY_CUDA(hy::k::sv_grad_fwd<double>(svec<double>(f), svec<double>(w), o, ops, cs, int(L),
+                                           static_cast<const double *>(sigma), norm2, g, st),
+                "forward gradient");
+    else
+        HY_CUDA(hy::k::sv_grad_fwd<float>(svec<float>(f), svec<float>(w), o, ops, cs, int(L),
+                                          static_cast<const float *>(sigma), norm2, g, st),
+                "forward gradient");
     return HY_OK;
 }
 

@@ -157,6 +157,14 @@ hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double thet
 // two per constituent); the state must be clean.
 hy_status sstate_prepare(SparseState *s, const hy_pool *p, const int32_t *ops, const double *cs,
                          int64_t L, bool renorm, double *norm2, void *stream);
+// In one CTA, for small supports: g[l] (device) = dE/dtheta_l in forward mode
+// (dE/dtheta_l = 2 <sigma| U_L .. U_{l+1} A_l U_l .. U_1 |HF>), with f and w
+// clean scratch sparse vectors, sigma = H psi (dense), ops / cs as for
+// sstate_prepare and norm2 (device, float states) the squared norm psi was
+// divided by (nullptr: none)
+hy_status sstate_grad_forward(SparseState *f, SparseState *w, const hy_pool *p, const int32_t *ops,
+                              const double *cs, int64_t L, const void *sigma, const double *norm2,
+                              double *g, void *stream);
 // *out (device) = sum over the support of v * y (y dense, same dtype), FP64
 hy_status sstate_dot(const SparseState *s, const void *y, double *out, void *stream);
 // v <- v / sqrt(*norm2) on the support (norm2 on the device)

@@ -183,8 +183,10 @@ cudaError_t occupations(const T *psi, int64_t Na, int64_t Nb, const uint32_t *as
                         const uint32_t *bstr, int n, double *partial, int G, float *out,
                         cudaStream_t st);
 // the same occupations from psi's touched-weight partials (no pass over psi)
+// scratch: 34 doubles, the last one zero on first use (left zero after each call)
 cudaError_t occupations_from_weights(const float *Bw, const float *rs, const uint32_t *astr,
-                                     int64_t Na, int n, float *out, cudaStream_t st);
+                                     int64_t Na, int n, double *scratch, float *out,
+                                     cudaStream_t st);
 cudaError_t features(const int32_t *desc, int64_t K, int n, const double *h1,
                      const double *eri, const float *occ, const float *extra, const float *Dpsi,
                      const float *Dsig, float *feat, cudaStream_t st);
@@ -280,6 +282,13 @@ cudaError_t sv_excite(const SVec<T> &x, const SvOpArgs &o, int k, int nc, double
 template <typename T>
 cudaError_t sv_prepare(const SVec<T> &x, const SvOpArgs &o, const int32_t *ops, const double *cs,
                        int L, bool renorm, double *norm2, cudaStream_t st);
+// one CTA: g[l] = dE/dtheta_l of psi = U_L .. U_1|HF> in forward mode, f and
+// w scratch sparse vectors (clean), sigma = H psi dense; norm2 (device, or
+// null): psi was divided by sqrt(*norm2), so the gradient is too
+template <typename T>
+cudaError_t sv_grad_fwd(const SVec<T> &f, const SVec<T> &w, const SvOpArgs &o, const int32_t *ops,
+                        const double *cs, int L, const T *sigma, const double *norm2, double *g,
+                        cudaStream_t st);
 // sum over the support of x.v * y (y dense), in FP64, into *out (partials:
 // 4 * num_sms doubles); scale: x.v <- x.v / sqrt(*norm2) on the support
 template <typename T>

@@ -85,36 +85,53 @@ __global__ void k_occ_final(const double *__restrict__ partial, int G, int n,
 // The same occupations from the touched-weight partials of psi (Bw, rs of
 // touched_weights), without another pass over the state: the beta
 // occupation of r is sum_a Bw[a][r*n+r], the alpha occupation of p is
-// sum_{a holding p} rs[a], the norm sum_a rs[a].  One warp per sum, fixed order.
-__global__ void __launch_bounds__(1024)
+// sum_{a holding p} rs[a], the norm sum_a rs[a].  Block i (of 33) forms sum
+// i in a fixed order; the last block to finish normalises.
+__global__ void __launch_bounds__(256)
 k_occ_from_weights(const float *__restrict__ Bw, const float *__restrict__ rs,
-                   const uint32_t *__restrict__ astr, int64_t Na, int n, float *__restrict__ out)
+                   const uint32_t *__restrict__ astr, int64_t Na, int n, double *__restrict__ sums,
+                   unsigned *__restrict__ done, float *__restrict__ out)
 {
-    __shared__ double sums[33];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nn = n * n;
-    for (int i = warp; i < 33; i += blockDim.x >> 5) {
-        double acc = 0.0;
-        if (i == 32 || (i < 16 && i < n) || (i >= 16 && i - 16 < n))
-            for (int64_t a = lane; a < Na; a += 32) {
-                if (i == 32) acc += double(rs[a]);
-                else if (i < 16) acc += ((astr[a] >> i) & 1u) ? double(rs[a]) : 0.0;
-                else acc += double(Bw[a * nn + (i - 16) * n + (i - 16)]);
-            }
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-        if (lane == 0) sums[i] = acc;
+    __shared__ double red[8];
+    __shared__ bool last;
+    const int i = blockIdx.x, nn = n * n;
+    double acc = 0.0;
+    if (i == 32 || (i < 16 && i < n) || (i >= 16 && i - 16 < n))
+        for (int64_t a = threadIdx.x; a < Na; a += blockDim.x) {
+            if (i == 32) acc += double(rs[a]);
+            else if (i < 16) acc += ((astr[a] >> i) & 1u) ? double(rs[a]) : 0.0;
+            else acc += double(Bw[a * nn + (i - 16) * n + (i - 16)]);
+        }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        sums[i] = t;
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    const int i = threadIdx.x;
-    if (i >= 33) return;
-    const double norm = sums[32] > 0.0 ? sums[32] : 1.0;
-    if (i < n) out[i] = float(sums[i] / norm);
-    else if (i >= 16 && i < 16 + n) out[n + (i - 16)] = float(sums[i] / norm);
+    if (!last) return;
+    __threadfence();
+    const int j = threadIdx.x;
+    if (j < 33) {
+        const double norm = sums[32] > 0.0 ? sums[32] : 1.0;
+        if (j < n) out[j] = float(sums[j] / norm);
+        else if (j >= 16 && j < 16 + n) out[n + (j - 16)] = float(sums[j] / norm);
+    }
+    if (j == 0) *done = 0u;
 }
 
 cudaError_t occupations_from_weights(const float *Bw, const float *rs, const uint32_t *astr,
-                                     int64_t Na, int n, float *out, cudaStream_t st)
+                                     int64_t Na, int n, double *scratch, float *out,
+                                     cudaStream_t st)
 {
-    k_occ_from_weights<<<1, 1024, 0, st>>>(Bw, rs, astr, Na, n, out); hy::count_launch();
+    // scratch: 33 sums then the finished-block counter
+    unsigned *done = reinterpret_cast<unsigned *>(scratch + 33);
+    k_occ_from_weights<<<33, 256, 0, st>>>(Bw, rs, astr, Na, n, scratch, done, out);
+    hy::count_launch();
     return cudaGetLastError();
 }
 

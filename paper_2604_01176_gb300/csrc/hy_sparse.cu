@@ -378,13 +378,140 @@ k_sv_excite(SVec<T> x, SvOpArgs o, int k, int ci, T c, T s)
 }
 
 
-// The whole state preparation of a small support in one CTA: clear the
-// previous support, set |HF>, apply every constituent rotation of the
-// ansatz in order (a block barrier between rotations takes the place of the
-// launch boundary and of the count snapshot), and for float states divide
-// by the FP64 norm over the support.  cs[2l], cs[2l+1] = cos, sin theta_l.
+// ---------------------------------------------------------------------------
+// Single-CTA routines for small supports: block barriers take the place of
+// launch boundaries and of the count snapshot.
+// ---------------------------------------------------------------------------
 constexpr int kPrepThreads = 1024;
 
+// zero x on its support (bits included) and empty the list
+template <typename T>
+__device__ void blk_clear(SVec<T> &x)
+{
+    const int64_t m = list_len(x.count, 0, x.cap);
+    for (int64_t t = threadIdx.x; t < m; t += blockDim.x) {
+        const int64_t i = x.list[t];
+        x.v[i] = T(0);
+        x.bits[i >> 5] = 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *x.count = 0ull;
+    __syncthreads();
+}
+
+// list index i of x (unlisted before) -- the caller owns i's bit
+template <typename T>
+__device__ __forceinline__ void blk_list(SVec<T> &x, int64_t i)
+{
+    atomicOr(x.bits + (i >> 5), 1u << (i & 31));
+    const unsigned long long pos = atomicAdd(x.count, 1ull);
+    if (pos < (unsigned long long)x.cap) x.list[pos] = i;
+}
+
+// current length of x's list, the same in every thread
+template <typename T>
+__device__ int64_t blk_len(const SVec<T> &x, unsigned long long *m_sh)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) *m_sh = *x.count;
+    __syncthreads();
+    return *m_sh < (unsigned long long)x.cap ? int64_t(*m_sh) : x.cap;
+}
+
+// exp(theta (C - C^dagger)) for constituent ci of operator k, as k_sv_excite
+template <typename T>
+__device__ void blk_rotate(SVec<T> &x, const SvOpArgs &o, int k, int ci, T c, T sn,
+                           const uint32_t (*C)[33], unsigned long long *m_sh)
+{
+    const int64_t m = blk_len(x, m_sh);
+    int fw[4], bw[4], len;
+    op_strings(o.desc + 11 * k + 1 + 5 * ci, fw, bw, len);
+    const int n = o.n;
+    const uint64_t lowm = (1ull << n) - 1;
+    for (int64_t t = threadIdx.x; t < m; t += blockDim.x) {
+        const int64_t d = x.list[t];
+        const uint64_t mask = uint64_t(o.astr[d / o.Nb]) | (uint64_t(o.bstr[d % o.Nb]) << n);
+        uint64_t u = mask;
+        int sg = 1;
+        int64_t dom, img, fresh;
+        if (apply_string(fw, len, u, sg)) {
+            dom = d;
+            img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+            fresh = member(x.bits, img) ? -1 : img;
+        } else {
+            u = mask;
+            sg = 1;
+            if (!apply_string(bw, len, u, sg)) continue;
+            img = d;
+            dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+            if (member(x.bits, dom)) continue;
+            fresh = dom;
+        }
+        const T ss = sg > 0 ? sn : -sn;
+        const T xv = x.v[dom], yv = x.v[img];
+        x.v[dom] = c * xv - ss * yv;
+        x.v[img] = c * yv + ss * xv;
+        if (fresh >= 0) blk_list(x, fresh);
+    }
+}
+
+// w <- w + (C - C^dagger) f for constituent ci of operator k over f's
+// entries < m.  The constituent pairs determinants one to one, so a target
+// has a single source (its partner) and is written by one thread.
+template <typename T>
+__device__ void blk_generator(const SVec<T> &f, SVec<T> &w, const SvOpArgs &o, int k, int ci,
+                              int64_t m, const uint32_t (*C)[33])
+{
+    int fw[4], bw[4], len;
+    op_strings(o.desc + 11 * k + 1 + 5 * ci, fw, bw, len);
+    const int n = o.n;
+    const uint64_t lowm = (1ull << n) - 1;
+    for (int64_t t = threadIdx.x; t < m; t += blockDim.x) {
+        const int64_t d = f.list[t];
+        const uint64_t mask = uint64_t(o.astr[d / o.Nb]) | (uint64_t(o.bstr[d % o.Nb]) << n);
+        uint64_t u = mask;
+        int sg = 1;
+        int64_t tgt;
+        T val;
+        if (apply_string(fw, len, u, sg)) {          // C|d> = sg |tgt>
+            tgt = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+            val = sg > 0 ? f.v[d] : -f.v[d];
+        } else {
+            u = mask;
+            sg = 1;
+            if (!apply_string(bw, len, u, sg)) continue;
+            // -C^dagger |d> = -sg |tgt>
+            tgt = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+            val = sg > 0 ? -f.v[d] : f.v[d];
+        }
+        if (!member(w.bits, tgt)) blk_list(w, tgt);  // tgt is reached from d alone
+        w.v[tgt] += val;
+    }
+}
+
+// sum over x's support of x * y (y dense), FP64, block-reduced; thread 0
+template <typename T>
+__device__ double blk_dot(const SVec<T> &x, const T *y, int64_t m, double *red)
+{
+    double acc = 0.0;
+    for (int64_t t = threadIdx.x; t < m; t += blockDim.x) {
+        const int64_t i = x.list[t];
+        acc = fma(double(x.v[i]), double(y[i]), acc);
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
+// The whole state preparation of a small support in one CTA: clear the
+// previous support, set |HF>, apply every constituent rotation of the
+// ansatz in order, and for float states divide by the FP64 norm over the
+// support.  cs[2l], cs[2l+1] = cos, sin theta_l.
 template <typename T>
 __global__ void __launch_bounds__(kPrepThreads)
 k_sv_prepare(SVec<T> x, SvOpArgs o, const int32_t *__restrict__ ops,
@@ -396,92 +523,86 @@ k_sv_prepare(SVec<T> x, SvOpArgs o, const int32_t *__restrict__ ops,
     __shared__ double fac;
     const int tid = threadIdx.x;
     for (int i = tid; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
-    // clear the previous support (all its bits belong to listed entries)
-    {
-        const int64_t m = list_len(x.count, 0, x.cap);
-        for (int64_t t = tid; t < m; t += blockDim.x) {
-            const int64_t i = x.list[t];
-            x.v[i] = T(0);
-            x.bits[i >> 5] = 0u;
-        }
-    }
-    __syncthreads();
+    blk_clear(x);
     if (tid == 0) {
         x.v[0] = T(1);
-        x.bits[0] = 1u;
-        x.list[0] = 0;
-        *x.count = 1ull;
+        blk_list(x, 0);
     }
-    const int n = o.n;
-    const uint64_t lowm = (1ull << n) - 1;
     for (int l = 0; l < L; ++l) {
         const int k = ops[l];
         const int nc = o.desc[11 * k];
-        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
-        for (int ci = 0; ci < nc; ++ci) {
-            __syncthreads();                        // previous rotation complete
-            if (tid == 0) m_sh = *x.count;
-            __syncthreads();
-            const int64_t m = m_sh < (unsigned long long)x.cap ? int64_t(m_sh) : x.cap;
-            int fw[4], bw[4], len;
-            op_strings(o.desc + 11 * k + 1 + 5 * ci, fw, bw, len);
-            for (int64_t t = tid; t < m; t += blockDim.x) {
-                const int64_t d = x.list[t];
-                const uint64_t mask = uint64_t(o.astr[d / o.Nb]) | (uint64_t(o.bstr[d % o.Nb]) << n);
-                uint64_t u = mask;
-                int sg = 1;
-                int64_t dom, img, fresh;
-                if (apply_string(fw, len, u, sg)) {
-                    dom = d;
-                    img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
-                          rank_bits(uint32_t(u >> n), C);
-                    fresh = member(x.bits, img) ? -1 : img;
-                } else {
-                    u = mask;
-                    sg = 1;
-                    if (!apply_string(bw, len, u, sg)) continue;
-                    img = d;
-                    dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
-                          rank_bits(uint32_t(u >> n), C);
-                    if (member(x.bits, dom)) continue;
-                    fresh = dom;
-                }
-                const T ss = sg > 0 ? sn : -sn;
-                const T xv = x.v[dom], yv = x.v[img];
-                x.v[dom] = c * xv - ss * yv;
-                x.v[img] = c * yv + ss * xv;
-                if (fresh >= 0) {
-                    atomicOr(x.bits + (fresh >> 5), 1u << (fresh & 31));
-                    const unsigned long long pos = atomicAdd(x.count, 1ull);
-                    if (pos < (unsigned long long)x.cap) x.list[pos] = fresh;
-                }
-            }
-        }
+        for (int ci = 0; ci < nc; ++ci)
+            blk_rotate(x, o, k, ci, T(cs[2 * l]), T(cs[2 * l + 1]), C, &m_sh);
     }
-    __syncthreads();
+    const int64_t m = blk_len(x, &m_sh);
     if (tid == 0) {                 // leave the snapshot consistent for later rotations
         *x.snap = *x.count;
         *x.done = 0ull;
     }
     if (!renorm) return;
-    const int64_t m = list_len(x.count, 0, x.cap);
-    double acc = 0.0;
-    for (int64_t t = tid; t < m; t += blockDim.x) {
-        const double v = double(x.v[x.list[t]]);
-        acc = fma(v, v, acc);
-    }
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if ((tid & 31) == 0) red[tid >> 5] = acc;
-    __syncthreads();
+    const double sum = blk_dot(x, x.v, m, red);
     if (tid == 0) {
-        double sum = 0.0;
-        for (int w = 0; w < kPrepThreads / 32; ++w) sum += red[w];
         if (norm2) *norm2 = sum;
         fac = 1.0 / sqrt(sum);
     }
     __syncthreads();
     const T f = T(fac);
     for (int64_t t = tid; t < m; t += blockDim.x) x.v[x.list[t]] *= f;
+}
+
+// Gradient of E = <psi|H|psi>, psi = U_L .. U_1 |HF> (U_l = exp(theta_l A_l)),
+// in forward mode for small supports, in one CTA:
+//   dE/dtheta_l = 2 <sigma| U_L .. U_{l+1} A_l phi_l>,  phi_l = U_l .. U_1 |HF>,
+// with sigma = H psi (dense array).  phi (f) is advanced one operator at a
+// time; w = A_l phi_l is formed in a second sparse vector and carried
+// through the later rotations.  Every vector stays within psi's support, so
+// each of the O(L^2) rotations costs O(support).  norm2 (float states): psi
+// was divided by sqrt(*norm2) while phi here is not, so each g_l is too.
+template <typename T>
+__global__ void __launch_bounds__(kPrepThreads)
+k_sv_grad_fwd(SVec<T> f, SVec<T> w, SvOpArgs o, const int32_t *__restrict__ ops,
+              const double *__restrict__ cs, int L, const T *__restrict__ sigma,
+              const double *__restrict__ norm2, double *__restrict__ g)
+{
+    __shared__ uint32_t C[33][33];
+    __shared__ unsigned long long m_sh;
+    __shared__ double red[kPrepThreads / 32];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
+    blk_clear(f);
+    if (tid == 0) {
+        f.v[0] = T(1);
+        blk_list(f, 0);
+    }
+    const double scale = norm2 ? 2.0 / sqrt(*norm2) : 2.0;
+    for (int l = 0; l < L; ++l) {
+        const int k = ops[l];
+        const int nc = o.desc[11 * k];
+        for (int ci = 0; ci < nc; ++ci)
+            blk_rotate(f, o, k, ci, T(cs[2 * l]), T(cs[2 * l + 1]), C, &m_sh);
+        blk_clear(w);
+        const int64_t mf = blk_len(f, &m_sh);
+        for (int ci = 0; ci < nc; ++ci) {
+            blk_generator(f, w, o, k, ci, mf, C);
+            __syncthreads();                         // constituents add in order
+        }
+        for (int l2 = l + 1; l2 < L; ++l2) {
+            const int k2 = ops[l2];
+            const int nc2 = o.desc[11 * k2];
+            for (int ci = 0; ci < nc2; ++ci)
+                blk_rotate(w, o, k2, ci, T(cs[2 * l2]), T(cs[2 * l2 + 1]), C, &m_sh);
+        }
+        const int64_t mw = blk_len(w, &m_sh);
+        const double gl = blk_dot(w, sigma, mw, red);
+        if (tid == 0) g[l] = scale * gl;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        *f.snap = *f.count;
+        *f.done = 0ull;
+        *w.snap = *w.count;
+        *w.done = 0ull;
+    }
 }
 
 template <typename T>
@@ -574,6 +695,16 @@ cudaError_t sv_prepare(const SVec<T> &x, const SvOpArgs &o, const int32_t *ops, 
 }
 
 template <typename T>
+cudaError_t sv_grad_fwd(const SVec<T> &f, const SVec<T> &w, const SvOpArgs &o, const int32_t *ops,
+                        const double *cs, int L, const T *sigma, const double *norm2, double *g,
+                        cudaStream_t st)
+{
+    k_sv_grad_fwd<T><<<1, kPrepThreads, 0, st>>>(f, w, o, ops, cs, L, sigma, norm2, g);
+    hy::count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t sv_dot(const SVec<T> &x, const T *y, double *partials, double *out, int num_sms,
                    cudaStream_t st)
 {
@@ -645,6 +776,9 @@ template cudaError_t grad_sparse<float>(const SparseGradArgs<float> &, int, cuda
                                       int, cudaStream_t);                                    \
     template cudaError_t sv_prepare<T>(const SVec<T> &, const SvOpArgs &, const int32_t *,  \
                                        const double *, int, bool, double *, cudaStream_t);  \
+    template cudaError_t sv_grad_fwd<T>(const SVec<T> &, const SVec<T> &, const SvOpArgs &, \
+                                        const int32_t *, const double *, int, const T *,    \
+                                        const double *, double *, cudaStream_t);            \
     template cudaError_t sv_dot<T>(const SVec<T> &, const T *, double *, double *, int,     \
                                    cudaStream_t);                                            \
     template cudaError_t sv_scale_rsqrt<T>(const SVec<T> &, const double *, int, cudaStream_t);
