@@ -393,6 +393,14 @@ hy_status hy_occupations(const hy_ham *h, const void *psi, hy_dtype dt,
 hy_status hy_touched_weights(const hy_ham *h, const void *psi, hy_dtype dt,
                              float *D, void *stream);
 
+/* The same from the state's support: list (device, m indices, e.g. from
+ * hy_support) holds every nonzero amplitude of psi (each once); O(m) work
+ * instead of a pass over the whole state (the ADAPT driver's sparse path uses
+ * it for psi).  Sums by atomic adds: equal to hy_touched_weights up to float
+ * rounding in the order of addition. */
+hy_status hy_touched_weights_sparse(const hy_ham *h, const void *psi, hy_dtype dt,
+                                    const int64_t *list, int64_t m, float *D, void *stream);
+
 /* The ranker is an addition with no counterpart in the paper's method: a
  * small MLP that predicts, per pool operator, t_k = log10(|g_k| / max|g| +
  * 1e-6) from 16 features, so that only its top-M operators are screened

@@ -479,6 +479,21 @@ def touched_weights(ham: Hamiltonian, psi: torch.Tensor, stream=None) -> torch.T
     return out.view(n * n, n * n)
 
 
+def touched_weights_sparse(ham: Hamiltonian, psi: torch.Tensor, support: torch.Tensor,
+                           stream=None) -> torch.Tensor:
+    """touched_weights from psi's support (int64 device tensor listing every
+    nonzero amplitude once, e.g. from hy_support): O(support) work."""
+    ham._check_state(psi)
+    if support.dtype != torch.int64 or support.device != psi.device:
+        raise TypeError("support must be an int64 tensor on the state's device")
+    n = ham.n_orb
+    out = torch.empty(n ** 4, dtype=torch.float32, device=psi.device)
+    check(_abi.load().hy_touched_weights_sparse(ham.handle, _ptr(psi), dtype_code(psi.dtype),
+                                                _ptr(support.contiguous()), support.numel(),
+                                                _ptr(out), stream_ptr(stream)))
+    return out.view(n * n, n * n)
+
+
 def topk(scores: torch.Tensor, k: int, stream=None) -> torch.Tensor:
     """Indices of the k largest scores (descending, ties to the lower index)."""
     _require_cuda(scores)

@@ -115,6 +115,7 @@ SIGNATURES = {
     "hy_occupations": (I32, [P, P, I32, P, P]),
     "hy_ranker_features": (I32, [P, P, P, P, I32, P, P, P]),
     "hy_touched_weights": (I32, [P, P, I32, P, P]),
+    "hy_touched_weights_sparse": (I32, [P, P, I32, P, I64, P, P]),
     "hy_ranker_create": (I32, [I32, ctypes.c_uint64, PP]),
     "hy_ranker_destroy": (I32, [P]),
     "hy_ranker_info": (I32, [P, PI64, PI64, P, P]),

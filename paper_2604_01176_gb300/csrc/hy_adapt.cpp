@@ -725,7 +725,9 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         HY_TRY(full_screen());
         pick(all, g);
         if (ranked) {
-            HY_TRY(hy_ranker_features(a->h, a->p, psi, sigma, bulk, a->d_extra, a->d_feat, st));
+            HY_TRY(hy::ranker_features_impl(a->h, a->p, psi,
+                                            a->sparse_m >= 0 ? a->ss[di(bulk)][0] : nullptr,
+                                            sigma, bulk, a->d_extra, a->d_feat, st));
             HY_TRY(hy_ranker_add_samples(a->ranker, a->d_feat, a->d_g, a->K, st));
             // the first fit after the warm-up, warm-started refits on the
             // grown training set at refresh iterations; both are owed until
@@ -744,7 +746,9 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
             a->fit_pending = 0;
             a->fitted_once = true;
         }
-        HY_TRY(hy_ranker_features(a->h, a->p, psi, sigma, bulk, a->d_extra, a->d_feat, st));
+        HY_TRY(hy::ranker_features_impl(a->h, a->p, psi,
+                                        a->sparse_m >= 0 ? a->ss[di(bulk)][0] : nullptr, sigma,
+                                        bulk, a->d_extra, a->d_feat, st));
         HY_TRY(hy_ranker_predict(a->ranker, a->d_feat, a->K, a->d_score, st));
         // proposals: the M / 4 operators with the largest Cauchy-Schwarz
         // gradient bound (feature 10, an upper bound on |g_k|), then the

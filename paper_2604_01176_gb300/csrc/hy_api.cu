@@ -1161,37 +1161,7 @@ hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
                              const void *sigma_or_null, hy_dtype dt, const float *extra,
                              float *feat, void *stream)
 {
-    if (!h || !p || !psi || !feat || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
-    if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
-    cudaStream_t st = as_stream(stream);
-    const size_t nn = size_t(h->n) * h->n;
-    // bytes only: the touched-weight product skips all-zero tiles, so its
-    // executed arithmetic depends on the state and is not known here
-    const double passes = sigma_or_null ? 2.0 : 1.0;
-    hy::ProfScope prof(HY_PROF_FEATURES, st, passes * double(h->N) * (dt == HY_F64 ? 8 : 4));
-    const void *vecs[2] = {psi, sigma_or_null};
-    for (int v = 0; v < 2 && vecs[v]; ++v) {
-        float *B = h->d_pairB + size_t(v) * h->Na * nn, *rs = h->d_pairRs + size_t(v) * h->Na;
-        float *D = h->d_pairD + size_t(v) * nn * nn;
-        if (dt == HY_F64)
-            HY_CUDA(hy::k::touched_weights<double>(static_cast<const double *>(vecs[v]), h->Na,
-                                                   h->Nb, h->d_astr, h->d_bstr, h->n, B, rs,
-                                                   h->d_pairRows, h->d_pairP, D, h->num_sms, st),
-                    "touched weights");
-        else
-            HY_CUDA(hy::k::touched_weights<float>(static_cast<const float *>(vecs[v]), h->Na,
-                                                  h->Nb, h->d_astr, h->d_bstr, h->n, B, rs,
-                                                  h->d_pairRows, h->d_pairP, D, h->num_sms, st),
-                    "touched weights");
-    }
-    // occupations from psi's touched-weight partials: no further pass over psi
-    HY_CUDA(hy::k::occupations_from_weights(h->d_pairB, h->d_pairRs, h->d_astr, h->Na, h->n,
-                                            h->d_occw, h->d_occ, st), "occupations");
-    const float *Dp = sigma_or_null ? h->d_pairD : nullptr;
-    const float *Ds = sigma_or_null ? h->d_pairD + nn * nn : nullptr;
-    HY_CUDA(hy::k::features(p->d_desc, int64_t(p->ops.size()), h->n, h->d_h1, h->d_eri,
-                            h->d_occ, extra, Dp, Ds, feat, st), "features");
-    return HY_OK;
+    return hy::ranker_features_impl(h, p, psi, nullptr, sigma_or_null, dt, extra, feat, stream);
 }
 
 hy_status hy_touched_weights(const hy_ham *h, const void *psi, hy_dtype dt, float *D,
@@ -1211,6 +1181,36 @@ hy_status hy_touched_weights(const hy_ham *h, const void *psi, hy_dtype dt, floa
                                               h->d_pairRs, h->d_pairRows, h->d_pairP, D,
                                               h->num_sms, st),
                 "touched weights");
+    return HY_OK;
+}
+
+hy_status hy_touched_weights_sparse(const hy_ham *hc, const void *psi, hy_dtype dt,
+                                    const int64_t *list, int64_t m, float *D, void *stream)
+{
+    hy_ham *h = const_cast<hy_ham *>(hc);
+    if (!h || !psi || !D || !valid_dtype(dt) || m < 0 || (m > 0 && !list))
+        return fail(HY_ERR_ARG, "bad arguments");
+    cudaStream_t st = as_stream(stream);
+    // the kernel reads the count from the device: stage m in the workspace
+    const WsLayout L = ws_layout(h, n_partials_needed(h, 0), dt == HY_F64 ? 8 : 4);
+    hy_status s = ensure_ws(h, L.total);
+    if (s != HY_OK) return s;
+    auto *cnt = reinterpret_cast<unsigned long long *>(static_cast<char *>(h->ws) + L.scalar);
+    const unsigned long long mm = (unsigned long long)m;
+    HY_CUDA(cudaMemcpyAsync(cnt, &mm, sizeof(mm), cudaMemcpyHostToDevice, st), "count");
+    if (dt == HY_F64)
+        HY_CUDA(hy::k::touched_weights_list<double>(static_cast<const double *>(psi), list, cnt, m,
+                                                    m, h->Na, h->Nb, h->d_astr, h->d_bstr, h->n,
+                                                    h->d_pairB, h->d_pairRs, h->d_pairRows,
+                                                    h->d_pairP, D, h->num_sms, st),
+                "touched weights (list)");
+    else
+        HY_CUDA(hy::k::touched_weights_list<float>(static_cast<const float *>(psi), list, cnt, m,
+                                                   m, h->Na, h->Nb, h->d_astr, h->d_bstr, h->n,
+                                                   h->d_pairB, h->d_pairRs, h->d_pairRows,
+                                                   h->d_pairP, D, h->num_sms, st),
+                "touched weights (list)");
+    // (a copy from pageable host memory has left `mm` when the call returns)
     return HY_OK;
 }
 
@@ -1838,5 +1838,65 @@ int64_t ham_connections(const hy_ham *h)
     return 1 + sa + sb + da + db + sa * sb;
 }
 int64_t sstate_cap(const SparseState *s) { return s->cap; }
+
+}  // namespace hy
+
+namespace hy {
+
+// hy_ranker_features, with psi's touched weights taken from its support
+// list when psi_state (a clean sparse vector over psi) is given
+hy_status ranker_features_impl(const hy_ham *h, const hy_pool *p, const void *psi,
+                               const SparseState *psi_state, const void *sigma_or_null,
+                               hy_dtype dt, const float *extra, float *feat, void *stream)
+{
+    if (!h || !p || !psi || !feat || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
+    if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
+    if (psi_state && (psi_state->v != psi || psi_state->dt != dt))
+        return fail(HY_ERR_ARG, "sparse state does not match psi");
+    cudaStream_t st = as_stream(stream);
+    const size_t nn = size_t(h->n) * h->n;
+    // bytes only: the touched-weight product skips all-zero tiles, so its
+    // executed arithmetic depends on the state and is not known here
+    const double passes = (sigma_or_null ? 1.0 : 0.0) + (psi_state ? 0.0 : 1.0);
+    hy::ProfScope prof(HY_PROF_FEATURES, st, passes * double(h->N) * (dt == HY_F64 ? 8 : 4));
+    const void *vecs[2] = {psi, sigma_or_null};
+    for (int v = 0; v < 2 && vecs[v]; ++v) {
+        float *B = h->d_pairB + size_t(v) * h->Na * nn, *rs = h->d_pairRs + size_t(v) * h->Na;
+        float *D = h->d_pairD + size_t(v) * nn * nn;
+        if (v == 0 && psi_state) {
+            const SparseState *S = psi_state;
+            if (dt == HY_F64)
+                HY_CUDA(hy::k::touched_weights_list<double>(
+                            static_cast<const double *>(S->v), S->list, S->cnt, S->cap, S->hint,
+                            h->Na, h->Nb, h->d_astr, h->d_bstr, h->n, B, rs, h->d_pairRows,
+                            h->d_pairP, D, h->num_sms, st),
+                        "touched weights (list)");
+            else
+                HY_CUDA(hy::k::touched_weights_list<float>(
+                            static_cast<const float *>(S->v), S->list, S->cnt, S->cap, S->hint,
+                            h->Na, h->Nb, h->d_astr, h->d_bstr, h->n, B, rs, h->d_pairRows,
+                            h->d_pairP, D, h->num_sms, st),
+                        "touched weights (list)");
+        } else if (dt == HY_F64) {
+            HY_CUDA(hy::k::touched_weights<double>(static_cast<const double *>(vecs[v]), h->Na,
+                                                   h->Nb, h->d_astr, h->d_bstr, h->n, B, rs,
+                                                   h->d_pairRows, h->d_pairP, D, h->num_sms, st),
+                    "touched weights");
+        } else {
+            HY_CUDA(hy::k::touched_weights<float>(static_cast<const float *>(vecs[v]), h->Na,
+                                                  h->Nb, h->d_astr, h->d_bstr, h->n, B, rs,
+                                                  h->d_pairRows, h->d_pairP, D, h->num_sms, st),
+                    "touched weights");
+        }
+    }
+    // occupations from psi's touched-weight partials: no further pass over psi
+    HY_CUDA(hy::k::occupations_from_weights(h->d_pairB, h->d_pairRs, h->d_astr, h->Na, h->n,
+                                            h->d_occw, h->d_occ, st), "occupations");
+    const float *Dp = sigma_or_null ? h->d_pairD : nullptr;
+    const float *Ds = sigma_or_null ? h->d_pairD + nn * nn : nullptr;
+    HY_CUDA(hy::k::features(p->d_desc, int64_t(p->ops.size()), h->n, h->d_h1, h->d_eri,
+                            h->d_occ, extra, Dp, Ds, feat, st), "features");
+    return HY_OK;
+}
 
 }  // namespace hy

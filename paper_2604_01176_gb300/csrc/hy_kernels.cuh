@@ -196,6 +196,14 @@ template <typename T>
 cudaError_t touched_weights(const T *psi, int64_t Na, int64_t Nb, const uint32_t *astr,
                             const uint32_t *bstr, int n, float *Bw, float *rs, int32_t *rows,
                             float *part, float *D, int num_sms, cudaStream_t st);
+// the same for a state given by its support list (v dense-backed; the device
+// count is clamped to cap; hint ~ the count, for the grid)
+template <typename T>
+cudaError_t touched_weights_list(const T *v, const int64_t *list, const unsigned long long *count,
+                                 int64_t cap, int64_t hint, int64_t Na, int64_t Nb,
+                                 const uint32_t *astr, const uint32_t *bstr, int n, float *Bw,
+                                 float *rs, int32_t *rows, float *part, float *D, int num_sms,
+                                 cudaStream_t st);
 
 // sparse-state path (hy_sparse.cu)
 template <typename T>

@@ -4,6 +4,7 @@
 // ranker has no counterpart in the paper's method: it proposes the M pool
 // operators most likely to have the largest |g_k|, which are then screened
 // exactly; the full screen stays the fallback and the judge.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -11,6 +12,7 @@
 #include <vector>
 
 #include "hyperion.h"
+
 #include "hy_kernels.cuh"
 
 namespace hy {
@@ -303,6 +305,61 @@ k_pair_reduce(const float *__restrict__ part, int64_t total, int S, float *__res
 
 int pair_splits() { return kPairSplits; }
 
+// Bw and rs of a state held as a list of its nonzero amplitudes (Bw, rs
+// zeroed by the caller): every listed determinant (A, B) adds w = x^2 to
+// rs[A] and to Bw[A][j*n+b] for each pair j, b of B's electrons.  O(support)
+// instead of a pass over the whole state.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_pair_weights_list(const T *__restrict__ v, const int64_t *__restrict__ list,
+                    const unsigned long long *__restrict__ count, int64_t cap, int64_t Nb,
+                    const uint32_t *__restrict__ bstr, int n, float *__restrict__ Bw,
+                    float *__restrict__ rs)
+{
+    const unsigned long long c = *count;
+    const int64_t m = c < (unsigned long long)cap ? int64_t(c) : cap;
+    const int nn = n * n;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < m;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t d = list[t];
+        const float x = float(v[d]);
+        const float w = x * x;
+        if (w == 0.0f) continue;
+        const int64_t A = d / Nb;
+        const uint32_t bm = bstr[d % Nb];
+        atomicAdd(rs + A, w);
+        for (uint32_t mj = bm; mj; mj &= mj - 1) {
+            const int j = __ffs(mj) - 1;
+            for (uint32_t mb = bm; mb; mb &= mb - 1)
+                atomicAdd(Bw + A * nn + j * n + (__ffs(mb) - 1), w);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t touched_weights_list(const T *v, const int64_t *list, const unsigned long long *count,
+                                 int64_t cap, int64_t hint, int64_t Na, int64_t Nb,
+                                 const uint32_t *astr, const uint32_t *bstr, int n, float *Bw,
+                                 float *rs, int32_t *rows, float *part, float *D, int num_sms,
+                                 cudaStream_t st)
+{
+    const int nn = n * n;
+    cudaError_t e = cudaMemsetAsync(Bw, 0, size_t(Na) * nn * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(rs, 0, size_t(Na) * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    int64_t g = (std::max<int64_t>(hint, 1) + 255) / 256;
+    if (g > int64_t(num_sms) * 8) g = int64_t(num_sms) * 8;
+    k_pair_weights_list<T><<<unsigned(g), 256, 0, st>>>(v, list, count, cap, Nb, bstr, n, Bw, rs);
+    hy::count_launch();
+    k_pair_rows<<<1, 1024, 0, st>>>(rs, Na, rows); hy::count_launch();
+    k_pair_contract<<<dim3(unsigned(nn), kPairSplits), 256, 0, st>>>(Bw, rs, astr, rows, n, part);
+    hy::count_launch();
+    const int64_t tot = int64_t(nn) * nn;
+    k_pair_reduce<<<unsigned((tot + 255) / 256), 256, 0, st>>>(part, tot, kPairSplits, D);
+    hy::count_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t touched_weights(const T *psi, int64_t Na, int64_t Nb, const uint32_t *astr,
                             const uint32_t *bstr, int n, float *Bw, float *rs, int32_t *rows,
@@ -325,6 +382,16 @@ cudaError_t touched_weights(const T *psi, int64_t Na, int64_t Nb, const uint32_t
 template cudaError_t touched_weights<double>(const double *, int64_t, int64_t, const uint32_t *,
                                              const uint32_t *, int, float *, float *, int32_t *,
                                              float *, float *, int, cudaStream_t);
+template cudaError_t touched_weights_list<double>(const double *, const int64_t *,
+                                                  const unsigned long long *, int64_t, int64_t,
+                                                  int64_t, int64_t, const uint32_t *,
+                                                  const uint32_t *, int, float *, float *,
+                                                  int32_t *, float *, float *, int, cudaStream_t);
+template cudaError_t touched_weights_list<float>(const float *, const int64_t *,
+                                                 const unsigned long long *, int64_t, int64_t,
+                                                 int64_t, int64_t, const uint32_t *,
+                                                 const uint32_t *, int, float *, float *,
+                                                 int32_t *, float *, float *, int, cudaStream_t);
 template cudaError_t touched_weights<float>(const float *, int64_t, int64_t, const uint32_t *,
                                             const uint32_t *, int, float *, float *, int32_t *,
                                             float *, float *, int, cudaStream_t);

@@ -234,3 +234,18 @@ def test_sparse_state_full_size_against_dense():
     assert np.abs(g_s - g_d).max() < 1e-9
     ps, pd = sp.state(), de.state()
     assert torch.max(torch.abs(ps - pd)).item() < 1e-13
+
+
+@pytest.mark.parametrize("cfg,dt", [((8, 4, 4, 1005), torch.float64), ((10, 5, 5, 1002), torch.float32),
+                                    ((16, 8, 8, 1004), torch.float32)])
+def test_touched_weights_from_support(cfg, dt):
+    """hy_touched_weights_sparse over a sparse state's support equals the
+    dense pass (float rounding of the summation order only)."""
+    import paper_2604_01176_gb300 as hy
+    ref, ham, pool = system(*cfg)
+    psi = torch.from_numpy(prepared(ref, 7, 6)).to("cuda", dt)
+    lst, m = support(ham, psi)
+    dense = hy.touched_weights(ham, psi)
+    sparse = hy.touched_weights_sparse(ham, psi, lst[:m])
+    assert torch.max(torch.abs(sparse - dense)).item() <= 2e-6 * dense[0, 0].item()
+    assert abs(dense[0, 0].item() - float((psi.double() ** 2).sum().item())) < 1e-5
