@@ -24,9 +24,11 @@
  *     I = rank(alpha) * N_beta + rank(beta); a state vector is a dense array
  *     of N_det = N_alpha * N_beta amplitudes in that order.
  *   - Precision: HY_F64 computes in double; HY_F32 keeps amplitudes and the
- *     bulk arithmetic in float with float accumulation.  Energies, norms,
- *     dot products and gradients are always accumulated and returned in
- *     double.
+ *     bulk arithmetic in float with float accumulation (the float coupling
+ *     of H psi runs on the tensor cores as TF32 products of split operands,
+ *     FP32 accuracy; hy_ham_set_coupling).  Energies, norms, dot products
+ *     and gradients are always returned in double and reduced with FP64
+ *     accuracy (see hy_dot).
  *   - Ownership: the caller owns every state vector and output buffer passed
  *     in (device pointers unless stated "host") and the CUDA stream (passed
  *     as void*, NULL = legacy default stream).  The library owns the tables
@@ -200,14 +202,19 @@ hy_status hy_unrank(const hy_ham *h, const int64_t *idx, uint64_t *dets,
 hy_status hy_apply_h(const hy_ham *h, const void *psi, void *sigma,
                      hy_dtype dt, void *stream);
 
-/* *e_out (device, one double) = <psi|sigma> accumulated in double; if
+/* *e_out (device, one double) = <psi|sigma> with FP64 accuracy (see hy_dot); if
  * sigma_or_null is NULL, sigma = H psi is computed first into the
  * workspace.  psi is not normalised by this call. */
 hy_status hy_energy(const hy_ham *h, const void *psi, const void *sigma_or_null,
                     hy_dtype dt, double *e_out, void *stream);
 
-/* *out (device, one double) = <x|y> accumulated in double (deterministic:
- * fixed grid and fixed summation order for a given device). */
+/* *out (device, one double) = <x|y> with FP64 accuracy: HY_F64 products
+ * summed in double; HY_F32 products formed exactly (FP32 TwoProduct) and
+ * summed with their rounding errors (TwoSum, the Dot2 scheme of Ogita, Rump
+ * and Oishi), each run of 32 flushed into a double -- the float->double
+ * conversion and FP64 add per element would bound the sweep on GB300's FP64
+ * pipe.  Products near the FP32 overflow threshold are taken in double.
+ * Deterministic: fixed grid and summation order for a given device. */
 hy_status hy_dot(const hy_ham *h, const void *x, const void *y, hy_dtype dt,
                  double *out, void *stream);
 
@@ -321,7 +328,7 @@ hy_status hy_apply_excitation_tracked(const hy_ham *h, const hy_pool *p, int64_t
 hy_status hy_renormalize(const hy_ham *h, void *psi, hy_dtype dt,
                          const double *norm2, void *stream);
 
-/* Scale psi by 1 / sqrt(<psi|psi>) (norm accumulated in double). */
+/* Scale psi by 1 / sqrt(<psi|psi>) (norm with FP64 accuracy, as hy_dot). */
 hy_status hy_normalize(const hy_ham *h, void *psi, hy_dtype dt, void *stream);
 
 /* ---------------------------------------------------------------------- */
