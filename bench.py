@@ -81,6 +81,8 @@ def parse():
                     help="plain FP64 ADAPT vs mixed+ranker ADAPT with the full screen as judge: "
                          "per-iteration rank of the true argmax and energy gap")
     ap.add_argument("--iters", type=int, default=12, help="iterations of --ranker-eval")
+    ap.add_argument("--sparse-eval", action="store_true",
+                    help="--ranker-eval on the sparse-state path (plain reference included)")
     ap.add_argument("--top-m", type=int, default=TOP_M,
                     help="operators the ranker proposes for the exact screen")
     ap.add_argument("--adapt-only", action="store_true",
@@ -167,15 +169,20 @@ def ranker_eval(args):
     ham = hy.Hamiltonian(h1, h2, ec, n, na, nb)
     pool = hy.Pool(ham)
     it = args.iters
-    plain = None if args.judge_only else hy.Adapt(ham, pool, "f64", max_iter=it).run(it)
+    # the sparse path makes the plain FP64 reference affordable at 32 q; the
+    # ranker is asked on every ranked iteration (no exact sparse screen)
+    sp = dict(sparse=True, exact_screen_work=-1.0) if args.sparse_eval else {}
+    plain = None if args.judge_only else hy.Adapt(ham, pool, "f64", max_iter=it,
+                                                  **sp).run(it)
     ranker = hy.Ranker(hidden=256, seed=7)
     ad = hy.Adapt(ham, pool, "mixed", max_iter=it, screen_top_m=args.top_m, judge=True,
-                  refine_every=0 if args.judge_only else 1)
+                  refine_every=0 if args.judge_only else 1, **sp)
     ad.set_ranker(ranker, warm_iters=args.warmup, epochs=30, refresh_every=REFRESH)
     ranked = ad.run(it)
     rows = []
     for i, r in enumerate(ranked):
         row = {"iter": r["iter"], "e_ranked": r["energy"], "true_rank": r["true_rank"],
+               "selected": r["selected"], "true_argmax": r["true_argmax"],
                "t_screen_ranked": round(r["t_screen"], 5), "t_total": round(r["t_total"], 3)}
         if plain is not None:
             p = plain[i]

@@ -469,8 +469,9 @@ hy_status hy_ranker_topk(const float *score, int64_t m, int64_t k,
  * warm_iters iterations run the full screen and feed the ranker (features,
  * exact |g|) pairs; it is then fitted (`epochs` passes) and from then on
  * M operators are proposed and screened exactly: the M / 4 with the largest
- * gradient bound (feature 10, an upper bound on |g_k|), then the MLP's top
- * ranks until M distinct operators.  Every
+ * gradient bound (feature 10, an upper bound on |g_k|), the M / 4 with the
+ * largest |g_k| at their last exact screen, then the MLP's top ranks until M
+ * distinct operators.  Every
  * refresh_every-th ranked iteration (0: never) selects from the full screen
  * instead, adds its pairs and refits the ranker (epochs / 4 passes, warm
  * start), which bounds the age of the stale-gradient features.  The full
@@ -542,6 +543,11 @@ typedef struct {
                              for double and N_det/256 for float evaluations
                              (about where the scatter H psi stops beating the
                              dense sweep)                                     */
+    double exact_screen_work; /* sparse path with a ranker: screen the whole
+                             pool exactly while (pool size) x (support) is at
+                             most this; 0: 5e9 (the cost of the ranker's
+                             feature pass at 32 qubits); < 0: never (always
+                             ask the ranker, e.g. to judge it)               */
 } hy_adapt_config;
 
 /* One ADAPT iteration (all times in seconds, host wall clock). */

@@ -558,6 +558,7 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
         c.judge = 0;
         c.sparse = 0;
         c.sparse_cap = 0;
+        c.exact_screen_work = 0.0;
     }
     if ((c.bulk != HY_F64 && c.bulk != HY_F32) || c.max_iter < 1 || c.max_iter > (1 << 20) ||
         !(c.eps_grad >= 0) || !(c.gtol > 0) || !(c.gtol_bulk > 0) || c.max_evals < 1 ||
@@ -689,7 +690,9 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     // much as the ranker's features: screen exactly (and keep feeding the
     // ranker) while K x nonzeros stays below kExactScreenWork
     const bool cheap_exact = a->sparse_m >= 0 &&
-                             double(a->sparse_m) * double(a->K) <= kExactScreenWork;
+                             double(a->sparse_m) * double(a->K) <=
+                                 (a->cfg.exact_screen_work == 0.0 ? kExactScreenWork
+                                                                  : a->cfg.exact_screen_work);
     const bool use_ranker = ranked && post >= 0 && !refresh && !cheap_exact;
     std::vector<double> g;
     std::vector<int64_t> cand;   // screened operators, in proposal order
@@ -751,8 +754,9 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
                                         bulk, a->d_extra, a->d_feat, st));
         HY_TRY(hy_ranker_predict(a->ranker, a->d_feat, a->K, a->d_score, st));
         // proposals: the M / 4 operators with the largest Cauchy-Schwarz
-        // gradient bound (feature 10, an upper bound on |g_k|), then the
-        // MLP's ranking until M distinct operators
+        // gradient bound (feature 10, an upper bound on |g_k|), the M / 4
+        // with the largest stale |g_k|, then the MLP's ranking until M
+        // distinct operators
         const int64_t Mb = M / 4;
         std::vector<int32_t> by_mlp(M), by_bound(Mb);
         HY_TRY(hy_ranker_topk(a->d_score, a->K, M, a->d_prop, st));
@@ -767,10 +771,26 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
                         "proposals readback"));
         }
         HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+        // the M / 4 operators with the largest |g| at their last exact
+        // screen (host bookkeeping): gradients change slowly between
+        // iterations, and this catches operators the MLP under-rates
+        std::vector<int32_t> by_stale;
+        {
+            std::vector<int32_t> idx;
+            for (int64_t k = 0; k < a->K; ++k)
+                if (a->last_g[k] >= 0.0) idx.push_back(int32_t(k));
+            const size_t ns = std::min<size_t>(size_t(Mb), idx.size());
+            std::partial_sort(idx.begin(), idx.begin() + ns, idx.end(), [&](int32_t x, int32_t y) {
+                return a->last_g[x] > a->last_g[y] || (a->last_g[x] == a->last_g[y] && x < y);
+            });
+            by_stale.assign(idx.begin(), idx.begin() + ns);
+        }
         std::vector<int32_t> prop;
         std::vector<char> taken(a->K, 0);
         for (int32_t k : by_bound)
             if (!taken[k]) { taken[k] = 1; prop.push_back(k); }
+        for (int32_t k : by_stale)
+            if (int64_t(prop.size()) < M && !taken[k]) { taken[k] = 1; prop.push_back(k); }
         for (int32_t k : by_mlp)
             if (int64_t(prop.size()) < M && !taken[k]) { taken[k] = 1; prop.push_back(k); }
         HY_TRY(xfer(a, a->d_prop, prop.data(), prop.size() * 4, cudaMemcpyHostToDevice, st,
