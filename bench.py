@@ -545,6 +545,7 @@ def leg_summary(leg, S):
            "n_evals": [rec["n_evals"] for rec in leg["timed"]],
            "t_screen_s": [round(rec["t_screen"], 4) for rec in leg["timed"]],
            "support": [rec["support"] for rec in leg["timed"]],
+           "sigma_support": [rec["sigma_support"] for rec in leg["timed"]],
            "energy_bulk": [rec["energy"] for rec in leg["timed"]],
            "final_energy_f64": leg["e_final"],
            "final_bulk_minus_f64": leg["e_bulk"] - leg["e_final"],
@@ -595,6 +596,7 @@ def main():
                           "iters_per_s": round(S / (r["head"]["ms"] / 1e3), 5),
                           "n_evals": [rec["n_evals"] for rec in r["head"]["timed"]],
                           "support": [rec["support"] for rec in r["head"]["timed"]],
+                          "sigma_support": [rec["sigma_support"] for rec in r["head"]["timed"]],
                           "t_total": [round(rec["t_total"], 4) for rec in r["head"]["timed"]],
                           "launches": r["head"]["launches"],
                           "e2e_iters_per_s": round(S / (r["head"]["ms_e2e"] / 1e3), 5),

@@ -571,6 +571,8 @@ typedef struct {
     double t_judge;        /* judge: time of the extra full screen and refit  */
     int64_t support;       /* nonzero amplitudes of psi at the screen when the
                               sparse path ran it, -1 for the dense sweeps     */
+    int64_t sigma_support; /* listed nonzeros of sigma = H psi there, -1 when
+                              sigma's support was not listed                  */
 } hy_adapt_record;
 
 

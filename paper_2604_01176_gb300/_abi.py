@@ -57,7 +57,8 @@ class AdaptRecord(ctypes.Structure):
                 ("true_argmax", ctypes.c_int64), ("true_rank", ctypes.c_int64),
                 ("t_screen", ctypes.c_double), ("t_optimise", ctypes.c_double),
                 ("t_total", ctypes.c_double), ("t_judge", ctypes.c_double),
-                ("support", ctypes.c_int64)]
+                ("support", ctypes.c_int64),
+                ("sigma_support", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -431,6 +431,12 @@ const double kStall64 = std::ldexp(1.0, -50);
 // ranker's feature pass at 32 qubits)
 const double kExactScreenWork = 5e9;
 
+// cost of one atomic add of the list-based touched weights in amplitudes of
+// the dense pass (the rule that picks sigma's list).  Measured at 32 qubits
+// on sigma supports of 0.15-2.1 M: about 12 ps per add, against 10-15 ps per
+// amplitude of the dense pass (compute-bound once most tiles are nonzero)
+const double kListAddCost = 1.0;
+
 
 // BFGS with backtracking (Armijo) line search on E(theta) in dt, starting
 // from a->theta and a->hinv; updates both.  *e_out = final energy.  With
@@ -678,6 +684,20 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     }
     void *psi = a->buf[di(bulk)][0], *sigma = a->buf[di(bulk)][1];
     rec->support = a->sparse_m;
+    const bool sig_listed = a->sparse_m >= 0 && a->sig_listed[di(bulk)];
+    rec->sigma_support = sig_listed ? a->sig_count[di(bulk)] : -1;
+    // the sparse path lists psi's support, and sigma's while it fits its list:
+    // the ranker's features then take psi's touched weights from its list,
+    // and sigma's while its list costs less than the pass over the dense
+    // array (one atomic add per electron pair of a listed determinant,
+    // counted as kListAddCost streamed amplitudes)
+    const hy::SparseState *psi_list = a->sparse_m >= 0 ? a->ss[di(bulk)][0] : nullptr;
+    const hy::SparseState *sigma_list =
+        sig_listed && double(a->sig_count[di(bulk)]) *
+                              double(hy::ham_list_weight_adds(a->h)) * kListAddCost <=
+                          double(a->N)
+            ? a->ss[di(bulk)][3]
+            : nullptr;
     // 2. screen: full, or the ranker's top-M proposals screened exactly
     const bool ranked = a->cfg.screen_top_m > 0;
     if (ranked && !a->ranker) return set_err(HY_ERR_UNSUPPORTED, "ranked screen needs a ranker");
@@ -728,9 +748,8 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         HY_TRY(full_screen());
         pick(all, g);
         if (ranked) {
-            HY_TRY(hy::ranker_features_impl(a->h, a->p, psi,
-                                            a->sparse_m >= 0 ? a->ss[di(bulk)][0] : nullptr,
-                                            sigma, bulk, a->d_extra, a->d_feat, st));
+            HY_TRY(hy::ranker_features_impl(a->h, a->p, psi, psi_list, sigma, sigma_list, bulk,
+                                            a->d_extra, a->d_feat, st));
             HY_TRY(hy_ranker_add_samples(a->ranker, a->d_feat, a->d_g, a->K, st));
             // the first fit after the warm-up, warm-started refits on the
             // grown training set at refresh iterations; both are owed until
@@ -749,9 +768,8 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
             a->fit_pending = 0;
             a->fitted_once = true;
         }
-        HY_TRY(hy::ranker_features_impl(a->h, a->p, psi,
-                                        a->sparse_m >= 0 ? a->ss[di(bulk)][0] : nullptr, sigma,
-                                        bulk, a->d_extra, a->d_feat, st));
+        HY_TRY(hy::ranker_features_impl(a->h, a->p, psi, psi_list, sigma, sigma_list, bulk,
+                                        a->d_extra, a->d_feat, st));
         HY_TRY(hy_ranker_predict(a->ranker, a->d_feat, a->K, a->d_score, st));
         // proposals: the M / 4 operators with the largest Cauchy-Schwarz
         // gradient bound (feature 10, an upper bound on |g_k|), the M / 4

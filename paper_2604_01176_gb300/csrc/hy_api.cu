@@ -1161,7 +1161,8 @@ hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
                              const void *sigma_or_null, hy_dtype dt, const float *extra,
                              float *feat, void *stream)
 {
-    return hy::ranker_features_impl(h, p, psi, nullptr, sigma_or_null, dt, extra, feat, stream);
+    return hy::ranker_features_impl(h, p, psi, nullptr, sigma_or_null, nullptr, dt, extra, feat,
+                                    stream);
 }
 
 hy_status hy_touched_weights(const hy_ham *h, const void *psi, hy_dtype dt, float *D,
@@ -1838,6 +1839,7 @@ int64_t ham_connections(const hy_ham *h)
     return 1 + sa + sb + da + db + sa * sb;
 }
 int64_t sstate_cap(const SparseState *s) { return s->cap; }
+int64_t ham_list_weight_adds(const hy_ham *h) { return 1 + int64_t(h->nb) * (h->nb + 1) / 2; }
 
 }  // namespace hy
 
@@ -1847,24 +1849,32 @@ namespace hy {
 // list when psi_state (a clean sparse vector over psi) is given
 hy_status ranker_features_impl(const hy_ham *h, const hy_pool *p, const void *psi,
                                const SparseState *psi_state, const void *sigma_or_null,
-                               hy_dtype dt, const float *extra, float *feat, void *stream)
+                               const SparseState *sigma_state, hy_dtype dt, const float *extra,
+                               float *feat, void *stream)
 {
     if (!h || !p || !psi || !feat || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
     if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
     if (psi_state && (psi_state->v != psi || psi_state->dt != dt))
         return fail(HY_ERR_ARG, "sparse state does not match psi");
+    if (sigma_state && (!sigma_or_null || sigma_state->v != sigma_or_null || sigma_state->dt != dt))
+        return fail(HY_ERR_ARG, "sparse state does not match sigma");
     cudaStream_t st = as_stream(stream);
     const size_t nn = size_t(h->n) * h->n;
     // bytes only: the touched-weight product skips all-zero tiles, so its
-    // executed arithmetic depends on the state and is not known here
-    const double passes = (sigma_or_null ? 1.0 : 0.0) + (psi_state ? 0.0 : 1.0);
-    hy::ProfScope prof(HY_PROF_FEATURES, st, passes * double(h->N) * (dt == HY_F64 ? 8 : 4));
+    // executed arithmetic depends on the state and is not known here.  A
+    // dense vector is read once; a listed one costs its index and value per
+    // support entry (the host's estimate of the support size)
+    const double esz = dt == HY_F64 ? 8.0 : 4.0;
+    const SparseState *states[2] = {psi_state, sigma_state};
     const void *vecs[2] = {psi, sigma_or_null};
+    double bytes = 0.0;
+    for (int v = 0; v < 2 && vecs[v]; ++v)
+        bytes += states[v] ? double(states[v]->hint) * (esz + 8.0) : double(h->N) * esz;
+    hy::ProfScope prof(HY_PROF_FEATURES, st, bytes);
     for (int v = 0; v < 2 && vecs[v]; ++v) {
         float *B = h->d_pairB + size_t(v) * h->Na * nn, *rs = h->d_pairRs + size_t(v) * h->Na;
         float *D = h->d_pairD + size_t(v) * nn * nn;
-        if (v == 0 && psi_state) {
-            const SparseState *S = psi_state;
+        if (const SparseState *S = states[v]) {
             if (dt == HY_F64)
                 HY_CUDA(hy::k::touched_weights_list<double>(
                             static_cast<const double *>(S->v), S->list, S->cnt, S->cap, S->hint,

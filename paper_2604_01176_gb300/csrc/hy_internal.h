@@ -178,15 +178,20 @@ hy_status sstate_apply_h(const SparseState *s, SparseState *sig, void *sigma, vo
 hy_status sstate_gradients(const SparseState *s, const void *lam, const hy_pool *p,
                            const int32_t *ops, int64_t n_ops, int64_t m_hint, double *g,
                            void *stream);
-// hy_ranker_features, with psi's touched weights taken from its support list
-// when psi_state (a clean sparse vector whose array is psi) is not null
+// hy_ranker_features, with psi's (sigma's) touched weights taken from its
+// support list when psi_state (sigma_state), a sparse vector whose array is
+// psi (sigma) and whose list holds its whole support, is not null
 hy_status ranker_features_impl(const hy_ham *h, const hy_pool *p, const void *psi,
                                const SparseState *psi_state, const void *sigma_or_null,
-                               hy_dtype dt, const float *extra, float *feat, void *stream);
+                               const SparseState *sigma_state, hy_dtype dt, const float *extra,
+                               float *feat, void *stream);
 const int64_t *sstate_count(const SparseState *s);   // device pointer
 // most determinants one determinant couples to through H (itself included):
 // 1 + s_a + s_b + d_a + d_b + s_a s_b (singles s, doubles d of each spin)
 int64_t ham_connections(const hy_ham *h);
+// atomic adds per listed determinant of the list-based touched weights
+// (its row sum and one per pair j <= b of its beta electrons)
+int64_t ham_list_weight_adds(const hy_ham *h);
 const int64_t *sstate_list(const SparseState *s);    // device pointer
 int64_t sstate_cap(const SparseState *s);
 

@@ -155,7 +155,9 @@ cudaError_t occupations(const T *psi, int64_t Na, int64_t Nb, const uint32_t *as
 //   D[(i,a)][(j,b)] = sum_alpha [i in alpha][a not in alpha] *
 //                     sum_beta w [j in beta][b not in beta]
 // with i == a (j == b) meaning "no condition on the alpha (beta) string".
-// The inner beta sum for j != b is Bw[.][j*n+j] - Bw[.][j*n+b].
+// The inner beta sum for j != b is Bw[.][j*n+j] - Bw[.][j*n+b].  Bw is
+// symmetric in (j, b): the contraction reads the upper triangle only
+// (j <= b), so the list-based weights fill only that.
 // ---------------------------------------------------------------------------
 // Bw is an indicator product, Bw = W I with W[a][c] = w(a, c) (N_a x N_b) and
 // I[c][jb] = [j in c][b in c] (N_b x n^2): a block owns 16 alpha rows, a
@@ -232,10 +234,12 @@ k_pair_weights(const T *__restrict__ psi, int64_t Na, int64_t Nb,
     }
 }
 
-// D[(i,a)][(j,b)] split over alpha rows: block (ia, split) sums the rows
-// split, split + S, ...; the alpha condition depends on (row, ia) only, so
-// the branch is uniform in the block; threads own jb.  Partials [S][n^4].
-constexpr int kPairSplits = 16;
+// D[(i,a)][(j,b)] split over alpha rows: block (group, split) owns 16
+// consecutive ia and sums the rows split, split + S, ...; threads own jb.
+// Each row's weight x (rs, or the beta difference) is read once per block and
+// added to the ia whose alpha condition the row meets, so Bw is read n^2 / 16
+// times in all (once per ia before).  Partials [S][n^4].
+constexpr int kPairSplits = 32, kPairGroup = 16;
 
 __global__ void __launch_bounds__(256)
 k_pair_contract(const float *__restrict__ Bw, const float *__restrict__ rs,
@@ -243,19 +247,34 @@ k_pair_contract(const float *__restrict__ Bw, const float *__restrict__ rs,
                 int n, float *__restrict__ part)
 {
     const int nn = n * n;
-    const int ia = blockIdx.x, jb = threadIdx.x;
-    const int i = ia / n, aa = ia % n;
+    const int ia0 = blockIdx.x * kPairGroup, jb = threadIdx.x;
     const int j = jb < nn ? jb / n : 0, b = jb < nn ? jb % n : 0;
+    const int ut = j <= b ? j * n + b : b * n + j;   // (j, b) in the upper triangle
+    // alpha condition of ia = (i, a): i == a (none), else i occupied, a empty
+    uint32_t need[kPairGroup], gone[kPairGroup];
+#pragma unroll
+    for (int q = 0; q < kPairGroup; ++q) {
+        const int ia = ia0 + q < nn ? ia0 + q : 0, i = ia / n, aa = ia % n;
+        need[q] = i == aa ? 0u : 1u << i;
+        gone[q] = i == aa ? 0u : 1u << aa;
+    }
     const int nrows = rows[0];
-    float acc = 0.0f;
+    float acc[kPairGroup];
+#pragma unroll
+    for (int q = 0; q < kPairGroup; ++q) acc[q] = 0.0f;
     if (jb < nn) {
+#pragma unroll 4
         for (int t = blockIdx.y; t < nrows; t += gridDim.y) {
             const int64_t al = rows[1 + t];
             const uint32_t m = astr[al];
-            if (i != aa && !(((m >> i) & 1u) && !((m >> aa) & 1u))) continue;
-            acc += (j == b) ? rs[al] : (Bw[al * nn + j * n + j] - Bw[al * nn + jb]);
+            const float x = (j == b) ? rs[al] : (Bw[al * nn + j * n + j] - Bw[al * nn + ut]);
+#pragma unroll
+            for (int q = 0; q < kPairGroup; ++q)
+                acc[q] += ((m & need[q]) == need[q] && (m & gone[q]) == 0u) ? x : 0.0f;
         }
-        part[int64_t(blockIdx.y) * nn * nn + int64_t(ia) * nn + jb] = acc;
+#pragma unroll
+        for (int q = 0; q < kPairGroup; ++q)
+            if (ia0 + q < nn) part[int64_t(blockIdx.y) * nn * nn + int64_t(ia0 + q) * nn + jb] = acc[q];
     }
 }
 
@@ -307,8 +326,9 @@ int pair_splits() { return kPairSplits; }
 
 // Bw and rs of a state held as a list of its nonzero amplitudes (Bw, rs
 // zeroed by the caller): every listed determinant (A, B) adds w = x^2 to
-// rs[A] and to Bw[A][j*n+b] for each pair j, b of B's electrons.  O(support)
-// instead of a pass over the whole state.
+// rs[A] and to Bw[A][j*n+b] for each pair j <= b of B's electrons (the upper
+// triangle, which is all the contraction reads).  O(support) instead of a
+// pass over the whole state.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_pair_weights_list(const T *__restrict__ v, const int64_t *__restrict__ list,
@@ -330,7 +350,7 @@ k_pair_weights_list(const T *__restrict__ v, const int64_t *__restrict__ list,
         atomicAdd(rs + A, w);
         for (uint32_t mj = bm; mj; mj &= mj - 1) {
             const int j = __ffs(mj) - 1;
-            for (uint32_t mb = bm; mb; mb &= mb - 1)
+            for (uint32_t mb = mj; mb; mb &= mb - 1)   // b >= j: mj's lowest bit is j
                 atomicAdd(Bw + A * nn + j * n + (__ffs(mb) - 1), w);
         }
     }
@@ -352,7 +372,8 @@ cudaError_t touched_weights_list(const T *v, const int64_t *list, const unsigned
     k_pair_weights_list<T><<<unsigned(g), 256, 0, st>>>(v, list, count, cap, Nb, bstr, n, Bw, rs);
     hy::count_launch();
     k_pair_rows<<<1, 1024, 0, st>>>(rs, Na, rows); hy::count_launch();
-    k_pair_contract<<<dim3(unsigned(nn), kPairSplits), 256, 0, st>>>(Bw, rs, astr, rows, n, part);
+    k_pair_contract<<<dim3(unsigned((nn + kPairGroup - 1) / kPairGroup), kPairSplits), 256, 0, st>>>(
+        Bw, rs, astr, rows, n, part);
     hy::count_launch();
     const int64_t tot = int64_t(nn) * nn;
     k_pair_reduce<<<unsigned((tot + 255) / 256), 256, 0, st>>>(part, tot, kPairSplits, D);
@@ -371,7 +392,8 @@ cudaError_t touched_weights(const T *psi, int64_t Na, int64_t Nb, const uint32_t
     hy::count_launch();
     const int nn = n * n;
     k_pair_rows<<<1, 1024, 0, st>>>(rs, Na, rows); hy::count_launch();
-    k_pair_contract<<<dim3(unsigned(nn), kPairSplits), 256, 0, st>>>(Bw, rs, astr, rows, n, part);
+    k_pair_contract<<<dim3(unsigned((nn + kPairGroup - 1) / kPairGroup), kPairSplits), 256, 0, st>>>(
+        Bw, rs, astr, rows, n, part);
     hy::count_launch();
     const int64_t tot = int64_t(nn) * nn;
     k_pair_reduce<<<unsigned((tot + 255) / 256), 256, 0, st>>>(part, tot, kPairSplits, D);
