@@ -92,6 +92,15 @@ struct hy_adapt {
     double *d_n2 = nullptr;       // tracked squared norm (float renormalisation)
     double *h_cs = nullptr, *d_cs = nullptr;   // cos, sin of the ansatz angles (pinned / device)
     double *d_one = nullptr;      // device constants {1.0, 1.0f}
+    // support program of the current ansatz (small supports): compiled from
+    // the first structural preparation after an append, then run by every
+    // evaluation and forward gradient of the iteration
+    hy::SupportProgram *prog = nullptr;
+    int prog_max_steps = 0;
+    std::vector<int64_t> prog_ops;       // the ansatz it was compiled for
+    int64_t prog_m = 0;                  // its support size
+    bool prog_grad_ok = false;           // its tables serve the forward gradient
+    bool prog_support[2] = {false, false};   // ss[dt][0] lists the program's support
 };
 
 namespace {
@@ -158,19 +167,38 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     void *psi = a->buf[d][0], *sigma = a->buf[d][1];
     const size_t L = a->ops.size();
     a->prep_small = a->sparse_m_last[d] <= kPrepareSmall;
+    // the support program serves this ansatz and S lists its support: only
+    // the amplitudes change
+    const bool prog_run = a->prep_small && L > 0 && a->prog && a->prog_support[d] &&
+                          a->prog_ops == a->ops;
+    bool prog_build = false;
+    int64_t steps = 0;
     if (a->prep_small) {
-        // small support: the whole preparation in one launch
-        if (!a->ss_clean[d][0]) HY_TRY(hy::sstate_reset(S, true, false, st));
-        a->ss_clean[d][0] = true;
         for (size_t l = 0; l < L; ++l) {
             a->h_cs[2 * l] = std::cos(th[l]);
             a->h_cs[2 * l + 1] = std::sin(th[l]);
         }
         if (L) HY_TRY(xfer(a, a->d_cs, a->h_cs, L * 2 * sizeof(double), cudaMemcpyHostToDevice, st,
                            "angles"));
+    }
+    if (prog_run) {
+        HY_TRY(hy::prog_prepare(a->prog, S, a->p, a->d_ops, a->d_cs, int64_t(L), dt == HY_F32,
+                                a->d_n2, st));
+    } else if (a->prep_small) {
+        // small support: the whole preparation in one launch, dating each
+        // listed determinant when a support program is to be compiled from it
+        if (!a->ss_clean[d][0]) HY_TRY(hy::sstate_reset(S, true, false, st));
+        a->ss_clean[d][0] = true;
+        a->prog_support[d] = false;
+        if (a->prog && L > 0 && a->prog_ops != a->ops) {
+            std::vector<int32_t> o32(a->ops.begin(), a->ops.end());
+            steps = hy::prog_steps(a->p, o32.data(), int64_t(L));
+            prog_build = steps <= a->prog_max_steps;
+        }
         HY_TRY(hy::sstate_prepare(S, a->p, a->d_ops, a->d_cs, int64_t(L), dt == HY_F32 && L > 0,
-                                  a->d_n2, st));
+                                  a->d_n2, st, prog_build ? hy::prog_step_len(a->prog) : nullptr));
     } else {
+        a->prog_support[d] = false;
         HY_TRY(hy::sstate_reset(S, !a->ss_clean[d][0], true, st));
         a->ss_clean[d][0] = true;
         for (size_t l = 0; l < L; ++l)
@@ -205,7 +233,23 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     *ok = cnt[0] <= hy::sstate_cap(S);
     if (!*ok) {
         a->ss_clean[d][0] = false;
+        a->prog_support[d] = false;
         return HY_OK;
+    }
+    if (prog_build && cnt[0] <= kPrepareSmall) {
+        HY_TRY(hy::prog_compile(a->prog, S, cnt[0], a->p, a->d_ops, int64_t(L), steps, st));
+        int flag = 1;
+        HY_TRY(xfer(a, &flag, hy::prog_flag(a->prog), sizeof(int), cudaMemcpyDeviceToHost, st,
+                    "support program check"));
+        HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+        a->prog_ops = a->ops;
+        a->prog_m = cnt[0];
+        a->prog_grad_ok = flag == 0;
+        a->prog_support[0] = a->prog_support[1] = false;
+        a->prog_support[d] = true;
+    } else if (a->prep_small && !prog_run && L > 0 && a->prog_ops == a->ops) {
+        // a structural preparation of the compiled ansatz lists the same support
+        a->prog_support[d] = cnt[0] == a->prog_m;
     }
     // sigma's values are complete either way; an overflowing list only
     // leaves its support unlisted (and its array to be cleared in full)
@@ -236,6 +280,7 @@ hy_status energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     a->ss_clean[d][0] = false;
     a->ss_clean[d][3] = false;
     a->sig_listed[d] = false;
+    a->prog_support[d] = false;
     HY_TRY(set_hf(a, psi, dt, st));
     // float states: the squared norm is tracked through the rotations in
     // double and the state renormalised once after the last one (equal to
@@ -294,6 +339,15 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     if (a->sparse_m < 0) return gradient_dense(a, th, dt, st, g);
     const int d = di(dt);
     hy::SparseState *P = a->ss[d][0], *F = a->ss[d][1], *L = a->ss[d][2], *G = a->ss[d][3];
+    if (a->prep_small && a->sparse_m <= kPrepareSmall && a->prog && a->prog_grad_ok &&
+        a->prog_support[d] && a->prog_ops == a->ops) {
+        // the support program's forward gradient: one CTA per angle
+        HY_TRY(hy::prog_grad(a->prog, a->p, a->d_ops, a->d_cs, int64_t(j), a->buf[d][1], dt,
+                             dt == HY_F32 ? a->d_n2 : nullptr, a->d_ga, st));
+        HY_TRY(xfer(a, g.data(), a->d_ga, j * sizeof(double), cudaMemcpyDeviceToHost, st,
+                    "gradient readback"));
+        return cu(cudaStreamSynchronize(st), "sync");
+    }
     if (a->prep_small && a->sparse_m <= kPrepareSmall) {
         // small support: the whole gradient in forward mode in one launch
         if (!a->ss_clean[d][1]) HY_TRY(hy::sstate_reset(F, true, false, st));
@@ -625,6 +679,9 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
             if (s == HY_OK) s = hy::sstate_create(h, dt, a->buf[d][1], lcap, &a->ss[d][3]);
         }
         a->conn = hy::ham_connections(h);
+        // two constituents at most per operator
+        a->prog_max_steps = int(std::min<int64_t>(254, 2 * int64_t(c.max_iter)));
+        if (s == HY_OK) s = hy::prog_create(h, a->prog_max_steps, &a->prog);
     }
     a->last_g.assign(a->K, -1.0);
     a->age.assign(a->K, 0);
@@ -659,6 +716,7 @@ hy_status hy_adapt_destroy(hy_adapt *a)
     cudaFree(a->d_one);
     for (auto &row : a->ss)
         for (hy::SparseState *&x : row) hy::sstate_destroy(x);
+    hy::prog_destroy(a->prog);
     delete a;
     return HY_OK;
 }

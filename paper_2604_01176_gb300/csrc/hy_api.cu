@@ -1682,7 +1682,7 @@ hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double thet
 }
 
 hy_status sstate_prepare(SparseState *s, const hy_pool *p, const int32_t *ops, const double *cs,
-                         int64_t L, bool renorm, double *norm2, void *stream)
+                         int64_t L, bool renorm, double *norm2, void *stream, int64_t *step_len)
 {
     const hy_ham *h = s->h;
     if (!p || p->h != h || (L > 0 && (!ops || !cs)) || L < 0 || L > (1 << 20))
@@ -1697,11 +1697,133 @@ hy_status sstate_prepare(SparseState *s, const hy_pool *p, const int32_t *ops, c
     cudaStream_t st = as_stream(stream);
     hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
     if (s->dt == HY_F64)
-        HY_CUDA(hy::k::sv_prepare<double>(svec<double>(s), o, ops, cs, int(L), renorm, norm2, st),
+        HY_CUDA(hy::k::sv_prepare<double>(svec<double>(s), o, ops, cs, int(L), renorm, norm2,
+                                          step_len, st),
                 "sparse preparation");
     else
-        HY_CUDA(hy::k::sv_prepare<float>(svec<float>(s), o, ops, cs, int(L), renorm, norm2, st),
+        HY_CUDA(hy::k::sv_prepare<float>(svec<float>(s), o, ops, cs, int(L), renorm, norm2,
+                                         step_len, st),
                 "sparse preparation");
+    return HY_OK;
+}
+
+struct SupportProgram {
+    const hy_ham *h = nullptr;
+    int max_steps = 0;
+    int64_t m = 0, steps = 0;
+    int64_t *key = nullptr, *step_len = nullptr;
+    int32_t *tab = nullptr;
+    int *flag = nullptr;
+};
+
+hy_status prog_create(const hy_ham *h, int max_steps, SupportProgram **out)
+{
+    if (!h || !out || max_steps < 1 || max_steps > 254) return fail(HY_ERR_ARG, "bad arguments");
+    *out = nullptr;
+    SupportProgram *g = new (std::nothrow) SupportProgram;
+    if (!g) return fail(HY_ERR_OOM, "host allocation failed");
+    g->h = h;
+    g->max_steps = max_steps;
+    cudaError_t e = cudaMalloc(&g->key, size_t(hy::k::kProgMax) * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&g->step_len, size_t(max_steps) * sizeof(int64_t));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&g->tab, size_t(max_steps) * hy::k::kProgMax * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&g->flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(g->flag, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        prog_destroy(g);
+        return cuda_fail(e, "cudaMalloc(support program)");
+    }
+    *out = g;
+    return HY_OK;
+}
+
+void prog_destroy(SupportProgram *g)
+{
+    if (!g) return;
+    cudaFree(g->key);
+    cudaFree(g->step_len);
+    cudaFree(g->tab);
+    cudaFree(g->flag);
+    delete g;
+}
+
+int64_t *prog_step_len(SupportProgram *g) { return g->step_len; }
+const int *prog_flag(const SupportProgram *g) { return g->flag; }
+
+int64_t prog_steps(const hy_pool *p, const int32_t *ops_host, int64_t L)
+{
+    int64_t s = 0;
+    for (int64_t l = 0; l < L; ++l) s += p->ops[size_t(ops_host[l])].desc[0];
+    return s;
+}
+
+namespace {
+hy::k::SvOpArgs sv_op_args(const hy_ham *h, const hy_pool *p)
+{
+    hy::k::SvOpArgs o;
+    o.desc = p->d_desc;
+    o.astr = h->d_astr;
+    o.bstr = h->d_bstr;
+    o.binom33 = h->d_binom;
+    o.n = h->n;
+    o.Nb = h->Nb;
+    return o;
+}
+}  // namespace
+
+hy_status prog_compile(SupportProgram *g, const SparseState *s, int64_t m, const hy_pool *p,
+                       const int32_t *ops, int64_t L, int64_t steps, void *stream)
+{
+    if (!g || !s || !p || p->h != g->h || s->h != g->h || !ops || L < 1 || m < 1 ||
+        m > hy::k::kProgMax || m > s->cap || steps < 1 || steps > g->max_steps)
+        return fail(HY_ERR_ARG, "bad arguments");
+    cudaStream_t st = as_stream(stream);
+    hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
+    HY_CUDA(hy::k::prog_compile(s->list, m, g->step_len, int(steps), sv_op_args(g->h, p), ops,
+                                int(L), g->key, g->tab, g->flag, st),
+            "support program");
+    g->m = m;
+    g->steps = steps;
+    return HY_OK;
+}
+
+hy_status prog_prepare(const SupportProgram *g, SparseState *s, const hy_pool *p,
+                       const int32_t *ops, const double *cs, int64_t L, bool renorm,
+                       double *norm2, void *stream)
+{
+    if (!g || !s || !p || p->h != g->h || s->h != g->h || !ops || !cs || L < 1 || g->m < 1)
+        return fail(HY_ERR_ARG, "bad arguments");
+    cudaStream_t st = as_stream(stream);
+    hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
+    if (s->dt == HY_F64)
+        HY_CUDA(hy::k::prog_prepare<double>(g->key, g->tab, g->m, p->d_desc, ops, cs, int(L),
+                                            renorm, norm2, static_cast<double *>(s->v), st),
+                "support program preparation");
+    else
+        HY_CUDA(hy::k::prog_prepare<float>(g->key, g->tab, g->m, p->d_desc, ops, cs, int(L),
+                                           renorm, norm2, static_cast<float *>(s->v), st),
+                "support program preparation");
+    return HY_OK;
+}
+
+hy_status prog_grad(const SupportProgram *g, const hy_pool *p, const int32_t *ops,
+                    const double *cs, int64_t L, const void *sigma, hy_dtype dt,
+                    const double *norm2, double *g_out, void *stream)
+{
+    if (!g || !p || p->h != g->h || !ops || !cs || L < 1 || !sigma || !g_out || g->m < 1 ||
+        !valid_dtype(dt))
+        return fail(HY_ERR_ARG, "bad arguments");
+    cudaStream_t st = as_stream(stream);
+    hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
+    if (dt == HY_F64)
+        HY_CUDA(hy::k::prog_grad<double>(g->key, g->tab, g->m, p->d_desc, ops, cs, int(L),
+                                         static_cast<const double *>(sigma), norm2, g_out, st),
+                "support program gradient");
+    else
+        HY_CUDA(hy::k::prog_grad<float>(g->key, g->tab, g->m, p->d_desc, ops, cs, int(L),
+                                        static_cast<const float *>(sigma), norm2, g_out, st),
+                "support program gradient");
     return HY_OK;
 }
 

@@ -156,7 +156,32 @@ hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double thet
 // the FP64 norm over the support.  For small supports (one launch instead of
 // two per constituent); the state must be clean.
 hy_status sstate_prepare(SparseState *s, const hy_pool *p, const int32_t *ops, const double *cs,
-                         int64_t L, bool renorm, double *norm2, void *stream);
+                         int64_t L, bool renorm, double *norm2, void *stream,
+                         int64_t *step_len = nullptr);
+// Support program of a fixed ansatz (see prog_compile in hy_kernels.cuh): the
+// rotations as pairings of the support's elements, compiled once per ansatz
+// from a structural sstate_prepare (with step_len = prog_step_len(g)) and
+// then run on m-vectors in shared memory.
+struct SupportProgram;
+hy_status prog_create(const hy_ham *h, int max_steps, SupportProgram **out);
+void prog_destroy(SupportProgram *g);
+int64_t *prog_step_len(SupportProgram *g);           // device, max_steps entries
+const int *prog_flag(const SupportProgram *g);        // device, set by prog_compile
+// constituent rotations of ops[0..L) (host array), i.e. the program's steps
+int64_t prog_steps(const hy_pool *p, const int32_t *ops_host, int64_t L);
+// compile from s (whose support, m <= 4096 elements, was just listed by a
+// structural sstate_prepare of ops[0..L) (device) with step_len)
+hy_status prog_compile(SupportProgram *g, const SparseState *s, int64_t m, const hy_pool *p,
+                       const int32_t *ops, int64_t L, int64_t steps, void *stream);
+// s.v on the program's support = U_L .. U_1|HF> (renormalised as
+// sstate_prepare); s's list and bits, which hold that support, are kept
+hy_status prog_prepare(const SupportProgram *g, SparseState *s, const hy_pool *p,
+                       const int32_t *ops, const double *cs, int64_t L, bool renorm,
+                       double *norm2, void *stream);
+// g_out[l] = dE/dtheta_l in forward mode (as sstate_grad_forward)
+hy_status prog_grad(const SupportProgram *g, const hy_pool *p, const int32_t *ops,
+                    const double *cs, int64_t L, const void *sigma, hy_dtype dt,
+                    const double *norm2, double *g_out, void *stream);
 // In one CTA, for small supports: g[l] (device) = dE/dtheta_l in forward mode
 // (dE/dtheta_l = 2 <sigma| U_L .. U_{l+1} A_l U_l .. U_1 |HF>), with f and w
 // clean scratch sparse vectors, sigma = H psi (dense), ops / cs as for

@@ -286,10 +286,44 @@ cudaError_t sv_excite(const SVec<T> &x, const SvOpArgs &o, int k, int nc, double
                       int num_sms, cudaStream_t st);
 // one CTA: clear x's support, |HF>, every constituent rotation of ops[0..L)
 // with cs[2l], cs[2l+1] = cos, sin theta_l, then (renorm) divide by the FP64
-// norm over the support (written to *norm2 if not null); for small supports
+// norm over the support (written to *norm2 if not null); for small supports.
+// step_len (device, or null): the list's length after each constituent
+// rotation, in order
 template <typename T>
 cudaError_t sv_prepare(const SVec<T> &x, const SvOpArgs &o, const int32_t *ops, const double *cs,
-                       int L, bool renorm, double *norm2, cudaStream_t st);
+                       int L, bool renorm, double *norm2, int64_t *step_len, cudaStream_t st);
+
+// Support programs (hy_sparse.cu).  The support of U_L .. U_1|HF> is fixed by
+// the ansatz (a rotation lists its partners whatever its angle), so once it
+// is known each constituent rotation is a fixed pairing of its elements:
+//   key[t]  = (determinant << 8) | (step that listed it + 1), ascending over
+//             the m <= kProgMax support elements (t = local index);
+//   tab[s*m + t] = +-(p + 1) when step s's forward string takes t to p with
+//             sign +-1 and p is in the support, else 0;
+//   *flag   = 1 when some generator A_l = sum (C - C^dagger) of op l would
+//             leave the support from an element that op l's own later
+//             constituents listed (then the forward gradient cannot use the
+//             tables and must take the general path).
+constexpr int kProgMax = 4096;
+// list: the m support elements in the order a structural sv_prepare listed
+// them, step_len its lengths after each of the `steps` rotations
+cudaError_t prog_compile(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
+                         const SvOpArgs &o, const int32_t *ops, int L, int64_t *key,
+                         int32_t *tab, int *flag, cudaStream_t st);
+// one CTA: the m-vector U_L .. U_1|HF> by the tables in shared memory, then
+// (renorm) divided by its FP64 norm (*norm2, if not null), written to
+// v[key[t] >> 8]; v outside the support is left as is
+template <typename T>
+cudaError_t prog_prepare(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
+                         const int32_t *ops, const double *cs, int L, bool renorm, double *norm2,
+                         T *v, cudaStream_t st);
+// L CTAs: g[l] = dE/dtheta_l in forward mode by the tables, CTA l forming
+// U_L .. U_{l+1} A_l U_l .. U_1|HF> in shared memory and reading sigma (dense)
+// on the support; norm2 as for sv_grad_fwd
+template <typename T>
+cudaError_t prog_grad(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
+                      const int32_t *ops, const double *cs, int L, const T *sigma,
+                      const double *norm2, double *g, cudaStream_t st);
 // one CTA: g[l] = dE/dtheta_l of psi = U_L .. U_1|HF> in forward mode, f and
 // w scratch sparse vectors (clean), sigma = H psi dense; norm2 (device, or
 // null): psi was divided by sqrt(*norm2), so the gradient is too

@@ -511,11 +511,14 @@ __device__ double blk_dot(const SVec<T> &x, const T *y, int64_t m, double *red)
 // The whole state preparation of a small support in one CTA: clear the
 // previous support, set |HF>, apply every constituent rotation of the
 // ansatz in order, and for float states divide by the FP64 norm over the
-// support.  cs[2l], cs[2l+1] = cos, sin theta_l.
+// support.  cs[2l], cs[2l+1] = cos, sin theta_l.  step_len (optional): the
+// list's length after each constituent rotation (the list only grows, so
+// these date every listed determinant to the rotation that listed it).
 template <typename T>
 __global__ void __launch_bounds__(kPrepThreads)
 k_sv_prepare(SVec<T> x, SvOpArgs o, const int32_t *__restrict__ ops,
-             const double *__restrict__ cs, int L, int renorm, double *__restrict__ norm2)
+             const double *__restrict__ cs, int L, int renorm, double *__restrict__ norm2,
+             int64_t *__restrict__ step_len)
 {
     __shared__ uint32_t C[33][33];
     __shared__ unsigned long long m_sh;
@@ -528,11 +531,17 @@ k_sv_prepare(SVec<T> x, SvOpArgs o, const int32_t *__restrict__ ops,
         x.v[0] = T(1);
         blk_list(x, 0);
     }
+    int step = 0;
     for (int l = 0; l < L; ++l) {
         const int k = ops[l];
         const int nc = o.desc[11 * k];
-        for (int ci = 0; ci < nc; ++ci)
+        for (int ci = 0; ci < nc; ++ci, ++step) {
             blk_rotate(x, o, k, ci, T(cs[2 * l]), T(cs[2 * l + 1]), C, &m_sh);
+            if (step_len) {
+                const int64_t ml = blk_len(x, &m_sh);
+                if (tid == 0) step_len[step] = ml;
+            }
+        }
     }
     const int64_t m = blk_len(x, &m_sh);
     if (tid == 0) {                 // leave the snapshot consistent for later rotations
@@ -640,6 +649,245 @@ k_sv_scale(SVec<T> x, const double *__restrict__ norm2)
         x.v[x.list[t]] *= f;
 }
 
+// ---------------------------------------------------------------------------
+// Support programs: the rotations of a fixed ansatz as pairings of the
+// support's elements (local indices), so that every evaluation of one ADAPT
+// iteration runs on m-vectors in shared memory, with no string ranking,
+// membership tests or list appends.
+// ---------------------------------------------------------------------------
+constexpr int kProgThreads = 512;
+
+// key[0..m) = (determinant << 8) | birth, ascending, birth = 0 for |HF> and
+// s + 1 for an element listed by rotation step s (from the list's lengths
+// after each step).  One CTA, bitonic sort over the next power of two.
+__global__ void __launch_bounds__(1024)
+k_prog_sort(const int64_t *__restrict__ list, int64_t m, const int64_t *__restrict__ step_len,
+            int steps, int64_t *__restrict__ key)
+{
+    __shared__ int64_t kk[kProgMax];
+    int P = 1;
+    while (P < m) P <<= 1;
+    for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        int64_t v = INT64_MAX;
+        if (t < m) {
+            int lo = 0, hi = steps;                  // first step whose length exceeds t
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (int64_t(t) < step_len[mid]) hi = mid;
+                else lo = mid + 1;
+            }
+            v = (list[t] << 8) | int64_t(t == 0 ? 0 : lo + 1);
+        }
+        kk[t] = v;
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < P; t += blockDim.x) {
+                const int u = t ^ j;
+                if (u > t) {
+                    const int64_t a = kk[t], b = kk[u];
+                    if ((a > b) == ((t & k) == 0)) {
+                        kk[t] = b;
+                        kk[u] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int t = threadIdx.x; t < m; t += blockDim.x) key[t] = kk[t];
+}
+
+// local index of determinant d in the sorted keys, or -1
+__device__ __forceinline__ int prog_find(const int64_t *__restrict__ key, int m, int64_t d)
+{
+    int lo = 0, hi = m;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((key[mid] >> 8) < d) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < m && (key[lo] >> 8) == d ? lo : -1;
+}
+
+// tab[s*m + t] for step s = blockIdx.y (constituent ci of op l)
+__global__ void __launch_bounds__(256)
+k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t *__restrict__ ops,
+              int L, int32_t *__restrict__ tab, int *__restrict__ flag)
+{
+    __shared__ uint32_t C[33][33];
+    for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
+    __syncthreads();
+    const int s = blockIdx.y;
+    int l = 0, ci = 0, last = -1, acc = 0;
+    for (; l < L; ++l) {
+        const int nc = o.desc[11 * ops[l]];
+        if (s < acc + nc) {
+            ci = s - acc;
+            last = acc + nc - 1;
+            break;
+        }
+        acc += nc;
+    }
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m || l >= L) return;
+    int fw[4], bw[4], len;
+    op_strings(o.desc + 11 * ops[l] + 1 + 5 * ci, fw, bw, len);
+    const int64_t kt = key[t], d = kt >> 8;
+    const int birth = int(kt & 255) - 1;             // -1: |HF>, else the listing step
+    const int n = o.n;
+    const uint64_t lowm = (1ull << n) - 1;
+    const uint64_t mask = uint64_t(o.astr[d / o.Nb]) | (uint64_t(o.bstr[d % o.Nb]) << n);
+    uint64_t u = mask;
+    int sg = 1;
+    int32_t e = 0;
+    bool escape = false;
+    if (apply_string(fw, len, u, sg)) {
+        const int64_t img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+        const int p = prog_find(key, m, img);
+        if (p >= 0) e = sg > 0 ? p + 1 : -(p + 1);
+        else escape = true;
+    } else {
+        u = mask;
+        sg = 1;
+        if (apply_string(bw, len, u, sg)) {
+            const int64_t dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+            escape = prog_find(key, m, dom) < 0;
+        }
+    }
+    tab[int64_t(s) * m + t] = e;
+    // a partner outside the support is harmless to the rotations (both ends
+    // are zero when step s runs) but not to op l's generator when t is in
+    // phi_l's support without having been seen by step s: listed later by
+    // op l's own constituents
+    if (escape && birth > s && birth <= last) *flag = 1;
+}
+
+// one constituent rotation on a local vector (pairs are disjoint: an image
+// end has no forward image)
+template <typename T>
+__device__ __forceinline__ void prog_rotate(T *x, const int32_t *__restrict__ row, int m, T c, T sn)
+{
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const int e = row[t];
+        if (e == 0) continue;
+        const int p = (e > 0 ? e : -e) - 1;
+        const T ss = e > 0 ? sn : -sn;
+        const T xv = x[t], yv = x[p];
+        x[t] = c * xv - ss * yv;
+        x[p] = c * yv + ss * xv;
+    }
+    __syncthreads();
+}
+
+// w <- w + (C - C^dagger) f for one constituent: C|t> = sg|p> adds sg f_t to
+// w_p and -sg f_p to w_t
+template <typename T>
+__device__ __forceinline__ void prog_generator(const T *f, T *w, const int32_t *__restrict__ row,
+                                               int m)
+{
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const int e = row[t];
+        if (e == 0) continue;
+        const int p = (e > 0 ? e : -e) - 1;
+        const T ft = f[t], fp = f[p];
+        if (e > 0) {
+            w[p] += ft;
+            w[t] -= fp;
+        } else {
+            w[p] -= ft;
+            w[t] += fp;
+        }
+    }
+    __syncthreads();
+}
+
+// FP64 block sum, valid in thread 0
+__device__ __forceinline__ double prog_block_sum(double acc, double *red)
+{
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kProgThreads)
+k_prog_prepare(const int64_t *__restrict__ key, const int32_t *__restrict__ tab, int m,
+               const int32_t *__restrict__ desc, const int32_t *__restrict__ ops,
+               const double *__restrict__ cs, int L, int renorm, double *__restrict__ norm2,
+               T *__restrict__ v)
+{
+    extern __shared__ __align__(16) unsigned char prog_sm[];
+    T *x = reinterpret_cast<T *>(prog_sm);
+    __shared__ double red[kProgThreads / 32];
+    __shared__ double fac;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) x[t] = t == 0 ? T(1) : T(0);   // |HF>
+    __syncthreads();
+    int s = 0;
+    for (int l = 0; l < L; ++l) {
+        const int nc = desc[11 * ops[l]];
+        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
+        for (int ci = 0; ci < nc; ++ci, ++s) prog_rotate(x, tab + int64_t(s) * m, m, c, sn);
+    }
+    if (renorm) {
+        double acc = 0.0;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) acc = fma(double(x[t]), double(x[t]), acc);
+        const double sum = prog_block_sum(acc, red);
+        if (threadIdx.x == 0) {
+            if (norm2) *norm2 = sum;
+            fac = 1.0 / sqrt(sum);
+        }
+        __syncthreads();
+        const T f = T(fac);
+        for (int t = threadIdx.x; t < m; t += blockDim.x) v[key[t] >> 8] = x[t] * f;
+    } else {
+        for (int t = threadIdx.x; t < m; t += blockDim.x) v[key[t] >> 8] = x[t];
+    }
+}
+
+// CTA l: g[l] = scale <sigma| U_L .. U_{l+1} A_l U_l .. U_1 |HF>
+template <typename T>
+__global__ void __launch_bounds__(kProgThreads)
+k_prog_grad(const int64_t *__restrict__ key, const int32_t *__restrict__ tab, int m,
+            const int32_t *__restrict__ desc, const int32_t *__restrict__ ops,
+            const double *__restrict__ cs, int L, const T *__restrict__ sigma,
+            const double *__restrict__ norm2, double *__restrict__ g)
+{
+    extern __shared__ __align__(16) unsigned char prog_sm[];
+    T *f = reinterpret_cast<T *>(prog_sm), *w = f + m;
+    __shared__ double red[kProgThreads / 32];
+    const int lg = blockIdx.x;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        f[t] = t == 0 ? T(1) : T(0);
+        w[t] = T(0);
+    }
+    __syncthreads();
+    int s = 0;
+    for (int l = 0; l <= lg; ++l) {                  // phi_lg = U_lg .. U_1 |HF>
+        const int nc = desc[11 * ops[l]];
+        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
+        for (int ci = 0; ci < nc; ++ci, ++s) prog_rotate(f, tab + int64_t(s) * m, m, c, sn);
+    }
+    const int ncg = desc[11 * ops[lg]];
+    for (int ci = 0; ci < ncg; ++ci)                 // constituents add in order
+        prog_generator(f, w, tab + int64_t(s - ncg + ci) * m, m);
+    for (int l = lg + 1; l < L; ++l) {
+        const int nc = desc[11 * ops[l]];
+        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
+        for (int ci = 0; ci < nc; ++ci, ++s) prog_rotate(w, tab + int64_t(s) * m, m, c, sn);
+    }
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < m; t += blockDim.x)
+        acc = fma(double(w[t]), double(sigma[key[t] >> 8]), acc);
+    const double dot = prog_block_sum(acc, red);
+    if (threadIdx.x == 0) g[lg] = (norm2 ? 2.0 / sqrt(*norm2) : 2.0) * dot;
+}
+
 namespace {
 // blocks for a list of about n entries (grid-stride loops cover any count)
 unsigned sv_grid(int64_t n, int num_sms)
@@ -687,9 +935,9 @@ cudaError_t sv_excite(const SVec<T> &x, const SvOpArgs &o, int k, int nc, double
 
 template <typename T>
 cudaError_t sv_prepare(const SVec<T> &x, const SvOpArgs &o, const int32_t *ops, const double *cs,
-                       int L, bool renorm, double *norm2, cudaStream_t st)
+                       int L, bool renorm, double *norm2, int64_t *step_len, cudaStream_t st)
 {
-    k_sv_prepare<T><<<1, kPrepThreads, 0, st>>>(x, o, ops, cs, L, renorm ? 1 : 0, norm2);
+    k_sv_prepare<T><<<1, kPrepThreads, 0, st>>>(x, o, ops, cs, L, renorm ? 1 : 0, norm2, step_len);
     hy::count_launch();
     return cudaGetLastError();
 }
@@ -761,6 +1009,67 @@ cudaError_t grad_sparse(const SparseGradArgs<T> &a, int num_sms, cudaStream_t st
     return cudaGetLastError();
 }
 
+cudaError_t prog_compile(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
+                         const SvOpArgs &o, const int32_t *ops, int L, int64_t *key,
+                         int32_t *tab, int *flag, cudaStream_t st)
+{
+    if (m < 1 || m > kProgMax || steps < 1 || steps > 254) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_prog_sort<<<1, 1024, 0, st>>>(list, m, step_len, steps, key); hy::count_launch();
+    k_prog_tables<<<dim3(unsigned((m + 255) / 256), unsigned(steps)), 256, 0, st>>>(
+        key, int(m), o, ops, L, tab, flag);
+    hy::count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t prog_prepare(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
+                         const int32_t *ops, const double *cs, int L, bool renorm, double *norm2,
+                         T *v, cudaStream_t st)
+{
+    if (m < 1 || m > kProgMax) return cudaErrorInvalidValue;
+    k_prog_prepare<T><<<1, kProgThreads, size_t(m) * sizeof(T), st>>>(key, tab, int(m), desc, ops,
+                                                                      cs, L, renorm ? 1 : 0,
+                                                                      norm2, v);
+    hy::count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t prog_grad(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
+                      const int32_t *ops, const double *cs, int L, const T *sigma,
+                      const double *norm2, double *g, cudaStream_t st)
+{
+    if (m < 1 || m > kProgMax || L < 1) return cudaErrorInvalidValue;
+    const size_t smem = 2 * size_t(m) * sizeof(T);
+    static bool attr = false;                        // up to 64 KB of dynamic shared memory
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k_prog_grad<T>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   int(2 * kProgMax * sizeof(T)));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_prog_grad<T><<<unsigned(L), kProgThreads, smem, st>>>(key, tab, int(m), desc, ops, cs, L,
+                                                            sigma, norm2, g);
+    hy::count_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t prog_prepare<double>(const int64_t *, const int32_t *, int64_t,
+                                          const int32_t *, const int32_t *, const double *, int,
+                                          bool, double *, double *, cudaStream_t);
+template cudaError_t prog_prepare<float>(const int64_t *, const int32_t *, int64_t,
+                                         const int32_t *, const int32_t *, const double *, int,
+                                         bool, double *, float *, cudaStream_t);
+template cudaError_t prog_grad<double>(const int64_t *, const int32_t *, int64_t, const int32_t *,
+                                       const int32_t *, const double *, int, const double *,
+                                       const double *, double *, cudaStream_t);
+template cudaError_t prog_grad<float>(const int64_t *, const int32_t *, int64_t, const int32_t *,
+                                      const int32_t *, const double *, int, const float *,
+                                      const double *, double *, cudaStream_t);
+
 template cudaError_t support<double>(const double *, int64_t, int64_t *, int64_t,
                                      unsigned long long *, int, cudaStream_t);
 template cudaError_t support<float>(const float *, int64_t, int64_t *, int64_t,
@@ -775,7 +1084,8 @@ template cudaError_t grad_sparse<float>(const SparseGradArgs<float> &, int, cuda
     template cudaError_t sv_excite<T>(const SVec<T> &, const SvOpArgs &, int, int, double,  \
                                       int, cudaStream_t);                                    \
     template cudaError_t sv_prepare<T>(const SVec<T> &, const SvOpArgs &, const int32_t *,  \
-                                       const double *, int, bool, double *, cudaStream_t);  \
+                                       const double *, int, bool, double *, int64_t *,      \
+                                       cudaStream_t);                                        \
     template cudaError_t sv_grad_fwd<T>(const SVec<T> &, const SVec<T> &, const SvOpArgs &, \
                                         const int32_t *, const double *, int, const T *,    \
                                         const double *, double *, cudaStream_t);            \
