@@ -152,8 +152,9 @@ hy_status finish_energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt)
 
 // last support up to which one CTA prepares the sparse state (its 1,024
 // threads then take at most a few dozen entries each per rotation, even
-// after a new operator quadruples the support)
-const int64_t kPrepareSmall = 4096;
+// after a new operator quadruples the support); also the largest support a
+// support program holds (its vectors live in shared memory)
+const int64_t kPrepareSmall = 12288;
 
 // The sparse evaluation: psi = U(theta)|HF> as a sparse vector (rotations
 // cost O(support)), renormalised over its support in double (float states),

@@ -304,7 +304,7 @@ cudaError_t sv_prepare(const SVec<T> &x, const SvOpArgs &o, const int32_t *ops, 
 //             leave the support from an element that op l's own later
 //             constituents listed (then the forward gradient cannot use the
 //             tables and must take the general path).
-constexpr int kProgMax = 4096;
+constexpr int kProgMax = 12288;   // shared-memory vectors: 2 x 12288 doubles per CTA
 // list: the m support elements in the order a structural sv_prepare listed
 // them, step_len its lengths after each of the `steps` rotations
 cudaError_t prog_compile(const int64_t *list, int64_t m, const int64_t *step_len, int steps,

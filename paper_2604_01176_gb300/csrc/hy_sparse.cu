@@ -659,12 +659,16 @@ constexpr int kProgThreads = 512;
 
 // key[0..m) = (determinant << 8) | birth, ascending, birth = 0 for |HF> and
 // s + 1 for an element listed by rotation step s (from the list's lengths
-// after each step).  One CTA, bitonic sort over the next power of two.
+// after each step).  One CTA, bitonic sort over the next power of two (P
+// keys of dynamic shared memory).
+constexpr int kProgSortMax = 16384;   // the power of two >= kProgMax
+static_assert(kProgSortMax >= kProgMax, "sort buffer");
+
 __global__ void __launch_bounds__(1024)
 k_prog_sort(const int64_t *__restrict__ list, int64_t m, const int64_t *__restrict__ step_len,
             int steps, int64_t *__restrict__ key)
 {
-    __shared__ int64_t kk[kProgMax];
+    extern __shared__ __align__(16) int64_t kk[];
     int P = 1;
     while (P < m) P <<= 1;
     for (int t = threadIdx.x; t < P; t += blockDim.x) {
@@ -1014,9 +1018,19 @@ cudaError_t prog_compile(const int64_t *list, int64_t m, const int64_t *step_len
                          int32_t *tab, int *flag, cudaStream_t st)
 {
     if (m < 1 || m > kProgMax || steps < 1 || steps > 254) return cudaErrorInvalidValue;
+    static bool attr = false;                        // up to 128 KB of dynamic shared memory
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            k_prog_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kProgSortMax * 8));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    k_prog_sort<<<1, 1024, 0, st>>>(list, m, step_len, steps, key); hy::count_launch();
+    int64_t P = 1;
+    while (P < m) P <<= 1;
+    k_prog_sort<<<1, 1024, size_t(P) * 8, st>>>(list, m, step_len, steps, key);
+    hy::count_launch();
     k_prog_tables<<<dim3(unsigned((m + 255) / 256), unsigned(steps)), 256, 0, st>>>(
         key, int(m), o, ops, L, tab, flag);
     hy::count_launch();
@@ -1029,6 +1043,14 @@ cudaError_t prog_prepare(const int64_t *key, const int32_t *tab, int64_t m, cons
                          T *v, cudaStream_t st)
 {
     if (m < 1 || m > kProgMax) return cudaErrorInvalidValue;
+    static bool attr = false;                        // up to 96 KB of dynamic shared memory
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k_prog_prepare<T>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   int(kProgMax * sizeof(T)));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     k_prog_prepare<T><<<1, kProgThreads, size_t(m) * sizeof(T), st>>>(key, tab, int(m), desc, ops,
                                                                       cs, L, renorm ? 1 : 0,
                                                                       norm2, v);
@@ -1043,7 +1065,7 @@ cudaError_t prog_grad(const int64_t *key, const int32_t *tab, int64_t m, const i
 {
     if (m < 1 || m > kProgMax || L < 1) return cudaErrorInvalidValue;
     const size_t smem = 2 * size_t(m) * sizeof(T);
-    static bool attr = false;                        // up to 64 KB of dynamic shared memory
+    static bool attr = false;                        // up to 192 KB of dynamic shared memory
     if (!attr) {
         const cudaError_t e = cudaFuncSetAttribute(k_prog_grad<T>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
