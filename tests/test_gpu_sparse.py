@@ -93,6 +93,11 @@ def test_sparse_path_matches_oracle_and_dense(cfg):
         S = sparse_h(ham, P, lst, m)
         s_ref = ref.sigma(psi)
         assert np.abs(S.cpu().numpy() - s_ref).max() < 1e-12
+        # listed zero amplitudes change nothing
+        zeros = np.setdiff1d(np.arange(len(psi)), np.nonzero(psi)[0])[:5]
+        lz = torch.cat([lst[:m], torch.from_numpy(zeros).cuda()])
+        Sz = sparse_h(ham, P, lz, lz.numel())
+        assert np.abs(Sz.cpu().numpy() - s_ref).max() < 1e-12
         g = sparse_g(ham, pool, P, S, lst, m).cpu().numpy()
         g_ref = ref.gradients(ref.pool(), psi, s_ref)
         assert np.abs(g - g_ref).max() < 1e-11
