@@ -81,63 +81,72 @@ __device__ __forceinline__ void emit(const SparseArgs<T> &a, int64_t o, T v)
     if (pos < (unsigned long long)a.ocap) a.olist[pos] = o;
 }
 
-// one CTA per support entry (grid-stride)
+// One CTA per support entry (grid-stride).  The alpha-beta part's targets
+// form a (1 + s_a) x (1 + s_b) grid: a thread keeps one beta excitation f
+// (its target column, orbitals and sign in registers) and walks a stride of
+// the alpha excitations, staged once per entry in shared memory, so the
+// inner loop is one table read, one V load and one atomic add; the
+// no-excitation row and column (diagonal sums) are taken apart.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_hpsi_scatter(SparseArgs<T> a)
 {
-    const int n = a.n, nn = n * n;
+    __shared__ uint32_t aexs[64];
+    const int n = a.n, nn = n * n, nexa = a.nexa, nexb = a.nexb;
     const int64_t Nb = a.Nb;
-    const int ne = a.nexa + 1, nf = a.nexb + 1;
     const int64_t m = list_len(a.d_m, a.m, a.cap);
+    // beta slot and alpha phase of this thread
+    const int P = nexb > 0 ? int(blockDim.x) / nexb : 0;
+    const bool slot = int(threadIdx.x) < P * nexb;
+    const int fs = slot ? int(threadIdx.x) % nexb : 0, ph = slot ? int(threadIdx.x) / nexb : 0;
     for (int64_t t = blockIdx.x; t < m; t += gridDim.x) {
         const int64_t d = a.list[t];
         const T x = a.psi[d];
         const int64_t A = d / Nb, B = d % Nb;
+        __syncthreads();                              // the previous entry's readers are done
+        if (int(threadIdx.x) < nexa) aexs[threadIdx.x] = a.aex[A * nexa + threadIdx.x];
         for (int k = a.Ma_ptr[A] + threadIdx.x; k < a.Ma_ptr[A + 1]; k += blockDim.x)
             emit(a, int64_t(a.Ma_col[k]) * Nb + B, a.Ma_val[k] * x);
         for (int k = a.Mb_ptr[B] + threadIdx.x; k < a.Mb_ptr[B + 1]; k += blockDim.x)
             emit(a, A * Nb + a.Mb_col[k], a.Mb_val[k] * x);
+        __syncthreads();
         const uint32_t am = a.astr[A], bm = a.bstr[B];
-        for (int idx = threadIdx.x; idx < ne * nf; idx += blockDim.x) {
-            const int e = idx / nf - 1, f = idx % nf - 1;
-            int64_t Ao = A, Bo = B;
-            int p = 0, q = 0, r = 0, s = 0;
-            bool neg = false;
-            if (e >= 0) {   // output alpha string: A with its entry e applied
-                const uint32_t u = a.aex[A * a.nexa + e];
-                Ao = u & 0xFFFFu;
-                p = (u >> 20) & 15;   // created on the output (held by Ao)
-                q = (u >> 16) & 15;   // held by A
-                neg ^= (u >> 31) != 0;
+        if (slot) {
+            const uint32_t w = a.bexT[size_t(fs) * Nb + B];
+            const int64_t Bo = w & 0xFFFFu;
+            const int rs = int((w >> 20) & 15) * n + int((w >> 16) & 15);
+            const bool negb = (w >> 31) != 0;
+            if (ph == 0) {                            // no alpha excitation
+                const T c = sum_diag<T>(a.V, n, nn, am, rs);
+                emit(a, A * Nb + Bo, (negb ? -c : c) * x);
             }
-            if (f >= 0) {
-                const uint32_t w = a.bexT[size_t(f) * Nb + B];
-                Bo = w & 0xFFFFu;
-                r = (w >> 20) & 15;
-                s = (w >> 16) & 15;
-                neg ^= (w >> 31) != 0;
+            const T *Vrs = a.V + rs;
+            for (int e = ph; e < nexa; e += P) {
+                const uint32_t u = aexs[e];
+                const int64_t Ao = u & 0xFFFFu;
+                const int pq = int((u >> 20) & 15) * n + int((u >> 16) & 15);
+                const T c = Vrs[size_t(pq) * nn];
+                emit(a, Ao * Nb + Bo, (negb != ((u >> 31) != 0) ? -c : c) * x);
             }
-            T c;
-            if (e >= 0 && f >= 0) {
-                c = a.V[size_t(p * n + q) * nn + r * n + s];
-            } else if (e >= 0) {
-                c = T(0);
-                for (uint32_t m = bm; m; m &= m - 1) {
-                    const int rr = __ffs(m) - 1;
-                    c += a.V[size_t(p * n + q) * nn + rr * n + rr];
-                }
-            } else if (f >= 0) {
-                c = sum_diag<T>(a.V, n, nn, am, r * n + s);
-            } else {
-                c = T(0);
-                for (uint32_t m = bm; m; m &= m - 1) {
-                    const int rr = __ffs(m) - 1;
+        }
+        // no beta excitation: the diagonal beta sum for each alpha excitation
+        for (int e = int(threadIdx.x) - 1; e < nexa; e += blockDim.x) {
+            T c = T(0);
+            if (e < 0) {
+                for (uint32_t mm = bm; mm; mm &= mm - 1) {
+                    const int rr = __ffs(mm) - 1;
                     c += sum_diag<T>(a.V, n, nn, am, rr * n + rr);
                 }
+                emit(a, A * Nb + B, c * x);
+            } else {
+                const uint32_t u = aexs[e];
+                const int pq = int((u >> 20) & 15) * n + int((u >> 16) & 15);
+                for (uint32_t mm = bm; mm; mm &= mm - 1) {
+                    const int rr = __ffs(mm) - 1;
+                    c += a.V[size_t(pq) * nn + rr * n + rr];
+                }
+                emit(a, int64_t(u & 0xFFFFu) * Nb + B, ((u >> 31) ? -c : c) * x);
             }
-            if (neg) c = -c;
-            emit(a, Ao * Nb + Bo, c * x);
         }
     }
 }
