@@ -505,6 +505,14 @@ def breakdown(prof, step_ms):
 # classes bound by arithmetic rather than HBM (the headline's bulk is float)
 ALU_CLASSES = ("hpsi",)
 
+# L2 reduction rate of the GB300 (5.61 M reduction sectors = 32.5 % of the
+# peak-sustained rate over a 45.8 us launch of k_hpsi_scatter under ncu) and
+# the rate of float atomic adds to pseudo-random addresses over 2 M targets
+# with the membership-bit test (paper_2604_01176_gb300/probes/l2_atomics.cu);
+# both in profiles/scatter_atomics_32q.md
+L2_RED_PEAK = 3.77e11
+L2_RANDOM_ADDS = 3.33e10
+
 
 def step_roofline(prof, peaks, peak_kind, fp32_peak):
     """Roofline of the kernel class with the most device time among those
@@ -537,6 +545,21 @@ def step_roofline(prof, peaks, peak_kind, fp32_peak):
                    peak_kind=f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)")
         if c in estimated:
             out["bytes_note"] = estimated[c]
+    if c == "hpsi_sparse" and v["flops"] > 0:
+        # the scatter is bound by its gathers and the L2 atomics, not by HBM:
+        # its atomic adds against the L2 reduction units' rate (derived from
+        # ncu's peak-sustained share of a captured launch) and a probe of
+        # pseudo-random adds over a sigma-sized footprint
+        adds = v["flops"] / (v["ms"] / 1e3)
+        out["l2_atomics"] = {
+            "adds_per_launch_est": round(v["flops"] / v["launches"]),
+            "achieved_adds_per_s": float(f"{adds:.4g}"),
+            "l2_red_peak_sectors_per_s": L2_RED_PEAK,
+            "frac_of_l2_red_peak": round(adds / L2_RED_PEAK, 4),
+            "probe_random_adds_per_s": L2_RANDOM_ADDS,
+            "note": "adds estimated as the couplings per amplitude x the support the host "
+                    "last read back; one add is one L2 reduction sector at most",
+            "source": "profiles/scatter_atomics_32q.md"}
     return out
 
 

@@ -1108,7 +1108,9 @@ hy_status hy_apply_h_sparse(const hy_ham *h, const void *psi, void *sigma, hy_dt
     if (!h || !psi || !sigma || !valid_dtype(dt) || m < 0 || (m > 0 && !list))
         return fail(HY_ERR_ARG, "bad arguments");
     if (psi == sigma) return fail(HY_ERR_ARG, "psi and sigma must not alias");
-    hy::ProfScope prof(HY_PROF_HPSI_SPARSE, stream, double(h->N) * (dt == HY_F64 ? 8 : 4));
+    // work: the atomic adds, at most one per coupling of a listed amplitude
+    hy::ProfScope prof(HY_PROF_HPSI_SPARSE, stream, double(h->N) * (dt == HY_F64 ? 8 : 4),
+                       double(m) * double(hy::ham_connections(h)));
     if (dt == HY_F64)
         HY_CUDA(hy::k::hpsi_scatter<double>(sparse_args<double>(h, psi, sigma, list, m), h->num_sms,
                                             as_stream(stream)), "sparse H psi");
@@ -1886,7 +1888,11 @@ hy_status sstate_apply_h(const SparseState *s, SparseState *sig, void *sigma, vo
 {
     cudaStream_t st = as_stream(stream);
     const hy_ham *h = s->h;
-    hy::ProfScope prof(HY_PROF_HPSI_SPARSE, stream, sig ? 0.0 : double(h->N) * (s->dt == HY_F64 ? 8 : 4));
+    // bytes: the clearing of sigma when its support is not listed; work: the
+    // atomic adds, at most one per coupling of a listed amplitude (from the
+    // support the host last read back)
+    hy::ProfScope prof(HY_PROF_HPSI_SPARSE, stream, sig ? 0.0 : double(h->N) * (s->dt == HY_F64 ? 8 : 4),
+                       double(s->hint) * double(hy::ham_connections(h)));
     if (sig && (sig->dt != s->dt || sig->v != sigma)) return fail(HY_ERR_ARG, "sigma state mismatch");
     auto out = [&](auto &a) {
         a.d_m = s->cnt;
