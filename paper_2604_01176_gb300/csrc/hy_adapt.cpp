@@ -91,6 +91,11 @@ struct hy_adapt {
                                          // (angles on the device for its theta)
     double *d_n2 = nullptr;       // tracked squared norm (float renormalisation)
     double *h_cs = nullptr, *d_cs = nullptr;   // cos, sin of the ansatz angles (pinned / device)
+    // pinned readback slots of an evaluation (energy, support counts, the
+    // ansatz gradient): its copies are queued and waited for once
+    void *h_pin = nullptr;
+    double *h_e = nullptr, *h_g = nullptr;
+    int64_t *h_cnt = nullptr;
     double *d_one = nullptr;      // device constants {1.0, 1.0f}
     // support program of the current ansatz (small supports): compiled from
     // the first structural preparation after an append, then run by every
@@ -224,13 +229,17 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     }
     HY_TRY(hy::sstate_dot(S, sigma, a->d_e, st));
     int64_t cnt[2] = {0, 0};
-    HY_TRY(xfer(a, e, a->d_e, sizeof(double), cudaMemcpyDeviceToHost, st, "energy readback"));
-    HY_TRY(xfer(a, &cnt[0], hy::sstate_count(S), sizeof(int64_t), cudaMemcpyDeviceToHost, st,
+    a->h_cnt[1] = 0;
+    HY_TRY(xfer(a, a->h_e, a->d_e, sizeof(double), cudaMemcpyDeviceToHost, st, "energy readback"));
+    HY_TRY(xfer(a, &a->h_cnt[0], hy::sstate_count(S), sizeof(int64_t), cudaMemcpyDeviceToHost, st,
                 "support count"));
     if (track)
-        HY_TRY(xfer(a, &cnt[1], hy::sstate_count(G), sizeof(int64_t), cudaMemcpyDeviceToHost, st,
-                    "support count"));
+        HY_TRY(xfer(a, &a->h_cnt[1], hy::sstate_count(G), sizeof(int64_t), cudaMemcpyDeviceToHost,
+                    st, "support count"));
     HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+    *e = a->h_e[0];
+    cnt[0] = a->h_cnt[0];
+    cnt[1] = a->h_cnt[1];
     *ok = cnt[0] <= hy::sstate_cap(S);
     if (!*ok) {
         a->ss_clean[d][0] = false;
@@ -345,9 +354,11 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
         // the support program's forward gradient: one CTA per angle
         HY_TRY(hy::prog_grad(a->prog, a->p, a->d_ops, a->d_cs, int64_t(j), a->buf[d][1], dt,
                              dt == HY_F32 ? a->d_n2 : nullptr, a->d_ga, st));
-        HY_TRY(xfer(a, g.data(), a->d_ga, j * sizeof(double), cudaMemcpyDeviceToHost, st,
+        HY_TRY(xfer(a, a->h_g, a->d_ga, j * sizeof(double), cudaMemcpyDeviceToHost, st,
                     "gradient readback"));
-        return cu(cudaStreamSynchronize(st), "sync");
+        HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+        std::copy(a->h_g, a->h_g + j, g.begin());
+        return HY_OK;
     }
     if (a->prep_small && a->sparse_m <= kPrepareSmall) {
         // small support: the whole gradient in forward mode in one launch
@@ -653,6 +664,13 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
     alloc(reinterpret_cast<void **>(&a->d_n2), 8);
     alloc(reinterpret_cast<void **>(&a->d_cs), size_t(c.max_iter) * 16);
     if (s == HY_OK) s = cu(cudaMallocHost(&a->h_cs, size_t(c.max_iter) * 16), "pinned angles");
+    if (s == HY_OK)
+        s = cu(cudaMallocHost(&a->h_pin, 64 + size_t(c.max_iter) * sizeof(double)), "pinned readbacks");
+    if (s == HY_OK) {
+        a->h_e = static_cast<double *>(a->h_pin);
+        a->h_cnt = reinterpret_cast<int64_t *>(static_cast<char *>(a->h_pin) + 16);
+        a->h_g = reinterpret_cast<double *>(static_cast<char *>(a->h_pin) + 64);
+    }
     alloc(reinterpret_cast<void **>(&a->d_one), 16);
     if (s == HY_OK) {
         unsigned char one[16] = {};
@@ -714,6 +732,7 @@ hy_status hy_adapt_destroy(hy_adapt *a)
     cudaFree(a->d_n2);
     cudaFree(a->d_cs);
     if (a->h_cs) cudaFreeHost(a->h_cs);
+    if (a->h_pin) cudaFreeHost(a->h_pin);
     cudaFree(a->d_one);
     for (auto &row : a->ss)
         for (hy::SparseState *&x : row) hy::sstate_destroy(x);

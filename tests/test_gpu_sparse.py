@@ -197,6 +197,35 @@ def test_sparse_state_evaluation_matches_oracle(cfg, cap):
         assert np.abs(psi - oadapt.prepare(ref, opd, o, t)).max() < 1e-12
 
 
+@pytest.mark.parametrize("cfg", [(7, 4, 3, 77), (8, 4, 4, 1005)])
+def test_support_program_reuse(cfg):
+    """One ansatz evaluated at several angles and in both precisions: the
+    first double evaluation lists the support and compiles it, the later ones
+    (new angles, then float, then double again) run on the compiled pairings;
+    every energy and gradient against the oracle."""
+    import oracle.adapt as oadapt
+    import paper_2604_01176_gb300 as hy
+    ref, ham, pool = system(*cfg)
+    opd = ref.pool()
+    ops, th = _ansatz(ref, 21, 7)
+    ad = hy.Adapt(ham, pool, "mixed", max_iter=16, sparse=True, sparse_cap=ham.n_det)
+    ad.set_ansatz(ops, th)
+    rng = np.random.default_rng(4)
+    for dt in (torch.float64, torch.float64, torch.float32, torch.float32, torch.float64):
+        t = th + rng.normal(0, 0.3, len(th))
+        e, g = ad.evaluate(t, dt)
+        e_ref, g_ref = oadapt.energy_and_gradient(ref, opd, ops, t)
+        if dt == torch.float64:
+            assert abs(e - e_ref) < 1e-10
+            assert np.abs(g - g_ref).max() < 1e-9
+        else:
+            assert abs(e - e_ref) < 2e-6 * max(1.0, abs(e_ref))
+            assert np.abs(g - g_ref).max() < 1e-4 * max(1.0, np.abs(g_ref).max())
+        psi = ad.state(dt).double().cpu().numpy()
+        tol = 1e-12 if dt == torch.float64 else 1e-5
+        assert np.abs(psi - oadapt.prepare(ref, opd, ops, t)).max() < tol
+
+
 @pytest.mark.parametrize("cfg", [(6, 3, 3, 1001), (8, 4, 4, 1005)])
 def test_sparse_state_float_evaluation(cfg):
     """Float sparse evaluation (support renormalised in double) against the
