@@ -104,6 +104,9 @@ struct hy_ham {
     // workspace (grown on demand; growth synchronises the device)
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    // row groups of a listed state for its touched weights (grown on demand,
+    // with a device synchronisation)
+    hy::k::TwGroups tw{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
     int dot_blocks = 0;
     // optional CUDA events around the alpha-beta coupling launch(es)
     bool prof = false;
@@ -616,6 +619,11 @@ hy_status hy_ham_destroy(hy_ham *h)
     if (h->h_status) cudaFreeHost(h->h_status);
     h->arena.release();
     if (h->ws) cudaFree(h->ws);
+    cudaFree(h->tw.cnt);
+    cudaFree(h->tw.ptr);
+    cudaFree(h->tw.cur);
+    cudaFree(h->tw.mask);
+    cudaFree(h->tw.w);
     delete h;
     return HY_OK;
 }
@@ -1187,6 +1195,37 @@ hy_status hy_touched_weights(const hy_ham *h, const void *psi, hy_dtype dt, floa
     return HY_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// row groups for a list of up to cap entries (grown with a device
+// synchronisation: work in flight may still read the old ones)
+hy_status ensure_tw(hy_ham *h, int64_t cap)
+{
+    if (h->tw.mask && h->tw.cap >= cap) return HY_OK;
+    if (cap > int64_t(INT32_MAX)) return HY_OK;      // the atomic fallback serves it
+    HY_CUDA(cudaDeviceSynchronize(), "synchronise before growing row groups");
+    cudaFree(h->tw.mask);
+    cudaFree(h->tw.w);
+    h->tw.mask = nullptr;
+    h->tw.w = nullptr;
+    h->tw.cap = 0;
+    cudaError_t e = cudaSuccess;
+    if (!h->tw.cnt) {
+        e = cudaMalloc(&h->tw.cnt, size_t(h->Na + 1) * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&h->tw.ptr, size_t(h->Na + 1) * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&h->tw.cur, size_t(h->Na) * sizeof(int32_t));
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&h->tw.mask, size_t(cap) * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&h->tw.w, size_t(cap) * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(row groups)");
+    h->tw.cap = cap;
+    return HY_OK;
+}
+}  // namespace
+
+extern "C" {
+
 hy_status hy_touched_weights_sparse(const hy_ham *hc, const void *psi, hy_dtype dt,
                                     const int64_t *list, int64_t m, float *D, void *stream)
 {
@@ -1199,19 +1238,21 @@ hy_status hy_touched_weights_sparse(const hy_ham *hc, const void *psi, hy_dtype 
     hy_status s = ensure_ws(h, L.total);
     if (s != HY_OK) return s;
     auto *cnt = reinterpret_cast<unsigned long long *>(static_cast<char *>(h->ws) + L.scalar);
+    s = ensure_tw(h, m);
+    if (s != HY_OK) return s;
     const unsigned long long mm = (unsigned long long)m;
     HY_CUDA(cudaMemcpyAsync(cnt, &mm, sizeof(mm), cudaMemcpyHostToDevice, st), "count");
     if (dt == HY_F64)
         HY_CUDA(hy::k::touched_weights_list<double>(static_cast<const double *>(psi), list, cnt, m,
                                                     m, h->Na, h->Nb, h->d_astr, h->d_bstr, h->n,
                                                     h->d_pairB, h->d_pairRs, h->d_pairRows,
-                                                    h->d_pairP, D, h->num_sms, st),
+                                                    h->d_pairP, D, h->tw, h->num_sms, st),
                 "touched weights (list)");
     else
         HY_CUDA(hy::k::touched_weights_list<float>(static_cast<const float *>(psi), list, cnt, m,
                                                    m, h->Na, h->Nb, h->d_astr, h->d_bstr, h->n,
                                                    h->d_pairB, h->d_pairRs, h->d_pairRows,
-                                                   h->d_pairP, D, h->num_sms, st),
+                                                   h->d_pairP, D, h->tw, h->num_sms, st),
                 "touched weights (list)");
     // (a copy from pageable host memory has left `mm` when the call returns)
     return HY_OK;
@@ -2003,17 +2044,19 @@ hy_status ranker_features_impl(const hy_ham *h, const hy_pool *p, const void *ps
         float *B = h->d_pairB + size_t(v) * h->Na * nn, *rs = h->d_pairRs + size_t(v) * h->Na;
         float *D = h->d_pairD + size_t(v) * nn * nn;
         if (const SparseState *S = states[v]) {
+            hy_status r = ensure_tw(const_cast<hy_ham *>(h), S->cap);
+            if (r != HY_OK) return r;
             if (dt == HY_F64)
                 HY_CUDA(hy::k::touched_weights_list<double>(
                             static_cast<const double *>(S->v), S->list, S->cnt, S->cap, S->hint,
                             h->Na, h->Nb, h->d_astr, h->d_bstr, h->n, B, rs, h->d_pairRows,
-                            h->d_pairP, D, h->num_sms, st),
+                            h->d_pairP, D, h->tw, h->num_sms, st),
                         "touched weights (list)");
             else
                 HY_CUDA(hy::k::touched_weights_list<float>(
                             static_cast<const float *>(S->v), S->list, S->cnt, S->cap, S->hint,
                             h->Na, h->Nb, h->d_astr, h->d_bstr, h->n, B, rs, h->d_pairRows,
-                            h->d_pairP, D, h->num_sms, st),
+                            h->d_pairP, D, h->tw, h->num_sms, st),
                         "touched weights (list)");
         } else if (dt == HY_F64) {
             HY_CUDA(hy::k::touched_weights<double>(static_cast<const double *>(vecs[v]), h->Na,

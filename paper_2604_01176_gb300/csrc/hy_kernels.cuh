@@ -196,14 +196,24 @@ template <typename T>
 cudaError_t touched_weights(const T *psi, int64_t Na, int64_t Nb, const uint32_t *astr,
                             const uint32_t *bstr, int n, float *Bw, float *rs, int32_t *rows,
                             float *part, float *D, int num_sms, cudaStream_t st);
+// scratch that groups a listed state's entries by alpha row: counts and
+// starts [Na + 1], cursors [Na], each entry's beta string and weight [cap]
+struct TwGroups {
+    int32_t *cnt, *ptr, *cur;
+    uint32_t *mask;
+    float *w;
+    int64_t cap;
+};
 // the same for a state given by its support list (v dense-backed; the device
-// count is clamped to cap; hint ~ the count, for the grid)
+// count is clamped to cap; hint ~ the count, for the grid).  With groups
+// (g.mask not null, g.cap >= cap) the entries are grouped by alpha row and
+// each row summed by one block; else every entry adds to Bw atomically.
 template <typename T>
 cudaError_t touched_weights_list(const T *v, const int64_t *list, const unsigned long long *count,
                                  int64_t cap, int64_t hint, int64_t Na, int64_t Nb,
                                  const uint32_t *astr, const uint32_t *bstr, int n, float *Bw,
-                                 float *rs, int32_t *rows, float *part, float *D, int num_sms,
-                                 cudaStream_t st);
+                                 float *rs, int32_t *rows, float *part, float *D,
+                                 const TwGroups &g, int num_sms, cudaStream_t st);
 
 // sparse-state path (hy_sparse.cu)
 template <typename T>

@@ -6,6 +6,7 @@
 // exactly; the full screen stays the fallback and the judge.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -356,12 +357,133 @@ k_pair_weights_list(const T *__restrict__ v, const int64_t *__restrict__ list,
     }
 }
 
+// The listed entries grouped by alpha row (count, scan, fill with each
+// entry's beta string and weight w = x^2), then one block per row sums its
+// entries into the row's pairs as k_pair_weights does over a whole row: no
+// atomics on Bw, each of its slots written once.
+__device__ __forceinline__ int64_t tw_len(const unsigned long long *count, int64_t cap)
+{
+    const unsigned long long c = *count;
+    return c < (unsigned long long)cap ? int64_t(c) : cap;
+}
+
+__global__ void __launch_bounds__(256)
+k_tw_count(const int64_t *__restrict__ list, const unsigned long long *__restrict__ count,
+           int64_t cap, int64_t Nb, int32_t *__restrict__ cnt)
+{
+    const int64_t m = tw_len(count, cap);
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < m;
+         t += int64_t(gridDim.x) * blockDim.x)
+        atomicAdd(cnt + list[t] / Nb, 1);
+}
+
+// exclusive scan of the row counts (one block): ptr[0..Na], cur = ptr
+__global__ void __launch_bounds__(1024)
+k_tw_scan(const int32_t *__restrict__ cnt, int64_t Na, int32_t *__restrict__ ptr,
+          int32_t *__restrict__ cur)
+{
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t per = (Na + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = tid * per, hi = lo + per < Na ? lo + per : Na;
+    int c = 0;
+    for (int64_t r = lo; r < hi; ++r) c += cnt[r];
+    int incl = c;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < int(blockDim.x >> 5) ? wsum[lane] : 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += u;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int pos = incl - c + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int64_t r = lo; r < hi; ++r) {
+        ptr[r] = pos;
+        cur[r] = pos;
+        pos += cnt[r];
+    }
+    if (tid == blockDim.x - 1) ptr[Na] = pos;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_tw_fill(const T *__restrict__ v, const int64_t *__restrict__ list,
+          const unsigned long long *__restrict__ count, int64_t cap, int64_t Nb,
+          const uint32_t *__restrict__ bstr, int32_t *__restrict__ cur,
+          uint32_t *__restrict__ mask, float *__restrict__ w)
+{
+    const int64_t m = tw_len(count, cap);
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < m;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t d = list[t];
+        const int pos = atomicAdd(cur + d / Nb, 1);
+        const float x = float(v[d]);
+        mask[pos] = bstr[d % Nb];
+        w[pos] = x * x;
+    }
+}
+
+constexpr int kTwThreads = 128;
+
+__global__ void __launch_bounds__(kTwThreads)
+k_tw_rows(const int32_t *__restrict__ ptr, const uint32_t *__restrict__ mask,
+          const float *__restrict__ w, int64_t Na, int n, float *__restrict__ Bw,
+          float *__restrict__ rs)
+{
+    __shared__ uint32_t ms[kTwThreads];
+    __shared__ float ws[kTwThreads];
+    __shared__ float red[kTwThreads / 32];
+    const int nn = n * n, t0 = threadIdx.x, t1 = threadIdx.x + kTwThreads;
+    // an unused slot asks for all 32 bits: no string of < 32 electrons has them
+    const uint32_t sel0 = t0 < nn ? (1u << (t0 / n)) | (1u << (t0 % n)) : 0xFFFFFFFFu;
+    const uint32_t sel1 = t1 < nn ? (1u << (t1 / n)) | (1u << (t1 % n)) : 0xFFFFFFFFu;
+    for (int64_t A = blockIdx.x; A < Na; A += gridDim.x) {
+        const int j0 = ptr[A], j1 = ptr[A + 1];
+        if (j0 == j1) continue;                      // the row stays zero
+        float acc0 = 0.0f, acc1 = 0.0f, rsum = 0.0f;
+        for (int c0 = j0; c0 < j1; c0 += kTwThreads) {
+            __syncthreads();                          // the previous chunk's readers are done
+            const int j = c0 + threadIdx.x;
+            const float wj = j < j1 ? w[j] : 0.0f;
+            ms[threadIdx.x] = j < j1 ? mask[j] : 0u;
+            ws[threadIdx.x] = wj;
+            rsum += wj;
+            __syncthreads();
+            const int cnt = j1 - c0 < kTwThreads ? j1 - c0 : kTwThreads;
+            for (int k = 0; k < cnt; ++k) {
+                const uint32_t mk = ms[k];
+                const float wk = ws[k];
+                acc0 += (mk & sel0) == sel0 ? wk : 0.0f;
+                acc1 += (mk & sel1) == sel1 ? wk : 0.0f;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) rsum += __shfl_down_sync(0xffffffffu, rsum, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float s = 0.0f;
+            for (int i = 0; i < kTwThreads / 32; ++i) s += red[i];
+            rs[A] = s;
+        }
+        if (t0 < nn) Bw[A * nn + t0] = acc0;
+        if (t1 < nn) Bw[A * nn + t1] = acc1;
+    }
+}
+
 template <typename T>
 cudaError_t touched_weights_list(const T *v, const int64_t *list, const unsigned long long *count,
                                  int64_t cap, int64_t hint, int64_t Na, int64_t Nb,
                                  const uint32_t *astr, const uint32_t *bstr, int n, float *Bw,
-                                 float *rs, int32_t *rows, float *part, float *D, int num_sms,
-                                 cudaStream_t st)
+                                 float *rs, int32_t *rows, float *part, float *D,
+                                 const TwGroups &gr, int num_sms, cudaStream_t st)
 {
     const int nn = n * n;
     cudaError_t e = cudaMemsetAsync(Bw, 0, size_t(Na) * nn * sizeof(float), st);
@@ -369,8 +491,22 @@ cudaError_t touched_weights_list(const T *v, const int64_t *list, const unsigned
     if (e != cudaSuccess) return e;
     int64_t g = (std::max<int64_t>(hint, 1) + 255) / 256;
     if (g > int64_t(num_sms) * 8) g = int64_t(num_sms) * 8;
-    k_pair_weights_list<T><<<unsigned(g), 256, 0, st>>>(v, list, count, cap, Nb, bstr, n, Bw, rs);
-    hy::count_launch();
+    if (gr.mask && gr.cap >= cap && cap <= int64_t(INT32_MAX)) {
+        e = cudaMemsetAsync(gr.cnt, 0, size_t(Na + 1) * sizeof(int32_t), st);
+        if (e != cudaSuccess) return e;
+        k_tw_count<<<unsigned(g), 256, 0, st>>>(list, count, cap, Nb, gr.cnt); hy::count_launch();
+        k_tw_scan<<<1, 1024, 0, st>>>(gr.cnt, Na, gr.ptr, gr.cur); hy::count_launch();
+        k_tw_fill<T><<<unsigned(g), 256, 0, st>>>(v, list, count, cap, Nb, bstr, gr.cur, gr.mask,
+                                                 gr.w);
+        hy::count_launch();
+        const int64_t gb = Na < int64_t(num_sms) * 16 ? Na : int64_t(num_sms) * 16;
+        k_tw_rows<<<unsigned(gb), kTwThreads, 0, st>>>(gr.ptr, gr.mask, gr.w, Na, n, Bw, rs);
+        hy::count_launch();
+    } else {
+        k_pair_weights_list<T><<<unsigned(g), 256, 0, st>>>(v, list, count, cap, Nb, bstr, n, Bw,
+                                                            rs);
+        hy::count_launch();
+    }
     k_pair_rows<<<1, 1024, 0, st>>>(rs, Na, rows); hy::count_launch();
     k_pair_contract<<<dim3(unsigned((nn + kPairGroup - 1) / kPairGroup), kPairSplits), 256, 0, st>>>(
         Bw, rs, astr, rows, n, part);
@@ -408,12 +544,14 @@ template cudaError_t touched_weights_list<double>(const double *, const int64_t 
                                                   const unsigned long long *, int64_t, int64_t,
                                                   int64_t, int64_t, const uint32_t *,
                                                   const uint32_t *, int, float *, float *,
-                                                  int32_t *, float *, float *, int, cudaStream_t);
+                                                  int32_t *, float *, float *, const TwGroups &,
+                                                  int, cudaStream_t);
 template cudaError_t touched_weights_list<float>(const float *, const int64_t *,
                                                  const unsigned long long *, int64_t, int64_t,
                                                  int64_t, int64_t, const uint32_t *,
                                                  const uint32_t *, int, float *, float *,
-                                                 int32_t *, float *, float *, int, cudaStream_t);
+                                                 int32_t *, float *, float *, const TwGroups &,
+                                                 int, cudaStream_t);
 template cudaError_t touched_weights<float>(const float *, int64_t, int64_t, const uint32_t *,
                                             const uint32_t *, int, float *, float *, int32_t *,
                                             float *, float *, int, cudaStream_t);
