@@ -96,6 +96,10 @@ struct hy_adapt {
     void *h_pin = nullptr;
     double *h_e = nullptr, *h_g = nullptr;
     int64_t *h_cnt = nullptr;
+    // pinned staging of the screen's gradients [K] and the ranker's extra
+    // features [K][4]
+    double *h_gs = nullptr;
+    float *h_extra = nullptr;
     double *d_one = nullptr;      // device constants {1.0, 1.0f}
     // support program of the current ansatz (small supports): compiled from
     // the first structural preparation after an append, then run by every
@@ -471,7 +475,7 @@ hy_status upload_extra(hy_adapt *a, cudaStream_t st)
     // stale |g| relative to the most recent screen's largest |g| (not the
     // largest ever seen, which early iterations dominate)
     const double mx = a->last_max;
-    std::vector<float> ex(size_t(a->K) * 4);
+    float *ex = a->h_extra;   // pinned: the previous upload finished with its iteration
     for (int64_t k = 0; k < a->K; ++k) {
         const double lg = a->last_g[k];
         ex[4 * k + 0] = lg < 0.0 ? -12.0f : float(std::log10(lg / (mx > 0 ? mx : 1.0) + 1e-12));
@@ -481,9 +485,8 @@ hy_status upload_extra(hy_adapt *a, cudaStream_t st)
     }
     for (size_t l = 0; l < a->ops.size(); ++l) ex[4 * a->ops[l] + 3] = 0.0f;
     for (size_t l = 0; l < a->ops.size(); ++l) ex[4 * a->ops[l] + 3] += float(std::fabs(a->theta[l]));
-    HY_TRY(xfer(a, a->d_extra, ex.data(), ex.size() * 4, cudaMemcpyHostToDevice, st,
-                "upload extra features"));
-    return cu(cudaStreamSynchronize(st), "sync");
+    return xfer(a, a->d_extra, ex, size_t(a->K) * 16, cudaMemcpyHostToDevice, st,
+                "upload extra features");
 }
 
 // Relative energy decrease below which an accepted double-precision step is
@@ -666,6 +669,9 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
     if (s == HY_OK) s = cu(cudaMallocHost(&a->h_cs, size_t(c.max_iter) * 16), "pinned angles");
     if (s == HY_OK)
         s = cu(cudaMallocHost(&a->h_pin, 64 + size_t(c.max_iter) * sizeof(double)), "pinned readbacks");
+    if (s == HY_OK) s = cu(cudaMallocHost(&a->h_gs, size_t(a->K) * 8 + 8), "pinned screen");
+    if (s == HY_OK && c.screen_top_m > 0)
+        s = cu(cudaMallocHost(&a->h_extra, size_t(a->K) * 16 + 16), "pinned extra features");
     if (s == HY_OK) {
         a->h_e = static_cast<double *>(a->h_pin);
         a->h_cnt = reinterpret_cast<int64_t *>(static_cast<char *>(a->h_pin) + 16);
@@ -733,6 +739,8 @@ hy_status hy_adapt_destroy(hy_adapt *a)
     cudaFree(a->d_cs);
     if (a->h_cs) cudaFreeHost(a->h_cs);
     if (a->h_pin) cudaFreeHost(a->h_pin);
+    if (a->h_gs) cudaFreeHost(a->h_gs);
+    if (a->h_extra) cudaFreeHost(a->h_extra);
     cudaFree(a->d_one);
     for (auto &row : a->ss)
         for (hy::SparseState *&x : row) hy::sstate_destroy(x);
@@ -802,10 +810,11 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
                                         a->sparse_m, a->d_g, st));
         else
             HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, nullptr, a->K, a->d_g, bulk, st));
-        g.assign(a->K, 0.0);
-        HY_TRY(xfer(a, g.data(), a->d_g, a->K * sizeof(double), cudaMemcpyDeviceToHost, st,
+        HY_TRY(xfer(a, a->h_gs, a->d_g, a->K * sizeof(double), cudaMemcpyDeviceToHost, st,
                     "screen readback"));
-        return cu(cudaStreamSynchronize(st), "sync");
+        HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+        g.assign(a->h_gs, a->h_gs + a->K);
+        return HY_OK;
     };
     auto pick = [&](const std::vector<int64_t> &ids, const std::vector<double> &gv) {
         gmax = 0.0;
