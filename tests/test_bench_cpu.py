@@ -1,0 +1,119 @@
+"""Host logic of bench.py on CPU: the kernel-class breakdown, the roofline
+object built from the library's event profiler, and the clock sampler's
+parsing (fed a fake nvidia-smi process)."""
+import math
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def bench():
+    import bench as b
+    return b
+
+
+def prof_entry(launches=0, ms=0.0, bytes_=0.0, flops=0.0):
+    return {"launches": launches, "ms": ms, "bytes": bytes_, "flops": flops}
+
+
+def empty_prof(bench):
+    return {c: prof_entry() for c in bench.CLASS_KERNELS}
+
+
+def test_breakdown_shares(bench):
+    prof = empty_prof(bench)
+    prof["hpsi_sparse"] = prof_entry(26, 5.0)
+    prof["features"] = prof_entry(4, 2.0)
+    out = bench.breakdown(prof, 10.0)
+    assert set(out) == {"hpsi_sparse", "features"}      # classes that never ran are left out
+    assert out["hpsi_sparse"] == {"launches": 26, "ms": 5.0, "share_of_step": 0.5}
+    assert out["features"]["share_of_step"] == 0.2
+
+
+def test_roofline_picks_the_longest_class_with_known_work(bench):
+    peaks = {"hbm_gbs": 6712.6}
+    prof = empty_prof(bench)
+    # the longest class has no known work: it is named as dominant only
+    prof["sparse_excite"] = prof_entry(51, 9.0)
+    prof["features"] = prof_entry(4, 2.0, bytes_=4 * 1.0e9)
+    prof["reduce"] = prof_entry(26, 1.0, bytes_=26 * 1.0e6)
+    r = bench.step_roofline(prof, peaks, "measured", 80.5)
+    assert r["kernel_class"] == "features" and r["dominant_class"] == "sparse_excite"
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    gbs = 4.0e9 / (2.0e-3) / 1e9
+    assert math.isclose(r["achieved"], round(gbs, 1))
+    assert math.isclose(r["frac"], round(gbs / 6712.6, 4))
+    assert r["bytes_per_launch"] == 1.0e9
+    assert r["traffic"] is None
+
+
+def test_roofline_alu_class_uses_flops(bench):
+    prof = empty_prof(bench)
+    prof["hpsi"] = prof_entry(2, 400.0, bytes_=2 * 1.3e9, flops=2 * 20.0e12)
+    r = bench.step_roofline(prof, {"hbm_gbs": 6712.6}, "measured", 80.5)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    tf = 40.0e12 / 0.4 / 1e12
+    assert math.isclose(r["achieved"], round(tf, 3))
+    assert math.isclose(r["frac"], round(tf / 80.5, 4))
+
+
+def test_roofline_scatter_reports_l2_atomics(bench):
+    prof = empty_prof(bench)
+    adds = 26 * 1.0e7
+    prof["hpsi_sparse"] = prof_entry(26, 5.0, bytes_=6 * 662.5e6, flops=adds)
+    r = bench.step_roofline(prof, {"hbm_gbs": 6712.6}, "measured", 80.5)
+    la = r["l2_atomics"]
+    rate = adds / 5.0e-3
+    assert math.isclose(la["achieved_adds_per_s"], float(f"{rate:.4g}"))
+    assert math.isclose(la["frac_of_l2_red_peak"], round(rate / bench.L2_RED_PEAK, 4))
+    assert la["adds_per_launch_est"] == round(adds / 26)
+    # a class without the adds estimate carries no such entry
+    prof["hpsi_sparse"] = prof_entry(26, 5.0, bytes_=6 * 662.5e6)
+    assert "l2_atomics" not in bench.step_roofline(prof, {"hbm_gbs": 6712.6}, "measured", 80.5)
+
+
+def test_roofline_without_known_work(bench):
+    prof = empty_prof(bench)
+    prof["sparse_excite"] = prof_entry(10, 1.0)
+    r = bench.step_roofline(prof, {"hbm_gbs": 6712.6}, "measured", 80.5)
+    assert r["achieved"] is None and r["frac"] is None
+    assert r["dominant_class"] == "sparse_excite"
+
+
+class _FakeSmi:
+    def __init__(self, text):
+        self.text = text
+        self.terminated = False
+
+    def terminate(self):
+        self.terminated = True
+
+    def communicate(self, timeout=None):
+        return self.text, ""
+
+
+def test_clock_sampler_parsing(bench):
+    rows = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1390.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",   # skipped
+    ]
+    c = bench.Clocks(0)
+    c.proc = _FakeSmi("\n".join(rows) + "\n")
+    out = c.stop()
+    assert c.proc.terminated
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi(bench):
+    c = bench.Clocks(0)
+    out = c.stop()
+    assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_job_throughput_counts_all_ranks(bench):
+    # 4 steps on each of 2 ranks in 10 ms (max over ranks): 800 steps/s for the job
+    assert math.isclose(bench.job_throughput(2, 4, 10.0), 800.0)
