@@ -1027,14 +1027,12 @@ cudaError_t prog_compile(const int64_t *list, int64_t m, const int64_t *step_len
                          int32_t *tab, int *flag, cudaStream_t st)
 {
     if (m < 1 || m > kProgMax || steps < 1 || steps > 254) return cudaErrorInvalidValue;
-    static bool attr = false;                        // up to 128 KB of dynamic shared memory
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            k_prog_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kProgSortMax * 8));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    // up to 128 KB of dynamic shared memory (set per call: the attribute
+    // belongs to the current device)
+    cudaError_t e = cudaFuncSetAttribute(k_prog_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(kProgSortMax * 8));
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(flag, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     int64_t P = 1;
     while (P < m) P <<= 1;
@@ -1052,14 +1050,11 @@ cudaError_t prog_prepare(const int64_t *key, const int32_t *tab, int64_t m, cons
                          T *v, cudaStream_t st)
 {
     if (m < 1 || m > kProgMax) return cudaErrorInvalidValue;
-    static bool attr = false;                        // up to 96 KB of dynamic shared memory
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(k_prog_prepare<T>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   int(kProgMax * sizeof(T)));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // up to 96 KB of dynamic shared memory
+    const cudaError_t e = cudaFuncSetAttribute(k_prog_prepare<T>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               int(kProgMax * sizeof(T)));
+    if (e != cudaSuccess) return e;
     k_prog_prepare<T><<<1, kProgThreads, size_t(m) * sizeof(T), st>>>(key, tab, int(m), desc, ops,
                                                                       cs, L, renorm ? 1 : 0,
                                                                       norm2, v);
@@ -1074,14 +1069,11 @@ cudaError_t prog_grad(const int64_t *key, const int32_t *tab, int64_t m, const i
 {
     if (m < 1 || m > kProgMax || L < 1) return cudaErrorInvalidValue;
     const size_t smem = 2 * size_t(m) * sizeof(T);
-    static bool attr = false;                        // up to 192 KB of dynamic shared memory
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(k_prog_grad<T>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   int(2 * kProgMax * sizeof(T)));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // up to 192 KB of dynamic shared memory
+    const cudaError_t e = cudaFuncSetAttribute(k_prog_grad<T>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               int(2 * kProgMax * sizeof(T)));
+    if (e != cudaSuccess) return e;
     k_prog_grad<T><<<unsigned(L), kProgThreads, smem, st>>>(key, tab, int(m), desc, ops, cs, L,
                                                             sigma, norm2, g);
     hy::count_launch();
