@@ -403,8 +403,10 @@ hy_status hy_touched_weights(const hy_ham *h, const void *psi, hy_dtype dt,
 /* The same from the state's support: list (device, m indices, e.g. from
  * hy_support) holds every nonzero amplitude of psi (each once); O(m) work
  * instead of a pass over the whole state (the ADAPT driver's sparse path uses
- * it for psi).  Sums by atomic adds: equal to hy_touched_weights up to float
- * rounding in the order of addition. */
+ * it for psi and, while it is listed, sigma).  The entries are grouped by
+ * alpha string (held by h, grown with a device synchronisation when m
+ * exceeds them) and each string's pair weights summed by one block; equal to
+ * hy_touched_weights up to float rounding in the order of addition. */
 hy_status hy_touched_weights_sparse(const hy_ham *h, const void *psi, hy_dtype dt,
                                     const int64_t *list, int64_t m, float *D, void *stream);
 
