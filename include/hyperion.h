@@ -537,9 +537,15 @@ typedef struct {
                              pairs with a listed end; when the list overflows
                              the evaluation is redone with the dense sweeps,
                              which stay in use while the ansatz is at least as
-                             long.  While (pool size) x (support) <= 5e9 the
-                             whole pool is screened exactly even when a
-                             ranker is attached (its pairs still train it).
+                             long.  Supports of up to 12,288 determinants
+                             are prepared by one CTA, and after each append
+                             the ansatz is compiled into pairings of its
+                             support, so that the iteration's further
+                             evaluations and forward-mode gradients run on
+                             shared-memory vectors.  While (pool size) x
+                             (support) <= 5e9 the whole pool is screened
+                             exactly even when a ranker is attached (its
+                             pairs still train it).
                              0: always the dense sweeps                        */
     int64_t sparse_cap;   /* support capacity of the sparse path; 0: N_det/64
                              for double and N_det/256 for float evaluations
