@@ -306,6 +306,33 @@ def test_gradient_matches_central_differences(n, na, nb, step):
         assert abs((ep - em) / (2 * h) - g[k]) < 1e-7
 
 
+@pytest.mark.parametrize("n,na,nb,seed", [(6, 3, 3, 1001), (8, 4, 4, 1005), (7, 4, 3, 77)])
+def test_prepared_support_fixed_by_the_ansatz(n, na, nb, seed):
+    """A rotation exp(theta tau) pairs determinants one to one (cos and sin
+    mix the two ends of a pair, nothing else), so for angles with nonzero
+    sine and cosine the support of U_L..U_1|HF> depends on the operators
+    only, and an operator of c constituents at most multiplies the support
+    by 2^c.  (The sparse path lists the support once per ansatz and bounds
+    its growth on these two facts.)"""
+    s = small_system(n, na, nb, seed)
+    pool = s.pool()
+    rng = np.random.default_rng(seed)
+    ops = [int(k) for k in rng.integers(0, len(pool), 6)]
+    supports = []
+    for _ in range(3):
+        th = rng.uniform(0.1, 1.4, len(ops)) * rng.choice([-1.0, 1.0], len(ops))
+        psi = oadapt.prepare(s, pool, ops, th)
+        supports.append(frozenset(np.flatnonzero(np.abs(psi) > 1e-13).tolist()))
+    assert supports[0] == supports[1] == supports[2]
+    prev = 1
+    for l in range(1, len(ops) + 1):
+        psi = oadapt.prepare(s, pool, ops[:l], th[:l])
+        m = int(np.count_nonzero(np.abs(psi) > 1e-13))
+        assert prev <= m <= prev * 2 ** int(pool[ops[l - 1]][0])
+        prev = m
+    assert prev == len(supports[0])
+
+
 # --------------------------------------------------------------------------
 # ADAPT-VQE loop
 # --------------------------------------------------------------------------
