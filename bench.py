@@ -563,6 +563,16 @@ def step_roofline(prof, peaks, peak_kind, fp32_peak):
     return out
 
 
+def c_tilde(records):
+    """The paper's amortised ADAPT coefficient C~ = j / sqrt(T_j) (Numerical
+    performance subsection): j iterations from Hartree-Fock, T_j their summed
+    wall time in seconds (each iteration's host-measured total)."""
+    t = sum(float(r["t_total"]) for r in records)
+    j = len(records)
+    return {"iterations": j, "t_s": round(t, 6),
+            "value": round(j / math.sqrt(t), 3) if t > 0 else None, "unit": "s^-1/2"}
+
+
 def leg_summary(leg, S):
     out = {"iters_per_s": round(S / (leg["ms"] / 1e3), 5),
            "n_evals": [rec["n_evals"] for rec in leg["timed"]],
@@ -572,7 +582,8 @@ def leg_summary(leg, S):
            "energy_bulk": [rec["energy"] for rec in leg["timed"]],
            "final_energy_f64": leg["e_final"],
            "final_bulk_minus_f64": leg["e_bulk"] - leg["e_final"],
-           "ranker_true_argmax_rank_judged": leg["true_rank"]}
+           "ranker_true_argmax_rank_judged": leg["true_rank"],
+           "c_tilde": c_tilde(list(leg["warm"]) + list(leg["timed"]))}
     if "plain_ms" in leg:
         out["plain_f64_full_screen"] = {
             "iters_per_s": round(1e3 / leg["plain_ms"], 5), "ms": round(leg["plain_ms"], 1),

@@ -117,3 +117,12 @@ def test_clock_sampler_without_nvidia_smi(bench):
 def test_job_throughput_counts_all_ranks(bench):
     # 4 steps on each of 2 ranks in 10 ms (max over ranks): 800 steps/s for the job
     assert math.isclose(bench.job_throughput(2, 4, 10.0), 800.0)
+
+
+def test_c_tilde(bench):
+    # the paper's amortised coefficient: j iterations in T_j seconds -> j / sqrt(T_j)
+    recs = [{"t_total": 0.25}, {"t_total": 0.5}, {"t_total": 0.25}]
+    c = bench.c_tilde(recs)
+    assert c["iterations"] == 3 and math.isclose(c["t_s"], 1.0)
+    assert math.isclose(c["value"], 3.0)
+    assert bench.c_tilde([])["value"] is None
