@@ -198,9 +198,10 @@ def test_pauli_table_counts_and_pruning(lib):
     assert len(x2) < len(x) and np.abs(cp).min() > 1e-3
 
 
-def test_atomic_ceiling_probe_compiles(tmp_path):
-    """The standalone L2 atomic-add probe (the scatter's ceiling measurement)
-    cross-compiles for sm_103a."""
+@pytest.mark.parametrize("probe", ["l2_atomics", "fma_smem", "tcgen05_tf32"])
+def test_peak_probes_compile(tmp_path, probe):
+    """The standalone peak probes (float atomic adds, FMA and shared-memory
+    gather rates, tcgen05 TF32 issue rate) cross-compile for sm_103a."""
     import shutil
     import subprocess
     nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
@@ -208,8 +209,8 @@ def test_atomic_ceiling_probe_compiles(tmp_path):
         nvcc = shutil.which("nvcc")
     if not nvcc:
         pytest.skip("nvcc not available")
-    src = os.path.join(ROOT, "paper_2604_01176_gb300", "probes", "l2_atomics.cu")
-    out = tmp_path / "l2_atomics.o"
+    src = os.path.join(ROOT, "paper_2604_01176_gb300", "probes", probe + ".cu")
+    out = tmp_path / (probe + ".o")
     r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-c", src,
                         "-o", str(out)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
