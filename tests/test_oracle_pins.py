@@ -359,3 +359,93 @@ def test_adapt_singles_reach_noninteracting_ground_state():
                if all(op[1 + 5 * q] == 1 for q in range(op[0]))]
     rec = oadapt.run(s, pool, max_iter=30, eps_grad=1e-9, pool_subset=singles)
     assert abs(rec["energy"][-1] - s.fci_energy()) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Ansatz energy and gradient (paper: Method, Eq. "ev" -- E(theta) =
+# <psi0|U(theta)^T H U(theta)|psi0>; Numerical performance -- the ADAPT
+# re-optimisation of every theta).  oadapt.energy_and_gradient is the checker
+# of every ansatz-gradient test on the GPU, so it is pinned here against a
+# numerical derivative of the energy and against dense JW matrices.
+# --------------------------------------------------------------------------
+def _generic_ansatz(s, pool, length, seed):
+    """Operators of every kind (singles, same-spin and opposite-spin doubles,
+    multi-constituent ones) and generic angles."""
+    rng = np.random.default_rng(seed)
+    multi = [k for k, op in enumerate(pool) if op[0] == 2]
+    singles = [k for k, op in enumerate(pool) if op[1] == 1]
+    doubles = [k for k, op in enumerate(pool) if op[1] == 2]
+    picks = [int(rng.choice(singles)), int(rng.choice(multi)), int(rng.choice(doubles))]
+    picks += [int(k) for k in rng.integers(0, len(pool), length - len(picks))]
+    thetas = rng.uniform(0.05, 0.6, length) * rng.choice([-1.0, 1.0], length)
+    return picks, thetas
+
+
+@pytest.mark.parametrize("n,na,nb,seed,length", [(6, 3, 3, 1001, 6), (8, 4, 4, 1005, 5)])
+def test_ansatz_gradient_matches_central_differences(n, na, nb, seed, length):
+    """Every component of dE/dtheta from energy_and_gradient equals the
+    central difference (E(theta + h e_l) - E(theta - h e_l)) / 2h of the
+    energy, h = 1e-4, |error| <= 1e-7 (the O(h^2) truncation is ~1e-9 here).
+    A wrong order of the later rotations, a missing factor 2 or a generator
+    applied at the wrong position breaks it."""
+    s = small_system(n, na, nb, seed)
+    pool = s.pool()
+    ops, th = _generic_ansatz(s, pool, length, seed)
+    e, grad = oadapt.energy_and_gradient(s, pool, ops, th)
+    assert abs(e - s.energy(oadapt.prepare(s, pool, ops, th))) < 1e-13
+    h = 1e-4
+    fd = np.zeros(length)
+    for l in range(length):
+        tp, tm = th.copy(), th.copy()
+        tp[l] += h
+        tm[l] -= h
+        ep = s.energy(oadapt.prepare(s, pool, ops, tp))
+        em = s.energy(oadapt.prepare(s, pool, ops, tm))
+        fd[l] = (ep - em) / (2 * h)
+    assert np.abs(grad).max() > 1e-3         # a generic point, not a stationary one
+    assert np.abs(grad - fd).max() < 1e-7
+
+
+def test_ansatz_energy_and_gradient_against_dense_expm():
+    """E(theta) and dE/dtheta on an 8-qubit system from dense matrices only:
+    H and every A_k from Jordan-Wigner Kronecker products restricted to
+    Omega_CIk, U(theta) as the ordered product of scipy expm(theta_l A_l),
+    the gradient as a central difference of that dense energy."""
+    n, na, nb = 4, 2, 2
+    h1, h2, ec = synth.integrals(n, 23)
+    s = oracle.System(h1, h2, ec, n, na, nb)
+    pool = s.pool()
+    ops, th = _generic_ansatz(s, pool, 6, 23)
+    Hjw, a = jw_hamiltonian(h1, h2, ec, n)
+    dets = s.dets().astype(np.int64)
+    H = Hjw.toarray()[np.ix_(dets, dets)]
+    A = {k: _dense_generator_jw(pool[k], n, dets, a) for k in set(ops)}
+    psi0 = np.zeros(s.n_det)
+    psi0[0] = 1.0
+
+    def e_dense(t):
+        v = psi0
+        for k, x in zip(ops, t):
+            v = scipy.linalg.expm(x * A[k]) @ v
+        return float(v @ H @ v)
+
+    e, grad = oadapt.energy_and_gradient(s, pool, ops, th)
+    assert abs(e - e_dense(th)) < 1e-12
+    h = 1e-4
+    for l in range(len(ops)):
+        tp, tm = th.copy(), th.copy()
+        tp[l] += h
+        tm[l] -= h
+        assert abs((e_dense(tp) - e_dense(tm)) / (2 * h) - grad[l]) < 1e-7
+
+
+def test_select_tie_break():
+    """The argmax reading where the paper is silent: the lowest pool index
+    among the operators whose |g| lies within 1e-12 * max|g| of the maximum;
+    anything further below does not tie."""
+    g = np.array([0.5, -1.0, 1.0 - 1e-13, 1.0, 0.9])
+    assert oadapt.select(g) == 1                       # exact tie, lower index, sign ignored
+    assert oadapt.select(np.array([1.0 - 5e-13, -1.0])) == 0     # within the band
+    assert oadapt.select(np.array([1.0 - 2e-12, -1.0])) == 1     # outside the band
+    assert oadapt.select(np.array([0.0, 0.0, 3e-7, -2e-7])) == 2
+    assert oadapt.select(np.array([-4.0])) == 0
