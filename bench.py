@@ -90,6 +90,13 @@ def parse():
                          "CPU), printing its iterations/s")
     ap.add_argument("--judge-only", action="store_true",
                     help="--ranker-eval without the plain run (ranks of the true argmax only)")
+    ap.add_argument("--hmat", action="store_true",
+                    help="the Hamiltonian stored explicitly: build it for --rows alpha strings of "
+                         "--workload and time H psi streamed from it against the matrix-free sweep")
+    ap.add_argument("--rows", default="all",
+                    help="--hmat row range 'b:e' in alpha strings, or 'all'")
+    ap.add_argument("--hmat-dtypes", default="f32,f64", help="dtypes of --hmat")
+    ap.add_argument("--reps", type=int, default=5, help="timed repetitions of --hmat")
     ap.add_argument("--batch", action="store_true",
                     help="64 molecules of 8-12 orbitals: H psi + energies of all in one persistent "
                          "graph-captured launch (autotuned tile) vs one launch sequence per molecule")
@@ -153,6 +160,76 @@ def batch_bench(args, count=64, reps=5):
                   "batched_launches": (l1 - l0) // reps, "looped_launches": (l3 - l2) // reps,
                   "molecules_per_s": round(count / (t_b / 1e3), 1),
                   "max_energy_diff_vs_looped": err}
+    print(json.dumps(out), flush=True)
+
+
+def hmat_bench(args):
+    """H psi streamed from the explicitly stored Hamiltonian (a range of its
+    rows) against the matrix-free sweep of the same rows: CUDA events on the
+    launching stream, inputs resident, the matrix far larger than L2 so every
+    repetition streams it from HBM.  Bytes = the stored matrix (16-bit beta
+    columns, values, segment partners) + psi rows read + sigma rows written."""
+    import torch
+    import paper_2604_01176_gb300 as hy
+    from paper_2604_01176_gb300 import build as hybuild
+    hybuild.build()
+    peaks, peak_kind = load_peaks()
+    n, na, nb, seed = synth.workload(args.workload)
+    h1, h2, ec = synth.integrals(n, seed)
+    ham = hy.Hamiltonian(h1, h2, ec, n, na, nb)
+    NA, NB = ham.n_alpha_str, ham.n_beta_str
+    b, e = (0, NA) if args.rows == "all" else tuple(int(x) for x in args.rows.split(":"))
+    st = torch.cuda.current_stream()
+    out = {"hmat": args.workload, "rows": [b, e], "n_det_rows": (e - b) * NB,
+           "row_len": None, "peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind}
+    for d in args.hmat_dtypes.split(","):
+        dt = torch.float64 if d == "f64" else torch.float32
+        by, nnz = hy.ExplicitH.size(ham, dt, b, e)
+        free, _ = torch.cuda.mem_get_info()
+        if by + (1 << 30) + 2 * ham.n_det * (8 if d == "f64" else 4) > free:
+            out[d] = {"skipped": f"needs {by} bytes, {free} free"}
+            continue
+        t0 = time.perf_counter()
+        m = hy.ExplicitH(ham, dt, b, e)
+        t_build = time.perf_counter() - t0
+        out["row_len"] = m.row_len
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(2)
+        psi = torch.randn(ham.n_det, dtype=dt, device="cuda", generator=gen)
+        sig = torch.empty((e - b) * NB, dtype=dt, device="cuda")
+        m.apply(psi, out=sig)
+        ham.apply_h_rows(psi, b, e, out=sig)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.reps + 2)]
+        torch.cuda.synchronize()
+        ms_m = []
+        for r in range(args.reps):
+            ev[2 * r].record(st)
+            m.apply(psi, out=sig)
+            ev[2 * r + 1].record(st)
+        torch.cuda.synchronize()
+        ms_m = [ev[2 * r].elapsed_time(ev[2 * r + 1]) for r in range(args.reps)]
+        ref = sig.clone()
+        ham.apply_h_rows(psi, b, e, out=sig)
+        diff = float(torch.max(torch.abs(sig - ref)).item() / torch.max(torch.abs(ref)).item())
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.reps):
+            ham.apply_h_rows(psi, b, e, out=sig)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_mf = e0.elapsed_time(e1) / args.reps
+        es = 8 if d == "f64" else 4
+        traffic = by + 2 * (e - b) * NB * es
+        ms = statistics.median(ms_m)
+        gbs = traffic / (ms / 1e3) / 1e9
+        out[d] = {"build_s": round(t_build, 2), "matrix_bytes": by, "nnz": nnz,
+                  "ms": round(ms, 4), "ms_all": [round(x, 4) for x in ms_m],
+                  "gbs": round(gbs, 1), "frac_of_hbm": round(gbs / peaks["hbm_gbs"], 4),
+                  "matrix_free_ms": round(ms_mf, 4),
+                  "max_rel_diff_vs_matrix_free": diff}
+        del m, psi, sig, ref
+        torch.cuda.empty_cache()
     print(json.dumps(out), flush=True)
 
 
@@ -604,6 +681,8 @@ def main():
         return ranker_eval(args)
     if args.batch:
         return batch_bench(args)
+    if args.hmat:
+        return hmat_bench(args)
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")

@@ -105,7 +105,10 @@ typedef enum {
     HY_PROF_FEATURES = 7,      /* ranker features: N s bytes per pass over psi
                                   or sigma (its arithmetic skips zero tiles and
                                   is not counted)                              */
-    HY_PROF_CLASSES = 8
+    HY_PROF_HMAT = 8,          /* H psi over the explicit H (hy_hmat_apply):
+                                  the stored matrix + read psi rows + write
+                                  sigma rows; 2 flops per stored entry         */
+    HY_PROF_CLASSES = 9
 } hy_prof_class;
 hy_status hy_profile_enable(uint32_t class_mask);
 hy_status hy_profile_read(int cls, int64_t *launches, double *ms, double *bytes,
@@ -166,9 +169,17 @@ hy_status hy_ham_profile(hy_ham *h, int enable);
  * tcgen05 TF32 MMAs with split hi/lo operands, FP32 accuracy) or on the FP32
  * SIMT pipes (impl = 1).  Both feed the same phase B.  A bounded wait of the
  * tensor-core kernel that runs out is returned as HY_ERR_TIMEOUT by the next
- * hy_apply_h on this handle. */
+ * hy_apply_h on this handle (the kernel itself gives up, releases its tensor
+ * memory and returns; the context stays usable).  impl = 2 is a test of that
+ * path: the tensor-core kernel runs with its MMAs withheld, so no stage
+ * barrier ever completes, every wait runs out after its limit and the
+ * float H|psi> of that call is wrong. */
 hy_status hy_ham_set_coupling(hy_ham *h, int impl);
 hy_status hy_ham_coupling_ms(const hy_ham *h, float *ms);
+
+/* Polls of an mbarrier before a wait of the tensor-core coupling gives up
+ * (default 2^26, seconds of waiting; >= 1). */
+hy_status hy_ham_set_wait_limit(hy_ham *h, int64_t polls);
 
 /* Copy the Pauli table (host outputs, caller-allocated).  Term t is
  * coeff[t] * P(x[t], z[t]) where P is the Hermitian Pauli string with X on
@@ -177,6 +188,52 @@ hy_status hy_ham_coupling_ms(const hy_ham *h, float *ms);
  * share x.  Arrays hold n_terms (x, z, coeff) and n_groups + 1 entries. */
 hy_status hy_ham_pauli_table(const hy_ham *h, uint64_t *x, uint64_t *z,
                              double *coeff, int64_t *group_offsets);
+
+/* ---------------------------------------------------------------------- */
+/* The Hamiltonian stored explicitly                                        */
+/* ---------------------------------------------------------------------- */
+
+/* The paper assembles H as a sparse matrix over Omega_CIk and distributes
+ * its rows (Sparse State-Vector Emulation section; Table 1 gives its size
+ * per molecule).  hy_hmat_build stores the rows of the determinants whose
+ * alpha string lies in [row_begin, row_end) (the same row unit as
+ * hy_apply_h_rows), with every structural nonzero of those rows -- 1 + s_a
+ * + s_b + d_a + d_b + s_a s_b entries per row (singles s, doubles d of each
+ * spin; 5,793 at 32 qubits), explicit zeros included -- in dt (HY_F64 or
+ * HY_F32 values, computed in double from the folded tables and rounded
+ * once).  Layout: rows grouped by alpha string; within a group the columns
+ * fall into segments, one per alpha partner (the string itself, its singles,
+ * its doubles), every row of the group having the same number of entries
+ * per segment; an entry is its beta column (16 bits) and its value, the
+ * segment's alpha partner is stored once, and entry j of all rows of a group
+ * is contiguous, so a row group is one contiguous stream.  Bytes: per alpha
+ * string S * 2 + w * N_bp * (2 + sizeof(dt)) with w the row length, S = 1 +
+ * s_a + d_a and N_bp = N_beta rounded up to 8 (padding rows hold zeros).
+ * The device memory is checked first: HY_ERR_OOM when the matrix plus 1 GiB
+ * does not fit the free memory.  The build synchronises the device.  *out
+ * receives an owned handle (hy_hmat_destroy); it refers to h, which must
+ * outlive it. */
+typedef struct hy_hmat hy_hmat;
+hy_status hy_hmat_bytes(const hy_ham *h, hy_dtype dt, int64_t row_begin,
+                        int64_t row_end, int64_t *bytes, int64_t *nnz);
+hy_status hy_hmat_build(const hy_ham *h, hy_dtype dt, int64_t row_begin,
+                        int64_t row_end, hy_hmat **out);
+hy_status hy_hmat_destroy(hy_hmat *m);
+/* Stored row range, entries (rows x row length), row length, bytes. */
+hy_status hy_hmat_info(const hy_hmat *m, int64_t *row_begin, int64_t *row_end,
+                       int64_t *nnz, int64_t *row_len, int64_t *bytes);
+/* sigma_rows = the stored rows of H times psi: psi the whole state (n_det
+ * elements of the matrix's dtype, device), sigma_rows (row_end - row_begin)
+ * * N_beta elements; the accumulation runs in the matrix's dtype.  One pass
+ * over the stored matrix (streaming loads); psi stays resident in L2. */
+hy_status hy_hmat_apply(const hy_hmat *m, const void *psi, void *sigma_rows,
+                        void *stream);
+/* The stored row of determinant det (its alpha string inside the stored
+ * range): *len = row length; with cap >= *len, cols[j] (host) = column
+ * determinant index and vals[j] (host) = value (widened to double), in
+ * storage order (segments, then ascending beta columns within each). */
+hy_status hy_hmat_row(const hy_hmat *m, int64_t det, int64_t *cols,
+                      double *vals, int64_t cap, int64_t *len);
 
 /* ---------------------------------------------------------------------- */
 /* Determinant indexing (bit-exact)                                         */
@@ -201,6 +258,34 @@ hy_status hy_unrank(const hy_ham *h, const int64_t *idx, uint64_t *dets,
  * not alias.  The first call per dtype allocates the handle's workspace. */
 hy_status hy_apply_h(const hy_ham *h, const void *psi, void *sigma,
                      hy_dtype dt, void *stream);
+
+/* Rows [row_begin, row_end) of sigma = H psi, counted in alpha strings: the
+ * block sigma[row_begin * N_beta .. row_end * N_beta) written to sigma_rows
+ * (device, (row_end - row_begin) * N_beta elements of dt); psi is the whole
+ * state (n_det elements) and must not overlap sigma_rows.  This is the
+ * paper's distribution of H by rows of Omega_CIk with the state replicated
+ * (Sparse State-Vector Emulation section, parallelisation paragraph): each
+ * process forms the components of its own rows, and one all-gather of the
+ * blocks (or an all-reduce of the scalars formed from them) completes the
+ * operation.  Every element is computed by the same arithmetic in the same
+ * order as in hy_apply_h, so blocks of any split concatenate to hy_apply_h's
+ * sigma bit for bit.  The same-spin parts and the FP64 coupling cost the
+ * range's share of the full sweep; the float tensor-core coupling forms its
+ * per-string products for the range's strings and their single-excitation
+ * partners (for a contiguous range of more than a few rows, nearly all).
+ * 0 <= row_begin <= row_end <= N_alpha, else HY_ERR_ARG. */
+hy_status hy_apply_h_rows(const hy_ham *h, const void *psi, void *sigma_rows,
+                          hy_dtype dt, int64_t row_begin, int64_t row_end,
+                          void *stream);
+
+/* *out (device, one double) = <x|y> over a block of rows [row_begin,
+ * row_end) (alpha strings), x_rows and y_rows holding that block only
+ * ((row_end - row_begin) * N_beta elements each), with FP64 accuracy as
+ * hy_dot: the per-process partial of a row-distributed inner product, summed
+ * over processes by one all-reduce (Sparse State-Vector Emulation section). */
+hy_status hy_dot_rows(const hy_ham *h, const void *x_rows, const void *y_rows,
+                      hy_dtype dt, int64_t row_begin, int64_t row_end,
+                      double *out, void *stream);
 
 /* *e_out (device, one double) = <psi|sigma> with FP64 accuracy (see hy_dot); if
  * sigma_or_null is NULL, sigma = H psi is computed first into the
@@ -266,11 +351,21 @@ hy_status hy_pool_size(const hy_pool *p, int64_t *k);
 hy_status hy_pool_describe(const hy_pool *p, int64_t k, int32_t *desc);
 
 /* g_out[i] (device doubles) = 2 <sigma | A_{op_i} psi> for op_i =
- * ops_or_null[i] (device int32 list of n_ops pool indices), or for every
- * pool operator in order when ops_or_null is NULL (n_ops is then ignored
- * and the pool size is used).  With sigma = H psi this is dE/dtheta of
- * exp(theta A) psi at theta = 0 (the ADAPT-VQE screen).  Pool indices are
- * assumed valid (the caller checks them). */
+ * ops_or_null[i] (int32 list of n_ops pool indices the device can read), or
+ * for every pool operator in order when ops_or_null is NULL (n_ops is then
+ * ignored and the pool size is used).  With sigma = H psi this is
+ * dE/dtheta of exp(theta A) psi at theta = 0 (the ADAPT-VQE screen).
+ * Operator lists (the same rules hold for hy_pool_gradients_sparse and
+ * hy_pool_gradients_noalloc):
+ *   - a list in pageable host memory is range-checked before any launch: an
+ *     index outside [0, pool size) returns HY_ERR_ARG naming its position;
+ *     where the device cannot read pageable memory such a list is refused;
+ *   - a device, pinned or managed list may still be written by work queued
+ *     on the stream, so the kernels check it: a refused entry reads nothing
+ *     out of range and its gradient is returned as NaN, and the next screen
+ *     call on the same pool (once the stream has passed this one) returns
+ *     HY_ERR_ARG with the first refused position and index, then clears the
+ *     report. */
 hy_status hy_pool_gradients(const hy_ham *h, const hy_pool *p, const void *psi,
                             const void *sigma, const int32_t *ops_or_null,
                             int64_t n_ops, double *g_out, hy_dtype dt,

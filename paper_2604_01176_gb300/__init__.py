@@ -21,7 +21,7 @@ import torch
 from . import _abi
 from ._abi import HY_F32, HY_F64, HyError, check
 
-__all__ = ["Hamiltonian", "Pool", "Adapt", "Ranker", "Batch", "HyError", "dtype_code",
+__all__ = ["Hamiltonian", "Pool", "Adapt", "Ranker", "Batch", "ExplicitH", "HyError", "dtype_code",
            "stream_ptr", "occupations", "ranker_features", "touched_weights", "topk"]
 
 N_FEATURES = 16
@@ -34,7 +34,7 @@ def launch_count() -> int:
 
 # kernel classes of hy_profile_* (include/hyperion.h, hy_prof_class)
 PROFILE_CLASSES = ("hpsi", "hpsi_sparse", "excite", "sparse_excite", "screen", "screen_sparse",
-                   "reduce", "features")
+                   "reduce", "features", "hmat")
 
 
 def profile_enable(classes=()) -> None:
@@ -151,8 +151,14 @@ class Hamiltonian:
 
     def set_coupling(self, impl: str) -> None:
         """Float coupling phase A on the tensor cores ("tensor", default) or
-        the FP32 SIMT pipes ("simt")."""
-        check(_abi.load().hy_ham_set_coupling(self._h, {"tensor": 0, "simt": 1}[impl]))
+        the FP32 SIMT pipes ("simt"); "withheld" runs the tensor-core kernel
+        without its MMAs, a test of its bounded waits (wrong results)."""
+        check(_abi.load().hy_ham_set_coupling(
+            self._h, {"tensor": 0, "simt": 1, "withheld": 2}[impl]))
+
+    def set_wait_limit(self, polls: int) -> None:
+        """Polls of a tensor-core stage barrier before the wait gives up."""
+        check(_abi.load().hy_ham_set_wait_limit(self._h, int(polls)))
 
     def profile_coupling(self, on: bool = True):
         """Record CUDA events around the alpha-beta coupling of later apply_h calls."""
@@ -200,6 +206,35 @@ class Hamiltonian:
                                      dtype_code(psi.dtype), stream_ptr(stream)))
         return out
 
+    def apply_h_rows(self, psi: torch.Tensor, row_begin: int, row_end: int,
+                     out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Rows [row_begin, row_end) of H psi (alpha strings): a block of
+        (row_end - row_begin) * n_beta_str amplitudes."""
+        self._check_state(psi)
+        n = (int(row_end) - int(row_begin)) * self.n_beta_str
+        if out is None:
+            out = torch.empty(max(n, 0), dtype=psi.dtype, device=psi.device)
+        _require_cuda(out)
+        if out.dtype != psi.dtype or out.numel() != n:
+            raise ValueError(f"out must hold {n} amplitudes of the state's dtype")
+        check(_abi.load().hy_apply_h_rows(self._h, _ptr(psi), _ptr(out), dtype_code(psi.dtype),
+                                          int(row_begin), int(row_end), stream_ptr(stream)))
+        return out
+
+    def dot_rows(self, x_rows: torch.Tensor, y_rows: torch.Tensor, row_begin: int,
+                 row_end: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """<x|y> over the row block [row_begin, row_end) (FP64 accuracy)."""
+        n = (int(row_end) - int(row_begin)) * self.n_beta_str
+        _require_cuda(x_rows, y_rows)
+        if x_rows.numel() != n or y_rows.numel() != n or x_rows.dtype != y_rows.dtype:
+            raise ValueError(f"row blocks must hold {n} amplitudes of one dtype")
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device=x_rows.device)
+        check(_abi.load().hy_dot_rows(self._h, _ptr(x_rows), _ptr(y_rows),
+                                      dtype_code(x_rows.dtype), int(row_begin), int(row_end),
+                                      _ptr(out), stream_ptr(stream)))
+        return out
+
     def energy(self, psi: torch.Tensor, sigma: torch.Tensor | None = None,
                out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """<psi|H|psi> (or <psi|sigma>) as a 0-d float64 device tensor."""
@@ -235,6 +270,77 @@ class Hamiltonian:
         check(_abi.load().hy_renormalize(self._h, _ptr(psi), dtype_code(psi.dtype),
                                          _ptr(norm2), stream_ptr(stream)))
         return psi
+
+
+class ExplicitH:
+    """The Hamiltonian stored explicitly for the determinants whose alpha
+    string lies in [row_begin, row_end) (hy_hmat_*): every structural
+    nonzero of those rows, sliced by alpha string, in float64 or float32."""
+
+    def __init__(self, ham: Hamiltonian, dtype=torch.float64, row_begin: int = 0,
+                 row_end: int | None = None):
+        self.ham = ham
+        self.dtype = dtype
+        self.row_begin = int(row_begin)
+        self.row_end = ham.n_alpha_str if row_end is None else int(row_end)
+        h = ctypes.c_void_p()
+        check(_abi.load().hy_hmat_build(ham.handle, dtype_code(dtype), self.row_begin,
+                                        self.row_end, ctypes.byref(h)))
+        self._m = h
+        vals = [ctypes.c_int64() for _ in range(5)]
+        check(_abi.load().hy_hmat_info(self._m, *[ctypes.byref(v) for v in vals]))
+        _, _, self.nnz, self.row_len, self.bytes = [v.value for v in vals]
+
+    @staticmethod
+    def size(ham: Hamiltonian, dtype=torch.float64, row_begin: int = 0,
+             row_end: int | None = None) -> tuple[int, int]:
+        """(bytes, stored entries) of the rows [row_begin, row_end)."""
+        b, z = ctypes.c_int64(), ctypes.c_int64()
+        check(_abi.load().hy_hmat_bytes(ham.handle, dtype_code(dtype), int(row_begin),
+                                        ham.n_alpha_str if row_end is None else int(row_end),
+                                        ctypes.byref(b), ctypes.byref(z)))
+        return b.value, z.value
+
+    def close(self):
+        if getattr(self, "_m", None):
+            _abi.load().hy_hmat_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._m
+
+    def apply(self, psi: torch.Tensor, out: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+        """The stored rows of H psi ((row_end - row_begin) * n_beta_str)."""
+        self.ham._check_state(psi)
+        if psi.dtype != self.dtype:
+            raise TypeError("psi must have the matrix's dtype")
+        n = (self.row_end - self.row_begin) * self.ham.n_beta_str
+        if out is None:
+            out = torch.empty(n, dtype=psi.dtype, device=psi.device)
+        _require_cuda(out)
+        if out.numel() != n or out.dtype != psi.dtype:
+            raise ValueError(f"out must hold {n} amplitudes of the matrix's dtype")
+        check(_abi.load().hy_hmat_apply(self._m, _ptr(psi), _ptr(out), stream_ptr(stream)))
+        return out
+
+    def row(self, det: int):
+        """(columns, values) of the stored row of determinant det."""
+        n = ctypes.c_int64()
+        check(_abi.load().hy_hmat_row(self._m, int(det), None, None, 0, ctypes.byref(n)))
+        cols = np.zeros(n.value, dtype=np.int64)
+        vals = np.zeros(n.value, dtype=np.float64)
+        check(_abi.load().hy_hmat_row(self._m, int(det), cols.ctypes.data_as(ctypes.c_void_p),
+                                      vals.ctypes.data_as(ctypes.c_void_p), n.value,
+                                      ctypes.byref(n)))
+        return cols, vals
 
 
 class Pool:

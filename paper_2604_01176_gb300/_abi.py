@@ -84,11 +84,20 @@ SIGNATURES = {
     "hy_ham_pauli_table": (I32, [P, P, P, P, P]),
     "hy_ham_profile": (I32, [P, I32]),
     "hy_ham_set_coupling": (I32, [P, I32]),
+    "hy_ham_set_wait_limit": (I32, [P, I64]),
     "hy_ham_coupling_ms": (I32, [P, P]),
     "hy_pauli_table_build": (I32, [P, P, D, I32, D, I64, P, P, P, P, PI64, PI64]),
     "hy_rank": (I32, [P, P, P, I64, P]),
     "hy_unrank": (I32, [P, P, P, I64, P]),
     "hy_apply_h": (I32, [P, P, P, I32, P]),
+    "hy_apply_h_rows": (I32, [P, P, P, I32, I64, I64, P]),
+    "hy_dot_rows": (I32, [P, P, P, I32, I64, I64, P, P]),
+    "hy_hmat_bytes": (I32, [P, I32, I64, I64, PI64, PI64]),
+    "hy_hmat_build": (I32, [P, I32, I64, I64, P]),
+    "hy_hmat_destroy": (I32, [P]),
+    "hy_hmat_info": (I32, [P, PI64, PI64, PI64, PI64, PI64]),
+    "hy_hmat_apply": (I32, [P, P, P, P]),
+    "hy_hmat_row": (I32, [P, I64, P, P, I64, PI64]),
     "hy_support": (I32, [P, P, I32, P, I64, P, P]),
     "hy_apply_h_sparse": (I32, [P, P, P, I32, P, I64, P]),
     "hy_pool_gradients_sparse": (I32, [P, P, P, P, P, I64, P, I64, P, I32, P]),

@@ -329,7 +329,7 @@ hy_status gradient_dense(hy_adapt *a, const std::vector<double> &th, hy_dtype dt
     HY_TRY(cu(cudaMemcpyAsync(phi, psi, size_t(a->N) * es, cudaMemcpyDeviceToDevice, st), "copy"));
     HY_TRY(cu(cudaMemcpyAsync(lam, sigma, size_t(a->N) * es, cudaMemcpyDeviceToDevice, st), "copy"));
     for (size_t l = j; l-- > 0;) {
-        HY_TRY(hy_pool_gradients(a->h, a->p, phi, lam, a->d_ops + l, 1, a->d_ga + l, dt, st));
+        HY_TRY(hy::pool_gradients_unchecked(a->h, a->p, phi, lam, a->d_ops + l, 1, a->d_ga + l, dt, st));
         if (l == 0) break;
         HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], -th[l], phi, dt, 0, st));
         HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], -th[l], lam, dt, 0, st));
@@ -809,7 +809,7 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
             HY_TRY(hy::sstate_gradients(a->ss[di(bulk)][0], sigma, a->p, nullptr, a->K,
                                         a->sparse_m, a->d_g, st));
         else
-            HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, nullptr, a->K, a->d_g, bulk, st));
+            HY_TRY(hy::pool_gradients_unchecked(a->h, a->p, psi, sigma, nullptr, a->K, a->d_g, bulk, st));
         HY_TRY(xfer(a, a->h_gs, a->d_g, a->K * sizeof(double), cudaMemcpyDeviceToHost, st,
                     "screen readback"));
         HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
@@ -905,7 +905,7 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
             HY_TRY(hy::sstate_gradients(a->ss[di(bulk)][0], sigma, a->p, a->d_prop, Mp,
                                         a->sparse_m, a->d_gp, st));
         else
-            HY_TRY(hy_pool_gradients(a->h, a->p, psi, sigma, a->d_prop, Mp, a->d_gp, bulk, st));
+            HY_TRY(hy::pool_gradients_unchecked(a->h, a->p, psi, sigma, a->d_prop, Mp, a->d_gp, bulk, st));
         std::vector<double> gp(Mp);
         HY_TRY(xfer(a, gp.data(), a->d_gp, Mp * 8, cudaMemcpyDeviceToHost, st,
                     "proposals readback"));

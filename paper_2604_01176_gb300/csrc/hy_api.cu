@@ -111,10 +111,15 @@ struct hy_ham {
     // optional CUDA events around the alpha-beta coupling launch(es)
     bool prof = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    // float coupling phase A: 0 tensor cores (tcgen05), 1 FP32 SIMT
+    // float coupling phase A: 0 tensor cores (tcgen05), 1 FP32 SIMT, 2 the
+    // tensor-core kernel with its MMAs withheld (a test of the bounded waits)
     int cpl_impl = 0;
+    long long tc_spin_limit = 1ll << 26;   // polls of a stage barrier before giving up
     int *d_status = nullptr;        // device: a bounded wait of k_cpl_tc ran out
     int *h_status = nullptr;        // pinned host mirror, copied after each launch
+    // alpha strings whose coupling rows a row range needs (hy_apply_h_rows)
+    int32_t *d_jlist = nullptr;
+    int64_t jl_r0 = -1, jl_r1 = -1, jl_n = 0;
 };
 
 struct hy_pool {
@@ -129,6 +134,11 @@ struct hy_pool {
     uint32_t *d_aent = nullptr, *d_bent = nullptr;
     int64_t *d_aoff = nullptr, *d_acnt = nullptr, *d_boff = nullptr, *d_bcnt = nullptr;
     int32_t *d_desc = nullptr;   // [K][11] operator descriptors (ranker features)
+    // first refused entry of a device operator list (position << 32 | index),
+    // ~0 when none; the pinned mirror is copied after each screen that read
+    // a device list and reported by the next screen call on this pool
+    unsigned long long *d_bad = nullptr;
+    unsigned long long *h_bad = nullptr;
 };
 
 struct hy_batch {
@@ -258,9 +268,53 @@ hy_status upload_csr(DevArena &ar, const hy::CsrHost &M, DevCsr<T> &D)
     return HY_OK;
 }
 
-template <typename T>
-hy_status apply_h_t(hy_ham *h, const T *psi, T *sigma, cudaStream_t st)
+// Phase A of the float coupling forms T rows per alpha string J; the output
+// rows [r0, r1) need the strings themselves and their single-excitation
+// partners.  Every J for the whole range; else a list (sorted, uploaded once
+// per distinct range and kept on the handle).
+hy_status coupling_jlist(hy_ham *h, int64_t r0, int64_t r1, const int32_t **list, int64_t *nJ)
 {
+    if (r0 == 0 && r1 == h->Na) {
+        *list = nullptr;
+        *nJ = h->Na;
+        return HY_OK;
+    }
+    if (h->jl_r0 != r0 || h->jl_r1 != r1) {
+        std::vector<uint8_t> need(size_t(h->Na), 0);
+        const int nex = h->A.nex;
+        for (int64_t a = r0; a < r1; ++a) {
+            need[size_t(a)] = 1;
+            for (int e = 0; e < nex; ++e) need[h->A.ex[size_t(a) * nex + e] & 0xFFFFu] = 1;
+        }
+        std::vector<int32_t> js;
+        for (int64_t j = 0; j < h->Na; ++j)
+            if (need[size_t(j)]) js.push_back(int32_t(j));
+        if (!h->d_jlist) {
+            cudaError_t e = cudaMalloc(&h->d_jlist, size_t(h->Na) * sizeof(int32_t));
+            if (e != cudaSuccess) {
+                h->d_jlist = nullptr;
+                return cuda_fail(e, "cudaMalloc(coupling row list)");
+            }
+        }
+        HY_CUDA(cudaMemcpy(h->d_jlist, js.data(), js.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice), "upload coupling row list");
+        h->jl_r0 = r0;
+        h->jl_r1 = r1;
+        h->jl_n = int64_t(js.size());
+    }
+    *list = h->d_jlist;
+    *nJ = h->jl_n;
+    return HY_OK;
+}
+
+// sigma rows [r0, r1) (alpha strings) of H psi; sigma holds those rows only.
+// Every output element is formed by the same arithmetic in the same order
+// whatever the range, so shards concatenate to the full sigma bit for bit.
+template <typename T>
+hy_status apply_h_t(hy_ham *h, const T *psi, T *sigma, cudaStream_t st, int64_t r0, int64_t r1)
+{
+    const int64_t nr = r1 - r0;
+    if (nr <= 0) return HY_OK;
     const WsLayout L = ws_layout(h, n_partials_needed(h, 0), sizeof(T));
     // float: room for the dense coupling's intermediate T after the state
     // buffers, sized before any launch; without it the direct kernel runs
@@ -287,14 +341,15 @@ hy_status apply_h_t(hy_ham *h, const T *psi, T *sigma, cudaStream_t st)
         Ma = &h->Ma32; Mb = &h->Mb32; V = h->d_V32;
     }
     (void)f64;
-    hy::ProfScope prof(HY_PROF_HPSI, st, 2.0 * double(h->N) * sizeof(T),
-                       2.0 * double(hy::ham_connections(h)) * double(h->N));
-    HY_CUDA(hy::k::spmm<T>(Ma->ptr, Ma->col, Ma->val, h->Na, psi, sigma, h->Nb,
+    const double rows_det = double(nr) * double(h->Nb);
+    hy::ProfScope prof(HY_PROF_HPSI, st, 2.0 * rows_det * sizeof(T),
+                       2.0 * double(hy::ham_connections(h)) * rows_det);
+    HY_CUDA(hy::k::spmm<T>(Ma->ptr + r0, Ma->col, Ma->val, nr, psi, sigma, h->Nb,
                            false, st), "alpha part");
-    HY_CUDA(hy::k::transpose<T>(psi, psiT, h->Na, h->Nb, st), "transpose");
-    HY_CUDA(hy::k::spmm<T>(Mb->ptr, Mb->col, Mb->val, h->Nb, psiT, tau, h->Na,
+    HY_CUDA(hy::k::transpose<T>(psi + r0 * h->Nb, psiT, nr, h->Nb, st), "transpose");
+    HY_CUDA(hy::k::spmm<T>(Mb->ptr, Mb->col, Mb->val, h->Nb, psiT, tau, nr,
                            false, st), "beta part");
-    HY_CUDA(hy::k::add_transposed<T>(tau, sigma, h->Na, h->Nb, st), "beta add");
+    HY_CUDA(hy::k::add_transposed<T>(tau, sigma, nr, h->Nb, st), "beta add");
     if constexpr (sizeof(T) == sizeof(float)) {
         if (dense) {
             hy::k::CplDenseArgs d;
@@ -313,10 +368,15 @@ hy_status apply_h_t(hy_ham *h, const T *psi, T *sigma, cudaStream_t st)
             d.Na = h->Na;
             d.Nb = h->Nb;
             d.Nbp = Nbp;
+            d.row0 = r0;
+            d.row1 = r1;
+            hy_status sj = coupling_jlist(h, r0, r1, &d.jlist, &d.nJ);
+            if (sj != HY_OK) return sj;
             if (h->prof) cudaEventRecord(h->ev0, st);
             bool done = false;
-            if (h->cpl_impl == 0 && h->d_status) {
-                const cudaError_t e = hy::k::coupling_tc(d, h->d_status, h->num_sms, st);
+            if ((h->cpl_impl == 0 || h->cpl_impl == 2) && h->d_status) {
+                const cudaError_t e = hy::k::coupling_tc(d, h->d_status, h->tc_spin_limit,
+                                                         h->cpl_impl == 0 ? 1 : 0, h->num_sms, st);
                 if (e == cudaSuccess) {
                     HY_CUDA(hy::k::coupling_gather(d, h->num_sms, st), "alpha-beta gather");
                     HY_CUDA(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int),
@@ -345,6 +405,8 @@ hy_status apply_h_t(hy_ham *h, const T *psi, T *sigma, cudaStream_t st)
     a.nexb = h->B.nex;
     a.Na = h->Na;
     a.Nb = h->Nb;
+    a.row0 = r0;
+    a.row1 = r1;
     if (h->prof) cudaEventRecord(h->ev0, st);
     HY_CUDA(hy::k::coupling<T>(a, h->num_sms, st), "alpha-beta coupling");
     if (h->prof) cudaEventRecord(h->ev1, st);
@@ -352,14 +414,16 @@ hy_status apply_h_t(hy_ham *h, const T *psi, T *sigma, cudaStream_t st)
 }
 
 template <typename T>
-hy_status dot_t(hy_ham *h, const T *x, const T *y, double *out, cudaStream_t st)
+hy_status dot_t(hy_ham *h, const T *x, const T *y, double *out, cudaStream_t st,
+                int64_t len = -1)
 {
+    if (len < 0) len = h->N;
     const WsLayout L = ws_layout(h, n_partials_needed(h, 0), sizeof(T));
     hy_status s = ensure_ws(h, L.total);
     if (s != HY_OK) return s;
     double *partials = reinterpret_cast<double *>(static_cast<char *>(h->ws) + L.partials);
-    hy::ProfScope prof(HY_PROF_REDUCE, st, 2.0 * double(h->N) * sizeof(T));
-    HY_CUDA(hy::k::dot<T>(x, y, h->N, partials, h->dot_blocks, out, st), "dot");
+    hy::ProfScope prof(HY_PROF_REDUCE, st, 2.0 * double(len) * sizeof(T));
+    HY_CUDA(hy::k::dot<T>(x, y, len, partials, h->dot_blocks, out, st), "dot");
     return HY_OK;
 }
 
@@ -385,7 +449,7 @@ hy_status energy_t(hy_ham *h, const T *psi, const T *sigma, double *e, cudaStrea
     if (s != HY_OK) return s;
     if (!sigma) {
         T *tmp = reinterpret_cast<T *>(static_cast<char *>(h->ws) + L.buf0);
-        s = apply_h_t<T>(h, psi, tmp, st);
+        s = apply_h_t<T>(h, psi, tmp, st, 0, h->Na);
         if (s != HY_OK) return s;
         sigma = tmp;
     }
@@ -417,6 +481,8 @@ hy_status grad_t(hy_ham *h, const hy_pool *p, const T *psi, const T *sigma,
     a.CH = grad_chunks(h, n_ops);
     a.partials = reinterpret_cast<double *>(static_cast<char *>(h->ws) + L.partials);
     a.g = g;
+    a.K = int64_t(p->ops.size());
+    a.bad = p->d_bad;
     double bytes = 0.0;     // pairs of the listed operators (known for the whole pool)
     if (!ops)
         for (const auto &od : p->opd)
@@ -617,6 +683,7 @@ hy_status hy_ham_destroy(hy_ham *h)
     if (h->ev1) cudaEventDestroy(h->ev1);
     cudaFree(h->d_status);
     if (h->h_status) cudaFreeHost(h->h_status);
+    if (h->d_jlist) cudaFree(h->d_jlist);
     h->arena.release();
     if (h->ws) cudaFree(h->ws);
     cudaFree(h->tw.cnt);
@@ -631,8 +698,17 @@ hy_status hy_ham_destroy(hy_ham *h)
 hy_status hy_ham_set_coupling(hy_ham *h, int impl)
 {
     if (!h) return fail(HY_ERR_ARG, "handle is NULL");
-    if (impl != 0 && impl != 1) return fail(HY_ERR_ARG, "impl must be 0 (tensor cores) or 1 (SIMT)");
+    if (impl < 0 || impl > 2)
+        return fail(HY_ERR_ARG, "impl must be 0 (tensor cores), 1 (SIMT) or 2 (test mode)");
     h->cpl_impl = impl;
+    return HY_OK;
+}
+
+hy_status hy_ham_set_wait_limit(hy_ham *h, int64_t polls)
+{
+    if (!h) return fail(HY_ERR_ARG, "handle is NULL");
+    if (polls < 1) return fail(HY_ERR_ARG, "the wait limit must be at least one poll");
+    h->tc_spin_limit = polls;
     return HY_OK;
 }
 
@@ -732,9 +808,57 @@ hy_status hy_apply_h(const hy_ham *hc, const void *psi, void *sigma, hy_dtype dt
     }
     if (dt == HY_F64)
         return apply_h_t<double>(h, static_cast<const double *>(psi),
-                                 static_cast<double *>(sigma), as_stream(stream));
+                                 static_cast<double *>(sigma), as_stream(stream), 0, h->Na);
     return apply_h_t<float>(h, static_cast<const float *>(psi),
-                            static_cast<float *>(sigma), as_stream(stream));
+                            static_cast<float *>(sigma), as_stream(stream), 0, h->Na);
+}
+
+hy_status hy_dot_rows(const hy_ham *hc, const void *x_rows, const void *y_rows, hy_dtype dt,
+                      int64_t row_begin, int64_t row_end, double *out, void *stream)
+{
+    hy_ham *h = const_cast<hy_ham *>(hc);
+    if (!h || !out || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
+    if (row_begin < 0 || row_end < row_begin || row_end > h->Na)
+        return fail(HY_ERR_ARG, "row range outside [0, N_alpha]");
+    const int64_t len = (row_end - row_begin) * h->Nb;
+    if (len > 0 && (!x_rows || !y_rows)) return fail(HY_ERR_ARG, "bad arguments");
+    if (len == 0) {
+        HY_CUDA(cudaMemsetAsync(out, 0, sizeof(double), as_stream(stream)), "zero dot");
+        return HY_OK;
+    }
+    if (dt == HY_F64)
+        return dot_t<double>(h, static_cast<const double *>(x_rows),
+                             static_cast<const double *>(y_rows), out, as_stream(stream), len);
+    return dot_t<float>(h, static_cast<const float *>(x_rows), static_cast<const float *>(y_rows),
+                        out, as_stream(stream), len);
+}
+
+hy_status hy_apply_h_rows(const hy_ham *hc, const void *psi, void *sigma_rows, hy_dtype dt,
+                          int64_t row_begin, int64_t row_end, void *stream)
+{
+    hy_ham *h = const_cast<hy_ham *>(hc);
+    if (!h || !psi || !sigma_rows || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
+    if (row_begin < 0 || row_end < row_begin || row_end > h->Na)
+        return fail(HY_ERR_ARG, "row range [" + std::to_string(row_begin) + ", " +
+                                    std::to_string(row_end) + ") outside [0, " +
+                                    std::to_string(h->Na) + ")");
+    const size_t es = dt == HY_F64 ? 8 : 4;
+    const char *pb = static_cast<const char *>(psi), *sb = static_cast<const char *>(sigma_rows);
+    const size_t psi_bytes = size_t(h->N) * es;
+    const size_t sig_bytes = size_t(row_end - row_begin) * size_t(h->Nb) * es;
+    if (sb < pb + psi_bytes && pb < sb + sig_bytes)
+        return fail(HY_ERR_ARG, "psi and sigma_rows must not overlap");
+    if (h->h_status && *h->h_status) {
+        *h->h_status = 0;
+        HY_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), as_stream(stream)), "status reset");
+        return fail(HY_ERR_TIMEOUT, "an earlier H psi's tensor-core coupling timed out");
+    }
+    if (dt == HY_F64)
+        return apply_h_t<double>(h, static_cast<const double *>(psi),
+                                 static_cast<double *>(sigma_rows), as_stream(stream), row_begin,
+                                 row_end);
+    return apply_h_t<float>(h, static_cast<const float *>(psi), static_cast<float *>(sigma_rows),
+                            as_stream(stream), row_begin, row_end);
 }
 
 hy_status hy_energy(const hy_ham *hc, const void *psi, const void *sigma_or_null,
@@ -846,6 +970,10 @@ hy_status hy_pool_create(const hy_ham *h, hy_pool_kind kind, hy_pool **out)
         desc.reserve(p->ops.size() * 11);
         for (const auto &op : p->ops) desc.insert(desc.end(), op.desc, op.desc + 11);
         up(ar.upload(&p->d_desc, desc.data(), desc.size()), "upload descriptors");
+        const unsigned long long none = ~0ull;
+        up(ar.upload(&p->d_bad, &none, 1), "upload list-check flag");
+        up(cudaMallocHost(&p->h_bad, sizeof(unsigned long long)), "list-check mirror");
+        if (p->h_bad) *p->h_bad = none;
     }
     if (s != HY_OK) {
         std::string msg = g_err;
@@ -860,6 +988,7 @@ hy_status hy_pool_create(const hy_ham *h, hy_pool_kind kind, hy_pool **out)
 hy_status hy_pool_destroy(hy_pool *p)
 {
     if (!p) return HY_OK;
+    if (p->h_bad) cudaFreeHost(p->h_bad);
     p->arena.release();
     delete p;
     return HY_OK;
@@ -890,16 +1019,100 @@ hy_status hy_pool_gradients(const hy_ham *hc, const hy_pool *p, const void *psi,
     if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
     if (!ops_or_null) n_ops = int64_t(p->ops.size());
     if (n_ops < 0 || n_ops > (int64_t(1) << 24)) return fail(HY_ERR_ARG, "n_ops out of range");
-    if (dt == HY_F64)
-        return grad_t<double>(h, p, static_cast<const double *>(psi),
-                              static_cast<const double *>(sigma), ops_or_null, n_ops,
-                              g_out, as_stream(stream));
-    return grad_t<float>(h, p, static_cast<const float *>(psi),
-                         static_cast<const float *>(sigma), ops_or_null, n_ops, g_out,
-                         as_stream(stream));
+    bool device_list = false;
+    hy_status s = hy::check_op_list(p, ops_or_null, n_ops, &device_list, stream);
+    if (s != HY_OK) return s;
+    s = hy::pool_gradients_unchecked(h, p, psi, sigma, ops_or_null, n_ops, g_out, dt, stream);
+    if (s == HY_OK && device_list) s = hy::fetch_op_list_flag(p, stream);
+    return s;
 }
 
 }  // extern "C"
+
+namespace hy {
+
+HamView ham_view(const hy_ham *h)
+{
+    HamView v;
+    v.n = h->n; v.na = h->na; v.nb = h->nb; v.device = h->device; v.num_sms = h->num_sms;
+    v.Na = h->Na; v.Nb = h->Nb; v.N = h->N;
+    v.A = &h->A; v.B = &h->B; v.kt = &h->kt;
+    return v;
+}
+
+hy_status pool_gradients_unchecked(const hy_ham *hc, const hy_pool *p, const void *psi,
+                                   const void *sigma, const int32_t *ops, int64_t n_ops,
+                                   double *g_out, hy_dtype dt, void *stream)
+{
+    hy_ham *h = const_cast<hy_ham *>(hc);
+    if (dt == HY_F64)
+        return grad_t<double>(h, p, static_cast<const double *>(psi),
+                              static_cast<const double *>(sigma), ops, n_ops, g_out,
+                              as_stream(stream));
+    return grad_t<float>(h, p, static_cast<const float *>(psi),
+                         static_cast<const float *>(sigma), ops, n_ops, g_out,
+                         as_stream(stream));
+}
+
+// Operator lists of the public screens.  A list in pageable host memory (the
+// caller wrote it on the host) is range-checked here, before any launch; a
+// device, pinned or managed list may still be written by work queued on the
+// stream, so the kernels check it (refuse_op: the entry's gradient becomes
+// NaN) and the first refused entry is reported by the next screen call on the
+// pool.  Indices are compared with the pool size.
+hy_status check_op_list(const hy_pool *p, const int32_t *ops, int64_t n_ops,
+                        bool *device_list, void *stream)
+{
+    *device_list = false;
+    const int64_t K = int64_t(p->ops.size());
+    if (p->h_bad && *p->h_bad != ~0ull) {
+        const unsigned long long v = *p->h_bad;
+        *p->h_bad = ~0ull;
+        HY_CUDA(cudaMemsetAsync(p->d_bad, 0xFF, sizeof(unsigned long long), as_stream(stream)),
+                "list-check reset");
+        return fail(HY_ERR_ARG, "an earlier screen's operator list held " +
+                                    std::to_string(int32_t(uint32_t(v & 0xFFFFFFFFull))) +
+                                    " at position " + std::to_string(v >> 32) +
+                                    ", not a pool index (pool size " + std::to_string(K) +
+                                    "); that gradient was returned as NaN");
+    }
+    if (!ops || n_ops == 0) return HY_OK;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ops) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HY_ERR_ARG, "ops_or_null is not a pointer the CUDA runtime can classify");
+    }
+    if (at.type != cudaMemoryTypeUnregistered) {
+        *device_list = true;
+        return HY_OK;
+    }
+    int dev = 0, pageable = 0;
+    HY_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    HY_CUDA(cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev),
+            "device attribute");
+    if (!pageable)
+        return fail(HY_ERR_ARG, "ops_or_null is pageable host memory the device cannot read; "
+                                "pass a device, pinned or managed list");
+    for (int64_t i = 0; i < n_ops; ++i)
+        if (ops[i] < 0 || int64_t(ops[i]) >= K)
+            return fail(HY_ERR_ARG, "ops_or_null[" + std::to_string(i) + "] = " +
+                                        std::to_string(ops[i]) +
+                                        " is not a pool index (pool size " + std::to_string(K) +
+                                        ")");
+    return HY_OK;
+}
+
+// after a screen that read a device list: bring the kernels' refusal flag to
+// the host (stream-ordered; read by the next screen call)
+hy_status fetch_op_list_flag(const hy_pool *p, void *stream)
+{
+    HY_CUDA(cudaMemcpyAsync(p->h_bad, p->d_bad, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, as_stream(stream)),
+            "list-check flag copy");
+    return HY_OK;
+}
+
+}  // namespace hy
 
 // ---------------------------------------------------------------------------
 // Allocation-free gradient screen.  Some callers cannot let a library call
@@ -963,6 +1176,8 @@ hy_status grad_noalloc_t(hy_ham *h, const hy_pool *p, const T *psi, const T *sig
     a.CH = grad_chunks(h, n_ops);
     a.partials = scratch;
     a.g = g;
+    a.K = int64_t(p->ops.size());
+    a.bad = p->d_bad;
     HY_CUDA(hy::k::grad<T>(a, st), "pool gradients (no-alloc)");
     return HY_OK;
 }
@@ -987,16 +1202,22 @@ hy_status hy_pool_gradients_noalloc(const hy_ham *hc, const hy_pool *p, const vo
         return fail(HY_ERR_ARG, "n_ops = " + std::to_string(n_ops) +
                                     " needs more partial sums than the no-alloc scratch holds (" +
                                     std::to_string(kNoAllocPartials) + "); use hy_pool_gradients");
+    bool device_list = false;
+    hy_status s = hy::check_op_list(p, ops_or_null, n_ops, &device_list, stream);
+    if (s != HY_OK) return s;
     double *scratch = nullptr;
-    hy_status s = noalloc_scratch(&scratch);
+    s = noalloc_scratch(&scratch);
     if (s != HY_OK) return s;
     if (dt == HY_F64)
-        return grad_noalloc_t<double>(h, p, static_cast<const double *>(psi),
-                                      static_cast<const double *>(sigma), ops_or_null, n_ops,
-                                      g_out, scratch, as_stream(stream));
-    return grad_noalloc_t<float>(h, p, static_cast<const float *>(psi),
-                                 static_cast<const float *>(sigma), ops_or_null, n_ops, g_out,
-                                 scratch, as_stream(stream));
+        s = grad_noalloc_t<double>(h, p, static_cast<const double *>(psi),
+                                   static_cast<const double *>(sigma), ops_or_null, n_ops,
+                                   g_out, scratch, as_stream(stream));
+    else
+        s = grad_noalloc_t<float>(h, p, static_cast<const float *>(psi),
+                                  static_cast<const float *>(sigma), ops_or_null, n_ops, g_out,
+                                  scratch, as_stream(stream));
+    if (s == HY_OK && device_list) s = hy::fetch_op_list_flag(p, stream);
+    return s;
 }
 
 hy_status hy_apply_excitation(const hy_ham *hc, const hy_pool *p, int64_t k,
@@ -1138,9 +1359,12 @@ hy_status hy_pool_gradients_sparse(const hy_ham *h, const hy_pool *p, const void
     if (p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
     if (!ops_or_null) n_ops = int64_t(p->ops.size());
     if (n_ops < 0) return fail(HY_ERR_ARG, "n_ops out of range");
+    bool device_list = false;
+    hy_status st = hy::check_op_list(p, ops_or_null, n_ops, &device_list, stream);
+    if (st != HY_OK) return st;
     hy_ham *hm = const_cast<hy_ham *>(h);
     const WsLayout L = ws_layout(hm, n_partials_needed(hm, n_ops), dt == HY_F64 ? 8 : 4);
-    hy_status st = ensure_ws(hm, L.total);
+    st = ensure_ws(hm, L.total);
     if (st != HY_OK) return st;
     auto fill = [&](auto &a) {
         a.list = list; a.m = m; a.d_m = nullptr; a.cap = m; a.bits = nullptr;
@@ -1148,7 +1372,7 @@ hy_status hy_pool_gradients_sparse(const hy_ham *h, const hy_pool *p, const void
         a.partials = reinterpret_cast<double *>(static_cast<char *>(hm->ws) + L.partials);
         a.desc = p->d_desc; a.ops = ops_or_null; a.n_ops = n_ops;
         a.astr = h->d_astr; a.bstr = h->d_bstr; a.binom33 = h->d_binom; a.n = h->n;
-        a.Nb = h->Nb; a.g = g_out;
+        a.Nb = h->Nb; a.g = g_out; a.K = int64_t(p->ops.size()); a.bad = p->d_bad;
     };
     hy::ProfScope prof(HY_PROF_SCREEN_SPARSE, stream, 0.0);
     if (dt == HY_F64) {
@@ -1164,7 +1388,7 @@ hy_status hy_pool_gradients_sparse(const hy_ham *h, const hy_pool *p, const void
         fill(a);
         HY_CUDA(hy::k::grad_sparse<float>(a, h->num_sms, as_stream(stream)), "sparse screen");
     }
-    return HY_OK;
+    return device_list ? hy::fetch_op_list_flag(p, stream) : HY_OK;
 }
 
 hy_status hy_ranker_features(const hy_ham *h, const hy_pool *p, const void *psi,
@@ -1976,7 +2200,7 @@ hy_status sstate_gradients(const SparseState *sc, const void *lam, const hy_pool
         a.chunks = chunks; a.partials = s->partials;
         a.desc = p->d_desc; a.ops = ops; a.n_ops = n_ops;
         a.astr = h->d_astr; a.bstr = h->d_bstr; a.binom33 = h->d_binom; a.n = h->n;
-        a.Nb = h->Nb; a.g = g;
+        a.Nb = h->Nb; a.g = g; a.K = int64_t(p->ops.size()); a.bad = p->d_bad;
     };
     if (s->dt == HY_F64) {
         hy::k::SparseGradArgs<double> a;

@@ -25,8 +25,9 @@
 // chunk are loaded while the current one is built.  A warp of its own issues
 // the MMAs (M = 64, N = 128, K = 8), so its wait for the tensor cores to
 // accept them never stalls a builder, and commits each stage to its mbarrier.
-// Every wait is bounded: on a timeout the kernel records it in *status, waits
-// (bounded) for its own MMAs, frees its tensor memory and returns.
+// Every wait is bounded (spin_limit polls of the mbarrier): on a timeout the
+// kernel records it in *status, waits (bounded) for its own MMAs, frees its
+// tensor memory and returns.
 #include "hy_kernels.cuh"
 
 namespace hy {
@@ -50,7 +51,6 @@ constexpr size_t kWBytes = size_t(kTcM) * kWRow * 4;       // W_J in FP32, 65 KB
 constexpr size_t kABytes = size_t(kTcM) * kTcKc * 4;       // one A chunk, 8 KB
 constexpr size_t kBBytes = size_t(kTcN) * kTcKc * 4;       // one G chunk, 16 KB
 constexpr size_t kStage = 2 * kABytes + 2 * kBBytes;       // hi, lo of both
-constexpr long long kSpinLimit = 1ll << 26;
 
 __device__ __forceinline__ uint32_t saddr(const void *p)
 {
@@ -87,11 +87,12 @@ __device__ __forceinline__ void commit(uint64_t *bar)
                  ::"r"(saddr(bar)) : "memory");
 }
 
-// bounded wait for the phase with parity `par` of an mbarrier
-__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t par)
+// bounded wait for the phase with parity `par` of an mbarrier: at most
+// `limit` polls
+__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t par, long long limit)
 {
     uint32_t done = 0;
-    for (long long it = 0; it < kSpinLimit; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      "selp.u32 %0, 1, 0, p;\n}"
                      : "=r"(done) : "r"(saddr(bar)), "r"(par) : "memory");
@@ -133,8 +134,11 @@ size_t cpl_tc_smem(int64_t Nb)
     return kWBytes + 2 * kStage + kTcK * 4 + 2 * kTcN * 4 + 64 + size_t((Nb + 3) / 4 * 16);
 }
 
+// issue = 0 is a test mode: nothing is multiplied or committed, so every
+// stage barrier stays pending and the builders' bounded waits run out (the
+// kernel then reports a timeout in *status and returns; no MMA is in flight)
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_cpl_tc(CplDenseArgs a, int *status)
+k_cpl_tc(CplDenseArgs a, int *status, long long spin_limit, int issue)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     float *Wf = reinterpret_cast<float *>(sm);                  // [64][kWRow]
@@ -172,7 +176,7 @@ k_cpl_tc(CplDenseArgs a, int *status)
     // wait until every commit made to a stage so far has completed
     auto drain = [&](uint64_t *b, uint32_t &waited, uint32_t issued) {
         while (ok && waited < issued) {
-            if (!wait_bar(b, waited & 1u)) {
+            if (!wait_bar(b, waited & 1u, spin_limit)) {
                 ok = false;
                 atomicExch(status, 1);
             }
@@ -182,7 +186,8 @@ k_cpl_tc(CplDenseArgs a, int *status)
     const bool gb = tid < kGThreadsTc;                        // a G builder
     const int col = tid & (kTcN - 1), half = (tid >> 7) & 1;  // 2 G builders per column
 
-    for (int64_t J = blockIdx.x; J < a.Na && ok; J += gridDim.x) {
+    for (int64_t jj = blockIdx.x; jj < a.nJ && ok; jj += gridDim.x) {
+        const int64_t J = a.jlist ? int64_t(a.jlist[jj]) : jj;
         // W_J in FP32 for the 64 MMA rows, Wd_J for the diagonal slot and
         // psi's row J.  The previous J's MMAs have all been waited for.
         const uint32_t jm = a.astr[J];
@@ -298,7 +303,7 @@ k_cpl_tc(CplDenseArgs a, int *status)
                 if (!ok) break;
                 // the issuing warp builds nothing: its wait for the tensor
                 // cores to accept the MMAs stays off the builders' path
-                if (warp == kIssueWarp && lane == 0) {
+                if (warp == kIssueWarp && lane == 0 && issue) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t ah = saddr(Ah), al = saddr(Al), bh = saddr(Bh), bl = saddr(Bl);
 #pragma unroll
@@ -351,8 +356,8 @@ k_cpl_tc(CplDenseArgs a, int *status)
     }
     // on a timeout, give the MMAs still in flight a bounded chance to finish
     if (!ok) {
-        while (waited0 < issued0) wait_bar(&bar[0], (waited0++) & 1u);
-        while (waited1 < issued1) wait_bar(&bar[1], (waited1++) & 1u);
+        while (waited0 < issued0) wait_bar(&bar[0], (waited0++) & 1u, spin_limit);
+        while (waited1 < issued1) wait_bar(&bar[1], (waited1++) & 1u, spin_limit);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -361,7 +366,8 @@ k_cpl_tc(CplDenseArgs a, int *status)
                      ::"r"(tmem), "r"(kTmemCols));
 }
 
-cudaError_t coupling_tc(const CplDenseArgs &a, int *status, int num_sms, cudaStream_t st)
+cudaError_t coupling_tc(const CplDenseArgs &a, int *status, long long spin_limit, int issue,
+                        int num_sms, cudaStream_t st)
 {
     if (a.Na == 0 || a.Nb == 0) return cudaSuccess;
     if (a.nexa > kTcM || a.n > 16) return cudaErrorInvalidValue;
@@ -369,9 +375,11 @@ cudaError_t coupling_tc(const CplDenseArgs &a, int *status, int num_sms, cudaStr
     cudaError_t err = cudaFuncSetAttribute(k_cpl_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            int(smem));
     if (err != cudaSuccess) return err;
+    if (a.nJ == 0) return cudaSuccess;
     int64_t grid = num_sms;
-    if (grid > a.Na) grid = a.Na;
-    k_cpl_tc<<<unsigned(grid), kTcThreads, smem, st>>>(a, status); hy::count_launch();
+    if (grid > a.nJ) grid = a.nJ;
+    k_cpl_tc<<<unsigned(grid), kTcThreads, smem, st>>>(a, status, spin_limit, issue);
+    hy::count_launch();
     return cudaGetLastError();
 }
 

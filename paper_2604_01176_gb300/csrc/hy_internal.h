@@ -218,6 +218,30 @@ int64_t ham_connections(const hy_ham *h);
 // (its row sum and one per pair j <= b of its beta electrons)
 int64_t ham_list_weight_adds(const hy_ham *h);
 const int64_t *sstate_list(const SparseState *s);    // device pointer
+
+// Read-only view of a Hamiltonian handle for the library's other
+// translation units (the explicit H build reads the string spaces and the
+// folded tables).
+struct HamView {
+    int n, na, nb, device, num_sms;
+    int64_t Na, Nb, N;
+    const StringSpace *A, *B;
+    const KernelTables *kt;
+};
+HamView ham_view(const hy_ham *h);
+void set_last_error(const std::string &msg);
+void count_launch();
+
+// hy_pool_gradients without the operator-list checks (the ADAPT driver's
+// lists are built by the library and always valid)
+hy_status pool_gradients_unchecked(const hy_ham *hc, const hy_pool *p, const void *psi,
+                                   const void *sigma, const int32_t *ops, int64_t n_ops,
+                                   double *g_out, hy_dtype dt, void *stream);
+// operator lists of the public screens (hy_api.cu): host lists are checked
+// here, device lists by the kernels with a deferred report
+hy_status check_op_list(const hy_pool *p, const int32_t *ops, int64_t n_ops,
+                        bool *device_list, void *stream);
+hy_status fetch_op_list_flag(const hy_pool *p, void *stream);
 int64_t sstate_cap(const SparseState *s);
 
 }  // namespace hy

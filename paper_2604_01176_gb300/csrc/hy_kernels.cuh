@@ -33,6 +33,7 @@ struct CouplingArgs {
     const T *V;             // n^4 alpha-beta coupling
     int n, nexa, nexb;
     int64_t Na, Nb;
+    int64_t row0, row1;     // output alpha rows [row0, row1); sigma holds row row0 first
 };
 
 template <typename T>
@@ -50,7 +51,21 @@ struct GradArgs {
     int CH;                 // row chunks per op (grid.y)
     double *partials;       // [n_ops][CH]
     double *g;              // [n_ops]
+    int64_t K;              // pool size: listed indices outside [0, K) are refused
+    unsigned long long *bad;   // (position << 32 | index) of the first refused entry
 };
+
+// A listed pool index outside [0, K): the entry's partial becomes NaN (so its
+// gradient reads NaN) and the smallest (position, index) key is kept in *bad
+// for the host to report; nothing out of range is read.
+__device__ __forceinline__ bool refuse_op(int64_t i, int k, int64_t K, unsigned long long *bad)
+{
+    if (k >= 0 && k < K) return false;
+    if (bad && threadIdx.x == 0)
+        atomicMin(bad, (static_cast<unsigned long long>(i) << 32) |
+                           static_cast<unsigned long long>(static_cast<uint32_t>(k)));
+    return true;
+}
 
 // float alpha-beta coupling through the dense intermediate T (hy_sigma.cu)
 struct CplDenseArgs {
@@ -64,6 +79,11 @@ struct CplDenseArgs {
     const float *V;         // n^4
     int n, nexa, nexb;
     int64_t Na, Nb, Nbp;    // Nbp: row stride of T (multiple of 64)
+    // phase A: the alpha strings J whose T rows are formed -- jlist[0 .. nJ)
+    // (device), or every J when jlist is null (nJ = Na)
+    const int32_t *jlist;
+    int64_t nJ;
+    int64_t row0, row1;     // phase B: output alpha rows; sigma holds row row0 first
 };
 size_t cpl_dense_smem(int64_t Nb, int n);
 // phase A (SIMT) + phase B
@@ -73,7 +93,8 @@ cudaError_t coupling_gather(const CplDenseArgs &a, int num_sms, cudaStream_t st)
 // phase A on the tensor cores (hy_cpl_tc.cu); *status (device) is set to 1
 // if a bounded wait ran out
 size_t cpl_tc_smem(int64_t Nb);
-cudaError_t coupling_tc(const CplDenseArgs &a, int *status, int num_sms, cudaStream_t st);
+cudaError_t coupling_tc(const CplDenseArgs &a, int *status, long long spin_limit, int issue,
+                        int num_sms, cudaStream_t st);
 
 template <typename T>
 cudaError_t spmm(const int32_t *ptr, const int32_t *col, const T *val,
@@ -254,6 +275,8 @@ struct SparseGradArgs {
     int n;
     int64_t Nb;
     double *g;
+    int64_t K;               // pool size: listed indices outside [0, K) are refused
+    unsigned long long *bad; // (position << 32 | index) of the first refused entry, or nullptr
 };
 template <typename T>
 cudaError_t support(const T *psi, int64_t N, int64_t *list, int64_t cap,

@@ -243,7 +243,7 @@ k_coupling(CouplingArgs<T> a, int cpt)
     T *Cdiag = reinterpret_cast<T *>(smem_raw + words * 4);     // [16]
     T *TL = Cdiag + 16, *TH = TL + 256;                         // [256] each
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int64_t ar = blockIdx.x; ar < a.Na; ar += gridDim.x) {
+    for (int64_t ar = a.row0 + blockIdx.x; ar < a.row1; ar += gridDim.x) {
         T acc[kCouplingMaxCpt];
 #pragma unroll
         for (int j = 0; j < kCouplingMaxCpt; ++j) acc[j] = T(0);
@@ -305,7 +305,7 @@ k_coupling(CouplingArgs<T> a, int cpt)
                 }
             }
         }
-        T *dst = a.sigma + ar * Nb;
+        T *dst = a.sigma + (ar - a.row0) * Nb;
 #pragma unroll
         for (int j = 0; j < kCouplingMaxCpt; ++j) {
             const int64_t b = tid + int64_t(j) * nt;
@@ -317,7 +317,7 @@ k_coupling(CouplingArgs<T> a, int cpt)
 template <typename T>
 cudaError_t coupling(const CouplingArgs<T> &a, int num_sms, cudaStream_t st)
 {
-    if (a.Na == 0 || a.Nb == 0) return cudaSuccess;
+    if (a.row1 <= a.row0 || a.Nb == 0) return cudaSuccess;
     int threads = int(a.Nb < 1024 ? (a.Nb + 31) / 32 * 32 : 1024);
     const int cpt = int((a.Nb + threads - 1) / threads);
     if (cpt > kCouplingMaxCpt) return cudaErrorInvalidValue;
@@ -330,7 +330,7 @@ cudaError_t coupling(const CouplingArgs<T> &a, int num_sms, cudaStream_t st)
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = int64_t(num_sms) * per_sm;
-    if (grid > a.Na) grid = a.Na;
+    if (grid > a.row1 - a.row0) grid = a.row1 - a.row0;
     k_coupling<T><<<unsigned(grid), threads, smem, st>>>(a, cpt); hy::count_launch();
     return cudaGetLastError();
 }
@@ -373,7 +373,8 @@ k_cpl_gemm(CplDenseArgs a)
     int16_t *pos = act + 256;                                   // [nn] type -> row of G
     int *misc = reinterpret_cast<int *>(pos + 256);             // or, and, n_active, warp counts[9]
     const int tid = threadIdx.x, mg = tid >> 5, ng = tid & 31;
-    for (int64_t J = blockIdx.x; J < a.Na; J += gridDim.x) {
+    for (int64_t jj = blockIdx.x; jj < a.nJ; jj += gridDim.x) {
+        const int64_t J = a.jlist ? int64_t(a.jlist[jj]) : jj;
         __syncthreads();
         const float *src = a.psi + J * Nb;
         const uint32_t jm = a.astr[J];
@@ -518,7 +519,7 @@ k_cpl_gather(CplDenseArgs a)
 {
     const int64_t Nb = a.Nb;
     const int nexa = a.nexa, slots = nexa + 1;
-    for (int64_t ar = blockIdx.x; ar < a.Na; ar += gridDim.x) {
+    for (int64_t ar = a.row0 + blockIdx.x; ar < a.row1; ar += gridDim.x) {
         for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) {
             float s = a.T[(ar * slots + nexa) * a.Nbp + b];
             for (int e = 0; e < nexa; ++e) {
@@ -526,7 +527,7 @@ k_cpl_gather(CplDenseArgs a)
                 const int m = a.inv[ar * nexa + e];
                 s += a.T[(J * slots + m) * a.Nbp + b];
             }
-            a.sigma[ar * Nb + b] += s;
+            a.sigma[(ar - a.row0) * Nb + b] += s;
         }
     }
 }
@@ -552,8 +553,11 @@ cudaError_t coupling_dense(const CplDenseArgs &a, int num_sms, cudaStream_t st)
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = int64_t(num_sms) * per_sm;
-    if (grid > a.Na) grid = a.Na;
-    k_cpl_gemm<<<unsigned(grid), kGThreads, smem, st>>>(a); hy::count_launch();
+    if (grid > a.nJ) grid = a.nJ;
+    if (grid > 0) {
+        k_cpl_gemm<<<unsigned(grid), kGThreads, smem, st>>>(a);
+        hy::count_launch();
+    }
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return coupling_gather(a, num_sms, st);
@@ -561,9 +565,9 @@ cudaError_t coupling_dense(const CplDenseArgs &a, int num_sms, cudaStream_t st)
 
 cudaError_t coupling_gather(const CplDenseArgs &a, int num_sms, cudaStream_t st)
 {
-    if (a.Na == 0 || a.Nb == 0) return cudaSuccess;
+    if (a.row1 <= a.row0 || a.Nb == 0) return cudaSuccess;
     int64_t g2 = int64_t(num_sms) * 8;
-    if (g2 > a.Na) g2 = a.Na;
+    if (g2 > a.row1 - a.row0) g2 = a.row1 - a.row0;
     k_cpl_gather<<<unsigned(g2), 256, 0, st>>>(a); hy::count_launch();
     return cudaGetLastError();
 }

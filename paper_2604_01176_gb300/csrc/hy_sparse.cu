@@ -219,6 +219,11 @@ k_grad_sparse(SparseGradArgs<T> a)
     const int64_t m = list_len(a.d_m, a.m, a.cap);
     const int64_t i = blockIdx.x;
     const int k = a.ops ? a.ops[i] : int(i);
+    if (refuse_op(i, k, a.K, blockIdx.y == 0 ? a.bad : nullptr)) {
+        if (threadIdx.x == 0)
+            a.partials[i * gridDim.y + blockIdx.y] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
     const int32_t *dsc = a.desc + 11 * k;
     double tot = 0.0;
     for (int c = 0; c < dsc[0]; ++c) {

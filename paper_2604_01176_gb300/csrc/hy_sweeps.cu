@@ -154,6 +154,10 @@ k_grad_partial(GradArgs<T> a)
     const int64_t i = blockIdx.x;
     const int chunk = blockIdx.y;
     const int k = a.ops ? a.ops[i] : int(i);
+    if (refuse_op(i, k, a.K, chunk == 0 ? a.bad : nullptr)) {
+        if (threadIdx.x == 0) a.partials[i * a.CH + chunk] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
     const OpDev od = a.opd[k];
     double tot = 0.0;
     for (int c = 0; c < od.nc; ++c) {
