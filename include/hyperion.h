@@ -181,6 +181,10 @@ hy_status hy_ham_coupling_ms(const hy_ham *h, float *ms);
  * (default 2^26, seconds of waiting; >= 1). */
 hy_status hy_ham_set_wait_limit(hy_ham *h, int64_t polls);
 
+/* Bytes the build of h (and of pool p, when not NULL) copied from host to
+ * device memory: the kernel tables, string lists, pool patterns. */
+hy_status hy_ham_upload_bytes(const hy_ham *h, const hy_pool *p, int64_t *bytes);
+
 /* Copy the Pauli table (host outputs, caller-allocated).  Term t is
  * coeff[t] * P(x[t], z[t]) where P is the Hermitian Pauli string with X on
  * bits of x & ~z, Z on z & ~x and Y on x & z (bit j = qubit j).  Terms are
@@ -606,8 +610,12 @@ hy_status hy_adapt_set_ranker(hy_adapt *a, hy_ranker *r, int warm_iters,
  *   refine_every-th iteration (and in hy_adapt_refine) it is followed by
  *   at most refine_steps BFGS steps in double, and that iteration's
  *   recorded energy is a double-precision evaluation with the float
- *   energy's error beside it.  Other iterations record the float-bulk
- *   energy (reduced in double) and energy_bulk_err = -1. */
+ *   energy's error beside it; the next iteration then screens the pool on
+ *   that double-precision state (its parameters are the double optimum, so
+ *   the selection is the one plain FP64 makes; float gradients, ~1e-6
+ *   relative off, can reorder near-equal operators).  Other iterations
+ *   record the float-bulk energy (reduced in double) and
+ *   energy_bulk_err = -1. */
 typedef struct {
     hy_dtype bulk;        /* HY_F64 or HY_F32                                  */
     int max_iter;         /* capacity of the ansatz (iterations)               */
@@ -676,6 +684,14 @@ typedef struct {
                               sparse path ran it, -1 for the dense sweeps     */
     int64_t sigma_support; /* listed nonzeros of sigma = H psi there, -1 when
                               sigma's support was not listed                  */
+    int32_t screen;        /* how the operator was selected: 0 the whole pool
+                              screened exactly by the dense sweep, 1 the whole
+                              pool screened exactly over psi's support (sparse
+                              path), 2 the ranker's proposals screened exactly,
+                              3 the proposals and then the whole pool (the
+                              fallback when the proposals' ||g|| would stop
+                              the loop)                                        */
+    int32_t pad_;
 } hy_adapt_record;
 
 

@@ -156,6 +156,13 @@ class Hamiltonian:
         check(_abi.load().hy_ham_set_coupling(
             self._h, {"tensor": 0, "simt": 1, "withheld": 2}[impl]))
 
+    def upload_bytes(self, pool=None) -> int:
+        """Bytes this Hamiltonian's build (and the pool's) copied host -> device."""
+        v = ctypes.c_int64()
+        check(_abi.load().hy_ham_upload_bytes(self._h, pool.handle if pool else None,
+                                              ctypes.byref(v)))
+        return v.value
+
     def set_wait_limit(self, polls: int) -> None:
         """Polls of a tensor-core stage barrier before the wait gives up."""
         check(_abi.load().hy_ham_set_wait_limit(self._h, int(polls)))

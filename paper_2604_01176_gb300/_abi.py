@@ -58,7 +58,8 @@ class AdaptRecord(ctypes.Structure):
                 ("t_screen", ctypes.c_double), ("t_optimise", ctypes.c_double),
                 ("t_total", ctypes.c_double), ("t_judge", ctypes.c_double),
                 ("support", ctypes.c_int64),
-                ("sigma_support", ctypes.c_int64)]
+                ("sigma_support", ctypes.c_int64),
+                ("screen", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -85,6 +86,7 @@ SIGNATURES = {
     "hy_ham_profile": (I32, [P, I32]),
     "hy_ham_set_coupling": (I32, [P, I32]),
     "hy_ham_set_wait_limit": (I32, [P, I64]),
+    "hy_ham_upload_bytes": (I32, [P, P, PI64]),
     "hy_ham_coupling_ms": (I32, [P, P]),
     "hy_pauli_table_build": (I32, [P, P, D, I32, D, I64, P, P, P, P, PI64, PI64]),
     "hy_rank": (I32, [P, P, P, I64, P]),

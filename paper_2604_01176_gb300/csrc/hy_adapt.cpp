@@ -64,6 +64,8 @@ struct hy_adapt {
     // which (dtype, theta) the psi/sigma buffers currently hold
     int valid_dt = -1;
     std::vector<double> valid_theta;
+    // the last iteration was refined in double: screen its double state
+    bool screen_f64_next = false;
     int evals = 0, evals64 = 0;
     int iter = 0;
     int64_t h2d = 0, d2h = 0;     // bytes copied host <-> device so far
@@ -159,11 +161,13 @@ hy_status finish_energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt)
     return HY_OK;
 }
 
-// last support up to which one CTA prepares the sparse state (its 1,024
-// threads then take at most a few dozen entries each per rotation, even
-// after a new operator quadruples the support); also the largest support a
-// support program holds (its vectors live in shared memory)
-const int64_t kPrepareSmall = 12288;
+// last support up to which one CTA prepares the sparse state and the ansatz
+// is compiled into a support program (up to 12,288 elements its vectors live
+// in shared memory, beyond that in an L2-resident global scratch); the
+// general single-CTA forward gradient (no program) stays with supports up to
+// kForwardSmall, above which the reverse sweep serves
+const int64_t kPrepareSmall = 65536;
+const int64_t kForwardSmall = 12288;
 
 // The sparse evaluation: psi = U(theta)|HF> as a sparse vector (rotations
 // cost O(support)), renormalised over its support in double (float states),
@@ -364,7 +368,7 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
         std::copy(a->h_g, a->h_g + j, g.begin());
         return HY_OK;
     }
-    if (a->prep_small && a->sparse_m <= kPrepareSmall) {
+    if (a->prep_small && a->sparse_m <= kForwardSmall) {
         // small support: the whole gradient in forward mode in one launch
         if (!a->ss_clean[d][1]) HY_TRY(hy::sstate_reset(F, true, false, st));
         if (!a->ss_clean[d][2]) HY_TRY(hy::sstate_reset(L, true, false, st));
@@ -763,26 +767,32 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     const double t0 = now_s();
     const int ev0 = a->evals, ev640 = a->evals64;
     const hy_dtype bulk = a->cfg.bulk;
-    // 1. state and sigma at the current parameters in the bulk precision
-    if (a->valid_dt != bulk || a->valid_theta != a->theta) {
+    // 1. state and sigma at the current parameters.  The screen runs in the
+    // bulk precision, except after an iteration refined in double: its
+    // parameters are then the double-precision optimum, and screening that
+    // state in double makes the selection the one plain FP64 would make
+    // (float gradients differ from it by ~1e-6 relative, enough to reorder
+    // near-equal operators)
+    const hy_dtype sdt = a->screen_f64_next ? HY_F64 : bulk;
+    if (a->valid_dt != sdt || a->valid_theta != a->theta) {
         double e;
-        HY_TRY(energy(a, a->theta, bulk, st, &e));
+        HY_TRY(energy(a, a->theta, sdt, st, &e));
     }
-    void *psi = a->buf[di(bulk)][0], *sigma = a->buf[di(bulk)][1];
+    void *psi = a->buf[di(sdt)][0], *sigma = a->buf[di(sdt)][1];
     rec->support = a->sparse_m;
-    const bool sig_listed = a->sparse_m >= 0 && a->sig_listed[di(bulk)];
-    rec->sigma_support = sig_listed ? a->sig_count[di(bulk)] : -1;
+    const bool sig_listed = a->sparse_m >= 0 && a->sig_listed[di(sdt)];
+    rec->sigma_support = sig_listed ? a->sig_count[di(sdt)] : -1;
     // the sparse path lists psi's support, and sigma's while it fits its list:
     // the ranker's features then take psi's touched weights from its list,
     // and sigma's while its list costs less than the pass over the dense
     // array (one atomic add per electron pair of a listed determinant,
     // counted as kListAddCost streamed amplitudes)
-    const hy::SparseState *psi_list = a->sparse_m >= 0 ? a->ss[di(bulk)][0] : nullptr;
+    const hy::SparseState *psi_list = a->sparse_m >= 0 ? a->ss[di(sdt)][0] : nullptr;
     const hy::SparseState *sigma_list =
-        sig_listed && double(a->sig_count[di(bulk)]) *
+        sig_listed && double(a->sig_count[di(sdt)]) *
                               double(hy::ham_list_weight_adds(a->h)) * kListAddCost <=
                           double(a->N)
-            ? a->ss[di(bulk)][3]
+            ? a->ss[di(sdt)][3]
             : nullptr;
     // 2. screen: full, or the ranker's top-M proposals screened exactly
     const bool ranked = a->cfg.screen_top_m > 0;
@@ -806,10 +816,10 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     double gmax = 0.0, gn2 = 0.0;
     auto full_screen = [&]() -> hy_status {
         if (a->sparse_m >= 0)
-            HY_TRY(hy::sstate_gradients(a->ss[di(bulk)][0], sigma, a->p, nullptr, a->K,
+            HY_TRY(hy::sstate_gradients(a->ss[di(sdt)][0], sigma, a->p, nullptr, a->K,
                                         a->sparse_m, a->d_g, st));
         else
-            HY_TRY(hy::pool_gradients_unchecked(a->h, a->p, psi, sigma, nullptr, a->K, a->d_g, bulk, st));
+            HY_TRY(hy::pool_gradients_unchecked(a->h, a->p, psi, sigma, nullptr, a->K, a->d_g, sdt, st));
         HY_TRY(xfer(a, a->h_gs, a->d_g, a->K * sizeof(double), cudaMemcpyDeviceToHost, st,
                     "screen readback"));
         HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
@@ -831,11 +841,12 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     for (int64_t k = 0; k < a->K; ++k) all[k] = k;
     double t_judge = 0.0;
     if (ranked) HY_TRY(upload_extra(a, st));
+    rec->screen = use_ranker ? 2 : (a->sparse_m >= 0 ? 1 : 0);
     if (!use_ranker) {
         HY_TRY(full_screen());
         pick(all, g);
         if (ranked) {
-            HY_TRY(hy::ranker_features_impl(a->h, a->p, psi, psi_list, sigma, sigma_list, bulk,
+            HY_TRY(hy::ranker_features_impl(a->h, a->p, psi, psi_list, sigma, sigma_list, sdt,
                                             a->d_extra, a->d_feat, st));
             HY_TRY(hy_ranker_add_samples(a->ranker, a->d_feat, a->d_g, a->K, st));
             // the first fit after the warm-up, warm-started refits on the
@@ -855,7 +866,7 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
             a->fit_pending = 0;
             a->fitted_once = true;
         }
-        HY_TRY(hy::ranker_features_impl(a->h, a->p, psi, psi_list, sigma, sigma_list, bulk,
+        HY_TRY(hy::ranker_features_impl(a->h, a->p, psi, psi_list, sigma, sigma_list, sdt,
                                         a->d_extra, a->d_feat, st));
         HY_TRY(hy_ranker_predict(a->ranker, a->d_feat, a->K, a->d_score, st));
         // proposals: the M / 4 operators with the largest Cauchy-Schwarz
@@ -902,10 +913,10 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
                     "proposals upload"));
         const int64_t Mp = int64_t(prop.size());
         if (a->sparse_m >= 0)
-            HY_TRY(hy::sstate_gradients(a->ss[di(bulk)][0], sigma, a->p, a->d_prop, Mp,
+            HY_TRY(hy::sstate_gradients(a->ss[di(sdt)][0], sigma, a->p, a->d_prop, Mp,
                                         a->sparse_m, a->d_gp, st));
         else
-            HY_TRY(hy::pool_gradients_unchecked(a->h, a->p, psi, sigma, a->d_prop, Mp, a->d_gp, bulk, st));
+            HY_TRY(hy::pool_gradients_unchecked(a->h, a->p, psi, sigma, a->d_prop, Mp, a->d_gp, sdt, st));
         std::vector<double> gp(Mp);
         HY_TRY(xfer(a, gp.data(), a->d_gp, Mp * 8, cudaMemcpyDeviceToHost, st,
                     "proposals readback"));
@@ -915,6 +926,7 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         note_screen(a, cand, gp);
         if (std::sqrt(gn2) < a->cfg.eps_grad) {
             // fallback: never stop on the proposals alone
+            rec->screen = 3;
             HY_TRY(full_screen());
             pick(all, g);
             note_screen(a, all, g);
@@ -973,12 +985,14 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         rec->energy_bulk = e32;
         rec->energy = e32;
         rec->energy_bulk_err = -1.0;
+        a->screen_f64_next = false;
         if (a->cfg.refine_every > 0 && (a->iter + 1) % a->cfg.refine_every == 0) {
             HY_TRY(energy(a, a->theta, HY_F64, st, &e64));
             rec->energy_bulk_err = std::fabs(e32 - e64);
             if (a->cfg.refine_steps > 0)
                 HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.refine_steps, st, &e64, kStall64));
             rec->energy = e64;
+            a->screen_f64_next = true;
         }
     }
     rec->n_evals = a->evals - ev0;
@@ -1059,6 +1073,7 @@ hy_status hy_adapt_set_ansatz(hy_adapt *a, const int64_t *ops, const double *the
     for (int64_t l = 0; l < len; ++l) a->hinv[l * len + l] = 1.0;
     a->hinv_fresh = true;
     a->valid_dt = -1;
+    a->screen_f64_next = false;
     a->iter = int(len);
     cudaStream_t st = nullptr;
     return upload_ops(a, st);

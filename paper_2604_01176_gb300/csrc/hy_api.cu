@@ -40,6 +40,7 @@ hy_status cuda_fail(cudaError_t e, const char *what)
 // Device allocations owned by a handle, released together.
 struct DevArena {
     std::vector<void *> ptrs;
+    int64_t uploaded = 0;        // bytes copied host -> device
     template <typename T>
     cudaError_t upload(T **dst, const T *src, size_t count)
     {
@@ -50,6 +51,7 @@ struct DevArena {
         if (e != cudaSuccess) return e;
         ptrs.push_back(p);
         e = cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice);
+        uploaded += int64_t(count * sizeof(T));
         *dst = static_cast<T *>(p);
         return e;
     }
@@ -744,6 +746,14 @@ hy_status hy_ham_info(const hy_ham *h, int64_t *n_det, int64_t *n_alpha_str,
     return HY_OK;
 }
 
+hy_status hy_ham_upload_bytes(const hy_ham *h, const hy_pool *p, int64_t *bytes)
+{
+    if (!h || !bytes) return fail(HY_ERR_ARG, "bad arguments");
+    if (p && p->h != h) return fail(HY_ERR_ARG, "pool belongs to another Hamiltonian");
+    *bytes = h->arena.uploaded + (p ? p->arena.uploaded : 0);
+    return HY_OK;
+}
+
 hy_status hy_ham_pauli_table(const hy_ham *h, uint64_t *x, uint64_t *z,
                              double *coeff, int64_t *group_offsets)
 {
@@ -837,11 +847,13 @@ hy_status hy_apply_h_rows(const hy_ham *hc, const void *psi, void *sigma_rows, h
                           int64_t row_begin, int64_t row_end, void *stream)
 {
     hy_ham *h = const_cast<hy_ham *>(hc);
-    if (!h || !psi || !sigma_rows || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
+    if (!h || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
     if (row_begin < 0 || row_end < row_begin || row_end > h->Na)
         return fail(HY_ERR_ARG, "row range [" + std::to_string(row_begin) + ", " +
                                     std::to_string(row_end) + ") outside [0, " +
                                     std::to_string(h->Na) + ")");
+    if (row_end == row_begin) return HY_OK;       // an empty block: nothing written
+    if (!psi || !sigma_rows) return fail(HY_ERR_ARG, "bad arguments");
     const size_t es = dt == HY_F64 ? 8 : 4;
     const char *pb = static_cast<const char *>(psi), *sb = static_cast<const char *>(sigma_rows);
     const size_t psi_bytes = size_t(h->N) * es;
@@ -1981,6 +1993,13 @@ struct SupportProgram {
     int64_t *key = nullptr, *step_len = nullptr;
     int32_t *tab = nullptr;
     int *flag = nullptr;
+    // supports beyond shared memory (allocated on first use): keys in
+    // listing order, tables, the index map over Omega_CIk and the vectors'
+    // global scratch (prepare: one vector; gradient: two per angle)
+    int64_t *key_big = nullptr;
+    int32_t *tab_big = nullptr, *idx_map = nullptr;
+    void *prep_scratch = nullptr, *grad_scratch = nullptr;
+    size_t grad_bytes = 0;
 };
 
 hy_status prog_create(const hy_ham *h, int max_steps, SupportProgram **out)
@@ -2012,8 +2031,15 @@ void prog_destroy(SupportProgram *g)
     cudaFree(g->step_len);
     cudaFree(g->tab);
     cudaFree(g->flag);
+    cudaFree(g->key_big);
+    cudaFree(g->tab_big);
+    cudaFree(g->idx_map);
+    cudaFree(g->prep_scratch);
+    cudaFree(g->grad_scratch);
     delete g;
 }
+
+int64_t prog_capacity() { return hy::k::kProgBig; }
 
 int64_t *prog_step_len(SupportProgram *g) { return g->step_len; }
 const int *prog_flag(const SupportProgram *g) { return g->flag; }
@@ -2043,13 +2069,29 @@ hy_status prog_compile(SupportProgram *g, const SparseState *s, int64_t m, const
                        const int32_t *ops, int64_t L, int64_t steps, void *stream)
 {
     if (!g || !s || !p || p->h != g->h || s->h != g->h || !ops || L < 1 || m < 1 ||
-        m > hy::k::kProgMax || m > s->cap || steps < 1 || steps > g->max_steps)
+        m > hy::k::kProgBig || m > s->cap || steps < 1 || steps > g->max_steps)
         return fail(HY_ERR_ARG, "bad arguments");
     cudaStream_t st = as_stream(stream);
     hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
-    HY_CUDA(hy::k::prog_compile(s->list, m, g->step_len, int(steps), sv_op_args(g->h, p), ops,
-                                int(L), g->key, g->tab, g->flag, st),
-            "support program");
+    if (m <= hy::k::kProgMax) {
+        HY_CUDA(hy::k::prog_compile(s->list, m, g->step_len, int(steps), sv_op_args(g->h, p), ops,
+                                    int(L), g->key, g->tab, g->flag, st),
+                "support program");
+    } else {
+        const size_t kb = size_t(hy::k::kProgBig);
+        cudaError_t e = cudaSuccess;
+        if (!g->key_big) e = cudaMalloc(&g->key_big, kb * sizeof(int64_t));
+        if (e == cudaSuccess && !g->tab_big)
+            e = cudaMalloc(&g->tab_big, size_t(g->max_steps) * kb * sizeof(int32_t));
+        if (e == cudaSuccess && !g->idx_map)
+            e = cudaMalloc(&g->idx_map, size_t(g->h->N) * sizeof(int32_t));
+        if (e == cudaSuccess && !g->prep_scratch) e = cudaMalloc(&g->prep_scratch, kb * sizeof(double));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(support program)");
+        HY_CUDA(hy::k::prog_compile_big(s->list, m, g->step_len, int(steps), sv_op_args(g->h, p),
+                                        ops, int(L), s->bits, g->key_big, g->tab_big, g->idx_map,
+                                        g->flag, st),
+                "support program");
+    }
     g->m = m;
     g->steps = steps;
     return HY_OK;
@@ -2063,6 +2105,21 @@ hy_status prog_prepare(const SupportProgram *g, SparseState *s, const hy_pool *p
         return fail(HY_ERR_ARG, "bad arguments");
     cudaStream_t st = as_stream(stream);
     hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
+    if (g->m > hy::k::kProgMax) {
+        if (s->dt == HY_F64)
+            HY_CUDA(hy::k::prog_prepare_big<double>(g->key_big, g->tab_big, g->m, p->d_desc, ops,
+                                                    cs, int(L), renorm, norm2,
+                                                    static_cast<double *>(s->v),
+                                                    static_cast<double *>(g->prep_scratch), st),
+                    "support program preparation");
+        else
+            HY_CUDA(hy::k::prog_prepare_big<float>(g->key_big, g->tab_big, g->m, p->d_desc, ops,
+                                                   cs, int(L), renorm, norm2,
+                                                   static_cast<float *>(s->v),
+                                                   static_cast<float *>(g->prep_scratch), st),
+                    "support program preparation");
+        return HY_OK;
+    }
     if (s->dt == HY_F64)
         HY_CUDA(hy::k::prog_prepare<double>(g->key, g->tab, g->m, p->d_desc, ops, cs, int(L),
                                             renorm, norm2, static_cast<double *>(s->v), st),
@@ -2083,6 +2140,30 @@ hy_status prog_grad(const SupportProgram *g, const hy_pool *p, const int32_t *op
         return fail(HY_ERR_ARG, "bad arguments");
     cudaStream_t st = as_stream(stream);
     hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
+    if (g->m > hy::k::kProgMax) {
+        SupportProgram *gm = const_cast<SupportProgram *>(g);
+        const size_t need = size_t(L) * 2 * size_t(g->m) * (dt == HY_F64 ? 8 : 4);
+        if (need > gm->grad_bytes) {
+            cudaFree(gm->grad_scratch);
+            gm->grad_scratch = nullptr;
+            gm->grad_bytes = 0;
+            const cudaError_t e = cudaMalloc(&gm->grad_scratch, need);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(support program gradient)");
+            gm->grad_bytes = need;
+        }
+        if (dt == HY_F64)
+            HY_CUDA(hy::k::prog_grad_big<double>(g->key_big, g->tab_big, g->m, p->d_desc, ops, cs,
+                                                 int(L), static_cast<const double *>(sigma), norm2,
+                                                 g_out, static_cast<double *>(gm->grad_scratch),
+                                                 st),
+                    "support program gradient");
+        else
+            HY_CUDA(hy::k::prog_grad_big<float>(g->key_big, g->tab_big, g->m, p->d_desc, ops, cs,
+                                                int(L), static_cast<const float *>(sigma), norm2,
+                                                g_out, static_cast<float *>(gm->grad_scratch), st),
+                    "support program gradient");
+        return HY_OK;
+    }
     if (dt == HY_F64)
         HY_CUDA(hy::k::prog_grad<double>(g->key, g->tab, g->m, p->d_desc, ops, cs, int(L),
                                          static_cast<const double *>(sigma), norm2, g_out, st),

@@ -219,8 +219,10 @@ __device__ __forceinline__ void cp_async_wait()
 }
 
 // Each thread owns MAXG groups of four rows b' (group g = tid + i*blockDim).
+// The float one-group form fits 32 registers, so two CTAs share an SM and
+// twice the loads are in flight.
 template <typename T, int MAXG>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(1024, (MAXG == 1 && sizeof(T) == 4) ? 2 : 1)
 k_hmat_spmv(SpmvArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -626,9 +628,10 @@ hy_status hy_hmat_info(const hy_hmat *m, int64_t *row_begin, int64_t *row_end, i
 
 hy_status hy_hmat_apply(const hy_hmat *m, const void *psi, void *sigma_rows, void *stream)
 {
-    if (!m || !psi || !sigma_rows) return hy::hfail(HY_ERR_ARG, "bad arguments");
+    if (!m) return hy::hfail(HY_ERR_ARG, "handle is NULL");
+    if (m->nr == 0) return HY_OK;                 // nothing stored, nothing written
+    if (!psi || !sigma_rows) return hy::hfail(HY_ERR_ARG, "bad arguments");
     if (psi == sigma_rows) return hy::hfail(HY_ERR_ARG, "psi and sigma_rows must not alias");
-    if (m->nr == 0) return HY_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t es = m->dt == HY_F64 ? 8 : 4;
     const double bytes = double(m->bytes) + double(m->nr * m->Nb) * double(es) * 2.0;

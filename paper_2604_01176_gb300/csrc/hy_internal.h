@@ -169,8 +169,10 @@ int64_t *prog_step_len(SupportProgram *g);           // device, max_steps entrie
 const int *prog_flag(const SupportProgram *g);        // device, set by prog_compile
 // constituent rotations of ops[0..L) (host array), i.e. the program's steps
 int64_t prog_steps(const hy_pool *p, const int32_t *ops_host, int64_t L);
-// compile from s (whose support, m <= 4096 elements, was just listed by a
-// structural sstate_prepare of ops[0..L) (device) with step_len)
+// the largest support a program holds
+int64_t prog_capacity();
+// compile from s (whose support, m <= prog_capacity() elements, was just
+// listed by a structural sstate_prepare of ops[0..L) (device) with step_len)
 hy_status prog_compile(SupportProgram *g, const SparseState *s, int64_t m, const hy_pool *p,
                        const int32_t *ops, int64_t L, int64_t steps, void *stream);
 // s.v on the program's support = U_L .. U_1|HF> (renormalised as

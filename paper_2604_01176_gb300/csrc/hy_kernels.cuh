@@ -357,6 +357,24 @@ template <typename T>
 cudaError_t prog_grad(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
                       const int32_t *ops, const double *cs, int L, const T *sigma,
                       const double *norm2, double *g, cudaStream_t st);
+// Support programs beyond shared memory, kProgMax < m <= kProgBig: the
+// support in listing order (key unsorted), local indices through idx_map
+// (N int32 over Omega_CIk, read where `bits`, the listing's membership
+// bitmap, has the determinant), vectors in global scratch (prepare: m
+// elements; gradient: 2 m per angle)
+constexpr int64_t kProgBig = 65536;
+cudaError_t prog_compile_big(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
+                             const SvOpArgs &o, const int32_t *ops, int L, const uint32_t *bits,
+                             int64_t *key, int32_t *tab, int32_t *idx_map, int *flag,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t prog_prepare_big(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
+                             const int32_t *ops, const double *cs, int L, bool renorm,
+                             double *norm2, T *v, T *scratch, cudaStream_t st);
+template <typename T>
+cudaError_t prog_grad_big(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
+                          const int32_t *ops, const double *cs, int L, const T *sigma,
+                          const double *norm2, double *g, T *scratch, cudaStream_t st);
 // one CTA: g[l] = dE/dtheta_l of psi = U_L .. U_1|HF> in forward mode, f and
 // w scratch sparse vectors (clean), sigma = H psi dense; norm2 (device, or
 // null): psi was divided by sqrt(*norm2), so the gradient is too

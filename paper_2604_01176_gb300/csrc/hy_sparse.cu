@@ -906,6 +906,161 @@ k_prog_grad(const int64_t *__restrict__ key, const int32_t *__restrict__ tab, in
     if (threadIdx.x == 0) g[lg] = (norm2 ? 2.0 / sqrt(*norm2) : 2.0) * dot;
 }
 
+// ---------------------------------------------------------------------------
+// Support programs beyond shared memory (kProgMax < m <= kProgBig).  The
+// support keeps the order in which the structural preparation listed it
+// (key[t] = (determinant << 8) | birth, as above, unsorted), an index map
+// over Omega_CIk gives each listed determinant its local index (read only
+// where the listing's membership bitmap has the determinant), and the
+// vectors live in a global scratch the size of the support, which stays in
+// L2.  Same tables, same arithmetic, same order of operations per element.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_prog_keys_big(const int64_t *__restrict__ list, int64_t m, const int64_t *__restrict__ step_len,
+                int steps, int64_t *__restrict__ key, int32_t *__restrict__ idx_map)
+{
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < m;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        int lo = 0, hi = steps;                      // first step whose length exceeds t
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (t < step_len[mid]) hi = mid;
+            else lo = mid + 1;
+        }
+        const int64_t d = list[t];
+        key[t] = (d << 8) | int64_t(t == 0 ? 0 : lo + 1);
+        idx_map[d] = int32_t(t);
+    }
+}
+
+// as k_prog_tables, with the partner found through the bitmap and index map
+__global__ void __launch_bounds__(256)
+k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
+                  const int32_t *__restrict__ ops, int L, const uint32_t *__restrict__ bits,
+                  const int32_t *__restrict__ idx_map, int32_t *__restrict__ tab,
+                  int *__restrict__ flag)
+{
+    __shared__ uint32_t C[33][33];
+    for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
+    __syncthreads();
+    const int s = blockIdx.y;
+    int l = 0, ci = 0, last = -1, acc = 0;
+    for (; l < L; ++l) {
+        const int nc = o.desc[11 * ops[l]];
+        if (s < acc + nc) {
+            ci = s - acc;
+            last = acc + nc - 1;
+            break;
+        }
+        acc += nc;
+    }
+    if (l >= L) return;
+    int fw[4], bw[4], len;
+    op_strings(o.desc + 11 * ops[l] + 1 + 5 * ci, fw, bw, len);
+    const int n = o.n;
+    const uint64_t lowm = (1ull << n) - 1;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
+        const int64_t kt = key[t], d = kt >> 8;
+        const int birth = int(kt & 255) - 1;
+        const uint64_t mask = uint64_t(o.astr[d / o.Nb]) | (uint64_t(o.bstr[d % o.Nb]) << n);
+        uint64_t u = mask;
+        int sg = 1;
+        int32_t e = 0;
+        bool escape = false;
+        if (apply_string(fw, len, u, sg)) {
+            const int64_t img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
+                                rank_bits(uint32_t(u >> n), C);
+            if (member(bits, img)) {
+                const int p = idx_map[img];
+                e = sg > 0 ? p + 1 : -(p + 1);
+            } else {
+                escape = true;
+            }
+        } else {
+            u = mask;
+            sg = 1;
+            if (apply_string(bw, len, u, sg)) {
+                const int64_t dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
+                                    rank_bits(uint32_t(u >> n), C);
+                escape = !member(bits, dom);
+            }
+        }
+        tab[int64_t(s) * m + t] = e;
+        if (escape && birth > s && birth <= last) *flag = 1;
+    }
+}
+
+// one CTA: as k_prog_prepare with the vector in global scratch x[0..m)
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_prog_prepare_big(const int64_t *__restrict__ key, const int32_t *__restrict__ tab, int m,
+                   const int32_t *__restrict__ desc, const int32_t *__restrict__ ops,
+                   const double *__restrict__ cs, int L, int renorm, double *__restrict__ norm2,
+                   T *__restrict__ v, T *__restrict__ x)
+{
+    __shared__ double red[32];
+    __shared__ double fac;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) x[t] = t == 0 ? T(1) : T(0);   // |HF>
+    __syncthreads();
+    int s = 0;
+    for (int l = 0; l < L; ++l) {
+        const int nc = desc[11 * ops[l]];
+        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
+        for (int ci = 0; ci < nc; ++ci, ++s) prog_rotate(x, tab + int64_t(s) * m, m, c, sn);
+    }
+    if (renorm) {
+        double acc = 0.0;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) acc = fma(double(x[t]), double(x[t]), acc);
+        const double sum = prog_block_sum(acc, red);
+        if (threadIdx.x == 0) {
+            if (norm2) *norm2 = sum;
+            fac = 1.0 / sqrt(sum);
+        }
+        __syncthreads();
+        const T f = T(fac);
+        for (int t = threadIdx.x; t < m; t += blockDim.x) v[key[t] >> 8] = x[t] * f;
+    } else {
+        for (int t = threadIdx.x; t < m; t += blockDim.x) v[key[t] >> 8] = x[t];
+    }
+}
+
+// CTA l: as k_prog_grad with f, w in global scratch (2 m per angle)
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_prog_grad_big(const int64_t *__restrict__ key, const int32_t *__restrict__ tab, int m,
+                const int32_t *__restrict__ desc, const int32_t *__restrict__ ops,
+                const double *__restrict__ cs, int L, const T *__restrict__ sigma,
+                const double *__restrict__ norm2, double *__restrict__ g, T *__restrict__ scratch)
+{
+    __shared__ double red[32];
+    const int lg = blockIdx.x;
+    T *f = scratch + size_t(lg) * 2 * size_t(m), *w = f + m;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        f[t] = t == 0 ? T(1) : T(0);
+        w[t] = T(0);
+    }
+    __syncthreads();
+    int s = 0;
+    for (int l = 0; l <= lg; ++l) {                  // phi_lg = U_lg .. U_1 |HF>
+        const int nc = desc[11 * ops[l]];
+        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
+        for (int ci = 0; ci < nc; ++ci, ++s) prog_rotate(f, tab + int64_t(s) * m, m, c, sn);
+    }
+    const int ncg = desc[11 * ops[lg]];
+    for (int ci = 0; ci < ncg; ++ci)                 // constituents add in order
+        prog_generator(f, w, tab + int64_t(s - ncg + ci) * m, m);
+    for (int l = lg + 1; l < L; ++l) {
+        const int nc = desc[11 * ops[l]];
+        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
+        for (int ci = 0; ci < nc; ++ci, ++s) prog_rotate(w, tab + int64_t(s) * m, m, c, sn);
+    }
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < m; t += blockDim.x)
+        acc = fma(double(w[t]), double(sigma[key[t] >> 8]), acc);
+    const double dot = prog_block_sum(acc, red);
+    if (threadIdx.x == 0) g[lg] = (norm2 ? 2.0 / sqrt(*norm2) : 2.0) * dot;
+}
+
 namespace {
 // blocks for a list of about n entries (grid-stride loops cover any count)
 unsigned sv_grid(int64_t n, int num_sms)
@@ -1104,6 +1259,62 @@ template cudaError_t support<float>(const float *, int64_t, int64_t *, int64_t,
                                     unsigned long long *, int, cudaStream_t);
 template cudaError_t hpsi_scatter<double>(const SparseArgs<double> &, int, cudaStream_t);
 template cudaError_t hpsi_scatter<float>(const SparseArgs<float> &, int, cudaStream_t);
+cudaError_t prog_compile_big(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
+                             const SvOpArgs &o, const int32_t *ops, int L, const uint32_t *bits,
+                             int64_t *key, int32_t *tab, int32_t *idx_map, int *flag,
+                             cudaStream_t st)
+{
+    if (m <= kProgMax || m > kProgBig || steps < 1 || steps > 254) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_prog_keys_big<<<unsigned((m + 255) / 256), 256, 0, st>>>(list, m, step_len, steps, key,
+                                                                idx_map);
+    hy::count_launch();
+    k_prog_tables_big<<<dim3(unsigned((m + 255) / 256), unsigned(steps)), 256, 0, st>>>(
+        key, int(m), o, ops, L, bits, idx_map, tab, flag);
+    hy::count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t prog_prepare_big(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
+                             const int32_t *ops, const double *cs, int L, bool renorm,
+                             double *norm2, T *v, T *scratch, cudaStream_t st)
+{
+    if (m <= kProgMax || m > kProgBig) return cudaErrorInvalidValue;
+    k_prog_prepare_big<T><<<1, 1024, 0, st>>>(key, tab, int(m), desc, ops, cs, L, renorm ? 1 : 0,
+                                              norm2, v, scratch);
+    hy::count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t prog_grad_big(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
+                          const int32_t *ops, const double *cs, int L, const T *sigma,
+                          const double *norm2, double *g, T *scratch, cudaStream_t st)
+{
+    if (m <= kProgMax || m > kProgBig || L < 1) return cudaErrorInvalidValue;
+    k_prog_grad_big<T><<<unsigned(L), 1024, 0, st>>>(key, tab, int(m), desc, ops, cs, L, sigma,
+                                                     norm2, g, scratch);
+    hy::count_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t prog_prepare_big<double>(const int64_t *, const int32_t *, int64_t,
+                                              const int32_t *, const int32_t *, const double *,
+                                              int, bool, double *, double *, double *,
+                                              cudaStream_t);
+template cudaError_t prog_prepare_big<float>(const int64_t *, const int32_t *, int64_t,
+                                             const int32_t *, const int32_t *, const double *, int,
+                                             bool, double *, float *, float *, cudaStream_t);
+template cudaError_t prog_grad_big<double>(const int64_t *, const int32_t *, int64_t,
+                                           const int32_t *, const int32_t *, const double *, int,
+                                           const double *, const double *, double *, double *,
+                                           cudaStream_t);
+template cudaError_t prog_grad_big<float>(const int64_t *, const int32_t *, int64_t,
+                                          const int32_t *, const int32_t *, const double *, int,
+                                          const float *, const double *, double *, float *,
+                                          cudaStream_t);
 template cudaError_t grad_sparse<double>(const SparseGradArgs<double> &, int, cudaStream_t);
 template cudaError_t grad_sparse<float>(const SparseGradArgs<float> &, int, cudaStream_t);
 #define HY_SV_INST(T)                                                                       \

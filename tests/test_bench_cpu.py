@@ -57,19 +57,31 @@ def test_roofline_alu_class_uses_flops(bench):
     assert math.isclose(r["frac"], round(tf / 80.5, 4))
 
 
-def test_roofline_scatter_reports_l2_atomics(bench):
+def test_traffic_record_follows_the_kernel_sources(bench, tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu record of the class and
+    turns None once the class's kernel sources differ from the hashed ones."""
+    import json
+    f = tmp_path / "traffic.json"
+    good = bench.source_hash(bench.CLASS_SOURCES["hmat"])
+    f.write_text(json.dumps({
+        "hmat": {"dram_bytes_per_launch": 1.5e9, "workload": "w", "source_sha": good},
+        "features": {"dram_bytes_per_launch": 2.0e6, "workload": "w", "source_sha": "stale"}}))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.traffic_for("hmat") == (1.5e9, "w")
+    assert bench.traffic_for("features") == (None, "w")
+    assert bench.traffic_for("reduce") == (None, None)
     prof = empty_prof(bench)
-    adds = 26 * 1.0e7
-    prof["hpsi_sparse"] = prof_entry(26, 5.0, bytes_=6 * 662.5e6, flops=adds)
-    r = bench.step_roofline(prof, {"hbm_gbs": 6712.6}, "measured", 80.5)
-    la = r["l2_atomics"]
-    rate = adds / 5.0e-3
-    assert math.isclose(la["achieved_adds_per_s"], float(f"{rate:.4g}"))
-    assert math.isclose(la["frac_of_l2_red_peak"], round(rate / bench.L2_RED_PEAK, 4))
-    assert la["adds_per_launch_est"] == round(adds / 26)
-    # a class without the adds estimate carries no such entry
-    prof["hpsi_sparse"] = prof_entry(26, 5.0, bytes_=6 * 662.5e6)
-    assert "l2_atomics" not in bench.step_roofline(prof, {"hbm_gbs": 6712.6}, "measured", 80.5)
+    prof["features"] = prof_entry(4, 2.0, bytes_=4 * 1.0e9)
+    assert bench.step_roofline(prof, {"hbm_gbs": 6712.6}, "measured", 80.5)["traffic"] is None
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.json"))
+    assert bench.traffic_for("hmat") == (None, None)
+
+
+def test_screens_used_counts_each_iteration(bench):
+    jobs = [([{"screen": 1}, {"screen": 1}, {"screen": 2}], -1.0, 0.1),
+            ([{"screen": 3}, {"screen": 0}], -1.0, 0.1)]
+    assert bench.screens_used(jobs) == {"exact_sparse": 2, "ranker": 1, "ranker_then_full": 1,
+                                        "exact_dense": 1}
 
 
 def test_roofline_without_known_work(bench):
@@ -115,7 +127,7 @@ def test_clock_sampler_without_nvidia_smi(bench):
 
 
 def test_job_throughput_counts_all_ranks(bench):
-    # 4 steps on each of 2 ranks in 10 ms (max over ranks): 800 steps/s for the job
+    # 4 iterations on each of 2 ranks in 10 ms (max over ranks): 800 iterations/s
     assert math.isclose(bench.job_throughput(2, 4, 10.0), 800.0)
 
 

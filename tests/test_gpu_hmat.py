@@ -154,7 +154,7 @@ def test_explicit_h_28q_row_block():
     g = got[torch.from_numpy(rows - b * NB).cuda()].double().cpu().numpy()
     assert np.abs(g - s_ref).max() <= 2e-5 * scale
     cols, vals = m.row(int(rows[0]))
-    assert len(cols) == row_length(n, na, nb) == 3381
+    assert len(cols) == row_length(n, na, nb) == 3382
 
 
 def test_explicit_h_size_query_and_bad_ranges():

@@ -283,3 +283,59 @@ def test_touched_weights_from_support(cfg, dt):
     sparse = hy.touched_weights_sparse(ham, psi, lst[:m])
     assert torch.max(torch.abs(sparse - dense)).item() <= 2e-6 * dense[0, 0].item()
     assert abs(dense[0, 0].item() - float((psi.double() ** 2).sum().item())) < 1e-5
+
+
+def _ansatz_with_support(ref, lo, hi, seed0):
+    """Ten singles and three other operators whose prepared support has
+    between lo and hi determinants (searched over seeds, the support
+    counted by the oracle; singles spread the state fastest)."""
+    import oracle.adapt as oadapt
+    opd = ref.pool()
+    singles = [k for k, op in enumerate(opd) if op[1] == 1]
+    for seed in range(seed0, seed0 + 200):
+        rng = np.random.default_rng(seed)
+        ops = [int(k) for k in rng.choice(singles, 10)] + \
+            [int(k) for k in rng.integers(0, len(opd), 3)]
+        th = rng.uniform(0.1, 0.7, len(ops)) * rng.choice([-1.0, 1.0], len(ops))
+        m = int(np.count_nonzero(oadapt.prepare(ref, opd, ops, th)))
+        if lo < m <= hi:
+            return ops, th, m
+    raise AssertionError("no ansatz with the requested support size")
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32], ids=["f64", "f32"])
+def test_support_program_beyond_shared_memory(dt):
+    """20 qubits, an ansatz whose support holds 12,289..63,504 determinants:
+    the support program then keeps its vectors in global memory (listing
+    order, index map).  Energy, forward gradient and state against the
+    oracle at several angles (double 1e-10 / 1e-9 / 1e-12; float 2e-6 /
+    1e-4 / 1e-5 relative), and the same evaluations on the dense sweeps."""
+    import oracle.adapt as oadapt
+    import paper_2604_01176_gb300 as hy
+    ref, ham, pool = system(10, 5, 5, 1002)
+    opd = ref.pool()
+    ops, th, m = _ansatz_with_support(ref, 12288, ham.n_det, 100)
+    prec = "f64" if dt == torch.float64 else "mixed"
+    ad = hy.Adapt(ham, pool, prec, max_iter=16, sparse=True, sparse_cap=ham.n_det)
+    de = hy.Adapt(ham, pool, prec, max_iter=16)
+    ad.set_ansatz(ops, th)
+    de.set_ansatz(ops, th)
+    rng = np.random.default_rng(7)
+    for rep in range(3):
+        t = th + (0 if rep == 0 else rng.normal(0, 0.2, len(th)))
+        e, g = ad.evaluate(t, dt)
+        e_d, g_d = de.evaluate(t, dt)
+        e_ref, g_ref = oadapt.energy_and_gradient(ref, opd, ops, t)
+        psi = ad.state(dt).double().cpu().numpy()
+        p_ref = oadapt.prepare(ref, opd, ops, t)
+        assert int(np.count_nonzero(p_ref)) == m
+        if dt == torch.float64:
+            assert abs(e - e_ref) < 1e-10 and abs(e_d - e_ref) < 1e-10
+            assert np.abs(g - g_ref).max() < 1e-9
+            assert np.abs(psi - p_ref).max() < 1e-12
+        else:
+            scale = max(1.0, abs(e_ref))
+            assert abs(e - e_ref) < 2e-6 * scale
+            assert np.abs(g - g_ref).max() < 1e-4 * max(1.0, np.abs(g_ref).max())
+            assert np.abs(g - g_d).max() < 1e-4 * max(1.0, np.abs(g_ref).max())
+            assert np.abs(psi - p_ref).max() < 1e-5
