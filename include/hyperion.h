@@ -63,7 +63,7 @@ typedef enum {
 
 typedef enum { HY_F64 = 0, HY_F32 = 1 } hy_dtype;
 
-typedef enum { HY_POOL_SPIN_ADAPTED_SD = 0 } hy_pool_kind;
+typedef enum { HY_POOL_SPIN_ADAPTED_SD = 0, HY_POOL_QEB = 1 } hy_pool_kind;
 
 typedef struct hy_ham hy_ham;
 typedef struct hy_pool hy_pool;
@@ -148,6 +148,25 @@ hy_status hy_pauli_table_build(const double *h1, const double *h2,
                                int64_t capacity, uint64_t *x, uint64_t *z,
                                double *coeff, int64_t *group_offsets,
                                int64_t *n_terms, int64_t *n_groups);
+
+/* Partitioned Hamiltonian of the SV-MPS scheme (Partitioned SV-MPS
+ * Emulation section): for a partitioning level eta the qubit chain is cut
+ * into 2^eta contiguous blocks of 2 n_orb / 2^eta qubits, and
+ * H = H_eta + sum B, where H_eta holds the Pauli terms of H that act inside
+ * one block (the blocks' local Hamiltonians H^(i), the identity term with
+ * them) and the B terms the interactions across blocks.  part = 0 builds a
+ * handle for H_eta, part = 1 one for the rest, from src's Pauli table (same
+ * integrals, determinant space and pruning); hy_energy on it gives the
+ * exact state-vector energy <psi|H_eta|psi> of the paper's expectation-value
+ * split (and <psi|B|psi>), every other call works on it as on any H.
+ * interleaved = 0 cuts the library's blocked qubit order (alpha spin
+ * orbitals, then beta); 1 cuts the chain with orbital p's alpha and beta
+ * spin orbitals adjacent (positions 2p, 2p + 1).  The paper does not state
+ * its qubit order; both are offered.  eta = 0 gives H itself (part 0).
+ * HY_ERR_ARG unless 2^eta divides 2 n_orb (eta <= 5); *out receives an
+ * owned handle (hy_ham_destroy). */
+hy_status hy_ham_partition(const hy_ham *src, int eta, int interleaved, int part,
+                           hy_ham **out);
 
 /* Release a handle and its device memory (NULL is accepted). */
 hy_status hy_ham_destroy(hy_ham *h);
@@ -338,16 +357,29 @@ hy_status hy_pool_gradients_sparse(const hy_ham *h, const hy_pool *p,
 /* Operator pool, gradients and exp(theta A)                                */
 /* ---------------------------------------------------------------------- */
 
-/* Spin-adapted singles and doubles relative to the Hartree-Fock determinant
- * (lowest n_alpha / n_beta orbitals occupied).  Order: singles (i<a), then
- * same-spin doubles (i<j, a<b), then opposite-spin doubles (i<=j, a<=b,
- * couplings); an operator whose constituents would share a spin orbital is
- * split into one pool entry per constituent, so every generator
- * A_k = sum_c (C_c - C_c^dagger) is a sum of commuting terms on disjoint
- * spin orbitals.  *out receives an owned pool (free with hy_pool_destroy). */
+/* HY_POOL_SPIN_ADAPTED_SD: spin-adapted singles and doubles relative to the
+ * Hartree-Fock determinant (lowest n_alpha / n_beta orbitals occupied).
+ * Order: singles (i<a), then same-spin doubles (i<j, a<b), then
+ * opposite-spin doubles (i<=j, a<=b, couplings); an operator whose
+ * constituents would share a spin orbital is split into one pool entry per
+ * constituent, so every generator A_k = sum_c (C_c - C_c^dagger) is a sum of
+ * commuting terms on disjoint spin orbitals.
+ * HY_POOL_QEB: the qubit-excitation-based pool the paper's ADAPT-VQE runs use
+ * (Numerical performance subsection): one operator per spin-orbital single
+ * i -> a (same spin) and double (i, j) -> (a, b) (S_z kept) from occupied to
+ * virtual spin orbitals of the Hartree-Fock determinant, each a qubit
+ * excitation: C = Q+_a Q_i or Q+_a Q+_b Q_j Q_i with Q+ = (X - iY)/2 acting
+ * on one qubit and no Jordan-Wigner parity string, so C maps determinant d
+ * to d with the electrons moved and sign +1.  Order: alpha singles, beta
+ * singles, alpha-alpha, beta-beta, alpha-beta doubles, each lexicographic in
+ * (i, [j,] a [, b]).  Descriptors have the same layout as the fermionic
+ * pool's (hy_pool_describe); hy_pool_qubit tells the two apart.
+ * *out receives an owned pool (free with hy_pool_destroy). */
 hy_status hy_pool_create(const hy_ham *h, hy_pool_kind kind, hy_pool **out);
 hy_status hy_pool_destroy(hy_pool *p);
 hy_status hy_pool_size(const hy_pool *p, int64_t *k);
+/* *qubit = 1 for a pool of qubit excitations (HY_POOL_QEB), else 0. */
+hy_status hy_pool_qubit(const hy_pool *p, int *qubit);
 
 /* Host output desc[11]: [n_constituents, then per constituent (rank, c0, c1,
  * a1, a0)]; rank 1 is a+_{c0} a_{a0}, rank 2 is a+_{c0} a+_{c1} a_{a1}
@@ -650,10 +682,11 @@ typedef struct {
                              exactly even when a ranker is attached (its
                              pairs still train it).
                              0: always the dense sweeps                        */
-    int64_t sparse_cap;   /* support capacity of the sparse path; 0: N_det/64
-                             for double and N_det/256 for float evaluations
-                             (about where the scatter H psi stops beating the
-                             dense sweep)                                     */
+    int64_t sparse_cap;   /* support capacity of the sparse path; 0: N_det/8
+                             for double and N_det/32 for float evaluations
+                             (the scatter H psi, ~29 ns per listed amplitude,
+                             beats the dense float sweep up to ~N_det/23 and
+                             the double one up to ~N_det/3)                   */
     double exact_screen_work; /* sparse path with a ranker: screen the whole
                              pool exactly while (pool size) x (support) is at
                              most this; 0: 5e9 (the cost of the ranker's

@@ -84,11 +84,16 @@ def _require_cuda(*ts):
 class Hamiltonian:
     """H built from integrals (chemists' notation) on Omega_CIk."""
 
-    def __init__(self, h1, h2, e_core, n_orb, n_alpha, n_beta, prune_tol=1e-14):
+    def __init__(self, h1, h2, e_core, n_orb, n_alpha, n_beta, prune_tol=1e-14, _handle=None):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
         lib = _abi.load()
         self.n_orb, self.n_alpha, self.n_beta = int(n_orb), int(n_alpha), int(n_beta)
+        if _handle is not None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+            self._h = _handle
+            self._info()
+            return
         h1 = np.ascontiguousarray(h1, dtype=np.float64)
         h2 = np.ascontiguousarray(h2, dtype=np.float64)
         if h1.shape != (n_orb, n_orb) or h2.shape != (n_orb,) * 4:
@@ -100,11 +105,22 @@ class Hamiltonian:
             float(e_core), self.n_orb, self.n_alpha, self.n_beta, float(prune_tol),
             ctypes.byref(handle)))
         self._h = handle
+        self._info()
+
+    def _info(self):
         vals = [ctypes.c_int64() for _ in range(5)]
-        check(lib.hy_ham_info(self._h, *[ctypes.byref(v) for v in vals]))
+        check(_abi.load().hy_ham_info(self._h, *[ctypes.byref(v) for v in vals]))
         (self.n_det, self.n_alpha_str, self.n_beta_str, self.n_groups,
          self.n_terms) = [v.value for v in vals]
         self._scalar = torch.zeros(4, dtype=torch.float64, device=self.device)
+
+    def partition(self, eta: int, interleaved: bool = False, part: int = 0) -> "Hamiltonian":
+        """H_eta (part 0: the Pauli terms inside one of 2^eta qubit blocks) or
+        the cross-block rest (part 1) of the SV-MPS split, as a Hamiltonian."""
+        h = ctypes.c_void_p()
+        check(_abi.load().hy_ham_partition(self._h, int(eta), 1 if interleaved else 0, int(part),
+                                           ctypes.byref(h)))
+        return Hamiltonian(None, None, 0.0, self.n_orb, self.n_alpha, self.n_beta, _handle=h)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -351,14 +367,17 @@ class ExplicitH:
 
 
 class Pool:
-    """Spin-adapted singles+doubles pool relative to the HF determinant."""
+    """Operator pool relative to the HF determinant: kind "sd" (spin-adapted
+    fermionic singles+doubles) or "qeb" (qubit-excitation-based: one qubit
+    excitation per spin-orbital single and double)."""
 
-    def __init__(self, ham: Hamiltonian):
+    def __init__(self, ham: Hamiltonian, kind: str = "sd"):
         lib = _abi.load()
         self.ham = ham
+        self.kind = kind
+        code = {"sd": _abi.HY_POOL_SPIN_ADAPTED_SD, "qeb": _abi.HY_POOL_QEB}[kind]
         handle = ctypes.c_void_p()
-        check(lib.hy_pool_create(ham.handle, _abi.HY_POOL_SPIN_ADAPTED_SD,
-                                 ctypes.byref(handle)))
+        check(lib.hy_pool_create(ham.handle, code, ctypes.byref(handle)))
         self._p = handle
         k = ctypes.c_int64()
         check(lib.hy_pool_size(self._p, ctypes.byref(k)))

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_PKG, "libhyperion.so")
 HY_OK, HY_ERR_ARG, HY_ERR_CUDA, HY_ERR_OOM, HY_ERR_TIMEOUT, HY_ERR_UNSUPPORTED = range(6)
 HY_F64, HY_F32 = 0, 1
 HY_POOL_SPIN_ADAPTED_SD = 0
+HY_POOL_QEB = 1
 
 _STATUS = {HY_ERR_ARG: "HY_ERR_ARG", HY_ERR_CUDA: "HY_ERR_CUDA",
            HY_ERR_OOM: "HY_ERR_OOM", HY_ERR_TIMEOUT: "HY_ERR_TIMEOUT",
@@ -87,6 +88,7 @@ SIGNATURES = {
     "hy_ham_set_coupling": (I32, [P, I32]),
     "hy_ham_set_wait_limit": (I32, [P, I64]),
     "hy_ham_upload_bytes": (I32, [P, P, PI64]),
+    "hy_ham_partition": (I32, [P, I32, I32, I32, P]),
     "hy_ham_coupling_ms": (I32, [P, P]),
     "hy_pauli_table_build": (I32, [P, P, D, I32, D, I64, P, P, P, P, PI64, PI64]),
     "hy_rank": (I32, [P, P, P, I64, P]),
@@ -109,6 +111,7 @@ SIGNATURES = {
     "hy_pool_create": (I32, [P, I32, PP]),
     "hy_pool_destroy": (I32, [P]),
     "hy_pool_size": (I32, [P, PI64]),
+    "hy_pool_qubit": (I32, [P, ctypes.POINTER(ctypes.c_int)]),
     "hy_pool_describe": (I32, [P, I64, P]),
     "hy_pool_gradients": (I32, [P, P, P, P, P, I64, P, I32, P]),
     "hy_apply_excitation": (I32, [P, P, I64, D, P, I32, I32, P]),

@@ -84,6 +84,7 @@ struct hy_ham {
     hy::StringSpace A, B;
     hy::PauliTable pauli;
     hy::KernelTables kt;
+    std::vector<double> h1h, h2h;   // the integrals (host copies)
     DevArena arena;
     uint32_t *d_astr = nullptr, *d_bstr = nullptr;
     uint32_t *d_aex = nullptr, *d_bexT = nullptr;
@@ -141,6 +142,7 @@ struct hy_pool {
     // a device list and reported by the next screen call on this pool
     unsigned long long *d_bad = nullptr;
     unsigned long long *h_bad = nullptr;
+    int qubit = 0;                  // HY_POOL_QEB: qubit excitations, no sign
 };
 
 struct hy_batch {
@@ -561,6 +563,10 @@ void copy_pauli(const hy::PauliTable &t, uint64_t *x, uint64_t *z, double *coeff
 
 }  // namespace
 
+namespace {
+hy_status finish_ham(hy_ham *h, hy_ham **out);
+}  // namespace
+
 extern "C" {
 
 const char *hy_last_error(void) { return g_err.c_str(); }
@@ -600,6 +606,22 @@ hy_status hy_build_hamiltonian(const double *h1, const double *h2, double e_core
         delete h;
         return fail(HY_ERR_UNSUPPORTED, why);
     }
+    h->h1h.assign(h1, h1 + size_t(n_orb) * n_orb);
+    h->h2h.assign(h2, h2 + size_t(n_orb) * n_orb * n_orb * n_orb);
+    return finish_ham(h, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The rest of a build from h's Pauli table (set, with the string spaces and
+// the host integrals): fold the kernel tables, query the device and upload.
+// Takes ownership of h (released on failure).
+hy_status finish_ham(hy_ham *h, hy_ham **out)
+{
+    const int n_orb = h->n;
+    const double *h1 = h->h1h.data(), *h2 = h->h2h.data();
     hy::fold_tables(h->pauli, n_orb, h->A, h->B, h->kt);
 
     cudaError_t e = cudaGetDevice(&h->device);
@@ -676,6 +698,76 @@ hy_status hy_build_hamiltonian(const double *h1, const double *h2, double e_core
     }
     *out = h;
     return HY_OK;
+}
+
+// position of spin orbital j (blocked order) along the qubit chain the
+// partition cuts: blocked keeps it, interleaved puts orbital p's alpha and
+// beta spin orbitals next to each other (2p, 2p + 1)
+int chain_position(int j, int n, int interleaved)
+{
+    if (!interleaved) return j;
+    return j < n ? 2 * j : 2 * (j - n) + 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+hy_status hy_ham_partition(const hy_ham *src, int eta, int interleaved, int part, hy_ham **out)
+{
+    if (!out) return fail(HY_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!src) return fail(HY_ERR_ARG, "handle is NULL");
+    const int n = src->n, nq = 2 * n;
+    if (eta < 0 || eta > 5 || (nq % (1 << eta)) != 0)
+        return fail(HY_ERR_ARG, "2^eta must divide the qubit count");
+    if (part != 0 && part != 1) return fail(HY_ERR_ARG, "part must be 0 (H_eta) or 1 (the rest)");
+    const int width = nq >> eta;                      // qubits per block
+    hy_ham *h = new (std::nothrow) hy_ham;
+    if (!h) return fail(HY_ERR_OOM, "host allocation failed");
+    h->n = n;
+    h->na = src->na;
+    h->nb = src->nb;
+    h->A = src->A;
+    h->B = src->B;
+    h->Na = src->Na;
+    h->Nb = src->Nb;
+    h->N = src->N;
+    h->h1h = src->h1h;
+    h->h2h = src->h2h;
+    // the terms whose support (x | z) lies inside one block (the identity
+    // included), or the others
+    const hy::PauliTable &t = src->pauli;
+    hy::PauliTable &f = h->pauli;
+    f.n_qubits = t.n_qubits;
+    const size_t G = t.group_off.size() - 1;
+    f.group_off.push_back(0);
+    for (size_t g = 0; g < G; ++g) {
+        for (int64_t i = t.group_off[g]; i < t.group_off[g + 1]; ++i) {
+            const uint64_t sup = t.x[size_t(i)] | t.z[size_t(i)];
+            int blk = -1;
+            bool inside = true;
+            for (uint64_t m = sup; m; m &= m - 1) {
+                const int b = chain_position(__builtin_ctzll(m), n, interleaved) / width;
+                if (blk < 0) blk = b;
+                else if (b != blk) { inside = false; break; }
+            }
+            if (inside != (part == 0)) continue;
+            f.x.push_back(t.x[size_t(i)]);
+            f.z.push_back(t.z[size_t(i)]);
+            f.cxz.push_back(t.cxz[size_t(i)]);
+        }
+        if (int64_t(f.x.size()) > f.group_off.back()) {
+            f.group_of_x[f.x.back()] = int64_t(f.group_off.size()) - 1;
+            f.group_off.push_back(int64_t(f.x.size()));
+        }
+    }
+    std::string why;
+    if (!hy::check_two_body_structure(f, n, why)) {
+        delete h;
+        return fail(HY_ERR_UNSUPPORTED, why);
+    }
+    return finish_ham(h, out);
 }
 
 hy_status hy_ham_destroy(hy_ham *h)
@@ -912,11 +1004,16 @@ hy_status hy_pool_create(const hy_ham *h, hy_pool_kind kind, hy_pool **out)
     if (!out) return fail(HY_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!h) return fail(HY_ERR_ARG, "handle is NULL");
-    if (kind != HY_POOL_SPIN_ADAPTED_SD) return fail(HY_ERR_UNSUPPORTED, "unknown pool kind");
+    if (kind != HY_POOL_SPIN_ADAPTED_SD && kind != HY_POOL_QEB)
+        return fail(HY_ERR_UNSUPPORTED, "unknown pool kind");
     hy_pool *p = new (std::nothrow) hy_pool;
     if (!p) return fail(HY_ERR_OOM, "host allocation failed");
     p->h = h;
-    hy::build_pool_spin_adapted(h->n, h->na, h->nb, p->ops);
+    p->qubit = kind == HY_POOL_QEB ? 1 : 0;
+    if (p->qubit)
+        hy::build_pool_qeb(h->n, h->na, h->nb, p->ops);
+    else
+        hy::build_pool_spin_adapted(h->n, h->na, h->nb, p->ops);
     const int n = h->n;
     for (const auto &op : p->ops) {
         hy::k::OpDev od{op.desc[0], -1, -1, 0};
@@ -936,7 +1033,7 @@ hy_status hy_pool_create(const hy_ham *h, hy_pool_kind kind, hy_pool **out)
             }
             // C = eps * (alpha ops in order) * (beta ops in order); eps counts
             // the transpositions that move alpha operators left of beta ones.
-            hy::PatternKey ka{0, {0, 0, 0, 0}}, kb{0, {0, 0, 0, 0}};
+            hy::PatternKey ka{0, {0, 0, 0, 0}, p->qubit}, kb{0, {0, 0, 0, 0}, p->qubit};
             int inv = 0, nbeta_seen = 0;
             for (int u = 0; u < no; ++u) {
                 bool beta = modes[u] >= n;
@@ -956,7 +1053,8 @@ hy_status hy_pool_create(const hy_ham *h, hy_pool_kind kind, hy_pool **out)
             hy::k::ConsDev cd;
             cd.ap = ka.nops ? p->pa.get(ka, h->A) : -1;
             cd.bp = kb.nops ? p->pb.get(kb, h->B) : -1;
-            cd.eps = (inv & 1) ? -1 : 1;
+            // qubit operators on different qubits commute: no reordering sign
+            cd.eps = (!p->qubit && (inv & 1)) ? -1 : 1;
             cd.pad = 0;
             int ci = int(p->cons.size());
             p->cons.push_back(cd);
@@ -1010,6 +1108,13 @@ hy_status hy_pool_size(const hy_pool *p, int64_t *k)
 {
     if (!p || !k) return fail(HY_ERR_ARG, "NULL argument");
     *k = int64_t(p->ops.size());
+    return HY_OK;
+}
+
+hy_status hy_pool_qubit(const hy_pool *p, int *qubit)
+{
+    if (!p || !qubit) return fail(HY_ERR_ARG, "bad arguments");
+    *qubit = p->qubit;
     return HY_OK;
 }
 
@@ -1385,6 +1490,7 @@ hy_status hy_pool_gradients_sparse(const hy_ham *h, const hy_pool *p, const void
         a.desc = p->d_desc; a.ops = ops_or_null; a.n_ops = n_ops;
         a.astr = h->d_astr; a.bstr = h->d_bstr; a.binom33 = h->d_binom; a.n = h->n;
         a.Nb = h->Nb; a.g = g_out; a.K = int64_t(p->ops.size()); a.bad = p->d_bad;
+        a.qubit = p->qubit;
     };
     hy::ProfScope prof(HY_PROF_SCREEN_SPARSE, stream, 0.0);
     if (dt == HY_F64) {
@@ -1943,6 +2049,7 @@ hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double thet
     o.binom33 = h->d_binom;
     o.n = h->n;
     o.Nb = h->Nb;
+    o.qubit = p->qubit;
     const int nc = p->ops[k].desc[0];
     cudaStream_t st = as_stream(stream);
     // bytes estimated from the support the host last read back (the count
@@ -1973,6 +2080,7 @@ hy_status sstate_prepare(SparseState *s, const hy_pool *p, const int32_t *ops, c
     o.binom33 = h->d_binom;
     o.n = h->n;
     o.Nb = h->Nb;
+    o.qubit = p->qubit;
     cudaStream_t st = as_stream(stream);
     hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
     if (s->dt == HY_F64)
@@ -2061,6 +2169,7 @@ hy::k::SvOpArgs sv_op_args(const hy_ham *h, const hy_pool *p)
     o.binom33 = h->d_binom;
     o.n = h->n;
     o.Nb = h->Nb;
+    o.qubit = p->qubit;
     return o;
 }
 }  // namespace
@@ -2190,6 +2299,7 @@ hy_status sstate_grad_forward(SparseState *f, SparseState *w, const hy_pool *p, 
     o.binom33 = h->d_binom;
     o.n = h->n;
     o.Nb = h->Nb;
+    o.qubit = p->qubit;
     cudaStream_t st = as_stream(stream);
     hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
     if (f->dt == HY_F64)
@@ -2282,6 +2392,7 @@ hy_status sstate_gradients(const SparseState *sc, const void *lam, const hy_pool
         a.desc = p->d_desc; a.ops = ops; a.n_ops = n_ops;
         a.astr = h->d_astr; a.bstr = h->d_bstr; a.binom33 = h->d_binom; a.n = h->n;
         a.Nb = h->Nb; a.g = g; a.K = int64_t(p->ops.size()); a.bad = p->d_bad;
+        a.qubit = p->qubit;
     };
     if (s->dt == HY_F64) {
         hy::k::SparseGradArgs<double> a;

@@ -412,9 +412,39 @@ void build_pool_spin_adapted(int n, int na, int nb, std::vector<PoolOpHost> &ops
                 }
 }
 
+void build_pool_qeb(int n, int na, int nb, std::vector<PoolOpHost> &ops)
+{
+    ops.clear();
+    PoolBuilder pb{n, na, nb, &ops};
+    // singles i -> a, alpha then beta
+    for (int sp = 0; sp < 2; ++sp)
+        for (int i = 0; i < n; ++i)
+            for (int a = 0; a < n; ++a)
+                if (pb.ok1(a + sp * n, i + sp * n)) pb.push({{1, a + sp * n, 0, 0, i + sp * n}});
+    // same-spin doubles (i < j) -> (a < b), alpha-alpha then beta-beta
+    for (int sp = 0; sp < 2; ++sp) {
+        const int o = sp * n;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j)
+                for (int a = 0; a < n; ++a)
+                    for (int b = a + 1; b < n; ++b) {
+                        std::array<int, 5> t{2, a + o, b + o, j + o, i + o};
+                        if (pb.ok2(t.data())) pb.push({t});
+                    }
+    }
+    // opposite-spin doubles (i alpha, j beta) -> (a alpha, b beta)
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            for (int a = 0; a < n; ++a)
+                for (int b = 0; b < n; ++b) {
+                    std::array<int, 5> t{2, a, b + n, j + n, i};
+                    if (pb.ok2(t.data())) pb.push({t});
+                }
+}
+
 bool PatternKey::operator==(const PatternKey &o) const
 {
-    if (nops != o.nops) return false;
+    if (nops != o.nops || qubit != o.qubit) return false;
     for (int i = 0; i < nops; ++i)
         if (ops[i] != o.ops[i]) return false;
     return true;
@@ -422,13 +452,14 @@ bool PatternKey::operator==(const PatternKey &o) const
 
 size_t PatternKeyHash::operator()(const PatternKey &k) const
 {
-    size_t h = size_t(k.nops);
+    size_t h = size_t(k.nops) * 2 + size_t(k.qubit);
     for (int i = 0; i < k.nops; ++i) h = h * 131 + size_t(k.ops[i]);
     return h;
 }
 
 // Apply a product of operators (rightmost first) to one spin string of n
-// modes; sign (-1)^(occupied modes below) per operator.
+// modes; sign (-1)^(occupied modes below) per fermionic operator, none for
+// qubit operators.
 static bool apply_within_string(const PatternKey &k, uint32_t s, uint32_t &out,
                                 int &neg)
 {
@@ -438,7 +469,7 @@ static bool apply_within_string(const PatternKey &k, uint32_t s, uint32_t &out,
         uint32_t bit = 1u << mode;
         int occ = (s & bit) != 0;
         if (occ == dag) return false;
-        neg ^= __builtin_popcount(s & (bit - 1)) & 1;
+        if (!k.qubit) neg ^= __builtin_popcount(s & (bit - 1)) & 1;
         s ^= bit;
     }
     out = s;

@@ -93,6 +93,11 @@ struct PoolOpHost {
     int32_t desc[11];   // [nc, (rank, c0, c1, a1, a0) x 2]
 };
 void build_pool_spin_adapted(int n, int na, int nb, std::vector<PoolOpHost> &ops);
+// Qubit-excitation-based pool: every spin-orbital single and double
+// excitation from the Hartree-Fock occupied to the virtual spin orbitals
+// that keeps S_z, one operator each (no spin complement), acting as a qubit
+// excitation (no Jordan-Wigner sign)
+void build_pool_qeb(int n, int na, int nb, std::vector<PoolOpHost> &ops);
 
 // A constituent split into its alpha part and beta part: C = eps * Ca * Cb.
 // Each part is a pattern id into the per-spin pattern lists, or -1 for the
@@ -100,6 +105,7 @@ void build_pool_spin_adapted(int n, int na, int nb, std::vector<PoolOpHost> &ops
 struct PatternKey {
     int nops;
     int ops[4];          // 2 * orbital + dagger, in product order
+    int qubit = 0;       // 1: qubit operators (no Jordan-Wigner sign)
     bool operator==(const PatternKey &o) const;
 };
 struct PatternKeyHash {

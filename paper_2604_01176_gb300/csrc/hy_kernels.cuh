@@ -277,6 +277,7 @@ struct SparseGradArgs {
     double *g;
     int64_t K;               // pool size: listed indices outside [0, K) are refused
     unsigned long long *bad; // (position << 32 | index) of the first refused entry, or nullptr
+    int qubit;               // 1: qubit excitations (no Jordan-Wigner sign)
 };
 template <typename T>
 cudaError_t support(const T *psi, int64_t N, int64_t *list, int64_t cap,
@@ -306,6 +307,7 @@ struct SvOpArgs {
     const uint32_t *astr, *bstr, *binom33;
     int n;
     int64_t Nb;
+    int qubit;                   // 1: the pool's operators are qubit excitations (no sign)
 };
 // v <- 0 on the support, bits cleared, count <- 0; then (hf) v[0] = 1 listed
 template <typename T>

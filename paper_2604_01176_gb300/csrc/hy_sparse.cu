@@ -161,14 +161,16 @@ __device__ __forceinline__ uint32_t rank_bits(uint32_t m, const uint32_t (*C)[33
 
 // Apply an operator string (application order; codes 2*mode + dagger) to a
 // determinant mask; false if it annihilates it.  Sign: (-1)^(occupied modes
-// below) per operator (Jordan-Wigner, blocked order).
-__device__ __forceinline__ bool apply_string(const int *code, int len, uint64_t &mask, int &sg)
+// below) per fermionic operator (Jordan-Wigner, blocked order); qubit
+// operators carry none.
+__device__ __forceinline__ bool apply_string(const int *code, int len, uint64_t &mask, int &sg,
+                                             int qubit)
 {
     for (int t = 0; t < len; ++t) {
         const int mode = code[t] >> 1, dag = code[t] & 1;
         const uint64_t bit = 1ull << mode;
         if (((mask & bit) != 0) == (dag != 0)) return false;
-        if (__popcll(mask & (bit - 1)) & 1) sg = -sg;
+        if (!qubit && (__popcll(mask & (bit - 1)) & 1)) sg = -sg;
         mask ^= bit;
     }
     return true;
@@ -236,7 +238,7 @@ k_grad_sparse(SparseGradArgs<T> a)
             const uint64_t mask = uint64_t(a.astr[d / a.Nb]) | (uint64_t(a.bstr[d % a.Nb]) << n);
             uint64_t o = mask;
             int sg = 1;
-            if (apply_string(fw, len, o, sg)) {       // d is the domain end
+            if (apply_string(fw, len, o, sg, a.qubit)) {       // d is the domain end
                 const int64_t d2 = int64_t(rank_bits(uint32_t(o & lowm), C)) * a.Nb +
                                    rank_bits(uint32_t(o >> n), C);
                 tot += sg * (double(a.sigma[d2]) * x - double(a.sigma[d]) * double(a.psi[d2]));
@@ -244,7 +246,7 @@ k_grad_sparse(SparseGradArgs<T> a)
             }
             o = mask;
             sg = 1;
-            if (apply_string(bw, len, o, sg)) {       // d is the image end
+            if (apply_string(bw, len, o, sg, a.qubit)) {       // d is the image end
                 const int64_t d0 = int64_t(rank_bits(uint32_t(o & lowm), C)) * a.Nb +
                                    rank_bits(uint32_t(o >> n), C);
                 const bool listed = a.bits ? member(a.bits, d0) : a.psi[d0] != T(0);
@@ -337,14 +339,14 @@ __device__ __forceinline__ void sv_rotate(SVec<T> &x, const SvOpArgs &o, int k, 
         uint64_t u = mask;
         int sg = 1;
         int64_t dom, img, fresh;
-        if (apply_string(fw, len, u, sg)) {
+        if (apply_string(fw, len, u, sg, o.qubit)) {
             dom = d;
             img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
             fresh = member(x.bits, img) ? -1 : img;
         } else {
             u = mask;
             sg = 1;
-            if (!apply_string(bw, len, u, sg)) continue;    // C and C^dagger annihilate d
+            if (!apply_string(bw, len, u, sg, o.qubit)) continue;    // C and C^dagger annihilate d
             img = d;
             dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
             if (member(x.bits, dom)) continue;              // the domain end rotates the pair
@@ -448,14 +450,14 @@ __device__ void blk_rotate(SVec<T> &x, const SvOpArgs &o, int k, int ci, T c, T 
         uint64_t u = mask;
         int sg = 1;
         int64_t dom, img, fresh;
-        if (apply_string(fw, len, u, sg)) {
+        if (apply_string(fw, len, u, sg, o.qubit)) {
             dom = d;
             img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
             fresh = member(x.bits, img) ? -1 : img;
         } else {
             u = mask;
             sg = 1;
-            if (!apply_string(bw, len, u, sg)) continue;
+            if (!apply_string(bw, len, u, sg, o.qubit)) continue;
             img = d;
             dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
             if (member(x.bits, dom)) continue;
@@ -487,13 +489,13 @@ __device__ void blk_generator(const SVec<T> &f, SVec<T> &w, const SvOpArgs &o, i
         int sg = 1;
         int64_t tgt;
         T val;
-        if (apply_string(fw, len, u, sg)) {          // C|d> = sg |tgt>
+        if (apply_string(fw, len, u, sg, o.qubit)) {          // C|d> = sg |tgt>
             tgt = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
             val = sg > 0 ? f.v[d] : -f.v[d];
         } else {
             u = mask;
             sg = 1;
-            if (!apply_string(bw, len, u, sg)) continue;
+            if (!apply_string(bw, len, u, sg, o.qubit)) continue;
             // -C^dagger |d> = -sg |tgt>
             tgt = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
             val = sg > 0 ? -f.v[d] : f.v[d];
@@ -760,7 +762,7 @@ k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t 
     int sg = 1;
     int32_t e = 0;
     bool escape = false;
-    if (apply_string(fw, len, u, sg)) {
+    if (apply_string(fw, len, u, sg, o.qubit)) {
         const int64_t img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
         const int p = prog_find(key, m, img);
         if (p >= 0) e = sg > 0 ? p + 1 : -(p + 1);
@@ -768,7 +770,7 @@ k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t 
     } else {
         u = mask;
         sg = 1;
-        if (apply_string(bw, len, u, sg)) {
+        if (apply_string(bw, len, u, sg, o.qubit)) {
             const int64_t dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
             escape = prog_find(key, m, dom) < 0;
         }
@@ -967,7 +969,7 @@ k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
         int sg = 1;
         int32_t e = 0;
         bool escape = false;
-        if (apply_string(fw, len, u, sg)) {
+        if (apply_string(fw, len, u, sg, o.qubit)) {
             const int64_t img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
                                 rank_bits(uint32_t(u >> n), C);
             if (member(bits, img)) {
@@ -979,7 +981,7 @@ k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
         } else {
             u = mask;
             sg = 1;
-            if (apply_string(bw, len, u, sg)) {
+            if (apply_string(bw, len, u, sg, o.qubit)) {
                 const int64_t dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
                                     rank_bits(uint32_t(u >> n), C);
                 escape = !member(bits, dom);

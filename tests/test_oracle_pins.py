@@ -449,3 +449,135 @@ def test_select_tie_break():
     assert oadapt.select(np.array([1.0 - 2e-12, -1.0])) == 1     # outside the band
     assert oadapt.select(np.array([0.0, 0.0, 3e-7, -2e-7])) == 2
     assert oadapt.select(np.array([-4.0])) == 0
+
+
+# --------------------------------------------------------------------------
+# QEB pool (paper: Numerical performance subsection -- the ADAPT-VQE runs
+# use a qubit-excitation-based pool).  A qubit excitation is the fermionic
+# excitation without Jordan-Wigner parity strings; pinned against Kronecker
+# products of single-qubit matrices, scipy expm, a closed-form count and
+# central differences.
+# --------------------------------------------------------------------------
+_QP = sp.csr_matrix(np.array([[0.0, 0.0], [1.0, 0.0]]))   # Q+ = |1><0|: occupies
+
+
+def _qubit_generator_kron(op, M, dets):
+    """A = C - C^dagger with C = Q+_a [Q+_b Q_j] Q_i built from 2x2 factors
+    (no Z strings), restricted to Omega_CIk."""
+    def single(j, mat):
+        factors = [_I] * (M - 1 - j) + [mat] + [_I] * j
+        m = factors[0]
+        for f in factors[1:]:
+            m = sp.kron(m, f, format="csr")
+        return m
+    qp = [single(j, _QP) for j in range(M)]
+    qm = [x.T.tocsr() for x in qp]
+    rank = int(op[1])
+    if rank == 1:
+        C = qp[op[2]] @ qm[op[5]]
+    else:
+        C = qp[op[2]] @ qp[op[3]] @ qm[op[4]] @ qm[op[5]]
+    A = (C - C.T).toarray()
+    return A[np.ix_(dets, dets)]
+
+
+def test_qeb_generator_and_exponential_against_qubit_matrices():
+    from oracle.qeb import QubitSystem
+    n, na, nb = 4, 2, 2
+    s = small_system(n, na, nb, 23)
+    q = QubitSystem(s)
+    pool = q.pool()
+    dets = s.dets().astype(np.int64)
+    eye = np.eye(s.n_det)
+    psi = synth.random_state(s.n_det, 9)
+    a = jw_annihilators(2 * n)
+    differs = 0
+    for op in pool:
+        Aq = _qubit_generator_kron(op, 2 * n, dets)
+        Aor = np.stack([q.apply_generator(op, eye[:, j]) for j in range(s.n_det)], axis=1)
+        assert np.array_equal(Aor, Aq)
+        for theta in (0.4, -1.3):
+            ref = scipy.linalg.expm(theta * Aq) @ psi
+            assert np.allclose(q.apply_excitation(op, theta, psi), ref, atol=1e-13)
+        # the fermionic operator on the same spin orbitals: same pairs, signs
+        # that differ exactly where a Jordan-Wigner string is odd
+        Af = _dense_generator_jw(op, n, dets, a)
+        assert np.array_equal(np.abs(Af), np.abs(Aq))
+        differs += int(np.any(Af != Aq))
+    assert differs > 0
+
+
+@pytest.mark.parametrize("n,na,nb", [(4, 2, 2), (6, 3, 3), (7, 4, 3), (5, 1, 4)])
+def test_qeb_pool_size_closed_form(n, na, nb):
+    from oracle.qeb import QubitSystem
+    q = QubitSystem(small_system(n, na, nb, 1))
+    c2 = lambda m: m * (m - 1) // 2
+    sa, sb = na * (n - na), nb * (n - nb)
+    expect = sa + sb + c2(na) * c2(n - na) + c2(nb) * c2(n - nb) + sa * sb
+    pool = q.pool()
+    assert len(pool) == expect
+    assert len({tuple(op) for op in pool.tolist()}) == expect
+
+
+def test_qeb_gradient_matches_central_differences_and_adapt():
+    from oracle.qeb import QubitSystem
+    s = small_system(6, 3, 3, 1001)
+    q = QubitSystem(s)
+    pool = q.pool()
+    psi = q.hf_state()
+    for k, t in [(0, 0.2), (len(pool) - 1, -0.3), (len(pool) // 2, 0.15)]:
+        psi = q.apply_excitation(pool[k], t, psi)
+    g = q.gradients(pool, psi, q.sigma(psi))
+    h = 1e-4
+    for k in range(0, len(pool), 3):
+        ep = q.energy(q.apply_excitation(pool[k], h, psi))
+        em = q.energy(q.apply_excitation(pool[k], -h, psi))
+        assert abs((ep - em) / (2 * h) - g[k]) < 1e-7
+    rec = oadapt.run(q, pool, max_iter=6)
+    e = np.array(rec["energy"])
+    assert np.all(np.diff(e) <= 1e-12) and np.all(e >= s.fci_energy() - 1e-12)
+
+
+# --------------------------------------------------------------------------
+# SV-MPS partition (paper: Partitioned SV-MPS Emulation section, H = H_eta +
+# sum B with H_eta the blocks' local Hamiltonians).  The oracle's Pauli
+# expansion is pinned against the Kronecker JW Hamiltonian; the split
+# against closed forms and invariants.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,na,nb", [(3, 2, 1), (4, 2, 2)])
+def test_pauli_expansion_equals_jordan_wigner_hamiltonian(n, na, nb):
+    from oracle import partition as opart
+    h1, h2, _ = synth.integrals(n, 7 + n)
+    terms = opart.jw_terms(h1, h2, 0.37, n)
+    Hjw, _ = jw_hamiltonian(h1, h2, 0.37, n)
+    assert np.abs(opart.dense_full(terms, 2 * n) - Hjw.toarray()).max() < 1e-12
+
+
+def test_partition_closed_forms_and_invariants():
+    from oracle import partition as opart
+    n, na, nb = 4, 2, 2
+    h1, h2, ec = synth.integrals(n, 23)
+    s = oracle.System(h1, h2, ec, n, na, nb)
+    H = s.dense_h()
+    psi = synth.random_state(s.n_det, 3)
+    full = opart.dense_full(opart.jw_terms(h1, h2, ec, n), 2 * n)
+    for eta in (0, 1, 2, 3):
+        for inter in (False, True):
+            a = opart.Partition(s, h1, h2, ec, eta, inter, 0)
+            b = opart.Partition(s, h1, h2, ec, eta, inter, 1)
+            assert a.leak < 1e-14 and b.leak < 1e-14          # both keep N and S_z
+            assert np.abs(a.H - a.H.T).max() < 1e-14          # Hermitian
+            assert abs(a.energy(psi) + b.energy(psi) - s.energy(psi)) < 1e-12
+            # only the identity has a trace over the full space: H_eta carries it
+            assert abs(a.trace_full - np.trace(full)) < 1e-9 and abs(b.trace_full) < 1e-9
+            if eta == 0:
+                assert np.abs(a.H - H).max() < 1e-12 and not b.terms
+            if eta == 3:                                       # one qubit per block: diagonal
+                assert np.abs(a.H - np.diag(np.diag(a.H))).max() < 1e-14
+    # blocked order, one block per spin: a one-body H lies inside the blocks
+    s0 = oracle.System(h1, 0 * h2, ec, n, na, nb)
+    a0 = opart.Partition(s0, h1, 0 * h2, ec, 1, False, 0)
+    assert np.abs(a0.H - s0.dense_h()).max() < 1e-12
+    # ... and with h2 the cross-spin density terms leave it
+    a1 = opart.Partition(s, h1, h2, ec, 1, False, 0)
+    assert np.abs(a1.H - H).max() > 1e-3
