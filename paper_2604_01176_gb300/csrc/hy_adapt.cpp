@@ -49,6 +49,9 @@ struct hy_adapt {
     double last_max = 0.0;        // largest |g| of the most recent screen
     hy_adapt_config cfg{};
     int64_t N = 0, K = 0;
+    int n_orb = 0;
+    std::vector<int32_t> p_desc_v;       // [K][11] pool descriptors (host)
+    const int32_t *p_desc = nullptr;
     // device state: [dtype][psi, sigma, phi, lam]
     void *buf[2][4] = {{nullptr, nullptr, nullptr, nullptr},
                        {nullptr, nullptr, nullptr, nullptr}};
@@ -66,6 +69,10 @@ struct hy_adapt {
     std::vector<double> valid_theta;
     // the last iteration was refined in double: screen its double state
     bool screen_f64_next = false;
+    // sigma = H psi holds every component (false after an evaluation that
+    // formed it on psi's support only, through the support Hamiltonian)
+    bool sigma_full[2] = {false, false};
+    bool want_full_sigma = false;        // the next evaluation must form all of sigma
     int evals = 0, evals64 = 0;
     int iter = 0;
     int64_t h2d = 0, d2h = 0;     // bytes copied host <-> device so far
@@ -168,6 +175,9 @@ hy_status finish_energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt)
 // kForwardSmall, above which the reverse sweep serves
 const int64_t kPrepareSmall = 65536;
 const int64_t kForwardSmall = 12288;
+// the support Hamiltonian is built when it holds at most this many entries
+// (12 bytes each)
+const int64_t kHssMaxEntries = int64_t(1) << 29;
 
 // The sparse evaluation: psi = U(theta)|HF> as a sparse vector (rotations
 // cost O(support)), renormalised over its support in double (float states),
@@ -222,12 +232,22 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
             HY_TRY(hy::sstate_scale_rsqrt(S, a->d_n2, st));
         }
     }
-    // list sigma's support while the last support times the couplings (an
-    // upper bound) fits its list; a list that still overflows (the support
-    // grew with a new operator) is caught below and costs only the listing
+    // sigma: within a compiled ansatz the energy and the forward gradients
+    // read it on psi's support only, so the support Hamiltonian forms just
+    // that part; otherwise the scatter forms all of it.  List sigma's
+    // support while the last support times the couplings (an upper bound)
+    // fits its list; a list that still overflows (the support grew with a new
+    // operator) is caught below and costs only the listing
+    // (the program's forward gradient is the one that reads sigma on the
+    // support only: without it the gradient reads sigma beyond the support)
+    const bool use_hss = prog_run && hy::prog_hss_ready(a->prog) && a->prog_grad_ok &&
+                         !a->want_full_sigma;
     const double est = double(std::max<int64_t>(a->sparse_m_last[d], 1)) * double(a->conn);
-    const bool track = est <= double(hy::sstate_cap(G));
-    if (track) {
+    const bool track = !use_hss && est <= double(hy::sstate_cap(G));
+    if (use_hss) {
+        a->ss_clean[d][3] = false;
+        HY_TRY(hy::prog_hss_apply(a->prog, psi, sigma, dt, st));
+    } else if (track) {
         HY_TRY(hy::sstate_reset(G, !a->ss_clean[d][3], false, st));
         a->ss_clean[d][3] = true;
         HY_TRY(hy::sstate_apply_h(S, G, sigma, st));
@@ -235,6 +255,7 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
         a->ss_clean[d][3] = false;
         HY_TRY(hy::sstate_apply_h(S, nullptr, sigma, st));
     }
+    a->sigma_full[d] = !use_hss;
     HY_TRY(hy::sstate_dot(S, sigma, a->d_e, st));
     int64_t cnt[2] = {0, 0};
     a->h_cnt[1] = 0;
@@ -256,6 +277,7 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     }
     if (prog_build && cnt[0] <= kPrepareSmall) {
         HY_TRY(hy::prog_compile(a->prog, S, cnt[0], a->p, a->d_ops, int64_t(L), steps, st));
+        HY_TRY(hy::prog_build_hss(a->prog, S, kHssMaxEntries, st));
         int flag = 1;
         HY_TRY(xfer(a, &flag, hy::prog_flag(a->prog), sizeof(int), cudaMemcpyDeviceToHost, st,
                     "support program check"));
@@ -314,6 +336,7 @@ hy_status energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     }
     if (track) HY_TRY(hy_renormalize(a->h, psi, dt, a->d_n2, st));
     HY_TRY(hy_apply_h(a->h, psi, sigma, dt, st));
+    a->sigma_full[d] = true;
     HY_TRY(hy_energy(a->h, psi, sigma, dt, a->d_e, st));
     HY_TRY(xfer(a, e, a->d_e, sizeof(double), cudaMemcpyDeviceToHost, st, "energy readback"));
     HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
@@ -650,6 +673,13 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
     a->cfg = c;
     hy_status s = hy_ham_info(h, &a->N, nullptr, nullptr, nullptr, nullptr);
     if (s == HY_OK) s = hy_pool_size(p, &a->K);
+    if (s == HY_OK) {
+        a->n_orb = hy::ham_view(h).n;
+        a->p_desc_v.assign(size_t(a->K) * 11, 0);
+        for (int64_t k = 0; k < a->K && s == HY_OK; ++k)
+            s = hy_pool_describe(p, k, a->p_desc_v.data() + 11 * k);
+        a->p_desc = a->p_desc_v.data();
+    }
     auto alloc = [&](void **ptr, size_t bytes) {
         if (s != HY_OK) return;
         s = cu(cudaMalloc(ptr, bytes ? bytes : 8), "cudaMalloc (driver)");
@@ -777,9 +807,12 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     // (float gradients differ from it by ~1e-6 relative, enough to reorder
     // near-equal operators)
     const hy_dtype sdt = a->screen_f64_next ? HY_F64 : bulk;
-    if (a->valid_dt != sdt || a->valid_theta != a->theta) {
+    if (a->valid_dt != sdt || a->valid_theta != a->theta || !a->sigma_full[di(sdt)]) {
         double e;
-        HY_TRY(energy(a, a->theta, sdt, st, &e));
+        a->want_full_sigma = true;           // the screen reads sigma beyond psi's support
+        const hy_status rs = energy(a, a->theta, sdt, st, &e);
+        a->want_full_sigma = false;
+        HY_TRY(rs);
     }
     void *psi = a->buf[di(sdt)][0], *sigma = a->buf[di(sdt)][1];
     rec->support = a->sparse_m;
@@ -873,14 +906,20 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
                                         a->d_extra, a->d_feat, st));
         HY_TRY(hy_ranker_predict(a->ranker, a->d_feat, a->K, a->d_score, st));
         // proposals: the M / 4 operators with the largest Cauchy-Schwarz
-        // gradient bound (feature 10, an upper bound on |g_k|), the M / 4
-        // with the largest stale |g_k|, then the MLP's ranking until M
-        // distinct operators
+        // gradient bound (feature 10, an upper bound on |g_k|), the M / 4 the
+        // MLP ranks highest among those sharing two or more spatial orbitals
+        // with the last appended operator (its rotation moves the gradients
+        // of exactly these the most), the M / 4 with the largest stale |g_k|,
+        // then the MLP's ranking until M distinct operators
         const int64_t Mb = M / 4;
         std::vector<int32_t> by_mlp(M), by_bound(Mb);
+        std::vector<float> score_h(a->ops.empty() ? 0 : size_t(a->K));
         HY_TRY(hy_ranker_topk(a->d_score, a->K, M, a->d_prop, st));
         HY_TRY(xfer(a, by_mlp.data(), a->d_prop, M * 4, cudaMemcpyDeviceToHost, st,
                     "proposals readback"));
+        if (!score_h.empty())
+            HY_TRY(xfer(a, score_h.data(), a->d_score, size_t(a->K) * 4, cudaMemcpyDeviceToHost,
+                        st, "scores readback"));
         if (Mb > 0) {
             HY_TRY(cu(cudaMemcpy2DAsync(a->d_score, sizeof(float), a->d_feat + 10,
                                         16 * sizeof(float), sizeof(float), size_t(a->K),
@@ -904,10 +943,37 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
             });
             by_stale.assign(idx.begin(), idx.begin() + ns);
         }
+        // neighbours of the last append: spatial-orbital masks of each
+        // operator's constituents, two or more orbitals in common
+        std::vector<int32_t> by_near;
+        if (!score_h.empty()) {
+            auto orbs = [&](int64_t k) {
+                const int32_t *dsc = a->p_desc + 11 * k;
+                uint32_t m = 0;
+                for (int c = 0; c < dsc[0]; ++c)
+                    for (int u = 1; u < 5; ++u) {
+                        const int32_t *q = dsc + 1 + 5 * c;
+                        if (q[0] == 1 && (u == 2 || u == 3)) continue;   // a single's unused slots
+                        m |= 1u << (q[u] % a->n_orb);
+                    }
+                return m;
+            };
+            const uint32_t last = orbs(a->ops.back());
+            std::vector<int32_t> idx;
+            for (int64_t k = 0; k < a->K; ++k)
+                if (__builtin_popcount(orbs(k) & last) >= 2) idx.push_back(int32_t(k));
+            const size_t nn = std::min<size_t>(size_t(Mb), idx.size());
+            std::partial_sort(idx.begin(), idx.begin() + nn, idx.end(), [&](int32_t x, int32_t y) {
+                return score_h[x] > score_h[y] || (score_h[x] == score_h[y] && x < y);
+            });
+            by_near.assign(idx.begin(), idx.begin() + nn);
+        }
         std::vector<int32_t> prop;
         std::vector<char> taken(a->K, 0);
         for (int32_t k : by_bound)
             if (!taken[k]) { taken[k] = 1; prop.push_back(k); }
+        for (int32_t k : by_near)
+            if (int64_t(prop.size()) < M && !taken[k]) { taken[k] = 1; prop.push_back(k); }
         for (int32_t k : by_stale)
             if (int64_t(prop.size()) < M && !taken[k]) { taken[k] = 1; prop.push_back(k); }
         for (int32_t k : by_mlp)

@@ -2108,6 +2108,15 @@ struct SupportProgram {
     int32_t *tab_big = nullptr, *idx_map = nullptr;
     void *prep_scratch = nullptr, *grad_scratch = nullptr;
     size_t grad_bytes = 0;
+    // H restricted to the program's support (rows in key order, columns as
+    // determinant indices): valid while hss_ok
+    int64_t *hss_ptr = nullptr;
+    int32_t *hss_cnt = nullptr;
+    uint32_t *hss_col = nullptr;
+    double *hss_val = nullptr;
+    int64_t hss_cap = 0, hss_nnz = 0;
+    bool hss_ok = false;
+    int64_t *h_nnz = nullptr;     // pinned readback slot
 };
 
 hy_status prog_create(const hy_ham *h, int max_steps, SupportProgram **out)
@@ -2144,6 +2153,11 @@ void prog_destroy(SupportProgram *g)
     cudaFree(g->idx_map);
     cudaFree(g->prep_scratch);
     cudaFree(g->grad_scratch);
+    cudaFree(g->hss_ptr);
+    cudaFree(g->hss_cnt);
+    cudaFree(g->hss_col);
+    cudaFree(g->hss_val);
+    if (g->h_nnz) cudaFreeHost(g->h_nnz);
     delete g;
 }
 
@@ -2203,6 +2217,92 @@ hy_status prog_compile(SupportProgram *g, const SparseState *s, int64_t m, const
     }
     g->m = m;
     g->steps = steps;
+    g->hss_ok = false;
+    return HY_OK;
+}
+
+namespace {
+const int64_t *prog_keys(const SupportProgram *g)
+{
+    return g->m > hy::k::kProgMax ? g->key_big : g->key;
+}
+}  // namespace
+
+hy_status prog_build_hss(SupportProgram *g, const SparseState *s, int64_t max_nnz, void *stream)
+{
+    if (!g || !s || s->h != g->h || g->m < 1) return fail(HY_ERR_ARG, "bad arguments");
+    const hy_ham *h = g->h;
+    cudaStream_t st = as_stream(stream);
+    g->hss_ok = false;
+    cudaError_t e = cudaSuccess;
+    const size_t kb = size_t(hy::k::kProgBig);
+    if (!g->hss_ptr) e = cudaMalloc(&g->hss_ptr, (kb + 1) * sizeof(int64_t));
+    if (e == cudaSuccess && !g->hss_cnt) e = cudaMalloc(&g->hss_cnt, kb * sizeof(int32_t));
+    if (e == cudaSuccess && !g->h_nnz) e = cudaMallocHost(&g->h_nnz, sizeof(int64_t));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(support Hamiltonian)");
+    hy::k::HssArgs a;
+    a.key = prog_keys(g);
+    a.m = g->m;
+    a.bits = s->bits;
+    a.Ma_ptr = h->Ma64.ptr; a.Ma_col = h->Ma64.col; a.Ma_val = h->Ma64.val;
+    a.Mb_ptr = h->Mb64.ptr; a.Mb_col = h->Mb64.col; a.Mb_val = h->Mb64.val;
+    a.V = h->d_V64;
+    a.aex = h->d_aex; a.bexT = h->d_bexT; a.astr = h->d_astr; a.bstr = h->d_bstr;
+    a.n = h->n; a.nexa = h->A.nex; a.nexb = h->B.nex; a.Nb = h->Nb;
+    a.ptr = g->hss_ptr; a.cnt = g->hss_cnt; a.col = nullptr; a.val = nullptr;
+    hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
+    HY_CUDA(hy::k::hss_count(a, h->num_sms, st), "support Hamiltonian count");
+    HY_CUDA(cudaMemcpyAsync(g->h_nnz, g->hss_ptr + g->m, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            st), "support Hamiltonian size");
+    HY_CUDA(cudaStreamSynchronize(st), "sync");
+    const int64_t nnz = *g->h_nnz;
+    if (nnz > max_nnz) return HY_OK;              // too large to pay off: not built
+    if (nnz > g->hss_cap) {
+        cudaFree(g->hss_col);
+        cudaFree(g->hss_val);
+        g->hss_col = nullptr;
+        g->hss_val = nullptr;
+        g->hss_cap = 0;
+        const int64_t cap = nnz + nnz / 4 + 1024;
+        e = cudaMalloc(&g->hss_col, size_t(cap) * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&g->hss_val, size_t(cap) * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(g->hss_col);
+            g->hss_col = nullptr;
+            return HY_OK;                         // no room: the scatter serves
+        }
+        g->hss_cap = cap;
+    }
+    a.col = g->hss_col;
+    a.val = g->hss_val;
+    HY_CUDA(hy::k::hss_fill(a, h->num_sms, st), "support Hamiltonian fill");
+    g->hss_nnz = nnz;
+    g->hss_ok = true;
+    return HY_OK;
+}
+
+bool prog_hss_ready(const SupportProgram *g) { return g && g->hss_ok; }
+
+hy_status prog_hss_apply(const SupportProgram *g, const void *psi, void *sigma, hy_dtype dt,
+                         void *stream)
+{
+    if (!g || !g->hss_ok || !psi || !sigma) return fail(HY_ERR_ARG, "bad arguments");
+    cudaStream_t st = as_stream(stream);
+    const double es = dt == HY_F64 ? 8.0 : 4.0;
+    hy::ProfScope prof(HY_PROF_HPSI_SPARSE, stream,
+                       double(g->hss_nnz) * 12.0 + 2.0 * double(g->m) * es,
+                       2.0 * double(g->hss_nnz));
+    if (dt == HY_F64)
+        HY_CUDA(hy::k::hss_apply<double>(prog_keys(g), g->m, g->hss_ptr, g->hss_col, g->hss_val,
+                                         static_cast<const double *>(psi),
+                                         static_cast<double *>(sigma), g->h->num_sms, st),
+                "support Hamiltonian apply");
+    else
+        HY_CUDA(hy::k::hss_apply<float>(prog_keys(g), g->m, g->hss_ptr, g->hss_col, g->hss_val,
+                                        static_cast<const float *>(psi),
+                                        static_cast<float *>(sigma), g->h->num_sms, st),
+                "support Hamiltonian apply");
     return HY_OK;
 }
 

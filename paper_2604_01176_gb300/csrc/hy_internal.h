@@ -177,6 +177,14 @@ const int *prog_flag(const SupportProgram *g);        // device, set by prog_com
 int64_t prog_steps(const hy_pool *p, const int32_t *ops_host, int64_t L);
 // the largest support a program holds
 int64_t prog_capacity();
+// H restricted to the program's support, built from s (which lists exactly
+// that support, as after prog_compile): skipped (left unbuilt) when it would
+// hold more than max_nnz entries or its memory cannot be had.  prog_hss_apply
+// writes sigma = H psi on the support only (the rest of sigma untouched).
+hy_status prog_build_hss(SupportProgram *g, const SparseState *s, int64_t max_nnz, void *stream);
+bool prog_hss_ready(const SupportProgram *g);
+hy_status prog_hss_apply(const SupportProgram *g, const void *psi, void *sigma, hy_dtype dt,
+                         void *stream);
 // compile from s (whose support, m <= prog_capacity() elements, was just
 // listed by a structural sstate_prepare of ops[0..L) (device) with step_len)
 hy_status prog_compile(SupportProgram *g, const SparseState *s, int64_t m, const hy_pool *p,

@@ -377,6 +377,35 @@ template <typename T>
 cudaError_t prog_grad_big(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
                           const int32_t *ops, const double *cs, int L, const T *sigma,
                           const double *norm2, double *g, T *scratch, cudaStream_t st);
+// The Hamiltonian restricted to a support S (both rows and columns in S):
+// row t is the determinant key[t] >> 8 of a support program, its entries
+// the couplings to determinants of S (membership bitmap `bits`), columns
+// stored as determinant indices.  The energy of a state on S and the
+// forward gradients read sigma only on S, so within one ansatz H_SS psi
+// serves every evaluation.  hss_count: row lengths into cnt[0..m) and their
+// exclusive prefix into ptr[0..m]; hss_fill: the entries (same enumeration,
+// fixed order); hss_apply: sigma[key[t] >> 8] = sum_e val[e] psi[col[e]]
+// for t < m, accumulated in T (sigma untouched elsewhere).
+struct HssArgs {
+    const int64_t *key;
+    int64_t m;
+    const uint32_t *bits;
+    const int32_t *Ma_ptr, *Ma_col, *Mb_ptr, *Mb_col;
+    const double *Ma_val, *Mb_val, *V;
+    const uint32_t *aex, *bexT, *astr, *bstr;
+    int n, nexa, nexb;
+    int64_t Nb;
+    int64_t *ptr;            // [m + 1]
+    int32_t *cnt;            // [m]
+    uint32_t *col;           // [nnz]
+    double *val;             // [nnz]
+};
+cudaError_t hss_count(const HssArgs &a, int num_sms, cudaStream_t st);
+cudaError_t hss_fill(const HssArgs &a, int num_sms, cudaStream_t st);
+template <typename T>
+cudaError_t hss_apply(const int64_t *key, int64_t m, const int64_t *ptr, const uint32_t *col,
+                      const double *val, const T *psi, T *sigma, int num_sms, cudaStream_t st);
+
 // one CTA: g[l] = dE/dtheta_l of psi = U_L .. U_1|HF> in forward mode, f and
 // w scratch sparse vectors (clean), sigma = H psi dense; norm2 (device, or
 // null): psi was divided by sqrt(*norm2), so the gradient is too

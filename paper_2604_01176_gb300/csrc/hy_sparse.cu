@@ -1063,6 +1063,228 @@ k_prog_grad_big(const int64_t *__restrict__ key, const int32_t *__restrict__ tab
     if (threadIdx.x == 0) g[lg] = (norm2 ? 2.0 / sqrt(*norm2) : 2.0) * dot;
 }
 
+// ---------------------------------------------------------------------------
+// H restricted to a support (see HssArgs).  Row t enumerates the couplings of
+// its determinant d = (A, B) exactly as k_hpsi_scatter enumerates the targets
+// of d (H is real symmetric, so the column of d is its row), keeping those
+// whose determinant is in the support.  The enumeration is the same in the
+// counting and the filling pass and, per thread, in a fixed order; a block
+// scan of the per-thread counts places each thread's entries.
+// ---------------------------------------------------------------------------
+template <typename F>
+__device__ __forceinline__ void hss_enumerate(const HssArgs &a, int64_t A, int64_t B,
+                                              const uint32_t *aexs, F &&take)
+{
+    const int n = a.n, nn = n * n, nexa = a.nexa, nexb = a.nexb;
+    const int64_t Nb = a.Nb;
+    const int P = nexb > 0 ? int(blockDim.x) / nexb : 0;
+    const bool slot = int(threadIdx.x) < P * nexb;
+    const int fs = slot ? int(threadIdx.x) % nexb : 0, ph = slot ? int(threadIdx.x) / nexb : 0;
+    for (int k = a.Ma_ptr[A] + threadIdx.x; k < a.Ma_ptr[A + 1]; k += blockDim.x)
+        take(int64_t(a.Ma_col[k]) * Nb + B, a.Ma_val[k]);
+    for (int k = a.Mb_ptr[B] + threadIdx.x; k < a.Mb_ptr[B + 1]; k += blockDim.x)
+        take(A * Nb + a.Mb_col[k], a.Mb_val[k]);
+    const uint32_t am = a.astr[A], bm = a.bstr[B];
+    if (slot) {
+        const uint32_t w = a.bexT[size_t(fs) * Nb + B];
+        const int64_t Bo = w & 0xFFFFu;
+        const int rs = int((w >> 20) & 15) * n + int((w >> 16) & 15);
+        const bool negb = (w >> 31) != 0;
+        if (ph == 0) {
+            const double c = sum_diag<double>(a.V, n, nn, am, rs);
+            take(A * Nb + Bo, negb ? -c : c);
+        }
+        const double *Vrs = a.V + rs;
+        for (int e = ph; e < nexa; e += P) {
+            const uint32_t u = aexs[e];
+            const int64_t Ao = u & 0xFFFFu;
+            const int pq = int((u >> 20) & 15) * n + int((u >> 16) & 15);
+            const double c = Vrs[size_t(pq) * nn];
+            take(Ao * Nb + Bo, negb != ((u >> 31) != 0) ? -c : c);
+        }
+    }
+    for (int e = int(threadIdx.x) - 1; e < nexa; e += blockDim.x) {
+        double c = 0.0;
+        if (e < 0) {
+            for (uint32_t mm = bm; mm; mm &= mm - 1) {
+                const int rr = __ffs(mm) - 1;
+                c += sum_diag<double>(a.V, n, nn, am, rr * n + rr);
+            }
+            take(A * Nb + B, c);
+        } else {
+            const uint32_t u = aexs[e];
+            const int pq = int((u >> 20) & 15) * n + int((u >> 16) & 15);
+            for (uint32_t mm = bm; mm; mm &= mm - 1) {
+                const int rr = __ffs(mm) - 1;
+                c += a.V[size_t(pq) * nn + rr * n + rr];
+            }
+            take(int64_t(u & 0xFFFFu) * Nb + B, (u >> 31) ? -c : c);
+        }
+    }
+}
+
+// exclusive prefix of v over the block (256 threads), total in *tot
+__device__ __forceinline__ int block_excl_scan(int v, int *warp_tot, int *tot)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int i = 0; i < int(blockDim.x >> 5); ++i) {
+            const int t = warp_tot[i];
+            warp_tot[i] = acc;
+            acc += t;
+        }
+        *tot = acc;
+    }
+    __syncthreads();
+    return warp_tot[w] + x - v;
+}
+
+__global__ void __launch_bounds__(256)
+k_hss_count(HssArgs a)
+{
+    __shared__ uint32_t aexs[64];
+    __shared__ int wt[8], tot;
+    for (int64_t t = blockIdx.x; t < a.m; t += gridDim.x) {
+        const int64_t d = a.key[t] >> 8;
+        const int64_t A = d / a.Nb, B = d % a.Nb;
+        __syncthreads();
+        if (int(threadIdx.x) < a.nexa) aexs[threadIdx.x] = a.aex[A * a.nexa + threadIdx.x];
+        __syncthreads();
+        int c = 0;
+        hss_enumerate(a, A, B, aexs, [&](int64_t o, double) {
+            if (member(a.bits, o)) ++c;
+        });
+        block_excl_scan(c, wt, &tot);
+        if (threadIdx.x == 0) a.cnt[t] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_hss_fill(HssArgs a)
+{
+    __shared__ uint32_t aexs[64];
+    __shared__ int wt[8], tot;
+    for (int64_t t = blockIdx.x; t < a.m; t += gridDim.x) {
+        const int64_t d = a.key[t] >> 8;
+        const int64_t A = d / a.Nb, B = d % a.Nb;
+        __syncthreads();
+        if (int(threadIdx.x) < a.nexa) aexs[threadIdx.x] = a.aex[A * a.nexa + threadIdx.x];
+        __syncthreads();
+        int c = 0;
+        hss_enumerate(a, A, B, aexs, [&](int64_t o, double) {
+            if (member(a.bits, o)) ++c;
+        });
+        int64_t pos = a.ptr[t] + block_excl_scan(c, wt, &tot);
+        hss_enumerate(a, A, B, aexs, [&](int64_t o, double v) {
+            if (member(a.bits, o)) {
+                a.col[pos] = uint32_t(o);
+                a.val[pos] = v;
+                ++pos;
+            }
+        });
+    }
+}
+
+// ptr[0] = 0, ptr[t + 1] = ptr[t] + cnt[t]: one block, chunks of 1024
+__global__ void __launch_bounds__(1024)
+k_hss_scan(const int32_t *__restrict__ cnt, int64_t m, int64_t *__restrict__ ptr)
+{
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        ptr[0] = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t base = 0; base < m; base += blockDim.x) {
+        const int64_t t = base + threadIdx.x;
+        int64_t x = t < m ? cnt[t] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t acc = 0;
+            for (int i = 0; i < int(blockDim.x >> 5); ++i) {
+                const int64_t v = wsum[i];
+                wsum[i] = acc;
+                acc += v;
+            }
+        }
+        __syncthreads();
+        if (t < m) ptr[t + 1] = carry + wsum[w] + x;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += wsum[w] + x;
+        __syncthreads();
+    }
+}
+
+// one warp per row: sigma[key[t] >> 8] = sum val * psi[col], lanes strided,
+// a fixed-order warp sum
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_hss_apply(const int64_t *__restrict__ key, int64_t m, const int64_t *__restrict__ ptr,
+            const uint32_t *__restrict__ col, const double *__restrict__ val,
+            const T *__restrict__ psi, T *__restrict__ sigma)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t t = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); t < m;
+         t += warps) {
+        T acc = T(0);
+        for (int64_t e = ptr[t] + lane; e < ptr[t + 1]; e += 32)
+            acc += T(val[e]) * psi[col[e]];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) sigma[key[t] >> 8] = acc;
+    }
+}
+
+cudaError_t hss_count(const HssArgs &a, int num_sms, cudaStream_t st)
+{
+    if (a.m < 1) return cudaSuccess;
+    int64_t g = a.m < int64_t(num_sms) * 16 ? a.m : int64_t(num_sms) * 16;
+    k_hss_count<<<unsigned(g), 256, 0, st>>>(a); hy::count_launch();
+    k_hss_scan<<<1, 1024, 0, st>>>(a.cnt, a.m, a.ptr); hy::count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t hss_fill(const HssArgs &a, int num_sms, cudaStream_t st)
+{
+    if (a.m < 1) return cudaSuccess;
+    int64_t g = a.m < int64_t(num_sms) * 16 ? a.m : int64_t(num_sms) * 16;
+    k_hss_fill<<<unsigned(g), 256, 0, st>>>(a); hy::count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t hss_apply(const int64_t *key, int64_t m, const int64_t *ptr, const uint32_t *col,
+                      const double *val, const T *psi, T *sigma, int num_sms, cudaStream_t st)
+{
+    if (m < 1) return cudaSuccess;
+    int64_t g = (m + 7) / 8;
+    if (g > int64_t(num_sms) * 16) g = int64_t(num_sms) * 16;
+    k_hss_apply<T><<<unsigned(g), 256, 0, st>>>(key, m, ptr, col, val, psi, sigma);
+    hy::count_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t hss_apply<double>(const int64_t *, int64_t, const int64_t *,
+                                       const uint32_t *, const double *, const double *,
+                                       double *, int, cudaStream_t);
+template cudaError_t hss_apply<float>(const int64_t *, int64_t, const int64_t *, const uint32_t *,
+                                      const double *, const float *, float *, int, cudaStream_t);
+
 namespace {
 // blocks for a list of about n entries (grid-stride loops cover any count)
 unsigned sv_grid(int64_t n, int num_sms)
