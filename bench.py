@@ -999,8 +999,9 @@ def main():
                             "double-precision refinement; the Hamiltonian resident"),
                    "mode": (f"mixed precision, ranker attached (top-{args.top_m} proposals when "
                             "consulted); psi a sparse vector while its support fits N/32 (float) "
-                            "or N/8 (double); the whole pool screened exactly while pool x "
-                            "support <= 5e9"),
+                            "or N/8 (double); float optimisation from 2^20 nonzero amplitudes, "
+                            "double below (every iteration of this job); the whole pool screened "
+                            "exactly while pool x support <= 5e9"),
                    "pool_ops": r["K"], "replicas": world,
                    "l2": "inputs larger than L2 (state vector 0.66 GB FP32 / 1.33 GB FP64)"},
         "mixed": {"iterations_timed": iters_timed,

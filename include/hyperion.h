@@ -647,7 +647,9 @@ hy_status hy_adapt_set_ranker(hy_adapt *a, hy_ranker *r, int warm_iters,
  *   the selection is the one plain FP64 makes; float gradients, ~1e-6
  *   relative off, can reorder near-equal operators).  Other iterations
  *   record the float-bulk energy (reduced in double) and
- *   energy_bulk_err = -1. */
+ *   energy_bulk_err = -1.  Iterations whose state has fewer nonzero
+ *   amplitudes than float_from / 4 optimise in double directly (energy =
+ *   energy_bulk in double, energy_bulk_err = 0). */
 typedef struct {
     hy_dtype bulk;        /* HY_F64 or HY_F32                                  */
     int max_iter;         /* capacity of the ansatz (iterations)               */
@@ -691,7 +693,18 @@ typedef struct {
                              pool exactly while (pool size) x (support) is at
                              most this; 0: 5e9 (the cost of the ranker's
                              feature pass at 32 qubits); < 0: never (always
-                             ask the ranker, e.g. to judge it)               */
+                             ask the ranker, e.g. to judge it).  The exact
+                             screens feed the ranker training pairs once
+                             (pool size) x (support) exceeds 1/64 of this
+                             (dense path: always)                            */
+    int64_t float_from;   /* HY_F32 bulk: an iteration whose state has fewer
+                             than float_from / 4 nonzero amplitudes at its
+                             screen (its support on the sparse path, every
+                             determinant on the dense sweeps) optimises in
+                             double directly (no refinement needed); there
+                             the evaluations are latency-bound and cost the
+                             same in either precision.  0: 2^20; 1: always
+                             float                                           */
 } hy_adapt_config;
 
 /* One ADAPT iteration (all times in seconds, host wall clock). */

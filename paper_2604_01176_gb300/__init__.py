@@ -468,7 +468,7 @@ class Adapt:
     def __init__(self, ham: Hamiltonian, pool: Pool, precision="f64", max_iter=64,
                  eps_grad=1e-5, gtol=1e-9, gtol_bulk=1e-5, max_evals=200,
                  refine_steps=4, refine_every=1, screen_top_m=0, judge=False, sparse=False,
-                 sparse_cap=0, exact_screen_work=0.0):
+                 sparse_cap=0, exact_screen_work=0.0, float_from=0):
         lib = _abi.load()
         self.ham, self.pool = ham, pool
         if precision not in ("f64", "mixed"):
@@ -477,7 +477,7 @@ class Adapt:
                                float(eps_grad), float(gtol), float(gtol_bulk),
                                int(max_evals), int(refine_steps), int(refine_every),
                                int(screen_top_m), 1 if judge else 0, 1 if sparse else 0,
-                               int(sparse_cap), float(exact_screen_work))
+                               int(sparse_cap), float(exact_screen_work), int(float_from))
         handle = ctypes.c_void_p()
         check(lib.hy_adapt_create(ham.handle, pool.handle, ctypes.byref(cfg),
                                   ctypes.byref(handle)))

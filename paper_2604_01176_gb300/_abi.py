@@ -45,7 +45,8 @@ class AdaptConfig(ctypes.Structure):
                 ("refine_steps", ctypes.c_int), ("refine_every", ctypes.c_int),
                 ("screen_top_m", ctypes.c_int),
                 ("judge", ctypes.c_int), ("sparse", ctypes.c_int),
-                ("sparse_cap", ctypes.c_int64), ("exact_screen_work", ctypes.c_double)]
+                ("sparse_cap", ctypes.c_int64), ("exact_screen_work", ctypes.c_double),
+                ("float_from", ctypes.c_int64)]
 
 
 class AdaptRecord(ctypes.Structure):

@@ -526,6 +526,12 @@ const double kStall64 = std::ldexp(1.0, -50);
 // replaces the ranker's proposals (~10 ms on a GB300, the cost of the
 // ranker's feature pass at 32 qubits)
 const double kExactScreenWork = 5e9;
+const double kCollectFactor = 64.0;
+// the mixed-precision driver optimises in float from this many nonzero
+// amplitudes on; below it an evaluation is latency-bound and costs the same
+// in either precision, so it optimises in double directly and needs no
+// refinement
+const int64_t kFloatFrom = int64_t(1) << 20;
 
 // cost of one atomic add of the list-based touched weights in amplitudes of
 // the dense pass (the rule that picks sigma's list).  Measured at 32 qubits
@@ -661,10 +667,12 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
         c.sparse = 0;
         c.sparse_cap = 0;
         c.exact_screen_work = 0.0;
+        c.float_from = 0;
     }
     if ((c.bulk != HY_F64 && c.bulk != HY_F32) || c.max_iter < 1 || c.max_iter > (1 << 20) ||
         !(c.eps_grad >= 0) || !(c.gtol > 0) || !(c.gtol_bulk > 0) || c.max_evals < 1 ||
-        c.refine_steps < 0 || c.refine_every < 0 || c.screen_top_m < 0 || c.sparse_cap < 0)
+        c.refine_steps < 0 || c.refine_every < 0 || c.screen_top_m < 0 || c.sparse_cap < 0 ||
+        c.float_from < 0)
         return set_err(HY_ERR_ARG, "invalid hy_adapt_config");
     hy_adapt *a = new (std::nothrow) hy_adapt;
     if (!a) return set_err(HY_ERR_OOM, "host allocation failed");
@@ -845,7 +853,21 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
                              double(a->sparse_m) * double(a->K) <=
                                  (a->cfg.exact_screen_work == 0.0 ? kExactScreenWork
                                                                   : a->cfg.exact_screen_work);
-    const bool use_ranker = ranked && post >= 0 && !refresh && !cheap_exact;
+    const double exact_work = a->cfg.exact_screen_work == 0.0 ? kExactScreenWork
+                                                               : a->cfg.exact_screen_work;
+    int64_t n_samples = 0;
+    if (ranked) HY_TRY(hy_ranker_info(a->ranker, nullptr, &n_samples, nullptr, nullptr));
+    // a ranker with nothing to learn from is not asked
+    const bool use_ranker = ranked && post >= 0 && !refresh && !cheap_exact &&
+                            (n_samples > 0 || a->fitted_once);
+    // exact screens feed the ranker once the work of the exact screen comes
+    // within kCollectFactor of the point where the ranker takes over (about
+    // three iterations of support growth ahead; earlier samples would only be
+    // collected, never used, and the feature pass is the costliest part of an
+    // iteration with a small support)
+    const bool collect = ranked && (a->sparse_m < 0 || exact_work < 0.0 ||
+                                    double(a->sparse_m) * double(a->K) * kCollectFactor >
+                                        exact_work);
     std::vector<double> g;
     std::vector<int64_t> cand;   // screened operators, in proposal order
     int64_t sel = -1;
@@ -881,7 +903,7 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     if (!use_ranker) {
         HY_TRY(full_screen());
         pick(all, g);
-        if (ranked) {
+        if (collect) {
             HY_TRY(hy::ranker_features_impl(a->h, a->p, psi, psi_list, sigma, sigma_list, sdt,
                                             a->d_extra, a->d_feat, st));
             HY_TRY(hy_ranker_add_samples(a->ranker, a->d_feat, a->d_g, a->K, st));
@@ -1046,6 +1068,15 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.max_evals, st, &e, kStall64));
         rec->energy = rec->energy_bulk = e;
         rec->energy_bulk_err = 0.0;
+    } else if ((a->sparse_m >= 0 ? a->sparse_m : a->N) * 4 <
+               (a->cfg.float_from > 0 ? a->cfg.float_from : kFloatFrom)) {
+        // few nonzero amplitudes (the support on the sparse path, every
+        // determinant on the dense sweeps; the new operator at most
+        // quadruples the support): double directly
+        HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.max_evals, st, &e, kStall64));
+        rec->energy = rec->energy_bulk = e;
+        rec->energy_bulk_err = 0.0;
+        a->screen_f64_next = true;
     } else {
         double e32 = 0.0, e64 = 0.0;
         // float phase; 2^-22 |E| is a few float roundings of the energy

@@ -2101,13 +2101,11 @@ struct SupportProgram {
     int64_t *key = nullptr, *step_len = nullptr;
     int32_t *tab = nullptr;
     int *flag = nullptr;
-    // supports beyond shared memory (allocated on first use): keys in
-    // listing order, tables, the index map over Omega_CIk and the vectors'
-    // global scratch (prepare: one vector; gradient: two per angle)
+    // supports beyond one CTA's shared memory (allocated on first use): keys
+    // in listing order, tables and the index map over Omega_CIk (the vectors
+    // live in the shared memory of a cluster of CTAs)
     int64_t *key_big = nullptr;
     int32_t *tab_big = nullptr, *idx_map = nullptr;
-    void *prep_scratch = nullptr, *grad_scratch = nullptr;
-    size_t grad_bytes = 0;
     // H restricted to the program's support (rows in key order, columns as
     // determinant indices): valid while hss_ok
     int64_t *hss_ptr = nullptr;
@@ -2151,8 +2149,6 @@ void prog_destroy(SupportProgram *g)
     cudaFree(g->key_big);
     cudaFree(g->tab_big);
     cudaFree(g->idx_map);
-    cudaFree(g->prep_scratch);
-    cudaFree(g->grad_scratch);
     cudaFree(g->hss_ptr);
     cudaFree(g->hss_cnt);
     cudaFree(g->hss_col);
@@ -2208,7 +2204,6 @@ hy_status prog_compile(SupportProgram *g, const SparseState *s, int64_t m, const
             e = cudaMalloc(&g->tab_big, size_t(g->max_steps) * kb * sizeof(int32_t));
         if (e == cudaSuccess && !g->idx_map)
             e = cudaMalloc(&g->idx_map, size_t(g->h->N) * sizeof(int32_t));
-        if (e == cudaSuccess && !g->prep_scratch) e = cudaMalloc(&g->prep_scratch, kb * sizeof(double));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(support program)");
         HY_CUDA(hy::k::prog_compile_big(s->list, m, g->step_len, int(steps), sv_op_args(g->h, p),
                                         ops, int(L), s->bits, g->key_big, g->tab_big, g->idx_map,
@@ -2318,14 +2313,12 @@ hy_status prog_prepare(const SupportProgram *g, SparseState *s, const hy_pool *p
         if (s->dt == HY_F64)
             HY_CUDA(hy::k::prog_prepare_big<double>(g->key_big, g->tab_big, g->m, p->d_desc, ops,
                                                     cs, int(L), renorm, norm2,
-                                                    static_cast<double *>(s->v),
-                                                    static_cast<double *>(g->prep_scratch), st),
+                                                    static_cast<double *>(s->v), st),
                     "support program preparation");
         else
             HY_CUDA(hy::k::prog_prepare_big<float>(g->key_big, g->tab_big, g->m, p->d_desc, ops,
                                                    cs, int(L), renorm, norm2,
-                                                   static_cast<float *>(s->v),
-                                                   static_cast<float *>(g->prep_scratch), st),
+                                                   static_cast<float *>(s->v), st),
                     "support program preparation");
         return HY_OK;
     }
@@ -2350,26 +2343,15 @@ hy_status prog_grad(const SupportProgram *g, const hy_pool *p, const int32_t *op
     cudaStream_t st = as_stream(stream);
     hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
     if (g->m > hy::k::kProgMax) {
-        SupportProgram *gm = const_cast<SupportProgram *>(g);
-        const size_t need = size_t(L) * 2 * size_t(g->m) * (dt == HY_F64 ? 8 : 4);
-        if (need > gm->grad_bytes) {
-            cudaFree(gm->grad_scratch);
-            gm->grad_scratch = nullptr;
-            gm->grad_bytes = 0;
-            const cudaError_t e = cudaMalloc(&gm->grad_scratch, need);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(support program gradient)");
-            gm->grad_bytes = need;
-        }
         if (dt == HY_F64)
             HY_CUDA(hy::k::prog_grad_big<double>(g->key_big, g->tab_big, g->m, p->d_desc, ops, cs,
                                                  int(L), static_cast<const double *>(sigma), norm2,
-                                                 g_out, static_cast<double *>(gm->grad_scratch),
-                                                 st),
+                                                 g_out, st),
                     "support program gradient");
         else
             HY_CUDA(hy::k::prog_grad_big<float>(g->key_big, g->tab_big, g->m, p->d_desc, ops, cs,
                                                 int(L), static_cast<const float *>(sigma), norm2,
-                                                g_out, static_cast<float *>(gm->grad_scratch), st),
+                                                g_out, st),
                     "support program gradient");
         return HY_OK;
     }

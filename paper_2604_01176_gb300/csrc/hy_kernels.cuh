@@ -359,11 +359,12 @@ template <typename T>
 cudaError_t prog_grad(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
                       const int32_t *ops, const double *cs, int L, const T *sigma,
                       const double *norm2, double *g, cudaStream_t st);
-// Support programs beyond shared memory, kProgMax < m <= kProgBig: the
-// support in listing order (key unsorted), local indices through idx_map
+// Support programs beyond one CTA's shared memory, kProgMax < m <= kProgBig:
+// the support in listing order (key unsorted), local indices through idx_map
 // (N int32 over Omega_CIk, read where `bits`, the listing's membership
-// bitmap, has the determinant), vectors in global scratch (prepare: m
-// elements; gradient: 2 m per angle)
+// bitmap, has the determinant), each vector split over the distributed shared
+// memory of a cluster of 8 CTAs (prepare: one cluster; gradient: one cluster
+// per angle)
 constexpr int64_t kProgBig = 65536;
 cudaError_t prog_compile_big(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
                              const SvOpArgs &o, const int32_t *ops, int L, const uint32_t *bits,
@@ -372,11 +373,11 @@ cudaError_t prog_compile_big(const int64_t *list, int64_t m, const int64_t *step
 template <typename T>
 cudaError_t prog_prepare_big(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
                              const int32_t *ops, const double *cs, int L, bool renorm,
-                             double *norm2, T *v, T *scratch, cudaStream_t st);
+                             double *norm2, T *v, cudaStream_t st);
 template <typename T>
 cudaError_t prog_grad_big(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
                           const int32_t *ops, const double *cs, int L, const T *sigma,
-                          const double *norm2, double *g, T *scratch, cudaStream_t st);
+                          const double *norm2, double *g, cudaStream_t st);
 // The Hamiltonian restricted to a support S (both rows and columns in S):
 // row t is the determinant key[t] >> 8 of a support program, its entries
 // the couplings to determinants of S (membership bitmap `bits`), columns

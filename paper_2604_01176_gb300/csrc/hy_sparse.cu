@@ -14,7 +14,11 @@
 //     partner with the binomial table.
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "hy_kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hy {
 namespace k {
@@ -992,75 +996,171 @@ k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
     }
 }
 
-// one CTA: as k_prog_prepare with the vector in global scratch x[0..m)
+// Vectors of 12,289..65,536 support elements: a thread-block cluster of
+// kClusterCtas CTAs holds one vector (or, for the gradient, the two vectors
+// of one angle) split over the CTAs' shared memories, chunk elements each;
+// element t lives in CTA t / chunk and is reached through distributed shared
+// memory when it is another CTA's.  A rotation step lets every CTA rotate the
+// pairs whose domain end it holds (an image end has no forward image, so each
+// pair has one writer) and ends with a cluster barrier.
+constexpr int kClusterCtas = 8;
+
 template <typename T>
-__global__ void __launch_bounds__(1024)
+struct ClusterVec {
+    T *loc;
+    int chunk, rank;
+    __device__ __forceinline__ T *at(cg::cluster_group &cl, int t) const
+    {
+        const int r = t / chunk;
+        return r == rank ? loc + (t - r * chunk) : cl.map_shared_rank(loc, r) + (t - r * chunk);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ void cl_rotate(cg::cluster_group &cl, const ClusterVec<T> &x,
+                                          const int32_t *__restrict__ row, int m, T c, T sn)
+{
+    const int t0 = x.rank * x.chunk, t1 = min(m, t0 + x.chunk);
+    for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x) {
+        const int e = row[t];
+        if (e == 0) continue;
+        const int p = (e > 0 ? e : -e) - 1;
+        const T ss = e > 0 ? sn : -sn;
+        T *xt = x.loc + (t - t0);
+        T *xp = x.at(cl, p);
+        const T xv = *xt, yv = *xp;
+        *xt = c * xv - ss * yv;
+        *xp = c * yv + ss * xv;
+    }
+    cl.sync();
+}
+
+// w <- w + (C - C^dagger) f for one constituent (see prog_generator)
+template <typename T>
+__device__ __forceinline__ void cl_generator(cg::cluster_group &cl, const ClusterVec<T> &f,
+                                             const ClusterVec<T> &w,
+                                             const int32_t *__restrict__ row, int m)
+{
+    const int t0 = f.rank * f.chunk, t1 = min(m, t0 + f.chunk);
+    for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x) {
+        const int e = row[t];
+        if (e == 0) continue;
+        const int p = (e > 0 ? e : -e) - 1;
+        const T ft = f.loc[t - t0], fp = *f.at(cl, p);
+        T *wp = w.at(cl, p), *wt = w.loc + (t - t0);
+        if (e > 0) {
+            *wp += ft;
+            *wt -= fp;
+        } else {
+            *wp -= ft;
+            *wt += fp;
+        }
+    }
+    cl.sync();
+}
+
+// FP64 sum over the cluster (each CTA's block sum, then the CTAs' sums in
+// rank order); valid in thread 0 of every CTA.  red: 40 doubles of shared
+// memory (32 per-warp slots, 8 per-CTA slots used on rank 0)
+__device__ __forceinline__ double cl_sum(cg::cluster_group &cl, double acc, double *red, int rank)
+{
+    const double s = prog_block_sum(acc, red);
+    if (threadIdx.x == 0) cl.map_shared_rank(red + 32, 0)[rank] = s;
+    cl.sync();
+    double tot = 0.0;
+    if (threadIdx.x == 0) {
+        const double *slot = cl.map_shared_rank(red + 32, 0);
+        for (int r = 0; r < kClusterCtas; ++r) tot += slot[r];
+    }
+    return tot;
+}
+
+// one cluster: as k_prog_prepare, the vector over the cluster's CTAs
+template <typename T>
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024)
 k_prog_prepare_big(const int64_t *__restrict__ key, const int32_t *__restrict__ tab, int m,
                    const int32_t *__restrict__ desc, const int32_t *__restrict__ ops,
                    const double *__restrict__ cs, int L, int renorm, double *__restrict__ norm2,
-                   T *__restrict__ v, T *__restrict__ x)
+                   T *__restrict__ v)
 {
-    __shared__ double red[32];
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char clsm[];
+    __shared__ double red[40];
     __shared__ double fac;
-    for (int t = threadIdx.x; t < m; t += blockDim.x) x[t] = t == 0 ? T(1) : T(0);   // |HF>
-    __syncthreads();
+    const int rank = int(cl.block_rank());
+    const int chunk = (m + kClusterCtas - 1) / kClusterCtas;
+    const ClusterVec<T> x{reinterpret_cast<T *>(clsm), chunk, rank};
+    const int t0 = rank * chunk, t1 = min(m, t0 + chunk);
+    for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x) x.loc[t - t0] = t == 0 ? T(1) : T(0);
+    cl.sync();                                       // every CTA of the cluster is running
     int s = 0;
     for (int l = 0; l < L; ++l) {
         const int nc = desc[11 * ops[l]];
         const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
-        for (int ci = 0; ci < nc; ++ci, ++s) prog_rotate(x, tab + int64_t(s) * m, m, c, sn);
+        for (int ci = 0; ci < nc; ++ci, ++s) cl_rotate(cl, x, tab + int64_t(s) * m, m, c, sn);
     }
+    T f = T(1);
     if (renorm) {
         double acc = 0.0;
-        for (int t = threadIdx.x; t < m; t += blockDim.x) acc = fma(double(x[t]), double(x[t]), acc);
-        const double sum = prog_block_sum(acc, red);
+        for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x) {
+            const double xv = double(x.loc[t - t0]);
+            acc = fma(xv, xv, acc);
+        }
+        const double tot = cl_sum(cl, acc, red, rank);
         if (threadIdx.x == 0) {
-            if (norm2) *norm2 = sum;
-            fac = 1.0 / sqrt(sum);
+            if (rank == 0 && norm2) *norm2 = tot;
+            fac = 1.0 / sqrt(tot);
         }
         __syncthreads();
-        const T f = T(fac);
-        for (int t = threadIdx.x; t < m; t += blockDim.x) v[key[t] >> 8] = x[t] * f;
-    } else {
-        for (int t = threadIdx.x; t < m; t += blockDim.x) v[key[t] >> 8] = x[t];
+        f = T(fac);
     }
+    for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x)
+        v[key[t] >> 8] = renorm ? x.loc[t - t0] * f : x.loc[t - t0];
+    cl.sync();                                       // no CTA leaves while others may read it
 }
 
-// CTA l: as k_prog_grad with f, w in global scratch (2 m per angle)
+// cluster lg (of L): as k_prog_grad, f and w over the cluster's CTAs
 template <typename T>
-__global__ void __launch_bounds__(1024)
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024)
 k_prog_grad_big(const int64_t *__restrict__ key, const int32_t *__restrict__ tab, int m,
                 const int32_t *__restrict__ desc, const int32_t *__restrict__ ops,
                 const double *__restrict__ cs, int L, const T *__restrict__ sigma,
-                const double *__restrict__ norm2, double *__restrict__ g, T *__restrict__ scratch)
+                const double *__restrict__ norm2, double *__restrict__ g)
 {
-    __shared__ double red[32];
-    const int lg = blockIdx.x;
-    T *f = scratch + size_t(lg) * 2 * size_t(m), *w = f + m;
-    for (int t = threadIdx.x; t < m; t += blockDim.x) {
-        f[t] = t == 0 ? T(1) : T(0);
-        w[t] = T(0);
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char clsm[];
+    __shared__ double red[40];
+    const int rank = int(cl.block_rank());
+    const int lg = int(blockIdx.x) / kClusterCtas;
+    const int chunk = (m + kClusterCtas - 1) / kClusterCtas;
+    const ClusterVec<T> f{reinterpret_cast<T *>(clsm), chunk, rank};
+    const ClusterVec<T> w{reinterpret_cast<T *>(clsm) + chunk, chunk, rank};
+    const int t0 = rank * chunk, t1 = min(m, t0 + chunk);
+    for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x) {
+        f.loc[t - t0] = t == 0 ? T(1) : T(0);
+        w.loc[t - t0] = T(0);
     }
-    __syncthreads();
+    cl.sync();
     int s = 0;
     for (int l = 0; l <= lg; ++l) {                  // phi_lg = U_lg .. U_1 |HF>
         const int nc = desc[11 * ops[l]];
         const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
-        for (int ci = 0; ci < nc; ++ci, ++s) prog_rotate(f, tab + int64_t(s) * m, m, c, sn);
+        for (int ci = 0; ci < nc; ++ci, ++s) cl_rotate(cl, f, tab + int64_t(s) * m, m, c, sn);
     }
     const int ncg = desc[11 * ops[lg]];
     for (int ci = 0; ci < ncg; ++ci)                 // constituents add in order
-        prog_generator(f, w, tab + int64_t(s - ncg + ci) * m, m);
+        cl_generator(cl, f, w, tab + int64_t(s - ncg + ci) * m, m);
     for (int l = lg + 1; l < L; ++l) {
         const int nc = desc[11 * ops[l]];
         const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
-        for (int ci = 0; ci < nc; ++ci, ++s) prog_rotate(w, tab + int64_t(s) * m, m, c, sn);
+        for (int ci = 0; ci < nc; ++ci, ++s) cl_rotate(cl, w, tab + int64_t(s) * m, m, c, sn);
     }
     double acc = 0.0;
-    for (int t = threadIdx.x; t < m; t += blockDim.x)
-        acc = fma(double(w[t]), double(sigma[key[t] >> 8]), acc);
-    const double dot = prog_block_sum(acc, red);
-    if (threadIdx.x == 0) g[lg] = (norm2 ? 2.0 / sqrt(*norm2) : 2.0) * dot;
+    for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x)
+        acc = fma(double(w.loc[t - t0]), double(sigma[key[t] >> 8]), acc);
+    const double dot = cl_sum(cl, acc, red, rank);
+    if (threadIdx.x == 0 && rank == 0) g[lg] = (norm2 ? 2.0 / sqrt(*norm2) : 2.0) * dot;
+    cl.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -1503,11 +1603,16 @@ cudaError_t prog_compile_big(const int64_t *list, int64_t m, const int64_t *step
 template <typename T>
 cudaError_t prog_prepare_big(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
                              const int32_t *ops, const double *cs, int L, bool renorm,
-                             double *norm2, T *v, T *scratch, cudaStream_t st)
+                             double *norm2, T *v, cudaStream_t st)
 {
     if (m <= kProgMax || m > kProgBig) return cudaErrorInvalidValue;
-    k_prog_prepare_big<T><<<1, 1024, 0, st>>>(key, tab, int(m), desc, ops, cs, L, renorm ? 1 : 0,
-                                              norm2, v, scratch);
+    const int chunk = int((m + kClusterCtas - 1) / kClusterCtas);
+    const size_t smem = size_t(chunk) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_prog_prepare_big<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_prog_prepare_big<T><<<kClusterCtas, 1024, smem, st>>>(key, tab, int(m), desc, ops, cs, L,
+                                                           renorm ? 1 : 0, norm2, v);
     hy::count_launch();
     return cudaGetLastError();
 }
@@ -1515,30 +1620,32 @@ cudaError_t prog_prepare_big(const int64_t *key, const int32_t *tab, int64_t m, 
 template <typename T>
 cudaError_t prog_grad_big(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
                           const int32_t *ops, const double *cs, int L, const T *sigma,
-                          const double *norm2, double *g, T *scratch, cudaStream_t st)
+                          const double *norm2, double *g, cudaStream_t st)
 {
     if (m <= kProgMax || m > kProgBig || L < 1) return cudaErrorInvalidValue;
-    k_prog_grad_big<T><<<unsigned(L), 1024, 0, st>>>(key, tab, int(m), desc, ops, cs, L, sigma,
-                                                     norm2, g, scratch);
+    const int chunk = int((m + kClusterCtas - 1) / kClusterCtas);
+    const size_t smem = 2 * size_t(chunk) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_prog_grad_big<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_prog_grad_big<T><<<unsigned(kClusterCtas * L), 1024, smem, st>>>(key, tab, int(m), desc, ops,
+                                                                       cs, L, sigma, norm2, g);
     hy::count_launch();
     return cudaGetLastError();
 }
 
 template cudaError_t prog_prepare_big<double>(const int64_t *, const int32_t *, int64_t,
                                               const int32_t *, const int32_t *, const double *,
-                                              int, bool, double *, double *, double *,
-                                              cudaStream_t);
+                                              int, bool, double *, double *, cudaStream_t);
 template cudaError_t prog_prepare_big<float>(const int64_t *, const int32_t *, int64_t,
                                              const int32_t *, const int32_t *, const double *, int,
-                                             bool, double *, float *, float *, cudaStream_t);
+                                             bool, double *, float *, cudaStream_t);
 template cudaError_t prog_grad_big<double>(const int64_t *, const int32_t *, int64_t,
                                            const int32_t *, const int32_t *, const double *, int,
-                                           const double *, const double *, double *, double *,
-                                           cudaStream_t);
+                                           const double *, const double *, double *, cudaStream_t);
 template cudaError_t prog_grad_big<float>(const int64_t *, const int32_t *, int64_t,
                                           const int32_t *, const int32_t *, const double *, int,
-                                          const float *, const double *, double *, float *,
-                                          cudaStream_t);
+                                          const float *, const double *, double *, cudaStream_t);
 template cudaError_t grad_sparse<double>(const SparseGradArgs<double> &, int, cudaStream_t);
 template cudaError_t grad_sparse<float>(const SparseGradArgs<float> &, int, cudaStream_t);
 #define HY_SV_INST(T)                                                                       \

@@ -87,7 +87,7 @@ def test_mixed_precision_matches_plain(n, seed, iters):
     import paper_2604_01176_gb300 as hy
     ref, ham, pool = make(n, n // 2, n // 2, seed)
     plain = hy.Adapt(ham, pool, "f64", max_iter=iters).run(iters)
-    mixed = hy.Adapt(ham, pool, "mixed", max_iter=iters, refine_steps=6).run(iters)
+    mixed = hy.Adapt(ham, pool, "mixed", max_iter=iters, refine_steps=6, float_from=1).run(iters)
     assert [r["selected"] for r in mixed] == [r["selected"] for r in plain]
     assert abs(mixed[-1]["energy"] - plain[-1]["energy"]) < 1e-6
     for r in mixed:

@@ -164,6 +164,14 @@ def test_sparse_driver_follows_dense_driver(cfg, iters):
     mixed = hy.Adapt(ham, pool, "mixed", max_iter=iters, sparse=True).run(iters)
     assert [r["selected"] for r in mixed] == [r["selected"] for r in dense]
     assert abs(mixed[-1]["energy"] - dense[-1]["energy"]) < 1e-6
+    # small supports optimise in double directly ...
+    assert all(r["energy_bulk_err"] == 0.0 for r in mixed)
+    # ... unless float is asked for at every size: float phase, double
+    # refinement, the next screen on the refined double state
+    flt = hy.Adapt(ham, pool, "mixed", max_iter=iters, sparse=True, float_from=1).run(iters)
+    assert [r["selected"] for r in flt] == [r["selected"] for r in dense]
+    assert abs(flt[-1]["energy"] - dense[-1]["energy"]) < 1e-9
+    assert all(0.0 < r["energy_bulk_err"] < 1e-4 for r in flt)
 
 
 def _ansatz(ref, seed, length):
