@@ -18,8 +18,10 @@ only once an exact screen would cost more than its feature pass), and the
 line reports how often each ran.
 
 Also reported: the same job in plain FP64 with the full exact screen (time,
-and the final energies of both legs with their gap, the north-star
-acceptance test), `e2e` (the job through the public API from host-resident
+and the final energies of both legs with their gap); `acceptance_long`, a
+longer trajectory from Hartree-Fock (18 iterations by default) in both
+precisions, which reaches supports of millions of determinants where float
+arithmetic and the ranker pay; `e2e` (the job through the public API from host-resident
 integrals: Hamiltonian build, pool, driver, 10 iterations, refinement,
 readback, release), matrix-free H|psi> at 32 qubits in FP64 and FP32, and
 H|psi> streamed from the explicitly stored Hamiltonian at 28 qubits (the
@@ -77,6 +79,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-sweeps", action="store_true", help="skip the H|psi> timings")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--accept-iters", type=int, default=18,
+                    help="iterations of the long plain-vs-mixed trajectory from Hartree-Fock "
+                         "reported as acceptance_long (0 skips it)")
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of oracle work per CPU sample")
     ap.add_argument("--hmat-workload", default="h14_28q",
@@ -104,6 +109,8 @@ def parse():
     ap.add_argument("--refine-every", type=int, default=1,
                     help="--trajectory: refine the mixed leg in double every k-th iteration")
     ap.add_argument("--dense", action="store_true", help="--trajectory on the dense sweeps only")
+    ap.add_argument("--classes", action="store_true",
+                    help="--trajectory: device time per kernel class per iteration")
     ap.add_argument("--config2", action="store_true",
                     help="20 qubits: --iters plain FP64 ADAPT iterations, and the full screen as "
                          "one launch against one launch per operator")
@@ -574,14 +581,19 @@ def plain_leg(ham, pool, hy, torch, args):
     ad = hy.Adapt(ham, pool, "f64", max_iter=J, sparse=True)
     run_job(ad, J, 0)
     torch.cuda.synchronize()
+    # the same per-launch events as the headline's timed region, so that
+    # both carry the same host cost of recording them
+    hy.profile_enable(hy.PROFILE_CLASSES)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     recs, e, _ = run_job(ad, J, 0)
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
+    prof = {c: hy.profile_read(c) for c in hy.PROFILE_CLASSES}
+    hy.profile_enable([])
     del ad
-    return dict(ms=ms, records=recs, energy=e)
+    return dict(ms=ms, records=recs, energy=e, prof=prof)
 
 
 def explicit_h_leg(hy, torch, args, peaks):
@@ -663,6 +675,8 @@ def run_ours(args, rank, world):
         out["head"]["ms"] = max_over_ranks([out["head"]["ms"]], torch.device("cuda"))[0]
     if not args.no_plain:
         out["plain"] = plain_leg(ham, pool, hy, torch, args)
+    if args.accept_iters > 0:
+        out["accept"] = acceptance_run(ham, pool, hy, args.accept_iters, args.top_m)
     if not args.no_sweeps:
         out["hpsi_ms_f64"], out["screen_ms_f64"], out["cpl_ms_f64"] = time_sweeps(
             ham, pool, torch.float64)
@@ -791,14 +805,79 @@ def screens_used(jobs):
     return counts
 
 
+def run_steps(ad, iters, hy, classes):
+    """`iters` ADAPT steps; with `classes`, the device time of every kernel
+    class per iteration (CUDA events around each launch) beside each record."""
+    recs = []
+    for _ in range(iters):
+        if classes:
+            hy.profile_enable(hy.PROFILE_CLASSES)
+        r = ad.step()
+        if classes:
+            r["classes_ms"] = {c: round(v["ms"], 2) for c in hy.PROFILE_CLASSES
+                               for v in [hy.profile_read(c)] if v["launches"]}
+            hy.profile_enable([])
+        recs.append(r)
+        if r["converged"]:
+            break
+    return recs
+
+
+def acceptance_run(ham, pool, hy, iters, top_m=TOP_M, refine_every=1, sparse=True,
+                   force_ranker=False, classes=False):
+    """Plain FP64 (whole pool screened exactly every iteration) and mixed
+    precision + ranker ADAPT from Hartree-Fock over `iters` iterations on one
+    resident Hamiltonian: per iteration the selected operators, the energies
+    (the mixed leg's refined in double every `refine_every` iterations, the
+    float error beside it), the screen used and the host wall time; then the
+    mixed leg's final double refinement and its gap to the plain energy."""
+    t0 = time.perf_counter()
+    plain = hy.Adapt(ham, pool, "f64", max_iter=iters, sparse=sparse)
+    precs = run_steps(plain, iters, hy, classes)
+    plain_s = time.perf_counter() - t0
+    plain.close()
+    ranker = hy.Ranker(hidden=256, seed=7)
+    extra = dict(exact_screen_work=-1.0) if force_ranker else {}
+    ad = hy.Adapt(ham, pool, "mixed", max_iter=iters, screen_top_m=top_m,
+                  refine_every=refine_every, refine_steps=REFINE_STEPS, sparse=sparse, **extra)
+    ad.set_ranker(ranker, warm_iters=3, epochs=30, refresh_every=REFRESH)
+    t0 = time.perf_counter()
+    mrecs = run_steps(ad, iters, hy, classes)
+    t1 = time.perf_counter()
+    e_final = ad.refine(steps=REFINE_STEPS)
+    mixed_s, refine_s = t1 - t0, time.perf_counter() - t1
+    ad.close()
+    ranker.close()
+    rows = []
+    for p, m in zip(precs, mrecs):
+        row = {"iter": p["iter"], "op_plain": p["selected"], "op_mixed": m["selected"],
+               "same_op": p["selected"] == m["selected"], "e_plain": p["energy"],
+               "e_mixed": m["energy"], "e_mixed_minus_plain": m["energy"] - p["energy"],
+               "mixed_f32_err": m["energy_bulk_err"],
+               "screen_mixed": SCREEN_NAMES.get(int(m["screen"])),
+               "support": m["support"], "evals_plain": p["n_evals"],
+               "evals_mixed": m["n_evals"], "evals_mixed_f64": m["n_evals_f64"],
+               "t_plain_s": round(p["t_total"], 4), "t_mixed_s": round(m["t_total"], 4)}
+        if classes:
+            row["classes_ms_plain"] = p["classes_ms"]
+            row["classes_ms_mixed"] = m["classes_ms"]
+        rows.append(row)
+    e_plain = precs[-1]["energy"]
+    return {"iterations": len(rows), "sparse_path": sparse, "ranker_forced": bool(force_ranker),
+            "refine_every": refine_every, "plain_s": round(plain_s, 3),
+            "mixed_s": round(mixed_s, 3), "refine_s": round(refine_s, 3),
+            "speedup": round(plain_s / (mixed_s + refine_s), 3),
+            "e_plain_final": e_plain, "e_mixed_final_refined": e_final,
+            "final_gap": e_final - e_plain,
+            "equal_final_energy_1e-6": abs(e_final - e_plain) <= 1e-6,
+            "same_selections": all(r["same_op"] for r in rows),
+            "ranker_consulted_iterations": sum(r["screen_mixed"] == "ranker" for r in rows),
+            "rows": rows}
+
+
 def trajectory(args):
-    """Plain FP64 and mixed precision (+ ranker) ADAPT from Hartree-Fock over
-    --iters iterations of --workload: per iteration the selected operators,
-    the energies (the mixed leg's in float bulk, or refined in double every
-    --refine-every iterations with the float error beside it), the screen
-    used and the wall time; then the mixed leg's refined final energy and
-    its gap to the plain one."""
-    import torch
+    """--iters iterations of --workload from Hartree-Fock, plain FP64 against
+    mixed precision + ranker (acceptance_run), printed as one JSON line."""
     import paper_2604_01176_gb300 as hy
     from paper_2604_01176_gb300 import build as hybuild
     hybuild.build()
@@ -806,45 +885,9 @@ def trajectory(args):
     h1, h2, ec = synth.integrals(n, seed)
     ham = hy.Hamiltonian(h1, h2, ec, n, na, nb)
     pool = hy.Pool(ham)
-    it = args.iters
-    sparse = not args.dense
-    legs = {}
-    t0 = time.perf_counter()
-    plain = hy.Adapt(ham, pool, "f64", max_iter=it, sparse=sparse)
-    precs = plain.run(it)
-    legs["plain_s"] = time.perf_counter() - t0
-    plain.close()
-    ranker = hy.Ranker(hidden=256, seed=7)
-    extra = dict(exact_screen_work=-1.0) if args.force_ranker else {}
-    ad = hy.Adapt(ham, pool, "mixed", max_iter=it, screen_top_m=args.top_m,
-                  refine_every=args.refine_every, refine_steps=REFINE_STEPS, sparse=sparse,
-                  **extra)
-    ad.set_ranker(ranker, warm_iters=3, epochs=30, refresh_every=REFRESH)
-    t0 = time.perf_counter()
-    mrecs = ad.run(it)
-    t1 = time.perf_counter()
-    e_final = ad.refine(steps=REFINE_STEPS)
-    legs["mixed_s"] = t1 - t0
-    legs["refine_s"] = time.perf_counter() - t1
-    rows = []
-    for p, m in zip(precs, mrecs):
-        rows.append({"iter": p["iter"], "op_plain": p["selected"], "op_mixed": m["selected"],
-                     "same_op": p["selected"] == m["selected"], "e_plain": p["energy"],
-                     "e_mixed": m["energy"], "e_mixed_minus_plain": m["energy"] - p["energy"],
-                     "mixed_f32_err": m["energy_bulk_err"],
-                     "screen_mixed": SCREEN_NAMES.get(int(m["screen"])),
-                     "support": m["support"], "evals_plain": p["n_evals"],
-                     "evals_mixed": m["n_evals"], "t_plain_s": round(p["t_total"], 4),
-                     "t_mixed_s": round(m["t_total"], 4)})
-    out = {"trajectory": args.workload, "iterations": len(rows), "sparse_path": sparse,
-           "ranker_forced": bool(args.force_ranker), "refine_every": args.refine_every,
-           "plain_s": round(legs["plain_s"], 3), "mixed_s": round(legs["mixed_s"], 3),
-           "refine_s": round(legs["refine_s"], 3),
-           "speedup": round(legs["plain_s"] / (legs["mixed_s"] + legs["refine_s"]), 3),
-           "e_plain_final": precs[-1]["energy"], "e_mixed_final_refined": e_final,
-           "final_gap": e_final - precs[-1]["energy"],
-           "equal_final_energy_1e-6": abs(e_final - precs[-1]["energy"]) <= 1e-6,
-           "same_selections": all(r["same_op"] for r in rows), "rows": rows}
+    out = {"trajectory": args.workload}
+    out.update(acceptance_run(ham, pool, hy, args.iters, args.top_m, args.refine_every,
+                              not args.dense, args.force_ranker, args.classes))
     print(json.dumps(out), flush=True)
 
 
@@ -1030,7 +1073,8 @@ def main():
             "iters_per_s": round(len(p["records"]) / (p["ms"] / 1e3), 4),
             "ms_per_job": round(p["ms"], 1), "final_energy": p["energy"],
             "selected": [x["selected"] for x in p["records"]],
-            "n_evals": [x["n_evals"] for x in p["records"]]}
+            "n_evals": [x["n_evals"] for x in p["records"]],
+            "kernel_breakdown": breakdown(p["prof"], p["ms"])}
         out["acceptance"] = {
             "test": "mixed+ranker job faster than the plain FP64 full-screen job at equal final "
                     "energy within 1e-6 Ha",
@@ -1038,6 +1082,25 @@ def main():
             "same_selections": out["plain_f64"]["selected"] == out["mixed"]["selected"],
             "speedup": round(p["ms"] / (head["ms"] / K), 3),
             "faster": p["ms"] > head["ms"] / K}
+    if "accept" in r:
+        a = r["accept"]
+        rows = a["rows"]
+        out["acceptance_long"] = {
+            "test": (f"{a['iterations']} ADAPT iterations from Hartree-Fock on the same resident "
+                     "Hamiltonian: mixed precision + ranker (then the final double refinement) "
+                     "against plain FP64 screening the whole pool exactly every iteration; host "
+                     "wall time of each leg"),
+            "plain_s": a["plain_s"], "mixed_s": round(a["mixed_s"] + a["refine_s"], 3),
+            "speedup": a["speedup"], "faster": a["speedup"] > 1.0,
+            "final_energy_gap": a["final_gap"],
+            "equal_final_energy": a["equal_final_energy_1e-6"],
+            "same_selections": a["same_selections"],
+            "ranker_consulted_iterations": a["ranker_consulted_iterations"],
+            "support": [x["support"] for x in rows],
+            "screen_mixed": [x["screen_mixed"] for x in rows],
+            "mixed_f32_err": [x["mixed_f32_err"] for x in rows],
+            "t_plain_s": [x["t_plain_s"] for x in rows],
+            "t_mixed_s": [x["t_mixed_s"] for x in rows]}
     if "hpsi_ms_f64" in r:
         def hp(ms, s):
             gbs = 2.0 * N * s / (ms / 1e3) / 1e9

@@ -756,7 +756,12 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream);
 /* HY_F32 drivers: refine the current ansatz in double precision (at most
  * `steps` BFGS steps from the current parameters) and return the double
  * energy in *e (host); the parameters are updated.  The run's final energy
- * in the mixed mode comes from this call. */
+ * in the mixed mode comes from this call.  When the last optimisation (of
+ * hy_adapt_step or of an earlier refinement) already ran in double and
+ * stopped by its own rule (max |dE/dtheta| < gtol, or no representable
+ * decrease) and the parameters have not changed since, steps > 0 returns
+ * that double energy without evaluating again: the refinement would
+ * re-evaluate the same point and stop there.  steps = 0 always evaluates. */
 hy_status hy_adapt_refine(hy_adapt *a, int steps, double *e, void *stream);
 
 /* Turn the judge (the extra full screen of every ranked iteration, see

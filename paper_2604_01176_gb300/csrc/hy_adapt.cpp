@@ -69,6 +69,11 @@ struct hy_adapt {
     std::vector<double> valid_theta;
     // the last iteration was refined in double: screen its double state
     bool screen_f64_next = false;
+    // the last optimisation ran in double until its own stopping rule
+    // (gradient below gtol, or no representable decrease), and theta has not
+    // changed since: a double refinement would stop at once with this energy
+    bool f64_settled = false;
+    double e_f64_settled = 0.0;
     // sigma = H psi holds every component (false after an evaluation that
     // formed it on psi's support only, through the support Hamiltonian)
     bool sigma_full[2] = {false, false};
@@ -546,8 +551,9 @@ const double kListAddCost = 1.0;
 // below stall * |E| (the rounding floor of a float evaluation, where further
 // steps only follow noise).
 hy_status bfgs(hy_adapt *a, hy_dtype dt, double gtol, int max_steps, cudaStream_t st,
-               double *e_out, double stall = 0.0)
+               double *e_out, double stall = 0.0, bool *settled = nullptr)
 {
+    bool done = false;   // stopped by the gradient, the line search or a stall
     const size_t j = a->ops.size();
     std::vector<double> x = a->theta, g, gn, pdir(j), xn(j), s(j), y(j), Hy(j);
     double e = 0.0;
@@ -556,7 +562,11 @@ hy_status bfgs(hy_adapt *a, hy_dtype dt, double gtol, int max_steps, cudaStream_
     std::vector<double> &H = a->hinv;
     const int ev_start = a->evals;
     for (int it = 0; it < max_steps; ++it) {
-        if (maxabs(g) < gtol || a->evals - ev_start >= a->cfg.max_evals) break;
+        if (maxabs(g) < gtol) {
+            done = true;
+            break;
+        }
+        if (a->evals - ev_start >= a->cfg.max_evals) break;
         for (size_t r = 0; r < j; ++r) {
             double v = 0.0;
             for (size_t c = 0; c < j; ++c) v -= H[r * j + c] * g[c];
@@ -589,6 +599,7 @@ hy_status bfgs(hy_adapt *a, hy_dtype dt, double gtol, int max_steps, cudaStream_
             // no decrease representable in this precision: keep x (the
             // buffers hold x's state unless a trial point was evaluated)
             if (tried) HY_TRY(energy(a, x, dt, st, &e));
+            done = true;
             break;
         }
         HY_TRY(gradient(a, xn, dt, st, gn));
@@ -618,10 +629,15 @@ hy_status bfgs(hy_adapt *a, hy_dtype dt, double gtol, int max_steps, cudaStream_
         x = xn;
         e = en;
         g = gn;
-        if (stalled) break;
+        if (stalled) {
+            done = true;
+            break;
+        }
     }
+    if (!done && max_steps > 0 && maxabs(g) < gtol) done = true;
     a->theta = x;
     *e_out = e;
+    if (settled) *settled = done;
     return HY_OK;
 }
 
@@ -1064,8 +1080,11 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     if (j == 0) a->hinv_fresh = true;
     HY_TRY(upload_ops(a, st));
     double e = 0.0;
+    a->f64_settled = false;
     if (bulk == HY_F64) {
-        HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.max_evals, st, &e, kStall64));
+        HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.max_evals, st, &e, kStall64,
+                    &a->f64_settled));
+        a->e_f64_settled = e;
         rec->energy = rec->energy_bulk = e;
         rec->energy_bulk_err = 0.0;
     } else if ((a->sparse_m >= 0 ? a->sparse_m : a->N) * 4 <
@@ -1073,7 +1092,9 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
         // few nonzero amplitudes (the support on the sparse path, every
         // determinant on the dense sweeps; the new operator at most
         // quadruples the support): double directly
-        HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.max_evals, st, &e, kStall64));
+        HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.max_evals, st, &e, kStall64,
+                    &a->f64_settled));
+        a->e_f64_settled = e;
         rec->energy = rec->energy_bulk = e;
         rec->energy_bulk_err = 0.0;
         a->screen_f64_next = true;
@@ -1090,7 +1111,9 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
             HY_TRY(energy(a, a->theta, HY_F64, st, &e64));
             rec->energy_bulk_err = std::fabs(e32 - e64);
             if (a->cfg.refine_steps > 0)
-                HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.refine_steps, st, &e64, kStall64));
+                HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, a->cfg.refine_steps, st, &e64, kStall64,
+                            &a->f64_settled));
+            a->e_f64_settled = e64;
             rec->energy = e64;
             a->screen_f64_next = true;
         }
@@ -1134,11 +1157,18 @@ hy_status hy_adapt_refine(hy_adapt *a, int steps, double *e, void *stream)
 {
     if (!a || !e || steps < 0) return set_err(HY_ERR_ARG, "bad arguments");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (steps > 0 && a->f64_settled) {
+        // the last optimisation already ended in double by its own rule at
+        // this theta: refining would re-evaluate this point and stop
+        *e = a->e_f64_settled;
+        return HY_OK;
+    }
     HY_TRY(upload_ops(a, st));
     double e64 = 0.0;
-    if (steps > 0)
-        HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, steps, st, &e64, kStall64));
-    else
+    if (steps > 0) {
+        HY_TRY(bfgs(a, HY_F64, a->cfg.gtol, steps, st, &e64, kStall64, &a->f64_settled));
+        a->e_f64_settled = e64;
+    } else
         HY_TRY(energy(a, a->theta, HY_F64, st, &e64));
     *e = e64;
     return HY_OK;
@@ -1174,6 +1204,7 @@ hy_status hy_adapt_set_ansatz(hy_adapt *a, const int64_t *ops, const double *the
     a->hinv_fresh = true;
     a->valid_dt = -1;
     a->screen_f64_next = false;
+    a->f64_settled = false;
     a->iter = int(len);
     cudaStream_t st = nullptr;
     return upload_ops(a, st);

@@ -113,3 +113,34 @@ def test_adapt_stops_on_gradient_norm():
     ad2 = hy.Adapt(ham, pool, "f64", max_iter=4, eps_grad=gn * 0.9999)
     r2 = ad2.step()
     assert r2["converged"] == 0 and r2["selected"] >= 0
+
+
+@pytest.mark.parametrize("sparse", [False, True], ids=["dense", "sparse"])
+def test_refine_after_settled_double_optimisation(sparse):
+    """A mixed driver whose iterations all optimise in double (few nonzero
+    amplitudes): its refinement returns the last double energy as it stands,
+    a fresh double evaluation of the same parameters (steps = 0) agrees with
+    it to rounding, and after the parameters move the refinement descends
+    again."""
+    import paper_2604_01176_gb300 as hy
+    ref, ham, pool = make(6, 3, 3, 1001)
+    iters = 5
+    plain = hy.Adapt(ham, pool, "f64", max_iter=iters, sparse=sparse).run(iters)
+    ad = hy.Adapt(ham, pool, "mixed", max_iter=iters, sparse=sparse, float_from=1 << 30)
+    recs = ad.run(iters)
+    assert [r["selected"] for r in recs] == [r["selected"] for r in plain]
+    assert all(r["energy_bulk_err"] == 0.0 for r in recs)
+    ops, th = ad.ansatz()
+    e_ref = oadapt.energy_and_gradient(ref, ref.pool(), list(ops), np.array(th))[0]
+    e_last = recs[-1]["energy"]
+    assert abs(e_last - e_ref) < 1e-10
+    assert ad.refine(steps=4) == e_last
+    assert abs(ad.refine(steps=0) - e_last) < 1e-12
+    # moved parameters: the shortcut no longer applies and the refinement
+    # descends from the moved point back toward the optimum
+    moved = np.array(th) + 1e-2
+    e_moved = oadapt.energy_and_gradient(ref, ref.pool(), list(ops), moved)[0]
+    ad.set_ansatz(list(ops), list(moved))
+    e_ref4 = ad.refine(steps=4)
+    assert e_ref4 < e_moved - 1e-9
+    assert e_ref4 >= e_last - 1e-9
