@@ -111,6 +111,9 @@ def parse():
     ap.add_argument("--dense", action="store_true", help="--trajectory on the dense sweeps only")
     ap.add_argument("--classes", action="store_true",
                     help="--trajectory: device time per kernel class per iteration")
+    ap.add_argument("--support-eval", action="store_true",
+                    help="--iters plain iterations, then --reps evaluations of that ansatz "
+                         "(large supports: sigma on the support)")
     ap.add_argument("--config2", action="store_true",
                     help="20 qubits: --iters plain FP64 ADAPT iterations, and the full screen as "
                          "one launch against one launch per operator")
@@ -891,6 +894,46 @@ def trajectory(args):
     print(json.dumps(out), flush=True)
 
 
+def support_eval(args):
+    """Large-support evaluations: --iters plain FP64 ADAPT iterations of
+    --workload from Hartree-Fock on the sparse path, then --reps evaluations
+    of the final ansatz in each precision (the first one lists the support,
+    the others form sigma on it only); device time per kernel class."""
+    import paper_2604_01176_gb300 as hy
+    from paper_2604_01176_gb300 import build as hybuild
+    hybuild.build()
+    n, na, nb, seed = synth.workload(args.workload)
+    h1, h2, ec = synth.integrals(n, seed)
+    ham = hy.Hamiltonian(h1, h2, ec, n, na, nb)
+    pool = hy.Pool(ham)
+    plain = hy.Adapt(ham, pool, "f64", max_iter=args.iters + 1, sparse=True)
+    recs = plain.run(args.iters)
+    ops, th = plain.ansatz()
+    plain.close()
+    import torch
+    out = {"support_eval": args.workload, "ansatz_len": len(ops),
+           "support": recs[-1]["support"]}
+    for prec, dt in (("f64", torch.float64), ("mixed", torch.float32)):
+        ad = hy.Adapt(ham, pool, prec, max_iter=len(ops) + 1, sparse=True,
+                      sparse_cap=ham.n_det // 8)
+        ad.set_ansatz(list(ops), list(th))
+        e0, _ = ad.evaluate(th, dt)
+        hy.profile_enable(hy.PROFILE_CLASSES)
+        t0 = time.perf_counter()
+        for _ in range(args.reps):
+            e, _ = ad.evaluate(th, dt)
+        dt_s = time.perf_counter() - t0
+        prof = {c: v for c in hy.PROFILE_CLASSES for v in [hy.profile_read(c)]
+                if v["launches"]}
+        hy.profile_enable([])
+        out[prec] = {"energy": e, "first_minus_rest": e0 - e,
+                     "ms_per_eval": round(dt_s / args.reps * 1e3, 3),
+                     "classes_ms_per_eval": {c: round(v["ms"] / args.reps, 3)
+                                             for c, v in prof.items()}}
+        ad.close()
+    print(json.dumps(out), flush=True)
+
+
 def config2(args):
     """20 qubits (63,504 determinants): --iters plain FP64 ADAPT iterations
     from Hartree-Fock on the dense sweeps (iterations/s), then at the final
@@ -998,6 +1041,8 @@ def main():
         return trajectory(args)
     if args.config2:
         return config2(args)
+    if args.support_eval:
+        return support_eval(args)
     if args.oracle_timing:
         return oracle_timing(args)
     if world > 1:
@@ -1041,7 +1086,7 @@ def main():
                             "iteration; the next screen on the refined double state) + the final "
                             "double-precision refinement; the Hamiltonian resident"),
                    "mode": (f"mixed precision, ranker attached (top-{args.top_m} proposals when "
-                            "consulted); psi a sparse vector while its support fits N/32 (float) "
+                            "consulted); psi a sparse vector while its support fits N/16 (float) "
                             "or N/8 (double); float optimisation from 2^20 nonzero amplitudes, "
                             "double below (every iteration of this job); the whole pool screened "
                             "exactly while pool x support <= 5e9"),

@@ -670,8 +670,12 @@ typedef struct {
                              support fits sparse_cap: state preparation,
                              renormalisation, energy and the adjoint's psi
                              side cost O(support), H psi is the scatter of
-                             hy_apply_h_sparse, and the screen visits only
-                             pairs with a listed end; when the list overflows
+                             hy_apply_h_sparse where all of it is needed (the
+                             screen, which visits only pairs with a listed
+                             end) and otherwise H psi on the support's rows
+                             only (the energy and the gradients read it
+                             nowhere else; the reverse sweep then keeps its
+                             vectors on the support); when the list overflows
                              the evaluation is redone with the dense sweeps,
                              which stay in use while the ansatz is at least as
                              long.  Supports of up to 12,288 determinants
@@ -685,10 +689,11 @@ typedef struct {
                              pairs still train it).
                              0: always the dense sweeps                        */
     int64_t sparse_cap;   /* support capacity of the sparse path; 0: N_det/8
-                             for double and N_det/32 for float evaluations
-                             (the scatter H psi, ~29 ns per listed amplitude,
-                             beats the dense float sweep up to ~N_det/23 and
-                             the double one up to ~N_det/3)                   */
+                             for double and N_det/16 for float evaluations (a
+                             sparse evaluation at large supports costs ~30 ns
+                             (float) / ~55 ns (double) per listed amplitude at
+                             32 qubits, a dense one ~1.5 ns / ~11 ns per
+                             determinant)                                     */
     double exact_screen_work; /* sparse path with a ranker: screen the whole
                              pool exactly while (pool size) x (support) is at
                              most this; 0: 5e9 (the cost of the ranker's

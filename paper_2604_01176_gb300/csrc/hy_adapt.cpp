@@ -77,6 +77,9 @@ struct hy_adapt {
     // sigma = H psi holds every component (false after an evaluation that
     // formed it on psi's support only, through the support Hamiltonian)
     bool sigma_full[2] = {false, false};
+    // sigma was formed on psi's support only (rows of the support): the
+    // reverse sweep then keeps lambda on that support too
+    bool sig_support[2] = {false, false};
     bool want_full_sigma = false;        // the next evaluation must form all of sigma
     int evals = 0, evals64 = 0;
     int iter = 0;
@@ -183,6 +186,13 @@ const int64_t kForwardSmall = 12288;
 // the support Hamiltonian is built when it holds at most this many entries
 // (12 bytes each)
 const int64_t kHssMaxEntries = int64_t(1) << 29;
+// cost of the scatter H psi per listed amplitude over the dense sweep's cost
+// per determinant, [double, float]: both scale with the couplings per
+// determinant.  Measured on a GB300 at 32 qubits: the scatter's atomics into
+// a sigma beyond L2 take ~175-235 ns per listed amplitude in double and ~170
+// ns in float at supports of 1-5 M, the dense sweep 10 ns (double, FP64-rate
+// bound) and 1.24 ns (float, tensor-core coupling) per determinant
+const double kScatterPerDense[2] = {20.0, 135.0};
 
 // The sparse evaluation: psi = U(theta)|HF> as a sparse vector (rotations
 // cost O(support)), renormalised over its support in double (float states),
@@ -247,11 +257,28 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     // support only: without it the gradient reads sigma beyond the support)
     const bool use_hss = prog_run && hy::prog_hss_ready(a->prog) && a->prog_grad_ok &&
                          !a->want_full_sigma;
+    // beyond the support programs the gradient is the reverse sweep, which
+    // reads sigma only through inner products with d psi / d theta_l, vectors
+    // inside psi's support: sigma is formed on that support alone, without
+    // atomics (rows of psi's list against the listed determinants)
+    const bool on_support = !use_hss && !a->prep_small && !a->want_full_sigma && L > 0;
     const double est = double(std::max<int64_t>(a->sparse_m_last[d], 1)) * double(a->conn);
-    const bool track = !use_hss && est <= double(hy::sstate_cap(G));
+    // all of sigma: by the scatter, or by the dense sweep over psi's array
+    // (zero off the support) once the scatter's atomics cost more
+    const bool dense_sigma = !use_hss && !on_support &&
+        double(a->sparse_m_last[d]) * kScatterPerDense[d] > double(a->N);
+    const bool track = !use_hss && !on_support && !dense_sigma &&
+                       est <= double(hy::sstate_cap(G));
     if (use_hss) {
         a->ss_clean[d][3] = false;
         HY_TRY(hy::prog_hss_apply(a->prog, psi, sigma, dt, st));
+    } else if (on_support) {
+        HY_TRY(hy::sstate_reset(G, !a->ss_clean[d][3], false, st));
+        a->ss_clean[d][3] = true;
+        HY_TRY(hy::sstate_apply_h_support(S, G, sigma, st));
+    } else if (dense_sigma) {
+        a->ss_clean[d][3] = false;
+        HY_TRY(hy_apply_h(a->h, psi, sigma, dt, st));
     } else if (track) {
         HY_TRY(hy::sstate_reset(G, !a->ss_clean[d][3], false, st));
         a->ss_clean[d][3] = true;
@@ -260,7 +287,8 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
         a->ss_clean[d][3] = false;
         HY_TRY(hy::sstate_apply_h(S, nullptr, sigma, st));
     }
-    a->sigma_full[d] = !use_hss;
+    a->sigma_full[d] = !use_hss && !on_support;
+    a->sig_support[d] = on_support;
     HY_TRY(hy::sstate_dot(S, sigma, a->d_e, st));
     int64_t cnt[2] = {0, 0};
     a->h_cnt[1] = 0;
@@ -298,11 +326,11 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     }
     // sigma's values are complete either way; an overflowing list only
     // leaves its support unlisted (and its array to be cleared in full)
-    a->sig_listed[d] = track && cnt[1] <= hy::sstate_cap(G);
-    a->sig_count[d] = cnt[1];
+    a->sig_listed[d] = (track && cnt[1] <= hy::sstate_cap(G)) || on_support;
+    a->sig_count[d] = on_support ? cnt[0] : cnt[1];
     if (track && !a->sig_listed[d]) a->ss_clean[d][3] = false;
     hy::sstate_set_hint(S, cnt[0]);
-    if (a->sig_listed[d]) hy::sstate_set_hint(G, cnt[1]);
+    if (a->sig_listed[d]) hy::sstate_set_hint(G, a->sig_count[d]);
     a->sparse_m = cnt[0];
     a->sparse_m_last[d] = cnt[0];
     return HY_OK;
@@ -325,6 +353,7 @@ hy_status energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     a->ss_clean[d][0] = false;
     a->ss_clean[d][3] = false;
     a->sig_listed[d] = false;
+    a->sig_support[d] = false;
     a->prog_support[d] = false;
     HY_TRY(set_hf(a, psi, dt, st));
     // float states: the squared norm is tracked through the rotations in
@@ -422,13 +451,20 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     HY_TRY(hy::sstate_copy(F, P, st));
     hy::sstate_set_hint(F, a->sparse_m);
     // lambda starts as sigma: a sparse copy when sigma's support is listed
-    // and, grown as last seen, still fits lambda's list
-    const bool lam_sparse = a->sig_listed[d] &&
-        double(a->sig_count[d]) * a->lam_growth[d] <= double(hy::sstate_cap(L));
+    // and, grown as last seen, still fits lambda's list.  When sigma was
+    // formed on psi's support S only, lambda stays on S (closed rotations):
+    // dE/dtheta_l = 2 <lam_l | A_l phi_l> reads lam_l only where A_l phi_l
+    // lives, inside S_l (the support after l operators), and lam_l there is
+    // U_{l+1}^T applied to lam_{l+1} on S_{l+1}, which holds every partner of
+    // S_l under operator l + 1 -- values on S off S_l are never read
+    const bool lam_closed = a->sig_support[d];
+    const bool lam_sparse = lam_closed || (a->sig_listed[d] &&
+        double(a->sig_count[d]) * a->lam_growth[d] <= double(hy::sstate_cap(L)));
     if (lam_sparse) {
         HY_TRY(hy::sstate_reset(L, !a->ss_clean[d][2], false, st));
         a->ss_clean[d][2] = true;
         HY_TRY(hy::sstate_copy(L, G, st));
+        if (lam_closed) hy::sstate_set_hint(L, a->sig_count[d]);
     } else {
         a->ss_clean[d][2] = false;
         HY_TRY(cu(cudaMemcpyAsync(lam, sigma, size_t(a->N) * es, cudaMemcpyDeviceToDevice, st),
@@ -437,9 +473,12 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     for (size_t l = j; l-- > 0;) {
         HY_TRY(hy::sstate_gradients(F, lam, a->p, a->d_ops + l, 1, a->sparse_m, a->d_ga + l, st));
         if (l == 0) break;
-        HY_TRY(hy::sstate_excite(F, a->p, a->ops[l], -th[l], st));
+        // phi_{l-1} = U_l^T phi_l lies inside S_{l-1}, within psi's support S:
+        // a partner off S holds an exact zero and would receive one, so phi's
+        // rotations keep S's list (closed) instead of listing such partners
+        HY_TRY(hy::sstate_excite(F, a->p, a->ops[l], -th[l], st, true));
         if (lam_sparse)
-            HY_TRY(hy::sstate_excite(L, a->p, a->ops[l], -th[l], st));
+            HY_TRY(hy::sstate_excite(L, a->p, a->ops[l], -th[l], st, lam_closed));
         else
             HY_TRY(hy_apply_excitation(a->h, a->p, a->ops[l], -th[l], lam, dt, 0, st));
     }
@@ -453,7 +492,7 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
                     "support count"));
     HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
     const bool f_ok = cnt[0] <= hy::sstate_cap(F), l_ok = cnt[1] <= hy::sstate_cap(L);
-    if (lam_sparse) {
+    if (lam_sparse && !lam_closed) {
         hy::sstate_set_hint(L, cnt[1]);
         a->lam_growth[d] = l_ok ? std::max(1.0, 1.25 * double(cnt[1]) /
                                                     double(std::max<int64_t>(a->sig_count[d], 1)))
@@ -747,13 +786,16 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
     if (c.sparse) {
         for (int d = 0; d < 2 && s == HY_OK; ++d) {
             if (!a->buf[d][0]) continue;
-            // the scatter H psi costs ~ support x 5,800 atomic adds, ~29 ns per
-            // listed amplitude at the measured ~2e11 adds/s: it matches the
-            // dense float sweep (205 ms at 32 qubits) near N/23 and the dense
-            // double one (1.65 s) near N/3.  Float lists hold N/32; double
-            // lists N/8 (the list memory, 8 bytes an entry, also bounds it)
+            // a sparse evaluation at large supports (state preparation,
+            // sigma on the support, the closed reverse sweep) costs ~30 ns per
+            // listed amplitude in float and ~55 ns in double at 32 qubits
+            // (2.67 M listed: 77 and 150 ms), against ~250 ms for a dense
+            // float evaluation (tensor-core H psi + rotations) and ~1.8 s for
+            // a dense double one.  Float lists hold N/16 (near the float
+            // break-even), double lists N/8 (their memory, 8 bytes an entry,
+            // bounds them before the break-even)
             int64_t cap = c.sparse_cap > 0 ? std::min(c.sparse_cap, a->N)
-                                           : a->N / (d == 0 ? 8 : 32);
+                                           : a->N / (d == 0 ? 8 : 16);
             cap = std::max<int64_t>(cap, 1);
             const hy_dtype dt = d == 0 ? HY_F64 : HY_F32;
             for (int b = 0; b < 2 && s == HY_OK; ++b)

@@ -88,6 +88,7 @@ struct hy_ham {
     DevArena arena;
     uint32_t *d_astr = nullptr, *d_bstr = nullptr;
     uint32_t *d_aex = nullptr, *d_bexT = nullptr;
+    uint32_t *d_bex = nullptr;   // beta excitations string-major [Nb][nexb]
     uint8_t *d_ainv = nullptr;   // inverse alpha excitation positions
     uint32_t *d_binom = nullptr;
     DevCsr<double> Ma64, Mb64;
@@ -662,6 +663,7 @@ hy_status finish_ham(hy_ham *h, hy_ham **out)
     up(ar.upload(&h->d_aex, h->A.ex.data(), h->A.ex.size()), "upload alpha excitations");
     up(ar.upload(&h->d_ainv, h->A.inv.data(), h->A.inv.size()), "upload inverse excitations");
     up(ar.upload(&h->d_bexT, bexT.data(), bexT.size()), "upload beta excitations");
+    up(ar.upload(&h->d_bex, h->B.ex.data(), h->B.ex.size()), "upload beta excitations");
     up(ar.upload(&h->d_binom, binom.data(), binom.size()), "upload binomials");
     up(ar.upload(&h->d_V64, h->kt.V.data(), h->kt.V.size()), "upload V");
     up(ar.upload(&h->d_V32, V32.data(), V32.size()), "upload V32");
@@ -1441,6 +1443,7 @@ hy::k::SparseArgs<T> sparse_args(const hy_ham *h, const void *psi, void *sigma,
     a.Ma_ptr = Ma->ptr; a.Ma_col = Ma->col; a.Ma_val = Ma->val;
     a.Mb_ptr = Mb->ptr; a.Mb_col = Mb->col; a.Mb_val = Mb->val;
     a.aex = h->d_aex; a.bexT = h->d_bexT; a.astr = h->d_astr; a.bstr = h->d_bstr;
+    a.bex = h->d_bex;
     a.n = h->n; a.nexa = h->A.nex; a.nexb = h->B.nex; a.Na = h->Na; a.Nb = h->Nb;
     return a;
 }
@@ -1933,6 +1936,13 @@ struct hy::SparseState {
     double *partials = nullptr;
     int64_t n_partials = 0;
     int64_t hint = 0;                    // host estimate of the count (grids)
+    int64_t *blk = nullptr;              // scratch of the bitmap compaction
+    // scratch of the support-row H psi, allocated on first use: runs and
+    // ralpha [Na], flags [Na + Nb], blist [Nb], counters [4]
+    int64_t *runs = nullptr;
+    int32_t *ralpha = nullptr, *blist = nullptr;
+    uint8_t *flags = nullptr;
+    unsigned long long *ctr = nullptr;
 };
 
 namespace {
@@ -1987,6 +1997,8 @@ hy_status sstate_create(const hy_ham *h, hy_dtype dt, void *v, int64_t cap, Spar
         s->n_partials = int64_t(8) * h->num_sms;
         e = cudaMalloc(&s->partials, size_t(s->n_partials) * sizeof(double));
     }
+    if (e == cudaSuccess)
+        e = cudaMalloc(&s->blk, size_t(hy::k::bits_compact_blocks(s->words)) * sizeof(int64_t));
     if (e != cudaSuccess) {
         sstate_destroy(s);
         return cuda_fail(e, "cudaMalloc(sparse state)");
@@ -2002,6 +2014,12 @@ void sstate_destroy(SparseState *s)
     cudaFree(s->bits);
     cudaFree(s->cnt);
     cudaFree(s->partials);
+    cudaFree(s->blk);
+    cudaFree(s->runs);
+    cudaFree(s->ralpha);
+    cudaFree(s->blist);
+    cudaFree(s->flags);
+    cudaFree(s->ctr);
     delete s;
 }
 
@@ -2037,7 +2055,8 @@ hy_status sstate_copy(SparseState *dst, const SparseState *src, void *stream)
 
 void sstate_set_hint(SparseState *s, int64_t n) { s->hint = n; }
 
-hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double theta, void *stream)
+hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double theta, void *stream,
+                        bool closed)
 {
     const hy_ham *h = s->h;
     if (!p || p->h != h || k < 0 || k >= int64_t(p->ops.size()))
@@ -2059,10 +2078,12 @@ hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double thet
     hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream,
                        double(std::max<int64_t>(s->hint, 0)) * nc * (12.0 + 4.0 * es));
     if (s->dt == HY_F64)
-        HY_CUDA(hy::k::sv_excite<double>(svec<double>(s), o, int(k), nc, theta, h->num_sms, st),
+        HY_CUDA(hy::k::sv_excite<double>(svec<double>(s), o, int(k), nc, theta, h->num_sms, st,
+                                         closed),
                 "sparse excitation");
     else
-        HY_CUDA(hy::k::sv_excite<float>(svec<float>(s), o, int(k), nc, theta, h->num_sms, st),
+        HY_CUDA(hy::k::sv_excite<float>(svec<float>(s), o, int(k), nc, theta, h->num_sms, st,
+                                        closed),
                 "sparse excitation");
     return HY_OK;
 }
@@ -2450,6 +2471,59 @@ hy_status sstate_apply_h(const SparseState *s, SparseState *sig, void *sigma, vo
         auto a = sparse_args<float>(h, s->v, sigma, s->list, 0);
         out(a);
         HY_CUDA(hy::k::hpsi_scatter<float>(a, h->num_sms, st), "sparse H psi");
+    }
+    return HY_OK;
+}
+
+hy_status sstate_apply_h_support(const SparseState *s, SparseState *sig, void *sigma, void *stream)
+{
+    cudaStream_t st = as_stream(stream);
+    const hy_ham *h = s->h;
+    if (!sig || sig->dt != s->dt || sig->v != sigma || sig->cap < s->cap)
+        return fail(HY_ERR_ARG, "sigma state mismatch");
+    // bytes: psi read once per listed row, sigma written once; work: the
+    // bitmap probes, one per coupling of a listed row
+    const double es = s->dt == HY_F64 ? 8.0 : 4.0;
+    hy::ProfScope prof(HY_PROF_HPSI_SPARSE, stream, double(s->hint) * 2.0 * es,
+                       double(s->hint) * double(hy::ham_connections(h)));
+    // sigma's bitmap becomes psi's, its list psi's support in determinant
+    // order (rows gathered together then share their alpha string, and the
+    // alpha rows of psi and of the bitmap that their couplings reach stay in
+    // L2), its count psi's; every listed row of sigma is then written
+    HY_CUDA(cudaMemcpyAsync(sig->bits, s->bits, size_t(s->words) * sizeof(uint32_t),
+                            cudaMemcpyDeviceToDevice, st), "copy bitmap");
+    HY_CUDA(hy::k::bits_compact(sig->bits, sig->words, sig->list, sig->cap, sig->cnt, sig->blk, st),
+            "support list");
+    if (!sig->runs) {
+        cudaError_t e = cudaMalloc(&sig->runs, size_t(h->Na) * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc(&sig->ralpha, size_t(h->Na) * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&sig->blist, size_t(h->Nb) * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&sig->flags, size_t(h->Na + h->Nb));
+        if (e == cudaSuccess) e = cudaMalloc(&sig->ctr, 4 * sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(support rows)");
+    }
+    auto run = [&](auto &a) {
+        a.list = sig->list;
+        a.cnt = sig->cnt;
+        a.cap = sig->cap;
+        a.bits = sig->bits;
+        a.runs = sig->runs;
+        a.ralpha = sig->ralpha;
+        a.flagA = sig->flags;
+        a.flagB = sig->flags + h->Na;
+        a.blist = sig->blist;
+        a.ctr = sig->ctr;
+    };
+    if (s->dt == HY_F64) {
+        hy::k::SupRowsArgs<double> a;
+        a.s = sparse_args<double>(h, s->v, sigma, sig->list, 0);
+        run(a);
+        HY_CUDA(hy::k::hpsi_support<double>(a, h->num_sms, st), "support H psi");
+    } else {
+        hy::k::SupRowsArgs<float> a;
+        a.s = sparse_args<float>(h, s->v, sigma, sig->list, 0);
+        run(a);
+        HY_CUDA(hy::k::hpsi_support<float>(a, h->num_sms, st), "support H psi");
     }
     return HY_OK;
 }

@@ -154,9 +154,19 @@ void sstate_destroy(SparseState *s);
 // else only the listed entries.  hf: then set v = |HF> (index 0).
 hy_status sstate_reset(SparseState *s, bool full, bool hf, void *stream);
 hy_status sstate_copy(SparseState *dst, const SparseState *src, void *stream);
+// sigma = H psi on psi's support only: sig (clean, over the array sigma)
+// receives psi's list and bitmap, and sigma every listed row of H psi, from
+// the couplings to listed determinants; sigma elsewhere stays zero.  Enough
+// for everything that reads sigma only on psi's support (the energy, and the
+// gradients, whose vectors d psi / d theta_l lie in that support).
+hy_status sstate_apply_h_support(const SparseState *s, SparseState *sig, void *sigma,
+                                 void *stream);
 // host estimate of the count, used only to size grids
 void sstate_set_hint(SparseState *s, int64_t n);
-hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double theta, void *stream);
+// closed: keep s's list fixed -- a pair whose other end is unlisted only
+// scales its listed end (for a vector that is read on a fixed support only)
+hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double theta, void *stream,
+                        bool closed = false);
 // In one CTA: clear the support, |HF>, the rotations of ops[0..L) (device)
 // with cs[2l], cs[2l+1] (device) = cos, sin theta_l, then (renorm) divide by
 // the FP64 norm over the support.  For small supports (one launch instead of

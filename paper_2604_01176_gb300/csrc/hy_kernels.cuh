@@ -254,6 +254,7 @@ struct SparseArgs {
     const int32_t *Ma_ptr, *Ma_col, *Mb_ptr, *Mb_col;
     const T *Ma_val, *Mb_val, *V;
     const uint32_t *aex, *bexT, *astr, *bstr;
+    const uint32_t *bex;            // beta excitations, string-major [Nb][nexb]
     int n, nexa, nexb;
     int64_t Na, Nb;
 };
@@ -284,6 +285,32 @@ cudaError_t support(const T *psi, int64_t N, int64_t *list, int64_t cap,
                     unsigned long long *count, int num_sms, cudaStream_t st);
 template <typename T>
 cudaError_t hpsi_scatter(const SparseArgs<T> &a, int num_sms, cudaStream_t st);
+// the set bits of a membership bitmap of `words` words as a list in
+// increasing order (at most cap written; cnt[0] = cnt[1] = the number of set
+// bits, cnt[2] = 0); blk: scratch of bits_compact_blocks(words) int64
+inline int64_t bits_compact_blocks(int64_t words) { return (words + 2047) / 2048; }
+cudaError_t bits_compact(const uint32_t *bits, int64_t words, int64_t *list, int64_t cap,
+                         unsigned long long *cnt, int64_t *blk, cudaStream_t st);
+// sigma = H psi on the rows of psi's support only (k_sup_alpha, k_sup_beta):
+// s holds psi's dense array (zero off the support), sigma and the tables;
+// list / cnt / cap the support sorted by determinant, bits its bitmap; the
+// rest is scratch (runs, ralpha: Na entries; flagA: Na, flagB, blist: Nb;
+// ctr: 4 counters).  sigma is written on the support only.
+template <typename T>
+struct SupRowsArgs {
+    SparseArgs<T> s;
+    const int64_t *list;
+    const unsigned long long *cnt;
+    int64_t cap;
+    const uint32_t *bits;
+    int64_t *runs;
+    int32_t *ralpha;
+    uint8_t *flagA, *flagB;
+    int32_t *blist;
+    unsigned long long *ctr;
+};
+template <typename T>
+cudaError_t hpsi_support(const SupRowsArgs<T> &a, int num_sms, cudaStream_t st);
 template <typename T>
 cudaError_t grad_sparse(const SparseGradArgs<T> &a, int num_sms, cudaStream_t st);
 
@@ -315,10 +342,11 @@ cudaError_t sv_reset(const SVec<T> &x, bool hf, int num_sms, cudaStream_t st);
 // dst <- src (dst must be reset)
 template <typename T>
 cudaError_t sv_copy(const SVec<T> &dst, const SVec<T> &src, int num_sms, cudaStream_t st);
-// exp(theta (C - C^dagger)) for every constituent C of operator k
+// exp(theta (C - C^dagger)) for every constituent C of operator k; closed:
+// keep the list fixed (a pair with an unlisted end only scales its listed end)
 template <typename T>
 cudaError_t sv_excite(const SVec<T> &x, const SvOpArgs &o, int k, int nc, double theta,
-                      int num_sms, cudaStream_t st);
+                      int num_sms, cudaStream_t st, bool closed = false);
 // one CTA: clear x's support, |HF>, every constituent rotation of ops[0..L)
 // with cs[2l], cs[2l+1] = cos, sin theta_l, then (renorm) divide by the FP64
 // norm over the support (written to *norm2 if not null); for small supports.

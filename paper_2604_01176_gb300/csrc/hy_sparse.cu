@@ -155,6 +155,259 @@ k_hpsi_scatter(SparseArgs<T> a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// sigma = H psi on psi's support S only, for large supports (rows = S's
+// determinants, sorted).  H's couplings of a row d = (A, B) are enumerated as
+// k_hpsi_scatter enumerates the targets of d (H is real symmetric, so the
+// column of d is its row); psi is zero off S, so each row's sum needs no
+// membership test.  Two passes, each reading psi from shared memory:
+//   k_sup_alpha, one CTA per alpha string A of S (the run of S's rows with
+//     that alpha string): psi's row A is staged, then, one alpha excitation
+//     e of A at a time, psi's row A_e; the rows (A, B) of the run collect
+//       the same-alpha part (beta-string CSR M_beta, the beta excitations
+//       with no alpha excitation, the diagonal) from row A and
+//       the alpha-beta part, sum_f sgn V[pq_e][rs_f] psi[A_e][B_f] plus the
+//       alpha excitation with a diagonal beta part, from row A_e,
+//     a warp per row, lanes over its beta excitations (B-major table);
+//     sigma[A, B] is written;
+//   k_sup_beta, one CTA per beta string B of S: psi's column B on the alpha
+//     strings of S is staged, and each row (A, B) of S adds the same-beta
+//     part (alpha-string CSR M_alpha) from it.
+// Every sum runs in a fixed order, so the result is deterministic.  Work is
+// handed out through an atomic counter (runs differ in length).
+// ---------------------------------------------------------------------------
+
+// the runs of the sorted support by alpha string (unordered; the CTA of a run
+// counts its length from the bitmap) and the beta strings present
+__global__ void __launch_bounds__(256)
+k_sup_runs(const int64_t *__restrict__ list, const unsigned long long *__restrict__ cnt,
+           int64_t cap, int64_t Nb, int64_t *__restrict__ runs, int32_t *__restrict__ ralpha,
+           uint8_t *__restrict__ flagA, uint8_t *__restrict__ flagB,
+           unsigned long long *__restrict__ ctr)
+{
+    const int64_t m = list_len(cnt, 0, cap);
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < m;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t d = list[t], A = d / Nb;
+        flagB[d - A * Nb] = 1;
+        if (t == 0 || list[t - 1] / Nb != A) {
+            const unsigned long long pos = atomicAdd(ctr + 0, 1ull);
+            runs[pos] = t;
+            ralpha[pos] = int32_t(A);
+            flagA[A] = 1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_sup_blist(const uint8_t *__restrict__ flagB, int64_t Nb, int32_t *__restrict__ blist,
+            unsigned long long *__restrict__ ctr)
+{
+    for (int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; b < Nb;
+         b += int64_t(gridDim.x) * blockDim.x)
+        if (flagB[b]) blist[atomicAdd(ctr + 1, 1ull)] = int32_t(b);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+constexpr int kSupThreads = 512;
+
+template <typename T>
+size_t sup_alpha_smem(int64_t Nb, int nn)
+{
+    return (2 * size_t((Nb + 3) / 4 * 4) + 2 * size_t(nn)) * sizeof(T);
+}
+
+// stage psi's row R (Nb amplitudes) into shared memory: every thread issues
+// its element copies without waiting (cp.async), then waits for its own;
+// the caller's barrier makes the row visible to the block
+template <typename T>
+__device__ __forceinline__ void stage_row(T *row, const T *src, int64_t Nb)
+{
+    for (int64_t i = threadIdx.x; i < Nb; i += blockDim.x) {
+        const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(row + i));
+        if (sizeof(T) == 8)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src + i)
+                         : "memory");
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + i)
+                         : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// The alpha-beta part runs a thread per row (A, B): the row's beta
+// excitations stay in registers, and each staged row A_e costs it one fused
+// multiply-add per beta excitation (plus one per occupied beta orbital, the
+// diagonal beta part) and no cross-lane reduction -- in double precision the
+// GB300's FP64 pipe is the bound, so every FP64 instruction is useful work.
+// The same-alpha part (CSR rows of ~n^4/4 entries) keeps a warp per row with
+// its lanes over the entries, reduced once per row.
+template <typename T>
+__global__ void __launch_bounds__(kSupThreads)
+k_sup_alpha(SupRowsArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char sup_sm[];
+    const SparseArgs<T> &h = a.s;
+    const int n = h.n, nn = n * n, nexa = h.nexa, nexb = h.nexb;
+    const int64_t Nb = h.Nb, Nbp = (Nb + 3) / 4 * 4;
+    T *row = reinterpret_cast<T *>(sup_sm);       // a staged row of psi
+    T *acc = row + Nbp;                           // the run's same-alpha sums
+    T *vrow = acc + Nbp;                          // V[pq_e][.] with e's sign
+    T *dA = vrow + nn;                            // sum_{p in A} V[pp][.]
+    __shared__ uint32_t aexs[64];
+    __shared__ int64_t sh_r, sh_cnt[kSupThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = kSupThreads / 32;
+    for (;;) {
+        __syncthreads();                          // the previous run is written
+        if (tid == 0) sh_r = int64_t(atomicAdd(a.ctr + 2, 1ull));
+        __syncthreads();
+        const int64_t r = sh_r;
+        if (r >= int64_t(a.ctr[0])) break;
+        const int64_t t0 = a.runs[r], A = a.ralpha[r];
+        // the run's length: A's row of the bitmap (bits A Nb .. A Nb + Nb - 1)
+        {
+            const int64_t b0 = A * Nb, b1 = b0 + Nb, w0 = b0 >> 5, w1 = (b1 - 1) >> 5;
+            int64_t c = 0;
+            for (int64_t w = w0 + tid; w <= w1; w += kSupThreads) {
+                uint32_t x = a.bits[w];
+                if (w == w0) x &= ~0u << (b0 & 31);
+                if (w == w1 && (b1 & 31)) x &= (1u << (b1 & 31)) - 1u;
+                c += __popc(x);
+            }
+            c = warp_sum(c);
+            if (lane == 0) sh_cnt[warp] = c;
+        }
+        if (tid < nexa) aexs[tid] = h.aex[A * nexa + tid];
+        const uint32_t am = h.astr[A];
+        for (int i = tid; i < nn; i += kSupThreads) {
+            T v = T(0);
+            for (uint32_t mm = am; mm; mm &= mm - 1) {
+                const int p = __ffs(mm) - 1;
+                v += h.V[size_t(p * n + p) * nn + i];
+            }
+            dA[i] = v;
+        }
+        stage_row(row, h.psi + A * Nb, Nb);
+        __syncthreads();
+        int64_t mA = 0;
+        for (int w = 0; w < nwarps; ++w) mA += sh_cnt[w];
+        if (t0 + mA > a.cap) mA = a.cap - t0;    // an overflowed (invalid) support
+        const int64_t *Brun = a.list + t0;
+        // same alpha string: M_beta, beta excitations without an alpha
+        // excitation, the diagonal; a warp per row
+        for (int64_t i = warp; i < mA; i += nwarps) {
+            const int64_t B = Brun[i] - A * Nb;
+            T part = T(0);
+            for (int k = h.Mb_ptr[B] + lane; k < h.Mb_ptr[B + 1]; k += 32)
+                part = fma(h.Mb_val[k], row[h.Mb_col[k]], part);
+            for (int f = lane; f < nexb; f += 32) {
+                const uint32_t w = h.bex[B * nexb + f];
+                const T c = dA[int((w >> 20) & 15) * n + int((w >> 16) & 15)];
+                part = fma((w >> 31) ? -c : c, row[w & 0xFFFFu], part);
+            }
+            if (lane < n && ((h.bstr[B] >> lane) & 1u))      // occupied beta orbital
+                part = fma(dA[lane * n + lane], row[B], part);
+            part = warp_sum(part);
+            if (lane == 0) acc[i] = part;
+        }
+        // alpha excitations: psi's rows A_e, a thread per row (A, B), chunks
+        // of one row per thread
+        for (int64_t c0 = 0; c0 < mA; c0 += kSupThreads) {
+            const int64_t i = c0 + tid;
+            const bool act = i < mA;
+            const int64_t B = act ? Brun[i] - A * Nb : 0;
+            uint32_t bx[64];
+#pragma unroll
+            for (int f = 0; f < 64; ++f) bx[f] = act && f < nexb ? h.bex[B * nexb + f] : 0u;
+            const uint32_t bm = act ? h.bstr[B] : 0u;
+            T s = T(0);
+            for (int e = 0; e < nexa; ++e) {
+                const uint32_t u = aexs[e];
+                const int64_t Ao = u & 0xFFFFu;
+                if (!a.flagA[Ao]) continue;       // psi's row A_e is zero
+                __syncthreads();                  // the previous row's readers are done
+                const int pq = int((u >> 20) & 15) * n + int((u >> 16) & 15);
+                for (int q = tid; q < nn; q += kSupThreads) {
+                    const T c = h.V[size_t(pq) * nn + q];
+                    vrow[q] = (u >> 31) ? -c : c;
+                }
+                stage_row(row, h.psi + Ao * Nb, Nb);
+                __syncthreads();
+                if (act) {
+#pragma unroll
+                    for (int f = 0; f < 64; ++f) {
+                        if (f < nexb) {
+                            const uint32_t w = bx[f];
+                            const T c = vrow[int((w >> 20) & 15) * n + int((w >> 16) & 15)];
+                            s = fma((w >> 31) ? -c : c, row[w & 0xFFFFu], s);
+                        }
+                    }
+                    const T xb = row[B];
+                    for (uint32_t mm = bm; mm; mm &= mm - 1) {
+                        const int rr = __ffs(mm) - 1;
+                        s = fma(vrow[rr * n + rr], xb, s);
+                    }
+                }
+            }
+            __syncthreads();
+            if (act) h.sigma[Brun[i]] = acc[i] + s;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSupThreads)
+k_sup_beta(SupRowsArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char sup_sm[];
+    const SparseArgs<T> &h = a.s;
+    const int64_t Na = h.Na, Nb = h.Nb;
+    T *col = reinterpret_cast<T *>(sup_sm);       // psi's column B over alpha strings
+    __shared__ int64_t sh_r;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = kSupThreads / 32;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) sh_r = int64_t(atomicAdd(a.ctr + 3, 1ull));
+        __syncthreads();
+        const int64_t r = sh_r;
+        if (r >= int64_t(a.ctr[1])) break;
+        const int64_t B = a.blist[r];
+        const int64_t nr = int64_t(a.ctr[0]);
+        for (int64_t i = tid; i < Na; i += kSupThreads) col[i] = T(0);
+        __syncthreads();
+        for (int64_t j = tid; j < nr; j += kSupThreads) {
+            const int64_t A = a.ralpha[j];
+            col[A] = h.psi[A * Nb + B];
+        }
+        __syncthreads();
+        // the rows (A, B) of S: a warp per row, lanes over A's M_alpha entries
+        for (int64_t j0 = int64_t(warp) * 32; j0 < nr; j0 += int64_t(nwarps) * 32) {
+            const int64_t j = j0 + lane;
+            const int64_t Aj = j < nr ? a.ralpha[j] : 0;
+            unsigned msk = __ballot_sync(0xffffffffu, j < nr && member(a.bits, Aj * Nb + B));
+            while (msk) {
+                const int l = __ffs(msk) - 1;
+                msk &= msk - 1;
+                const int64_t A = __shfl_sync(0xffffffffu, Aj, l);
+                T part = T(0);
+                for (int k = h.Ma_ptr[A] + lane; k < h.Ma_ptr[A + 1]; k += 32)
+                    part = fma(h.Ma_val[k], col[h.Ma_col[k]], part);
+                part = warp_sum(part);
+                if (lane == 0) h.sigma[A * Nb + B] += part;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ uint32_t rank_bits(uint32_t m, const uint32_t (*C)[33])
 {
     uint32_t r = 0;
@@ -330,7 +583,7 @@ k_sv_copy(SVec<T> dst, SVec<T> src)
 // the rotation loop of k_sv_excite over this block's share of entries < m
 template <typename T>
 __device__ __forceinline__ void sv_rotate(SVec<T> &x, const SvOpArgs &o, int k, int ci, T c, T s,
-                                          int64_t m, const uint32_t (*C)[33])
+                                          int64_t m, const uint32_t (*C)[33], bool closed = false)
 {
     int fw[4], bw[4], len;
     op_strings(o.desc + 11 * k + 1 + 5 * ci, fw, bw, len);
@@ -357,6 +610,12 @@ __device__ __forceinline__ void sv_rotate(SVec<T> &x, const SvOpArgs &o, int k, 
             fresh = dom;
         }
         const T ss = sg > 0 ? s : -s;
+        if (closed && fresh >= 0) {
+            // the other end lies off the support: its amplitude is zero and
+            // is not kept, only the listed end is scaled
+            x.v[d] = c * x.v[d];
+            continue;
+        }
         const T xv = x.v[dom], yv = x.v[img];
         x.v[dom] = c * xv - ss * yv;
         x.v[img] = c * yv + ss * xv;
@@ -374,9 +633,11 @@ __device__ __forceinline__ void sv_rotate(SVec<T> &x, const SvOpArgs &o, int k, 
 // disjoint, so the rotation is race-free; entries appended here (positions >=
 // the snapshot) are not visited again.  The last block to finish copies the
 // final count into the snapshot for the next rotation.
+// closed: the list is kept as it is (a pair whose other end is unlisted only
+// scales its listed end), for vectors needed on a fixed support only.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_sv_excite(SVec<T> x, SvOpArgs o, int k, int ci, T c, T s)
+k_sv_excite(SVec<T> x, SvOpArgs o, int k, int ci, T c, T s, int closed)
 {
     const int64_t m = list_len(x.snap, 0, x.cap);
     const bool idle = int64_t(blockIdx.x) * blockDim.x >= m;     // block-uniform
@@ -384,7 +645,7 @@ k_sv_excite(SVec<T> x, SvOpArgs o, int k, int ci, T c, T s)
     if (!idle) {
         for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
         __syncthreads();
-        sv_rotate(x, o, k, ci, c, s, m, C);
+        sv_rotate(x, o, k, ci, c, s, m, C, closed != 0);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1247,6 +1508,93 @@ __device__ __forceinline__ int block_excl_scan(int v, int *warp_tot, int *tot)
     return warp_tot[w] + x - v;
 }
 
+// ---------------------------------------------------------------------------
+// A support list in determinant order from its membership bitmap (stream
+// compaction in three passes): block b owns words [b * 2048, (b + 1) * 2048)
+// (8 consecutive words a thread), counts their set bits, the block totals
+// are scanned by one block, and every block then writes its determinants in
+// order from its offset.  Rows processed together by a later kernel are then
+// neighbours in Omega_CIk: they share their alpha string, and with it the
+// alpha rows their couplings reach.
+// ---------------------------------------------------------------------------
+constexpr int kCompactWords = 8;
+constexpr int kCompactThreads = 256;
+
+__global__ void __launch_bounds__(kCompactThreads)
+k_bits_count(const uint32_t *__restrict__ bits, int64_t words, int64_t *__restrict__ blk)
+{
+    __shared__ int wsum[kCompactThreads / 32];
+    const int64_t w0 = (int64_t(blockIdx.x) * kCompactThreads + threadIdx.x) * kCompactWords;
+    int c = 0;
+    for (int j = 0; j < kCompactWords; ++j)
+        if (w0 + j < words) c += __popc(bits[w0 + j]);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t t = 0;
+        for (int w = 0; w < kCompactThreads / 32; ++w) t += wsum[w];
+        blk[blockIdx.x] = t;
+    }
+}
+
+// exclusive scan of blk[0..nb) in place by one block of 1024 threads, each
+// owning a contiguous run; the total goes to cnt[0] (count) and cnt[1]
+// (rotation snapshot), cnt[2] (finished blocks) is cleared
+__global__ void __launch_bounds__(1024)
+k_blk_scan(int64_t *__restrict__ blk, int64_t nb, unsigned long long *__restrict__ cnt)
+{
+    __shared__ long long wt[32];
+    const int64_t per = (nb + blockDim.x - 1) / blockDim.x;
+    const int64_t b0 = int64_t(threadIdx.x) * per, b1 = b0 + per < nb ? b0 + per : nb;
+    long long run = 0;
+    for (int64_t b = b0; b < b1; ++b) run += blk[b];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long x = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int i = 0; i < int(blockDim.x >> 5); ++i) {
+            const long long t = wt[i];
+            wt[i] = acc;
+            acc += t;
+        }
+        cnt[0] = (unsigned long long)acc;
+        cnt[1] = (unsigned long long)acc;
+        cnt[2] = 0ull;
+    }
+    __syncthreads();
+    long long off = wt[w] + x - run;
+    for (int64_t b = b0; b < b1; ++b) {
+        const long long c = blk[b];
+        blk[b] = off;
+        off += c;
+    }
+}
+
+__global__ void __launch_bounds__(kCompactThreads)
+k_bits_emit(const uint32_t *__restrict__ bits, int64_t words, const int64_t *__restrict__ blk,
+            int64_t *__restrict__ list, int64_t cap)
+{
+    __shared__ int wt[kCompactThreads / 32], tot;
+    const int64_t w0 = (int64_t(blockIdx.x) * kCompactThreads + threadIdx.x) * kCompactWords;
+    uint32_t wv[kCompactWords];
+    int c = 0;
+    for (int j = 0; j < kCompactWords; ++j) {
+        wv[j] = w0 + j < words ? bits[w0 + j] : 0u;
+        c += __popc(wv[j]);
+    }
+    int64_t pos = blk[blockIdx.x] + block_excl_scan(c, wt, &tot);
+    for (int j = 0; j < kCompactWords; ++j)
+        for (uint32_t m = wv[j]; m; m &= m - 1, ++pos)
+            if (pos < cap) list[pos] = (w0 + j) * 32 + (__ffs(m) - 1);
+}
+
 __global__ void __launch_bounds__(256)
 k_hss_count(HssArgs a)
 {
@@ -1420,11 +1768,12 @@ cudaError_t sv_copy(const SVec<T> &dst, const SVec<T> &src, int num_sms, cudaStr
 
 template <typename T>
 cudaError_t sv_excite(const SVec<T> &x, const SvOpArgs &o, int k, int nc, double theta,
-                      int num_sms, cudaStream_t st)
+                      int num_sms, cudaStream_t st, bool closed)
 {
     const T c = T(std::cos(theta)), s = T(std::sin(theta));
     for (int ci = 0; ci < nc; ++ci) {
-        k_sv_excite<T><<<sv_grid(sv_n(x), num_sms), 256, 0, st>>>(x, o, k, ci, c, s);
+        k_sv_excite<T><<<sv_grid(sv_n(x), num_sms), 256, 0, st>>>(x, o, k, ci, c, s,
+                                                                  closed ? 1 : 0);
         hy::count_launch();
     }
     return cudaGetLastError();
@@ -1490,6 +1839,47 @@ cudaError_t hpsi_scatter(const SparseArgs<T> &a, int num_sms, cudaStream_t st)
     if (g > int64_t(num_sms) * 32) g = int64_t(num_sms) * 32;
     if (g < 1) g = 1;
     k_hpsi_scatter<T><<<unsigned(g), 256, 0, st>>>(a); hy::count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t bits_compact(const uint32_t *bits, int64_t words, int64_t *list, int64_t cap,
+                         unsigned long long *cnt, int64_t *blk, cudaStream_t st)
+{
+    const int64_t nb = bits_compact_blocks(words);
+    k_bits_count<<<unsigned(nb), kCompactThreads, 0, st>>>(bits, words, blk); hy::count_launch();
+    k_blk_scan<<<1, 1024, 0, st>>>(blk, nb, cnt); hy::count_launch();
+    k_bits_emit<<<unsigned(nb), kCompactThreads, 0, st>>>(bits, words, blk, list, cap);
+    hy::count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t hpsi_support(const SupRowsArgs<T> &a, int num_sms, cudaStream_t st)
+{
+    const SparseArgs<T> &h = a.s;
+    if (h.nexa > 64 || h.n > 16) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(a.ctr, 0, 4 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.flagA, 0, size_t(h.Na), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.flagB, 0, size_t(h.Nb), st);
+    if (e != cudaSuccess) return e;
+    int64_t g = (a.cap + 255) / 256;
+    if (g > int64_t(num_sms) * 8) g = int64_t(num_sms) * 8;
+    if (g < 1) g = 1;
+    k_sup_runs<<<unsigned(g), 256, 0, st>>>(a.list, a.cnt, a.cap, h.Nb, a.runs, a.ralpha,
+                                             a.flagA, a.flagB, a.ctr);
+    hy::count_launch();
+    k_sup_blist<<<unsigned(num_sms), 256, 0, st>>>(a.flagB, h.Nb, a.blist, a.ctr);
+    hy::count_launch();
+    const size_t sa = sup_alpha_smem<T>(h.Nb, h.n * h.n), sb = size_t(h.Na) * sizeof(T);
+    e = cudaFuncSetAttribute(k_sup_alpha<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sa));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sup_beta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sb));
+    if (e != cudaSuccess) return e;
+    const unsigned per_sm = sizeof(T) == 8 ? 1u : 2u;
+    k_sup_alpha<T><<<unsigned(num_sms) * per_sm, kSupThreads, sa, st>>>(a);
+    hy::count_launch();
+    k_sup_beta<T><<<unsigned(num_sms) * per_sm, kSupThreads, sb, st>>>(a);
+    hy::count_launch();
     return cudaGetLastError();
 }
 
@@ -1583,6 +1973,8 @@ template cudaError_t support<float>(const float *, int64_t, int64_t *, int64_t,
                                     unsigned long long *, int, cudaStream_t);
 template cudaError_t hpsi_scatter<double>(const SparseArgs<double> &, int, cudaStream_t);
 template cudaError_t hpsi_scatter<float>(const SparseArgs<float> &, int, cudaStream_t);
+template cudaError_t hpsi_support<double>(const SupRowsArgs<double> &, int, cudaStream_t);
+template cudaError_t hpsi_support<float>(const SupRowsArgs<float> &, int, cudaStream_t);
 cudaError_t prog_compile_big(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
                              const SvOpArgs &o, const int32_t *ops, int L, const uint32_t *bits,
                              int64_t *key, int32_t *tab, int32_t *idx_map, int *flag,
@@ -1652,7 +2044,7 @@ template cudaError_t grad_sparse<float>(const SparseGradArgs<float> &, int, cuda
     template cudaError_t sv_reset<T>(const SVec<T> &, bool, int, cudaStream_t);              \
     template cudaError_t sv_copy<T>(const SVec<T> &, const SVec<T> &, int, cudaStream_t);   \
     template cudaError_t sv_excite<T>(const SVec<T> &, const SvOpArgs &, int, int, double,  \
-                                      int, cudaStream_t);                                    \
+                                      int, cudaStream_t, bool);                              \
     template cudaError_t sv_prepare<T>(const SVec<T> &, const SvOpArgs &, const int32_t *,  \
                                        const double *, int, bool, double *, int64_t *,      \
                                        cudaStream_t);                                        \

@@ -347,3 +347,52 @@ def test_support_program_beyond_shared_memory(dt):
             assert np.abs(g - g_ref).max() < 1e-4 * max(1.0, np.abs(g_ref).max())
             assert np.abs(g - g_d).max() < 1e-4 * max(1.0, np.abs(g_ref).max())
             assert np.abs(psi - p_ref).max() < 1e-5
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32], ids=["f64", "f32"])
+def test_support_sigma_beyond_programs(dt):
+    """24 qubits, an ansatz whose support exceeds the support programs'
+    65,536 determinants: from the second evaluation on, sigma is formed on
+    psi's support only (rows of the support list against the listed
+    determinants, no atomics) and the gradient comes from the reverse sweep
+    started on that restricted sigma.  Energy, gradient and state against
+    the oracle at several angles (double 1e-10 / 1e-9 / 1e-12; float 2e-6 /
+    1e-4 / 1e-5 relative), and the screen that follows (which needs all of
+    sigma) against the oracle's screen."""
+    import oracle.adapt as oadapt
+    import paper_2604_01176_gb300 as hy
+    ref, ham, pool = system(12, 6, 6, 1006)
+    opd = ref.pool()
+    ops, th, m = _ansatz_with_support(ref, 65536, ham.n_det // 4, 300)
+    prec = "f64" if dt == torch.float64 else "mixed"
+    ad = hy.Adapt(ham, pool, prec, max_iter=16, sparse=True, sparse_cap=ham.n_det)
+    ad.set_ansatz(ops, th)
+    rng = np.random.default_rng(11)
+    for rep in range(3):
+        t = th + (0 if rep == 0 else rng.normal(0, 0.2, len(th)))
+        e, g = ad.evaluate(t, dt)
+        if rep == 0:
+            e, g = ad.evaluate(t, dt)      # the support is known: restricted sigma
+        e_ref, g_ref = oadapt.energy_and_gradient(ref, opd, ops, t)
+        psi = ad.state(dt).double().cpu().numpy()
+        p_ref = oadapt.prepare(ref, opd, ops, t)
+        assert int(np.count_nonzero(p_ref)) == m
+        if dt == torch.float64:
+            assert abs(e - e_ref) < 1e-10
+            assert np.abs(g - g_ref).max() < 1e-9
+            assert np.abs(psi - p_ref).max() < 1e-12
+        else:
+            scale = max(1.0, abs(e_ref))
+            assert abs(e - e_ref) < 2e-6 * scale
+            assert np.abs(g - g_ref).max() < 1e-4 * max(1.0, np.abs(g_ref).max())
+            assert np.abs(psi - p_ref).max() < 1e-5
+    if dt == torch.float64:
+        # one ADAPT step from this ansatz: its screen reads all of sigma
+        ad.set_ansatz(ops, th)
+        r = ad.step()
+        p_ref = oadapt.prepare(ref, opd, ops, th)
+        g_scr = ref.gradients(opd, p_ref, ref.sigma(p_ref))
+        best = np.abs(g_scr)
+        assert r["selected"] == int(np.argmax(best)) or \
+            best[r["selected"]] >= best.max() * (1 - 1e-9)
+        assert abs(r["max_grad"] - best.max()) < 1e-9
