@@ -257,11 +257,13 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     // support only: without it the gradient reads sigma beyond the support)
     const bool use_hss = prog_run && hy::prog_hss_ready(a->prog) && a->prog_grad_ok &&
                          !a->want_full_sigma;
-    // beyond the support programs the gradient is the reverse sweep, which
-    // reads sigma only through inner products with d psi / d theta_l, vectors
-    // inside psi's support: sigma is formed on that support alone, without
-    // atomics (rows of psi's list against the listed determinants)
-    const bool on_support = !use_hss && !a->prep_small && !a->want_full_sigma && L > 0;
+    // the energy and the gradients read sigma only through inner products
+    // with psi and with d psi / d theta_l, vectors inside psi's support: sigma
+    // is formed on that support alone, without atomics (rows of psi's list
+    // against the listed determinants).  Only the screen (and the general
+    // single-CTA forward gradient, which re-forms sigma in full when it
+    // runs) read it beyond
+    const bool on_support = !use_hss && !a->want_full_sigma && L > 0;
     const double est = double(std::max<int64_t>(a->sparse_m_last[d], 1)) * double(a->conn);
     // all of sigma: by the scatter, or by the dense sweep over psi's array
     // (zero off the support) once the scatter's atomics cost more
@@ -400,6 +402,20 @@ hy_status gradient_dense(hy_adapt *a, const std::vector<double> &th, hy_dtype dt
     return cu(cudaStreamSynchronize(st), "sync");
 }
 
+// sigma = H psi in full for the sparse psi of the last evaluation in dt (whose
+// sigma was formed on psi's support only), by the scatter
+hy_status full_sigma_sparse(hy_adapt *a, int d, cudaStream_t st)
+{
+    hy::SparseState *S = a->ss[d][0], *G = a->ss[d][3];
+    HY_TRY(hy::sstate_reset(G, !a->ss_clean[d][3], false, st));
+    a->ss_clean[d][3] = false;
+    HY_TRY(hy::sstate_apply_h(S, nullptr, a->buf[d][1], st));
+    a->sig_support[d] = false;
+    a->sig_listed[d] = false;
+    a->sigma_full[d] = true;
+    return HY_OK;
+}
+
 // adjoint gradient at the point of the last energy() call in dt:
 // dE/dtheta_l = 2 <lam_l | A_l phi_l> with phi_l = U_l..U_1|HF> and lam_l =
 // U_{l+1}^dag..U_L^dag H psi, both walked back from (psi, H psi).  After a
@@ -426,7 +442,11 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
         return HY_OK;
     }
     if (a->prep_small && a->sparse_m <= kForwardSmall) {
-        // small support: the whole gradient in forward mode in one launch
+        // small support: the whole gradient in forward mode in one launch.
+        // Its vectors may leave the support (a generator of several
+        // constituents from an element a later constituent listed), so it
+        // reads sigma in full
+        if (a->sig_support[d]) HY_TRY(full_sigma_sparse(a, d, st));
         if (!a->ss_clean[d][1]) HY_TRY(hy::sstate_reset(F, true, false, st));
         if (!a->ss_clean[d][2]) HY_TRY(hy::sstate_reset(L, true, false, st));
         a->ss_clean[d][1] = a->ss_clean[d][2] = true;
