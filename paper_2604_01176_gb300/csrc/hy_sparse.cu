@@ -1179,8 +1179,9 @@ k_prog_grad(const int64_t *__restrict__ key, const int32_t *__restrict__ tab, in
 // (key[t] = (determinant << 8) | birth, as above, unsorted), an index map
 // over Omega_CIk gives each listed determinant its local index (read only
 // where the listing's membership bitmap has the determinant), and the
-// vectors live in a global scratch the size of the support, which stays in
-// L2.  Same tables, same arithmetic, same order of operations per element.
+// vectors are split over the shared memories of a thread-block cluster
+// (below).  Same tables, same arithmetic, same order of operations per
+// element.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_prog_keys_big(const int64_t *__restrict__ list, int64_t m, const int64_t *__restrict__ step_len,
