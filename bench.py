@@ -702,11 +702,14 @@ def run_ours(args, rank, world):
 # kernels behind each class of the library's event profiler
 CLASS_KERNELS = {
     "hpsi": "k_spmm + k_transpose + k_add_transposed + coupling (dense H|psi>)",
-    "hpsi_sparse": "sigma memset + k_hpsi_scatter (scatter H|psi>)",
+    "hpsi_sparse": "sparse H|psi>: k_hpsi_scatter (all of sigma, after a memset), "
+                   "k_hss_apply (the stored support Hamiltonian), k_sup_alpha + k_sup_beta "
+                   "(rows of the support)",
     "excite": "k_excite / k_excite_n (dense pair rotations: 4 s bytes per pair)",
-    "sparse_excite": "k_sv_excite, k_sv_prepare, k_prog_prepare (sparse-state rotations)",
+    "sparse_excite": "k_sv_excite, k_sv_prepare, support programs k_prog_prepare[_big] + "
+                     "k_prog_grad[_big] and their compilation, H_SS build",
     "screen": "k_grad_partial + k_grad_final (dense pool gradients)",
-    "screen_sparse": "k_grad_sparse + k_grad_sparse_final, k_prog_grad (support-restricted "
+    "screen_sparse": "k_grad_sparse + k_grad_sparse_final (support-restricted pool "
                      "gradients)",
     "reduce": "dots, norms, renormalisation",
     "features": "k_pair_weights + k_pair_contract + k_pair_reduce + occupations + k_features",
