@@ -247,6 +247,37 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
             HY_TRY(hy::sstate_scale_rsqrt(S, a->d_n2, st));
         }
     }
+    // a new ansatz whose structural preparation has just been queued: read
+    // its support's size, then compile its support program and support
+    // Hamiltonian before sigma, so that already this first evaluation's sigma
+    // is H_SS psi (the program's gradient flag comes back with the energy)
+    bool compiled = false;
+    int *h_flag = reinterpret_cast<int *>(&a->h_cnt[2]);
+    if (prog_build) {
+        HY_TRY(xfer(a, &a->h_cnt[0], hy::sstate_count(S), sizeof(int64_t), cudaMemcpyDeviceToHost,
+                    st, "support count"));
+        HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+        const int64_t c0 = a->h_cnt[0];
+        if (c0 > hy::sstate_cap(S)) {
+            *ok = false;
+            a->ss_clean[d][0] = false;
+            a->prog_support[d] = false;
+            return HY_OK;
+        }
+        if (c0 <= kPrepareSmall) {
+            HY_TRY(hy::prog_compile(a->prog, S, c0, a->p, a->d_ops, int64_t(L), steps, st));
+            HY_TRY(hy::prog_build_hss(a->prog, S, kHssMaxEntries, st));
+            *h_flag = 1;
+            HY_TRY(xfer(a, h_flag, hy::prog_flag(a->prog), sizeof(int), cudaMemcpyDeviceToHost, st,
+                        "support program check"));
+            a->prog_ops = a->ops;
+            a->prog_m = c0;
+            a->prog_grad_ok = false;            // until the flag is read
+            a->prog_support[0] = a->prog_support[1] = false;
+            a->prog_support[d] = true;
+            compiled = true;
+        }
+    }
     // sigma: within a compiled ansatz the energy and the forward gradients
     // read it on psi's support only, so the support Hamiltonian forms just
     // that part; otherwise the scatter forms all of it.  List sigma's
@@ -255,8 +286,8 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     // operator) is caught below and costs only the listing
     // (the program's forward gradient is the one that reads sigma on the
     // support only: without it the gradient reads sigma beyond the support)
-    const bool use_hss = prog_run && hy::prog_hss_ready(a->prog) && a->prog_grad_ok &&
-                         !a->want_full_sigma;
+    const bool use_hss = (prog_run || compiled) && hy::prog_hss_ready(a->prog) &&
+                         (compiled || a->prog_grad_ok) && !a->want_full_sigma;
     // the energy and the gradients read sigma only through inner products
     // with psi and with d psi / d theta_l, vectors inside psi's support: sigma
     // is formed on that support alone, without atomics (rows of psi's list
@@ -310,18 +341,8 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
         a->prog_support[d] = false;
         return HY_OK;
     }
-    if (prog_build && cnt[0] <= kPrepareSmall) {
-        HY_TRY(hy::prog_compile(a->prog, S, cnt[0], a->p, a->d_ops, int64_t(L), steps, st));
-        HY_TRY(hy::prog_build_hss(a->prog, S, kHssMaxEntries, st));
-        int flag = 1;
-        HY_TRY(xfer(a, &flag, hy::prog_flag(a->prog), sizeof(int), cudaMemcpyDeviceToHost, st,
-                    "support program check"));
-        HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
-        a->prog_ops = a->ops;
-        a->prog_m = cnt[0];
-        a->prog_grad_ok = flag == 0;
-        a->prog_support[0] = a->prog_support[1] = false;
-        a->prog_support[d] = true;
+    if (compiled) {
+        a->prog_grad_ok = *h_flag == 0;
     } else if (a->prep_small && !prog_run && L > 0 && a->prog_ops == a->ops) {
         // a structural preparation of the compiled ansatz lists the same support
         a->prog_support[d] = cnt[0] == a->prog_m;
@@ -446,7 +467,7 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
         // Its vectors may leave the support (a generator of several
         // constituents from an element a later constituent listed), so it
         // reads sigma in full
-        if (a->sig_support[d]) HY_TRY(full_sigma_sparse(a, d, st));
+        if (!a->sigma_full[d]) HY_TRY(full_sigma_sparse(a, d, st));
         if (!a->ss_clean[d][1]) HY_TRY(hy::sstate_reset(F, true, false, st));
         if (!a->ss_clean[d][2]) HY_TRY(hy::sstate_reset(L, true, false, st));
         a->ss_clean[d][1] = a->ss_clean[d][2] = true;
@@ -465,6 +486,9 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
         if (cnt[1] > hy::sstate_cap(L)) a->ss_clean[d][2] = false;
         return gradient_dense(a, th, dt, st, g);
     }
+    // sigma formed by the support Hamiltonian for a program whose own
+    // gradient cannot serve: the reverse sweep needs it in full
+    if (!a->sigma_full[d] && !a->sig_support[d]) HY_TRY(full_sigma_sparse(a, d, st));
     void *sigma = a->buf[d][1], *lam = a->buf[d][3];
     HY_TRY(hy::sstate_reset(F, !a->ss_clean[d][1], false, st));
     a->ss_clean[d][1] = true;
