@@ -2129,13 +2129,14 @@ struct SupportProgram {
     int32_t *tab_big = nullptr, *idx_map = nullptr;
     // H restricted to the program's support (rows in key order, columns as
     // determinant indices): valid while hss_ok
-    int64_t *hss_ptr = nullptr;
+    // (row t's entries at [t * hss_w, t * hss_w + hss_cnt[t]))
     int32_t *hss_cnt = nullptr;
     uint32_t *hss_col = nullptr;
     double *hss_val = nullptr;
-    int64_t hss_cap = 0, hss_nnz = 0;
+    int64_t hss_cap = 0, hss_w = 0;
     bool hss_ok = false;
-    int64_t *h_nnz = nullptr;     // pinned readback slot
+    int64_t *d_nnz = nullptr;     // the entries' total (device) ...
+    int64_t *h_nnz = nullptr;     // ... copied to a pinned slot, valid after the next sync
 };
 
 hy_status prog_create(const hy_ham *h, int max_steps, SupportProgram **out)
@@ -2170,7 +2171,7 @@ void prog_destroy(SupportProgram *g)
     cudaFree(g->key_big);
     cudaFree(g->tab_big);
     cudaFree(g->idx_map);
-    cudaFree(g->hss_ptr);
+    cudaFree(g->d_nnz);
     cudaFree(g->hss_cnt);
     cudaFree(g->hss_col);
     cudaFree(g->hss_val);
@@ -2250,36 +2251,36 @@ hy_status prog_build_hss(SupportProgram *g, const SparseState *s, int64_t max_nn
     const hy_ham *h = g->h;
     cudaStream_t st = as_stream(stream);
     g->hss_ok = false;
+    if (!g->hss_w) {
+        // a row's couplings: its CSR rows of both spins, then the
+        // (1 + nexa) x (1 + nexb) grid of alpha-beta terms
+        int64_t wa = 0, wb = 0;
+        for (size_t r = 0; r + 1 < h->kt.Ma.ptr.size(); ++r)
+            wa = std::max<int64_t>(wa, h->kt.Ma.ptr[r + 1] - h->kt.Ma.ptr[r]);
+        for (size_t r = 0; r + 1 < h->kt.Mb.ptr.size(); ++r)
+            wb = std::max<int64_t>(wb, h->kt.Mb.ptr[r + 1] - h->kt.Mb.ptr[r]);
+        g->hss_w = wa + wb + int64_t(h->A.nex + 1) * (h->B.nex + 1);
+    }
+    const int64_t need = g->m * g->hss_w;
+    if (need > max_nnz) return HY_OK;              // too large to pay off: not built
     cudaError_t e = cudaSuccess;
     const size_t kb = size_t(hy::k::kProgBig);
-    if (!g->hss_ptr) e = cudaMalloc(&g->hss_ptr, (kb + 1) * sizeof(int64_t));
-    if (e == cudaSuccess && !g->hss_cnt) e = cudaMalloc(&g->hss_cnt, kb * sizeof(int32_t));
-    if (e == cudaSuccess && !g->h_nnz) e = cudaMallocHost(&g->h_nnz, sizeof(int64_t));
+    if (!g->hss_cnt) e = cudaMalloc(&g->hss_cnt, kb * sizeof(int32_t));
+    if (e == cudaSuccess && !g->d_nnz) e = cudaMalloc(&g->d_nnz, sizeof(int64_t));
+    if (e == cudaSuccess && !g->h_nnz) {
+        e = cudaMallocHost(&g->h_nnz, sizeof(int64_t));
+        if (e == cudaSuccess) *g->h_nnz = 0;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(support Hamiltonian)");
-    hy::k::HssArgs a;
-    a.key = prog_keys(g);
-    a.m = g->m;
-    a.bits = s->bits;
-    a.Ma_ptr = h->Ma64.ptr; a.Ma_col = h->Ma64.col; a.Ma_val = h->Ma64.val;
-    a.Mb_ptr = h->Mb64.ptr; a.Mb_col = h->Mb64.col; a.Mb_val = h->Mb64.val;
-    a.V = h->d_V64;
-    a.aex = h->d_aex; a.bexT = h->d_bexT; a.astr = h->d_astr; a.bstr = h->d_bstr;
-    a.n = h->n; a.nexa = h->A.nex; a.nexb = h->B.nex; a.Nb = h->Nb;
-    a.ptr = g->hss_ptr; a.cnt = g->hss_cnt; a.col = nullptr; a.val = nullptr;
-    hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
-    HY_CUDA(hy::k::hss_count(a, h->num_sms, st), "support Hamiltonian count");
-    HY_CUDA(cudaMemcpyAsync(g->h_nnz, g->hss_ptr + g->m, sizeof(int64_t), cudaMemcpyDeviceToHost,
-                            st), "support Hamiltonian size");
-    HY_CUDA(cudaStreamSynchronize(st), "sync");
-    const int64_t nnz = *g->h_nnz;
-    if (nnz > max_nnz) return HY_OK;              // too large to pay off: not built
-    if (nnz > g->hss_cap) {
+    if (need > g->hss_cap) {
+        // queued applies may still read the old arrays
+        HY_CUDA(cudaStreamSynchronize(st), "sync");
         cudaFree(g->hss_col);
         cudaFree(g->hss_val);
         g->hss_col = nullptr;
         g->hss_val = nullptr;
         g->hss_cap = 0;
-        const int64_t cap = nnz + nnz / 4 + 1024;
+        const int64_t cap = need + need / 4 + 1024;
         e = cudaMalloc(&g->hss_col, size_t(cap) * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMalloc(&g->hss_val, size_t(cap) * sizeof(double));
         if (e != cudaSuccess) {
@@ -2290,10 +2291,20 @@ hy_status prog_build_hss(SupportProgram *g, const SparseState *s, int64_t max_nn
         }
         g->hss_cap = cap;
     }
-    a.col = g->hss_col;
-    a.val = g->hss_val;
-    HY_CUDA(hy::k::hss_fill(a, h->num_sms, st), "support Hamiltonian fill");
-    g->hss_nnz = nnz;
+    hy::k::HssArgs a;
+    a.key = prog_keys(g);
+    a.m = g->m;
+    a.bits = s->bits;
+    a.Ma_ptr = h->Ma64.ptr; a.Ma_col = h->Ma64.col; a.Ma_val = h->Ma64.val;
+    a.Mb_ptr = h->Mb64.ptr; a.Mb_col = h->Mb64.col; a.Mb_val = h->Mb64.val;
+    a.V = h->d_V64;
+    a.aex = h->d_aex; a.bexT = h->d_bexT; a.astr = h->d_astr; a.bstr = h->d_bstr;
+    a.n = h->n; a.nexa = h->A.nex; a.nexb = h->B.nex; a.Nb = h->Nb;
+    a.stride = g->hss_w; a.cnt = g->hss_cnt; a.col = g->hss_col; a.val = g->hss_val;
+    hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
+    HY_CUDA(hy::k::hss_fill(a, g->d_nnz, h->num_sms, st), "support Hamiltonian fill");
+    HY_CUDA(cudaMemcpyAsync(g->h_nnz, g->d_nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, st),
+            "support Hamiltonian size");
     g->hss_ok = true;
     return HY_OK;
 }
@@ -2306,17 +2317,21 @@ hy_status prog_hss_apply(const SupportProgram *g, const void *psi, void *sigma, 
     if (!g || !g->hss_ok || !psi || !sigma) return fail(HY_ERR_ARG, "bad arguments");
     cudaStream_t st = as_stream(stream);
     const double es = dt == HY_F64 ? 8.0 : 4.0;
-    hy::ProfScope prof(HY_PROF_HPSI_SPARSE, stream,
-                       double(g->hss_nnz) * 12.0 + 2.0 * double(g->m) * es,
-                       2.0 * double(g->hss_nnz));
+    // bytes: the stored entries (12 each) and psi / sigma on the support;
+    // the entry count is the pinned copy of the last build's total, read
+    // without waiting (an ansatz's first apply, queued right after its build,
+    // may count with the previous support's)
+    const double nnz = double(*g->h_nnz);
+    hy::ProfScope prof(HY_PROF_HPSI_SPARSE, stream, nnz * 12.0 + 2.0 * double(g->m) * es,
+                       2.0 * nnz);
     if (dt == HY_F64)
-        HY_CUDA(hy::k::hss_apply<double>(prog_keys(g), g->m, g->hss_ptr, g->hss_col, g->hss_val,
-                                         static_cast<const double *>(psi),
+        HY_CUDA(hy::k::hss_apply<double>(prog_keys(g), g->m, g->hss_cnt, g->hss_w, g->hss_col,
+                                         g->hss_val, static_cast<const double *>(psi),
                                          static_cast<double *>(sigma), g->h->num_sms, st),
                 "support Hamiltonian apply");
     else
-        HY_CUDA(hy::k::hss_apply<float>(prog_keys(g), g->m, g->hss_ptr, g->hss_col, g->hss_val,
-                                        static_cast<const float *>(psi),
+        HY_CUDA(hy::k::hss_apply<float>(prog_keys(g), g->m, g->hss_cnt, g->hss_w, g->hss_col,
+                                        g->hss_val, static_cast<const float *>(psi),
                                         static_cast<float *>(sigma), g->h->num_sms, st),
                 "support Hamiltonian apply");
     return HY_OK;

@@ -424,16 +424,18 @@ struct HssArgs {
     const uint32_t *aex, *bexT, *astr, *bstr;
     int n, nexa, nexb;
     int64_t Nb;
-    int64_t *ptr;            // [m + 1]
-    int32_t *cnt;            // [m]
-    uint32_t *col;           // [nnz]
-    double *val;             // [nnz]
+    int64_t stride;          // entries reserved per row (>= any row's couplings)
+    int32_t *cnt;            // [m] entries of each row
+    uint32_t *col;           // [m * stride]
+    double *val;             // [m * stride]
 };
-cudaError_t hss_count(const HssArgs &a, int num_sms, cudaStream_t st);
-cudaError_t hss_fill(const HssArgs &a, int num_sms, cudaStream_t st);
+// one pass: row t's entries at [t * stride, t * stride + cnt[t]), fixed
+// order; then *nnz (device) = their total
+cudaError_t hss_fill(const HssArgs &a, int64_t *nnz, int num_sms, cudaStream_t st);
 template <typename T>
-cudaError_t hss_apply(const int64_t *key, int64_t m, const int64_t *ptr, const uint32_t *col,
-                      const double *val, const T *psi, T *sigma, int num_sms, cudaStream_t st);
+cudaError_t hss_apply(const int64_t *key, int64_t m, const int32_t *cnt, int64_t stride,
+                      const uint32_t *col, const double *val, const T *psi, T *sigma, int num_sms,
+                      cudaStream_t st);
 
 // one CTA: g[l] = dE/dtheta_l of psi = U_L .. U_1|HF> in forward mode, f and
 // w scratch sparse vectors (clean), sigma = H psi dense; norm2 (device, or

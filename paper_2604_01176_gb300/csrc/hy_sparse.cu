@@ -1429,9 +1429,11 @@ k_prog_grad_big(const int64_t *__restrict__ key, const int32_t *__restrict__ tab
 // H restricted to a support (see HssArgs).  Row t enumerates the couplings of
 // its determinant d = (A, B) exactly as k_hpsi_scatter enumerates the targets
 // of d (H is real symmetric, so the column of d is its row), keeping those
-// whose determinant is in the support.  The enumeration is the same in the
-// counting and the filling pass and, per thread, in a fixed order; a block
-// scan of the per-thread counts places each thread's entries.
+// whose determinant is in the support.  Each row has a fixed slot of
+// `stride` entries (an upper bound of its couplings), so one launch builds the
+// whole matrix with no count pass and no host round trip: per row the block
+// counts each thread's entries, a block scan places them, and a second walk of
+// the same fixed-order enumeration writes them.
 // ---------------------------------------------------------------------------
 template <typename F>
 __device__ __forceinline__ void hss_enumerate(const HssArgs &a, int64_t A, int64_t B,
@@ -1597,26 +1599,6 @@ k_bits_emit(const uint32_t *__restrict__ bits, int64_t words, const int64_t *__r
 }
 
 __global__ void __launch_bounds__(256)
-k_hss_count(HssArgs a)
-{
-    __shared__ uint32_t aexs[64];
-    __shared__ int wt[8], tot;
-    for (int64_t t = blockIdx.x; t < a.m; t += gridDim.x) {
-        const int64_t d = a.key[t] >> 8;
-        const int64_t A = d / a.Nb, B = d % a.Nb;
-        __syncthreads();
-        if (int(threadIdx.x) < a.nexa) aexs[threadIdx.x] = a.aex[A * a.nexa + threadIdx.x];
-        __syncthreads();
-        int c = 0;
-        hss_enumerate(a, A, B, aexs, [&](int64_t o, double) {
-            if (member(a.bits, o)) ++c;
-        });
-        block_excl_scan(c, wt, &tot);
-        if (threadIdx.x == 0) a.cnt[t] = tot;
-    }
-}
-
-__global__ void __launch_bounds__(256)
 k_hss_fill(HssArgs a)
 {
     __shared__ uint32_t aexs[64];
@@ -1631,51 +1613,37 @@ k_hss_fill(HssArgs a)
         hss_enumerate(a, A, B, aexs, [&](int64_t o, double) {
             if (member(a.bits, o)) ++c;
         });
-        int64_t pos = a.ptr[t] + block_excl_scan(c, wt, &tot);
+        // row t owns entries [t * stride, (t + 1) * stride); stride bounds the
+        // enumeration's length, and no write passes the row's end
+        const int64_t row0 = t * a.stride, row1 = row0 + a.stride;
+        int64_t pos = row0 + block_excl_scan(c, wt, &tot);
         hss_enumerate(a, A, B, aexs, [&](int64_t o, double v) {
             if (member(a.bits, o)) {
-                a.col[pos] = uint32_t(o);
-                a.val[pos] = v;
+                if (pos < row1) {
+                    a.col[pos] = uint32_t(o);
+                    a.val[pos] = v;
+                }
                 ++pos;
             }
         });
+        if (threadIdx.x == 0) a.cnt[t] = int32_t(tot < a.stride ? tot : a.stride);
     }
 }
 
-// ptr[0] = 0, ptr[t + 1] = ptr[t] + cnt[t]: one block, chunks of 1024
+// *nnz = sum of cnt[0 .. m), one block, fixed order
 __global__ void __launch_bounds__(1024)
-k_hss_scan(const int32_t *__restrict__ cnt, int64_t m, int64_t *__restrict__ ptr)
+k_hss_total(const int32_t *__restrict__ cnt, int64_t m, int64_t *__restrict__ nnz)
 {
-    __shared__ int64_t wsum[32];
-    __shared__ int64_t carry;
-    if (threadIdx.x == 0) {
-        carry = 0;
-        ptr[0] = 0;
-    }
+    __shared__ long long wsum[32];
+    long long x = 0;
+    for (int64_t t = threadIdx.x; t < m; t += blockDim.x) x += cnt[t];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = x;
     __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int64_t base = 0; base < m; base += blockDim.x) {
-        const int64_t t = base + threadIdx.x;
-        int64_t x = t < m ? cnt[t] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[w] = x;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int64_t acc = 0;
-            for (int i = 0; i < int(blockDim.x >> 5); ++i) {
-                const int64_t v = wsum[i];
-                wsum[i] = acc;
-                acc += v;
-            }
-        }
-        __syncthreads();
-        if (t < m) ptr[t + 1] = carry + wsum[w] + x;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry += wsum[w] + x;
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        long long tot = 0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) tot += wsum[w];
+        *nnz = tot;
     }
 }
 
@@ -1683,8 +1651,8 @@ k_hss_scan(const int32_t *__restrict__ cnt, int64_t m, int64_t *__restrict__ ptr
 // a fixed-order warp sum
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_hss_apply(const int64_t *__restrict__ key, int64_t m, const int64_t *__restrict__ ptr,
-            const uint32_t *__restrict__ col, const double *__restrict__ val,
+k_hss_apply(const int64_t *__restrict__ key, int64_t m, const int32_t *__restrict__ cnt,
+            int64_t stride, const uint32_t *__restrict__ col, const double *__restrict__ val,
             const T *__restrict__ psi, T *__restrict__ sigma)
 {
     const int lane = threadIdx.x & 31;
@@ -1692,47 +1660,42 @@ k_hss_apply(const int64_t *__restrict__ key, int64_t m, const int64_t *__restric
     for (int64_t t = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); t < m;
          t += warps) {
         T acc = T(0);
-        for (int64_t e = ptr[t] + lane; e < ptr[t + 1]; e += 32)
+        const int64_t e1 = t * stride + cnt[t];
+        for (int64_t e = t * stride + lane; e < e1; e += 32)
             acc += T(val[e]) * psi[col[e]];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) sigma[key[t] >> 8] = acc;
     }
 }
 
-cudaError_t hss_count(const HssArgs &a, int num_sms, cudaStream_t st)
+cudaError_t hss_fill(const HssArgs &a, int64_t *nnz, int num_sms, cudaStream_t st)
 {
-    if (a.m < 1) return cudaSuccess;
-    int64_t g = a.m < int64_t(num_sms) * 16 ? a.m : int64_t(num_sms) * 16;
-    k_hss_count<<<unsigned(g), 256, 0, st>>>(a); hy::count_launch();
-    k_hss_scan<<<1, 1024, 0, st>>>(a.cnt, a.m, a.ptr); hy::count_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t hss_fill(const HssArgs &a, int num_sms, cudaStream_t st)
-{
-    if (a.m < 1) return cudaSuccess;
+    if (a.m < 1 || a.stride < 1) return cudaErrorInvalidValue;
     int64_t g = a.m < int64_t(num_sms) * 16 ? a.m : int64_t(num_sms) * 16;
     k_hss_fill<<<unsigned(g), 256, 0, st>>>(a); hy::count_launch();
+    k_hss_total<<<1, 1024, 0, st>>>(a.cnt, a.m, nnz); hy::count_launch();
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t hss_apply(const int64_t *key, int64_t m, const int64_t *ptr, const uint32_t *col,
-                      const double *val, const T *psi, T *sigma, int num_sms, cudaStream_t st)
+cudaError_t hss_apply(const int64_t *key, int64_t m, const int32_t *cnt, int64_t stride,
+                      const uint32_t *col, const double *val, const T *psi, T *sigma, int num_sms,
+                      cudaStream_t st)
 {
     if (m < 1) return cudaSuccess;
     int64_t g = (m + 7) / 8;
     if (g > int64_t(num_sms) * 16) g = int64_t(num_sms) * 16;
-    k_hss_apply<T><<<unsigned(g), 256, 0, st>>>(key, m, ptr, col, val, psi, sigma);
+    k_hss_apply<T><<<unsigned(g), 256, 0, st>>>(key, m, cnt, stride, col, val, psi, sigma);
     hy::count_launch();
     return cudaGetLastError();
 }
 
-template cudaError_t hss_apply<double>(const int64_t *, int64_t, const int64_t *,
+template cudaError_t hss_apply<double>(const int64_t *, int64_t, const int32_t *, int64_t,
                                        const uint32_t *, const double *, const double *,
                                        double *, int, cudaStream_t);
-template cudaError_t hss_apply<float>(const int64_t *, int64_t, const int64_t *, const uint32_t *,
-                                      const double *, const float *, float *, int, cudaStream_t);
+template cudaError_t hss_apply<float>(const int64_t *, int64_t, const int32_t *, int64_t,
+                                      const uint32_t *, const double *, const float *, float *,
+                                      int, cudaStream_t);
 
 namespace {
 // blocks for a list of about n entries (grid-stride loops cover any count)
