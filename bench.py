@@ -127,6 +127,9 @@ def parse():
                     help="--hmat row range 'b:e' in alpha strings, or 'all'")
     ap.add_argument("--hmat-dtypes", default="f32,f64", help="dtypes of --hmat")
     ap.add_argument("--reps", type=int, default=5, help="timed repetitions of --hmat")
+    ap.add_argument("--batch-rank", action="store_true",
+                    help="config 5: the 64-molecule batch with the ranker's top-M screened in "
+                         "one persistent launch, the full batched screen as judge")
     ap.add_argument("--batch", action="store_true",
                     help="64 molecules of 8-12 orbitals: H psi + energies of all in one persistent "
                          "graph-captured launch (autotuned tile) vs one launch sequence per molecule")
@@ -190,6 +193,120 @@ def batch_bench(args, count=64, reps=5):
                   "batched_launches": (l1 - l0) // reps, "looped_launches": (l3 - l2) // reps,
                   "molecules_per_s": round(count / (t_b / 1e3), 1),
                   "max_energy_diff_vs_looped": err}
+    print(json.dumps(out), flush=True)
+
+
+def batch_rank_bench(args, count=64, train_iters=3, reps=5):
+    """Config 5: the uneven 64-molecule batch with the learned ranker.  Each
+    molecule runs `train_iters` + 1 plain FP64 ADAPT iterations from
+    Hartree-Fock; the exact full screens of the states after iterations
+    1 .. train_iters train one MLP ranker (3 x 256) for the whole batch.  On
+    the states after the last iteration (held out) the batch then does, on
+    packed buffers: sigma = H psi in one persistent launch, the features of
+    every molecule's pool, one MLP inference over all operators, the top-32
+    per molecule, and the exact screen of those proposals in one persistent
+    launch; the full batched screen is the judge (its argmax per molecule
+    and its rank among the proposals).  Timings: CUDA events on the stream,
+    the ranked batch screen against the full batched screen and against a
+    loop of per-molecule full screens."""
+    import torch
+    import paper_2604_01176_gb300 as hy
+    from paper_2604_01176_gb300 import build as hybuild
+    hybuild.build()
+    hams, pools, states, train = [], [], [], []
+    for n, na, nb, seed in synth.batch_molecules(count):
+        h1, h2, ec = synth.integrals(n, seed)
+        ham = hy.Hamiltonian(h1, h2, ec, n, na, nb)
+        pool = hy.Pool(ham)
+        ad = hy.Adapt(ham, pool, "f64", max_iter=train_iters + 2)
+        for it in range(train_iters + 1):
+            ad.step()
+            if it < train_iters:
+                train.append((len(hams), ad.state(torch.float64)))
+        states.append(ad.state(torch.float64))
+        ad.close()
+        hams.append(ham)
+        pools.append(pool)
+    ranker = hy.Ranker(hidden=256, seed=7)
+    for m, x in train:
+        sig = hams[m].apply_h(x)
+        feat = hy.ranker_features(hams[m], pools[m], x, sigma=sig)
+        ranker.add_samples(feat, pools[m].gradients(x, sig))
+    loss = ranker.fit(epochs=30)
+    b = hy.Batch(hams)
+    b.set_pools(pools)
+    K = np.array([len(p) for p in pools])
+    poff = b.pool_offsets
+    M = args.top_m
+    st = torch.cuda.current_stream()
+    psi = b.pack(states, torch.float64)
+    sig = torch.zeros_like(psi)
+    feat = torch.empty((int(poff[-1]), 16), dtype=torch.float32, device="cuda")
+    prop = torch.empty(count * M, dtype=torch.int32, device="cuda")
+    poffs = torch.arange(count + 1, dtype=torch.int64, device="cuda") * M
+    psis, sigs = b.unpack(psi), b.unpack(sig)
+
+    def ranked():
+        b.apply_h(psi, sig, graph=True)
+        for m in range(count):
+            hy.ranker_features(hams[m], pools[m], psis[m], sigma=sigs[m],
+                               out=feat[int(poff[m]):int(poff[m + 1])])
+        score = ranker.predict(feat)
+        for m in range(count):
+            kk = min(M, int(K[m]))
+            prop[m * M:m * M + kk] = hy.topk(score[int(poff[m]):int(poff[m + 1])], kk)
+            if kk < M:                            # a pool smaller than M: repeat its first
+                prop[m * M + kk:(m + 1) * M] = prop[m * M]
+        return b.gradients(psi, sig, ops=prop, op_offsets=poffs)
+
+    def full():
+        b.apply_h(psi, sig, graph=True)
+        return b.gradients(psi, sig)
+
+    def looped():
+        out = []
+        for m in range(count):
+            y = hams[m].apply_h(psis[m])
+            out.append(pools[m].gradients(psis[m], y))
+        return out
+
+    times = {}
+    for name, fn in (("ranked", ranked), ("full", full), ("looped", looped)):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = hy.launch_count()
+        e0.record(st)
+        for _ in range(reps):
+            r = fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        times[name] = (e0.elapsed_time(e1) / reps, (hy.launch_count() - l0) // reps)
+    gp = ranked().cpu().numpy()
+    gf = full().cpu().numpy()
+    pr = prop.cpu().numpy()
+    hits, ranks, gaps = 0, [], []
+    for m in range(count):
+        gm = np.abs(gf[poff[m]:poff[m + 1]])
+        true = int(np.argmax(gm))
+        sub = pr[m * M:m * M + min(M, int(K[m]))]
+        pick = int(sub[int(np.argmax(np.abs(gp[m * M:m * M + len(sub)])))])
+        hits += pick == true
+        where = np.flatnonzero(sub == true)
+        ranks.append(int(where[0]) if where.size else -1)
+        gaps.append(float(gm[true] - gm[pick]) / max(gm[true], 1e-300))
+    out = {"batch_rank": f"{count} molecules, n = 8..12 at half filling, seeds 2000+i",
+           "determinants": int(sum(h.n_det for h in hams)), "operators": int(poff[-1]),
+           "train": {"states": len(train), "samples": ranker.info()["n_samples"],
+                     "final_loss": round(float(loss), 5)},
+           "top_m": M,
+           "selected_true_argmax": f"{hits} of {count}",
+           "true_argmax_rank_in_proposals": ranks,
+           "max_relative_gradient_shortfall": round(max(gaps), 4),
+           "ms": {k: round(v[0], 3) for k, v in times.items()},
+           "launches": {k: v[1] for k, v in times.items()},
+           "speedup_ranked_vs_full_batched": round(times["full"][0] / times["ranked"][0], 2),
+           "speedup_full_batched_vs_looped": round(times["looped"][0] / times["full"][0], 2)}
     print(json.dumps(out), flush=True)
 
 
@@ -1038,6 +1155,8 @@ def main():
         return ranker_eval(args)
     if args.batch:
         return batch_bench(args)
+    if args.batch_rank:
+        return batch_rank_bench(args)
     if args.hmat:
         return hmat_bench(args)
     if args.trajectory:

@@ -505,6 +505,30 @@ hy_status hy_batch_apply_h(hy_batch *b, const void *psi, void *sigma,
 hy_status hy_batch_graph_launch(hy_batch *b, const void *psi, void *sigma,
                                 hy_dtype dt, double *energies, void *stream);
 
+/* Batched pool-gradient screen (the paper's screen g_k = 2<H psi|A_k psi>,
+ * Numerical performance subsection, for many molecules at once).
+ * hy_batch_set_pools: pools[m] (host array of `count` handles, pool m built on
+ * the batch's Hamiltonian m) are attached to the batch; they must outlive it.
+ * hy_batch_pool_offsets: offsets (host, count + 1): where molecule m's
+ * gradients start in g of a full screen.
+ * hy_batch_gradients: g (device doubles) for every molecule's listed
+ * operators in one persistent launch over (molecule, operator, row chunk)
+ * tasks plus one summing kernel.  psi, sigma: packed states of dt (sigma =
+ * H psi, e.g. from hy_batch_apply_h).  ops = NULL: every operator of every
+ * pool, g packed by hy_batch_pool_offsets.  Otherwise ops (device int32) holds
+ * per-molecule lists of local pool indices, molecule m's at [op_offsets[m],
+ * op_offsets[m + 1]) of ops and of g, op_offsets a device array of count + 1
+ * entries, n_entries (host) = op_offsets[count].  An index outside its pool
+ * gives NaN for that entry and is reported (HY_ERR_ARG, with its position)
+ * by the next call on this batch.  No host synchronisation except when a
+ * larger call first grows the partial-sum workspace (make the first call of
+ * each size before capturing a CUDA graph). */
+hy_status hy_batch_set_pools(hy_batch *b, const hy_pool *const *pools);
+hy_status hy_batch_pool_offsets(const hy_batch *b, int64_t *offsets);
+hy_status hy_batch_gradients(hy_batch *b, const void *psi, const void *sigma,
+                             const int32_t *ops, const int64_t *op_offsets,
+                             int64_t n_entries, double *g, hy_dtype dt, void *stream);
+
 /* Autotuner: times every tile shape (gsize in 32..512, groups in 1..8,
  * within the shared-memory and barrier limits) on these buffers with CUDA
  * events (2 warm-up + 3 timed launches each), keeps the fastest as the

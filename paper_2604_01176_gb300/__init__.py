@@ -582,10 +582,15 @@ def occupations(ham: Hamiltonian, psi: torch.Tensor, stream=None) -> torch.Tenso
 
 def ranker_features(ham: Hamiltonian, pool: Pool, psi: torch.Tensor,
                     extra: torch.Tensor | None = None, sigma: torch.Tensor | None = None,
-                    stream=None) -> torch.Tensor:
-    """Per-operator ranker features, (K, 16) float32 on the device."""
+                    stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Per-operator ranker features, (K, 16) float32 on the device (into
+    `out` when given, e.g. a slice of a packed feature buffer)."""
     ham._check_state(psi, sigma)
-    out = torch.empty((len(pool), N_FEATURES), dtype=torch.float32, device=psi.device)
+    if out is None:
+        out = torch.empty((len(pool), N_FEATURES), dtype=torch.float32, device=psi.device)
+    elif out.dtype != torch.float32 or out.shape != (len(pool), N_FEATURES) \
+            or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 tensor of shape (K, 16)")
     if extra is not None:
         _require_cuda(extra)
         if extra.dtype != torch.float32 or extra.shape != (len(pool), 4):
@@ -759,6 +764,40 @@ class Batch:
         check(fn(self._b, _ptr(psi), _ptr(sigma), dtype_code(psi.dtype),
                  _ptr(energies) if energies is not None else None, stream_ptr(stream)))
         return sigma
+
+    def set_pools(self, pools):
+        """Attach one pool per molecule (pool m built on Hamiltonian m)."""
+        self.pools = list(pools)
+        arr = (ctypes.c_void_p * len(self.pools))(*[p.handle for p in self.pools])
+        check(_abi.load().hy_batch_set_pools(self._b, arr))
+        off = np.zeros(len(self.hams) + 1, dtype=np.int64)
+        check(_abi.load().hy_batch_pool_offsets(self._b, off.ctypes.data_as(ctypes.c_void_p)))
+        self.pool_offsets = off
+
+    def gradients(self, psi, sigma, ops=None, op_offsets=None, out=None, stream=None):
+        """Pool gradients of every molecule in one persistent launch: all
+        operators (packed by `pool_offsets`), or per-molecule lists of local
+        pool indices `ops` (device int32) with `op_offsets` (device int64,
+        molecules + 1 entries; molecule m's entries at [op_offsets[m],
+        op_offsets[m + 1]))."""
+        self._check(psi, sigma, None)
+        if ops is None:
+            n = int(self.pool_offsets[-1])
+        else:
+            _require_cuda(ops, op_offsets)
+            if ops.dtype != torch.int32 or op_offsets.dtype != torch.int64 \
+                    or op_offsets.numel() != len(self.hams) + 1:
+                raise ValueError("ops must be int32, op_offsets int64 with molecules + 1 entries")
+            n = ops.numel()
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=psi.device)
+        if out.dtype != torch.float64 or out.numel() < n:
+            raise ValueError("out must be float64 with room for every entry")
+        check(_abi.load().hy_batch_gradients(
+            self._b, _ptr(psi), _ptr(sigma), _ptr(ops) if ops is not None else None,
+            _ptr(op_offsets) if ops is not None else None, n, _ptr(out),
+            dtype_code(psi.dtype), stream_ptr(stream)))
+        return out
 
     @property
     def tile(self) -> dict:

@@ -128,6 +128,9 @@ SIGNATURES = {
     "hy_batch_apply_h": (I32, [P, P, P, I32, P, P]),
     "hy_batch_graph_launch": (I32, [P, P, P, I32, P, P]),
     "hy_batch_tune": (I32, [P, P, P, I32, P, P, P]),
+    "hy_batch_set_pools": (I32, [P, P]),
+    "hy_batch_pool_offsets": (I32, [P, P]),
+    "hy_batch_gradients": (I32, [P, P, P, P, P, I64, P, I32, P]),
     "hy_occupations": (I32, [P, P, I32, P, P]),
     "hy_ranker_features": (I32, [P, P, P, P, I32, P, P, P]),
     "hy_touched_weights": (I32, [P, P, I32, P, P]),

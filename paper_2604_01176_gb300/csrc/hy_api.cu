@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "hy_internal.h"
@@ -166,6 +167,14 @@ struct hy_batch {
     double *g_energies = nullptr;
     int g_dt = -1;
     hy_batch_tile g_tile{0, 0, 0};
+    // pool screen (hy_batch_set_pools / hy_batch_gradients)
+    std::vector<const hy_pool *> pools;
+    std::vector<int64_t> pool_base;            // count + 1: full-screen entries
+    hy::k::BatchPool *d_pools = nullptr;
+    int64_t *d_pool_base = nullptr;
+    double *d_gpart = nullptr;
+    int64_t n_gpart = 0;
+    unsigned long long *d_gctr = nullptr, *d_gbad = nullptr, *h_gbad = nullptr;
 };
 
 namespace {
@@ -1784,7 +1793,121 @@ hy_status hy_batch_destroy(hy_batch *b)
     cudaFree(b->d_row_energy);
     cudaFree(b->d_base);
     cudaFree(b->d_rows);
+    cudaFree(b->d_pools);
+    cudaFree(b->d_pool_base);
+    cudaFree(b->d_gpart);
+    cudaFree(b->d_gctr);
+    cudaFree(b->d_gbad);
+    cudaFreeHost(b->h_gbad);
     delete b;
+    return HY_OK;
+}
+
+hy_status hy_batch_set_pools(hy_batch *b, const hy_pool *const *pools)
+{
+    if (!b || !pools) return fail(HY_ERR_ARG, "NULL argument");
+    const int count = int(b->hams.size());
+    std::vector<hy::k::BatchPool> mp(count);
+    std::vector<int64_t> base(count + 1, 0);
+    for (int m = 0; m < count; ++m) {
+        const hy_pool *p = pools[m];
+        if (!p || p->h != b->hams[m])
+            return fail(HY_ERR_ARG, "pool m must be built on the batch's Hamiltonian m");
+        const hy_ham *h = b->hams[m];
+        hy::k::BatchPool &q = mp[m];
+        q.opd = p->d_op; q.cons = p->d_cons;
+        q.aent = p->d_aent; q.bent = p->d_bent;
+        q.aoff = p->d_aoff; q.acnt = p->d_acnt; q.boff = p->d_boff; q.bcnt = p->d_bcnt;
+        q.Na = h->Na; q.Nb = h->Nb; q.off = b->offsets[m]; q.K = int64_t(p->ops.size());
+        base[m + 1] = base[m] + q.K;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!b->d_pools) e = cudaMalloc(&b->d_pools, size_t(count) * sizeof(hy::k::BatchPool));
+    if (e == cudaSuccess && !b->d_pool_base)
+        e = cudaMalloc(&b->d_pool_base, size_t(count + 1) * sizeof(int64_t));
+    if (e == cudaSuccess && !b->d_gctr) e = cudaMalloc(&b->d_gctr, sizeof(unsigned long long));
+    if (e == cudaSuccess && !b->d_gbad) e = cudaMalloc(&b->d_gbad, sizeof(unsigned long long));
+    if (e == cudaSuccess && !b->h_gbad) e = cudaMallocHost(&b->h_gbad, sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_pools, mp.data(), size_t(count) * sizeof(hy::k::BatchPool),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_pool_base, base.data(), size_t(count + 1) * sizeof(int64_t),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->d_gbad, 0xFF, sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(e, "batch pools");
+    *b->h_gbad = ~0ull;
+    b->pools.assign(pools, pools + count);
+    b->pool_base = base;
+    return HY_OK;
+}
+
+hy_status hy_batch_pool_offsets(const hy_batch *b, int64_t *offsets)
+{
+    if (!b || !offsets) return fail(HY_ERR_ARG, "NULL argument");
+    if (b->pools.empty()) return fail(HY_ERR_ARG, "no pools set (hy_batch_set_pools)");
+    std::copy(b->pool_base.begin(), b->pool_base.end(), offsets);
+    return HY_OK;
+}
+
+hy_status hy_batch_gradients(hy_batch *b, const void *psi, const void *sigma, const int32_t *ops,
+                             const int64_t *op_offsets, int64_t n_entries, double *g, hy_dtype dt,
+                             void *stream)
+{
+    if (!b || !psi || !sigma || !g || !valid_dtype(dt)) return fail(HY_ERR_ARG, "bad arguments");
+    if (b->pools.empty()) return fail(HY_ERR_ARG, "no pools set (hy_batch_set_pools)");
+    if (ops && (!op_offsets || n_entries < 0)) return fail(HY_ERR_ARG, "operator lists need offsets");
+    // a refused entry of the previous call's lists (read after that call's
+    // stream work finished)
+    if (*b->h_gbad != ~0ull) {
+        const unsigned long long v = *b->h_gbad;
+        *b->h_gbad = ~0ull;
+        cudaMemset(b->d_gbad, 0xFF, sizeof(unsigned long long));
+        return fail(HY_ERR_ARG, "operator index out of range at entry " +
+                                    std::to_string(v >> 32) + ": " +
+                                    std::to_string(int32_t(uint32_t(v))));
+    }
+    const int64_t n = ops ? n_entries : b->pool_base.back();
+    if (n == 0) return HY_OK;
+    cudaStream_t st = as_stream(stream);
+    int64_t ch = (int64_t(8) * b->num_sms + n - 1) / n;
+    if (ch < 1) ch = 1;
+    if (ch > 256) ch = 256;
+    if (n * ch > b->n_gpart) {
+        // before any graph capture: the first call of a size allocates
+        HY_CUDA(cudaStreamSynchronize(st), "sync");
+        cudaFree(b->d_gpart);
+        b->d_gpart = nullptr;
+        b->n_gpart = 0;
+        HY_CUDA(cudaMalloc(&b->d_gpart, size_t(n * ch) * sizeof(double)), "cudaMalloc(partials)");
+        b->n_gpart = n * ch;
+    }
+    hy::ProfScope prof(HY_PROF_SCREEN, stream, 0.0);
+    auto run = [&](auto *tag) -> cudaError_t {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        hy::k::BatchGradArgs<T> a;
+        a.mols = b->d_pools;
+        a.count = int(b->hams.size());
+        a.psi = static_cast<const T *>(psi);
+        a.sigma = static_cast<const T *>(sigma);
+        a.ops = ops;
+        a.base = ops ? op_offsets : b->d_pool_base;
+        a.CH = int(ch);
+        a.n_tasks = n * ch;
+        a.partials = b->d_gpart;
+        a.g = g;
+        a.counter = b->d_gctr;
+        a.bad = b->d_gbad;
+        cudaError_t e = hy::k::batch_grad<T>(a, 8 * b->num_sms, st);
+        if (e == cudaSuccess && ops)
+            e = cudaMemcpyAsync(b->h_gbad, b->d_gbad, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, st);
+        return e;
+    };
+    if (dt == HY_F64)
+        HY_CUDA(run(static_cast<double *>(nullptr)), "batched pool gradients");
+    else
+        HY_CUDA(run(static_cast<float *>(nullptr)), "batched pool gradients");
     return HY_OK;
 }
 

@@ -200,6 +200,118 @@ __global__ void k_batch_energy(const double *__restrict__ row_energy,
     energies[mol] = s;
 }
 
+// ---------------------------------------------------------------------------
+// Batched pool-gradient screen: g_k = 2 <sigma|A_k psi> for listed operators
+// of many molecules in one persistent launch.  A task is one row chunk of one
+// (molecule, operator) entry; CTAs take tasks through an atomic counter, and
+// a task sums, over the chunk's rows of every constituent pattern pair of the
+// operator, sb * sa * (sigma[d'] psi[d] - sigma[d] psi[d']) (the pairs of
+// C - C^dagger), as the single-molecule screen does; a second kernel adds an
+// entry's chunks in a fixed order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double batch_block_sum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_batch_grad(BatchGradArgs<T> a)
+{
+    __shared__ double red[8];
+    __shared__ long long sh_task;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) sh_task = (long long)atomicAdd(a.counter, 1ull);
+        __syncthreads();
+        const int64_t task = sh_task;
+        if (task >= a.n_tasks) break;
+        const int64_t e = task / a.CH;
+        const int chunk = int(task - e * a.CH);
+        int lo = 0, hi = a.count;                 // molecule: base[m] <= e < base[m + 1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) / 2;
+            if (a.base[mid] <= e) lo = mid; else hi = mid;
+        }
+        const BatchPool mp = a.mols[lo];
+        const int64_t i = e - a.base[lo];
+        const int k = a.ops ? a.ops[e] : int(i);
+        if (refuse_op(e, k, mp.K, chunk == 0 ? a.bad : nullptr)) {
+            if (threadIdx.x == 0) a.partials[task] = __longlong_as_double(0x7ff8000000000000ll);
+            continue;
+        }
+        const T *psi = a.psi + mp.off, *sigma = a.sigma + mp.off;
+        const OpDev od = mp.opd[k];
+        double tot = 0.0;
+        for (int c = 0; c < od.nc; ++c) {
+            const ConsDev cd = mp.cons[c == 0 ? od.c0 : od.c1];
+            const int64_t nrows = cd.ap < 0 ? mp.Na : mp.acnt[cd.ap];
+            const int64_t ncols = cd.bp < 0 ? mp.Nb : mp.bcnt[cd.bp];
+            const uint32_t *ae = cd.ap < 0 ? nullptr : mp.aent + mp.aoff[cd.ap];
+            const uint32_t *be = cd.bp < 0 ? nullptr : mp.bent + mp.boff[cd.bp];
+            T part = T(0);
+            for (int64_t rr = chunk; rr < nrows; rr += a.CH) {
+                int64_t A = rr, A2 = rr;
+                T sa = T(1);
+                if (ae) {
+                    const uint32_t u = ae[rr];
+                    A = u & 0x7FFFu;
+                    A2 = (u >> 15) & 0x7FFFu;
+                    if (u >> 31) sa = T(-1);
+                }
+                const T *pA = psi + A * mp.Nb, *pA2 = psi + A2 * mp.Nb;
+                const T *sA = sigma + A * mp.Nb, *sA2 = sigma + A2 * mp.Nb;
+                T rowpart = T(0);
+                for (int64_t t = threadIdx.x; t < ncols; t += blockDim.x) {
+                    int64_t B = t, B2 = t;
+                    T sb = T(1);
+                    if (be) {
+                        const uint32_t u = be[t];
+                        B = u & 0x7FFFu;
+                        B2 = (u >> 15) & 0x7FFFu;
+                        if (u >> 31) sb = T(-1);
+                    }
+                    rowpart += sb * (sA2[B2] * pA[B] - sA[B] * pA2[B2]);
+                }
+                part += sa * rowpart;
+            }
+            tot += double(cd.eps) * double(part);
+        }
+        tot = batch_block_sum(tot, red);
+        if (threadIdx.x == 0) a.partials[task] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_batch_grad_final(const double *__restrict__ partials, int CH, int64_t n, double *__restrict__ g)
+{
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double s = 0.0;
+    for (int c = 0; c < CH; ++c) s += partials[e * CH + c];
+    g[e] = 2.0 * s;
+}
+
+template <typename T>
+cudaError_t batch_grad(const BatchGradArgs<T> &a, int grid, cudaStream_t st)
+{
+    const int64_t n = a.n_tasks / (a.CH > 0 ? a.CH : 1);
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_batch_grad<T><<<unsigned(grid), 256, 0, st>>>(a); hy::count_launch();
+    k_batch_grad_final<<<unsigned((n + 255) / 256), 256, 0, st>>>(a.partials, a.CH, n, a.g);
+    hy::count_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 size_t batch_group_smem(int nb_max, int nn_max, int gsize)
 {
@@ -247,6 +359,8 @@ template cudaError_t batch_rows<double>(const BatchArgs<double> &, int, cudaStre
 template cudaError_t batch_rows<float>(const BatchArgs<float> &, int, cudaStream_t);
 template cudaError_t batch_occupancy<double>(const BatchArgs<double> &, int *);
 template cudaError_t batch_occupancy<float>(const BatchArgs<float> &, int *);
+template cudaError_t batch_grad<double>(const BatchGradArgs<double> &, int, cudaStream_t);
+template cudaError_t batch_grad<float>(const BatchGradArgs<float> &, int, cudaStream_t);
 
 }  // namespace k
 }  // namespace hy

@@ -482,6 +482,33 @@ template <typename T>
 cudaError_t batch_rows(const BatchArgs<T> &a, int grid, cudaStream_t st);
 template <typename T>
 cudaError_t batch_occupancy(const BatchArgs<T> &a, int *per_sm);
+// Batched pool-gradient screen: per molecule its pool's pair tables (as in
+// GradArgs) and its place in the packed state buffers
+struct BatchPool {
+    const OpDev *opd;
+    const ConsDev *cons;
+    const uint32_t *aent, *bent;
+    const int64_t *aoff, *acnt, *boff, *bcnt;
+    int64_t Na, Nb, off, K;
+};
+template <typename T>
+struct BatchGradArgs {
+    const BatchPool *mols;
+    int count;
+    const T *psi, *sigma;             // packed states
+    const int32_t *ops;               // packed per-molecule operator lists, or nullptr
+    const int64_t *base;              // [count + 1] entries of each molecule in ops / g
+    int CH;                           // row chunks per entry
+    int64_t n_tasks;                  // base[count] * CH
+    double *partials;                 // [n_tasks]
+    double *g;                        // [base[count]]
+    unsigned long long *counter;      // work counter, zeroed before the launch
+    unsigned long long *bad;          // first refused entry: (position << 32) | index
+};
+// one persistent launch over the (molecule, entry, row chunk) tasks, then the
+// per-entry sums g = 2 * sum of its chunks
+template <typename T>
+cudaError_t batch_grad(const BatchGradArgs<T> &a, int grid, cudaStream_t st);
 cudaError_t batch_energy(const double *row_energy, const int64_t *base, const int64_t *rows,
                          int count, double *energies, cudaStream_t st);
 

@@ -101,3 +101,68 @@ def test_batch_matches_single_molecule_path(batch):
     for i, h in enumerate(hams):
         single = h.apply_h(torch.from_numpy(states[i]).cuda())
         assert torch.max(torch.abs(single - sig[i])).item() < 1e-13
+
+
+def _lists(pools, rng):
+    """Per molecule a random subset of its pool in random order, packed."""
+    ops, offs = [], [0]
+    for p in pools:
+        K = len(p)
+        sel = rng.permutation(K)[: max(0, K // 3)] if K else np.zeros(0, dtype=np.int64)
+        ops.extend(int(k) for k in sel)
+        offs.append(len(ops))
+    return np.array(ops, dtype=np.int32), np.array(offs, dtype=np.int64)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batch_gradients_match_oracle_and_lists(batch, dtype):
+    """The batched screen (hy_batch_gradients): every molecule's full screen
+    against the oracle's gradients of the same state (FP64 1e-11, FP32 1e-4
+    relative to max(1, max|g|)), per-molecule operator lists against the
+    full screen (1e-13 / 1e-6 relative: only the chunking of the sums
+    differs), and
+    an out-of-range list entry: NaN in its slot, reported by the next call."""
+    import paper_2604_01176_gb300 as hy
+    refs, hams, b = batch
+    pools = [hy.Pool(h) for h in hams]
+    b.set_pools(pools)
+    K = [len(p) for p in pools]
+    assert np.array_equal(np.diff(b.pool_offsets), K)
+    states = [synth.random_state(r.n_det, 60 + i) for i, r in enumerate(refs)]
+    if dtype == torch.float32:
+        states = [s.astype(np.float32).astype(np.float64) for s in states]
+    psi = b.pack([torch.from_numpy(s) for s in states], dtype)
+    sig = b.apply_h(psi)
+    g = b.gradients(psi, sig).cpu().numpy()
+    off = b.pool_offsets
+    for i, r in enumerate(refs):
+        if K[i] == 0:
+            continue
+        ref = r.gradients(r.pool(), states[i], r.sigma(states[i]))
+        got = g[off[i]:off[i + 1]]
+        tol = 1e-11 if dtype == torch.float64 else 1e-4
+        assert np.abs(got - ref).max() <= tol * max(1.0, np.abs(ref).max()), i
+    # lists against the full screen: only the chunking of the sums differs
+    # (FP32 sums: float rounding)
+    ltol = 1e-13 if dtype == torch.float64 else 1e-6
+    rng = np.random.default_rng(3)
+    ops, offs = _lists(pools, rng)
+    O = torch.from_numpy(ops).cuda()
+    OF = torch.from_numpy(offs).cuda()
+    gl = b.gradients(psi, sig, ops=O, op_offsets=OF).cpu().numpy()
+    for i in range(len(refs)):
+        sub = ops[offs[i]:offs[i + 1]]
+        if sub.size == 0:
+            continue
+        want = g[off[i] + sub]
+        assert np.abs(gl[offs[i]:offs[i + 1]] - want).max() <= ltol * max(1.0, np.abs(g).max())
+    # an index one past molecule m's pool
+    m = int(np.argmax(K))
+    bad = ops.copy()
+    bad[offs[m]] = K[m]
+    gb = b.gradients(psi, sig, ops=torch.from_numpy(bad).cuda(), op_offsets=OF).cpu().numpy()
+    assert np.isnan(gb[offs[m]])
+    with pytest.raises(hy.HyError):
+        b.gradients(psi, sig, ops=O, op_offsets=OF)
+    gl2 = b.gradients(psi, sig, ops=O, op_offsets=OF).cpu().numpy()   # the report is cleared
+    assert np.abs(gl2 - gl).max() <= ltol * max(1.0, np.abs(g).max())
