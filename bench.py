@@ -29,8 +29,9 @@ paper's CSR regime) with its fraction of the measured HBM bandwidth.
 
 Every sweep runs in the library's kernels (libhyperion.so); the FP64 CPU
 oracle is timed on a bounded sample for `cpu_baseline` and for the
-`--impl reference` arm.  Other modes: --trajectory, --config2, --batch,
---hmat, --ranker-eval, --sweeps-only, --oracle-timing.
+`--impl reference` arm.  Other modes: --trajectory, --support-eval,
+--config2, --batch, --batch-rank, --hmat, --ranker-eval, --sweeps-only,
+--oracle-timing.
 """
 from __future__ import annotations
 
