@@ -835,7 +835,8 @@ CLASS_KERNELS = {
 }
 # the source files whose kernels each class launches (for the traffic record)
 CLASS_SOURCES = {
-    "hpsi": ["hy_sigma.cu", "hy_cpl_tc.cu"], "hpsi_sparse": ["hy_sparse.cu"],
+    "hpsi": ["hy_sigma.cu", "hy_cpl_tc.cu"],
+    "hpsi_sparse": ["hy_sparse.cu", "hy_api.cu", "hy_adapt.cpp"],
     "excite": ["hy_sweeps.cu"], "sparse_excite": ["hy_sparse.cu"],
     "screen": ["hy_sweeps.cu"], "screen_sparse": ["hy_sparse.cu"],
     "reduce": ["hy_sweeps.cu"], "features": ["hy_ranker.cu"], "hmat": ["hy_hmat.cu"],
