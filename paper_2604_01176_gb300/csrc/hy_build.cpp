@@ -83,8 +83,10 @@ void build_string_space(int n, int k, StringSpace &s)
     s.N = binom(n, k);
     s.nex = k * (n - k);
     s.str.resize(s.N);
+#pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < s.N; ++r) s.str[r] = string_unrank(uint32_t(r), k);
     s.ex.assign(size_t(s.N) * s.nex, 0u);
+#pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < s.N; ++r) {
         uint32_t K = s.str[r];
         int e = 0;
@@ -99,18 +101,27 @@ void build_string_space(int n, int k, StringSpace &s)
         }
     }
     // inverse positions: the partner J of (r, e) lists r at the entry whose
-    // orbitals are swapped (J lacks p and holds q)
+    // orbitals are swapped (J lacks p and holds q).  A string lists its
+    // excitations by occupied orbital, then by empty orbital, both ascending,
+    // so that entry is (rank of q among J's occupied) * (n - k) + (rank of p
+    // among J's empty orbitals)
     s.inv.assign(size_t(s.N) * s.nex, 0);
-    for (int64_t r = 0; r < s.N; ++r)
-        for (int e = 0; e < s.nex; ++e) {
-            const uint32_t u = s.ex[size_t(r) * s.nex + e];
-            const uint32_t J = u & 0xFFFFu;
-            for (int f = 0; f < s.nex; ++f)
-                if ((s.ex[size_t(J) * s.nex + f] & 0xFFFFu) == uint32_t(r)) {
-                    s.inv[size_t(r) * s.nex + e] = uint8_t(f);
-                    break;
-                }
+    const uint32_t full = n >= 32 ? ~0u : (1u << n) - 1u;
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < s.N; ++r) {
+        const uint32_t K = s.str[r];
+        int e = 0;
+        for (int p = 0; p < n; ++p) {
+            if (!((K >> p) & 1)) continue;
+            for (int q = 0; q < n; ++q) {
+                if ((K >> q) & 1) continue;
+                const uint32_t J = K ^ (1u << p) ^ (1u << q);
+                const int oq = __builtin_popcount(J & ((1u << q) - 1u));
+                const int ep = __builtin_popcount(~J & full & ((1u << p) - 1u));
+                s.inv[size_t(r) * s.nex + e++] = uint8_t(oq * (n - k) + ep);
+            }
         }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -122,8 +133,70 @@ void build_string_space(int n, int k, StringSpace &s)
 // with L_j the qubits below j, and
 //   (X^x1 Z^z1)(X^x2 Z^z2) = (-1)^popcount(z1 & x2) X^(x1^x2) Z^(z1^z2).
 namespace {
-void add_operator_product(const int *mode, const int *dag, int nops, double coef,
-                          std::unordered_map<uint64_t, double> &acc)
+// Coefficient accumulator keyed by (x | z << 32): open addressing with
+// linear probing; every key keeps its contributions in insertion order, so
+// the sums do not depend on the table's size or layout.
+class PauliAcc {
+  public:
+    PauliAcc() : key_(size_t(1) << 16), val_(size_t(1) << 16), used_(size_t(1) << 16, 0) {}
+    double &operator[](uint64_t k)
+    {
+        size_t h = slot(k);
+        if (!used_[h]) {
+            if (2 * (count_ + 1) > used_.size()) {
+                grow();
+                h = slot(k);
+            }
+            used_[h] = 1;
+            key_[h] = k;
+            val_[h] = 0.0;
+            ++count_;
+        }
+        return val_[h];
+    }
+    size_t size() const { return count_; }
+    template <typename F>
+    void for_each(F &&f) const
+    {
+        for (size_t i = 0; i < used_.size(); ++i)
+            if (used_[i]) f(key_[i], val_[i]);
+    }
+
+  private:
+    size_t slot(uint64_t k) const
+    {
+        const size_t mask = used_.size() - 1;
+        uint64_t x = k * 0x9E3779B97F4A7C15ull;
+        size_t h = size_t(x >> 17) & mask;
+        while (used_[h] && key_[h] != k) h = (h + 1) & mask;
+        return h;
+    }
+    void grow()
+    {
+        std::vector<uint64_t> k0;
+        std::vector<double> v0;
+        std::vector<uint8_t> u0;
+        k0.swap(key_);
+        v0.swap(val_);
+        u0.swap(used_);
+        key_.assign(2 * u0.size(), 0);
+        val_.assign(2 * u0.size(), 0.0);
+        used_.assign(2 * u0.size(), 0);
+        for (size_t i = 0; i < u0.size(); ++i)
+            if (u0[i]) {
+                const size_t h = slot(k0[i]);
+                used_[h] = 1;
+                key_[h] = k0[i];
+                val_[h] = v0[i];
+            }
+    }
+    std::vector<uint64_t> key_;
+    std::vector<double> val_;
+    std::vector<uint8_t> used_;
+    size_t count_ = 0;
+};
+
+void add_operator_product(const int *mode, const int *dag, int nops, double coef, PauliAcc &acc)
 {
     for (int choice = 0; choice < (1 << nops); ++choice) {
         uint64_t x = 0, z = 0;
@@ -145,8 +218,7 @@ void add_operator_product(const int *mode, const int *dag, int nops, double coef
 bool build_pauli_table(const double *h1, const double *h2, double e_core, int n,
                        double prune_tol, PauliTable &t, std::string &err)
 {
-    std::unordered_map<uint64_t, double> acc;
-    acc.reserve(size_t(1) << 20);
+    PauliAcc acc;
     acc[0] += e_core;
     for (int sp = 0; sp < 2; ++sp)
         for (int p = 0; p < n; ++p)
@@ -174,15 +246,17 @@ bool build_pauli_table(const double *h1, const double *h2, double e_core, int n,
     struct Term { uint64_t x, z; double c; };
     std::vector<Term> terms;
     terms.reserve(acc.size());
-    for (auto &kv : acc) {
-        if (std::fabs(kv.second) <= prune_tol) continue;
-        uint64_t x = kv.first & 0xffffffffull, z = kv.first >> 32;
-        if (__builtin_popcountll(x & z) & 1) {
-            err = "Pauli term with an odd number of Y survives: the "
-                  "Hamiltonian is not real symmetric";
-            return false;
-        }
-        terms.push_back({x, z, kv.second});
+    bool odd_y = false;
+    acc.for_each([&](uint64_t key, double c) {
+        if (std::fabs(c) <= prune_tol) return;
+        uint64_t x = key & 0xffffffffull, z = key >> 32;
+        if (__builtin_popcountll(x & z) & 1) odd_y = true;
+        terms.push_back({x, z, c});
+    });
+    if (odd_y) {
+        err = "Pauli term with an odd number of Y survives: the "
+              "Hamiltonian is not real symmetric";
+        return false;
     }
     std::sort(terms.begin(), terms.end(), [](const Term &a, const Term &b) {
         return a.x != b.x ? a.x < b.x : a.z < b.z;
@@ -262,43 +336,81 @@ static void build_csr(const PauliTable &t, const StringSpace &S, int shift,
 {
     const int n = S.n;
     M.rows = S.N;
+    // the groups whose X-mask lies in this spin's qubits, indexed by the
+    // mask's n bits: the element of a same-spin pair is a direct lookup
+    std::vector<int64_t> grp(size_t(1) << n, -1);
+    for (const auto &kv : t.group_of_x)
+        if ((kv.first >> shift) << shift == kv.first && (kv.first >> shift) < (uint64_t(1) << n))
+            grp[kv.first >> shift] = kv.second;
+    auto elem = [&](uint64_t bra, uint64_t ket) {
+        const int64_t g = grp[(bra ^ ket) >> shift];
+        if (g < 0) return 0.0;
+        double v = 0.0;
+        for (int64_t j = t.group_off[g]; j < t.group_off[g + 1]; ++j)
+            v += (__builtin_popcountll(ket & t.z[j]) & 1) ? -t.cxz[j] : t.cxz[j];
+        return v;
+    };
     std::vector<std::vector<std::pair<int32_t, double>>> rows(S.N);
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t r = 0; r < S.N; ++r) {
         uint32_t K = S.str[r];
         auto &row = rows[r];
+        {
+            const size_t no = size_t(S.k), nv = size_t(n - S.k);
+            row.reserve(1 + no * nv + no * (no - (no > 0)) / 2 * (nv * (nv - (nv > 0)) / 2));
+        }
+        auto push = [&](int32_t c, double v) { row.emplace_back(c, v); };
         uint64_t bra = uint64_t(K) << shift;
-        row.push_back({int32_t(r), t.element(bra, bra) - subtract_diag});
+        push(int32_t(r), elem(bra, bra) - subtract_diag);
         int occ[kMaxOrb], vir[kMaxOrb], no = 0, nv = 0;
         for (int p = 0; p < n; ++p) {
             if ((K >> p) & 1) occ[no++] = p; else vir[nv++] = p;
         }
+        // partner ranks from the excitation lists: K's single (i -> a) is
+        // entry i * nv + a of K's list; the double (i, j -> a, b) is then the
+        // single (j -> b) of that partner K1, entry (rank of j among K1's
+        // occupied) * nv + (rank of b among K1's empty orbitals)
+        const uint32_t full = n >= 32 ? ~0u : (1u << n) - 1u;
+        const uint32_t *exK = S.ex.data() + size_t(r) * S.nex;
         for (int i = 0; i < no; ++i)
             for (int a = 0; a < nv; ++a) {
                 uint32_t J = K ^ (1u << occ[i]) ^ (1u << vir[a]);
-                double v = t.element(bra, uint64_t(J) << shift);
-                if (v != 0.0) row.push_back({int32_t(string_rank(J)), v});
+                double v = elem(bra, uint64_t(J) << shift);
+                if (v != 0.0) push(int32_t(exK[i * nv + a] & 0xFFFFu), v);
             }
         for (int i = 0; i < no; ++i)
-            for (int j = i + 1; j < no; ++j)
-                for (int a = 0; a < nv; ++a)
+            for (int a = 0; a < nv; ++a) {
+                const uint32_t K1 = K ^ (1u << occ[i]) ^ (1u << vir[a]);
+                const uint32_t *ex1 = S.ex.data() + size_t(exK[i * nv + a] & 0xFFFFu) * S.nex;
+                for (int j = i + 1; j < no; ++j) {
+                    const int oj = __builtin_popcount(K1 & ((1u << occ[j]) - 1u));
                     for (int b = a + 1; b < nv; ++b) {
-                        uint32_t J = K ^ (1u << occ[i]) ^ (1u << occ[j]) ^
-                                     (1u << vir[a]) ^ (1u << vir[b]);
-                        double v = t.element(bra, uint64_t(J) << shift);
-                        if (v != 0.0) row.push_back({int32_t(string_rank(J)), v});
+                        const uint32_t J = K1 ^ (1u << occ[j]) ^ (1u << vir[b]);
+                        double v = elem(bra, uint64_t(J) << shift);
+                        if (v == 0.0) continue;
+                        const int eb = __builtin_popcount(~K1 & full & ((1u << vir[b]) - 1u));
+                        push(int32_t(ex1[oj * nv + eb] & 0xFFFFu), v);
                     }
-        std::sort(row.begin(), row.end());
+                }
+            }
+        // columns are distinct: order by column alone
+        std::sort(row.begin(), row.end(),
+                  [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
+                      return a.first < b.first;
+                  });
     }
     M.ptr.assign(S.N + 1, 0);
     for (int64_t r = 0; r < S.N; ++r) M.ptr[r + 1] = M.ptr[r] + int32_t(rows[r].size());
     M.col.resize(M.ptr[S.N]);
     M.val.resize(M.ptr[S.N]);
-    for (int64_t r = 0; r < S.N; ++r)
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < S.N; ++r) {
         for (size_t e = 0; e < rows[r].size(); ++e) {
             M.col[M.ptr[r] + e] = rows[r][e].first;
             M.val[M.ptr[r] + e] = rows[r][e].second;
         }
+        std::vector<std::pair<int32_t, double>>().swap(rows[r]);
+    }
 }
 
 void fold_tables(const PauliTable &t, int n, const StringSpace &A,
