@@ -1062,8 +1062,8 @@ hy_status hy_pool_create(const hy_ham *h, hy_pool_kind kind, hy_pool **out)
                 return fail(HY_ERR_UNSUPPORTED, "constituent changes a spin's particle number");
             }
             hy::k::ConsDev cd;
-            cd.ap = ka.nops ? p->pa.get(ka, h->A) : -1;
-            cd.bp = kb.nops ? p->pb.get(kb, h->B) : -1;
+            cd.ap = ka.nops ? p->pa.get(ka) : -1;
+            cd.bp = kb.nops ? p->pb.get(kb) : -1;
             // qubit operators on different qubits commute: no reordering sign
             cd.eps = (!p->qubit && (inv & 1)) ? -1 : 1;
             cd.pad = 0;
@@ -1073,6 +1073,8 @@ hy_status hy_pool_create(const hy_ham *h, hy_pool_kind kind, hy_pool **out)
         }
         p->opd.push_back(od);
     }
+    p->pa.finalize(h->A);
+    p->pb.finalize(h->B);
     hy_status s = HY_OK;
     auto up = [&](cudaError_t err, const char *what) {
         if (s == HY_OK && err != cudaSuccess) s = cuda_fail(err, what);

@@ -588,24 +588,43 @@ static bool apply_within_string(const PatternKey &k, uint32_t s, uint32_t &out,
     return true;
 }
 
-int PatternLists::get(const PatternKey &k, const StringSpace &s)
+int PatternLists::get(const PatternKey &k)
 {
     auto it = id.find(k);
     if (it != id.end()) return it->second;
-    int pid = int(off.size());
+    const int pid = int(keys.size());
     id[k] = pid;
-    off.push_back(int64_t(entry.size()));
-    int64_t c = 0;
-    for (int64_t r = 0; r < s.N; ++r) {
-        uint32_t out;
-        int neg;
-        if (!apply_within_string(k, s.str[r], out, neg)) continue;
-        uint32_t img = string_rank(out);
-        entry.push_back(uint32_t(r) | (img << 15) | (uint32_t(neg) << 31));
-        ++c;
-    }
-    cnt.push_back(c);
+    keys.push_back(k);
     return pid;
+}
+
+void PatternLists::finalize(const StringSpace &s)
+{
+    const int64_t np = int64_t(keys.size());
+    std::vector<std::vector<uint32_t>> lists(np);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t pid = 0; pid < np; ++pid) {
+        auto &l = lists[pid];
+        for (int64_t r = 0; r < s.N; ++r) {
+            uint32_t out;
+            int neg;
+            if (!apply_within_string(keys[pid], s.str[r], out, neg)) continue;
+            const uint32_t img = string_rank(out);
+            l.push_back(uint32_t(r) | (img << 15) | (uint32_t(neg) << 31));
+        }
+    }
+    off.assign(np, 0);
+    cnt.assign(np, 0);
+    int64_t tot = 0;
+    for (int64_t pid = 0; pid < np; ++pid) {
+        off[pid] = tot;
+        cnt[pid] = int64_t(lists[pid].size());
+        tot += cnt[pid];
+    }
+    entry.resize(tot);
+#pragma omp parallel for schedule(static)
+    for (int64_t pid = 0; pid < np; ++pid)
+        std::copy(lists[pid].begin(), lists[pid].end(), entry.begin() + off[pid]);
 }
 
 }  // namespace hy

@@ -118,7 +118,11 @@ struct PatternLists {
     std::vector<int64_t> off;   // per pattern
     std::vector<int64_t> cnt;
     std::unordered_map<PatternKey, int, PatternKeyHash> id;
-    int get(const PatternKey &k, const StringSpace &s);
+    std::vector<PatternKey> keys;   // by id
+    // id of pattern k (registered on first use); finalize() then lists every
+    // registered pattern's pairs (patterns in parallel, stored in id order)
+    int get(const PatternKey &k);
+    void finalize(const StringSpace &s);
 };
 
 // Kernel-class timing (hy_profile.cpp): records an event pair on `stream`
