@@ -18,7 +18,7 @@ LIB = os.path.join(PKG, "libhyperion.so")
 
 SOURCES = ["hy_build.cpp", "hy_api.cu", "hy_sigma.cu", "hy_sweeps.cu",
            "hy_adapt.cpp", "hy_ranker.cu", "hy_batch.cu", "hy_sparse.cu", "hy_profile.cpp",
-           "hy_cpl_tc.cu", "hy_hmat.cu"]
+           "hy_cpl_tc.cu", "hy_hmat.cu", "hy_fold.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler",
                 "-fPIC,-fopenmp,-O3", "-I", INCLUDE, "-I", CSRC]

@@ -56,6 +56,20 @@ struct DevArena {
         *dst = static_cast<T *>(p);
         return e;
     }
+    // device memory owned by the arena, not copied from the host
+    template <typename T>
+    cudaError_t alloc(T **dst, size_t count, bool zero = false)
+    {
+        *dst = nullptr;
+        if (count == 0) return cudaSuccess;
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) return e;
+        ptrs.push_back(p);
+        if (zero) e = cudaMemset(p, 0, count * sizeof(T));
+        *dst = static_cast<T *>(p);
+        return e;
+    }
     void release()
     {
         for (void *p : ptrs) cudaFree(p);
@@ -84,7 +98,8 @@ struct hy_ham {
     int device = 0, num_sms = 0;
     hy::StringSpace A, B;
     hy::PauliTable pauli;
-    hy::KernelTables kt;
+    hy::KernelTables kt;            // E0 and V; Ma / Mb copied from the device on demand
+    int64_t nnz_a = 0, nnz_b = 0;   // entries of the same-spin tables
     std::vector<double> h1h, h2h;   // the integrals (host copies)
     DevArena arena;
     uint32_t *d_astr = nullptr, *d_bstr = nullptr;
@@ -270,16 +285,6 @@ bool check_symmetric(const double *h1, const double *h2, int n, std::string &why
                     }
                 }
     return true;
-}
-
-template <typename T>
-hy_status upload_csr(DevArena &ar, const hy::CsrHost &M, DevCsr<T> &D)
-{
-    std::vector<T> v(M.val.begin(), M.val.end());
-    HY_CUDA(ar.upload(&D.ptr, M.ptr.data(), M.ptr.size()), "upload csr ptr");
-    HY_CUDA(ar.upload(&D.col, M.col.data(), M.col.size()), "upload csr col");
-    HY_CUDA(ar.upload(&D.val, v.data(), v.size()), "upload csr val");
-    return HY_OK;
 }
 
 // Phase A of the float coupling forms T rows per alpha string J; the output
@@ -628,11 +633,114 @@ namespace {
 // The rest of a build from h's Pauli table (set, with the string spaces and
 // the host integrals): fold the kernel tables, query the device and upload.
 // Takes ownership of h (released on failure).
+// The same-spin tables Ma (alpha strings) and Mb (beta strings, minus E0 on
+// the diagonal) folded on the device from the Pauli table (hy_fold.cu): the
+// table's groups and terms and, per spin, a direct map from an X-mask within
+// the spin to its group are uploaded; rows go through a fixed-stride scratch
+// and are compacted into CSR arrays shared by the double and float views.
+hy_status fold_same_spin(hy_ham *h)
+{
+    const int n = h->n;
+    const hy::PauliTable &t = h->pauli;
+    std::vector<int32_t> grpA(size_t(1) << n, -1), grpB(size_t(1) << n, -1);
+    const uint64_t low = (uint64_t(1) << n) - 1;
+    for (const auto &kv : t.group_of_x) {
+        if ((kv.first & ~low) == 0) grpA[kv.first] = int32_t(kv.second);
+        if ((kv.first & low) == 0 && (kv.first >> n) <= low) grpB[kv.first >> n] = int32_t(kv.second);
+    }
+    DevArena &ar = h->arena;
+    int32_t *d_grpA = nullptr, *d_grpB = nullptr;
+    int64_t *d_goff = nullptr;
+    uint64_t *d_z = nullptr;
+    double *d_c = nullptr;
+    HY_CUDA(ar.upload(&d_grpA, grpA.data(), grpA.size()), "upload Pauli groups");
+    HY_CUDA(ar.upload(&d_grpB, grpB.data(), grpB.size()), "upload Pauli groups");
+    HY_CUDA(ar.upload(&d_goff, t.group_off.data(), t.group_off.size()), "upload Pauli groups");
+    HY_CUDA(ar.upload(&d_z, t.z.data(), t.z.size()), "upload Pauli terms");
+    HY_CUDA(ar.upload(&d_c, t.cxz.data(), t.cxz.size()), "upload Pauli terms");
+    const int64_t stride = std::max(hy::k::fold_candidates(n, h->na), hy::k::fold_candidates(n, h->nb));
+    const int64_t rows = std::max(h->Na, h->Nb);
+    int32_t *tcol = nullptr, *len = nullptr;
+    double *tval = nullptr;
+    cudaError_t e = cudaMalloc(&tcol, size_t(rows * stride) * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&tval, size_t(rows * stride) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&len, size_t(rows) * sizeof(int32_t));
+    auto done = [&]() {
+        cudaFree(tcol);
+        cudaFree(tval);
+        cudaFree(len);
+    };
+    for (int spin = 0; spin < 2 && e == cudaSuccess; ++spin) {
+        const int64_t N = spin == 0 ? h->Na : h->Nb;
+        hy::k::FoldArgs a;
+        a.str = spin == 0 ? h->d_astr : h->d_bstr;
+        a.N = N;
+        a.n = n;
+        a.k = spin == 0 ? h->na : h->nb;
+        a.shift = spin == 0 ? 0 : n;
+        a.sub_diag = spin == 0 ? 0.0 : h->kt.E0;
+        a.grp = spin == 0 ? d_grpA : d_grpB;
+        a.goff = d_goff;
+        a.z = d_z;
+        a.c = d_c;
+        a.binom33 = h->d_binom;
+        a.stride = stride;
+        a.tcol = tcol;
+        a.tval = tval;
+        a.len = len;
+        DevCsr<double> &M64 = spin == 0 ? h->Ma64 : h->Mb64;
+        DevCsr<float> &M32 = spin == 0 ? h->Ma32 : h->Mb32;
+        const int64_t cap = N * hy::k::fold_candidates(n, a.k);
+        e = ar.alloc(&M64.ptr, size_t(N + 1));
+        if (e == cudaSuccess) e = ar.alloc(&M64.col, size_t(cap > 0 ? cap : 1));
+        if (e == cudaSuccess) e = ar.alloc(&M64.val, size_t(cap > 0 ? cap : 1));
+        if (e == cudaSuccess) e = ar.alloc(&M32.val, size_t(cap > 0 ? cap : 1));
+        if (e != cudaSuccess) break;
+        M32.ptr = M64.ptr;
+        M32.col = M64.col;
+        e = hy::k::fold_rows(a, h->num_sms, nullptr);
+        if (e == cudaSuccess)
+            e = hy::k::fold_compact(a, M64.ptr, M64.col, M64.val, M32.val, h->num_sms, nullptr);
+        int32_t nnz = 0;
+        if (e == cudaSuccess)
+            e = cudaMemcpy(&nnz, M64.ptr + N, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        (spin == 0 ? h->nnz_a : h->nnz_b) = nnz;
+    }
+    done();
+    if (e != cudaSuccess) return cuda_fail(e, "same-spin tables");
+    return HY_OK;
+}
+
+// host copies of the same-spin tables, for host consumers (the explicit-H
+// builder); copied once from the device
+hy_status ensure_host_csr(hy_ham *h)
+{
+    if (!h->kt.Ma.ptr.empty()) return HY_OK;
+    for (int spin = 0; spin < 2; ++spin) {
+        hy::CsrHost &M = spin == 0 ? h->kt.Ma : h->kt.Mb;
+        const DevCsr<double> &D = spin == 0 ? h->Ma64 : h->Mb64;
+        const int64_t N = spin == 0 ? h->Na : h->Nb, nnz = spin == 0 ? h->nnz_a : h->nnz_b;
+        M.rows = N;
+        M.ptr.resize(size_t(N + 1));
+        M.col.resize(size_t(nnz));
+        M.val.resize(size_t(nnz));
+        HY_CUDA(cudaMemcpy(M.ptr.data(), D.ptr, size_t(N + 1) * sizeof(int32_t),
+                           cudaMemcpyDeviceToHost), "copy same-spin table");
+        if (nnz) {
+            HY_CUDA(cudaMemcpy(M.col.data(), D.col, size_t(nnz) * sizeof(int32_t),
+                               cudaMemcpyDeviceToHost), "copy same-spin table");
+            HY_CUDA(cudaMemcpy(M.val.data(), D.val, size_t(nnz) * sizeof(double),
+                               cudaMemcpyDeviceToHost), "copy same-spin table");
+        }
+    }
+    return HY_OK;
+}
+
 hy_status finish_ham(hy_ham *h, hy_ham **out)
 {
     const int n_orb = h->n;
     const double *h1 = h->h1h.data(), *h2 = h->h2h.data();
-    hy::fold_tables(h->pauli, n_orb, h->A, h->B, h->kt);
+    hy::fold_coupling(h->pauli, n_orb, h->kt);
 
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess)
@@ -680,27 +788,18 @@ hy_status finish_ham(hy_ham *h, hy_ham **out)
     up(ar.upload(&h->d_eri, h2, size_t(n_orb) * n_orb * n_orb * n_orb), "upload h2");
     h->occ_blocks = 2 * h->num_sms;
     {
-        std::vector<double> zp(size_t(h->occ_blocks) * 33, 0.0);
-        std::vector<float> zo(size_t(2 * n_orb), 0.0f);
-        up(ar.upload(&h->d_occ_partial, zp.data(), zp.size()), "occupation partials");
-        up(ar.upload(&h->d_occ, zo.data(), zo.size()), "occupations");
         const size_t nn = size_t(n_orb) * n_orb;
-        std::vector<float> zb(2 * size_t(h->Na) * nn, 0.0f), zr(2 * size_t(h->Na), 0.0f),
-            zd(2 * nn * nn, 0.0f);
-        up(ar.upload(&h->d_pairB, zb.data(), zb.size()), "touched-weight partials");
-        up(ar.upload(&h->d_pairRs, zr.data(), zr.size()), "touched-weight partials");
-        up(ar.upload(&h->d_pairD, zd.data(), zd.size()), "touched weights");
-        std::vector<float> zq(size_t(hy::k::pair_splits()) * nn * nn, 0.0f);
-        up(ar.upload(&h->d_pairP, zq.data(), zq.size()), "touched-weight partials");
-        std::vector<int32_t> zrow(size_t(h->Na) + 1, 0);
-        up(ar.upload(&h->d_pairRows, zrow.data(), zrow.size()), "touched-weight rows");
-        std::vector<double> zw(34, 0.0);
-        up(ar.upload(&h->d_occw, zw.data(), zw.size()), "occupation scratch");
+        up(ar.alloc(&h->d_occ_partial, size_t(h->occ_blocks) * 33, true), "occupation partials");
+        up(ar.alloc(&h->d_occ, size_t(2 * n_orb), true), "occupations");
+        up(ar.alloc(&h->d_pairB, 2 * size_t(h->Na) * nn, true), "touched-weight partials");
+        up(ar.alloc(&h->d_pairRs, 2 * size_t(h->Na), true), "touched-weight partials");
+        up(ar.alloc(&h->d_pairD, 2 * nn * nn, true), "touched weights");
+        up(ar.alloc(&h->d_pairP, size_t(hy::k::pair_splits()) * nn * nn, true),
+           "touched-weight partials");
+        up(ar.alloc(&h->d_pairRows, size_t(h->Na) + 1, true), "touched-weight rows");
+        up(ar.alloc(&h->d_occw, size_t(34), true), "occupation scratch");
     }
-    if (s == HY_OK) s = upload_csr<double>(ar, h->kt.Ma, h->Ma64);
-    if (s == HY_OK) s = upload_csr<double>(ar, h->kt.Mb, h->Mb64);
-    if (s == HY_OK) s = upload_csr<float>(ar, h->kt.Ma, h->Ma32);
-    if (s == HY_OK) s = upload_csr<float>(ar, h->kt.Mb, h->Mb32);
+    if (s == HY_OK) s = fold_same_spin(h);
     if (s != HY_OK) {
         std::string msg = g_err;
         hy_ham_destroy(h);
@@ -1161,8 +1260,11 @@ hy_status hy_pool_gradients(const hy_ham *hc, const hy_pool *p, const void *psi,
 
 namespace hy {
 
-HamView ham_view(const hy_ham *h)
+HamView ham_view(const hy_ham *h, bool host_tables)
 {
+    // the same-spin tables live on the device; host consumers get a copy
+    // (made once per handle)
+    if (host_tables && h->kt.Ma.ptr.empty()) ensure_host_csr(const_cast<hy_ham *>(h));
     HamView v;
     v.n = h->n; v.na = h->na; v.nb = h->nb; v.device = h->device; v.num_sms = h->num_sms;
     v.Na = h->Na; v.Nb = h->Nb; v.N = h->N;
@@ -1710,7 +1812,7 @@ hy_status hy_batch_create(const hy_ham *const *hams, int count, hy_batch **out)
     for (int i = 0; i < count; ++i) {
         const hy_ham *h = hams[i];
         const double rowc = double(h->Nb) *
-            (double(h->kt.Ma.ptr.back()) / double(h->Na) + double(h->kt.Mb.ptr.back()) / double(h->Nb) +
+            (double(h->nnz_a) / double(h->Na) + double(h->nnz_b) / double(h->Nb) +
              double(h->A.nex + 1) * double(h->B.nex + 1));
         cost[i] = rowc;
         b->order.push_back(i);
@@ -2377,14 +2479,11 @@ hy_status prog_build_hss(SupportProgram *g, const SparseState *s, int64_t max_nn
     cudaStream_t st = as_stream(stream);
     g->hss_ok = false;
     if (!g->hss_w) {
-        // a row's couplings: its CSR rows of both spins, then the
+        // a row's couplings: its CSR rows of both spins (at most the
+        // diagonal, the singles and the doubles of its string), then the
         // (1 + nexa) x (1 + nexb) grid of alpha-beta terms
-        int64_t wa = 0, wb = 0;
-        for (size_t r = 0; r + 1 < h->kt.Ma.ptr.size(); ++r)
-            wa = std::max<int64_t>(wa, h->kt.Ma.ptr[r + 1] - h->kt.Ma.ptr[r]);
-        for (size_t r = 0; r + 1 < h->kt.Mb.ptr.size(); ++r)
-            wb = std::max<int64_t>(wb, h->kt.Mb.ptr[r + 1] - h->kt.Mb.ptr[r]);
-        g->hss_w = wa + wb + int64_t(h->A.nex + 1) * (h->B.nex + 1);
+        g->hss_w = int64_t(hy::k::fold_candidates(h->n, h->na)) +
+                   hy::k::fold_candidates(h->n, h->nb) + int64_t(h->A.nex + 1) * (h->B.nex + 1);
     }
     const int64_t need = g->m * g->hss_w;
     if (need > max_nnz) return HY_OK;              // too large to pay off: not built

@@ -331,94 +331,11 @@ bool check_two_body_structure(const PauliTable &t, int n, std::string &err)
 //     one-electron-per-spin determinants: single-excitation elements are
 //     affine in the spectator occupations and the diagonal is quadratic,
 //     so the differences below isolate exactly the cross terms.
-static void build_csr(const PauliTable &t, const StringSpace &S, int shift,
-                      double subtract_diag, CsrHost &M)
-{
-    const int n = S.n;
-    M.rows = S.N;
-    // the groups whose X-mask lies in this spin's qubits, indexed by the
-    // mask's n bits: the element of a same-spin pair is a direct lookup
-    std::vector<int64_t> grp(size_t(1) << n, -1);
-    for (const auto &kv : t.group_of_x)
-        if ((kv.first >> shift) << shift == kv.first && (kv.first >> shift) < (uint64_t(1) << n))
-            grp[kv.first >> shift] = kv.second;
-    auto elem = [&](uint64_t bra, uint64_t ket) {
-        const int64_t g = grp[(bra ^ ket) >> shift];
-        if (g < 0) return 0.0;
-        double v = 0.0;
-        for (int64_t j = t.group_off[g]; j < t.group_off[g + 1]; ++j)
-            v += (__builtin_popcountll(ket & t.z[j]) & 1) ? -t.cxz[j] : t.cxz[j];
-        return v;
-    };
-    std::vector<std::vector<std::pair<int32_t, double>>> rows(S.N);
-#pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t r = 0; r < S.N; ++r) {
-        uint32_t K = S.str[r];
-        auto &row = rows[r];
-        {
-            const size_t no = size_t(S.k), nv = size_t(n - S.k);
-            row.reserve(1 + no * nv + no * (no - (no > 0)) / 2 * (nv * (nv - (nv > 0)) / 2));
-        }
-        auto push = [&](int32_t c, double v) { row.emplace_back(c, v); };
-        uint64_t bra = uint64_t(K) << shift;
-        push(int32_t(r), elem(bra, bra) - subtract_diag);
-        int occ[kMaxOrb], vir[kMaxOrb], no = 0, nv = 0;
-        for (int p = 0; p < n; ++p) {
-            if ((K >> p) & 1) occ[no++] = p; else vir[nv++] = p;
-        }
-        // partner ranks from the excitation lists: K's single (i -> a) is
-        // entry i * nv + a of K's list; the double (i, j -> a, b) is then the
-        // single (j -> b) of that partner K1, entry (rank of j among K1's
-        // occupied) * nv + (rank of b among K1's empty orbitals)
-        const uint32_t full = n >= 32 ? ~0u : (1u << n) - 1u;
-        const uint32_t *exK = S.ex.data() + size_t(r) * S.nex;
-        for (int i = 0; i < no; ++i)
-            for (int a = 0; a < nv; ++a) {
-                uint32_t J = K ^ (1u << occ[i]) ^ (1u << vir[a]);
-                double v = elem(bra, uint64_t(J) << shift);
-                if (v != 0.0) push(int32_t(exK[i * nv + a] & 0xFFFFu), v);
-            }
-        for (int i = 0; i < no; ++i)
-            for (int a = 0; a < nv; ++a) {
-                const uint32_t K1 = K ^ (1u << occ[i]) ^ (1u << vir[a]);
-                const uint32_t *ex1 = S.ex.data() + size_t(exK[i * nv + a] & 0xFFFFu) * S.nex;
-                for (int j = i + 1; j < no; ++j) {
-                    const int oj = __builtin_popcount(K1 & ((1u << occ[j]) - 1u));
-                    for (int b = a + 1; b < nv; ++b) {
-                        const uint32_t J = K1 ^ (1u << occ[j]) ^ (1u << vir[b]);
-                        double v = elem(bra, uint64_t(J) << shift);
-                        if (v == 0.0) continue;
-                        const int eb = __builtin_popcount(~K1 & full & ((1u << vir[b]) - 1u));
-                        push(int32_t(ex1[oj * nv + eb] & 0xFFFFu), v);
-                    }
-                }
-            }
-        // columns are distinct: order by column alone
-        std::sort(row.begin(), row.end(),
-                  [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
-                      return a.first < b.first;
-                  });
-    }
-    M.ptr.assign(S.N + 1, 0);
-    for (int64_t r = 0; r < S.N; ++r) M.ptr[r + 1] = M.ptr[r] + int32_t(rows[r].size());
-    M.col.resize(M.ptr[S.N]);
-    M.val.resize(M.ptr[S.N]);
-#pragma omp parallel for schedule(static)
-    for (int64_t r = 0; r < S.N; ++r) {
-        for (size_t e = 0; e < rows[r].size(); ++e) {
-            M.col[M.ptr[r] + e] = rows[r][e].first;
-            M.val[M.ptr[r] + e] = rows[r][e].second;
-        }
-        std::vector<std::pair<int32_t, double>>().swap(rows[r]);
-    }
-}
-
-void fold_tables(const PauliTable &t, int n, const StringSpace &A,
-                 const StringSpace &B, KernelTables &kt)
+// The two same-spin parts are folded on the GPU (hy_fold.cu, the same
+// element formula as PauliTable::element); the host keeps E0 and V.
+void fold_coupling(const PauliTable &t, int n, KernelTables &kt)
 {
     kt.E0 = t.element(0, 0);
-    build_csr(t, A, 0, 0.0, kt.Ma);
-    build_csr(t, B, n, kt.E0, kt.Mb);
     kt.V.assign(size_t(n) * n * n * n, 0.0);
     auto a_ = [](int p) { return 1ull << p; };
     auto b_ = [n](int r) { return 1ull << (n + r); };

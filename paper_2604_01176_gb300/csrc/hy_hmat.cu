@@ -433,7 +433,7 @@ hy_status hy_hmat_bytes(const hy_ham *h, hy_dtype dt, int64_t row_begin, int64_t
                         int64_t *bytes, int64_t *nnz)
 {
     if (!h || (dt != HY_F64 && dt != HY_F32)) return hy::hfail(HY_ERR_ARG, "bad arguments");
-    const hy::HamView v = hy::ham_view(h);
+    const hy::HamView v = hy::ham_view(h, true);
     if (row_begin < 0 || row_end < row_begin || row_end > v.Na)
         return hy::hfail(HY_ERR_ARG, "row range outside [0, N_alpha]");
     const hy::Geometry g = hy::geometry(v);
@@ -448,7 +448,7 @@ hy_status hy_hmat_build(const hy_ham *h, hy_dtype dt, int64_t row_begin, int64_t
     if (!out) return hy::hfail(HY_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!h || (dt != HY_F64 && dt != HY_F32)) return hy::hfail(HY_ERR_ARG, "bad arguments");
-    const hy::HamView v = hy::ham_view(h);
+    const hy::HamView v = hy::ham_view(h, true);
     if (row_begin < 0 || row_end < row_begin || row_end > v.Na)
         return hy::hfail(HY_ERR_ARG, "row range outside [0, N_alpha]");
     const hy::Geometry g = hy::geometry(v);

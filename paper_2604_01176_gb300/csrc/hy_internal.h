@@ -83,8 +83,10 @@ struct KernelTables {
     std::vector<double> V;   // n^4, index ((p*n+q)*n+r)*n+s
     double E0 = 0.0;         // <vacuum|H|vacuum>
 };
-void fold_tables(const PauliTable &t, int n, const StringSpace &A,
-                 const StringSpace &B, KernelTables &kt);
+// E0 = <vacuum|H|vacuum> and the alpha-beta coupling V from the Pauli table;
+// the same-spin CSR tables are folded on the device (hy_fold.cu) and copied
+// into Ma / Mb on the host only when a host consumer asks (ham_view)
+void fold_coupling(const PauliTable &t, int n, KernelTables &kt);
 
 // ---------------------------------------------------------------------------
 // Operator pool.
@@ -258,7 +260,8 @@ struct HamView {
     const StringSpace *A, *B;
     const KernelTables *kt;
 };
-HamView ham_view(const hy_ham *h);
+// host_tables: also make the host copy of the same-spin tables (kt->Ma, Mb)
+HamView ham_view(const hy_ham *h, bool host_tables = false);
 void set_last_error(const std::string &msg);
 void count_launch();
 

@@ -482,6 +482,31 @@ template <typename T>
 cudaError_t batch_rows(const BatchArgs<T> &a, int grid, cudaStream_t st);
 template <typename T>
 cudaError_t batch_occupancy(const BatchArgs<T> &a, int *per_sm);
+// Same-spin kernel table of one spin folded on the device from the Pauli
+// table (hy_fold.cu): candidates of row r = the diagonal, the singles and the
+// doubles of str[r]; element = the Pauli group with X-mask K ^ J evaluated on J
+// (placed at qubit `shift`), minus sub_diag on the diagonal
+struct FoldArgs {
+    const uint32_t *str;
+    int64_t N;
+    int n, k, shift;
+    double sub_diag;
+    const int32_t *grp;        // [1 << n] group of an X-mask within the spin, or -1
+    const int64_t *goff;       // [groups + 1]
+    const uint64_t *z;         // [terms]
+    const double *c;           // [terms]
+    const uint32_t *binom33;
+    int64_t stride;            // scratch entries per row (>= fold_candidates)
+    int32_t *tcol;             // [N * stride] scratch
+    double *tval;              // [N * stride] scratch
+    int32_t *len;              // [N]
+};
+int fold_candidates(int n, int k);
+cudaError_t fold_rows(const FoldArgs &a, int num_sms, cudaStream_t st);
+// row pointers [N + 1] and the CSR columns and values (double and float)
+cudaError_t fold_compact(const FoldArgs &a, int32_t *ptr, int32_t *col, double *val64,
+                         float *val32, int num_sms, cudaStream_t st);
+
 // Batched pool-gradient screen: per molecule its pool's pair tables (as in
 // GradArgs) and its place in the packed state buffers
 struct BatchPool {
