@@ -11,6 +11,10 @@
 #include <cmath>
 #include <cstring>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #include "hy_internal.h"
 
 namespace hy {
@@ -218,41 +222,66 @@ void add_operator_product(const int *mode, const int *dag, int nops, double coef
 bool build_pauli_table(const double *h1, const double *h2, double e_core, int n,
                        double prune_tol, PauliTable &t, std::string &err)
 {
-    PauliAcc acc;
-    acc[0] += e_core;
-    for (int sp = 0; sp < 2; ++sp)
-        for (int p = 0; p < n; ++p)
-            for (int q = 0; q < n; ++q) {
-                double c = h1[p * n + q];
-                if (c == 0.0) continue;
-                int mode[2] = {p + sp * n, q + sp * n}, dag[2] = {1, 0};
-                add_operator_product(mode, dag, 2, c, acc);
-            }
-    for (int s1 = 0; s1 < 2; ++s1)
-        for (int s2 = 0; s2 < 2; ++s2)
+    // Every product's Pauli strings share its X-mask (the XOR of its modes),
+    // so the X-masks split the work: each thread accumulates the products
+    // whose X-mask falls in its class, visiting them in the loop order below.
+    // Every coefficient is therefore summed in exactly the serial order,
+    // whatever the number of threads.
+    int nthreads = 1;
+#ifdef _OPENMP
+    nthreads = omp_get_max_threads();
+#endif
+    std::vector<PauliAcc> part(nthreads);
+    auto cls = [nthreads](uint64_t x) {
+        return int(((x * 0x9E3779B97F4A7C15ull) >> 40) % uint64_t(nthreads));
+    };
+#pragma omp parallel num_threads(nthreads)
+    {
+        int me = 0;
+#ifdef _OPENMP
+        me = omp_get_thread_num();
+#endif
+        PauliAcc &acc = part[me];
+        if (cls(0) == me) acc[0] += e_core;
+        for (int sp = 0; sp < 2; ++sp)
             for (int p = 0; p < n; ++p)
-                for (int q = 0; q < n; ++q)
-                    for (int r = 0; r < n; ++r)
-                        for (int s = 0; s < n; ++s) {
-                            double c = h2[((size_t(p) * n + q) * n + r) * n + s];
-                            if (c == 0.0) continue;
-                            int P = p + s1 * n, Q = q + s1 * n;
-                            int R = r + s2 * n, S = s + s2 * n;
-                            if (P == R || Q == S) continue;   // a+a+ / aa vanish
-                            // 1/2 (pq|rs) a+_P a+_R a_S a_Q
-                            int mode[4] = {P, R, S, Q}, dag[4] = {1, 1, 0, 0};
-                            add_operator_product(mode, dag, 4, 0.5 * c, acc);
-                        }
+                for (int q = 0; q < n; ++q) {
+                    double c = h1[p * n + q];
+                    if (c == 0.0) continue;
+                    int P = p + sp * n, Q = q + sp * n;
+                    if (cls((1ull << P) ^ (1ull << Q)) != me) continue;
+                    int mode[2] = {P, Q}, dag[2] = {1, 0};
+                    add_operator_product(mode, dag, 2, c, acc);
+                }
+        for (int s1 = 0; s1 < 2; ++s1)
+            for (int s2 = 0; s2 < 2; ++s2)
+                for (int p = 0; p < n; ++p)
+                    for (int q = 0; q < n; ++q)
+                        for (int r = 0; r < n; ++r)
+                            for (int s = 0; s < n; ++s) {
+                                double c = h2[((size_t(p) * n + q) * n + r) * n + s];
+                                if (c == 0.0) continue;
+                                int P = p + s1 * n, Q = q + s1 * n;
+                                int R = r + s2 * n, S = s + s2 * n;
+                                if (P == R || Q == S) continue;   // a+a+ / aa vanish
+                                const uint64_t x = (1ull << P) ^ (1ull << Q) ^ (1ull << R) ^
+                                                   (1ull << S);
+                                if (cls(x) != me) continue;
+                                // 1/2 (pq|rs) a+_P a+_R a_S a_Q
+                                int mode[4] = {P, R, S, Q}, dag[4] = {1, 1, 0, 0};
+                                add_operator_product(mode, dag, 4, 0.5 * c, acc);
+                            }
+    }
     struct Term { uint64_t x, z; double c; };
     std::vector<Term> terms;
-    terms.reserve(acc.size());
     bool odd_y = false;
-    acc.for_each([&](uint64_t key, double c) {
-        if (std::fabs(c) <= prune_tol) return;
-        uint64_t x = key & 0xffffffffull, z = key >> 32;
-        if (__builtin_popcountll(x & z) & 1) odd_y = true;
-        terms.push_back({x, z, c});
-    });
+    for (const PauliAcc &acc : part)
+        acc.for_each([&](uint64_t key, double c) {
+            if (std::fabs(c) <= prune_tol) return;
+            uint64_t x = key & 0xffffffffull, z = key >> 32;
+            if (__builtin_popcountll(x & z) & 1) odd_y = true;
+            terms.push_back({x, z, c});
+        });
     if (odd_y) {
         err = "Pauli term with an odd number of Y survives: the "
               "Hamiltonian is not real symmetric";

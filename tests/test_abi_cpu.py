@@ -196,3 +196,27 @@ def test_pauli_table_counts_and_pruning(lib):
     assert len(off) - 1 == 1 + 2 * c2 + 2 * c4 + c2 * c2    # 286 at 12 qubits
     x2, _, cp, _ = pauli_table(lib, h1, h2, 0.0, n, prune=1e-3)
     assert len(x2) < len(x) and np.abs(cp).min() > 1e-3
+
+
+def test_pauli_table_identical_across_thread_counts():
+    """The host Pauli table is built by threads that each own a class of
+    X-masks and visit the products in one fixed order, so every coefficient
+    is summed in the same order whatever the thread count: the table built
+    with 1, 3 and 8 threads (separate processes) is identical bit for bit."""
+    import subprocess
+    import sys
+    code = (
+        "import ctypes, hashlib, sys; sys.path.insert(0, {root!r}); import numpy as np, synth;"
+        "from tests.test_abi_cpu import pauli_table; from paper_2604_01176_gb300 import _abi;"
+        "h1, h2, ec = synth.integrals(10, 1002);"
+        "x, z, c, off = pauli_table(_abi.load(), h1, h2, ec, 10);"
+        "print(hashlib.sha256(x.tobytes() + z.tobytes() + c.tobytes() + off.tobytes()).hexdigest())"
+    ).format(root=ROOT)
+    digests = set()
+    for threads in ("1", "3", "8"):
+        env = dict(os.environ, OMP_NUM_THREADS=threads)
+        out = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT,
+                             capture_output=True, text=True, timeout=300)
+        assert out.returncode == 0, out.stderr
+        digests.add(out.stdout.strip().splitlines()[-1])
+    assert len(digests) == 1
