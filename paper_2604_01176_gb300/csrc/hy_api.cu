@@ -2347,13 +2347,17 @@ struct SupportProgram {
     int max_steps = 0;
     int64_t m = 0, steps = 0;
     int64_t *key = nullptr, *step_len = nullptr;
-    int32_t *tab = nullptr;
+    // the pair lists of the steps (hy_kernels.cuh, ProgTabs), their counts
+    // and the operator of each step
+    int2 *pairs = nullptr;
+    int *npairs = nullptr, *step_l = nullptr;
     int *flag = nullptr;
     // supports beyond one CTA's shared memory (allocated on first use): keys
-    // in listing order, tables and the index map over Omega_CIk (the vectors
-    // live in the shared memory of a cluster of CTAs)
+    // in listing order, pair lists per cluster rank and the index map over
+    // Omega_CIk (the vectors live in the shared memory of a cluster of CTAs)
     int64_t *key_big = nullptr;
-    int32_t *tab_big = nullptr, *idx_map = nullptr;
+    int2 *pairs_big = nullptr;
+    int32_t *idx_map = nullptr;
     // H restricted to the program's support (rows in key order, columns as
     // determinant indices): valid while hss_ok
     // (row t's entries at [t * hss_w, t * hss_w + hss_cnt[t]))
@@ -2368,7 +2372,8 @@ struct SupportProgram {
 
 hy_status prog_create(const hy_ham *h, int max_steps, SupportProgram **out)
 {
-    if (!h || !out || max_steps < 1 || max_steps > 254) return fail(HY_ERR_ARG, "bad arguments");
+    if (!h || !out || max_steps < 1 || max_steps > hy::k::kProgSteps)
+        return fail(HY_ERR_ARG, "bad arguments");
     *out = nullptr;
     SupportProgram *g = new (std::nothrow) SupportProgram;
     if (!g) return fail(HY_ERR_OOM, "host allocation failed");
@@ -2377,7 +2382,10 @@ hy_status prog_create(const hy_ham *h, int max_steps, SupportProgram **out)
     cudaError_t e = cudaMalloc(&g->key, size_t(hy::k::kProgMax) * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc(&g->step_len, size_t(max_steps) * sizeof(int64_t));
     if (e == cudaSuccess)
-        e = cudaMalloc(&g->tab, size_t(max_steps) * hy::k::kProgMax * sizeof(int32_t));
+        e = cudaMalloc(&g->pairs, size_t(max_steps) * hy::k::kProgMax * sizeof(int2));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&g->npairs, size_t(max_steps) * hy::k::kClusterCtas * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&g->step_l, size_t(max_steps) * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&g->flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(g->flag, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -2393,10 +2401,12 @@ void prog_destroy(SupportProgram *g)
     if (!g) return;
     cudaFree(g->key);
     cudaFree(g->step_len);
-    cudaFree(g->tab);
+    cudaFree(g->pairs);
+    cudaFree(g->npairs);
+    cudaFree(g->step_l);
     cudaFree(g->flag);
     cudaFree(g->key_big);
-    cudaFree(g->tab_big);
+    cudaFree(g->pairs_big);
     cudaFree(g->idx_map);
     cudaFree(g->d_nnz);
     cudaFree(g->hss_cnt);
@@ -2443,20 +2453,22 @@ hy_status prog_compile(SupportProgram *g, const SparseState *s, int64_t m, const
     hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
     if (m <= hy::k::kProgMax) {
         HY_CUDA(hy::k::prog_compile(s->list, m, g->step_len, int(steps), sv_op_args(g->h, p), ops,
-                                    int(L), g->key, g->tab, g->flag, st),
+                                    int(L), g->key, g->pairs, g->npairs, g->step_l, g->flag, st),
                 "support program");
     } else {
         const size_t kb = size_t(hy::k::kProgBig);
         cudaError_t e = cudaSuccess;
         if (!g->key_big) e = cudaMalloc(&g->key_big, kb * sizeof(int64_t));
-        if (e == cudaSuccess && !g->tab_big)
-            e = cudaMalloc(&g->tab_big, size_t(g->max_steps) * kb * sizeof(int32_t));
+        // kClusterCtas lists of ceil(m / kClusterCtas) <= kb / kClusterCtas
+        // pairs per step
+        if (e == cudaSuccess && !g->pairs_big)
+            e = cudaMalloc(&g->pairs_big, size_t(g->max_steps) * kb * sizeof(int2));
         if (e == cudaSuccess && !g->idx_map)
             e = cudaMalloc(&g->idx_map, size_t(g->h->N) * sizeof(int32_t));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(support program)");
         HY_CUDA(hy::k::prog_compile_big(s->list, m, g->step_len, int(steps), sv_op_args(g->h, p),
-                                        ops, int(L), s->bits, g->key_big, g->tab_big, g->idx_map,
-                                        g->flag, st),
+                                        ops, int(L), s->bits, g->key_big, g->pairs_big,
+                                        g->npairs, g->step_l, g->idx_map, g->flag, st),
                 "support program");
     }
     g->m = m;
@@ -2561,6 +2573,24 @@ hy_status prog_hss_apply(const SupportProgram *g, const void *psi, void *sigma, 
     return HY_OK;
 }
 
+namespace {
+// the compiled program's tables as the kernels read them
+hy::k::ProgTabs prog_tabs(const SupportProgram *g)
+{
+    hy::k::ProgTabs t;
+    const bool big = g->m > hy::k::kProgMax;
+    t.key = big ? g->key_big : g->key;
+    t.pairs = big ? g->pairs_big : g->pairs;
+    t.npairs = g->npairs;
+    t.step_l = g->step_l;
+    t.m = int(g->m);
+    t.steps = int(g->steps);
+    t.ranks = big ? hy::k::kClusterCtas : 1;
+    t.chunk = big ? int((g->m + hy::k::kClusterCtas - 1) / hy::k::kClusterCtas) : int(g->m);
+    return t;
+}
+}  // namespace
+
 hy_status prog_prepare(const SupportProgram *g, SparseState *s, const hy_pool *p,
                        const int32_t *ops, const double *cs, int64_t L, bool renorm,
                        double *norm2, void *stream)
@@ -2569,26 +2599,23 @@ hy_status prog_prepare(const SupportProgram *g, SparseState *s, const hy_pool *p
         return fail(HY_ERR_ARG, "bad arguments");
     cudaStream_t st = as_stream(stream);
     hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
+    const hy::k::ProgTabs t = prog_tabs(g);
     if (g->m > hy::k::kProgMax) {
         if (s->dt == HY_F64)
-            HY_CUDA(hy::k::prog_prepare_big<double>(g->key_big, g->tab_big, g->m, p->d_desc, ops,
-                                                    cs, int(L), renorm, norm2,
+            HY_CUDA(hy::k::prog_prepare_big<double>(t, cs, renorm, norm2,
                                                     static_cast<double *>(s->v), st),
                     "support program preparation");
         else
-            HY_CUDA(hy::k::prog_prepare_big<float>(g->key_big, g->tab_big, g->m, p->d_desc, ops,
-                                                   cs, int(L), renorm, norm2,
+            HY_CUDA(hy::k::prog_prepare_big<float>(t, cs, renorm, norm2,
                                                    static_cast<float *>(s->v), st),
                     "support program preparation");
         return HY_OK;
     }
     if (s->dt == HY_F64)
-        HY_CUDA(hy::k::prog_prepare<double>(g->key, g->tab, g->m, p->d_desc, ops, cs, int(L),
-                                            renorm, norm2, static_cast<double *>(s->v), st),
+        HY_CUDA(hy::k::prog_prepare<double>(t, cs, renorm, norm2, static_cast<double *>(s->v), st),
                 "support program preparation");
     else
-        HY_CUDA(hy::k::prog_prepare<float>(g->key, g->tab, g->m, p->d_desc, ops, cs, int(L),
-                                           renorm, norm2, static_cast<float *>(s->v), st),
+        HY_CUDA(hy::k::prog_prepare<float>(t, cs, renorm, norm2, static_cast<float *>(s->v), st),
                 "support program preparation");
     return HY_OK;
 }
@@ -2602,26 +2629,25 @@ hy_status prog_grad(const SupportProgram *g, const hy_pool *p, const int32_t *op
         return fail(HY_ERR_ARG, "bad arguments");
     cudaStream_t st = as_stream(stream);
     hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
+    const hy::k::ProgTabs t = prog_tabs(g);
     if (g->m > hy::k::kProgMax) {
         if (dt == HY_F64)
-            HY_CUDA(hy::k::prog_grad_big<double>(g->key_big, g->tab_big, g->m, p->d_desc, ops, cs,
-                                                 int(L), static_cast<const double *>(sigma), norm2,
-                                                 g_out, st),
+            HY_CUDA(hy::k::prog_grad_big<double>(t, cs, int(L), static_cast<const double *>(sigma),
+                                                 norm2, g_out, st),
                     "support program gradient");
         else
-            HY_CUDA(hy::k::prog_grad_big<float>(g->key_big, g->tab_big, g->m, p->d_desc, ops, cs,
-                                                int(L), static_cast<const float *>(sigma), norm2,
-                                                g_out, st),
+            HY_CUDA(hy::k::prog_grad_big<float>(t, cs, int(L), static_cast<const float *>(sigma),
+                                                norm2, g_out, st),
                     "support program gradient");
         return HY_OK;
     }
     if (dt == HY_F64)
-        HY_CUDA(hy::k::prog_grad<double>(g->key, g->tab, g->m, p->d_desc, ops, cs, int(L),
-                                         static_cast<const double *>(sigma), norm2, g_out, st),
+        HY_CUDA(hy::k::prog_grad<double>(t, cs, int(L), static_cast<const double *>(sigma), norm2,
+                                         g_out, st),
                 "support program gradient");
     else
-        HY_CUDA(hy::k::prog_grad<float>(g->key, g->tab, g->m, p->d_desc, ops, cs, int(L),
-                                        static_cast<const float *>(sigma), norm2, g_out, st),
+        HY_CUDA(hy::k::prog_grad<float>(t, cs, int(L), static_cast<const float *>(sigma), norm2,
+                                        g_out, st),
                 "support program gradient");
     return HY_OK;
 }

@@ -359,53 +359,71 @@ cudaError_t sv_prepare(const SVec<T> &x, const SvOpArgs &o, const int32_t *ops, 
 // Support programs (hy_sparse.cu).  The support of U_L .. U_1|HF> is fixed by
 // the ansatz (a rotation lists its partners whatever its angle), so once it
 // is known each constituent rotation is a fixed pairing of its elements:
-//   key[t]  = (determinant << 8) | (step that listed it + 1), ascending over
-//             the m <= kProgMax support elements (t = local index);
-//   tab[s*m + t] = +-(p + 1) when step s's forward string takes t to p with
-//             sign +-1 and p is in the support, else 0;
+//   key[t]  = (determinant << 8) | (step that listed it + 1) for the m
+//             support elements (t = local index; ascending for m <=
+//             kProgMax, listing order beyond);
+//   the pairs of step s: {t, +-(p + 1)} for every t that step s's forward
+//             string takes to a support element p with sign +-1.  They are
+//             kept as compact lists, one per step and part of the support:
+//             with `ranks` parts of `chunk` = ceil(m / ranks) elements (one
+//             part for one CTA, kClusterCtas for a cluster), the pairs of
+//             step s whose domain end t lies in part r are
+//             pairs[(s * ranks + r) * chunk + i], i < npairs[s * ranks + r],
+//             in no fixed order: the pairs of one step are disjoint (an image
+//             end has no forward image), so no result depends on it;
+//   step_l[s] = the operator (position in the ansatz) of step s;
 //   *flag   = 1 when some generator A_l = sum (C - C^dagger) of op l would
 //             leave the support from an element that op l's own later
 //             constituents listed (then the forward gradient cannot use the
 //             tables and must take the general path).
 constexpr int kProgMax = 12288;   // shared-memory vectors: 2 x 12288 doubles per CTA
+constexpr int kProgSteps = 254;   // steps of one program (8-bit birth tags)
+struct ProgTabs {
+    const int64_t *key;
+    const int2 *pairs;
+    const int *npairs;
+    const int *step_l;
+    int m, steps, ranks, chunk;
+};
 // list: the m support elements in the order a structural sv_prepare listed
-// them, step_len its lengths after each of the `steps` rotations
+// them, step_len its lengths after each of the `steps` rotations; pairs holds
+// steps * m entries, npairs `steps` counts, step_l `steps` entries
 cudaError_t prog_compile(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
                          const SvOpArgs &o, const int32_t *ops, int L, int64_t *key,
-                         int32_t *tab, int *flag, cudaStream_t st);
-// one CTA: the m-vector U_L .. U_1|HF> by the tables in shared memory, then
-// (renorm) divided by its FP64 norm (*norm2, if not null), written to
-// v[key[t] >> 8]; v outside the support is left as is
+                         int2 *pairs, int *npairs, int *step_l, int *flag, cudaStream_t st);
+// one CTA: the m-vector U_L .. U_1|HF> by the pair lists in shared memory,
+// with cs[2l], cs[2l+1] = cos, sin theta_l, then (renorm) divided by its FP64
+// norm (*norm2, if not null), written to v[key[t] >> 8]; v outside the
+// support is left as is
 template <typename T>
-cudaError_t prog_prepare(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
-                         const int32_t *ops, const double *cs, int L, bool renorm, double *norm2,
-                         T *v, cudaStream_t st);
-// L CTAs: g[l] = dE/dtheta_l in forward mode by the tables, CTA l forming
+cudaError_t prog_prepare(const ProgTabs &g, const double *cs, bool renorm, double *norm2, T *v,
+                         cudaStream_t st);
+// L CTAs: g[l] = dE/dtheta_l in forward mode by the pair lists, CTA l forming
 // U_L .. U_{l+1} A_l U_l .. U_1|HF> in shared memory and reading sigma (dense)
 // on the support; norm2 as for sv_grad_fwd
 template <typename T>
-cudaError_t prog_grad(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
-                      const int32_t *ops, const double *cs, int L, const T *sigma,
-                      const double *norm2, double *g, cudaStream_t st);
+cudaError_t prog_grad(const ProgTabs &g, const double *cs, int L, const T *sigma,
+                      const double *norm2, double *gout, cudaStream_t st);
 // Support programs beyond one CTA's shared memory, kProgMax < m <= kProgBig:
 // the support in listing order (key unsorted), local indices through idx_map
 // (N int32 over Omega_CIk, read where `bits`, the listing's membership
 // bitmap, has the determinant), each vector split over the distributed shared
 // memory of a cluster of 8 CTAs (prepare: one cluster; gradient: one cluster
-// per angle)
+// per angle); the pair lists per step and CTA (ranks = kClusterCtas), pairs
+// holding steps * kClusterCtas * ceil(m / kClusterCtas) entries and npairs
+// steps * kClusterCtas counts
 constexpr int64_t kProgBig = 65536;
+constexpr int kClusterCtas = 8;
 cudaError_t prog_compile_big(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
                              const SvOpArgs &o, const int32_t *ops, int L, const uint32_t *bits,
-                             int64_t *key, int32_t *tab, int32_t *idx_map, int *flag,
-                             cudaStream_t st);
+                             int64_t *key, int2 *pairs, int *npairs, int *step_l,
+                             int32_t *idx_map, int *flag, cudaStream_t st);
 template <typename T>
-cudaError_t prog_prepare_big(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
-                             const int32_t *ops, const double *cs, int L, bool renorm,
-                             double *norm2, T *v, cudaStream_t st);
+cudaError_t prog_prepare_big(const ProgTabs &g, const double *cs, bool renorm, double *norm2,
+                             T *v, cudaStream_t st);
 template <typename T>
-cudaError_t prog_grad_big(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
-                          const int32_t *ops, const double *cs, int L, const T *sigma,
-                          const double *norm2, double *g, cudaStream_t st);
+cudaError_t prog_grad_big(const ProgTabs &g, const double *cs, int L, const T *sigma,
+                          const double *norm2, double *gout, cudaStream_t st);
 // The Hamiltonian restricted to a support S (both rows and columns in S):
 // row t is the determinant key[t] >> 8 of a support program, its entries
 // the couplings to determinants of S (membership bitmap `bits`), columns

@@ -995,96 +995,257 @@ __device__ __forceinline__ int prog_find(const int64_t *__restrict__ key, int m,
     return lo < m && (key[lo] >> 8) == d ? lo : -1;
 }
 
-// tab[s*m + t] for step s = blockIdx.y (constituent ci of op l)
+// warp-aggregated append: every lane with `has` adds v to list `slot`
+// (count counts[slot], items from out + slot * stride); the lanes of one warp
+// that share a slot take one atomic.  Every lane of the warp must call it.
+__device__ __forceinline__ void warp_append(bool has, int slot, int2 v, int2 *__restrict__ out,
+                                            int64_t stride, int *__restrict__ counts)
+{
+    const unsigned act = __ballot_sync(0xffffffffu, has);
+    if (!has) return;
+    const unsigned grp = __match_any_sync(act, slot);
+    const int lane = int(threadIdx.x & 31);
+    const int leader = __ffs(int(grp)) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counts + slot, __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    out[int64_t(slot) * stride + base + __popc(grp & ((1u << lane) - 1u))] = v;
+}
+
+// the op (l), constituent (ci) and last step of op l for step s; l = L when
+// s is beyond the ansatz's steps
+__device__ __forceinline__ void prog_step_op(const int32_t *__restrict__ desc,
+                                             const int32_t *__restrict__ ops, int L, int s, int &l,
+                                             int &ci, int &last)
+{
+    int acc = 0;
+    ci = 0;
+    last = -1;
+    for (l = 0; l < L; ++l) {
+        const int nc = desc[11 * ops[l]];
+        if (s < acc + nc) {
+            ci = s - acc;
+            last = acc + nc - 1;
+            return;
+        }
+        acc += nc;
+    }
+}
+
+// the pairs of step s = blockIdx.y (constituent ci of op l), one list per step
 __global__ void __launch_bounds__(256)
 k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t *__restrict__ ops,
-              int L, int32_t *__restrict__ tab, int *__restrict__ flag)
+              int L, int2 *__restrict__ pairs, int *__restrict__ npairs, int *__restrict__ step_l,
+              int *__restrict__ flag)
 {
     __shared__ uint32_t C[33][33];
     for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
     __syncthreads();
     const int s = blockIdx.y;
-    int l = 0, ci = 0, last = -1, acc = 0;
-    for (; l < L; ++l) {
-        const int nc = o.desc[11 * ops[l]];
-        if (s < acc + nc) {
-            ci = s - acc;
-            last = acc + nc - 1;
-            break;
-        }
-        acc += nc;
-    }
+    int l, ci, last;
+    prog_step_op(o.desc, ops, L, s, l, ci, last);
+    if (l >= L) return;                              // whole block
+    if (blockIdx.x == 0 && threadIdx.x == 0) step_l[s] = l;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m || l >= L) return;
-    int fw[4], bw[4], len;
-    op_strings(o.desc + 11 * ops[l] + 1 + 5 * ci, fw, bw, len);
-    const int64_t kt = key[t], d = kt >> 8;
-    const int birth = int(kt & 255) - 1;             // -1: |HF>, else the listing step
-    const int n = o.n;
-    const uint64_t lowm = (1ull << n) - 1;
-    const uint64_t mask = uint64_t(o.astr[d / o.Nb]) | (uint64_t(o.bstr[d % o.Nb]) << n);
-    uint64_t u = mask;
-    int sg = 1;
     int32_t e = 0;
-    bool escape = false;
-    if (apply_string(fw, len, u, sg, o.qubit)) {
-        const int64_t img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
-        const int p = prog_find(key, m, img);
-        if (p >= 0) e = sg > 0 ? p + 1 : -(p + 1);
-        else escape = true;
-    } else {
-        u = mask;
-        sg = 1;
-        if (apply_string(bw, len, u, sg, o.qubit)) {
-            const int64_t dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
-            escape = prog_find(key, m, dom) < 0;
+    if (t < m) {
+        int fw[4], bw[4], len;
+        op_strings(o.desc + 11 * ops[l] + 1 + 5 * ci, fw, bw, len);
+        const int64_t kt = key[t], d = kt >> 8;
+        const int birth = int(kt & 255) - 1;         // -1: |HF>, else the listing step
+        const int n = o.n;
+        const uint64_t lowm = (1ull << n) - 1;
+        const uint64_t mask = uint64_t(o.astr[d / o.Nb]) | (uint64_t(o.bstr[d % o.Nb]) << n);
+        uint64_t u = mask;
+        int sg = 1;
+        bool escape = false;
+        if (apply_string(fw, len, u, sg, o.qubit)) {
+            const int64_t img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
+                                rank_bits(uint32_t(u >> n), C);
+            const int p = prog_find(key, m, img);
+            if (p >= 0) e = sg > 0 ? p + 1 : -(p + 1);
+            else escape = true;
+        } else {
+            u = mask;
+            sg = 1;
+            if (apply_string(bw, len, u, sg, o.qubit)) {
+                const int64_t dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
+                                    rank_bits(uint32_t(u >> n), C);
+                escape = prog_find(key, m, dom) < 0;
+            }
         }
+        // a partner outside the support is harmless to the rotations (both
+        // ends are zero when step s runs) but not to op l's generator when t
+        // is in phi_l's support without having been seen by step s: listed
+        // later by op l's own constituents
+        if (escape && birth > s && birth <= last) *flag = 1;
     }
-    tab[int64_t(s) * m + t] = e;
-    // a partner outside the support is harmless to the rotations (both ends
-    // are zero when step s runs) but not to op l's generator when t is in
-    // phi_l's support without having been seen by step s: listed later by
-    // op l's own constituents
-    if (escape && birth > s && birth <= last) *flag = 1;
+    warp_append(e != 0, s, make_int2(t, e), pairs, m, npairs);
 }
 
-// one constituent rotation on a local vector (pairs are disjoint: an image
-// end has no forward image)
-template <typename T>
-__device__ __forceinline__ void prog_rotate(T *x, const int32_t *__restrict__ row, int m, T c, T sn)
+// pairs a thread takes per round of a step (loaded together, so that their
+// latencies overlap)
+constexpr int kPairU = 4;
+
+__device__ __forceinline__ void pairs_load(int2 (&q)[kPairU], const int2 *__restrict__ pr, int n,
+                                           int i0)
 {
-    for (int t = threadIdx.x; t < m; t += blockDim.x) {
-        const int e = row[t];
+#pragma unroll
+    for (int k = 0; k < kPairU; ++k) {
+        const int i = i0 + k * int(blockDim.x);
+        q[k] = i < n ? pr[i] : make_int2(0, 0);
+    }
+}
+
+// a vector in one CTA's shared memory
+template <typename T>
+struct LocalVec {
+    T *x;
+    __device__ __forceinline__ T *dom(int t) const { return x + t; }
+    __device__ __forceinline__ T *img(int p) const { return x + p; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+// a vector split over the shared memories of a cluster's CTAs, chunk
+// elements each: element t lives in CTA t / chunk and is reached through
+// distributed shared memory when it is another CTA's.  A CTA's pair lists
+// hold the pairs whose domain end is its own
+template <typename T>
+struct ClusterVec {
+    T *loc;
+    int chunk, rank, t0;
+    cg::cluster_group *cl;
+    __device__ __forceinline__ T *dom(int t) const { return loc + (t - t0); }
+    __device__ __forceinline__ T *img(int p) const
+    {
+        const int r = p / chunk;
+        return r == rank ? loc + (p - t0) : cl->map_shared_rank(loc, r) + (p - r * chunk);
+    }
+    __device__ __forceinline__ void sync() const { cl->sync(); }
+};
+
+// one round of a constituent rotation (pairs are disjoint: each has one
+// writer)
+template <typename T, class V>
+__device__ __forceinline__ void pairs_rotate(const V &x, const int2 (&q)[kPairU], T c, T sn)
+{
+#pragma unroll
+    for (int k = 0; k < kPairU; ++k) {
+        const int e = q[k].y;
         if (e == 0) continue;
         const int p = (e > 0 ? e : -e) - 1;
         const T ss = e > 0 ? sn : -sn;
-        const T xv = x[t], yv = x[p];
-        x[t] = c * xv - ss * yv;
-        x[p] = c * yv + ss * xv;
+        T *xt = x.dom(q[k].x), *xp = x.img(p);
+        const T xv = *xt, yv = *xp;
+        *xt = c * xv - ss * yv;
+        *xp = c * yv + ss * xv;
     }
-    __syncthreads();
 }
 
-// w <- w + (C - C^dagger) f for one constituent: C|t> = sg|p> adds sg f_t to
-// w_p and -sg f_p to w_t
-template <typename T>
-__device__ __forceinline__ void prog_generator(const T *f, T *w, const int32_t *__restrict__ row,
-                                               int m)
+// one round of w <- w + (C - C^dagger) f for one constituent: C|t> = sg|p>
+// adds sg f_t to w_p and -sg f_p to w_t
+template <class V>
+__device__ __forceinline__ void pairs_generator(const V &f, const V &w, const int2 (&q)[kPairU])
 {
-    for (int t = threadIdx.x; t < m; t += blockDim.x) {
-        const int e = row[t];
+#pragma unroll
+    for (int k = 0; k < kPairU; ++k) {
+        const int e = q[k].y;
         if (e == 0) continue;
-        const int p = (e > 0 ? e : -e) - 1;
-        const T ft = f[t], fp = f[p];
+        const int t = q[k].x, p = (e > 0 ? e : -e) - 1;
+        const auto ft = *f.dom(t), fp = *f.img(p);
+        auto *wp = w.img(p), *wt = w.dom(t);
         if (e > 0) {
-            w[p] += ft;
-            w[t] -= fp;
+            *wp += ft;
+            *wt -= fp;
         } else {
-            w[p] -= ft;
-            w[t] += fp;
+            *wp -= ft;
+            *wt += fp;
         }
     }
-    __syncthreads();
+}
+
+// per-step values of a program in shared memory: this part's pair counts,
+// the operator of each step and its cos / sin
+template <typename T>
+struct ProgSteps {
+    int np[kProgSteps];
+    int sl[kProgSteps];
+    T c[kProgSteps], sn[kProgSteps];
+};
+
+// fills st (the caller synchronises); every thread of the CTA calls it
+template <typename T>
+__device__ __forceinline__ void prog_load_steps(const ProgTabs &g, int rank,
+                                                const double *__restrict__ cs, ProgSteps<T> &st)
+{
+    for (int s = threadIdx.x; s < g.steps; s += blockDim.x) {
+        const int l = g.step_l[s];
+        st.sl[s] = l;
+        st.np[s] = g.npairs[s * g.ranks + rank];
+        st.c[s] = T(cs[2 * l]);
+        st.sn[s] = T(cs[2 * l + 1]);
+    }
+}
+
+// steps [s0, s1) on x, one barrier (CTA or cluster) after each; the first
+// round of the next step's pairs is loaded while the current step runs
+template <typename T, class V>
+__device__ __forceinline__ void prog_run(const V &x, const ProgTabs &g, int rank,
+                                         const ProgSteps<T> &st, int s0, int s1)
+{
+    if (s0 >= s1) return;
+    const int R = kPairU * int(blockDim.x);
+    const int64_t stride = g.chunk;
+    int2 q[kPairU];
+    pairs_load(q, g.pairs + (int64_t(s0) * g.ranks + rank) * stride, st.np[s0], int(threadIdx.x));
+    for (int s = s0; s < s1; ++s) {
+        const int n = st.np[s];
+        const int2 *pr = g.pairs + (int64_t(s) * g.ranks + rank) * stride;
+        int2 nq[kPairU];
+        if (s + 1 < s1)
+            pairs_load(nq, g.pairs + (int64_t(s + 1) * g.ranks + rank) * stride, st.np[s + 1],
+                       int(threadIdx.x));
+        pairs_rotate<T>(x, q, st.c[s], st.sn[s]);
+        for (int i0 = int(threadIdx.x) + R; i0 < n; i0 += R) {
+            int2 r[kPairU];
+            pairs_load(r, pr, n, i0);
+            pairs_rotate<T>(x, r, st.c[s], st.sn[s]);
+        }
+        x.sync();
+        if (s + 1 < s1) {
+#pragma unroll
+            for (int k = 0; k < kPairU; ++k) q[k] = nq[k];
+        }
+    }
+}
+
+// the generator of op lg (its constituent steps [b, e), in order) from f
+// into w, one barrier after each constituent
+template <class V>
+__device__ __forceinline__ void prog_generate(const V &f, const V &w, const ProgTabs &g, int rank,
+                                              const int *np, int b, int e)
+{
+    const int R = kPairU * int(blockDim.x);
+    for (int s = b; s < e; ++s) {
+        const int2 *pr = g.pairs + (int64_t(s) * g.ranks + rank) * g.chunk;
+        for (int i0 = int(threadIdx.x); i0 < np[s]; i0 += R) {
+            int2 q[kPairU];
+            pairs_load(q, pr, np[s], i0);
+            pairs_generator(f, w, q);
+        }
+        f.sync();
+    }
+}
+
+// the steps of op lg: [*b, *e) (steps are in ansatz order)
+__device__ __forceinline__ void prog_op_steps(const int *sl, int steps, int lg, int &b, int &e)
+{
+    b = 0;
+    e = 0;
+    for (int s = 0; s < steps; ++s) {
+        if (sl[s] < lg) b = s + 1;
+        if (sl[s] <= lg) e = s + 1;
+    }
 }
 
 // FP64 block sum, valid in thread 0
@@ -1102,26 +1263,23 @@ __device__ __forceinline__ double prog_block_sum(double acc, double *red)
 
 template <typename T>
 __global__ void __launch_bounds__(kProgThreads)
-k_prog_prepare(const int64_t *__restrict__ key, const int32_t *__restrict__ tab, int m,
-               const int32_t *__restrict__ desc, const int32_t *__restrict__ ops,
-               const double *__restrict__ cs, int L, int renorm, double *__restrict__ norm2,
+k_prog_prepare(ProgTabs g, const double *__restrict__ cs, int renorm, double *__restrict__ norm2,
                T *__restrict__ v)
 {
     extern __shared__ __align__(16) unsigned char prog_sm[];
-    T *x = reinterpret_cast<T *>(prog_sm);
+    const LocalVec<T> x{reinterpret_cast<T *>(prog_sm)};
+    __shared__ ProgSteps<T> st;
     __shared__ double red[kProgThreads / 32];
     __shared__ double fac;
-    for (int t = threadIdx.x; t < m; t += blockDim.x) x[t] = t == 0 ? T(1) : T(0);   // |HF>
+    const int m = g.m;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) x.x[t] = t == 0 ? T(1) : T(0);   // |HF>
+    prog_load_steps(g, 0, cs, st);
     __syncthreads();
-    int s = 0;
-    for (int l = 0; l < L; ++l) {
-        const int nc = desc[11 * ops[l]];
-        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
-        for (int ci = 0; ci < nc; ++ci, ++s) prog_rotate(x, tab + int64_t(s) * m, m, c, sn);
-    }
+    prog_run<T>(x, g, 0, st, 0, g.steps);
     if (renorm) {
         double acc = 0.0;
-        for (int t = threadIdx.x; t < m; t += blockDim.x) acc = fma(double(x[t]), double(x[t]), acc);
+        for (int t = threadIdx.x; t < m; t += blockDim.x)
+            acc = fma(double(x.x[t]), double(x.x[t]), acc);
         const double sum = prog_block_sum(acc, red);
         if (threadIdx.x == 0) {
             if (norm2) *norm2 = sum;
@@ -1129,48 +1287,40 @@ k_prog_prepare(const int64_t *__restrict__ key, const int32_t *__restrict__ tab,
         }
         __syncthreads();
         const T f = T(fac);
-        for (int t = threadIdx.x; t < m; t += blockDim.x) v[key[t] >> 8] = x[t] * f;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) v[g.key[t] >> 8] = x.x[t] * f;
     } else {
-        for (int t = threadIdx.x; t < m; t += blockDim.x) v[key[t] >> 8] = x[t];
+        for (int t = threadIdx.x; t < m; t += blockDim.x) v[g.key[t] >> 8] = x.x[t];
     }
 }
 
 // CTA l: g[l] = scale <sigma| U_L .. U_{l+1} A_l U_l .. U_1 |HF>
 template <typename T>
 __global__ void __launch_bounds__(kProgThreads)
-k_prog_grad(const int64_t *__restrict__ key, const int32_t *__restrict__ tab, int m,
-            const int32_t *__restrict__ desc, const int32_t *__restrict__ ops,
-            const double *__restrict__ cs, int L, const T *__restrict__ sigma,
-            const double *__restrict__ norm2, double *__restrict__ g)
+k_prog_grad(ProgTabs g, const double *__restrict__ cs, const T *__restrict__ sigma,
+            const double *__restrict__ norm2, double *__restrict__ gout)
 {
     extern __shared__ __align__(16) unsigned char prog_sm[];
-    T *f = reinterpret_cast<T *>(prog_sm), *w = f + m;
+    const int m = g.m;
+    const LocalVec<T> f{reinterpret_cast<T *>(prog_sm)}, w{reinterpret_cast<T *>(prog_sm) + m};
+    __shared__ ProgSteps<T> st;
     __shared__ double red[kProgThreads / 32];
     const int lg = blockIdx.x;
     for (int t = threadIdx.x; t < m; t += blockDim.x) {
-        f[t] = t == 0 ? T(1) : T(0);
-        w[t] = T(0);
+        f.x[t] = t == 0 ? T(1) : T(0);
+        w.x[t] = T(0);
     }
+    prog_load_steps(g, 0, cs, st);
     __syncthreads();
-    int s = 0;
-    for (int l = 0; l <= lg; ++l) {                  // phi_lg = U_lg .. U_1 |HF>
-        const int nc = desc[11 * ops[l]];
-        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
-        for (int ci = 0; ci < nc; ++ci, ++s) prog_rotate(f, tab + int64_t(s) * m, m, c, sn);
-    }
-    const int ncg = desc[11 * ops[lg]];
-    for (int ci = 0; ci < ncg; ++ci)                 // constituents add in order
-        prog_generator(f, w, tab + int64_t(s - ncg + ci) * m, m);
-    for (int l = lg + 1; l < L; ++l) {
-        const int nc = desc[11 * ops[l]];
-        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
-        for (int ci = 0; ci < nc; ++ci, ++s) prog_rotate(w, tab + int64_t(s) * m, m, c, sn);
-    }
+    int b, e;
+    prog_op_steps(st.sl, g.steps, lg, b, e);
+    prog_run<T>(f, g, 0, st, 0, e);                  // phi_lg = U_lg .. U_1 |HF>
+    prog_generate(f, w, g, 0, st.np, b, e);          // constituents add in order
+    prog_run<T>(w, g, 0, st, e, g.steps);
     double acc = 0.0;
     for (int t = threadIdx.x; t < m; t += blockDim.x)
-        acc = fma(double(w[t]), double(sigma[key[t] >> 8]), acc);
+        acc = fma(double(w.x[t]), double(sigma[g.key[t] >> 8]), acc);
     const double dot = prog_block_sum(acc, red);
-    if (threadIdx.x == 0) g[lg] = (norm2 ? 2.0 / sqrt(*norm2) : 2.0) * dot;
+    if (threadIdx.x == 0) gout[lg] = (norm2 ? 2.0 / sqrt(*norm2) : 2.0) * dot;
 }
 
 // ---------------------------------------------------------------------------
@@ -1180,7 +1330,7 @@ k_prog_grad(const int64_t *__restrict__ key, const int32_t *__restrict__ tab, in
 // over Omega_CIk gives each listed determinant its local index (read only
 // where the listing's membership bitmap has the determinant), and the
 // vectors are split over the shared memories of a thread-block cluster
-// (below).  Same tables, same arithmetic, same order of operations per
+// (ClusterVec).  Same pairs, same arithmetic, same order of operations per
 // element.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
@@ -1202,123 +1352,60 @@ k_prog_keys_big(const int64_t *__restrict__ list, int64_t m, const int64_t *__re
 }
 
 // as k_prog_tables, with the partner found through the bitmap and index map
+// and one list per step and cluster rank (the part holding the domain end)
 __global__ void __launch_bounds__(256)
 k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
                   const int32_t *__restrict__ ops, int L, const uint32_t *__restrict__ bits,
-                  const int32_t *__restrict__ idx_map, int32_t *__restrict__ tab,
-                  int *__restrict__ flag)
+                  const int32_t *__restrict__ idx_map, int2 *__restrict__ pairs,
+                  int *__restrict__ npairs, int *__restrict__ step_l, int *__restrict__ flag)
 {
     __shared__ uint32_t C[33][33];
     for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
     __syncthreads();
     const int s = blockIdx.y;
-    int l = 0, ci = 0, last = -1, acc = 0;
-    for (; l < L; ++l) {
-        const int nc = o.desc[11 * ops[l]];
-        if (s < acc + nc) {
-            ci = s - acc;
-            last = acc + nc - 1;
-            break;
-        }
-        acc += nc;
-    }
-    if (l >= L) return;
+    int l, ci, last;
+    prog_step_op(o.desc, ops, L, s, l, ci, last);
+    if (l >= L) return;                              // whole block
+    if (blockIdx.x == 0 && threadIdx.x == 0) step_l[s] = l;
     int fw[4], bw[4], len;
     op_strings(o.desc + 11 * ops[l] + 1 + 5 * ci, fw, bw, len);
     const int n = o.n;
     const uint64_t lowm = (1ull << n) - 1;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
-        const int64_t kt = key[t], d = kt >> 8;
-        const int birth = int(kt & 255) - 1;
-        const uint64_t mask = uint64_t(o.astr[d / o.Nb]) | (uint64_t(o.bstr[d % o.Nb]) << n);
-        uint64_t u = mask;
-        int sg = 1;
+    const int chunk = (m + kClusterCtas - 1) / kClusterCtas;
+    // block-uniform trip count: every lane reaches the warp-wide append
+    for (int t0 = blockIdx.x * blockDim.x; t0 < m; t0 += gridDim.x * blockDim.x) {
+        const int t = t0 + int(threadIdx.x);
         int32_t e = 0;
-        bool escape = false;
-        if (apply_string(fw, len, u, sg, o.qubit)) {
-            const int64_t img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
-                                rank_bits(uint32_t(u >> n), C);
-            if (member(bits, img)) {
-                const int p = idx_map[img];
-                e = sg > 0 ? p + 1 : -(p + 1);
-            } else {
-                escape = true;
-            }
-        } else {
-            u = mask;
-            sg = 1;
-            if (apply_string(bw, len, u, sg, o.qubit)) {
-                const int64_t dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
+        if (t < m) {
+            const int64_t kt = key[t], d = kt >> 8;
+            const int birth = int(kt & 255) - 1;
+            const uint64_t mask = uint64_t(o.astr[d / o.Nb]) | (uint64_t(o.bstr[d % o.Nb]) << n);
+            uint64_t u = mask;
+            int sg = 1;
+            bool escape = false;
+            if (apply_string(fw, len, u, sg, o.qubit)) {
+                const int64_t img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
                                     rank_bits(uint32_t(u >> n), C);
-                escape = !member(bits, dom);
+                if (member(bits, img)) {
+                    const int p = idx_map[img];
+                    e = sg > 0 ? p + 1 : -(p + 1);
+                } else {
+                    escape = true;
+                }
+            } else {
+                u = mask;
+                sg = 1;
+                if (apply_string(bw, len, u, sg, o.qubit)) {
+                    const int64_t dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
+                                        rank_bits(uint32_t(u >> n), C);
+                    escape = !member(bits, dom);
+                }
             }
+            if (escape && birth > s && birth <= last) *flag = 1;
         }
-        tab[int64_t(s) * m + t] = e;
-        if (escape && birth > s && birth <= last) *flag = 1;
+        const int r = (t < m ? t : 0) / chunk;
+        warp_append(e != 0, s * kClusterCtas + r, make_int2(t, e), pairs, chunk, npairs);
     }
-}
-
-// Vectors of 12,289..65,536 support elements: a thread-block cluster of
-// kClusterCtas CTAs holds one vector (or, for the gradient, the two vectors
-// of one angle) split over the CTAs' shared memories, chunk elements each;
-// element t lives in CTA t / chunk and is reached through distributed shared
-// memory when it is another CTA's.  A rotation step lets every CTA rotate the
-// pairs whose domain end it holds (an image end has no forward image, so each
-// pair has one writer) and ends with a cluster barrier.
-constexpr int kClusterCtas = 8;
-
-template <typename T>
-struct ClusterVec {
-    T *loc;
-    int chunk, rank;
-    __device__ __forceinline__ T *at(cg::cluster_group &cl, int t) const
-    {
-        const int r = t / chunk;
-        return r == rank ? loc + (t - r * chunk) : cl.map_shared_rank(loc, r) + (t - r * chunk);
-    }
-};
-
-template <typename T>
-__device__ __forceinline__ void cl_rotate(cg::cluster_group &cl, const ClusterVec<T> &x,
-                                          const int32_t *__restrict__ row, int m, T c, T sn)
-{
-    const int t0 = x.rank * x.chunk, t1 = min(m, t0 + x.chunk);
-    for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x) {
-        const int e = row[t];
-        if (e == 0) continue;
-        const int p = (e > 0 ? e : -e) - 1;
-        const T ss = e > 0 ? sn : -sn;
-        T *xt = x.loc + (t - t0);
-        T *xp = x.at(cl, p);
-        const T xv = *xt, yv = *xp;
-        *xt = c * xv - ss * yv;
-        *xp = c * yv + ss * xv;
-    }
-    cl.sync();
-}
-
-// w <- w + (C - C^dagger) f for one constituent (see prog_generator)
-template <typename T>
-__device__ __forceinline__ void cl_generator(cg::cluster_group &cl, const ClusterVec<T> &f,
-                                             const ClusterVec<T> &w,
-                                             const int32_t *__restrict__ row, int m)
-{
-    const int t0 = f.rank * f.chunk, t1 = min(m, t0 + f.chunk);
-    for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x) {
-        const int e = row[t];
-        if (e == 0) continue;
-        const int p = (e > 0 ? e : -e) - 1;
-        const T ft = f.loc[t - t0], fp = *f.at(cl, p);
-        T *wp = w.at(cl, p), *wt = w.loc + (t - t0);
-        if (e > 0) {
-            *wp += ft;
-            *wt -= fp;
-        } else {
-            *wp -= ft;
-            *wt += fp;
-        }
-    }
-    cl.sync();
 }
 
 // FP64 sum over the cluster (each CTA's block sum, then the CTAs' sums in
@@ -1340,27 +1427,22 @@ __device__ __forceinline__ double cl_sum(cg::cluster_group &cl, double acc, doub
 // one cluster: as k_prog_prepare, the vector over the cluster's CTAs
 template <typename T>
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024)
-k_prog_prepare_big(const int64_t *__restrict__ key, const int32_t *__restrict__ tab, int m,
-                   const int32_t *__restrict__ desc, const int32_t *__restrict__ ops,
-                   const double *__restrict__ cs, int L, int renorm, double *__restrict__ norm2,
-                   T *__restrict__ v)
+k_prog_prepare_big(ProgTabs g, const double *__restrict__ cs, int renorm,
+                   double *__restrict__ norm2, T *__restrict__ v)
 {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char clsm[];
+    __shared__ ProgSteps<T> st;
     __shared__ double red[40];
     __shared__ double fac;
     const int rank = int(cl.block_rank());
-    const int chunk = (m + kClusterCtas - 1) / kClusterCtas;
-    const ClusterVec<T> x{reinterpret_cast<T *>(clsm), chunk, rank};
+    const int m = g.m, chunk = g.chunk;
     const int t0 = rank * chunk, t1 = min(m, t0 + chunk);
+    const ClusterVec<T> x{reinterpret_cast<T *>(clsm), chunk, rank, t0, &cl};
     for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x) x.loc[t - t0] = t == 0 ? T(1) : T(0);
+    prog_load_steps(g, rank, cs, st);
     cl.sync();                                       // every CTA of the cluster is running
-    int s = 0;
-    for (int l = 0; l < L; ++l) {
-        const int nc = desc[11 * ops[l]];
-        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
-        for (int ci = 0; ci < nc; ++ci, ++s) cl_rotate(cl, x, tab + int64_t(s) * m, m, c, sn);
-    }
+    prog_run<T>(x, g, rank, st, 0, g.steps);
     T f = T(1);
     if (renorm) {
         double acc = 0.0;
@@ -1377,51 +1459,42 @@ k_prog_prepare_big(const int64_t *__restrict__ key, const int32_t *__restrict__ 
         f = T(fac);
     }
     for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x)
-        v[key[t] >> 8] = renorm ? x.loc[t - t0] * f : x.loc[t - t0];
+        v[g.key[t] >> 8] = renorm ? x.loc[t - t0] * f : x.loc[t - t0];
     cl.sync();                                       // no CTA leaves while others may read it
 }
 
 // cluster lg (of L): as k_prog_grad, f and w over the cluster's CTAs
 template <typename T>
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024)
-k_prog_grad_big(const int64_t *__restrict__ key, const int32_t *__restrict__ tab, int m,
-                const int32_t *__restrict__ desc, const int32_t *__restrict__ ops,
-                const double *__restrict__ cs, int L, const T *__restrict__ sigma,
-                const double *__restrict__ norm2, double *__restrict__ g)
+k_prog_grad_big(ProgTabs g, const double *__restrict__ cs, const T *__restrict__ sigma,
+                const double *__restrict__ norm2, double *__restrict__ gout)
 {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char clsm[];
+    __shared__ ProgSteps<T> st;
     __shared__ double red[40];
     const int rank = int(cl.block_rank());
     const int lg = int(blockIdx.x) / kClusterCtas;
-    const int chunk = (m + kClusterCtas - 1) / kClusterCtas;
-    const ClusterVec<T> f{reinterpret_cast<T *>(clsm), chunk, rank};
-    const ClusterVec<T> w{reinterpret_cast<T *>(clsm) + chunk, chunk, rank};
+    const int m = g.m, chunk = g.chunk;
     const int t0 = rank * chunk, t1 = min(m, t0 + chunk);
+    const ClusterVec<T> f{reinterpret_cast<T *>(clsm), chunk, rank, t0, &cl};
+    const ClusterVec<T> w{reinterpret_cast<T *>(clsm) + chunk, chunk, rank, t0, &cl};
     for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x) {
         f.loc[t - t0] = t == 0 ? T(1) : T(0);
         w.loc[t - t0] = T(0);
     }
+    prog_load_steps(g, rank, cs, st);
     cl.sync();
-    int s = 0;
-    for (int l = 0; l <= lg; ++l) {                  // phi_lg = U_lg .. U_1 |HF>
-        const int nc = desc[11 * ops[l]];
-        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
-        for (int ci = 0; ci < nc; ++ci, ++s) cl_rotate(cl, f, tab + int64_t(s) * m, m, c, sn);
-    }
-    const int ncg = desc[11 * ops[lg]];
-    for (int ci = 0; ci < ncg; ++ci)                 // constituents add in order
-        cl_generator(cl, f, w, tab + int64_t(s - ncg + ci) * m, m);
-    for (int l = lg + 1; l < L; ++l) {
-        const int nc = desc[11 * ops[l]];
-        const T c = T(cs[2 * l]), sn = T(cs[2 * l + 1]);
-        for (int ci = 0; ci < nc; ++ci, ++s) cl_rotate(cl, w, tab + int64_t(s) * m, m, c, sn);
-    }
+    int b, e;
+    prog_op_steps(st.sl, g.steps, lg, b, e);
+    prog_run<T>(f, g, rank, st, 0, e);               // phi_lg = U_lg .. U_1 |HF>
+    prog_generate(f, w, g, rank, st.np, b, e);       // constituents add in order
+    prog_run<T>(w, g, rank, st, e, g.steps);
     double acc = 0.0;
     for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x)
-        acc = fma(double(w.loc[t - t0]), double(sigma[key[t] >> 8]), acc);
+        acc = fma(double(w.loc[t - t0]), double(sigma[g.key[t] >> 8]), acc);
     const double dot = cl_sum(cl, acc, red, rank);
-    if (threadIdx.x == 0 && rank == 0) g[lg] = (norm2 ? 2.0 / sqrt(*norm2) : 2.0) * dot;
+    if (threadIdx.x == 0 && rank == 0) gout[lg] = (norm2 ? 2.0 / sqrt(*norm2) : 2.0) * dot;
     cl.sync();
 }
 
@@ -1862,73 +1935,70 @@ cudaError_t grad_sparse(const SparseGradArgs<T> &a, int num_sms, cudaStream_t st
 
 cudaError_t prog_compile(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
                          const SvOpArgs &o, const int32_t *ops, int L, int64_t *key,
-                         int32_t *tab, int *flag, cudaStream_t st)
+                         int2 *pairs, int *npairs, int *step_l, int *flag, cudaStream_t st)
 {
-    if (m < 1 || m > kProgMax || steps < 1 || steps > 254) return cudaErrorInvalidValue;
+    if (m < 1 || m > kProgMax || steps < 1 || steps > kProgSteps) return cudaErrorInvalidValue;
     // up to 128 KB of dynamic shared memory (set per call: the attribute
     // belongs to the current device)
     cudaError_t e = cudaFuncSetAttribute(k_prog_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(kProgSortMax * 8));
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(npairs, 0, size_t(steps) * sizeof(int), st);
     if (e != cudaSuccess) return e;
     int64_t P = 1;
     while (P < m) P <<= 1;
     k_prog_sort<<<1, 1024, size_t(P) * 8, st>>>(list, m, step_len, steps, key);
     hy::count_launch();
     k_prog_tables<<<dim3(unsigned((m + 255) / 256), unsigned(steps)), 256, 0, st>>>(
-        key, int(m), o, ops, L, tab, flag);
+        key, int(m), o, ops, L, pairs, npairs, step_l, flag);
     hy::count_launch();
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t prog_prepare(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
-                         const int32_t *ops, const double *cs, int L, bool renorm, double *norm2,
-                         T *v, cudaStream_t st)
+cudaError_t prog_prepare(const ProgTabs &g, const double *cs, bool renorm, double *norm2, T *v,
+                         cudaStream_t st)
 {
-    if (m < 1 || m > kProgMax) return cudaErrorInvalidValue;
+    if (g.m < 1 || g.m > kProgMax || g.steps < 1 || g.steps > kProgSteps || g.ranks != 1 ||
+        g.chunk != g.m)
+        return cudaErrorInvalidValue;
     // up to 96 KB of dynamic shared memory
     const cudaError_t e = cudaFuncSetAttribute(k_prog_prepare<T>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                int(kProgMax * sizeof(T)));
     if (e != cudaSuccess) return e;
-    k_prog_prepare<T><<<1, kProgThreads, size_t(m) * sizeof(T), st>>>(key, tab, int(m), desc, ops,
-                                                                      cs, L, renorm ? 1 : 0,
-                                                                      norm2, v);
+    k_prog_prepare<T><<<1, kProgThreads, size_t(g.m) * sizeof(T), st>>>(g, cs, renorm ? 1 : 0,
+                                                                        norm2, v);
     hy::count_launch();
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t prog_grad(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
-                      const int32_t *ops, const double *cs, int L, const T *sigma,
-                      const double *norm2, double *g, cudaStream_t st)
+cudaError_t prog_grad(const ProgTabs &g, const double *cs, int L, const T *sigma,
+                      const double *norm2, double *gout, cudaStream_t st)
 {
-    if (m < 1 || m > kProgMax || L < 1) return cudaErrorInvalidValue;
-    const size_t smem = 2 * size_t(m) * sizeof(T);
+    if (g.m < 1 || g.m > kProgMax || g.steps < 1 || g.steps > kProgSteps || g.ranks != 1 ||
+        g.chunk != g.m || L < 1)
+        return cudaErrorInvalidValue;
+    const size_t smem = 2 * size_t(g.m) * sizeof(T);
     // up to 192 KB of dynamic shared memory
     const cudaError_t e = cudaFuncSetAttribute(k_prog_grad<T>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                int(2 * kProgMax * sizeof(T)));
     if (e != cudaSuccess) return e;
-    k_prog_grad<T><<<unsigned(L), kProgThreads, smem, st>>>(key, tab, int(m), desc, ops, cs, L,
-                                                            sigma, norm2, g);
+    k_prog_grad<T><<<unsigned(L), kProgThreads, smem, st>>>(g, cs, sigma, norm2, gout);
     hy::count_launch();
     return cudaGetLastError();
 }
 
-template cudaError_t prog_prepare<double>(const int64_t *, const int32_t *, int64_t,
-                                          const int32_t *, const int32_t *, const double *, int,
-                                          bool, double *, double *, cudaStream_t);
-template cudaError_t prog_prepare<float>(const int64_t *, const int32_t *, int64_t,
-                                         const int32_t *, const int32_t *, const double *, int,
-                                         bool, double *, float *, cudaStream_t);
-template cudaError_t prog_grad<double>(const int64_t *, const int32_t *, int64_t, const int32_t *,
-                                       const int32_t *, const double *, int, const double *,
+template cudaError_t prog_prepare<double>(const ProgTabs &, const double *, bool, double *,
+                                          double *, cudaStream_t);
+template cudaError_t prog_prepare<float>(const ProgTabs &, const double *, bool, double *, float *,
+                                         cudaStream_t);
+template cudaError_t prog_grad<double>(const ProgTabs &, const double *, int, const double *,
                                        const double *, double *, cudaStream_t);
-template cudaError_t prog_grad<float>(const int64_t *, const int32_t *, int64_t, const int32_t *,
-                                      const int32_t *, const double *, int, const float *,
+template cudaError_t prog_grad<float>(const ProgTabs &, const double *, int, const float *,
                                       const double *, double *, cudaStream_t);
 
 template cudaError_t support<double>(const double *, int64_t, int64_t *, int64_t,
@@ -1941,67 +2011,68 @@ template cudaError_t hpsi_support<double>(const SupRowsArgs<double> &, int, cuda
 template cudaError_t hpsi_support<float>(const SupRowsArgs<float> &, int, cudaStream_t);
 cudaError_t prog_compile_big(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
                              const SvOpArgs &o, const int32_t *ops, int L, const uint32_t *bits,
-                             int64_t *key, int32_t *tab, int32_t *idx_map, int *flag,
-                             cudaStream_t st)
+                             int64_t *key, int2 *pairs, int *npairs, int *step_l,
+                             int32_t *idx_map, int *flag, cudaStream_t st)
 {
-    if (m <= kProgMax || m > kProgBig || steps < 1 || steps > 254) return cudaErrorInvalidValue;
+    if (m <= kProgMax || m > kProgBig || steps < 1 || steps > kProgSteps)
+        return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(npairs, 0, size_t(steps) * kClusterCtas * sizeof(int), st);
     if (e != cudaSuccess) return e;
     k_prog_keys_big<<<unsigned((m + 255) / 256), 256, 0, st>>>(list, m, step_len, steps, key,
                                                                 idx_map);
     hy::count_launch();
     k_prog_tables_big<<<dim3(unsigned((m + 255) / 256), unsigned(steps)), 256, 0, st>>>(
-        key, int(m), o, ops, L, bits, idx_map, tab, flag);
+        key, int(m), o, ops, L, bits, idx_map, pairs, npairs, step_l, flag);
     hy::count_launch();
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t prog_prepare_big(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
-                             const int32_t *ops, const double *cs, int L, bool renorm,
-                             double *norm2, T *v, cudaStream_t st)
+namespace {
+bool big_tabs_ok(const ProgTabs &g)
 {
-    if (m <= kProgMax || m > kProgBig) return cudaErrorInvalidValue;
-    const int chunk = int((m + kClusterCtas - 1) / kClusterCtas);
-    const size_t smem = size_t(chunk) * sizeof(T);
+    return g.m > kProgMax && g.m <= kProgBig && g.steps >= 1 && g.steps <= kProgSteps &&
+           g.ranks == kClusterCtas && g.chunk == int((g.m + kClusterCtas - 1) / kClusterCtas);
+}
+}  // namespace
+
+template <typename T>
+cudaError_t prog_prepare_big(const ProgTabs &g, const double *cs, bool renorm, double *norm2,
+                             T *v, cudaStream_t st)
+{
+    if (!big_tabs_ok(g)) return cudaErrorInvalidValue;
+    const size_t smem = size_t(g.chunk) * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(k_prog_prepare_big<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    k_prog_prepare_big<T><<<kClusterCtas, 1024, smem, st>>>(key, tab, int(m), desc, ops, cs, L,
-                                                           renorm ? 1 : 0, norm2, v);
+    k_prog_prepare_big<T><<<kClusterCtas, 1024, smem, st>>>(g, cs, renorm ? 1 : 0, norm2, v);
     hy::count_launch();
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t prog_grad_big(const int64_t *key, const int32_t *tab, int64_t m, const int32_t *desc,
-                          const int32_t *ops, const double *cs, int L, const T *sigma,
-                          const double *norm2, double *g, cudaStream_t st)
+cudaError_t prog_grad_big(const ProgTabs &g, const double *cs, int L, const T *sigma,
+                          const double *norm2, double *gout, cudaStream_t st)
 {
-    if (m <= kProgMax || m > kProgBig || L < 1) return cudaErrorInvalidValue;
-    const int chunk = int((m + kClusterCtas - 1) / kClusterCtas);
-    const size_t smem = 2 * size_t(chunk) * sizeof(T);
+    if (!big_tabs_ok(g) || L < 1) return cudaErrorInvalidValue;
+    const size_t smem = 2 * size_t(g.chunk) * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(k_prog_grad_big<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    k_prog_grad_big<T><<<unsigned(kClusterCtas * L), 1024, smem, st>>>(key, tab, int(m), desc, ops,
-                                                                       cs, L, sigma, norm2, g);
+    k_prog_grad_big<T><<<unsigned(kClusterCtas * L), 1024, smem, st>>>(g, cs, sigma, norm2, gout);
     hy::count_launch();
     return cudaGetLastError();
 }
 
-template cudaError_t prog_prepare_big<double>(const int64_t *, const int32_t *, int64_t,
-                                              const int32_t *, const int32_t *, const double *,
-                                              int, bool, double *, double *, cudaStream_t);
-template cudaError_t prog_prepare_big<float>(const int64_t *, const int32_t *, int64_t,
-                                             const int32_t *, const int32_t *, const double *, int,
-                                             bool, double *, float *, cudaStream_t);
-template cudaError_t prog_grad_big<double>(const int64_t *, const int32_t *, int64_t,
-                                           const int32_t *, const int32_t *, const double *, int,
-                                           const double *, const double *, double *, cudaStream_t);
-template cudaError_t prog_grad_big<float>(const int64_t *, const int32_t *, int64_t,
-                                          const int32_t *, const int32_t *, const double *, int,
-                                          const float *, const double *, double *, cudaStream_t);
+template cudaError_t prog_prepare_big<double>(const ProgTabs &, const double *, bool, double *,
+                                              double *, cudaStream_t);
+template cudaError_t prog_prepare_big<float>(const ProgTabs &, const double *, bool, double *,
+                                             float *, cudaStream_t);
+template cudaError_t prog_grad_big<double>(const ProgTabs &, const double *, int, const double *,
+                                           const double *, double *, cudaStream_t);
+template cudaError_t prog_grad_big<float>(const ProgTabs &, const double *, int, const float *,
+                                          const double *, double *, cudaStream_t);
 template cudaError_t grad_sparse<double>(const SparseGradArgs<double> &, int, cudaStream_t);
 template cudaError_t grad_sparse<float>(const SparseGradArgs<float> &, int, cudaStream_t);
 #define HY_SV_INST(T)                                                                       \
