@@ -2349,19 +2349,20 @@ struct SupportProgram {
     int64_t *key = nullptr, *step_len = nullptr;
     // the pair lists of the steps (hy_kernels.cuh, ProgTabs), their counts
     // and the operator of each step
-    int2 *pairs = nullptr;
+    uint32_t *pairs = nullptr;
     int *npairs = nullptr, *step_l = nullptr;
     int *flag = nullptr;
     // supports beyond one CTA's shared memory (allocated on first use): keys
     // in listing order, pair lists per cluster rank and the index map over
     // Omega_CIk (the vectors live in the shared memory of a cluster of CTAs)
     int64_t *key_big = nullptr;
-    int2 *pairs_big = nullptr;
+    uint32_t *pairs_big = nullptr;
     int32_t *idx_map = nullptr;
     // H restricted to the program's support (rows in key order, columns as
     // determinant indices): valid while hss_ok
     // (row t's entries at [t * hss_w, t * hss_w + hss_cnt[t]))
     int32_t *hss_cnt = nullptr;
+    uint32_t *hss_strs = nullptr;   // the support's alpha and beta string sets
     uint32_t *hss_col = nullptr;
     double *hss_val = nullptr;
     int64_t hss_cap = 0, hss_w = 0;
@@ -2382,7 +2383,7 @@ hy_status prog_create(const hy_ham *h, int max_steps, SupportProgram **out)
     cudaError_t e = cudaMalloc(&g->key, size_t(hy::k::kProgMax) * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc(&g->step_len, size_t(max_steps) * sizeof(int64_t));
     if (e == cudaSuccess)
-        e = cudaMalloc(&g->pairs, size_t(max_steps) * hy::k::kProgMax * sizeof(int2));
+        e = cudaMalloc(&g->pairs, size_t(max_steps) * hy::k::kProgMax * sizeof(uint32_t));
     if (e == cudaSuccess)
         e = cudaMalloc(&g->npairs, size_t(max_steps) * hy::k::kClusterCtas * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&g->step_l, size_t(max_steps) * sizeof(int));
@@ -2410,6 +2411,7 @@ void prog_destroy(SupportProgram *g)
     cudaFree(g->idx_map);
     cudaFree(g->d_nnz);
     cudaFree(g->hss_cnt);
+    cudaFree(g->hss_strs);
     cudaFree(g->hss_col);
     cudaFree(g->hss_val);
     if (g->h_nnz) cudaFreeHost(g->h_nnz);
@@ -2462,7 +2464,7 @@ hy_status prog_compile(SupportProgram *g, const SparseState *s, int64_t m, const
         // kClusterCtas lists of ceil(m / kClusterCtas) <= kb / kClusterCtas
         // pairs per step
         if (e == cudaSuccess && !g->pairs_big)
-            e = cudaMalloc(&g->pairs_big, size_t(g->max_steps) * kb * sizeof(int2));
+            e = cudaMalloc(&g->pairs_big, size_t(g->max_steps) * kb * sizeof(uint32_t));
         if (e == cudaSuccess && !g->idx_map)
             e = cudaMalloc(&g->idx_map, size_t(g->h->N) * sizeof(int32_t));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(support program)");
@@ -2501,7 +2503,9 @@ hy_status prog_build_hss(SupportProgram *g, const SparseState *s, int64_t max_nn
     if (need > max_nnz) return HY_OK;              // too large to pay off: not built
     cudaError_t e = cudaSuccess;
     const size_t kb = size_t(hy::k::kProgBig);
+    const size_t wa = size_t((h->Na + 31) >> 5), wb = size_t((h->Nb + 31) >> 5);
     if (!g->hss_cnt) e = cudaMalloc(&g->hss_cnt, kb * sizeof(int32_t));
+    if (e == cudaSuccess && !g->hss_strs) e = cudaMalloc(&g->hss_strs, (wa + wb) * sizeof(uint32_t));
     if (e == cudaSuccess && !g->d_nnz) e = cudaMalloc(&g->d_nnz, sizeof(int64_t));
     if (e == cudaSuccess && !g->h_nnz) {
         e = cudaMallocHost(&g->h_nnz, sizeof(int64_t));
@@ -2535,7 +2539,8 @@ hy_status prog_build_hss(SupportProgram *g, const SparseState *s, int64_t max_nn
     a.Mb_ptr = h->Mb64.ptr; a.Mb_col = h->Mb64.col; a.Mb_val = h->Mb64.val;
     a.V = h->d_V64;
     a.aex = h->d_aex; a.bexT = h->d_bexT; a.astr = h->d_astr; a.bstr = h->d_bstr;
-    a.n = h->n; a.nexa = h->A.nex; a.nexb = h->B.nex; a.Nb = h->Nb;
+    a.n = h->n; a.nexa = h->A.nex; a.nexb = h->B.nex; a.Na = h->Na; a.Nb = h->Nb;
+    a.sa = g->hss_strs; a.sb = g->hss_strs + wa;
     a.stride = g->hss_w; a.cnt = g->hss_cnt; a.col = g->hss_col; a.val = g->hss_val;
     hy::ProfScope prof(HY_PROF_SPARSE_EXCITE, stream, 0.0);
     HY_CUDA(hy::k::hss_fill(a, g->d_nnz, h->num_sms, st), "support Hamiltonian fill");

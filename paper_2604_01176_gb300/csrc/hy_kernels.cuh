@@ -362,8 +362,9 @@ cudaError_t sv_prepare(const SVec<T> &x, const SvOpArgs &o, const int32_t *ops, 
 //   key[t]  = (determinant << 8) | (step that listed it + 1) for the m
 //             support elements (t = local index; ascending for m <=
 //             kProgMax, listing order beyond);
-//   the pairs of step s: {t, +-(p + 1)} for every t that step s's forward
-//             string takes to a support element p with sign +-1.  They are
+//   the pairs of step s: (t, p, sign) for every t that step s's forward
+//             string takes to a support element p with sign +-1, packed in
+//             one word (t's index within its part, p, the sign).  They are
 //             kept as compact lists, one per step and part of the support:
 //             with `ranks` parts of `chunk` = ceil(m / ranks) elements (one
 //             part for one CTA, kClusterCtas for a cluster), the pairs of
@@ -380,7 +381,7 @@ constexpr int kProgMax = 12288;   // shared-memory vectors: 2 x 12288 doubles pe
 constexpr int kProgSteps = 254;   // steps of one program (8-bit birth tags)
 struct ProgTabs {
     const int64_t *key;
-    const int2 *pairs;
+    const uint32_t *pairs;
     const int *npairs;
     const int *step_l;
     int m, steps, ranks, chunk;
@@ -390,7 +391,7 @@ struct ProgTabs {
 // steps * m entries, npairs `steps` counts, step_l `steps` entries
 cudaError_t prog_compile(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
                          const SvOpArgs &o, const int32_t *ops, int L, int64_t *key,
-                         int2 *pairs, int *npairs, int *step_l, int *flag, cudaStream_t st);
+                         uint32_t *pairs, int *npairs, int *step_l, int *flag, cudaStream_t st);
 // one CTA: the m-vector U_L .. U_1|HF> by the pair lists in shared memory,
 // with cs[2l], cs[2l+1] = cos, sin theta_l, then (renorm) divided by its FP64
 // norm (*norm2, if not null), written to v[key[t] >> 8]; v outside the
@@ -416,7 +417,7 @@ constexpr int64_t kProgBig = 65536;
 constexpr int kClusterCtas = 8;
 cudaError_t prog_compile_big(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
                              const SvOpArgs &o, const int32_t *ops, int L, const uint32_t *bits,
-                             int64_t *key, int2 *pairs, int *npairs, int *step_l,
+                             int64_t *key, uint32_t *pairs, int *npairs, int *step_l,
                              int32_t *idx_map, int *flag, cudaStream_t st);
 template <typename T>
 cudaError_t prog_prepare_big(const ProgTabs &g, const double *cs, bool renorm, double *norm2,
@@ -429,10 +430,10 @@ cudaError_t prog_grad_big(const ProgTabs &g, const double *cs, int L, const T *s
 // the couplings to determinants of S (membership bitmap `bits`), columns
 // stored as determinant indices.  The energy of a state on S and the
 // forward gradients read sigma only on S, so within one ansatz H_SS psi
-// serves every evaluation.  hss_count: row lengths into cnt[0..m) and their
-// exclusive prefix into ptr[0..m]; hss_fill: the entries (same enumeration,
-// fixed order); hss_apply: sigma[key[t] >> 8] = sum_e val[e] psi[col[e]]
-// for t < m, accumulated in T (sigma untouched elsewhere).
+// serves every evaluation.  hss_fill: the entries of every row (the
+// candidates filtered by the support's alpha and beta string sets first,
+// then by its bitmap; fixed order); hss_apply: sigma[key[t] >> 8] = sum_e
+// val[e] psi[col[e]] for t < m, accumulated in T (sigma untouched elsewhere).
 struct HssArgs {
     const int64_t *key;
     int64_t m;
@@ -441,7 +442,8 @@ struct HssArgs {
     const double *Ma_val, *Mb_val, *V;
     const uint32_t *aex, *bexT, *astr, *bstr;
     int n, nexa, nexb;
-    int64_t Nb;
+    int64_t Na, Nb;
+    uint32_t *sa, *sb;       // scratch: bitmaps over the alpha / beta strings
     int64_t stride;          // entries reserved per row (>= any row's couplings)
     int32_t *cnt;            // [m] entries of each row
     uint32_t *col;           // [m * stride]

@@ -995,11 +995,21 @@ __device__ __forceinline__ int prog_find(const int64_t *__restrict__ key, int m,
     return lo < m && (key[lo] >> 8) == d ? lo : -1;
 }
 
+// a pair of a step packed into one word: the domain end's index within its
+// part (tl < 2^14), the image end p (< 2^16) and the sign of the forward
+// string; kNoPair marks an empty register slot
+__device__ __forceinline__ uint32_t pair_word(int tl, int p, bool neg)
+{
+    return uint32_t(tl) | (uint32_t(p) << 14) | (neg ? 1u << 30 : 0u);
+}
+constexpr uint32_t kNoPair = 0xFFFFFFFFu;
+
 // warp-aggregated append: every lane with `has` adds v to list `slot`
 // (count counts[slot], items from out + slot * stride); the lanes of one warp
 // that share a slot take one atomic.  Every lane of the warp must call it.
-__device__ __forceinline__ void warp_append(bool has, int slot, int2 v, int2 *__restrict__ out,
-                                            int64_t stride, int *__restrict__ counts)
+__device__ __forceinline__ void warp_append(bool has, int slot, uint32_t v,
+                                            uint32_t *__restrict__ out, int64_t stride,
+                                            int *__restrict__ counts)
 {
     const unsigned act = __ballot_sync(0xffffffffu, has);
     if (!has) return;
@@ -1035,8 +1045,8 @@ __device__ __forceinline__ void prog_step_op(const int32_t *__restrict__ desc,
 // the pairs of step s = blockIdx.y (constituent ci of op l), one list per step
 __global__ void __launch_bounds__(256)
 k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t *__restrict__ ops,
-              int L, int2 *__restrict__ pairs, int *__restrict__ npairs, int *__restrict__ step_l,
-              int *__restrict__ flag)
+              int L, uint32_t *__restrict__ pairs, int *__restrict__ npairs,
+              int *__restrict__ step_l, int *__restrict__ flag)
 {
     __shared__ uint32_t C[33][33];
     for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
@@ -1047,7 +1057,8 @@ k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t 
     if (l >= L) return;                              // whole block
     if (blockIdx.x == 0 && threadIdx.x == 0) step_l[s] = l;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int32_t e = 0;
+    int p = -1;
+    bool neg = false;
     if (t < m) {
         int fw[4], bw[4], len;
         op_strings(o.desc + 11 * ops[l] + 1 + 5 * ci, fw, bw, len);
@@ -1062,9 +1073,9 @@ k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t 
         if (apply_string(fw, len, u, sg, o.qubit)) {
             const int64_t img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
                                 rank_bits(uint32_t(u >> n), C);
-            const int p = prog_find(key, m, img);
-            if (p >= 0) e = sg > 0 ? p + 1 : -(p + 1);
-            else escape = true;
+            p = prog_find(key, m, img);
+            neg = sg < 0;
+            escape = p < 0;
         } else {
             u = mask;
             sg = 1;
@@ -1080,20 +1091,20 @@ k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t 
         // later by op l's own constituents
         if (escape && birth > s && birth <= last) *flag = 1;
     }
-    warp_append(e != 0, s, make_int2(t, e), pairs, m, npairs);
+    warp_append(p >= 0, s, pair_word(t, p, neg), pairs, m, npairs);
 }
 
-// pairs a thread takes per round of a step (loaded together, so that their
-// latencies overlap)
+// pairs a thread takes per round of a step read from global memory (loaded
+// together, so that their latencies overlap)
 constexpr int kPairU = 4;
 
-__device__ __forceinline__ void pairs_load(int2 (&q)[kPairU], const int2 *__restrict__ pr, int n,
-                                           int i0)
+__device__ __forceinline__ void pairs_load(uint32_t (&q)[kPairU], const uint32_t *__restrict__ pr,
+                                           int n, int i0)
 {
 #pragma unroll
     for (int k = 0; k < kPairU; ++k) {
         const int i = i0 + k * int(blockDim.x);
-        q[k] = i < n ? pr[i] : make_int2(0, 0);
+        q[k] = i < n ? pr[i] : kNoPair;
     }
 }
 
@@ -1101,7 +1112,7 @@ __device__ __forceinline__ void pairs_load(int2 (&q)[kPairU], const int2 *__rest
 template <typename T>
 struct LocalVec {
     T *x;
-    __device__ __forceinline__ T *dom(int t) const { return x + t; }
+    __device__ __forceinline__ T *own(int tl) const { return x + tl; }
     __device__ __forceinline__ T *img(int p) const { return x + p; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
@@ -1109,71 +1120,62 @@ struct LocalVec {
 // a vector split over the shared memories of a cluster's CTAs, chunk
 // elements each: element t lives in CTA t / chunk and is reached through
 // distributed shared memory when it is another CTA's.  A CTA's pair lists
-// hold the pairs whose domain end is its own
+// hold the pairs whose domain end is its own (own: by its local index)
 template <typename T>
 struct ClusterVec {
     T *loc;
-    int chunk, rank, t0;
-    cg::cluster_group *cl;
-    __device__ __forceinline__ T *dom(int t) const { return loc + (t - t0); }
+    int chunk, rank;
+    __device__ __forceinline__ T *own(int tl) const { return loc + tl; }
     __device__ __forceinline__ T *img(int p) const
     {
         const int r = p / chunk;
-        return r == rank ? loc + (p - t0) : cl->map_shared_rank(loc, r) + (p - r * chunk);
+        return r == rank ? loc + (p - r * chunk)
+                         : cg::this_cluster().map_shared_rank(loc, r) + (p - r * chunk);
     }
-    __device__ __forceinline__ void sync() const { cl->sync(); }
+    __device__ __forceinline__ void sync() const { cg::this_cluster().sync(); }
 };
 
-// one round of a constituent rotation (pairs are disjoint: each has one
-// writer)
+// one pair of a constituent rotation (the pairs of a step are disjoint: each
+// has one writer)
 template <typename T, class V>
-__device__ __forceinline__ void pairs_rotate(const V &x, const int2 (&q)[kPairU], T c, T sn)
+__device__ __forceinline__ void pair_rotate(const V &x, uint32_t w, T c, T sn)
 {
-#pragma unroll
-    for (int k = 0; k < kPairU; ++k) {
-        const int e = q[k].y;
-        if (e == 0) continue;
-        const int p = (e > 0 ? e : -e) - 1;
-        const T ss = e > 0 ? sn : -sn;
-        T *xt = x.dom(q[k].x), *xp = x.img(p);
-        const T xv = *xt, yv = *xp;
-        *xt = c * xv - ss * yv;
-        *xp = c * yv + ss * xv;
-    }
+    const T ss = (w >> 30) & 1u ? -sn : sn;
+    T *xt = x.own(int(w & 0x3FFFu)), *xp = x.img(int((w >> 14) & 0xFFFFu));
+    const T xv = *xt, yv = *xp;
+    *xt = c * xv - ss * yv;
+    *xp = c * yv + ss * xv;
 }
 
-// one round of w <- w + (C - C^dagger) f for one constituent: C|t> = sg|p>
+// one pair of w <- w + (C - C^dagger) f for one constituent: C|t> = sg|p>
 // adds sg f_t to w_p and -sg f_p to w_t
 template <class V>
-__device__ __forceinline__ void pairs_generator(const V &f, const V &w, const int2 (&q)[kPairU])
+__device__ __forceinline__ void pair_generator(const V &f, const V &w, uint32_t wd)
 {
-#pragma unroll
-    for (int k = 0; k < kPairU; ++k) {
-        const int e = q[k].y;
-        if (e == 0) continue;
-        const int t = q[k].x, p = (e > 0 ? e : -e) - 1;
-        const auto ft = *f.dom(t), fp = *f.img(p);
-        auto *wp = w.img(p), *wt = w.dom(t);
-        if (e > 0) {
-            *wp += ft;
-            *wt -= fp;
-        } else {
-            *wp -= ft;
-            *wt += fp;
-        }
+    const int tl = int(wd & 0x3FFFu), p = int((wd >> 14) & 0xFFFFu);
+    const auto ft = *f.own(tl), fp = *f.img(p);
+    auto *wp = w.img(p), *wt = w.own(tl);
+    if ((wd >> 30) & 1u) {
+        *wp -= ft;
+        *wt += fp;
+    } else {
+        *wp += ft;
+        *wt -= fp;
     }
 }
 
 // per-step values of a program in shared memory: this part's pair counts,
-// the operator of each step and its cos / sin
+// the operator of each step and its cos / sin, and where the step's pairs
+// were staged in shared memory (-1: read from global memory)
 template <typename T>
 struct ProgSteps {
     int np[kProgSteps];
     int sl[kProgSteps];
+    int off[kProgSteps];
     T c[kProgSteps], sn[kProgSteps];
 };
 
-// fills st (the caller synchronises); every thread of the CTA calls it
+// fills st.np, sl, c, sn (the caller synchronises); every thread calls it
 template <typename T>
 __device__ __forceinline__ void prog_load_steps(const ProgTabs &g, int rank,
                                                 const double *__restrict__ cs, ProgSteps<T> &st)
@@ -1187,52 +1189,82 @@ __device__ __forceinline__ void prog_load_steps(const ProgTabs &g, int rank,
     }
 }
 
-// steps [s0, s1) on x, one barrier (CTA or cluster) after each; the first
-// round of the next step's pairs is loaded while the current step runs
+__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                 ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))), "l"(src)
+                 : "memory");
+}
+
+// copies the pair lists of this part into sp (cap words of shared memory),
+// steps in order while they fit, and sets st.off (after st.np is loaded and
+// synchronised); ends synchronised
+template <typename T>
+__device__ __forceinline__ void prog_stage(const ProgTabs &g, int rank, ProgSteps<T> &st,
+                                           uint32_t *sp, int cap)
+{
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int s = 0; s < g.steps; ++s) {
+            const int n = st.np[s];
+            if (n <= cap - acc) {
+                st.off[s] = acc;
+                acc += n;
+            } else {
+                st.off[s] = -1;
+            }
+        }
+    }
+    __syncthreads();
+    for (int s = 0; s < g.steps; ++s) {
+        const int o = st.off[s];
+        if (o < 0) continue;
+        const uint32_t *src = g.pairs + (int64_t(s) * g.ranks + rank) * g.chunk;
+        for (int i = threadIdx.x; i < st.np[s]; i += blockDim.x) cp_async4(sp + o + i, src + i);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+}
+
+// steps [s0, s1) on x, one barrier (CTA or cluster) after each
 template <typename T, class V>
 __device__ __forceinline__ void prog_run(const V &x, const ProgTabs &g, int rank,
-                                         const ProgSteps<T> &st, int s0, int s1)
+                                         const ProgSteps<T> &st, const uint32_t *sp, int s0,
+                                         int s1)
 {
-    if (s0 >= s1) return;
     const int R = kPairU * int(blockDim.x);
-    const int64_t stride = g.chunk;
-    int2 q[kPairU];
-    pairs_load(q, g.pairs + (int64_t(s0) * g.ranks + rank) * stride, st.np[s0], int(threadIdx.x));
     for (int s = s0; s < s1; ++s) {
-        const int n = st.np[s];
-        const int2 *pr = g.pairs + (int64_t(s) * g.ranks + rank) * stride;
-        int2 nq[kPairU];
-        if (s + 1 < s1)
-            pairs_load(nq, g.pairs + (int64_t(s + 1) * g.ranks + rank) * stride, st.np[s + 1],
-                       int(threadIdx.x));
-        pairs_rotate<T>(x, q, st.c[s], st.sn[s]);
-        for (int i0 = int(threadIdx.x) + R; i0 < n; i0 += R) {
-            int2 r[kPairU];
-            pairs_load(r, pr, n, i0);
-            pairs_rotate<T>(x, r, st.c[s], st.sn[s]);
+        const int n = st.np[s], o = st.off[s];
+        const T c = st.c[s], sn = st.sn[s];
+        if (o >= 0) {
+            const uint32_t *pr = sp + o;
+#pragma unroll 4
+            for (int i = threadIdx.x; i < n; i += blockDim.x) pair_rotate<T>(x, pr[i], c, sn);
+        } else {
+            const uint32_t *pr = g.pairs + (int64_t(s) * g.ranks + rank) * g.chunk;
+            for (int i0 = threadIdx.x; i0 < n; i0 += R) {
+                uint32_t q[kPairU];
+                pairs_load(q, pr, n, i0);
+#pragma unroll
+                for (int k = 0; k < kPairU; ++k)
+                    if (q[k] != kNoPair) pair_rotate<T>(x, q[k], c, sn);
+            }
         }
         x.sync();
-        if (s + 1 < s1) {
-#pragma unroll
-            for (int k = 0; k < kPairU; ++k) q[k] = nq[k];
-        }
     }
 }
 
 // the generator of op lg (its constituent steps [b, e), in order) from f
 // into w, one barrier after each constituent
-template <class V>
+template <typename T, class V>
 __device__ __forceinline__ void prog_generate(const V &f, const V &w, const ProgTabs &g, int rank,
-                                              const int *np, int b, int e)
+                                              const ProgSteps<T> &st, const uint32_t *sp, int b,
+                                              int e)
 {
-    const int R = kPairU * int(blockDim.x);
     for (int s = b; s < e; ++s) {
-        const int2 *pr = g.pairs + (int64_t(s) * g.ranks + rank) * g.chunk;
-        for (int i0 = int(threadIdx.x); i0 < np[s]; i0 += R) {
-            int2 q[kPairU];
-            pairs_load(q, pr, np[s], i0);
-            pairs_generator(f, w, q);
-        }
+        const int n = st.np[s], o = st.off[s];
+        const uint32_t *pr = o >= 0 ? sp + o : g.pairs + (int64_t(s) * g.ranks + rank) * g.chunk;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) pair_generator(f, w, pr[i]);
         f.sync();
     }
 }
@@ -1261,21 +1293,25 @@ __device__ __forceinline__ double prog_block_sum(double acc, double *red)
     return s;
 }
 
+// The program kernels take all of a block's opt-in shared memory: the
+// vectors first, then (cap words) the staged pair lists
 template <typename T>
 __global__ void __launch_bounds__(kProgThreads)
 k_prog_prepare(ProgTabs g, const double *__restrict__ cs, int renorm, double *__restrict__ norm2,
-               T *__restrict__ v)
+               T *__restrict__ v, int cap)
 {
     extern __shared__ __align__(16) unsigned char prog_sm[];
+    const int m = g.m;
     const LocalVec<T> x{reinterpret_cast<T *>(prog_sm)};
+    uint32_t *sp = reinterpret_cast<uint32_t *>(x.x + m);
     __shared__ ProgSteps<T> st;
     __shared__ double red[kProgThreads / 32];
     __shared__ double fac;
-    const int m = g.m;
     for (int t = threadIdx.x; t < m; t += blockDim.x) x.x[t] = t == 0 ? T(1) : T(0);   // |HF>
     prog_load_steps(g, 0, cs, st);
     __syncthreads();
-    prog_run<T>(x, g, 0, st, 0, g.steps);
+    prog_stage(g, 0, st, sp, cap);
+    prog_run<T>(x, g, 0, st, sp, 0, g.steps);
     if (renorm) {
         double acc = 0.0;
         for (int t = threadIdx.x; t < m; t += blockDim.x)
@@ -1297,11 +1333,12 @@ k_prog_prepare(ProgTabs g, const double *__restrict__ cs, int renorm, double *__
 template <typename T>
 __global__ void __launch_bounds__(kProgThreads)
 k_prog_grad(ProgTabs g, const double *__restrict__ cs, const T *__restrict__ sigma,
-            const double *__restrict__ norm2, double *__restrict__ gout)
+            const double *__restrict__ norm2, double *__restrict__ gout, int cap)
 {
     extern __shared__ __align__(16) unsigned char prog_sm[];
     const int m = g.m;
     const LocalVec<T> f{reinterpret_cast<T *>(prog_sm)}, w{reinterpret_cast<T *>(prog_sm) + m};
+    uint32_t *sp = reinterpret_cast<uint32_t *>(w.x + m);
     __shared__ ProgSteps<T> st;
     __shared__ double red[kProgThreads / 32];
     const int lg = blockIdx.x;
@@ -1311,11 +1348,12 @@ k_prog_grad(ProgTabs g, const double *__restrict__ cs, const T *__restrict__ sig
     }
     prog_load_steps(g, 0, cs, st);
     __syncthreads();
+    prog_stage(g, 0, st, sp, cap);
     int b, e;
     prog_op_steps(st.sl, g.steps, lg, b, e);
-    prog_run<T>(f, g, 0, st, 0, e);                  // phi_lg = U_lg .. U_1 |HF>
-    prog_generate(f, w, g, 0, st.np, b, e);          // constituents add in order
-    prog_run<T>(w, g, 0, st, e, g.steps);
+    prog_run<T>(f, g, 0, st, sp, 0, e);              // phi_lg = U_lg .. U_1 |HF>
+    prog_generate<T>(f, w, g, 0, st, sp, b, e);      // constituents add in order
+    prog_run<T>(w, g, 0, st, sp, e, g.steps);
     double acc = 0.0;
     for (int t = threadIdx.x; t < m; t += blockDim.x)
         acc = fma(double(w.x[t]), double(sigma[g.key[t] >> 8]), acc);
@@ -1356,7 +1394,7 @@ k_prog_keys_big(const int64_t *__restrict__ list, int64_t m, const int64_t *__re
 __global__ void __launch_bounds__(256)
 k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
                   const int32_t *__restrict__ ops, int L, const uint32_t *__restrict__ bits,
-                  const int32_t *__restrict__ idx_map, int2 *__restrict__ pairs,
+                  const int32_t *__restrict__ idx_map, uint32_t *__restrict__ pairs,
                   int *__restrict__ npairs, int *__restrict__ step_l, int *__restrict__ flag)
 {
     __shared__ uint32_t C[33][33];
@@ -1375,7 +1413,8 @@ k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
     // block-uniform trip count: every lane reaches the warp-wide append
     for (int t0 = blockIdx.x * blockDim.x; t0 < m; t0 += gridDim.x * blockDim.x) {
         const int t = t0 + int(threadIdx.x);
-        int32_t e = 0;
+        int p = -1;
+        bool neg = false;
         if (t < m) {
             const int64_t kt = key[t], d = kt >> 8;
             const int birth = int(kt & 255) - 1;
@@ -1387,8 +1426,8 @@ k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
                 const int64_t img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
                                     rank_bits(uint32_t(u >> n), C);
                 if (member(bits, img)) {
-                    const int p = idx_map[img];
-                    e = sg > 0 ? p + 1 : -(p + 1);
+                    p = idx_map[img];
+                    neg = sg < 0;
                 } else {
                     escape = true;
                 }
@@ -1404,7 +1443,8 @@ k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
             if (escape && birth > s && birth <= last) *flag = 1;
         }
         const int r = (t < m ? t : 0) / chunk;
-        warp_append(e != 0, s * kClusterCtas + r, make_int2(t, e), pairs, chunk, npairs);
+        warp_append(p >= 0, s * kClusterCtas + r, pair_word(t - r * chunk, p, neg), pairs, chunk,
+                    npairs);
     }
 }
 
@@ -1426,9 +1466,9 @@ __device__ __forceinline__ double cl_sum(cg::cluster_group &cl, double acc, doub
 
 // one cluster: as k_prog_prepare, the vector over the cluster's CTAs
 template <typename T>
-__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024)
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024, 1)
 k_prog_prepare_big(ProgTabs g, const double *__restrict__ cs, int renorm,
-                   double *__restrict__ norm2, T *__restrict__ v)
+                   double *__restrict__ norm2, T *__restrict__ v, int cap)
 {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char clsm[];
@@ -1438,11 +1478,14 @@ k_prog_prepare_big(ProgTabs g, const double *__restrict__ cs, int renorm,
     const int rank = int(cl.block_rank());
     const int m = g.m, chunk = g.chunk;
     const int t0 = rank * chunk, t1 = min(m, t0 + chunk);
-    const ClusterVec<T> x{reinterpret_cast<T *>(clsm), chunk, rank, t0, &cl};
+    const ClusterVec<T> x{reinterpret_cast<T *>(clsm), chunk, rank};
+    uint32_t *sp = reinterpret_cast<uint32_t *>(x.loc + chunk);
     for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x) x.loc[t - t0] = t == 0 ? T(1) : T(0);
     prog_load_steps(g, rank, cs, st);
+    __syncthreads();
+    prog_stage(g, rank, st, sp, cap);
     cl.sync();                                       // every CTA of the cluster is running
-    prog_run<T>(x, g, rank, st, 0, g.steps);
+    prog_run<T>(x, g, rank, st, sp, 0, g.steps);
     T f = T(1);
     if (renorm) {
         double acc = 0.0;
@@ -1467,7 +1510,7 @@ k_prog_prepare_big(ProgTabs g, const double *__restrict__ cs, int renorm,
 template <typename T>
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024)
 k_prog_grad_big(ProgTabs g, const double *__restrict__ cs, const T *__restrict__ sigma,
-                const double *__restrict__ norm2, double *__restrict__ gout)
+                const double *__restrict__ norm2, double *__restrict__ gout, int cap)
 {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char clsm[];
@@ -1477,19 +1520,22 @@ k_prog_grad_big(ProgTabs g, const double *__restrict__ cs, const T *__restrict__
     const int lg = int(blockIdx.x) / kClusterCtas;
     const int m = g.m, chunk = g.chunk;
     const int t0 = rank * chunk, t1 = min(m, t0 + chunk);
-    const ClusterVec<T> f{reinterpret_cast<T *>(clsm), chunk, rank, t0, &cl};
-    const ClusterVec<T> w{reinterpret_cast<T *>(clsm) + chunk, chunk, rank, t0, &cl};
+    const ClusterVec<T> f{reinterpret_cast<T *>(clsm), chunk, rank};
+    const ClusterVec<T> w{reinterpret_cast<T *>(clsm) + chunk, chunk, rank};
+    uint32_t *sp = reinterpret_cast<uint32_t *>(w.loc + chunk);
     for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x) {
         f.loc[t - t0] = t == 0 ? T(1) : T(0);
         w.loc[t - t0] = T(0);
     }
     prog_load_steps(g, rank, cs, st);
+    __syncthreads();
+    prog_stage(g, rank, st, sp, cap);
     cl.sync();
     int b, e;
     prog_op_steps(st.sl, g.steps, lg, b, e);
-    prog_run<T>(f, g, rank, st, 0, e);               // phi_lg = U_lg .. U_1 |HF>
-    prog_generate(f, w, g, rank, st.np, b, e);       // constituents add in order
-    prog_run<T>(w, g, rank, st, e, g.steps);
+    prog_run<T>(f, g, rank, st, sp, 0, e);           // phi_lg = U_lg .. U_1 |HF>
+    prog_generate<T>(f, w, g, rank, st, sp, b, e);   // constituents add in order
+    prog_run<T>(w, g, rank, st, sp, e, g.steps);
     double acc = 0.0;
     for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x)
         acc = fma(double(w.loc[t - t0]), double(sigma[g.key[t] >> 8]), acc);
@@ -1500,47 +1546,91 @@ k_prog_grad_big(ProgTabs g, const double *__restrict__ cs, const T *__restrict__
 
 // ---------------------------------------------------------------------------
 // H restricted to a support (see HssArgs).  Row t enumerates the couplings of
-// its determinant d = (A, B) exactly as k_hpsi_scatter enumerates the targets
-// of d (H is real symmetric, so the column of d is its row), keeping those
-// whose determinant is in the support.  Each row has a fixed slot of
+// its determinant d = (A, B) in the order k_hpsi_scatter enumerates the
+// targets of d (H is real symmetric, so the column of d is its row), keeping
+// those whose determinant is in the support.  A coupling (A', B') can be in
+// the support only if A' is the alpha string and B' the beta string of some
+// support element, so the alpha and beta partners of the row are first
+// filtered by the support's string sets (sa, sb: bitmaps over the alpha and
+// beta strings, in shared memory), and only the surviving candidates are
+// tested against the support's bitmap.  Each row has a fixed slot of
 // `stride` entries (an upper bound of its couplings), so one launch builds the
 // whole matrix with no count pass and no host round trip: per row the block
 // counts each thread's entries, a block scan places them, and a second walk of
 // the same fixed-order enumeration writes them.
 // ---------------------------------------------------------------------------
+constexpr int kHssStrWords = (12870 + 31) / 32;   // C(16, 8) strings of one spin
+
+// the row's alpha excitations whose partner string is in the support's alpha
+// set (fa, *naf) and its beta excitations likewise (fb, *nbf), in excitation
+// order; warp 0 filters alpha, warp 1 beta
+__device__ __forceinline__ void hss_filter(const HssArgs &a, int64_t A, int64_t B,
+                                           const uint32_t *sa, const uint32_t *sb, uint32_t *fa,
+                                           uint32_t *fb, int *naf, int *nbf)
+{
+    const int w = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
+    if (w > 1) return;
+    const int nex = w == 0 ? a.nexa : a.nexb;
+    const uint32_t *bits = w == 0 ? sa : sb;
+    uint32_t *out = w == 0 ? fa : fb;
+    int cnt = 0;
+    for (int e0 = 0; e0 < nex; e0 += 32) {
+        const int e = e0 + lane;
+        uint32_t u = 0u;
+        bool keep = false;
+        if (e < nex) {
+            u = w == 0 ? a.aex[A * a.nexa + e] : a.bexT[size_t(e) * a.Nb + B];
+            const uint32_t o = u & 0xFFFFu;
+            keep = (bits[o >> 5] >> (o & 31)) & 1u;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) out[cnt + __popc(bal & ((1u << lane) - 1u))] = u;
+        cnt += __popc(bal);
+    }
+    if (lane == 0) *(w == 0 ? naf : nbf) = cnt;
+}
+
 template <typename F>
 __device__ __forceinline__ void hss_enumerate(const HssArgs &a, int64_t A, int64_t B,
-                                              const uint32_t *aexs, F &&take)
+                                              const uint32_t *sa, const uint32_t *sb,
+                                              const uint32_t *fa, int naf, const uint32_t *fb,
+                                              int nbf, F &&take)
 {
-    const int n = a.n, nn = n * n, nexa = a.nexa, nexb = a.nexb;
+    const int n = a.n, nn = n * n;
     const int64_t Nb = a.Nb;
-    const int P = nexb > 0 ? int(blockDim.x) / nexb : 0;
-    const bool slot = int(threadIdx.x) < P * nexb;
-    const int fs = slot ? int(threadIdx.x) % nexb : 0, ph = slot ? int(threadIdx.x) / nexb : 0;
-    for (int k = a.Ma_ptr[A] + threadIdx.x; k < a.Ma_ptr[A + 1]; k += blockDim.x)
-        take(int64_t(a.Ma_col[k]) * Nb + B, a.Ma_val[k]);
-    for (int k = a.Mb_ptr[B] + threadIdx.x; k < a.Mb_ptr[B + 1]; k += blockDim.x)
-        take(A * Nb + a.Mb_col[k], a.Mb_val[k]);
+    const int bd = int(blockDim.x), tid = int(threadIdx.x);
+    // same-spin couplings: the CSR rows of both strings
+    for (int k = a.Ma_ptr[A] + tid; k < a.Ma_ptr[A + 1]; k += bd) {
+        const uint32_t Ao = uint32_t(a.Ma_col[k]);
+        if ((sa[Ao >> 5] >> (Ao & 31)) & 1u) take(int64_t(Ao) * Nb + B, a.Ma_val[k]);
+    }
+    for (int k = a.Mb_ptr[B] + tid; k < a.Mb_ptr[B + 1]; k += bd) {
+        const uint32_t Bo = uint32_t(a.Mb_col[k]);
+        if ((sb[Bo >> 5] >> (Bo & 31)) & 1u) take(A * Nb + Bo, a.Mb_val[k]);
+    }
     const uint32_t am = a.astr[A], bm = a.bstr[B];
-    if (slot) {
-        const uint32_t w = a.bexT[size_t(fs) * Nb + B];
-        const int64_t Bo = w & 0xFFFFu;
-        const int rs = int((w >> 20) & 15) * n + int((w >> 16) & 15);
-        const bool negb = (w >> 31) != 0;
-        if (ph == 0) {
+    // alpha-beta couplings with a beta excitation: the (alpha diagonal +
+    // filtered alpha excitations) x (filtered beta excitations) grid
+    const int na1 = naf + 1;
+    for (int i = tid; i < nbf * na1; i += bd) {
+        const uint32_t wv = fb[i / na1];
+        const int e = i % na1 - 1;
+        const int64_t Bo = wv & 0xFFFFu;
+        const int rs = int((wv >> 20) & 15) * n + int((wv >> 16) & 15);
+        const bool negb = (wv >> 31) != 0;
+        if (e < 0) {
             const double c = sum_diag<double>(a.V, n, nn, am, rs);
             take(A * Nb + Bo, negb ? -c : c);
-        }
-        const double *Vrs = a.V + rs;
-        for (int e = ph; e < nexa; e += P) {
-            const uint32_t u = aexs[e];
-            const int64_t Ao = u & 0xFFFFu;
+        } else {
+            const uint32_t u = fa[e];
             const int pq = int((u >> 20) & 15) * n + int((u >> 16) & 15);
-            const double c = Vrs[size_t(pq) * nn];
-            take(Ao * Nb + Bo, negb != ((u >> 31) != 0) ? -c : c);
+            const double c = a.V[size_t(pq) * nn + rs];
+            take(int64_t(u & 0xFFFFu) * Nb + Bo, negb != ((u >> 31) != 0) ? -c : c);
         }
     }
-    for (int e = int(threadIdx.x) - 1; e < nexa; e += blockDim.x) {
+    // alpha-beta couplings diagonal in beta: the diagonal and the filtered
+    // alpha excitations
+    for (int e = tid - 1; e < naf; e += bd) {
         double c = 0.0;
         if (e < 0) {
             for (uint32_t mm = bm; mm; mm &= mm - 1) {
@@ -1549,7 +1639,7 @@ __device__ __forceinline__ void hss_enumerate(const HssArgs &a, int64_t A, int64
             }
             take(A * Nb + B, c);
         } else {
-            const uint32_t u = aexs[e];
+            const uint32_t u = fa[e];
             const int pq = int((u >> 20) & 15) * n + int((u >> 16) & 15);
             for (uint32_t mm = bm; mm; mm &= mm - 1) {
                 const int rr = __ffs(mm) - 1;
@@ -1557,6 +1647,19 @@ __device__ __forceinline__ void hss_enumerate(const HssArgs &a, int64_t A, int64
             }
             take(int64_t(u & 0xFFFFu) * Nb + B, (u >> 31) ? -c : c);
         }
+    }
+}
+
+// the support's alpha and beta string sets (sa, sb cleared before)
+__global__ void __launch_bounds__(256)
+k_hss_strings(const int64_t *__restrict__ key, int64_t m, int64_t Nb, uint32_t *__restrict__ sa,
+              uint32_t *__restrict__ sb)
+{
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < m;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t d = key[t] >> 8, A = d / Nb, B = d % Nb;
+        atomicOr(sa + (A >> 5), 1u << (A & 31));
+        atomicOr(sb + (B >> 5), 1u << (B & 31));
     }
 }
 
@@ -1674,23 +1777,28 @@ k_bits_emit(const uint32_t *__restrict__ bits, int64_t words, const int64_t *__r
 __global__ void __launch_bounds__(256)
 k_hss_fill(HssArgs a)
 {
-    __shared__ uint32_t aexs[64];
+    __shared__ uint32_t sa[kHssStrWords], sb[kHssStrWords];
+    __shared__ uint32_t fa[64], fb[64];
+    __shared__ int naf, nbf;
     __shared__ int wt[8], tot;
+    for (int i = threadIdx.x; i < int((a.Na + 31) >> 5); i += blockDim.x) sa[i] = a.sa[i];
+    for (int i = threadIdx.x; i < int((a.Nb + 31) >> 5); i += blockDim.x) sb[i] = a.sb[i];
     for (int64_t t = blockIdx.x; t < a.m; t += gridDim.x) {
         const int64_t d = a.key[t] >> 8;
         const int64_t A = d / a.Nb, B = d % a.Nb;
         __syncthreads();
-        if (int(threadIdx.x) < a.nexa) aexs[threadIdx.x] = a.aex[A * a.nexa + threadIdx.x];
+        hss_filter(a, A, B, sa, sb, fa, fb, &naf, &nbf);
         __syncthreads();
+        const int na = naf, nb = nbf;
         int c = 0;
-        hss_enumerate(a, A, B, aexs, [&](int64_t o, double) {
+        hss_enumerate(a, A, B, sa, sb, fa, na, fb, nb, [&](int64_t o, double) {
             if (member(a.bits, o)) ++c;
         });
         // row t owns entries [t * stride, (t + 1) * stride); stride bounds the
         // enumeration's length, and no write passes the row's end
         const int64_t row0 = t * a.stride, row1 = row0 + a.stride;
         int64_t pos = row0 + block_excl_scan(c, wt, &tot);
-        hss_enumerate(a, A, B, aexs, [&](int64_t o, double v) {
+        hss_enumerate(a, A, B, sa, sb, fa, na, fb, nb, [&](int64_t o, double v) {
             if (member(a.bits, o)) {
                 if (pos < row1) {
                     a.col[pos] = uint32_t(o);
@@ -1743,7 +1851,16 @@ k_hss_apply(const int64_t *__restrict__ key, int64_t m, const int32_t *__restric
 
 cudaError_t hss_fill(const HssArgs &a, int64_t *nnz, int num_sms, cudaStream_t st)
 {
-    if (a.m < 1 || a.stride < 1) return cudaErrorInvalidValue;
+    if (a.m < 1 || a.stride < 1 || a.Na > 12870 || a.Nb > 12870 || a.nexa > 64 || a.nexb > 64)
+        return cudaErrorInvalidValue;
+    const size_t wa = size_t((a.Na + 31) >> 5), wb = size_t((a.Nb + 31) >> 5);
+    cudaError_t e = cudaMemsetAsync(a.sa, 0, wa * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.sb, 0, wb * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    int64_t gs = (a.m + 255) / 256;
+    if (gs > int64_t(num_sms) * 8) gs = int64_t(num_sms) * 8;
+    k_hss_strings<<<unsigned(gs), 256, 0, st>>>(a.key, a.m, a.Nb, a.sa, a.sb);
+    hy::count_launch();
     int64_t g = a.m < int64_t(num_sms) * 16 ? a.m : int64_t(num_sms) * 16;
     k_hss_fill<<<unsigned(g), 256, 0, st>>>(a); hy::count_launch();
     k_hss_total<<<1, 1024, 0, st>>>(a.cnt, a.m, nnz); hy::count_launch();
@@ -1935,7 +2052,7 @@ cudaError_t grad_sparse(const SparseGradArgs<T> &a, int num_sms, cudaStream_t st
 
 cudaError_t prog_compile(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
                          const SvOpArgs &o, const int32_t *ops, int L, int64_t *key,
-                         int2 *pairs, int *npairs, int *step_l, int *flag, cudaStream_t st)
+                         uint32_t *pairs, int *npairs, int *step_l, int *flag, cudaStream_t st)
 {
     if (m < 1 || m > kProgMax || steps < 1 || steps > kProgSteps) return cudaErrorInvalidValue;
     // up to 128 KB of dynamic shared memory (set per call: the attribute
@@ -1956,6 +2073,27 @@ cudaError_t prog_compile(const int64_t *list, int64_t m, const int64_t *step_len
     return cudaGetLastError();
 }
 
+namespace {
+// dynamic shared memory of a program launch: the vectors (vec bytes) and as
+// many staged pair words (*cap) as the block's opt-in limit leaves beside
+// the kernel's static shared memory (its ProgSteps and reduction slots, at
+// most sizeof(ProgSteps<T>) + 512 bytes)
+template <typename T, typename K>
+cudaError_t prog_smem(K kernel, size_t vec, size_t *smem, int *cap)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const size_t stat = sizeof(ProgSteps<T>) + 512;
+    if (size_t(optin) < stat + vec) return cudaErrorInvalidValue;
+    const size_t words = (size_t(optin) - stat - vec) / 4;
+    *cap = int(words);
+    *smem = vec + words * 4;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(*smem));
+}
+}  // namespace
+
 template <typename T>
 cudaError_t prog_prepare(const ProgTabs &g, const double *cs, bool renorm, double *norm2, T *v,
                          cudaStream_t st)
@@ -1963,13 +2101,11 @@ cudaError_t prog_prepare(const ProgTabs &g, const double *cs, bool renorm, doubl
     if (g.m < 1 || g.m > kProgMax || g.steps < 1 || g.steps > kProgSteps || g.ranks != 1 ||
         g.chunk != g.m)
         return cudaErrorInvalidValue;
-    // up to 96 KB of dynamic shared memory
-    const cudaError_t e = cudaFuncSetAttribute(k_prog_prepare<T>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               int(kProgMax * sizeof(T)));
+    size_t smem = 0;
+    int cap = 0;
+    const cudaError_t e = prog_smem<T>(k_prog_prepare<T>, size_t(g.m) * sizeof(T), &smem, &cap);
     if (e != cudaSuccess) return e;
-    k_prog_prepare<T><<<1, kProgThreads, size_t(g.m) * sizeof(T), st>>>(g, cs, renorm ? 1 : 0,
-                                                                        norm2, v);
+    k_prog_prepare<T><<<1, kProgThreads, smem, st>>>(g, cs, renorm ? 1 : 0, norm2, v, cap);
     hy::count_launch();
     return cudaGetLastError();
 }
@@ -1981,13 +2117,11 @@ cudaError_t prog_grad(const ProgTabs &g, const double *cs, int L, const T *sigma
     if (g.m < 1 || g.m > kProgMax || g.steps < 1 || g.steps > kProgSteps || g.ranks != 1 ||
         g.chunk != g.m || L < 1)
         return cudaErrorInvalidValue;
-    const size_t smem = 2 * size_t(g.m) * sizeof(T);
-    // up to 192 KB of dynamic shared memory
-    const cudaError_t e = cudaFuncSetAttribute(k_prog_grad<T>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               int(2 * kProgMax * sizeof(T)));
+    size_t smem = 0;
+    int cap = 0;
+    const cudaError_t e = prog_smem<T>(k_prog_grad<T>, 2 * size_t(g.m) * sizeof(T), &smem, &cap);
     if (e != cudaSuccess) return e;
-    k_prog_grad<T><<<unsigned(L), kProgThreads, smem, st>>>(g, cs, sigma, norm2, gout);
+    k_prog_grad<T><<<unsigned(L), kProgThreads, smem, st>>>(g, cs, sigma, norm2, gout, cap);
     hy::count_launch();
     return cudaGetLastError();
 }
@@ -2011,7 +2145,7 @@ template cudaError_t hpsi_support<double>(const SupRowsArgs<double> &, int, cuda
 template cudaError_t hpsi_support<float>(const SupRowsArgs<float> &, int, cudaStream_t);
 cudaError_t prog_compile_big(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
                              const SvOpArgs &o, const int32_t *ops, int L, const uint32_t *bits,
-                             int64_t *key, int2 *pairs, int *npairs, int *step_l,
+                             int64_t *key, uint32_t *pairs, int *npairs, int *step_l,
                              int32_t *idx_map, int *flag, cudaStream_t st)
 {
     if (m <= kProgMax || m > kProgBig || steps < 1 || steps > kProgSteps)
@@ -2042,11 +2176,12 @@ cudaError_t prog_prepare_big(const ProgTabs &g, const double *cs, bool renorm, d
                              T *v, cudaStream_t st)
 {
     if (!big_tabs_ok(g)) return cudaErrorInvalidValue;
-    const size_t smem = size_t(g.chunk) * sizeof(T);
-    cudaError_t e = cudaFuncSetAttribute(k_prog_prepare_big<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    size_t smem = 0;
+    int cap = 0;
+    const cudaError_t e = prog_smem<T>(k_prog_prepare_big<T>, size_t(g.chunk) * sizeof(T), &smem,
+                                       &cap);
     if (e != cudaSuccess) return e;
-    k_prog_prepare_big<T><<<kClusterCtas, 1024, smem, st>>>(g, cs, renorm ? 1 : 0, norm2, v);
+    k_prog_prepare_big<T><<<kClusterCtas, 1024, smem, st>>>(g, cs, renorm ? 1 : 0, norm2, v, cap);
     hy::count_launch();
     return cudaGetLastError();
 }
@@ -2056,11 +2191,13 @@ cudaError_t prog_grad_big(const ProgTabs &g, const double *cs, int L, const T *s
                           const double *norm2, double *gout, cudaStream_t st)
 {
     if (!big_tabs_ok(g) || L < 1) return cudaErrorInvalidValue;
-    const size_t smem = 2 * size_t(g.chunk) * sizeof(T);
-    cudaError_t e = cudaFuncSetAttribute(k_prog_grad_big<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    size_t smem = 0;
+    int cap = 0;
+    const cudaError_t e = prog_smem<T>(k_prog_grad_big<T>, 2 * size_t(g.chunk) * sizeof(T), &smem,
+                                       &cap);
     if (e != cudaSuccess) return e;
-    k_prog_grad_big<T><<<unsigned(kClusterCtas * L), 1024, smem, st>>>(g, cs, sigma, norm2, gout);
+    k_prog_grad_big<T><<<unsigned(kClusterCtas * L), 1024, smem, st>>>(g, cs, sigma, norm2, gout,
+                                                                       cap);
     hy::count_launch();
     return cudaGetLastError();
 }
