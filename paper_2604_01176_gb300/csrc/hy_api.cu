@@ -2385,7 +2385,7 @@ hy_status prog_create(const hy_ham *h, int max_steps, SupportProgram **out)
     if (e == cudaSuccess)
         e = cudaMalloc(&g->pairs, size_t(max_steps) * hy::k::kProgMax * sizeof(uint32_t));
     if (e == cudaSuccess)
-        e = cudaMalloc(&g->npairs, size_t(max_steps) * hy::k::kClusterCtas * sizeof(int));
+        e = cudaMalloc(&g->npairs, 2 * size_t(max_steps) * hy::k::kClusterCtas * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&g->step_l, size_t(max_steps) * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&g->flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(g->flag, 0, sizeof(int));
@@ -2587,6 +2587,7 @@ hy::k::ProgTabs prog_tabs(const SupportProgram *g)
     t.key = big ? g->key_big : g->key;
     t.pairs = big ? g->pairs_big : g->pairs;
     t.npairs = g->npairs;
+    t.nrest = g->npairs + g->steps * (big ? hy::k::kClusterCtas : 1);
     t.step_l = g->step_l;
     t.m = int(g->m);
     t.steps = int(g->steps);

@@ -370,8 +370,12 @@ cudaError_t sv_prepare(const SVec<T> &x, const SvOpArgs &o, const int32_t *ops, 
 //             part for one CTA, kClusterCtas for a cluster), the pairs of
 //             step s whose domain end t lies in part r are
 //             pairs[(s * ranks + r) * chunk + i], i < npairs[s * ranks + r],
-//             in no fixed order: the pairs of one step are disjoint (an image
-//             end has no forward image), so no result depends on it;
+//             those with an end listed before step s (the only ones that can
+//             be nonzero when the preparation reaches step s), and
+//             pairs[(s * ranks + r + 1) * chunk - 1 - i], i < nrest[s * ranks
+//             + r], the others; in no fixed order: the pairs of one step are
+//             disjoint (an image end has no forward image), so no result
+//             depends on it;
 //   step_l[s] = the operator (position in the ansatz) of step s;
 //   *flag   = 1 when some generator A_l = sum (C - C^dagger) of op l would
 //             leave the support from an element that op l's own later
@@ -382,13 +386,14 @@ constexpr int kProgSteps = 254;   // steps of one program (8-bit birth tags)
 struct ProgTabs {
     const int64_t *key;
     const uint32_t *pairs;
-    const int *npairs;
+    const int *npairs, *nrest;
     const int *step_l;
     int m, steps, ranks, chunk;
 };
 // list: the m support elements in the order a structural sv_prepare listed
 // them, step_len its lengths after each of the `steps` rotations; pairs holds
-// steps * m entries, npairs `steps` counts, step_l `steps` entries
+// steps * m entries, npairs 2 * steps counts (nrest = npairs + steps), step_l
+// `steps` entries
 cudaError_t prog_compile(const int64_t *list, int64_t m, const int64_t *step_len, int steps,
                          const SvOpArgs &o, const int32_t *ops, int L, int64_t *key,
                          uint32_t *pairs, int *npairs, int *step_l, int *flag, cudaStream_t st);
@@ -412,7 +417,7 @@ cudaError_t prog_grad(const ProgTabs &g, const double *cs, int L, const T *sigma
 // memory of a cluster of 8 CTAs (prepare: one cluster; gradient: one cluster
 // per angle); the pair lists per step and CTA (ranks = kClusterCtas), pairs
 // holding steps * kClusterCtas * ceil(m / kClusterCtas) entries and npairs
-// steps * kClusterCtas counts
+// 2 * steps * kClusterCtas counts (nrest = npairs + steps * kClusterCtas)
 constexpr int64_t kProgBig = 65536;
 constexpr int kClusterCtas = 8;
 cudaError_t prog_compile_big(const int64_t *list, int64_t m, const int64_t *step_len, int steps,

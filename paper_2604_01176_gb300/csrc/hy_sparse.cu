@@ -1005,11 +1005,12 @@ __device__ __forceinline__ uint32_t pair_word(int tl, int p, bool neg)
 constexpr uint32_t kNoPair = 0xFFFFFFFFu;
 
 // warp-aggregated append: every lane with `has` adds v to list `slot`
-// (count counts[slot], items from out + slot * stride); the lanes of one warp
+// (count counts[slot], items from out + slot * stride forwards, or with
+// `back` from out + (slot + 1) * stride - 1 backwards); the lanes of one warp
 // that share a slot take one atomic.  Every lane of the warp must call it.
 __device__ __forceinline__ void warp_append(bool has, int slot, uint32_t v,
                                             uint32_t *__restrict__ out, int64_t stride,
-                                            int *__restrict__ counts)
+                                            int *__restrict__ counts, bool back = false)
 {
     const unsigned act = __ballot_sync(0xffffffffu, has);
     if (!has) return;
@@ -1019,7 +1020,8 @@ __device__ __forceinline__ void warp_append(bool has, int slot, uint32_t v,
     int base = 0;
     if (lane == leader) base = atomicAdd(counts + slot, __popc(grp));
     base = __shfl_sync(grp, base, leader);
-    out[int64_t(slot) * stride + base + __popc(grp & ((1u << lane) - 1u))] = v;
+    const int64_t i = base + __popc(grp & ((1u << lane) - 1u));
+    out[back ? (int64_t(slot) + 1) * stride - 1 - i : int64_t(slot) * stride + i] = v;
 }
 
 // the op (l), constituent (ci) and last step of op l for step s; l = L when
@@ -1046,7 +1048,7 @@ __device__ __forceinline__ void prog_step_op(const int32_t *__restrict__ desc,
 __global__ void __launch_bounds__(256)
 k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t *__restrict__ ops,
               int L, uint32_t *__restrict__ pairs, int *__restrict__ npairs,
-              int *__restrict__ step_l, int *__restrict__ flag)
+              int *__restrict__ nrest, int *__restrict__ step_l, int *__restrict__ flag)
 {
     __shared__ uint32_t C[33][33];
     for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
@@ -1058,7 +1060,7 @@ k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t 
     if (blockIdx.x == 0 && threadIdx.x == 0) step_l[s] = l;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     int p = -1;
-    bool neg = false;
+    bool neg = false, active = false;
     if (t < m) {
         int fw[4], bw[4], len;
         op_strings(o.desc + 11 * ops[l] + 1 + 5 * ci, fw, bw, len);
@@ -1076,6 +1078,9 @@ k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t 
             p = prog_find(key, m, img);
             neg = sg < 0;
             escape = p < 0;
+            // a pair can be nonzero before step s only if an end was listed
+            // before it (tag = listing step + 1, 0 for |HF>)
+            active = p >= 0 && (int(kt & 255) <= s || int(key[p] & 255) <= s);
         } else {
             u = mask;
             sg = 1;
@@ -1091,7 +1096,8 @@ k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t 
         // later by op l's own constituents
         if (escape && birth > s && birth <= last) *flag = 1;
     }
-    warp_append(p >= 0, s, pair_word(t, p, neg), pairs, m, npairs);
+    warp_append(p >= 0 && active, s, pair_word(t, p, neg), pairs, m, npairs);
+    warp_append(p >= 0 && !active, s, pair_word(t, p, neg), pairs, m, nrest, true);
 }
 
 // pairs a thread takes per round of a step read from global memory (loaded
@@ -1164,12 +1170,14 @@ __device__ __forceinline__ void pair_generator(const V &f, const V &w, uint32_t 
     }
 }
 
-// per-step values of a program in shared memory: this part's pair counts,
-// the operator of each step and its cos / sin, and where the step's pairs
-// were staged in shared memory (-1: read from global memory)
+// per-step values of a program in shared memory: this part's pair counts
+// (np: pairs with an end listed before the step, at the front of the step's
+// list; nr: the others, at its back), the operator of each step and its
+// cos / sin, and where the step's pairs were staged in shared memory (np
+// words, then nr; -1: read from global memory)
 template <typename T>
 struct ProgSteps {
-    int np[kProgSteps];
+    int np[kProgSteps], nr[kProgSteps];
     int sl[kProgSteps];
     int off[kProgSteps];
     T c[kProgSteps], sn[kProgSteps];
@@ -1184,6 +1192,7 @@ __device__ __forceinline__ void prog_load_steps(const ProgTabs &g, int rank,
         const int l = g.step_l[s];
         st.sl[s] = l;
         st.np[s] = g.npairs[s * g.ranks + rank];
+        st.nr[s] = g.nrest[s * g.ranks + rank];
         st.c[s] = T(cs[2 * l]);
         st.sn[s] = T(cs[2 * l + 1]);
     }
@@ -1206,7 +1215,7 @@ __device__ __forceinline__ void prog_stage(const ProgTabs &g, int rank, ProgStep
     if (threadIdx.x == 0) {
         int acc = 0;
         for (int s = 0; s < g.steps; ++s) {
-            const int n = st.np[s];
+            const int n = st.np[s] + st.nr[s];
             if (n <= cap - acc) {
                 st.off[s] = acc;
                 acc += n;
@@ -1220,51 +1229,72 @@ __device__ __forceinline__ void prog_stage(const ProgTabs &g, int rank, ProgStep
         const int o = st.off[s];
         if (o < 0) continue;
         const uint32_t *src = g.pairs + (int64_t(s) * g.ranks + rank) * g.chunk;
-        for (int i = threadIdx.x; i < st.np[s]; i += blockDim.x) cp_async4(sp + o + i, src + i);
+        const int np = st.np[s], nr = st.nr[s];
+        for (int i = threadIdx.x; i < np; i += blockDim.x) cp_async4(sp + o + i, src + i);
+        const uint32_t *rest = src + g.chunk - nr;
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) cp_async4(sp + o + np + i, rest + i);
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
 }
 
-// steps [s0, s1) on x, one barrier (CTA or cluster) after each
+// n pairs from global memory at pr, a round of kPairU per thread at a time
+template <typename T, class V>
+__device__ __forceinline__ void pairs_rotate_global(const V &x, const uint32_t *__restrict__ pr,
+                                                    int n, T c, T sn)
+{
+    const int R = kPairU * int(blockDim.x);
+    for (int i0 = threadIdx.x; i0 < n; i0 += R) {
+        uint32_t q[kPairU];
+        pairs_load(q, pr, n, i0);
+#pragma unroll
+        for (int k = 0; k < kPairU; ++k)
+            if (q[k] != kNoPair) pair_rotate<T>(x, q[k], c, sn);
+    }
+}
+
+// steps [s0, s1) on x, one barrier (CTA or cluster) after each: the pairs
+// with an end listed before the step only (x is U_s .. U_1|HF>, zero on
+// determinants listed later), or with `all` every pair
 template <typename T, class V>
 __device__ __forceinline__ void prog_run(const V &x, const ProgTabs &g, int rank,
                                          const ProgSteps<T> &st, const uint32_t *sp, int s0,
-                                         int s1)
+                                         int s1, bool all)
 {
-    const int R = kPairU * int(blockDim.x);
     for (int s = s0; s < s1; ++s) {
-        const int n = st.np[s], o = st.off[s];
+        const int np = st.np[s], nr = all ? st.nr[s] : 0, o = st.off[s];
         const T c = st.c[s], sn = st.sn[s];
         if (o >= 0) {
             const uint32_t *pr = sp + o;
+            const int n = np + nr;
 #pragma unroll 4
             for (int i = threadIdx.x; i < n; i += blockDim.x) pair_rotate<T>(x, pr[i], c, sn);
         } else {
             const uint32_t *pr = g.pairs + (int64_t(s) * g.ranks + rank) * g.chunk;
-            for (int i0 = threadIdx.x; i0 < n; i0 += R) {
-                uint32_t q[kPairU];
-                pairs_load(q, pr, n, i0);
-#pragma unroll
-                for (int k = 0; k < kPairU; ++k)
-                    if (q[k] != kNoPair) pair_rotate<T>(x, q[k], c, sn);
-            }
+            pairs_rotate_global<T>(x, pr, np, c, sn);
+            if (nr) pairs_rotate_global<T>(x, pr + g.chunk - nr, nr, c, sn);
         }
         x.sync();
     }
 }
 
-// the generator of op lg (its constituent steps [b, e), in order) from f
-// into w, one barrier after each constituent
+// the generator of op lg (its constituent steps [b, e), in order, every
+// pair) from f into w, one barrier after each constituent
 template <typename T, class V>
 __device__ __forceinline__ void prog_generate(const V &f, const V &w, const ProgTabs &g, int rank,
                                               const ProgSteps<T> &st, const uint32_t *sp, int b,
                                               int e)
 {
     for (int s = b; s < e; ++s) {
-        const int n = st.np[s], o = st.off[s];
-        const uint32_t *pr = o >= 0 ? sp + o : g.pairs + (int64_t(s) * g.ranks + rank) * g.chunk;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) pair_generator(f, w, pr[i]);
+        const int np = st.np[s], nr = st.nr[s], o = st.off[s];
+        if (o >= 0) {
+            for (int i = threadIdx.x; i < np + nr; i += blockDim.x) pair_generator(f, w, sp[o + i]);
+        } else {
+            const uint32_t *pr = g.pairs + (int64_t(s) * g.ranks + rank) * g.chunk;
+            for (int i = threadIdx.x; i < np; i += blockDim.x) pair_generator(f, w, pr[i]);
+            const uint32_t *rest = pr + g.chunk - nr;
+            for (int i = threadIdx.x; i < nr; i += blockDim.x) pair_generator(f, w, rest[i]);
+        }
         f.sync();
     }
 }
@@ -1311,7 +1341,7 @@ k_prog_prepare(ProgTabs g, const double *__restrict__ cs, int renorm, double *__
     prog_load_steps(g, 0, cs, st);
     __syncthreads();
     prog_stage(g, 0, st, sp, cap);
-    prog_run<T>(x, g, 0, st, sp, 0, g.steps);
+    prog_run<T>(x, g, 0, st, sp, 0, g.steps, false);
     if (renorm) {
         double acc = 0.0;
         for (int t = threadIdx.x; t < m; t += blockDim.x)
@@ -1351,9 +1381,9 @@ k_prog_grad(ProgTabs g, const double *__restrict__ cs, const T *__restrict__ sig
     prog_stage(g, 0, st, sp, cap);
     int b, e;
     prog_op_steps(st.sl, g.steps, lg, b, e);
-    prog_run<T>(f, g, 0, st, sp, 0, e);              // phi_lg = U_lg .. U_1 |HF>
+    prog_run<T>(f, g, 0, st, sp, 0, e, false);       // phi_lg = U_lg .. U_1 |HF>
     prog_generate<T>(f, w, g, 0, st, sp, b, e);      // constituents add in order
-    prog_run<T>(w, g, 0, st, sp, e, g.steps);
+    prog_run<T>(w, g, 0, st, sp, e, g.steps, true);  // w may hold later-listed elements
     double acc = 0.0;
     for (int t = threadIdx.x; t < m; t += blockDim.x)
         acc = fma(double(w.x[t]), double(sigma[g.key[t] >> 8]), acc);
@@ -1395,7 +1425,8 @@ __global__ void __launch_bounds__(256)
 k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
                   const int32_t *__restrict__ ops, int L, const uint32_t *__restrict__ bits,
                   const int32_t *__restrict__ idx_map, uint32_t *__restrict__ pairs,
-                  int *__restrict__ npairs, int *__restrict__ step_l, int *__restrict__ flag)
+                  int *__restrict__ npairs, int *__restrict__ nrest, int *__restrict__ step_l,
+                  int *__restrict__ flag)
 {
     __shared__ uint32_t C[33][33];
     for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = o.binom33[i];
@@ -1414,7 +1445,7 @@ k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
     for (int t0 = blockIdx.x * blockDim.x; t0 < m; t0 += gridDim.x * blockDim.x) {
         const int t = t0 + int(threadIdx.x);
         int p = -1;
-        bool neg = false;
+        bool neg = false, active = false;
         if (t < m) {
             const int64_t kt = key[t], d = kt >> 8;
             const int birth = int(kt & 255) - 1;
@@ -1428,6 +1459,7 @@ k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
                 if (member(bits, img)) {
                     p = idx_map[img];
                     neg = sg < 0;
+                    active = int(kt & 255) <= s || int(key[p] & 255) <= s;
                 } else {
                     escape = true;
                 }
@@ -1443,8 +1475,9 @@ k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
             if (escape && birth > s && birth <= last) *flag = 1;
         }
         const int r = (t < m ? t : 0) / chunk;
-        warp_append(p >= 0, s * kClusterCtas + r, pair_word(t - r * chunk, p, neg), pairs, chunk,
-                    npairs);
+        const uint32_t wd = pair_word(t - r * chunk, p, neg);
+        warp_append(p >= 0 && active, s * kClusterCtas + r, wd, pairs, chunk, npairs);
+        warp_append(p >= 0 && !active, s * kClusterCtas + r, wd, pairs, chunk, nrest, true);
     }
 }
 
@@ -1485,7 +1518,7 @@ k_prog_prepare_big(ProgTabs g, const double *__restrict__ cs, int renorm,
     __syncthreads();
     prog_stage(g, rank, st, sp, cap);
     cl.sync();                                       // every CTA of the cluster is running
-    prog_run<T>(x, g, rank, st, sp, 0, g.steps);
+    prog_run<T>(x, g, rank, st, sp, 0, g.steps, false);
     T f = T(1);
     if (renorm) {
         double acc = 0.0;
@@ -1508,7 +1541,7 @@ k_prog_prepare_big(ProgTabs g, const double *__restrict__ cs, int renorm,
 
 // cluster lg (of L): as k_prog_grad, f and w over the cluster's CTAs
 template <typename T>
-__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024)
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(1024, 1)
 k_prog_grad_big(ProgTabs g, const double *__restrict__ cs, const T *__restrict__ sigma,
                 const double *__restrict__ norm2, double *__restrict__ gout, int cap)
 {
@@ -1533,9 +1566,9 @@ k_prog_grad_big(ProgTabs g, const double *__restrict__ cs, const T *__restrict__
     cl.sync();
     int b, e;
     prog_op_steps(st.sl, g.steps, lg, b, e);
-    prog_run<T>(f, g, rank, st, sp, 0, e);           // phi_lg = U_lg .. U_1 |HF>
+    prog_run<T>(f, g, rank, st, sp, 0, e, false);    // phi_lg = U_lg .. U_1 |HF>
     prog_generate<T>(f, w, g, rank, st, sp, b, e);   // constituents add in order
-    prog_run<T>(w, g, rank, st, sp, e, g.steps);
+    prog_run<T>(w, g, rank, st, sp, e, g.steps, true);
     double acc = 0.0;
     for (int t = t0 + int(threadIdx.x); t < t1; t += blockDim.x)
         acc = fma(double(w.loc[t - t0]), double(sigma[g.key[t] >> 8]), acc);
@@ -2061,14 +2094,16 @@ cudaError_t prog_compile(const int64_t *list, int64_t m, const int64_t *step_len
                                          int(kProgSortMax * 8));
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(flag, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(npairs, 0, size_t(steps) * sizeof(int), st);
+    // the counts of the front (npairs[0, steps)) and back (npairs[steps,
+    // 2 steps)) lists
+    if (e == cudaSuccess) e = cudaMemsetAsync(npairs, 0, 2 * size_t(steps) * sizeof(int), st);
     if (e != cudaSuccess) return e;
     int64_t P = 1;
     while (P < m) P <<= 1;
     k_prog_sort<<<1, 1024, size_t(P) * 8, st>>>(list, m, step_len, steps, key);
     hy::count_launch();
     k_prog_tables<<<dim3(unsigned((m + 255) / 256), unsigned(steps)), 256, 0, st>>>(
-        key, int(m), o, ops, L, pairs, npairs, step_l, flag);
+        key, int(m), o, ops, L, pairs, npairs, npairs + steps, step_l, flag);
     hy::count_launch();
     return cudaGetLastError();
 }
@@ -2152,13 +2187,14 @@ cudaError_t prog_compile_big(const int64_t *list, int64_t m, const int64_t *step
         return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(npairs, 0, size_t(steps) * kClusterCtas * sizeof(int), st);
+        e = cudaMemsetAsync(npairs, 0, 2 * size_t(steps) * kClusterCtas * sizeof(int), st);
     if (e != cudaSuccess) return e;
     k_prog_keys_big<<<unsigned((m + 255) / 256), 256, 0, st>>>(list, m, step_len, steps, key,
                                                                 idx_map);
     hy::count_launch();
     k_prog_tables_big<<<dim3(unsigned((m + 255) / 256), unsigned(steps)), 256, 0, st>>>(
-        key, int(m), o, ops, L, bits, idx_map, pairs, npairs, step_l, flag);
+        key, int(m), o, ops, L, bits, idx_map, pairs, npairs, npairs + steps * kClusterCtas, step_l,
+        flag);
     hy::count_launch();
     return cudaGetLastError();
 }
