@@ -127,6 +127,14 @@ struct hy_adapt {
     int64_t prog_m = 0;                  // its support size
     bool prog_grad_ok = false;           // its tables serve the forward gradient
     bool prog_support[2] = {false, false};   // ss[dt][0] lists the program's support
+    // an optimiser's evaluation on a compiled program also queues that
+    // point's forward gradient (read into h_g) behind the energy, and waits
+    // only for the energy (ev_energy): the gradient that usually follows is
+    // then already on its way
+    bool spec_pending = false;
+    hy_dtype spec_dt = HY_F64;
+    std::vector<double> spec_theta;
+    cudaEvent_t ev_energy = nullptr;
 };
 
 namespace {
@@ -199,7 +207,7 @@ const double kScatterPerDense[2] = {20.0, 135.0};
 // sigma = H psi by the scatter, E = <psi|sigma> over the support.  *ok =
 // false when the support list overflowed (nothing valid is left).
 hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
-                        cudaStream_t st, double *e, bool *ok)
+                        cudaStream_t st, double *e, bool *ok, bool speculate)
 {
     const int d = di(dt);
     hy::SparseState *S = a->ss[d][0], *G = a->ss[d][3];
@@ -303,8 +311,9 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     const bool track = !use_hss && !on_support && !dense_sigma &&
                        est <= double(hy::sstate_cap(G));
     if (use_hss) {
+        // the energy comes with the apply (psi on the support = S's list)
         a->ss_clean[d][3] = false;
-        HY_TRY(hy::prog_hss_apply(a->prog, psi, sigma, dt, st));
+        HY_TRY(hy::prog_hss_apply(a->prog, psi, sigma, dt, a->d_e, st));
     } else if (on_support) {
         HY_TRY(hy::sstate_reset(G, !a->ss_clean[d][3], false, st));
         a->ss_clean[d][3] = true;
@@ -322,7 +331,7 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     }
     a->sigma_full[d] = !use_hss && !on_support;
     a->sig_support[d] = on_support;
-    HY_TRY(hy::sstate_dot(S, sigma, a->d_e, st));
+    if (!use_hss) HY_TRY(hy::sstate_dot(S, sigma, a->d_e, st));
     int64_t cnt[2] = {0, 0};
     a->h_cnt[1] = 0;
     HY_TRY(xfer(a, a->h_e, a->d_e, sizeof(double), cudaMemcpyDeviceToHost, st, "energy readback"));
@@ -331,12 +340,28 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     if (track)
         HY_TRY(xfer(a, &a->h_cnt[1], hy::sstate_count(G), sizeof(int64_t), cudaMemcpyDeviceToHost,
                     st, "support count"));
-    HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+    // within a compiled ansatz whose tables serve the forward gradient, the
+    // gradient the optimiser asks for next is this point's: queue it behind
+    // the energy and wait for the energy alone
+    if (speculate && prog_run && use_hss && a->prog_grad_ok && L > 0) {
+        HY_TRY(cu(cudaEventRecord(a->ev_energy, st), "event"));
+        HY_TRY(hy::prog_grad(a->prog, a->p, a->d_ops, a->d_cs, int64_t(L), sigma, dt,
+                             dt == HY_F32 ? a->d_n2 : nullptr, a->d_ga, st));
+        HY_TRY(xfer(a, a->h_g, a->d_ga, L * sizeof(double), cudaMemcpyDeviceToHost, st,
+                    "gradient readback"));
+        a->spec_pending = true;
+        a->spec_dt = dt;
+        a->spec_theta = th;
+        HY_TRY(cu(cudaEventSynchronize(a->ev_energy), "sync"));
+    } else {
+        HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+    }
     *e = a->h_e[0];
     cnt[0] = a->h_cnt[0];
     cnt[1] = a->h_cnt[1];
     *ok = cnt[0] <= hy::sstate_cap(S);
     if (!*ok) {
+        a->spec_pending = false;
         a->ss_clean[d][0] = false;
         a->prog_support[d] = false;
         return HY_OK;
@@ -359,16 +384,18 @@ hy_status energy_sparse(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     return HY_OK;
 }
 
-// psi = U(theta) |HF>, sigma = H psi, returns E = <psi|sigma>
+// psi = U(theta) |HF>, sigma = H psi, returns E = <psi|sigma>; speculate:
+// the caller will most likely ask for the gradient at th next
 hy_status energy(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
-                 cudaStream_t st, double *e)
+                 cudaStream_t st, double *e, bool speculate = false)
 {
     const int d = di(dt);
     a->sparse_m = -1;
     a->prep_small = false;
+    a->spec_pending = false;
     if (a->cfg.sparse && a->ops.size() < a->sparse_fail_len[d]) {
         bool ok = false;
-        HY_TRY(energy_sparse(a, th, dt, st, e, &ok));
+        HY_TRY(energy_sparse(a, th, dt, st, e, &ok, speculate));
         if (ok) return finish_energy(a, th, dt);
         a->sparse_fail_len[d] = a->ops.size();
     }
@@ -451,6 +478,13 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     if (a->sparse_m < 0) return gradient_dense(a, th, dt, st, g);
     const int d = di(dt);
     hy::SparseState *P = a->ss[d][0], *F = a->ss[d][1], *L = a->ss[d][2], *G = a->ss[d][3];
+    if (a->spec_pending && a->spec_dt == dt && a->spec_theta == th && a->prog_ops == a->ops) {
+        // queued with the energy at this point
+        a->spec_pending = false;
+        HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+        std::copy(a->h_g, a->h_g + j, g.begin());
+        return HY_OK;
+    }
     if (a->prep_small && a->sparse_m <= kPrepareSmall && a->prog && a->prog_grad_ok &&
         a->prog_support[d] && a->prog_ops == a->ops) {
         // the support program's forward gradient: one CTA per angle
@@ -640,10 +674,14 @@ hy_status bfgs(hy_adapt *a, hy_dtype dt, double gtol, int max_steps, cudaStream_
     const size_t j = a->ops.size();
     std::vector<double> x = a->theta, g, gn, pdir(j), xn(j), s(j), y(j), Hy(j);
     double e = 0.0;
-    HY_TRY(energy(a, x, dt, st, &e));
+    HY_TRY(energy(a, x, dt, st, &e, true));
     HY_TRY(gradient(a, x, dt, st, g));
     std::vector<double> &H = a->hinv;
     const int ev_start = a->evals;
+    // a full step's trial point queues its gradient with its energy unless
+    // the last full step was rejected (then it most likely is again);
+    // backtracked trial points always do
+    bool full_ok = true;
     for (int it = 0; it < max_steps; ++it) {
         if (maxabs(g) < gtol) {
             done = true;
@@ -670,12 +708,14 @@ hy_status bfgs(hy_adapt *a, hy_dtype dt, double gtol, int max_steps, cudaStream_
             // rounding floor cannot be told apart from noise: stop trying
             if (stall > 0.0 && -alpha * slope < stall * std::fabs(e)) break;
             for (size_t r = 0; r < j; ++r) xn[r] = x[r] + alpha * pdir[r];
-            HY_TRY(energy(a, xn, dt, st, &en));
+            HY_TRY(energy(a, xn, dt, st, &en, ls > 0 || full_ok));
             tried = true;
             if (en <= e + 1e-4 * alpha * slope) {
                 ok = true;
+                if (ls == 0) full_ok = true;
                 break;
             }
+            if (ls == 0) full_ok = false;
             alpha *= 0.5;
         }
         if (!ok) {
@@ -819,6 +859,8 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
         a->h_g = reinterpret_cast<double *>(static_cast<char *>(a->h_pin) + 64);
     }
     alloc(reinterpret_cast<void **>(&a->d_one), 16);
+    if (s == HY_OK)
+        s = cu(cudaEventCreateWithFlags(&a->ev_energy, cudaEventDisableTiming), "event");
     if (s == HY_OK) {
         unsigned char one[16] = {};
         const double one64 = 1.0;
@@ -889,6 +931,7 @@ hy_status hy_adapt_destroy(hy_adapt *a)
     if (a->h_gs) cudaFreeHost(a->h_gs);
     if (a->h_extra) cudaFreeHost(a->h_extra);
     cudaFree(a->d_one);
+    if (a->ev_energy) cudaEventDestroy(a->ev_energy);
     for (auto &row : a->ss)
         for (hy::SparseState *&x : row) hy::sstate_destroy(x);
     hy::prog_destroy(a->prog);

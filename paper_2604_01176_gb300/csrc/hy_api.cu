@@ -2345,6 +2345,7 @@ hy_status sstate_prepare(SparseState *s, const hy_pool *p, const int32_t *ops, c
 struct SupportProgram {
     const hy_ham *h = nullptr;
     int max_steps = 0;
+    int optin = 0;                // opt-in shared memory per block of its device
     int64_t m = 0, steps = 0;
     int64_t *key = nullptr, *step_len = nullptr;
     // the pair lists of the steps (hy_kernels.cuh, ProgTabs), their counts
@@ -2363,6 +2364,7 @@ struct SupportProgram {
     // (row t's entries at [t * hss_w, t * hss_w + hss_cnt[t]))
     int32_t *hss_cnt = nullptr;
     uint32_t *hss_strs = nullptr;   // the support's alpha and beta string sets
+    double *hss_part = nullptr;     // per-block partial energies of an apply
     uint32_t *hss_col = nullptr;
     double *hss_val = nullptr;
     int64_t hss_cap = 0, hss_w = 0;
@@ -2380,7 +2382,14 @@ hy_status prog_create(const hy_ham *h, int max_steps, SupportProgram **out)
     if (!g) return fail(HY_ERR_OOM, "host allocation failed");
     g->h = h;
     g->max_steps = max_steps;
-    cudaError_t e = cudaMalloc(&g->key, size_t(hy::k::kProgMax) * sizeof(int64_t));
+    // the kernels' shared-memory limits are raised once, on the device the
+    // program is created on (and used on)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&g->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = hy::k::prog_attrs(g->optin);
+    if (e == cudaSuccess) e = cudaMalloc(&g->key, size_t(hy::k::kProgMax) * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMalloc(&g->step_len, size_t(max_steps) * sizeof(int64_t));
     if (e == cudaSuccess)
         e = cudaMalloc(&g->pairs, size_t(max_steps) * hy::k::kProgMax * sizeof(uint32_t));
@@ -2412,6 +2421,7 @@ void prog_destroy(SupportProgram *g)
     cudaFree(g->d_nnz);
     cudaFree(g->hss_cnt);
     cudaFree(g->hss_strs);
+    cudaFree(g->hss_part);
     cudaFree(g->hss_col);
     cudaFree(g->hss_val);
     if (g->h_nnz) cudaFreeHost(g->h_nnz);
@@ -2506,6 +2516,8 @@ hy_status prog_build_hss(SupportProgram *g, const SparseState *s, int64_t max_nn
     const size_t wa = size_t((h->Na + 31) >> 5), wb = size_t((h->Nb + 31) >> 5);
     if (!g->hss_cnt) e = cudaMalloc(&g->hss_cnt, kb * sizeof(int32_t));
     if (e == cudaSuccess && !g->hss_strs) e = cudaMalloc(&g->hss_strs, (wa + wb) * sizeof(uint32_t));
+    if (e == cudaSuccess && !g->hss_part)
+        e = cudaMalloc(&g->hss_part, size_t(h->num_sms) * 16 * sizeof(double));
     if (e == cudaSuccess && !g->d_nnz) e = cudaMalloc(&g->d_nnz, sizeof(int64_t));
     if (e == cudaSuccess && !g->h_nnz) {
         e = cudaMallocHost(&g->h_nnz, sizeof(int64_t));
@@ -2553,9 +2565,10 @@ hy_status prog_build_hss(SupportProgram *g, const SparseState *s, int64_t max_nn
 bool prog_hss_ready(const SupportProgram *g) { return g && g->hss_ok; }
 
 hy_status prog_hss_apply(const SupportProgram *g, const void *psi, void *sigma, hy_dtype dt,
-                         void *stream)
+                         double *dot, void *stream)
 {
-    if (!g || !g->hss_ok || !psi || !sigma) return fail(HY_ERR_ARG, "bad arguments");
+    if (!g || !g->hss_ok || !psi || !sigma || (dot && !g->hss_part))
+        return fail(HY_ERR_ARG, "bad arguments");
     cudaStream_t st = as_stream(stream);
     const double es = dt == HY_F64 ? 8.0 : 4.0;
     // bytes: the stored entries (12 each) and psi / sigma on the support;
@@ -2568,12 +2581,14 @@ hy_status prog_hss_apply(const SupportProgram *g, const void *psi, void *sigma, 
     if (dt == HY_F64)
         HY_CUDA(hy::k::hss_apply<double>(prog_keys(g), g->m, g->hss_cnt, g->hss_w, g->hss_col,
                                          g->hss_val, static_cast<const double *>(psi),
-                                         static_cast<double *>(sigma), g->h->num_sms, st),
+                                         static_cast<double *>(sigma), g->h->num_sms,
+                                         g->hss_part, dot, st),
                 "support Hamiltonian apply");
     else
         HY_CUDA(hy::k::hss_apply<float>(prog_keys(g), g->m, g->hss_cnt, g->hss_w, g->hss_col,
                                         g->hss_val, static_cast<const float *>(psi),
-                                        static_cast<float *>(sigma), g->h->num_sms, st),
+                                        static_cast<float *>(sigma), g->h->num_sms,
+                                        g->hss_part, dot, st),
                 "support Hamiltonian apply");
     return HY_OK;
 }
@@ -2593,6 +2608,7 @@ hy::k::ProgTabs prog_tabs(const SupportProgram *g)
     t.steps = int(g->steps);
     t.ranks = big ? hy::k::kClusterCtas : 1;
     t.chunk = big ? int((g->m + hy::k::kClusterCtas - 1) / hy::k::kClusterCtas) : int(g->m);
+    t.optin = g->optin;
     return t;
 }
 }  // namespace

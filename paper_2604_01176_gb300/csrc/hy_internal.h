@@ -196,11 +196,12 @@ int64_t prog_capacity();
 // H restricted to the program's support, built from s (which lists exactly
 // that support, as after prog_compile): skipped (left unbuilt) when it would
 // hold more than max_nnz entries or its memory cannot be had.  prog_hss_apply
-// writes sigma = H psi on the support only (the rest of sigma untouched).
+// writes sigma = H psi on the support only (the rest of sigma untouched) and,
+// with dot (device) not null, *dot = <psi|sigma> in FP64.
 hy_status prog_build_hss(SupportProgram *g, const SparseState *s, int64_t max_nnz, void *stream);
 bool prog_hss_ready(const SupportProgram *g);
 hy_status prog_hss_apply(const SupportProgram *g, const void *psi, void *sigma, hy_dtype dt,
-                         void *stream);
+                         double *dot, void *stream);
 // compile from s (whose support, m <= prog_capacity() elements, was just
 // listed by a structural sstate_prepare of ops[0..L) (device) with step_len)
 hy_status prog_compile(SupportProgram *g, const SparseState *s, int64_t m, const hy_pool *p,

@@ -389,7 +389,11 @@ struct ProgTabs {
     const int *npairs, *nrest;
     const int *step_l;
     int m, steps, ranks, chunk;
+    int optin;                 // the device's opt-in shared memory per block
 };
+// raises the program kernels' dynamic shared-memory limit on the current
+// device to what an opt-in limit of `optin` bytes per block leaves them
+cudaError_t prog_attrs(int optin);
 // list: the m support elements in the order a structural sv_prepare listed
 // them, step_len its lengths after each of the `steps` rotations; pairs holds
 // steps * m entries, npairs 2 * steps counts (nrest = npairs + steps), step_l
@@ -438,7 +442,9 @@ cudaError_t prog_grad_big(const ProgTabs &g, const double *cs, int L, const T *s
 // serves every evaluation.  hss_fill: the entries of every row (the
 // candidates filtered by the support's alpha and beta string sets first,
 // then by its bitmap; fixed order); hss_apply: sigma[key[t] >> 8] = sum_e
-// val[e] psi[col[e]] for t < m, accumulated in T (sigma untouched elsewhere).
+// val[e] psi[col[e]] for t < m, accumulated in T (sigma untouched elsewhere),
+// and with dot not null also *dot = <psi|sigma> over the support in FP64
+// (partials: one double per block, at most 16 per SM).
 struct HssArgs {
     const int64_t *key;
     int64_t m;
@@ -460,7 +466,7 @@ cudaError_t hss_fill(const HssArgs &a, int64_t *nnz, int num_sms, cudaStream_t s
 template <typename T>
 cudaError_t hss_apply(const int64_t *key, int64_t m, const int32_t *cnt, int64_t stride,
                       const uint32_t *col, const double *val, const T *psi, T *sigma, int num_sms,
-                      cudaStream_t st);
+                      double *partials, double *dot, cudaStream_t st);
 
 // one CTA: g[l] = dE/dtheta_l of psi = U_L .. U_1|HF> in forward mode, f and
 // w scratch sparse vectors (clean), sigma = H psi dense; norm2 (device, or

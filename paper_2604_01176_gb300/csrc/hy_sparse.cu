@@ -59,15 +59,24 @@ __device__ __forceinline__ bool member(const uint32_t *bits, int64_t i)
     return (bits[i >> 5] >> (i & 31)) & 1u;
 }
 
+// sum over the set bits p of mask (n <= 16 orbitals), in ascending order, of
+// base[p * stride]: the loads are independent and issued together, the
+// additions keep the ascending order
+template <typename T>
+__device__ __forceinline__ T sum_mask(const T *base, int stride, uint32_t mask)
+{
+    T v = T(0);
+#pragma unroll
+    for (int p = 0; p < 16; ++p)
+        if ((mask >> p) & 1u) v += base[size_t(p) * stride];
+    return v;
+}
+
+// sum over the occupied orbitals p of mask of V[pp][rs]
 template <typename T>
 __device__ __forceinline__ T sum_diag(const T *V, int n, int nn, uint32_t mask, int rs)
 {
-    T v = T(0);
-    for (uint32_t m = mask; m; m &= m - 1) {
-        const int p = __ffs(m) - 1;
-        v += V[size_t(p * n + p) * nn + rs];
-    }
-    return v;
+    return sum_mask(V + rs, (n + 1) * nn, mask);
 }
 
 // sigma[o] += v; with an output list, o is also listed the first time it is
@@ -145,10 +154,7 @@ k_hpsi_scatter(SparseArgs<T> a)
             } else {
                 const uint32_t u = aexs[e];
                 const int pq = int((u >> 20) & 15) * n + int((u >> 16) & 15);
-                for (uint32_t mm = bm; mm; mm &= mm - 1) {
-                    const int rr = __ffs(mm) - 1;
-                    c += a.V[size_t(pq) * nn + rr * n + rr];
-                }
+                c = sum_mask(a.V + size_t(pq) * nn, n + 1, bm);
                 emit(a, int64_t(u & 0xFFFFu) * Nb + B, ((u >> 31) ? -c : c) * x);
             }
         }
@@ -287,14 +293,7 @@ k_sup_alpha(SupRowsArgs<T> a)
         }
         if (tid < nexa) aexs[tid] = h.aex[A * nexa + tid];
         const uint32_t am = h.astr[A];
-        for (int i = tid; i < nn; i += kSupThreads) {
-            T v = T(0);
-            for (uint32_t mm = am; mm; mm &= mm - 1) {
-                const int p = __ffs(mm) - 1;
-                v += h.V[size_t(p * n + p) * nn + i];
-            }
-            dA[i] = v;
-        }
+        for (int i = tid; i < nn; i += kSupThreads) dA[i] = sum_diag<T>(h.V, n, nn, am, i);
         stage_row(row, h.psi + A * Nb, Nb);
         __syncthreads();
         int64_t mA = 0;
@@ -1674,10 +1673,7 @@ __device__ __forceinline__ void hss_enumerate(const HssArgs &a, int64_t A, int64
         } else {
             const uint32_t u = fa[e];
             const int pq = int((u >> 20) & 15) * n + int((u >> 16) & 15);
-            for (uint32_t mm = bm; mm; mm &= mm - 1) {
-                const int rr = __ffs(mm) - 1;
-                c += a.V[size_t(pq) * nn + rr * n + rr];
-            }
+            c = sum_mask(a.V + size_t(pq) * nn, n + 1, bm);
             take(int64_t(u & 0xFFFFu) * Nb + B, (u >> 31) ? -c : c);
         }
     }
@@ -1862,15 +1858,18 @@ k_hss_total(const int32_t *__restrict__ cnt, int64_t m, int64_t *__restrict__ nn
 }
 
 // one warp per row: sigma[key[t] >> 8] = sum val * psi[col], lanes strided,
-// a fixed-order warp sum
+// a fixed-order warp sum; with partials, also <psi|sigma> over the rows in
+// FP64 (each warp its rows in order, the block's warps in order)
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_hss_apply(const int64_t *__restrict__ key, int64_t m, const int32_t *__restrict__ cnt,
             int64_t stride, const uint32_t *__restrict__ col, const double *__restrict__ val,
-            const T *__restrict__ psi, T *__restrict__ sigma)
+            const T *__restrict__ psi, T *__restrict__ sigma, double *__restrict__ partials)
 {
+    __shared__ double red[8];
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    double dot = 0.0;
     for (int64_t t = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); t < m;
          t += warps) {
         T acc = T(0);
@@ -1878,7 +1877,19 @@ k_hss_apply(const int64_t *__restrict__ key, int64_t m, const int32_t *__restric
         for (int64_t e = t * stride + lane; e < e1; e += 32)
             acc += T(val[e]) * psi[col[e]];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) sigma[key[t] >> 8] = acc;
+        if (lane == 0) {
+            const int64_t d = key[t] >> 8;
+            sigma[d] = acc;
+            dot = fma(double(psi[d]), double(acc), dot);
+        }
+    }
+    if (!partials) return;
+    if (lane == 0) red[threadIdx.x >> 5] = dot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) s += red[w];
+        partials[blockIdx.x] = s;
     }
 }
 
@@ -1903,22 +1914,27 @@ cudaError_t hss_fill(const HssArgs &a, int64_t *nnz, int num_sms, cudaStream_t s
 template <typename T>
 cudaError_t hss_apply(const int64_t *key, int64_t m, const int32_t *cnt, int64_t stride,
                       const uint32_t *col, const double *val, const T *psi, T *sigma, int num_sms,
-                      cudaStream_t st)
+                      double *partials, double *dot, cudaStream_t st)
 {
     if (m < 1) return cudaSuccess;
     int64_t g = (m + 7) / 8;
     if (g > int64_t(num_sms) * 16) g = int64_t(num_sms) * 16;
-    k_hss_apply<T><<<unsigned(g), 256, 0, st>>>(key, m, cnt, stride, col, val, psi, sigma);
+    k_hss_apply<T><<<unsigned(g), 256, 0, st>>>(key, m, cnt, stride, col, val, psi, sigma,
+                                                dot ? partials : nullptr);
     hy::count_launch();
+    if (dot) {
+        k_sv_sum<<<1, 256, 0, st>>>(partials, int(g), dot);
+        hy::count_launch();
+    }
     return cudaGetLastError();
 }
 
 template cudaError_t hss_apply<double>(const int64_t *, int64_t, const int32_t *, int64_t,
                                        const uint32_t *, const double *, const double *,
-                                       double *, int, cudaStream_t);
+                                       double *, int, double *, double *, cudaStream_t);
 template cudaError_t hss_apply<float>(const int64_t *, int64_t, const int32_t *, int64_t,
                                       const uint32_t *, const double *, const float *, float *,
-                                      int, cudaStream_t);
+                                      int, double *, double *, cudaStream_t);
 
 namespace {
 // blocks for a list of about n entries (grid-stride loops cover any count)
@@ -2109,25 +2125,46 @@ cudaError_t prog_compile(const int64_t *list, int64_t m, const int64_t *step_len
 }
 
 namespace {
+// static shared memory of a program kernel: its ProgSteps and reduction
+// slots, at most sizeof(ProgSteps<T>) + 512 bytes
+template <typename T>
+constexpr size_t prog_static() { return sizeof(ProgSteps<T>) + 512; }
+
 // dynamic shared memory of a program launch: the vectors (vec bytes) and as
-// many staged pair words (*cap) as the block's opt-in limit leaves beside
-// the kernel's static shared memory (its ProgSteps and reduction slots, at
-// most sizeof(ProgSteps<T>) + 512 bytes)
-template <typename T, typename K>
-cudaError_t prog_smem(K kernel, size_t vec, size_t *smem, int *cap)
+// many staged pair words (*cap) as the block's opt-in limit leaves beside the
+// kernel's static shared memory (prog_attrs has raised the kernels' limit)
+template <typename T>
+cudaError_t prog_smem(const ProgTabs &g, size_t vec, size_t *smem, int *cap)
 {
-    int dev = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return e;
-    const size_t stat = sizeof(ProgSteps<T>) + 512;
-    if (size_t(optin) < stat + vec) return cudaErrorInvalidValue;
-    const size_t words = (size_t(optin) - stat - vec) / 4;
+    const size_t stat = prog_static<T>();
+    if (g.optin < 0 || size_t(g.optin) < stat + vec) return cudaErrorInvalidValue;
+    const size_t words = (size_t(g.optin) - stat - vec) / 4;
     *cap = int(words);
     *smem = vec + words * 4;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(*smem));
+    return cudaSuccess;
+}
+
+template <typename T, typename K>
+cudaError_t prog_attr(K kernel, int optin)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - int(prog_static<T>()));
 }
 }  // namespace
+
+cudaError_t prog_attrs(int optin)
+{
+    if (optin < int(prog_static<double>()) + 1024) return cudaErrorInvalidValue;
+    cudaError_t e = prog_attr<double>(k_prog_prepare<double>, optin);
+    if (e == cudaSuccess) e = prog_attr<float>(k_prog_prepare<float>, optin);
+    if (e == cudaSuccess) e = prog_attr<double>(k_prog_grad<double>, optin);
+    if (e == cudaSuccess) e = prog_attr<float>(k_prog_grad<float>, optin);
+    if (e == cudaSuccess) e = prog_attr<double>(k_prog_prepare_big<double>, optin);
+    if (e == cudaSuccess) e = prog_attr<float>(k_prog_prepare_big<float>, optin);
+    if (e == cudaSuccess) e = prog_attr<double>(k_prog_grad_big<double>, optin);
+    if (e == cudaSuccess) e = prog_attr<float>(k_prog_grad_big<float>, optin);
+    return e;
+}
 
 template <typename T>
 cudaError_t prog_prepare(const ProgTabs &g, const double *cs, bool renorm, double *norm2, T *v,
@@ -2138,7 +2175,7 @@ cudaError_t prog_prepare(const ProgTabs &g, const double *cs, bool renorm, doubl
         return cudaErrorInvalidValue;
     size_t smem = 0;
     int cap = 0;
-    const cudaError_t e = prog_smem<T>(k_prog_prepare<T>, size_t(g.m) * sizeof(T), &smem, &cap);
+    const cudaError_t e = prog_smem<T>(g, size_t(g.m) * sizeof(T), &smem, &cap);
     if (e != cudaSuccess) return e;
     k_prog_prepare<T><<<1, kProgThreads, smem, st>>>(g, cs, renorm ? 1 : 0, norm2, v, cap);
     hy::count_launch();
@@ -2154,7 +2191,7 @@ cudaError_t prog_grad(const ProgTabs &g, const double *cs, int L, const T *sigma
         return cudaErrorInvalidValue;
     size_t smem = 0;
     int cap = 0;
-    const cudaError_t e = prog_smem<T>(k_prog_grad<T>, 2 * size_t(g.m) * sizeof(T), &smem, &cap);
+    const cudaError_t e = prog_smem<T>(g, 2 * size_t(g.m) * sizeof(T), &smem, &cap);
     if (e != cudaSuccess) return e;
     k_prog_grad<T><<<unsigned(L), kProgThreads, smem, st>>>(g, cs, sigma, norm2, gout, cap);
     hy::count_launch();
@@ -2214,8 +2251,7 @@ cudaError_t prog_prepare_big(const ProgTabs &g, const double *cs, bool renorm, d
     if (!big_tabs_ok(g)) return cudaErrorInvalidValue;
     size_t smem = 0;
     int cap = 0;
-    const cudaError_t e = prog_smem<T>(k_prog_prepare_big<T>, size_t(g.chunk) * sizeof(T), &smem,
-                                       &cap);
+    const cudaError_t e = prog_smem<T>(g, size_t(g.chunk) * sizeof(T), &smem, &cap);
     if (e != cudaSuccess) return e;
     k_prog_prepare_big<T><<<kClusterCtas, 1024, smem, st>>>(g, cs, renorm ? 1 : 0, norm2, v, cap);
     hy::count_launch();
@@ -2229,8 +2265,7 @@ cudaError_t prog_grad_big(const ProgTabs &g, const double *cs, int L, const T *s
     if (!big_tabs_ok(g) || L < 1) return cudaErrorInvalidValue;
     size_t smem = 0;
     int cap = 0;
-    const cudaError_t e = prog_smem<T>(k_prog_grad_big<T>, 2 * size_t(g.chunk) * sizeof(T), &smem,
-                                       &cap);
+    const cudaError_t e = prog_smem<T>(g, 2 * size_t(g.chunk) * sizeof(T), &smem, &cap);
     if (e != cudaSuccess) return e;
     k_prog_grad_big<T><<<unsigned(kClusterCtas * L), 1024, smem, st>>>(g, cs, sigma, norm2, gout,
                                                                        cap);
