@@ -107,6 +107,7 @@ struct hy_ham {
     uint32_t *d_bex = nullptr;   // beta excitations string-major [Nb][nexb]
     uint8_t *d_ainv = nullptr;   // inverse alpha excitation positions
     uint32_t *d_binom = nullptr;
+    uint16_t *d_rank16 = nullptr;   // [1 << n] colex rank of every n-bit string
     DevCsr<double> Ma64, Mb64;
     DevCsr<float> Ma32, Mb32;
     double *d_V64 = nullptr;
@@ -768,6 +769,15 @@ hy_status finish_ham(hy_ham *h, hy_ham **out)
     std::vector<uint32_t> binom(33 * 33);
     for (int i = 0; i < 33; ++i)
         for (int j = 0; j < 33; ++j) binom[i * 33 + j] = hy::binom(i, j);
+    // colex rank of every n-bit string (sum over its set bits, the i-th from
+    // the bottom at position p, of C(p, i + 1)), one string at a time from
+    // the string without its top bit
+    std::vector<uint16_t> rank16(size_t(1) << n_orb, 0);
+    for (uint32_t msk = 1; msk < (1u << n_orb); ++msk) {
+        const int top = 31 - __builtin_clz(msk);
+        rank16[msk] = uint16_t(rank16[msk & ~(1u << top)] +
+                               hy::binom(top, __builtin_popcount(msk)));
+    }
     std::vector<float> V32(h->kt.V.begin(), h->kt.V.end());
 
     hy_status s = HY_OK;
@@ -782,6 +792,7 @@ hy_status finish_ham(hy_ham *h, hy_ham **out)
     up(ar.upload(&h->d_bexT, bexT.data(), bexT.size()), "upload beta excitations");
     up(ar.upload(&h->d_bex, h->B.ex.data(), h->B.ex.size()), "upload beta excitations");
     up(ar.upload(&h->d_binom, binom.data(), binom.size()), "upload binomials");
+    up(ar.upload(&h->d_rank16, rank16.data(), rank16.size()), "upload string ranks");
     up(ar.upload(&h->d_V64, h->kt.V.data(), h->kt.V.size()), "upload V");
     up(ar.upload(&h->d_V32, V32.data(), V32.size()), "upload V32");
     up(ar.upload(&h->d_h1, h1, size_t(n_orb) * n_orb), "upload h1");
@@ -1605,6 +1616,7 @@ hy_status hy_pool_gradients_sparse(const hy_ham *h, const hy_pool *p, const void
         a.partials = reinterpret_cast<double *>(static_cast<char *>(hm->ws) + L.partials);
         a.desc = p->d_desc; a.ops = ops_or_null; a.n_ops = n_ops;
         a.astr = h->d_astr; a.bstr = h->d_bstr; a.binom33 = h->d_binom; a.n = h->n;
+        a.rank16 = h->d_rank16;
         a.Nb = h->Nb; a.g = g_out; a.K = int64_t(p->ops.size()); a.bad = p->d_bad;
         a.qubit = p->qubit;
     };
@@ -2293,6 +2305,7 @@ hy_status sstate_excite(SparseState *s, const hy_pool *p, int64_t k, double thet
     o.astr = h->d_astr;
     o.bstr = h->d_bstr;
     o.binom33 = h->d_binom;
+    o.rank16 = h->d_rank16;
     o.n = h->n;
     o.Nb = h->Nb;
     o.qubit = p->qubit;
@@ -2326,6 +2339,7 @@ hy_status sstate_prepare(SparseState *s, const hy_pool *p, const int32_t *ops, c
     o.astr = h->d_astr;
     o.bstr = h->d_bstr;
     o.binom33 = h->d_binom;
+    o.rank16 = h->d_rank16;
     o.n = h->n;
     o.Nb = h->Nb;
     o.qubit = p->qubit;
@@ -2448,6 +2462,7 @@ hy::k::SvOpArgs sv_op_args(const hy_ham *h, const hy_pool *p)
     o.astr = h->d_astr;
     o.bstr = h->d_bstr;
     o.binom33 = h->d_binom;
+    o.rank16 = h->d_rank16;
     o.n = h->n;
     o.Nb = h->Nb;
     o.qubit = p->qubit;
@@ -2687,6 +2702,7 @@ hy_status sstate_grad_forward(SparseState *f, SparseState *w, const hy_pool *p, 
     o.astr = h->d_astr;
     o.bstr = h->d_bstr;
     o.binom33 = h->d_binom;
+    o.rank16 = h->d_rank16;
     o.n = h->n;
     o.Nb = h->Nb;
     o.qubit = p->qubit;
@@ -2834,6 +2850,7 @@ hy_status sstate_gradients(const SparseState *sc, const void *lam, const hy_pool
         a.chunks = chunks; a.partials = s->partials;
         a.desc = p->d_desc; a.ops = ops; a.n_ops = n_ops;
         a.astr = h->d_astr; a.bstr = h->d_bstr; a.binom33 = h->d_binom; a.n = h->n;
+        a.rank16 = h->d_rank16;
         a.Nb = h->Nb; a.g = g; a.K = int64_t(p->ops.size()); a.bad = p->d_bad;
         a.qubit = p->qubit;
     };

@@ -273,6 +273,7 @@ struct SparseGradArgs {
     const int32_t *ops;      // operator list or nullptr (all)
     int64_t n_ops;
     const uint32_t *astr, *bstr, *binom33;
+    const uint16_t *rank16;  // [1 << n] colex rank of every n-bit string
     int n;
     int64_t Nb;
     double *g;
@@ -332,6 +333,7 @@ struct SVec {
 struct SvOpArgs {
     const int32_t *desc;         // [K][11]
     const uint32_t *astr, *bstr, *binom33;
+    const uint16_t *rank16;      // [1 << n] colex rank of every n-bit string
     int n;
     int64_t Nb;
     int qubit;                   // 1: the pool's operators are qubit excitations (no sign)

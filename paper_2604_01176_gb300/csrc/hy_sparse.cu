@@ -415,6 +415,14 @@ __device__ __forceinline__ uint32_t rank_bits(uint32_t m, const uint32_t (*C)[33
     return r;
 }
 
+// index of the determinant with spin strings u = alpha | beta << n, from the
+// table of colex ranks of all n-bit strings (the same rank as rank_bits)
+__device__ __forceinline__ int64_t det_index(const uint16_t *__restrict__ r16, uint64_t u, int n,
+                                             uint64_t lowm, int64_t Nb)
+{
+    return int64_t(__ldg(r16 + (u & lowm))) * Nb + __ldg(r16 + (u >> n));
+}
+
 // Apply an operator string (application order; codes 2*mode + dagger) to a
 // determinant mask; false if it annihilates it.  Sign: (-1)^(occupied modes
 // below) per fermionic operator (Jordan-Wigner, blocked order); qubit
@@ -469,9 +477,6 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_grad_sparse(SparseGradArgs<T> a)
 {
-    __shared__ uint32_t C[33][33];
-    for (int i = threadIdx.x; i < 33 * 33; i += blockDim.x) C[i / 33][i % 33] = a.binom33[i];
-    __syncthreads();
     const int n = a.n;
     const uint64_t lowm = (1ull << n) - 1;
     const int64_t m = list_len(a.d_m, a.m, a.cap);
@@ -495,16 +500,14 @@ k_grad_sparse(SparseGradArgs<T> a)
             uint64_t o = mask;
             int sg = 1;
             if (apply_string(fw, len, o, sg, a.qubit)) {       // d is the domain end
-                const int64_t d2 = int64_t(rank_bits(uint32_t(o & lowm), C)) * a.Nb +
-                                   rank_bits(uint32_t(o >> n), C);
+                const int64_t d2 = det_index(a.rank16, o, n, lowm, a.Nb);
                 tot += sg * (double(a.sigma[d2]) * x - double(a.sigma[d]) * double(a.psi[d2]));
                 continue;
             }
             o = mask;
             sg = 1;
             if (apply_string(bw, len, o, sg, a.qubit)) {       // d is the image end
-                const int64_t d0 = int64_t(rank_bits(uint32_t(o & lowm), C)) * a.Nb +
-                                   rank_bits(uint32_t(o >> n), C);
+                const int64_t d0 = det_index(a.rank16, o, n, lowm, a.Nb);
                 const bool listed = a.bits ? member(a.bits, d0) : a.psi[d0] != T(0);
                 if (!listed) tot -= sg * double(a.sigma[d0]) * x;
             }
@@ -597,14 +600,14 @@ __device__ __forceinline__ void sv_rotate(SVec<T> &x, const SvOpArgs &o, int k, 
         int64_t dom, img, fresh;
         if (apply_string(fw, len, u, sg, o.qubit)) {
             dom = d;
-            img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+            img = det_index(o.rank16, u, n, lowm, o.Nb);
             fresh = member(x.bits, img) ? -1 : img;
         } else {
             u = mask;
             sg = 1;
             if (!apply_string(bw, len, u, sg, o.qubit)) continue;    // C and C^dagger annihilate d
             img = d;
-            dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+            dom = det_index(o.rank16, u, n, lowm, o.Nb);
             if (member(x.bits, dom)) continue;              // the domain end rotates the pair
             fresh = dom;
         }
@@ -716,14 +719,14 @@ __device__ void blk_rotate(SVec<T> &x, const SvOpArgs &o, int k, int ci, T c, T 
         int64_t dom, img, fresh;
         if (apply_string(fw, len, u, sg, o.qubit)) {
             dom = d;
-            img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+            img = det_index(o.rank16, u, n, lowm, o.Nb);
             fresh = member(x.bits, img) ? -1 : img;
         } else {
             u = mask;
             sg = 1;
             if (!apply_string(bw, len, u, sg, o.qubit)) continue;
             img = d;
-            dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+            dom = det_index(o.rank16, u, n, lowm, o.Nb);
             if (member(x.bits, dom)) continue;
             fresh = dom;
         }
@@ -754,14 +757,14 @@ __device__ void blk_generator(const SVec<T> &f, SVec<T> &w, const SvOpArgs &o, i
         int64_t tgt;
         T val;
         if (apply_string(fw, len, u, sg, o.qubit)) {          // C|d> = sg |tgt>
-            tgt = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+            tgt = det_index(o.rank16, u, n, lowm, o.Nb);
             val = sg > 0 ? f.v[d] : -f.v[d];
         } else {
             u = mask;
             sg = 1;
             if (!apply_string(bw, len, u, sg, o.qubit)) continue;
             // -C^dagger |d> = -sg |tgt>
-            tgt = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb + rank_bits(uint32_t(u >> n), C);
+            tgt = det_index(o.rank16, u, n, lowm, o.Nb);
             val = sg > 0 ? -f.v[d] : f.v[d];
         }
         if (!member(w.bits, tgt)) blk_list(w, tgt);  // tgt is reached from d alone
@@ -1072,8 +1075,7 @@ k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t 
         int sg = 1;
         bool escape = false;
         if (apply_string(fw, len, u, sg, o.qubit)) {
-            const int64_t img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
-                                rank_bits(uint32_t(u >> n), C);
+            const int64_t img = det_index(o.rank16, u, n, lowm, o.Nb);
             p = prog_find(key, m, img);
             neg = sg < 0;
             escape = p < 0;
@@ -1084,8 +1086,7 @@ k_prog_tables(const int64_t *__restrict__ key, int m, SvOpArgs o, const int32_t 
             u = mask;
             sg = 1;
             if (apply_string(bw, len, u, sg, o.qubit)) {
-                const int64_t dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
-                                    rank_bits(uint32_t(u >> n), C);
+                const int64_t dom = det_index(o.rank16, u, n, lowm, o.Nb);
                 escape = prog_find(key, m, dom) < 0;
             }
         }
@@ -1453,8 +1454,7 @@ k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
             int sg = 1;
             bool escape = false;
             if (apply_string(fw, len, u, sg, o.qubit)) {
-                const int64_t img = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
-                                    rank_bits(uint32_t(u >> n), C);
+                const int64_t img = det_index(o.rank16, u, n, lowm, o.Nb);
                 if (member(bits, img)) {
                     p = idx_map[img];
                     neg = sg < 0;
@@ -1466,8 +1466,7 @@ k_prog_tables_big(const int64_t *__restrict__ key, int m, SvOpArgs o,
                 u = mask;
                 sg = 1;
                 if (apply_string(bw, len, u, sg, o.qubit)) {
-                    const int64_t dom = int64_t(rank_bits(uint32_t(u & lowm), C)) * o.Nb +
-                                        rank_bits(uint32_t(u >> n), C);
+                    const int64_t dom = det_index(o.rank16, u, n, lowm, o.Nb);
                     escape = !member(bits, dom);
                 }
             }
