@@ -960,7 +960,38 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     // (float gradients differ from it by ~1e-6 relative, enough to reorder
     // near-equal operators)
     const hy_dtype sdt = a->screen_f64_next ? HY_F64 : bulk;
-    if (a->valid_dt != sdt || a->valid_theta != a->theta || !a->sigma_full[di(sdt)]) {
+    if (a->valid_dt == sdt && a->valid_theta == a->theta && !a->sigma_full[di(sdt)] &&
+        a->sparse_m >= 0) {
+        // psi (sparse) is this point's: only sigma beyond psi's support is
+        // missing (formed on the support by the last evaluation): the
+        // scatter, listing sigma's support while it fits its list (as the
+        // evaluation would), or the dense sweep once the scatter's atomics
+        // cost more
+        const int d = di(sdt);
+        hy::SparseState *S = a->ss[d][0], *G = a->ss[d][3];
+        const double est = double(std::max<int64_t>(a->sparse_m, 1)) * double(a->conn);
+        a->sig_support[d] = false;
+        a->sig_listed[d] = false;
+        a->sigma_full[d] = true;
+        if (double(a->sparse_m) * kScatterPerDense[d] > double(a->N)) {
+            a->ss_clean[d][3] = false;
+            HY_TRY(hy_apply_h(a->h, a->buf[d][0], a->buf[d][1], sdt, st));
+        } else if (est <= double(hy::sstate_cap(G))) {
+            HY_TRY(hy::sstate_reset(G, !a->ss_clean[d][3], false, st));
+            a->ss_clean[d][3] = true;
+            HY_TRY(hy::sstate_apply_h(S, G, a->buf[d][1], st));
+            a->h_cnt[1] = 0;
+            HY_TRY(xfer(a, &a->h_cnt[1], hy::sstate_count(G), sizeof(int64_t),
+                        cudaMemcpyDeviceToHost, st, "support count"));
+            HY_TRY(cu(cudaStreamSynchronize(st), "sync"));
+            a->sig_listed[d] = a->h_cnt[1] <= hy::sstate_cap(G);
+            a->sig_count[d] = a->h_cnt[1];
+            if (a->sig_listed[d]) hy::sstate_set_hint(G, a->sig_count[d]);
+            else a->ss_clean[d][3] = false;
+        } else {
+            HY_TRY(full_sigma_sparse(a, d, st));
+        }
+    } else if (a->valid_dt != sdt || a->valid_theta != a->theta || !a->sigma_full[di(sdt)]) {
         double e;
         a->want_full_sigma = true;           // the screen reads sigma beyond psi's support
         const hy_status rs = energy(a, a->theta, sdt, st, &e);
