@@ -108,6 +108,7 @@ struct hy_adapt {
                                          // (angles on the device for its theta)
     double *d_n2 = nullptr;       // tracked squared norm (float renormalisation)
     double *h_cs = nullptr, *d_cs = nullptr;   // cos, sin of the ansatz angles (pinned / device)
+    int32_t *h_ops = nullptr;                  // pinned staging of the ansatz's operators
     // pinned readback slots of an evaluation (energy, support counts, the
     // ansatz gradient): its copies are queued and waited for once
     void *h_pin = nullptr;
@@ -582,13 +583,17 @@ hy_status gradient(hy_adapt *a, const std::vector<double> &th, hy_dtype dt,
     return gradient_dense(a, th, dt, st, g);   // a list overflowed: redo densely
 }
 
-hy_status upload_ops(hy_adapt *a, cudaStream_t st)
+// the ansatz's operators to the device, staged in pinned memory.  With wait
+// false the copy is only queued: the caller's kernels that read them run on
+// the same stream, and the staging slot is not written again before the
+// stream has been synchronised (an ADAPT step's evaluations synchronise it)
+hy_status upload_ops(hy_adapt *a, cudaStream_t st, bool wait = true)
 {
-    std::vector<int32_t> o(a->ops.begin(), a->ops.end());
-    if (o.empty()) return HY_OK;
-    HY_TRY(xfer(a, a->d_ops, o.data(), o.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st,
+    if (a->ops.empty()) return HY_OK;
+    for (size_t l = 0; l < a->ops.size(); ++l) a->h_ops[l] = int32_t(a->ops[l]);
+    HY_TRY(xfer(a, a->d_ops, a->h_ops, a->ops.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st,
                 "upload ops"));
-    return cu(cudaStreamSynchronize(st), "sync");
+    return wait ? cu(cudaStreamSynchronize(st), "sync") : HY_OK;
 }
 
 double dotv(const std::vector<double> &x, const std::vector<double> &y)
@@ -848,6 +853,7 @@ hy_status hy_adapt_create(const hy_ham *h, const hy_pool *p, const hy_adapt_conf
     alloc(reinterpret_cast<void **>(&a->d_n2), 8);
     alloc(reinterpret_cast<void **>(&a->d_cs), size_t(c.max_iter) * 16);
     if (s == HY_OK) s = cu(cudaMallocHost(&a->h_cs, size_t(c.max_iter) * 16), "pinned angles");
+    if (s == HY_OK) s = cu(cudaMallocHost(&a->h_ops, size_t(c.max_iter) * 4), "pinned ops");
     if (s == HY_OK)
         s = cu(cudaMallocHost(&a->h_pin, 64 + size_t(c.max_iter) * sizeof(double)), "pinned readbacks");
     if (s == HY_OK) s = cu(cudaMallocHost(&a->h_gs, size_t(a->K) * 8 + 8), "pinned screen");
@@ -927,6 +933,7 @@ hy_status hy_adapt_destroy(hy_adapt *a)
     cudaFree(a->d_n2);
     cudaFree(a->d_cs);
     if (a->h_cs) cudaFreeHost(a->h_cs);
+    if (a->h_ops) cudaFreeHost(a->h_ops);
     if (a->h_pin) cudaFreeHost(a->h_pin);
     if (a->h_gs) cudaFreeHost(a->h_gs);
     if (a->h_extra) cudaFreeHost(a->h_extra);
@@ -1238,7 +1245,7 @@ hy_status hy_adapt_step(hy_adapt *a, hy_adapt_record *rec, void *stream)
     H[j * (j + 1) + j] = 1.0;
     a->hinv = H;
     if (j == 0) a->hinv_fresh = true;
-    HY_TRY(upload_ops(a, st));
+    HY_TRY(upload_ops(a, st, false));
     double e = 0.0;
     a->f64_settled = false;
     if (bulk == HY_F64) {

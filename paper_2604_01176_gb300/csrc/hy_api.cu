@@ -2379,6 +2379,7 @@ struct SupportProgram {
     int32_t *hss_cnt = nullptr;
     uint32_t *hss_strs = nullptr;   // the support's alpha and beta string sets
     double *hss_part = nullptr;     // per-block partial energies of an apply
+    unsigned *hss_done = nullptr;   // its blocks' finish counter (zero between applies)
     uint32_t *hss_col = nullptr;
     double *hss_val = nullptr;
     int64_t hss_cap = 0, hss_w = 0;
@@ -2436,6 +2437,7 @@ void prog_destroy(SupportProgram *g)
     cudaFree(g->hss_cnt);
     cudaFree(g->hss_strs);
     cudaFree(g->hss_part);
+    cudaFree(g->hss_done);
     cudaFree(g->hss_col);
     cudaFree(g->hss_val);
     if (g->h_nnz) cudaFreeHost(g->h_nnz);
@@ -2533,6 +2535,10 @@ hy_status prog_build_hss(SupportProgram *g, const SparseState *s, int64_t max_nn
     if (e == cudaSuccess && !g->hss_strs) e = cudaMalloc(&g->hss_strs, (wa + wb) * sizeof(uint32_t));
     if (e == cudaSuccess && !g->hss_part)
         e = cudaMalloc(&g->hss_part, size_t(h->num_sms) * 16 * sizeof(double));
+    if (e == cudaSuccess && !g->hss_done) {
+        e = cudaMalloc(&g->hss_done, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->hss_done, 0, sizeof(unsigned), st);
+    }
     if (e == cudaSuccess && !g->d_nnz) e = cudaMalloc(&g->d_nnz, sizeof(int64_t));
     if (e == cudaSuccess && !g->h_nnz) {
         e = cudaMallocHost(&g->h_nnz, sizeof(int64_t));
@@ -2582,7 +2588,7 @@ bool prog_hss_ready(const SupportProgram *g) { return g && g->hss_ok; }
 hy_status prog_hss_apply(const SupportProgram *g, const void *psi, void *sigma, hy_dtype dt,
                          double *dot, void *stream)
 {
-    if (!g || !g->hss_ok || !psi || !sigma || (dot && !g->hss_part))
+    if (!g || !g->hss_ok || !psi || !sigma || (dot && (!g->hss_part || !g->hss_done)))
         return fail(HY_ERR_ARG, "bad arguments");
     cudaStream_t st = as_stream(stream);
     const double es = dt == HY_F64 ? 8.0 : 4.0;
@@ -2597,13 +2603,13 @@ hy_status prog_hss_apply(const SupportProgram *g, const void *psi, void *sigma, 
         HY_CUDA(hy::k::hss_apply<double>(prog_keys(g), g->m, g->hss_cnt, g->hss_w, g->hss_col,
                                          g->hss_val, static_cast<const double *>(psi),
                                          static_cast<double *>(sigma), g->h->num_sms,
-                                         g->hss_part, dot, st),
+                                         g->hss_part, g->hss_done, dot, st),
                 "support Hamiltonian apply");
     else
         HY_CUDA(hy::k::hss_apply<float>(prog_keys(g), g->m, g->hss_cnt, g->hss_w, g->hss_col,
                                         g->hss_val, static_cast<const float *>(psi),
                                         static_cast<float *>(sigma), g->h->num_sms,
-                                        g->hss_part, dot, st),
+                                        g->hss_part, g->hss_done, dot, st),
                 "support Hamiltonian apply");
     return HY_OK;
 }

@@ -446,7 +446,8 @@ cudaError_t prog_grad_big(const ProgTabs &g, const double *cs, int L, const T *s
 // then by its bitmap; fixed order); hss_apply: sigma[key[t] >> 8] = sum_e
 // val[e] psi[col[e]] for t < m, accumulated in T (sigma untouched elsewhere),
 // and with dot not null also *dot = <psi|sigma> over the support in FP64
-// (partials: one double per block, at most 16 per SM).
+// (partials: one double per block, at most 16 per SM; done: a counter that
+// is zero between launches, the last block to finish adds the partials).
 struct HssArgs {
     const int64_t *key;
     int64_t m;
@@ -468,7 +469,7 @@ cudaError_t hss_fill(const HssArgs &a, int64_t *nnz, int num_sms, cudaStream_t s
 template <typename T>
 cudaError_t hss_apply(const int64_t *key, int64_t m, const int32_t *cnt, int64_t stride,
                       const uint32_t *col, const double *val, const T *psi, T *sigma, int num_sms,
-                      double *partials, double *dot, cudaStream_t st);
+                      double *partials, unsigned *done, double *dot, cudaStream_t st);
 
 // one CTA: g[l] = dE/dtheta_l of psi = U_L .. U_1|HF> in forward mode, f and
 // w scratch sparse vectors (clean), sigma = H psi dense; norm2 (device, or

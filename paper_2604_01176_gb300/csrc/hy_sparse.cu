@@ -1857,15 +1857,19 @@ k_hss_total(const int32_t *__restrict__ cnt, int64_t m, int64_t *__restrict__ nn
 }
 
 // one warp per row: sigma[key[t] >> 8] = sum val * psi[col], lanes strided,
-// a fixed-order warp sum; with partials, also <psi|sigma> over the rows in
-// FP64 (each warp its rows in order, the block's warps in order)
+// a fixed-order warp sum; with partials, also *dot = <psi|sigma> over the
+// rows in FP64 (each warp its rows in order, the block's warps in order, then
+// the last block to finish adds the blocks' partials in block order, as
+// k_sv_sum would, and re-arms *done for the next launch)
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_hss_apply(const int64_t *__restrict__ key, int64_t m, const int32_t *__restrict__ cnt,
             int64_t stride, const uint32_t *__restrict__ col, const double *__restrict__ val,
-            const T *__restrict__ psi, T *__restrict__ sigma, double *__restrict__ partials)
+            const T *__restrict__ psi, T *__restrict__ sigma, double *__restrict__ partials,
+            unsigned *__restrict__ done, double *__restrict__ out)
 {
     __shared__ double red[8];
+    __shared__ bool last;
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
     double dot = 0.0;
@@ -1889,6 +1893,18 @@ k_hss_apply(const int64_t *__restrict__ key, int64_t m, const int32_t *__restric
         double s = 0.0;
         for (int w = 0; w < int(blockDim.x >> 5); ++w) s += red[w];
         partials[blockIdx.x] = s;
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int b = threadIdx.x; b < int(gridDim.x); b += blockDim.x) s += __ldcg(partials + b);
+    s = block_sum_d(s);
+    if (threadIdx.x == 0) {
+        *out = s;
+        *done = 0u;
     }
 }
 
@@ -1913,27 +1929,25 @@ cudaError_t hss_fill(const HssArgs &a, int64_t *nnz, int num_sms, cudaStream_t s
 template <typename T>
 cudaError_t hss_apply(const int64_t *key, int64_t m, const int32_t *cnt, int64_t stride,
                       const uint32_t *col, const double *val, const T *psi, T *sigma, int num_sms,
-                      double *partials, double *dot, cudaStream_t st)
+                      double *partials, unsigned *done, double *dot, cudaStream_t st)
 {
     if (m < 1) return cudaSuccess;
+    if (dot && (!partials || !done)) return cudaErrorInvalidValue;
     int64_t g = (m + 7) / 8;
     if (g > int64_t(num_sms) * 16) g = int64_t(num_sms) * 16;
     k_hss_apply<T><<<unsigned(g), 256, 0, st>>>(key, m, cnt, stride, col, val, psi, sigma,
-                                                dot ? partials : nullptr);
+                                                dot ? partials : nullptr, done, dot);
     hy::count_launch();
-    if (dot) {
-        k_sv_sum<<<1, 256, 0, st>>>(partials, int(g), dot);
-        hy::count_launch();
-    }
     return cudaGetLastError();
 }
 
 template cudaError_t hss_apply<double>(const int64_t *, int64_t, const int32_t *, int64_t,
                                        const uint32_t *, const double *, const double *,
-                                       double *, int, double *, double *, cudaStream_t);
+                                       double *, int, double *, unsigned *, double *,
+                                       cudaStream_t);
 template cudaError_t hss_apply<float>(const int64_t *, int64_t, const int32_t *, int64_t,
                                       const uint32_t *, const double *, const float *, float *,
-                                      int, double *, double *, cudaStream_t);
+                                      int, double *, unsigned *, double *, cudaStream_t);
 
 namespace {
 // blocks for a list of about n entries (grid-stride loops cover any count)
