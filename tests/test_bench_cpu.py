@@ -47,6 +47,25 @@ def test_roofline_picks_the_longest_class_with_known_work(bench):
     assert r["traffic"] is None
 
 
+def test_timed_region_records_the_roofline_class_only(bench):
+    """The class the timed region records is the one the roofline reports
+    from a fully recorded warm-up job, and the roofline built from a
+    one-class record names the warm-up's dominant class."""
+    peaks = {"hbm_gbs": 6696.8}
+    warm = empty_prof(bench)
+    warm["sparse_excite"] = prof_entry(210, 9.0)          # longest, no known work
+    warm["hpsi_sparse"] = prof_entry(105, 5.0, bytes_=105 * 49.0e6)
+    warm["screen_sparse"] = prof_entry(10, 2.8)
+    warm["reduce"] = prof_entry(1, 0.01, bytes_=1.0e6)
+    assert bench.roofline_class(warm) == "hpsi_sparse"
+    assert bench.roofline_class(empty_prof(bench)) is None
+    timed = empty_prof(bench)
+    timed["hpsi_sparse"] = prof_entry(525, 26.0, bytes_=525 * 49.0e6)
+    r = bench.step_roofline(timed, peaks, "measured", 80.5, dominant="sparse_excite")
+    assert r["kernel_class"] == "hpsi_sparse" and r["dominant_class"] == "sparse_excite"
+    assert math.isclose(r["achieved"], round(525 * 49.0e6 / 26.0e-3 / 1e9, 1))
+
+
 def test_roofline_alu_class_uses_flops(bench):
     prof = empty_prof(bench)
     prof["hpsi"] = prof_entry(2, 400.0, bytes_=2 * 1.3e9, flops=2 * 20.0e12)
