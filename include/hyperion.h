@@ -702,12 +702,14 @@ typedef struct {
                              vectors on the support); when the list overflows
                              the evaluation is redone with the dense sweeps,
                              which stay in use while the ansatz is at least as
-                             long.  Supports of up to 12,288 determinants
-                             are prepared by one CTA, and after each append
-                             the ansatz is compiled into pairings of its
-                             support, so that the iteration's further
+                             long.  After each append an ansatz whose
+                             support holds at most 65,536 determinants is
+                             compiled into per-rotation lists of the pairs
+                             of its support, so that the iteration's further
                              evaluations and forward-mode gradients run on
-                             shared-memory vectors.  While (pool size) x
+                             vectors in shared memory (one CTA's up to
+                             12,288 determinants, an 8-CTA cluster's
+                             beyond).  While (pool size) x
                              (support) <= 5e9 the whole pool is screened
                              exactly even when a ranker is attached (its
                              pairs still train it).
